@@ -1,0 +1,243 @@
+"""Python face of the CPU oracle (``slrme_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product path never imports this
+module.  Every function is a thin numpy <-> C marshalling wrapper; the
+arithmetic, with its citations to the paper, lives in the C file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "slrme_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, IEEE arithmetic, no contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _lib.oracle_i128_to_double_parts.restype = ctypes.c_double
+            _lib.oracle_i128_to_double_parts.argtypes = [ctypes.c_int64, ctypes.c_uint64]
+            _lib.oracle_rgbe_from_float.restype = ctypes.c_int
+            _lib.oracle_base_roundtrip.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+NBIN, NSUM, NRES = 256, 13, 511
+
+
+# ---------------------------------------------------------------- format
+def rgbe_from_float(f: np.ndarray) -> np.ndarray:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty(f.shape[:-1], dtype=np.uint32)
+    rc = lib().oracle_rgbe_from_float(_p(f), ctypes.c_int64(out.size), _p(out))
+    if rc != 0:
+        raise ValueError("exponent outside [1, 255]")
+    return out
+
+
+def rgbe_to_float(rgbe: np.ndarray) -> np.ndarray:
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    out = np.empty(rgbe.shape + (3,), dtype=np.float64)
+    lib().oracle_rgbe_to_float(_p(rgbe), ctypes.c_int64(rgbe.size), _p(out))
+    return out
+
+
+def rgbe_split(rgbe: np.ndarray):
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    m3 = np.empty((3,) + rgbe.shape, dtype=np.uint8)
+    e = np.empty(rgbe.shape, dtype=np.uint8)
+    lib().oracle_rgbe_split(_p(rgbe), ctypes.c_int64(rgbe.size), _p(m3), _p(e))
+    return m3, e
+
+
+# ---------------------------------------------------------------- tables
+def log2_table() -> np.ndarray:
+    t = np.empty(2048, dtype=np.int32)
+    lib().oracle_log2_table(_p(t))
+    return t
+
+
+def gamma_thresholds() -> np.ndarray:
+    t = np.empty(256, dtype=np.float32)
+    lib().oracle_gamma_thresholds(_p(t))
+    return t
+
+
+def key_tables():
+    kr = np.empty(16, dtype=np.float32)
+    wr = np.empty(16, dtype=np.float32)
+    lib().oracle_key_tables(_p(kr), _p(wr))
+    return kr, wr
+
+
+def quant_table(quality: int) -> np.ndarray:
+    q = np.empty(64, dtype=np.int32)
+    lib().oracle_quant_table(ctypes.c_int(quality), _p(q))
+    return q.reshape(8, 8)
+
+
+def dct_matrix() -> np.ndarray:
+    d = np.empty(64, dtype=np.int32)
+    lib().oracle_dct_matrix(_p(d))
+    return d.reshape(8, 8)
+
+
+# ---------------------------------------------------------------- base layer
+def lum_stats(rgbe: np.ndarray) -> np.ndarray:
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    st = np.zeros(2, dtype=np.int64)
+    lib().oracle_lum_stats(_p(rgbe), ctypes.c_int64(rgbe.size), _p(st))
+    return st
+
+
+def key(stats: np.ndarray):
+    stats = np.ascontiguousarray(stats, dtype=np.int64)
+    J = ctypes.c_int32()
+    r = ctypes.c_int32()
+    lib().oracle_key(_p(stats), ctypes.byref(J), ctypes.byref(r))
+    return J.value, r.value
+
+
+def tmo(rgbe: np.ndarray, J: int, r: int) -> np.ndarray:
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    sdr3 = np.empty((3,) + rgbe.shape, dtype=np.uint8)
+    lib().oracle_tmo(_p(rgbe), ctypes.c_int64(rgbe.size), ctypes.c_int32(J), ctypes.c_int32(r), _p(sdr3))
+    return sdr3
+
+
+def base_roundtrip(sdr3: np.ndarray, quality: int) -> np.ndarray:
+    sdr3 = np.ascontiguousarray(sdr3, dtype=np.uint8)
+    _, h, w = sdr3.shape
+    s3 = np.empty_like(sdr3)
+    rc = lib().oracle_base_roundtrip(_p(sdr3), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(quality), _p(s3))
+    if rc != 0:
+        raise ValueError("quality must be in [1, 100]")
+    return s3
+
+
+# ---------------------------------------------------------------- SLRME
+def gf(s3: np.ndarray, gf_on: bool = True) -> np.ndarray:
+    s3 = np.ascontiguousarray(s3, dtype=np.uint8)
+    _, h, w = s3.shape
+    x3 = np.empty((3, h, w), dtype=np.int32)
+    lib().oracle_gf(_p(s3), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(int(gf_on)), _p(x3))
+    return x3
+
+
+def bin_sums(x3: np.ndarray, m3: np.ndarray, e: np.ndarray) -> np.ndarray:
+    x3 = np.ascontiguousarray(x3, dtype=np.int32)
+    m3 = np.ascontiguousarray(m3, dtype=np.uint8)
+    e = np.ascontiguousarray(e, dtype=np.uint8)
+    sums = np.empty((NBIN, NSUM), dtype=np.int64)
+    lib().oracle_bin_sums(_p(x3), _p(m3), _p(e), ctypes.c_int64(e.size), _p(sums))
+    return sums
+
+
+def i128_to_double(v: int) -> float:
+    lo = v & ((1 << 64) - 1)
+    hi = v >> 64
+    return lib().oracle_i128_to_double_parts(ctypes.c_int64(hi), ctypes.c_uint64(lo))
+
+
+def solve(sums: np.ndarray):
+    """Returns (a[3,256] f32, b[3,256] f32, n[256] i32, n_used)."""
+    sums = np.ascontiguousarray(sums, dtype=np.int64)
+    a = np.empty((3, NBIN), dtype=np.float32)
+    b = np.empty((3, NBIN), dtype=np.float32)
+    n = np.empty(NBIN, dtype=np.int32)
+    nu = ctypes.c_int32()
+    lib().oracle_solve(_p(sums), _p(a), _p(b), _p(n), ctypes.byref(nu))
+    return a, b, n, nu.value
+
+
+def predict(x3: np.ndarray, e: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    x3 = np.ascontiguousarray(x3, dtype=np.int32)
+    e = np.ascontiguousarray(e, dtype=np.uint8)
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    ms = np.empty(x3.shape, dtype=np.uint8)
+    lib().oracle_predict(_p(x3), _p(e), ctypes.c_int64(e.size), _p(a), _p(b), _p(ms))
+    return ms
+
+
+def residual(m3: np.ndarray, mstar3: np.ndarray):
+    m3 = np.ascontiguousarray(m3, dtype=np.uint8)
+    mstar3 = np.ascontiguousarray(mstar3, dtype=np.uint8)
+    r3 = np.empty(m3.shape, dtype=np.int16)
+    hist = np.empty((3, NRES), dtype=np.uint32)
+    lib().oracle_residual(_p(m3), _p(mstar3), ctypes.c_int64(m3[0].size), _p(r3), _p(hist))
+    return r3, hist
+
+
+def decode(s3: np.ndarray, e: np.ndarray, r3: np.ndarray, a: np.ndarray, b: np.ndarray,
+           gf_on: bool = True) -> np.ndarray:
+    s3 = np.ascontiguousarray(s3, dtype=np.uint8)
+    e = np.ascontiguousarray(e, dtype=np.uint8)
+    r3 = np.ascontiguousarray(r3, dtype=np.int16)
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    _, h, w = s3.shape
+    out = np.empty((h, w), dtype=np.uint32)
+    lib().oracle_decode(_p(s3), _p(e), _p(r3), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(int(gf_on)),
+                        _p(a), _p(b), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- pipeline
+def encode(rgbe: np.ndarray, quality: int, gf_on: bool = True) -> dict:
+    """Whole encoder (Fig. 2, bottom): split, TMO, base round trip, SLRME fit,
+    prediction and residual.  Returns every intermediate."""
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    m3, e = rgbe_split(rgbe)
+    st = lum_stats(rgbe)
+    J, r = key(st)
+    sdr3 = tmo(rgbe, J, r)
+    s3 = base_roundtrip(sdr3, quality)
+    x3 = gf(s3, gf_on)
+    sums = bin_sums(x3, m3, e)
+    a, b, n, n_used = solve(sums)
+    ms = predict(x3, e, a, b)
+    r3, hist = residual(m3, ms)
+    return dict(m3=m3, e=e, stats=st, J=J, r=r, sdr3=sdr3, s3=s3, x3=x3, sums=sums,
+                a=a, b=b, n=n, n_used=n_used, mstar3=ms, r3=r3, hist=hist)
+
+
+def entropy_bits(hist: np.ndarray) -> float:
+    """Order-0 entropy (bits per symbol) of one histogram, float64."""
+    h = np.asarray(hist, dtype=np.float64)
+    tot = h.sum()
+    if tot == 0:
+        return 0.0
+    p = h[h > 0] / tot
+    return float(-(p * np.log2(p)).sum())

@@ -1,0 +1,532 @@
+/*
+ * CPU oracle for the dual-layer lossless Radiance (RGBE) coder with the
+ * simple linear regressive mantissa estimator (SLRME), arXiv 2309.11072.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file.  It is a plain, slow,
+ * single-threaded statement of what the codec computes, written from the
+ * paper (sections and equations cited per function) and from the readings
+ * the paper leaves open (marked READING).  It shares no code, header, table
+ * or constant generator with the CUDA library.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared
+ * (float and double arithmetic is plain IEEE round-to-nearest, no FMA
+ * contraction; >> on negative int is an arithmetic shift under gcc).
+ *
+ * Layouts: images are row-major, h rows by w columns.  Colour planes are
+ * planar, plane c (R=0, G=1, B=2) at offset c*h*w.  A packed RGBE word is
+ * R | G<<8 | B<<16 | E<<24.
+ *
+ * Parity status: every function here is pinned by a test against something
+ * other than itself (closed forms, invariants, brute force, library
+ * routines); none is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NBIN 256        /* one region per 8-bit exponent value E            */
+#define NSUM 13         /* N_E, then (sum x, sum y, sum xy, sum xx) per channel */
+#define NRES 511        /* residual values -255..255                         */
+
+/* ----------------------------------------------------------------------
+ * Sec. II-A, Eqs. (1)-(2): RGBE forward conversion.
+ * READING: Eq. (1) with a ceiling gives M = 256 at exact powers of two,
+ * which does not fit 8 bits; the Radiance convention (frexp exponent + 128,
+ * so the largest mantissa is in [128, 255]) is used instead.  It agrees
+ * with Eq. (1) everywhere else.  Returns -1 if an exponent leaves [1, 255].
+ * ---------------------------------------------------------------------- */
+int oracle_rgbe_from_float(const double* f, int64_t n_px, uint32_t* rgbe)
+{
+    for (int64_t p = 0; p < n_px; ++p) {
+        double r = f[3 * p], g = f[3 * p + 1], b = f[3 * p + 2];
+        double v = r > g ? r : g;
+        v = v > b ? v : b;
+        if (v < 1e-32) { rgbe[p] = 0; continue; }
+        int ex;
+        frexp(v, &ex);                     /* v = m * 2^ex, m in [0.5, 1) */
+        int E = ex + 128;
+        if (E < 1 || E > 255) return -1;
+        /* Eq. (2): M = floor(256 f / 2^(E-128)) = floor(f * 2^(136-E)) */
+        uint32_t M[3];
+        const double c3[3] = {r, g, b};
+        for (int c = 0; c < 3; ++c) M[c] = (uint32_t)floor(ldexp(c3[c], 136 - E));
+        rgbe[p] = M[0] | (M[1] << 8) | (M[2] << 16) | ((uint32_t)E << 24);
+    }
+    return 0;
+}
+
+/* Sec. II-A, Eq. (3): f = (M + 0.5) / 256 * 2^(E-128); E = 0 is the zero pixel. */
+void oracle_rgbe_to_float(const uint32_t* rgbe, int64_t n_px, double* f)
+{
+    for (int64_t p = 0; p < n_px; ++p) {
+        uint32_t wd = rgbe[p];
+        int E = (int)(wd >> 24);
+        for (int c = 0; c < 3; ++c) {
+            int M = (int)((wd >> (8 * c)) & 255u);
+            f[3 * p + c] = (E == 0) ? 0.0 : ldexp(M + 0.5, E - 128 - 8);
+        }
+    }
+}
+
+/* Sec. III-A: the coder works on the mantissas M_R, M_G, M_B and the
+ * exponent E directly; the split takes the bytes of each word apart. */
+void oracle_rgbe_split(const uint32_t* rgbe, int64_t n_px, uint8_t* m3, uint8_t* e)
+{
+    for (int64_t p = 0; p < n_px; ++p) {
+        uint32_t wd = rgbe[p];
+        m3[p] = (uint8_t)(wd & 255u);
+        m3[n_px + p] = (uint8_t)((wd >> 8) & 255u);
+        m3[2 * n_px + p] = (uint8_t)((wd >> 16) & 255u);
+        e[p] = (uint8_t)(wd >> 24);
+    }
+}
+
+/* ======================================================================
+ * Base layer, part 1: the tone-mapping operator (Sec. II-B, Fig. 2; the
+ * experiments of Sec. IV use Reinhard et al.'s global operator).  The
+ * paper gives no parameters; every constant below is a READING:
+ *   key 0.18 over the log-average luminance, L_d = L / (1 + L), colour
+ *   carried by the ratio f_c / Y, BT.709 luma weights, display gamma 2.2.
+ * The pixel luminance is exact in integers: with f_c = (2M_c+1) 2^(E-137)
+ * (Eq. 3), 10^4 * Y = Yq * 2^(E-137) where
+ *   Yq = 2126 (2M_R+1) + 7152 (2M_G+1) + 722 (2M_B+1)   (10^4 <= Yq < 2^23).
+ * ====================================================================== */
+
+/* lut[i] = round(65536 * log2(2048 + i)), i = 0..2047 */
+void oracle_log2_table(int32_t* lut)
+{
+    for (int i = 0; i < 2048; ++i) lut[i] = (int32_t)llround(65536.0 * log2((double)(2048 + i)));
+}
+
+/* t[k] = float32(((k - 0.5) / 255) ^ 2.2), k = 1..255; t[0] = 0 (unused).
+ * The 8-bit display value of a linear value v is #{k in 1..255 : v >= t[k]},
+ * i.e. round(255 v^(1/2.2)) with ties settled by the table. */
+void oracle_gamma_thresholds(float* t)
+{
+    t[0] = 0.0f;
+    for (int k = 1; k < 256; ++k) t[k] = (float)pow((k - 0.5) / 255.0, 2.2);
+}
+
+/* Key scale tables for the fractional sixteenth r = 0..15 of the log-average:
+ * kr[r] = float32(0.18 * 2^(-r/16)),  wr[r] = float32(1800 * 2^(-r/16)). */
+void oracle_key_tables(float* kr, float* wr)
+{
+    for (int r = 0; r < 16; ++r) {
+        kr[r] = (float)(0.18 * pow(2.0, -r / 16.0));
+        wr[r] = (float)(1800.0 * pow(2.0, -r / 16.0));
+    }
+}
+
+static int64_t yq_of(uint32_t wd)
+{
+    int64_t R = wd & 255u, G = (wd >> 8) & 255u, B = (wd >> 16) & 255u;
+    return 2126 * (2 * R + 1) + 7152 * (2 * G + 1) + 722 * (2 * B + 1);
+}
+
+static int bitlen64(int64_t v)
+{
+    int n = 0;
+    while (v > 0) { ++n; v >>= 1; }
+    return n;
+}
+
+/* Log-average statistic: stats[0] = sum over E > 0 of l(p), stats[1] = count,
+ * where l = 65536 (E - 137 + k) + lut[m - 2048], k = bitlen(Yq) - 12,
+ * m = Yq >> k, so l / 65536 ~ log2(10^4 Y). */
+void oracle_lum_stats(const uint32_t* rgbe, int64_t n_px, int64_t* stats)
+{
+    int32_t lut[2048];
+    oracle_log2_table(lut);
+    int64_t s = 0, n = 0;
+    for (int64_t p = 0; p < n_px; ++p) {
+        int E = (int)(rgbe[p] >> 24);
+        if (E == 0) continue;
+        int64_t Yq = yq_of(rgbe[p]);
+        int k = bitlen64(Yq) - 12;
+        int64_t m = Yq >> k;
+        s += 65536 * (int64_t)(E - 137 + k) + lut[m - 2048];
+        n += 1;
+    }
+    stats[0] = s;
+    stats[1] = n;
+}
+
+static int64_t floor_div(int64_t a, int64_t b)   /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+/* j = round-half-up(16 * mu), mu = stats[0] / (65536 stats[1]); j = 16 J + r.
+ * An image with no non-zero pixel takes j = 0. */
+void oracle_key(const int64_t* stats, int32_t* J, int32_t* r)
+{
+    int64_t j = 0;
+    if (stats[1] > 0) j = floor_div(stats[0] + 2048 * stats[1], 4096 * stats[1]);
+    int64_t Jj = floor_div(j, 16);
+    *J = (int32_t)Jj;
+    *r = (int32_t)(j - 16 * Jj);
+}
+
+/* Per pixel, float32 round-to-nearest, as the READING fixes it:
+ *   d = clamp(E - 137 - J, -100, 100)
+ *   L = (kr[r] * Yq) * 2^d                       (scaled luminance, exact scale)
+ *   H = (wr[r] * 2^d) / (1 + L)                  (= L_d / Y, times 10^4)
+ *   v_c = H * (2 M_c + 1)                        (= L_d * f_c / Y)
+ *   SDR_c = #{k : v_c >= t[k]};   E = 0 gives SDR = 0. */
+void oracle_tmo(const uint32_t* rgbe, int64_t n_px, int32_t J, int32_t r, uint8_t* sdr3)
+{
+    float t[256], kr[16], wr[16];
+    oracle_gamma_thresholds(t);
+    oracle_key_tables(kr, wr);
+    for (int64_t p = 0; p < n_px; ++p) {
+        uint32_t wd = rgbe[p];
+        int E = (int)(wd >> 24);
+        if (E == 0) { sdr3[p] = sdr3[n_px + p] = sdr3[2 * n_px + p] = 0; continue; }
+        int d = E - 137 - J;
+        if (d < -100) d = -100;
+        if (d > 100) d = 100;
+        float P = kr[r] * (float)yq_of(wd);
+        float L = ldexpf(P, d);
+        float den = 1.0f + L;
+        float num = ldexpf(wr[r], d);
+        float H = num / den;
+        for (int c = 0; c < 3; ++c) {
+            int M = (int)((wd >> (8 * c)) & 255u);
+            float v = H * (float)(2 * M + 1);
+            /* count thresholds <= v by bisection over the increasing table */
+            int lo = 0, hi = 256;            /* invariant: t[1..lo] <= v < t[hi..255] */
+            while (hi - lo > 1) {
+                int mid = (lo + hi) / 2;
+                if (v >= t[mid]) lo = mid; else hi = mid;
+            }
+            sdr3[(int64_t)c * n_px + p] = (uint8_t)lo;
+        }
+    }
+}
+
+/* ======================================================================
+ * Base layer, part 2: the lossy base coder round trip (Sec. IV uses JPEG
+ * at quality Q).  Only the transform and quantiser change the decoded
+ * SDRI S, so only they are computed (entropy coding does not change S).
+ * READINGS: each colour plane is coded on its own, 4:4:4, with the ITU-T
+ * T.81 Annex K.1 luminance table scaled by the IJG quality rule; the
+ * last row/column is replicated up to a multiple of 8; the DCT is a
+ * fixed-point matrix product with constants round(4096 * D) and a
+ * round-half-up shift after each 1-D pass (9, 15 forward; 9, 15 inverse).
+ * ====================================================================== */
+
+static const int32_t k_luma_q50[64] = {
+    16, 11, 10, 16, 24, 40, 51, 61,
+    12, 12, 14, 19, 26, 58, 60, 55,
+    14, 13, 16, 24, 40, 57, 69, 56,
+    14, 17, 22, 29, 51, 87, 80, 62,
+    18, 22, 37, 56, 68, 109, 103, 77,
+    24, 35, 55, 64, 81, 104, 113, 92,
+    49, 64, 78, 87, 103, 121, 120, 101,
+    72, 92, 95, 98, 112, 100, 103, 99};
+
+/* q[v*8+u]: quantiser step for vertical frequency v, horizontal u. */
+void oracle_quant_table(int quality, int32_t* q)
+{
+    int s = quality < 50 ? 5000 / quality : 200 - 2 * quality;
+    for (int i = 0; i < 64; ++i) {
+        int v = (k_luma_q50[i] * s + 50) / 100;
+        q[i] = v < 1 ? 1 : (v > 255 ? 255 : v);
+    }
+}
+
+/* d[u*8+x] = round(4096 * alpha_u * cos((2x+1) u pi / 16)),
+ * alpha_0 = sqrt(1/8), alpha_u = 1/2 (orthonormal DCT-II). */
+void oracle_dct_matrix(int32_t* d)
+{
+    const double pi = 3.14159265358979323846;
+    for (int u = 0; u < 8; ++u)
+        for (int x = 0; x < 8; ++x) {
+            double a = (u == 0) ? sqrt(1.0 / 8.0) : 0.5;
+            d[u * 8 + x] = (int32_t)llround(4096.0 * a * cos((2 * x + 1) * u * pi / 16.0));
+        }
+}
+
+static int32_t rshift_round(int64_t v, int s) { return (int32_t)((v + ((int64_t)1 << (s - 1))) >> s); }
+
+/* Forward 2-D DCT of one block, X[y*8+x] in [-128, 127] -> F[v*8+u]:
+ * along x first, T[y][u] = (sum_x D[u][x] X[y][x]) >> 9 (rounded), then
+ * along y, F[v][u] = (sum_y D[v][y] T[y][u]) >> 15 (rounded).  The scale
+ * 4096^2 = 2^(9+15) makes F the orthonormal DCT-II up to rounding. */
+static const int32_t* dct_constants(void)
+{
+    static int32_t D[64];
+    static int ready = 0;
+    if (!ready) { oracle_dct_matrix(D); ready = 1; }
+    return D;
+}
+
+void oracle_fdct_block(const int32_t* X, int32_t* F)
+{
+    const int32_t* D = dct_constants();
+    int32_t T[64];
+    for (int y = 0; y < 8; ++y)
+        for (int u = 0; u < 8; ++u) {
+            int64_t acc = 0;
+            for (int x = 0; x < 8; ++x) acc += (int64_t)D[u * 8 + x] * X[y * 8 + x];
+            T[y * 8 + u] = rshift_round(acc, 9);
+        }
+    for (int v = 0; v < 8; ++v)
+        for (int u = 0; u < 8; ++u) {
+            int64_t acc = 0;
+            for (int y = 0; y < 8; ++y) acc += (int64_t)D[v * 8 + y] * T[y * 8 + u];
+            F[v * 8 + u] = rshift_round(acc, 15);
+        }
+}
+
+/* Quantise (level = sign(F) floor((|F| + floor(q/2)) / q), i.e. half away
+ * from zero) and dequantise (level * q), coefficient by coefficient. */
+void oracle_quant_dequant_block(const int32_t* F, const int32_t* Q, int32_t* Fq)
+{
+    for (int i = 0; i < 64; ++i) {
+        int32_t q = Q[i];
+        int32_t a = F[i] < 0 ? -F[i] : F[i];
+        int32_t lvl = (a + q / 2) / q;
+        Fq[i] = (F[i] < 0 ? -lvl : lvl) * q;
+    }
+}
+
+/* Inverse 2-D DCT: along y first, G[y][u] = (sum_v D[v][y] F[v][u]) >> 9,
+ * then along x, X[y][x] = (sum_u D[u][x] G[y][u]) >> 15 (both rounded). */
+void oracle_idct_block(const int32_t* F, int32_t* X)
+{
+    const int32_t* D = dct_constants();
+    int32_t G[64];
+    for (int y = 0; y < 8; ++y)
+        for (int u = 0; u < 8; ++u) {
+            int64_t acc = 0;
+            for (int v = 0; v < 8; ++v) acc += (int64_t)D[v * 8 + y] * F[v * 8 + u];
+            G[y * 8 + u] = rshift_round(acc, 9);
+        }
+    for (int y = 0; y < 8; ++y)
+        for (int x = 0; x < 8; ++x) {
+            int64_t acc = 0;
+            for (int u = 0; u < 8; ++u) acc += (int64_t)D[u * 8 + x] * G[y * 8 + u];
+            X[y * 8 + x] = rshift_round(acc, 15);
+        }
+}
+
+/* sdr3 (planar uint8) -> decoded SDRI s3 (planar uint8). Returns -1 on bad quality. */
+int oracle_base_roundtrip(const uint8_t* sdr3, int h, int w, int quality, uint8_t* s3)
+{
+    if (quality < 1 || quality > 100) return -1;
+    int32_t Q[64];
+    oracle_quant_table(quality, Q);
+    int64_t n_px = (int64_t)h * w;
+    for (int c = 0; c < 3; ++c) {
+        const uint8_t* in = sdr3 + c * n_px;
+        uint8_t* out = s3 + c * n_px;
+        for (int by = 0; by < h; by += 8)
+            for (int bx = 0; bx < w; bx += 8) {
+                int32_t X[64], F[64], Fq[64], Y[64];
+                for (int y = 0; y < 8; ++y)
+                    for (int x = 0; x < 8; ++x) {
+                        int yy = by + y < h ? by + y : h - 1;
+                        int xx = bx + x < w ? bx + x : w - 1;
+                        X[y * 8 + x] = (int32_t)in[(int64_t)yy * w + xx] - 128;
+                    }
+                oracle_fdct_block(X, F);
+                oracle_quant_dequant_block(F, Q, Fq);
+                oracle_idct_block(Fq, Y);
+                for (int y = 0; y < 8 && by + y < h; ++y)
+                    for (int x = 0; x < 8 && bx + x < w; ++x) {
+                        int32_t s = Y[y * 8 + x] + 128;
+                        out[(int64_t)(by + y) * w + bx + x] = (uint8_t)(s < 0 ? 0 : (s > 255 ? 255 : s));
+                    }
+            }
+    }
+    return 0;
+}
+
+/* ======================================================================
+ * Sec. III-B: SLRME.
+ * ====================================================================== */
+
+/* Gaussian-filter restoration S -> S* (Sec. III-B and its footnote).
+ * READING: 3x3 binomial kernel [1 2 1]^T [1 2 1] with edge replication,
+ * kept unrounded as an integer in 1/16 units: x = 16 S* in [0, 4080].
+ * gf_on = 0 gives x = 16 S (no restoration). */
+void oracle_gf(const uint8_t* s3, int h, int w, int gf_on, int32_t* x3)
+{
+    int64_t n_px = (int64_t)h * w;
+    static const int wt[3] = {1, 2, 1};
+    for (int c = 0; c < 3; ++c) {
+        const uint8_t* S = s3 + c * n_px;
+        int32_t* X = x3 + c * n_px;
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                if (!gf_on) { X[(int64_t)y * w + x] = 16 * S[(int64_t)y * w + x]; continue; }
+                int32_t acc = 0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int yy = y + dy, xx = x + dx;
+                        yy = yy < 0 ? 0 : (yy >= h ? h - 1 : yy);
+                        xx = xx < 0 ? 0 : (xx >= w ? w - 1 : xx);
+                        acc += wt[dy + 1] * wt[dx + 1] * S[(int64_t)yy * w + xx];
+                    }
+                X[(int64_t)y * w + x] = acc;
+            }
+    }
+}
+
+/* Eqs. (9)-(10) need, for each region E (all q with that exponent) and each
+ * channel c, the sums over q of 1, S*, M, S* M and S*^2.  Layout:
+ * sums[E*13 + 0] = N_E, sums[E*13 + 1 + 4c + {0,1,2,3}] =
+ * {sum x, sum y, sum x y, sum x x} with x = 16 S*_c, y = M_c.  Exact int64. */
+void oracle_bin_sums(const int32_t* x3, const uint8_t* m3, const uint8_t* e, int64_t n_px, int64_t* sums)
+{
+    memset(sums, 0, sizeof(int64_t) * NBIN * NSUM);
+    for (int64_t p = 0; p < n_px; ++p) {
+        int64_t* s = sums + (int64_t)e[p] * NSUM;
+        s[0] += 1;
+        for (int c = 0; c < 3; ++c) {
+            int64_t x = x3[c * n_px + p], y = m3[c * n_px + p];
+            s[1 + 4 * c] += x;
+            s[2 + 4 * c] += y;
+            s[3 + 4 * c] += x * y;
+            s[4 + 4 * c] += x * x;
+        }
+    }
+}
+
+/* Correctly rounded (nearest, ties to even) conversion of a signed 128-bit
+ * integer to double, written out: keep the top 53 significant bits and
+ * round on the rest. */
+double oracle_i128_to_double(__int128 v)
+{
+    if (v == 0) return 0.0;
+    int neg = v < 0;
+    unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+    int nb = 0;
+    for (unsigned __int128 t = u; t != 0; t >>= 1) ++nb;
+    double r;
+    if (nb <= 53) {
+        r = (double)(uint64_t)u;
+    } else {
+        int sh = nb - 53;
+        unsigned __int128 mant = u >> sh;
+        unsigned __int128 rem = u - (mant << sh);
+        unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) mant += 1;   /* may reach 2^53: still exact */
+        r = ldexp((double)(uint64_t)mant, sh);
+    }
+    return neg ? -r : r;
+}
+
+/* Entry point so tests can check the conversion: v = hi * 2^64 + lo. */
+double oracle_i128_to_double_parts(int64_t hi, uint64_t lo)
+{
+    __int128 v = ((__int128)hi << 64) | (__int128)lo;
+    return oracle_i128_to_double(v);
+}
+
+/* Eqs. (9)-(10) (the normal equations (6)-(7) of Sec. II-C restricted to
+ * region E), quantised to the 32-bit values Sec. III-C transmits.
+ *   D_xx = N sum x^2 - (sum x)^2,  D_xy = N sum xy - sum x sum y   (exact int128)
+ *   a_E  = float32( double(D_xy) / double(D_xx) )
+ *   b_E  = float32( (double(sum y) - double(a_E) * double(sum x)) / double(N) )
+ * READINGS: per channel and per E (Eq. 8 is written per mantissa); x is
+ * S* in 1/16 units, so a_E is per 1/16 step; b_E is computed from the
+ * quantised a_E (the intercept that is optimal for the slope actually
+ * sent); N_E = 0 leaves the region unused (a = b = 0, not sent); D_xx = 0
+ * (all x equal) gives a = 0, b = float32(sum y / N). */
+void oracle_solve(const int64_t* sums, float* a, float* b, int32_t* n_e, int32_t* n_used)
+{
+    int used = 0;
+    for (int E = 0; E < NBIN; ++E) {
+        const int64_t* s = sums + E * NSUM;
+        int64_t N = s[0];
+        n_e[E] = (int32_t)N;
+        if (N > 0) ++used;
+        for (int c = 0; c < 3; ++c) {
+            float* ac = a + c * NBIN + E;
+            float* bc = b + c * NBIN + E;
+            if (N == 0) { *ac = 0.0f; *bc = 0.0f; continue; }
+            int64_t sx = s[1 + 4 * c], sy = s[2 + 4 * c], sxy = s[3 + 4 * c], sxx = s[4 + 4 * c];
+            __int128 dxx = (__int128)N * sxx - (__int128)sx * sx;
+            __int128 dxy = (__int128)N * sxy - (__int128)sx * sy;
+            if (dxx == 0) {
+                *ac = 0.0f;
+                *bc = (float)((double)sy / (double)N);
+                continue;
+            }
+            double ad = oracle_i128_to_double(dxy) / oracle_i128_to_double(dxx);
+            float af = (float)ad;
+            double t = (double)af * (double)sx;
+            double bd = ((double)sy - t) / (double)N;
+            *ac = af;
+            *bc = (float)bd;
+        }
+    }
+    *n_used = used;
+}
+
+/* Eq. (8): M*(q) = round(a_E S*(q) + b_E) clipped to [0, 255].
+ * READINGS: t = float32(float32(a x) + b) with x = 16 S* (no fused
+ * multiply-add); round is half away from zero (MATLAB's round, the
+ * paper's platform). */
+static uint8_t predict1(float a, float b, int32_t x)
+{
+    float t = a * (float)x;
+    t = t + b;
+    if (!(t > 0.0f)) return 0;            /* t <= 0 (round of t <= 0 is <= 0) */
+    if (t >= 255.0f) return 255;
+    float tr = truncf(t);
+    int r = (int)tr;
+    if (t - tr >= 0.5f) r += 1;
+    return (uint8_t)(r > 255 ? 255 : r);
+}
+
+void oracle_predict(const int32_t* x3, const uint8_t* e, int64_t n_px, const float* a, const float* b, uint8_t* mstar3)
+{
+    for (int c = 0; c < 3; ++c)
+        for (int64_t p = 0; p < n_px; ++p) {
+            int E = e[p];
+            mstar3[c * n_px + p] = predict1(a[c * NBIN + E], b[c * NBIN + E], x3[c * n_px + p]);
+        }
+}
+
+/* Sec. III-C: the enhancement layer carries R = M - M*; hist[c*511 + R + 255]
+ * counts each value (the order-0 statistics used for the bit rate). */
+void oracle_residual(const uint8_t* m3, const uint8_t* mstar3, int64_t n_px, int16_t* r3, uint32_t* hist)
+{
+    if (hist) memset(hist, 0, sizeof(uint32_t) * 3 * NRES);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t p = 0; p < n_px; ++p) {
+            int r = (int)m3[c * n_px + p] - (int)mstar3[c * n_px + p];
+            r3[c * n_px + p] = (int16_t)r;
+            if (hist) hist[c * NRES + r + 255] += 1;
+        }
+}
+
+/* Decoder (Sec. I, III-C): M = R + M*(S, E, a, b), M* recomputed from the
+ * decoded SDRI and the transmitted parameters without refitting; the word
+ * is repacked with the transmitted exponent plane. */
+void oracle_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w, int gf_on,
+                   const float* a, const float* b, uint32_t* rgbe)
+{
+    int64_t n_px = (int64_t)h * w;
+    int32_t* x3 = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)n_px);
+    uint8_t* ms = (uint8_t*)malloc(3 * (size_t)n_px);
+    oracle_gf(s3, h, w, gf_on, x3);
+    oracle_predict(x3, e, n_px, a, b, ms);
+    for (int64_t p = 0; p < n_px; ++p) {
+        uint32_t wd = (uint32_t)e[p] << 24;
+        for (int c = 0; c < 3; ++c) {
+            int M = (int)r3[c * n_px + p] + (int)ms[c * n_px + p];
+            wd |= ((uint32_t)M & 255u) << (8 * c);
+        }
+        rgbe[p] = wd;
+    }
+    free(x3);
+    free(ms);
+}
