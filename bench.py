@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: encode + decode throughput of the SLRME dual-layer lossless
+RGBE coder on one GB300 (or N independent replicas, one per GPU).
+
+Workload (one "step"): the 2048x1536 synthetic RGBE image (fBm luminance over
+8 decades, 40 sharp-edged rectangles, 200 specular highlights; seed 2), coded
+at base qualities 50, 75 and 90: per quality rgbe_split, sdri_base_roundtrip,
+slr_fit, residual_encode, then residual_decode, with the decoded words
+checked against the input.  The input is resident in HBM when timing starts;
+L2 is flushed (a 256 MiB write) between timed steps, outside the step events.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead
+(rank 0 only) on the same workload, one quality per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encode+decode MPixel/s (bit-exact); enh.-layer bits/px, learned vs SLR, 1 GB300"
+UNIT = "MPixel/s"
+
+# Algorithmic HBM bytes per pixel of each C-ABI call (reads + writes of the
+# planes it must touch once): split 4+4, base 4+3, fit 7, residual 7+6,
+# decode 10+4.
+BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residual_encode": 13,
+                "residual_decode": 14}
+# DRAM bytes per pixel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# over one launch, divided by its pixels) with the sha256 of the kernel source the
+# counters were taken on; a changed source reports null.  See profiles/.
+TRAFFIC = {}
+KERNEL_SOURCE = {"rgbe_split": "split.cu", "sdri_base_roundtrip": "base.cu", "slr_fit": "slr.cu",
+                 "residual_encode": "slr.cu", "residual_decode": "slr.cu"}
+
+
+def _sha(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2309_11072_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"slrme_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+
+    from paper_2309_11072_gb300 import codec, native, synth
+    from paper_2309_11072_gb300.metrics import enhancement_bits_per_pixel
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    native.lib()
+
+    wl = synth.workload_2k()
+    (h, w), = wl.sizes
+    img = synth.make_workload_images(wl)[0]
+    n = h * w
+    qualities = wl.qualities
+    stream = torch.cuda.current_stream()
+    rgbe = torch.from_numpy(img.view(np.int32).reshape(-1).copy()).cuda()
+    c = codec.Codec(h, w, "cuda", gf_on=True)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    calls = ["rgbe_split", "sdri_base_roundtrip", "slr_fit", "residual_encode", "residual_decode"]
+
+    def step(ev=None):
+        for q in qualities:
+            if ev is not None:
+                ev[q][0].record(stream)
+            native.rgbe_split(rgbe, h, w, c.m3, c.e, c.stats, stream)
+            if ev is not None:
+                ev[q][1].record(stream)
+            native.sdri_base_roundtrip(c.m3, c.e, h, w, c.stats, q, c.s3, None, stream)
+            if ev is not None:
+                ev[q][2].record(stream)
+            native.slr_fit(c.s3, c.m3, c.e, h, w, 1, c.sums, c.params, stream)
+            if ev is not None:
+                ev[q][3].record(stream)
+            native.residual_encode(c.s3, c.m3, c.e, h, w, 1, c.params, c.r3, c.hist, stream)
+            if ev is not None:
+                ev[q][4].record(stream)
+            native.residual_decode(c.s3, c.e, c.r3, h, w, 1, c.params, c.out, stream)
+            if ev is not None:
+                ev[q][5].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    # bit-exact check and rates at each quality (outside the timed region)
+    bit_exact = True
+    bpp = {}
+    ident = torch.from_numpy(codec.params_from_numpy(np.full((3, 256), 1 / 16, np.float32),
+                                                     np.zeros((3, 256), np.float32))).cuda()
+    for q in qualities:
+        L = c.encode(rgbe, q)
+        out = c.decode(L.s3, L.e, L.r3, L.params)
+        bit_exact &= bool(torch.equal(out, rgbe))
+        slr = c.bits_per_pixel()
+        native.residual_encode(c.s3, c.m3, c.e, h, w, 0, ident, c.r3, c.hist, stream)
+        # without SLRME nothing but the residual planes is sent (M* = S)
+        plain = enhancement_bits_per_pixel(c.hist.view(3, 511).cpu().numpy().view(np.uint32), 0, n) - 256.0 / n
+        bpp[str(q)] = {"slr": round(slr, 4), "without_slrme": round(plain, 4), "learned": None}
+    torch.cuda.synchronize()
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    call_ev = [{q: [torch.cuda.Event(enable_timing=True) for _ in range(6)] for q in qualities}
+               for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            step_ev[k][0].record(stream)
+            step(call_ev[k])
+            step_ev[k][1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    total_ms = sum(step_ms)
+    per_call = {name: [] for name in calls}
+    for k in range(args.steps):
+        for q in qualities:
+            ev = call_ev[k][q]
+            for i, name in enumerate(calls):
+                per_call[name].append(ev[i].elapsed_time(ev[i + 1]))
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    px_per_step = n * len(qualities)
+    value = world * px_per_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # roofline of the dominant call
+    peaks = load_peaks()
+    avg_us = {name: 1e3 * statistics.mean(v) for name, v in per_call.items()}
+    dom = max(avg_us, key=lambda k: avg_us[k])
+    achieved = BYTES_PER_PX[dom] * n / (avg_us[dom] * 1e-6) / 1e9
+    tr = TRAFFIC.get(dom)
+    traffic = None
+    if tr and tr["sha"] == _sha(KERNEL_SOURCE[dom]):
+        traffic = tr["bytes_per_px"] * n
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": dom,
+                "algorithmic_bytes": BYTES_PER_PX[dom] * n, "peak_source": peaks["src"]}
+    stage_us = {name: round(v, 2) for name, v in avg_us.items()}
+    stage_frac = {name: round(BYTES_PER_PX[name] * n / (avg_us[name] * 1e-6) / 1e9 / peaks["hbm_gbs"], 4)
+                  for name in calls}
+
+    # end to end through the public API with host buffers
+    hc = codec.HostCodec(h, w, "cuda", gf_on=True)
+    h_rgbe = torch.from_numpy(img.view(np.int32).reshape(-1).copy()).pin_memory()
+    for _ in range(args.warmup):
+        for q in qualities:
+            hc.roundtrip(h_rgbe, q)
+    torch.cuda.synchronize()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        e2e_ev[k][0].record(stream)
+        for q in qualities:
+            hc.roundtrip(h_rgbe, q)
+        e2e_ev[k][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    e2e_ok = bool(torch.equal(hc.h_out, h_rgbe))
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * px_per_step * args.steps / (e2e_ms / 1e3) / 1e6
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(img, qualities, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{wl.name} q{{50,75,90}} encode+decode, SLR, gaussian restoration on",
+                       "pixels_per_step": px_per_step, "image": f"{w}x{h}", "qualities": list(qualities),
+                       "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{world}"},
+            "bit_exact": bit_exact and e2e_ok,
+            "bits_per_px": bpp,
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": hc.h2d_bytes() * len(qualities),
+                    "d2h_bytes_per_step": hc.d2h_bytes() * len(qualities)},
+            "gpu_launches": args.steps * len(qualities) * 6,
+            "roofline": roofline, "stage_us": stage_us, "stage_hbm_frac": stage_frac,
+            "clocks": clocks.summary(), "cpu_baseline": cpu, "wall_s_timed": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(img, qualities, budget_s: float) -> dict:
+    """The CPU oracle, as it stands, on the same image: full encode + decode per
+    quality, cycling through the qualities until about budget_s seconds."""
+    from oracle import oracle as O
+    n = img.size
+    done, t0 = 0, time.perf_counter()
+    i = 0
+    while True:
+        q = qualities[i % len(qualities)]
+        o = O.encode(img, q)
+        O.decode(o["s3"], o["e"], o["r3"], o["a"], o["b"])
+        done += n
+        i += 1
+        if time.perf_counter() - t0 >= budget_s and i >= len(qualities):
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{i} full-image encode+decode passes of the {img.shape[1]}x{img.shape[0]} image "
+                      f"cycling q in {list(qualities)}, single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2309_11072_gb300 import synth
+    O.build()
+    wl = synth.workload_2k()
+    img = synth.make_workload_images(wl)[0]
+    qualities = wl.qualities
+
+    def one(k):
+        q = qualities[k % len(qualities)]
+        o = O.encode(img, q)
+        d = O.decode(o["s3"], o["e"], o["r3"], o["a"], o["b"])
+        return bool((d == img).all())
+
+    for k in range(args.warmup):
+        one(k)
+    ok = True
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ok &= one(k)
+    dt = time.perf_counter() - t0
+    value = img.size * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{wl.name} encode+decode, SLR, gaussian restoration on",
+                       "pixels_per_step": int(img.size), "qualities": list(qualities),
+                       "step": "one full-image encode+decode, quality cycling 50/75/90"},
+            "bit_exact": ok,
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full-image passes, single-threaded C oracle"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "ours":
+        args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps on the GPU
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

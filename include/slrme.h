@@ -1,0 +1,150 @@
+/*
+ * slrme.h -- C ABI of the GB300 (sm_103a) dual-layer lossless Radiance
+ * (RGBE) coder with the simple linear regressive mantissa estimator
+ * (SLRME) of Suzuki, Yukikata, Yang and Yoshida, "Lightning-Fast
+ * Dual-Layer Lossless Coding for Radiance Format High Dynamic Range
+ * Images" (arXiv 2309.11072).
+ *
+ * Encoder (Fig. 2, bottom):  rgbe_split -> sdri_base_roundtrip -> slr_fit
+ *                            -> residual_encode
+ * Decoder:                   residual_decode
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are h rows by w columns, row-major, row pitch = w elements.
+ *   A packed RGBE word is R | G<<8 | B<<16 | E<<24 (the byte order of a
+ *   Radiance file).  Colour planes are planar: plane c (R=0, G=1, B=2) of
+ *   an "x3" buffer starts at element c*h*w.
+ * - All image, workspace and parameter pointers are DEVICE pointers owned
+ *   by the caller; the library allocates no memory.  Calls are asynchronous
+ *   on `stream` (NULL = the legacy default stream) unless stated otherwise.
+ * - 0 <= h, 0 <= w, h*w < 2^31.  An empty image (h*w == 0) is valid: the
+ *   call only clears the outputs it documents as cleared.
+ * - Typed buffers must be naturally aligned (uint32/float/int32: 4 bytes,
+ *   int16: 2, int64: 8); a misaligned one is rejected with SLRME_EINVAL.
+ *   Byte planes may start anywhere.  Buffers aligned to 16 bytes with
+ *   w % 8 == 0 take the vectorised path, others a scalar path.
+ * - Return value: SLRME_OK, or a negative SLRME_E* code; the text of the
+ *   last error of the calling thread is in slrme_last_error().
+ *   SLRME_EINVAL is returned before anything is enqueued.  SLRME_ECUDA
+ *   reports a launch error seen when the call returns (errors of the
+ *   asynchronous execution surface at the caller's next synchronisation).
+ */
+#ifndef SLRME_H
+#define SLRME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLRME_OK        0
+#define SLRME_EINVAL   (-1)   /* bad argument: null pointer, size, quality, flag   */
+#define SLRME_ECUDA    (-2)   /* CUDA launch / runtime error                        */
+
+#define SLRME_NBIN      256   /* exponent regions: one per 8-bit exponent value E  */
+#define SLRME_NSUM      13    /* per region: N_E, then per channel sum x, sum y,
+                                 sum xy, sum xx                                     */
+#define SLRME_NRES      511   /* residual values -255..255                          */
+
+typedef struct CUstream_st* slrme_stream_t;   /* identical to cudaStream_t */
+
+/* The transmitted SLRME parameters (Sec. III-C): one 32-bit slope a_E and one
+ * 32-bit intercept b_E per colour channel and per used exponent region E.
+ * The slope is per 1/16 grey level of the restored SDRI (x = 16 S*).
+ * n[E] = N_E, the pixel count of region E; a region with N_E = 0 is unused
+ * (a = b = 0) and is not transmitted.  7184 bytes, 4-byte aligned. */
+typedef struct slrme_params {
+    float   a[3][SLRME_NBIN];
+    float   b[3][SLRME_NBIN];
+    int32_t n[SLRME_NBIN];
+    int32_t n_used;
+    int32_t reserved[3];
+} slrme_params;
+
+/* RGBE split (Sec. II-A Fig. 1, Sec. III-A): separates the words into the
+ * mantissa planes M_R, M_G, M_B (m3, uint8 [3][h][w]) and the exponent plane
+ * E (e, uint8 [h][w]), and accumulates the log-average luminance statistic
+ * of the tone-mapping operator into lum_stats (int64[2], device):
+ *   lum_stats[0] = sum over pixels with E > 0 of l(p),  lum_stats[1] = their count,
+ *   l = 65536 (E - 137 + k) + round(65536 log2 m),  Yq = 2126(2M_R+1) +
+ *   7152(2M_G+1) + 722(2M_B+1), k = bitlen(Yq) - 12, m = Yq >> k,
+ * i.e. l / 65536 approximates log2(10^4 Y) of the Eq. (3) floats.
+ * lum_stats is cleared by the call before accumulation. */
+int rgbe_split(const uint32_t* rgbe, int h, int w, uint8_t* m3, uint8_t* e,
+               int64_t* lum_stats, slrme_stream_t stream);
+
+/* Host helper, synchronous, no GPU: the key of the tone-mapping operator from
+ * a host copy of lum_stats: j = round-half-up(16 mu), mu = lum_stats[0] /
+ * (65536 lum_stats[1]) (j = 0 for an image without non-zero pixels), returned
+ * as j = 16 J + r with 0 <= r < 16. */
+int rgbe_key_scale(const int64_t lum_stats[2], int32_t* J, int32_t* r);
+
+/* Base layer round trip (Sec. II-B, Fig. 2; JPEG at quality Q in Sec. IV):
+ * tone maps M, E to the 8-bit SDRI with Reinhard's global operator
+ * (key 0.18 over the log-average read from lum_stats on the device, float32
+ * steps, gamma 2.2 by a threshold table), then runs every 8x8 block of each
+ * colour plane through a fixed-point DCT (constants round(4096 D), rounding
+ * shifts 9 and 15), quantisation with the T.81 Annex K.1 luminance table
+ * scaled to `quality` (1..100, IJG rule), dequantisation and the inverse DCT,
+ * and writes the decoded SDRI S (s_dec3, uint8 [3][h][w]).  Blocks at a
+ * ragged edge replicate the last row/column.  sdr3 (uint8 [3][h][w]) receives
+ * the tone-mapped SDRI before coding, or is NULL. */
+int sdri_base_roundtrip(const uint8_t* m3, const uint8_t* e, int h, int w,
+                        const int64_t* lum_stats, int quality,
+                        uint8_t* s_dec3, uint8_t* sdr3, slrme_stream_t stream);
+
+/* SLRME fit (Sec. III-B, Eqs. 9-10 from the normal equations 6-7 of Sec. II-C):
+ * restores S with the 3x3 binomial Gaussian filter (gf_on = 1; x = 16 S* in
+ * [0, 4080], edge replicated) or takes x = 16 S (gf_on = 0), accumulates per
+ * exponent region E the exact int64 sums into bin_sums (workspace, int64
+ * [256][13]: N_E, then per channel c sum x, sum y, sum xy, sum xx with y = M_c;
+ * cleared by the call), and solves each (channel, region) on the device:
+ *   D_xx = N sum xx - (sum x)^2, D_xy = N sum xy - sum x sum y  (int128),
+ *   a_E = float(double(D_xy) / double(D_xx)),
+ *   b_E = float((double(sum y) - double(a_E) double(sum x)) / N),
+ * with a = 0, b = float(sum y / N) when D_xx = 0 and a = b = 0 when N_E = 0.
+ * params receives the result (device, slrme_params). */
+int slr_fit(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w,
+            int gf_on, int64_t* bin_sums, slrme_params* params, slrme_stream_t stream);
+
+/* Bytes of the bin_sums workspace slr_fit needs (256 * 13 * 8). */
+size_t slr_fit_workspace_bytes(void);
+
+/* Residual formation (Eq. 8, Sec. III-C): M*(q) = round(a_E S*(q) + b_E)
+ * clipped to [0, 255] (float32 multiply then add, round half away from zero),
+ * R = M - M* (r3, int16 [3][h][w]).  hist (uint32 [3][511], device, may be
+ * NULL) is cleared and receives the count of each residual value per channel
+ * (index R + 255), the statistics of the enhancement-layer rate. */
+int residual_encode(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w,
+                    int gf_on, const slrme_params* params, int16_t* r3, uint32_t* hist,
+                    slrme_stream_t stream);
+
+/* Decoder (Sec. I and III-C): recomputes M* from the decoded SDRI, the
+ * exponent plane and the transmitted parameters (no refitting), adds the
+ * residual, M = R + M*, and repacks the RGBE words (rgbe_out, uint32 [h][w]).
+ * For any params this inverts residual_encode exactly. */
+int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, int h, int w,
+                    int gf_on, const slrme_params* params, uint32_t* rgbe_out,
+                    slrme_stream_t stream);
+
+/* Host, no GPU: copies the library's own constant tables (built by the
+ * library's host code) for inspection: log2_lut[2048] = round(65536 log2(2048+i)),
+ * gamma[256] thresholds (gamma[k] = float(((k-0.5)/255)^2.2), gamma[0] = 0),
+ * kr[16] = float(0.18 2^(-r/16)), wr[16] = float(1800 2^(-r/16)),
+ * quant[64] the steps for `quality` (row-major, vertical frequency first),
+ * dct[64] = round(4096 alpha_u cos((2x+1) u pi / 16)) (row u).  Any pointer
+ * may be NULL.  Returns SLRME_EINVAL for a quality outside 1..100. */
+int slrme_host_tables(int32_t* log2_lut, float* gamma, float* kr, float* wr,
+                      int quality, int32_t* quant, int32_t* dct);
+
+/* Text of the last error reported to the calling thread ("" if none). */
+const char* slrme_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLRME_H */

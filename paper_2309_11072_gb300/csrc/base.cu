@@ -1,0 +1,260 @@
+// Base layer round trip: tone-mapping operator + fixed-point 8x8 DCT,
+// quantise, dequantise, inverse DCT (Sec. II-B, Fig. 2; Sec. IV's JPEG
+// base layer at quality Q).
+//
+// Work unit: one warp owns a band of 8 rows x 32 columns = four 8x8 blocks
+// per colour plane.  Lane l handles block (l >> 3) and row (l & 7):
+//   phase 1  (lane = row):     load 8 pixels of M_R, M_G, M_B, E; tone map;
+//                              forward 1-D DCT along x; T' -> shared
+//   phase 2  (lane = column):  forward 1-D DCT along y, quantise/dequantise,
+//                              inverse 1-D DCT along y; G -> shared
+//   phase 3  (lane = row):     inverse 1-D DCT along x, +128, clamp, store S
+// Only __syncwarp is needed between phases.  The shared tile of a block is
+// 8 rows of stride 9 words and blocks are 72 words apart, which makes both
+// the row-wise and the column-wise accesses of a warp conflict-free.
+//
+// Exactness: every product and sum is an exact int32 (worst cases: 2^21
+// after pass 1, 2^25.1 before the second shift, 2^24 and 2^28.2 in the
+// inverse), so the even/odd factorisation below yields the same integers as
+// the plain matrix products with the same rounding shifts.
+#include "slrme_internal.cuh"
+
+namespace slrme {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kTileWords = 3 * 4 * 72;    // per warp: 3 planes x 4 blocks x (8 x 9)
+
+// Fixed-point DCT constants round(4096 * alpha_u * cos((2x+1) u pi / 16)).
+constexpr int C4 = 1448;   // alpha_0 * 4096 and cos(pi/4) / 2 * 4096
+constexpr int C1 = 2009, C2 = 1892, C3 = 1703, C5 = 1138, C6 = 784, C7 = 400;
+
+struct BaseParams {
+    TmoTables tmo;
+    QuantTable qt;
+};
+
+__device__ __forceinline__ int rshift_round(int v, int s) { return (v + (1 << (s - 1))) >> s; }
+
+// Forward 8-point transform along one line: out[u] = sum_x D[u][x] in[x].
+__device__ __forceinline__ void fdct8(const int (&x)[8], int (&F)[8]) {
+    const int s07 = x[0] + x[7], d07 = x[0] - x[7];
+    const int s16 = x[1] + x[6], d16 = x[1] - x[6];
+    const int s25 = x[2] + x[5], d25 = x[2] - x[5];
+    const int s34 = x[3] + x[4], d34 = x[3] - x[4];
+    const int e0 = s07 + s34, e1 = s16 + s25, e2 = s07 - s34, e3 = s16 - s25;
+    F[0] = C4 * (e0 + e1);
+    F[4] = C4 * (e0 - e1);
+    F[2] = C2 * e2 + C6 * e3;
+    F[6] = C6 * e2 - C2 * e3;
+    F[1] = C1 * d07 + C3 * d16 + C5 * d25 + C7 * d34;
+    F[3] = C3 * d07 - C7 * d16 - C1 * d25 - C5 * d34;
+    F[5] = C5 * d07 - C1 * d16 + C7 * d25 + C3 * d34;
+    F[7] = C7 * d07 - C5 * d16 + C3 * d25 - C1 * d34;
+}
+
+// Inverse 8-point transform along one line: out[x] = sum_u D[u][x] in[u].
+__device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8]) {
+    const int a = C4 * (F[0] + F[4]), b = C4 * (F[0] - F[4]);
+    const int c = C2 * F[2] + C6 * F[6], d = C6 * F[2] - C2 * F[6];
+    const int E0 = a + c, E3 = a - c, E1 = b + d, E2 = b - d;
+    const int O0 = C1 * F[1] + C3 * F[3] + C5 * F[5] + C7 * F[7];
+    const int O1 = C3 * F[1] - C7 * F[3] - C1 * F[5] - C5 * F[7];
+    const int O2 = C5 * F[1] - C1 * F[3] + C7 * F[5] + C3 * F[7];
+    const int O3 = C7 * F[1] - C5 * F[3] + C3 * F[5] - C1 * F[7];
+    x[0] = E0 + O0; x[7] = E0 - O0;
+    x[1] = E1 + O1; x[6] = E1 - O1;
+    x[2] = E2 + O2; x[5] = E2 - O2;
+    x[3] = E3 + O3; x[4] = E3 - O3;
+}
+
+// 8-bit display value: #{k in 1..255 : v >= gamma[k]} by bisection.
+__device__ __forceinline__ int gamma_code(float v, const float* g) {
+    int k = 0;
+#pragma unroll
+    for (int step = 128; step > 0; step >>= 1)
+        if (v >= g[k + step]) k += step;
+    return k;
+}
+
+__device__ __forceinline__ void load8(const uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
+                                      uint8_t (&out)[8]) {
+    y = y < h ? y : h - 1;
+    if (fast && x0 + 8 <= w) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(plane + (int64_t)y * w + x0));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            out[i] = (uint8_t)byte_of(v.x, i);
+            out[4 + i] = (uint8_t)byte_of(v.y, i);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int x = x0 + i;
+            x = x < w ? x : w - 1;
+            out[i] = __ldg(plane + (int64_t)y * w + x);
+        }
+    }
+}
+
+__device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
+                                       const uint32_t lo, const uint32_t hi) {
+    if (y >= h) return;
+    if (fast && x0 + 8 <= w) {
+        *reinterpret_cast<uint2*>(plane + (int64_t)y * w + x0) = make_uint2(lo, hi);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (x0 + i < w) plane[(int64_t)y * w + x0 + i] = (uint8_t)byte_of(i < 4 ? lo : hi, i & 3);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
+                                                   int h, int w, const int64_t* __restrict__ lum_stats,
+                                                   uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3, int fast_io,
+                                                   const BaseParams P) {
+    __shared__ float gam[256];
+    __shared__ int tile[kWarps][kTileWords];
+    __shared__ int keyJ, keyR;
+    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = P.tmo.gamma[i];
+    if (threadIdx.x == 0) key_from_stats(lum_stats, &keyJ, &keyR);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int blk = lane >> 3, sub = lane & 7;     // block in the band, row (phases 1, 3) or column (phase 2)
+    const int J = keyJ;
+    const float kr = P.tmo.kr[keyR], wr = P.tmo.wr[keyR];
+    const int64_t n = (int64_t)h * w;
+    const bool fast = fast_io != 0;
+
+    // quantiser column `sub` of the block: q[v][sub], v = 0..7
+    int qcol[8];
+    uint32_t qmcol[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        qcol[v] = P.qt.q[v * 8 + sub];
+        qmcol[v] = P.qt.qm[v * 8 + sub];
+    }
+
+    int* T = tile[warp];
+    const int bands = (h + 7) >> 3, cols = (w + 31) >> 5;
+    const int64_t tasks = (int64_t)bands * cols;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
+        const int y0 = (int)(t / cols) * 8, xb = (int)(t % cols) * 32;
+        const int x0 = xb + 8 * blk;          // first column of this lane's block
+        const int y = y0 + sub;               // this lane's row in phases 1 and 3
+
+        // ---------------- phase 1: tone map and forward DCT along x
+        {
+            uint8_t mr[8], mg[8], mb[8], ee[8];
+            // rows past the bottom and columns past the right edge replicate the last row/column
+            load8(m3, h, w, y, x0, fast, mr);
+            load8(m3 + n, h, w, y, x0, fast, mg);
+            load8(m3 + 2 * n, h, w, y, x0, fast, mb);
+            load8(e, h, w, y, x0, fast, ee);
+            int sdr[3][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int E = ee[i];
+                if (E == 0) {
+                    sdr[0][i] = sdr[1][i] = sdr[2][i] = 0;
+                    continue;
+                }
+                const int yq = 2126 * (2 * mr[i] + 1) + 7152 * (2 * mg[i] + 1) + 722 * (2 * mb[i] + 1);
+                int d = E - 137 - J;
+                d = d < -100 ? -100 : (d > 100 ? 100 : d);
+                const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
+                const float L = __fmul_rn(__fmul_rn(kr, __int2float_rn(yq)), p2d);
+                const float den = __fadd_rn(1.0f, L);
+                const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
+                sdr[0][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mr[i] + 1)), gam);
+                sdr[1][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mg[i] + 1)), gam);
+                sdr[2][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mb[i] + 1)), gam);
+            }
+            if (sdr3 && x0 < w) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const uint32_t lo = sdr[c][0] | (sdr[c][1] << 8) | (sdr[c][2] << 16) | (sdr[c][3] << 24);
+                    const uint32_t hi = sdr[c][4] | (sdr[c][5] << 8) | (sdr[c][6] << 16) | (sdr[c][7] << 24);
+                    store8(sdr3 + c * n, h, w, y, x0, fast, lo, hi);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                int X[8], F[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) X[i] = sdr[c][i] - 128;
+                fdct8(X, F);
+                int* row = T + (c * 4 + blk) * 72 + sub * 9;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) row[u] = rshift_round(F[u], 9);
+            }
+        }
+        __syncwarp();
+
+        // ---------------- phase 2: along y: forward DCT, quantiser, inverse DCT
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int* col = T + (c * 4 + blk) * 72 + sub;
+            int Tc[8], F[8], G[8];
+#pragma unroll
+            for (int yy = 0; yy < 8; ++yy) Tc[yy] = col[yy * 9];
+            fdct8(Tc, F);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const int f = rshift_round(F[v], 15);
+                const uint32_t a = (uint32_t)(f < 0 ? -f : f);
+                const int lvl = (int)__umulhi((a + (uint32_t)(qcol[v] >> 1)) << 8, qmcol[v]);
+                F[v] = (f < 0 ? -lvl : lvl) * qcol[v];
+            }
+            idct8(F, G);
+#pragma unroll
+            for (int yy = 0; yy < 8; ++yy) col[yy * 9] = rshift_round(G[yy], 9);
+        }
+        __syncwarp();
+
+        // ---------------- phase 3: inverse DCT along x, store S
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int* row = T + (c * 4 + blk) * 72 + sub * 9;
+            int G[8], X[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) G[u] = row[u];
+            idct8(G, X);
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                int s = rshift_round(X[i], 15) + 128;
+                s = s < 0 ? 0 : (s > 255 ? 255 : s);
+                if (i < 4) lo |= (uint32_t)s << (8 * i);
+                else hi |= (uint32_t)s << (8 * (i - 4));
+            }
+            if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, const QuantTable& qt,
+                uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s) {
+    const Geometry g = geometry();
+    BaseParams P;
+    P.tmo = tmo_tables();
+    P.qt = qt;
+    const int64_t n = (int64_t)h * w;
+    const bool fast = (w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
+                      ((uintptr_t)s_dec3 % 8 == 0) && (!sdr3 || (uintptr_t)sdr3 % 8 == 0) && (n % 8 == 0);
+    const int64_t tasks = (int64_t)((h + 7) / 8) * ((w + 31) / 32);
+    int64_t blocks = (tasks + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)g.sms * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_base<<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, fast ? 1 : 0, P);
+    return cuda_status("sdri_base_roundtrip launch");
+}
+
+}  // namespace slrme

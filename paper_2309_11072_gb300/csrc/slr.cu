@@ -1,0 +1,531 @@
+// SLRME (Sec. III-B, Eqs. 8-10) and the enhancement layer (Sec. III-C):
+//   k_fit        Gaussian restoration of S + exponent-binned exact sums
+//   k_solve      per (channel, region) slope/intercept from the sums
+//   k_residual   restoration + Eq. (8) prediction + R = M - M* + histograms
+//   k_decode     restoration + Eq. (8) prediction + M = R + M* + repack
+//
+// Shared structure: a warp owns a strip 256 columns wide (8 per lane) and
+// kStripRows rows tall and slides a 3-row window of S down it, so every row
+// of S is loaded once per strip.  The neighbours a lane needs left and right
+// of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
+// them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
+// 32-bit add (values stay <= 4080).
+#include "slrme_internal.cuh"
+
+namespace slrme {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kStripRows = 16;
+constexpr int kStripCols = 256;
+// Per-lane run accumulators are 32-bit: a run holds at most 8 * kStripRows
+// pixels, and 8 * kStripRows * 4080^2 must stay below 2^32.
+static_assert(8ull * kStripRows * 4080ull * 4080ull < (1ull << 32), "run accumulators would overflow");
+
+struct Row10 {
+    uint32_t lo, hi;   // bytes at x0 .. x0+7
+    uint32_t l, r;     // bytes at x0-1 and x0+8 (edge replicated)
+};
+
+// One row of a plane for the 8 pixels of this lane plus its two neighbours.
+// Must be called by all 32 lanes together (it shuffles).
+__device__ __forceinline__ Row10 fetch_row(const uint8_t* __restrict__ plane, int h, int w, int y, int xs,
+                                           bool fast, int lane) {
+    y = y < 0 ? 0 : (y >= h ? h - 1 : y);
+    const uint8_t* row = plane + (int64_t)y * w;
+    const int x0 = xs + 8 * lane;
+    Row10 R;
+    if (fast && x0 + 8 <= w) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(row + x0));
+        R.lo = v.x;
+        R.hi = v.y;
+    } else {
+        uint32_t b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int x = x0 + i;
+            x = x < w ? x : w - 1;
+            b[i] = __ldg(row + x);
+        }
+        R.lo = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        R.hi = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+    }
+    const uint32_t from_left = __shfl_up_sync(0xffffffffu, R.hi >> 24, 1);
+    const uint32_t from_right = __shfl_down_sync(0xffffffffu, R.lo & 255u, 1);
+    if (lane == 0) {
+        const int xl = x0 > 0 ? x0 - 1 : 0;
+        R.l = __ldg(row + (xl < w ? xl : w - 1));
+    } else {
+        R.l = from_left;
+    }
+    if (lane == 31) {
+        const int xr = x0 + 8 < w ? x0 + 8 : w - 1;
+        R.r = __ldg(row + xr);
+    } else {
+        R.r = from_right;
+    }
+    return R;
+}
+
+// 16-bit pairs (pixel 2k in the low half, 2k+1 in the high half) of the 8 bytes.
+__device__ __forceinline__ void unpack_pairs(const Row10& a, uint32_t (&p)[4]) {
+    p[0] = __byte_perm(a.lo, 0, 0x4140);
+    p[1] = __byte_perm(a.lo, 0, 0x4342);
+    p[2] = __byte_perm(a.hi, 0, 0x4140);
+    p[3] = __byte_perm(a.hi, 0, 0x4342);
+}
+
+// x = 16 S* (3x3 binomial, gf_on = 1) or x = 16 S (gf_on = 0), as 16-bit pairs.
+__device__ __forceinline__ void gf_pairs(const Row10& a, const Row10& b, const Row10& c, bool gf_on,
+                                         uint32_t (&X)[4]) {
+    uint32_t pb[4];
+    unpack_pairs(b, pb);
+    if (!gf_on) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) X[k] = pb[k] << 4;
+        return;
+    }
+    uint32_t pa[4], pc[4], V[4];
+    unpack_pairs(a, pa);
+    unpack_pairs(c, pc);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) V[k] = pa[k] + 2u * pb[k] + pc[k];
+    const uint32_t Vl = a.l + 2u * b.l + c.l, Vr = a.r + 2u * b.r + c.r;
+    const uint32_t L0 = __byte_perm(Vl, V[0], 0x5410);     // (V[-1], V[0])
+    const uint32_t L1 = __byte_perm(V[0], V[1], 0x5432);   // (V[1], V[2])
+    const uint32_t L2 = __byte_perm(V[1], V[2], 0x5432);   // (V[3], V[4])
+    const uint32_t L3 = __byte_perm(V[2], V[3], 0x5432);   // (V[5], V[6])
+    const uint32_t R3 = __byte_perm(V[3], Vr, 0x5432);     // (V[7], V[8])
+    X[0] = L0 + 2u * V[0] + L1;
+    X[1] = L1 + 2u * V[1] + L2;
+    X[2] = L2 + 2u * V[2] + L3;
+    X[3] = L3 + 2u * V[3] + R3;
+}
+
+__device__ __forceinline__ int half_of(const uint32_t (&X)[4], int i) {
+    return (int)((X[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+}
+
+__device__ __forceinline__ void load_bytes8(const uint8_t* __restrict__ plane, int w, int y, int x0, bool fast,
+                                            uint32_t& lo, uint32_t& hi) {
+    const uint8_t* row = plane + (int64_t)y * w;
+    if (fast && x0 + 8 <= w) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(row + x0));
+        lo = v.x;
+        hi = v.y;
+    } else {
+        uint32_t b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) b[i] = (x0 + i < w) ? (uint32_t)__ldg(row + x0 + i) : 0u;
+        lo = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+        hi = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+    }
+}
+
+// Eq. (8): round(a x + b) clipped to [0, 255]; float32 multiply then add,
+// half away from zero.  NaN and t <= 0 give 0.
+__device__ __forceinline__ int predict(float a, float b, int x) {
+    float t = __fadd_rn(__fmul_rn(a, __int2float_rn(x)), b);
+    t = fminf(fmaxf(t, 0.0f), 255.0f);
+    const int r = __float2int_rz(t);
+    return r + (__fsub_rn(t, __int2float_rn(r)) >= 0.5f ? 1 : 0);
+}
+
+// ====================================================================== fit
+
+struct RunAcc {
+    int E;            // region of the run, -1 = empty
+    uint32_t n;
+    uint32_t sx[3], sy[3], sxy[3], sxx[3];
+};
+
+__device__ __forceinline__ void run_reset(RunAcc& a, int E) {
+    a.E = E;
+    a.n = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.sx[c] = a.sy[c] = a.sxy[c] = a.sxx[c] = 0;
+}
+
+__device__ __forceinline__ void run_flush(const RunAcc& a, unsigned long long* bins) {
+    if (a.E < 0 || a.n == 0) return;
+    unsigned long long* b = bins + a.E * kNsum;
+    atomicAdd(b, (unsigned long long)a.n);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        atomicAdd(b + 1 + 4 * c, (unsigned long long)a.sx[c]);
+        atomicAdd(b + 2 + 4 * c, (unsigned long long)a.sy[c]);
+        atomicAdd(b + 3 + 4 * c, (unsigned long long)a.sxy[c]);
+        atomicAdd(b + 4 + 4 * c, (unsigned long long)a.sxx[c]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
+                                                  const uint8_t* __restrict__ e, int h, int w, int gf_on, int fast_io,
+                                                  unsigned long long* __restrict__ gbins) {
+    __shared__ unsigned long long bins[kNbin * kNsum];
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins[i] = 0ull;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = (int64_t)h * w;
+    const bool fast = fast_io != 0, gf = gf_on != 0;
+    const int bands = (h + kStripRows - 1) / kStripRows, cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)bands * cols;
+
+    RunAcc acc;
+    run_reset(acc, -1);
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
+        const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
+        const int x0 = xs + 8 * lane;
+        const int y1 = min(y0 + kStripRows, h);
+        Row10 prv[3], cur[3], nxt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
+            prv[c] = gf ? fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane) : cur[c];
+        }
+        for (int y = y0; y < y1; ++y) {
+            uint32_t X[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nxt[c] = gf ? fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane) : cur[c];
+                gf_pairs(prv[c], cur[c], nxt[c], gf, X[c]);
+            }
+            if (x0 < w) {
+                uint32_t mlo[3], mhi[3], elo, ehi;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) load_bytes8(m3 + c * n, w, y, x0, fast, mlo[c], mhi[c]);
+                load_bytes8(e, w, y, x0, fast, elo, ehi);
+                const bool full = x0 + 8 <= w;
+                const bool uniform = full && elo == ehi && elo == __byte_perm(elo, 0, 0x0000);
+                if (uniform) {
+                    const int E = (int)(elo & 255u);
+                    if (E != acc.E) {
+                        run_flush(acc, bins);
+                        run_reset(acc, E);
+                    }
+                    acc.n += 8;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const uint32_t ps = X[c][0] + X[c][1] + X[c][2] + X[c][3];
+                        acc.sx[c] += (ps & 0xFFFFu) + (ps >> 16);
+                        acc.sy[c] = __dp4a(mlo[c], 0x01010101u, __dp4a(mhi[c], 0x01010101u, acc.sy[c]));
+                        acc.sxy[c] = __dp2a_lo(X[c][0], mlo[c], acc.sxy[c]);
+                        acc.sxy[c] = __dp2a_hi(X[c][1], mlo[c], acc.sxy[c]);
+                        acc.sxy[c] = __dp2a_lo(X[c][2], mhi[c], acc.sxy[c]);
+                        acc.sxy[c] = __dp2a_hi(X[c][3], mhi[c], acc.sxy[c]);
+                        uint32_t q = acc.sxx[c];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t lo16 = X[c][k] & 0xFFFFu, hi16 = X[c][k] >> 16;
+                            q += lo16 * lo16 + hi16 * hi16;
+                        }
+                        acc.sxx[c] = q;
+                    }
+                } else {
+                    const int cnt = min(8, w - x0);
+                    for (int i = 0; i < cnt; ++i) {
+                        const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
+                        if (E != acc.E) {
+                            run_flush(acc, bins);
+                            run_reset(acc, E);
+                        }
+                        acc.n += 1;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const uint32_t x = (uint32_t)half_of(X[c], i);
+                            const uint32_t yv = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
+                            acc.sx[c] += x;
+                            acc.sy[c] += yv;
+                            acc.sxy[c] += x * yv;
+                            acc.sxx[c] += x * x;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                prv[c] = cur[c];
+                cur[c] = nxt[c];
+            }
+        }
+        // keep every run within one strip so the 32-bit accumulators cannot overflow
+        run_flush(acc, bins);
+        run_reset(acc, -1);
+    }
+    __syncthreads();
+    for (int E = threadIdx.x; E < kNbin; E += kThreads) {
+        const unsigned long long* b = bins + E * kNsum;
+        if (b[0] == 0ull) continue;
+#pragma unroll
+        for (int j = 0; j < kNsum; ++j) atomicAdd(gbins + E * kNsum + j, b[j]);
+    }
+}
+
+// ====================================================================== solve
+
+// Correctly rounded (nearest, ties to even) signed 128-bit integer -> double.
+__device__ __forceinline__ double i128_to_f64(__int128 v) {
+    if (v == 0) return 0.0;
+    const bool neg = v < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+    double r;
+    if (nb <= 53) {
+        r = __ull2double_rn(lo);
+    } else {
+        const int sh = nb - 53;
+        uint64_t mant = (uint64_t)(u >> sh);
+        const unsigned __int128 rem = u - ((unsigned __int128)mant << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) mant += 1;   // 2^53 is still exact
+        r = __dmul_rn(__ull2double_rn(mant), __longlong_as_double((long long)(1023 + sh) << 52));
+    }
+    return neg ? -r : r;
+}
+
+__global__ void __launch_bounds__(768) k_solve(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
+    const int c = threadIdx.x >> 8, E = threadIdx.x & 255;
+    const int64_t* s = sums + E * kNsum;
+    const int64_t N = s[0];
+    float a = 0.0f, b = 0.0f;
+    if (N > 0) {
+        const int64_t sx = s[1 + 4 * c], sy = s[2 + 4 * c], sxy = s[3 + 4 * c], sxx = s[4 + 4 * c];
+        const __int128 dxx = (__int128)N * sxx - (__int128)sx * sx;
+        const __int128 dxy = (__int128)N * sxy - (__int128)sx * sy;
+        if (dxx == 0) {
+            b = __double2float_rn(__ddiv_rn(__ll2double_rn(sy), __ll2double_rn(N)));
+        } else {
+            a = __double2float_rn(__ddiv_rn(i128_to_f64(dxy), i128_to_f64(dxx)));
+            const double t = __dmul_rn((double)a, __ll2double_rn(sx));
+            b = __double2float_rn(__ddiv_rn(__dsub_rn(__ll2double_rn(sy), t), __ll2double_rn(N)));
+        }
+    }
+    P->a[c][E] = a;
+    P->b[c][E] = b;
+    const int used = __syncthreads_count(c == 0 && N > 0);
+    if (c == 0) P->n[E] = (int32_t)N;
+    if (threadIdx.x == 0) {
+        P->n_used = used;
+        P->reserved[0] = P->reserved[1] = P->reserved[2] = 0;
+    }
+}
+
+// ====================================================================== residual
+
+__device__ __forceinline__ void load_params(const slrme_params* __restrict__ P, float* sa, float* sb) {
+    for (int i = threadIdx.x; i < 3 * kNbin; i += blockDim.x) {
+        sa[i] = (&P->a[0][0])[i];
+        sb[i] = (&P->b[0][0])[i];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
+                                                       const uint8_t* __restrict__ e, int h, int w, int gf_on,
+                                                       int fast_io, const slrme_params* __restrict__ P,
+                                                       int16_t* __restrict__ r3, uint32_t* __restrict__ ghist) {
+    __shared__ float sa[3 * kNbin], sb[3 * kNbin];
+    __shared__ uint32_t hist[3 * kNres];
+    load_params(P, sa, sb);
+    if (ghist)
+        for (int i = threadIdx.x; i < 3 * kNres; i += kThreads) hist[i] = 0u;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = (int64_t)h * w;
+    const bool fast = fast_io != 0, gf = gf_on != 0;
+    const int bands = (h + kStripRows - 1) / kStripRows, cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)bands * cols;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
+        const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
+        const int x0 = xs + 8 * lane;
+        const int y1 = min(y0 + kStripRows, h);
+        Row10 prv[3], cur[3], nxt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
+            prv[c] = gf ? fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane) : cur[c];
+        }
+        for (int y = y0; y < y1; ++y) {
+            uint32_t X[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nxt[c] = gf ? fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane) : cur[c];
+                gf_pairs(prv[c], cur[c], nxt[c], gf, X[c]);
+            }
+            if (x0 < w) {
+                uint32_t elo, ehi;
+                load_bytes8(e, w, y, x0, fast, elo, ehi);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t mlo, mhi;
+                    load_bytes8(m3 + c * n, w, y, x0, fast, mlo, mhi);
+                    int r[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
+                        const int M = (int)byte_of(i < 4 ? mlo : mhi, i & 3);
+                        r[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
+                    }
+                    int16_t* row = r3 + c * n + (int64_t)y * w + x0;
+                    if (fast && x0 + 8 <= w) {
+                        uint4 v;
+                        v.x = (uint32_t)(r[0] & 0xFFFF) | ((uint32_t)r[1] << 16);
+                        v.y = (uint32_t)(r[2] & 0xFFFF) | ((uint32_t)r[3] << 16);
+                        v.z = (uint32_t)(r[4] & 0xFFFF) | ((uint32_t)r[5] << 16);
+                        v.w = (uint32_t)(r[6] & 0xFFFF) | ((uint32_t)r[7] << 16);
+                        *reinterpret_cast<uint4*>(row) = v;
+                        if (ghist) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + r[i] + 255], 1u);
+                        }
+                    } else {
+                        const int cnt = min(8, w - x0);
+                        for (int i = 0; i < cnt; ++i) {
+                            row[i] = (int16_t)r[i];
+                            if (ghist) atomicAdd(&hist[c * kNres + r[i] + 255], 1u);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                prv[c] = cur[c];
+                cur[c] = nxt[c];
+            }
+        }
+    }
+    if (ghist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * kNres; i += kThreads)
+            if (hist[i]) atomicAdd(ghist + i, hist[i]);
+    }
+}
+
+// ====================================================================== decode
+
+__global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ e,
+                                                     const int16_t* __restrict__ r3, int h, int w, int gf_on,
+                                                     int fast_io, const slrme_params* __restrict__ P,
+                                                     uint32_t* __restrict__ out) {
+    __shared__ float sa[3 * kNbin], sb[3 * kNbin];
+    load_params(P, sa, sb);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n = (int64_t)h * w;
+    const bool fast = fast_io != 0, gf = gf_on != 0;
+    const int bands = (h + kStripRows - 1) / kStripRows, cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)bands * cols;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
+        const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
+        const int x0 = xs + 8 * lane;
+        const int y1 = min(y0 + kStripRows, h);
+        Row10 prv[3], cur[3], nxt[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
+            prv[c] = gf ? fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane) : cur[c];
+        }
+        for (int y = y0; y < y1; ++y) {
+            uint32_t X[3][4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nxt[c] = gf ? fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane) : cur[c];
+                gf_pairs(prv[c], cur[c], nxt[c], gf, X[c]);
+            }
+            if (x0 < w) {
+                uint32_t elo, ehi;
+                load_bytes8(e, w, y, x0, fast, elo, ehi);
+                uint32_t word[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? elo : ehi, i & 3) << 24;
+                const bool vec = fast && x0 + 8 <= w;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int16_t* row = r3 + c * n + (int64_t)y * w + x0;
+                    int r[8];
+                    if (vec) {
+                        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row));
+                        const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            r[2 * k] = (int)(int16_t)(q[k] & 0xFFFFu);
+                            r[2 * k + 1] = (int)(int16_t)(q[k] >> 16);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) r[i] = (x0 + i < w) ? (int)__ldg(row + i) : 0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int E = (int)(word[i] >> 24);
+                        const int M = r[i] + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
+                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
+                    }
+                }
+                uint32_t* orow = out + (int64_t)y * w + x0;
+                if (vec) {
+                    reinterpret_cast<uint4*>(orow)[0] = make_uint4(word[0], word[1], word[2], word[3]);
+                    reinterpret_cast<uint4*>(orow)[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                } else {
+                    const int cnt = min(8, w - x0);
+                    for (int i = 0; i < cnt; ++i) orow[i] = word[i];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                prv[c] = cur[c];
+                cur[c] = nxt[c];
+            }
+        }
+    }
+}
+
+int strip_blocks(int h, int w, int per_sm) {
+    const int64_t tasks = (int64_t)((h + kStripRows - 1) / kStripRows) * ((w + kStripCols - 1) / kStripCols);
+    int64_t blocks = (tasks + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)geometry().sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    return (int)(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+
+int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on, int64_t* bin_sums,
+               slrme_params* params, cudaStream_t s) {
+    if (cudaMemsetAsync(bin_sums, 0, sizeof(int64_t) * kNbin * kNsum, s) != cudaSuccess)
+        return cuda_status("slr_fit memset");
+    const int64_t n = (int64_t)h * w;
+    if (n > 0) {
+        const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
+                          ((uintptr_t)e % 8 == 0);
+        k_fit<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0,
+                                                         reinterpret_cast<unsigned long long*>(bin_sums));
+        int st = cuda_status("slr_fit launch");
+        if (st != SLRME_OK) return st;
+    }
+    k_solve<<<1, 768, 0, s>>>(bin_sums, params);
+    return cuda_status("slr_fit solve launch");
+}
+
+int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
+                           const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
+    const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
+                      ((uintptr_t)e % 8 == 0) && ((uintptr_t)r3 % 16 == 0);
+    k_residual<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, params, r3, hist);
+    return cuda_status("residual_encode launch");
+}
+
+int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w, int gf_on,
+                           const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s) {
+    const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
+                      ((uintptr_t)r3 % 16 == 0) && ((uintptr_t)rgbe_out % 16 == 0);
+    k_decode<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, params, rgbe_out);
+    return cuda_status("residual_decode launch");
+}
+
+}  // namespace slrme

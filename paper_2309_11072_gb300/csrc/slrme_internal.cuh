@@ -1,0 +1,83 @@
+// Internal declarations shared by the library's translation units.
+// Device helpers, constant tables passed to kernels by value, and the
+// launcher functions behind the C ABI in include/slrme.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/slrme.h"
+
+namespace slrme {
+
+constexpr int kNbin = SLRME_NBIN;
+constexpr int kNsum = SLRME_NSUM;
+constexpr int kNres = SLRME_NRES;
+
+// ---------------------------------------------------------------- tables
+// Tone-mapping constants, built once on the host (tables.cu).
+struct TmoTables {
+    float gamma[256];   // gamma[k] = float(((k - 0.5) / 255)^2.2), gamma[0] = 0
+    float kr[16];       // float(0.18 * 2^(-r/16))
+    float wr[16];       // float(1800 * 2^(-r/16))
+};
+
+// Quantiser for one quality: steps q[v*8+u] and the reciprocal multipliers
+// qm = ceil(2^24 / q), so floor(n / q) == umulhi(n << 8, qm) for 0 <= n < 4096.
+struct QuantTable {
+    int32_t q[64];
+    uint32_t qm[64];
+};
+
+struct Log2Table {
+    int32_t lut[2048];  // round(65536 * log2(2048 + i))
+};
+
+const TmoTables& tmo_tables();
+const Log2Table& log2_table();
+bool quant_table(int quality, QuantTable* out);
+
+// ---------------------------------------------------------------- launch geometry
+struct Geometry {
+    int sms;
+};
+Geometry geometry();
+
+// ---------------------------------------------------------------- error reporting
+void set_error(const char* fmt, ...);
+int cuda_status(const char* what);   // SLRME_OK or SLRME_ECUDA after a launch
+
+// ---------------------------------------------------------------- launchers
+int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e,
+                 int64_t* lum_stats, cudaStream_t s);
+int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s);
+int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
+               int64_t* bin_sums, slrme_params* params, cudaStream_t s);
+int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w,
+                           int gf_on, const slrme_params* params, int16_t* r3, uint32_t* hist,
+                           cudaStream_t s);
+int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w,
+                           int gf_on, const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ int64_t floor_div64(int64_t a, int64_t b) {   // b > 0
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+// Key of the tone-mapping operator from the log-average statistic:
+// j = floor((sum + 2048 n) / (4096 n)) = round-half-up(16 mu), j = 16 J + r.
+__device__ __forceinline__ void key_from_stats(const int64_t* stats, int* J, int* r) {
+    int64_t s = stats[0], n = stats[1];
+    int64_t j = 0;
+    if (n > 0) j = floor_div64(s + 2048 * n, 4096 * n);
+    int64_t JJ = floor_div64(j, 16);
+    *J = (int)JJ;
+    *r = (int)(j - 16 * JJ);
+}
+
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int i) { return (w >> (8 * i)) & 255u; }
+
+}  // namespace slrme

@@ -1,0 +1,152 @@
+// RGBE split (Sec. II-A, Sec. III-A) fused with the log-average luminance
+// statistic of the tone-mapping operator.
+//
+// HBM-bound: 4 bytes read and 4 bytes written per pixel.  The vector path
+// reads 16 bytes (4 words) per thread per step with non-allocating loads and
+// writes one 32-bit word to each of the four planes; the byte transposition
+// is 6 byte-permutes per 4 pixels.  The statistic is reduced per thread in
+// int64, then per warp and block, with one 64-bit atomic per block.
+#include "slrme_internal.cuh"
+
+namespace slrme {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// l(p) of one word (0 for E = 0), from the table in shared memory.
+__device__ __forceinline__ int32_t log_lum(uint32_t wd, const int32_t* lut) {
+    const int E = (int)(wd >> 24);
+    if (E == 0) return 0;
+    const int yq = 2126 * (2 * (int)(wd & 255u) + 1) + 7152 * (2 * (int)((wd >> 8) & 255u) + 1) +
+                   722 * (2 * (int)((wd >> 16) & 255u) + 1);
+    const int k = (32 - __clz(yq)) - 12;        // bitlen(Yq) - 12, in [2, 11]
+    const int m = yq >> k;                       // 2048 .. 4095
+    return 65536 * (E - 137 + k) + lut[m - 2048];
+}
+
+__device__ __forceinline__ void block_reduce_add(int64_t s, int64_t c, int64_t* stats) {
+    __shared__ int64_t red[2][kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = s;
+        red[1][wid] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t ts = 0, tc = 0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            ts += red[0][i];
+            tc += red[1][i];
+        }
+        if (tc != 0 || ts != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(stats), (unsigned long long)ts);
+            atomicAdd(reinterpret_cast<unsigned long long*>(stats + 1), (unsigned long long)tc);
+        }
+    }
+}
+
+// Vector path: n % 4 == 0, rgbe 16-byte aligned, planes 4-byte aligned.
+__global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict__ rgbe4, int64_t nv,
+                                                        uint32_t* __restrict__ mR, uint32_t* __restrict__ mG,
+                                                        uint32_t* __restrict__ mB, uint32_t* __restrict__ eP,
+                                                        int64_t* __restrict__ stats, const Log2Table tab) {
+    __shared__ int32_t lut[2048];
+    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = tab.lut[i];
+    __syncthreads();
+
+    int64_t s = 0, c = 0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    constexpr int U = 4;   // independent 16-byte loads in flight per thread
+    for (; i + (U - 1) * stride < nv; i += U * stride) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_stream(rgbe4 + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t lo01 = __byte_perm(v[u].x, v[u].y, 0x5140), hi01 = __byte_perm(v[u].x, v[u].y, 0x7362);
+            const uint32_t lo23 = __byte_perm(v[u].z, v[u].w, 0x5140), hi23 = __byte_perm(v[u].z, v[u].w, 0x7362);
+            const int64_t j = i + u * stride;
+            mR[j] = __byte_perm(lo01, lo23, 0x5410);
+            mG[j] = __byte_perm(lo01, lo23, 0x7632);
+            mB[j] = __byte_perm(hi01, hi23, 0x5410);
+            eP[j] = __byte_perm(hi01, hi23, 0x7632);
+            int32_t part = log_lum(v[u].x, lut) + log_lum(v[u].y, lut);
+            int32_t part2 = log_lum(v[u].z, lut) + log_lum(v[u].w, lut);
+            s += (int64_t)part + part2;
+            c += (v[u].x >> 24 != 0) + (v[u].y >> 24 != 0) + (v[u].z >> 24 != 0) + (v[u].w >> 24 != 0);
+        }
+    }
+    for (; i < nv; i += stride) {
+        const uint4 v = ld_stream(rgbe4 + i);
+        const uint32_t lo01 = __byte_perm(v.x, v.y, 0x5140), hi01 = __byte_perm(v.x, v.y, 0x7362);
+        const uint32_t lo23 = __byte_perm(v.z, v.w, 0x5140), hi23 = __byte_perm(v.z, v.w, 0x7362);
+        mR[i] = __byte_perm(lo01, lo23, 0x5410);
+        mG[i] = __byte_perm(lo01, lo23, 0x7632);
+        mB[i] = __byte_perm(hi01, hi23, 0x5410);
+        eP[i] = __byte_perm(hi01, hi23, 0x7632);
+        s += (int64_t)log_lum(v.x, lut) + log_lum(v.y, lut) + log_lum(v.z, lut) + log_lum(v.w, lut);
+        c += (v.x >> 24 != 0) + (v.y >> 24 != 0) + (v.z >> 24 != 0) + (v.w >> 24 != 0);
+    }
+    block_reduce_add(s, c, stats);
+}
+
+// Scalar path: any size and alignment, one word per thread per step.
+__global__ void __launch_bounds__(kThreads) k_split_scalar(const uint32_t* __restrict__ rgbe, int64_t n,
+                                                           uint8_t* __restrict__ m3, uint8_t* __restrict__ e,
+                                                           int64_t* __restrict__ stats, const Log2Table tab) {
+    __shared__ int32_t lut[2048];
+    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = tab.lut[i];
+    __syncthreads();
+    int64_t s = 0, c = 0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        const uint32_t wd = __ldg(rgbe + i);
+        m3[i] = (uint8_t)(wd & 255u);
+        m3[n + i] = (uint8_t)((wd >> 8) & 255u);
+        m3[2 * n + i] = (uint8_t)((wd >> 16) & 255u);
+        e[i] = (uint8_t)(wd >> 24);
+        s += log_lum(wd, lut);
+        c += (wd >> 24) != 0;
+    }
+    block_reduce_add(s, c, stats);
+}
+
+}  // namespace
+
+int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e, int64_t* lum_stats, cudaStream_t s) {
+    const Geometry g = geometry();
+    const bool vec = (n % 4 == 0) && ((uintptr_t)rgbe % 16 == 0) && ((uintptr_t)m3 % 4 == 0) &&
+                     ((uintptr_t)e % 4 == 0);
+    const int64_t units = vec ? n / 4 : n;
+    int64_t blocks = (units + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)g.sms * 8;   // 8 resident blocks of 256 threads per SM
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (vec) {
+        const int64_t nv = n / 4;
+        k_split_vec<<<(unsigned)blocks, kThreads, 0, s>>>(
+            reinterpret_cast<const uint4*>(rgbe), nv, reinterpret_cast<uint32_t*>(m3),
+            reinterpret_cast<uint32_t*>(m3 + n), reinterpret_cast<uint32_t*>(m3 + 2 * n),
+            reinterpret_cast<uint32_t*>(e), lum_stats, log2_table());
+    } else {
+        k_split_scalar<<<(unsigned)blocks, kThreads, 0, s>>>(rgbe, n, m3, e, lum_stats, log2_table());
+    }
+    return cuda_status("rgbe_split launch");
+}
+
+}  // namespace slrme

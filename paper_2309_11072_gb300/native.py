@@ -1,0 +1,145 @@
+"""ctypes binding of the C ABI in ``include/slrme.h``.
+
+Argument marshalling only: each function takes torch CUDA tensors (or raw
+device addresses) and forwards pointers, sizes and the stream to the entry
+point of the same name in ``_build/libslrme.so``.  A non-zero status raises
+``SlrmeError`` with the library's message.  There is no fallback: if the
+library cannot be loaded the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+HEADER = os.path.join(ROOT, "include", "slrme.h")
+
+SLRME_NBIN, SLRME_NSUM, SLRME_NRES = 256, 13, 511
+PARAMS_BYTES = 7184
+
+
+class SlrmeError(RuntimeError):
+    def __init__(self, name: str, code: int, msg: str):
+        super().__init__(f"{name} failed with status {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+_SIGS = {
+    "rgbe_split": [_vp, _i32, _i32, _vp, _vp, _vp, _vp],
+    "rgbe_key_scale": [_vp, _vp, _vp],
+    "sdri_base_roundtrip": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp],
+    "slr_fit": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
+    "residual_encode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
+    "residual_decode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
+    "slrme_host_tables": [_vp, _vp, _vp, _vp, _i32, _vp, _vp],
+}
+
+
+def library_path() -> str:
+    from . import build
+    return build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build
+            path = build.build()
+            L = ctypes.CDLL(path)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.slrme_last_error.restype = ctypes.c_char_p
+            L.slrme_last_error.argtypes = []
+            L.slr_fit_workspace_bytes.restype = ctypes.c_size_t
+            L.slr_fit_workspace_bytes.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(name: str, code: int) -> None:
+    if code != 0:
+        raise SlrmeError(name, code, lib().slrme_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().slrme_last_error().decode()
+
+
+# ---------------------------------------------------------------- entry points
+
+def rgbe_split(rgbe, h: int, w: int, m3, e, lum_stats, stream=None) -> None:
+    _check("rgbe_split", lib().rgbe_split(_ptr(rgbe), h, w, _ptr(m3), _ptr(e), _ptr(lum_stats), _stream(stream)))
+
+
+def rgbe_key_scale(lum_stats_host) -> tuple:
+    """Host helper: (J, r) from a host (CPU) pair of int64 statistics."""
+    buf = (ctypes.c_int64 * 2)(int(lum_stats_host[0]), int(lum_stats_host[1]))
+    J, r = ctypes.c_int32(), ctypes.c_int32()
+    _check("rgbe_key_scale", lib().rgbe_key_scale(ctypes.addressof(buf), ctypes.addressof(J), ctypes.addressof(r)))
+    return J.value, r.value
+
+
+def sdri_base_roundtrip(m3, e, h: int, w: int, lum_stats, quality: int, s_dec3, sdr3=None, stream=None) -> None:
+    _check("sdri_base_roundtrip", lib().sdri_base_roundtrip(_ptr(m3), _ptr(e), h, w, _ptr(lum_stats), quality,
+                                                            _ptr(s_dec3), _ptr(sdr3), _stream(stream)))
+
+
+def slr_fit(s_dec3, m3, e, h: int, w: int, gf_on: int, bin_sums, params, stream=None) -> None:
+    _check("slr_fit", lib().slr_fit(_ptr(s_dec3), _ptr(m3), _ptr(e), h, w, int(gf_on), _ptr(bin_sums),
+                                    _ptr(params), _stream(stream)))
+
+
+def slr_fit_workspace_bytes() -> int:
+    return int(lib().slr_fit_workspace_bytes())
+
+
+def residual_encode(s_dec3, m3, e, h: int, w: int, gf_on: int, params, r3, hist=None, stream=None) -> None:
+    _check("residual_encode", lib().residual_encode(_ptr(s_dec3), _ptr(m3), _ptr(e), h, w, int(gf_on),
+                                                    _ptr(params), _ptr(r3), _ptr(hist), _stream(stream)))
+
+
+def residual_decode(s_dec3, e, r3, h: int, w: int, gf_on: int, params, rgbe_out, stream=None) -> None:
+    _check("residual_decode", lib().residual_decode(_ptr(s_dec3), _ptr(e), _ptr(r3), h, w, int(gf_on),
+                                                    _ptr(params), _ptr(rgbe_out), _stream(stream)))
+
+
+def host_tables(quality: int = 50) -> dict:
+    """The library's own constant tables (host code, no GPU)."""
+    import numpy as np
+    lut = np.empty(2048, np.int32)
+    gam = np.empty(256, np.float32)
+    kr = np.empty(16, np.float32)
+    wr = np.empty(16, np.float32)
+    q = np.empty(64, np.int32)
+    d = np.empty(64, np.int32)
+    _check("slrme_host_tables", lib().slrme_host_tables(lut.ctypes.data, gam.ctypes.data, kr.ctypes.data,
+                                                        wr.ctypes.data, quality, q.ctypes.data, d.ctypes.data))
+    return dict(log2_lut=lut, gamma=gam, kr=kr, wr=wr, quant=q.reshape(8, 8), dct=d.reshape(8, 8))

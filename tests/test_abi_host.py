@@ -1,0 +1,112 @@
+"""CPU-only checks of the CUDA library: it builds for sm_103a, loads,
+exports every entry point declared in include/*.h, rejects bad arguments
+before touching the GPU, and its host-built constant tables equal the
+oracle's (built independently) and the closed forms they come from."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy.fft import dct
+
+from oracle import oracle as O
+from paper_2309_11072_gb300 import native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            if m.group(1) not in ("if", "defined", "sizeof"):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = native.lib()
+    names = _declared_functions()
+    assert "rgbe_split" in names and "residual_decode" in names and len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), f"missing export {name}"
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_2309_11072_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert os.path.exists(native.library_path())
+
+
+def test_host_tables_equal_oracle_tables():
+    t = native.host_tables(75)
+    assert np.array_equal(t["log2_lut"], O.log2_table())
+    assert np.array_equal(t["gamma"].view(np.uint32), O.gamma_thresholds().view(np.uint32))
+    kr, wr = O.key_tables()
+    assert np.array_equal(t["kr"].view(np.uint32), kr.view(np.uint32))
+    assert np.array_equal(t["wr"].view(np.uint32), wr.view(np.uint32))
+    for q in (1, 25, 50, 75, 90, 100):
+        assert np.array_equal(native.host_tables(q)["quant"], O.quant_table(q))
+
+
+def test_library_dct_constants_against_scipy():
+    d = native.host_tables()["dct"]
+    ref = np.round(dct(np.eye(8), type=2, norm="ortho", axis=0) * 4096.0)
+    assert np.array_equal(d, ref.astype(np.int32))
+
+
+@pytest.mark.parametrize("num,n", [(0, 0), (5, 1), (-1, 1), (-2049, 3), (10 ** 15, 77777), (-(10 ** 14), 12345)])
+def test_key_scale_matches_oracle(num, n):
+    assert native.rgbe_key_scale([num, n]) == O.key(np.array([num, n], np.int64))
+
+
+def test_bad_arguments_rejected_before_any_gpu_work():
+    L = native.lib()
+    EINVAL = -1
+    assert L.rgbe_split(None, 4, 4, None, None, None, None) == EINVAL
+    assert L.rgbe_split(None, -1, 4, None, None, None, None) == EINVAL
+    assert L.rgbe_split(None, 65536, 32768, None, None, None, None) == EINVAL     # h*w = 2^31
+    assert L.sdri_base_roundtrip(1, 1, 8, 8, 1, 0, 1, None, None) == EINVAL       # quality 0
+    assert L.sdri_base_roundtrip(1, 1, 8, 8, 1, 101, 1, None, None) == EINVAL     # quality 101
+    assert "quality" in native.last_error()
+    assert L.slr_fit(1, 1, 1, 8, 8, 2, 1, 1, None) == EINVAL                      # gf_on 2
+    assert L.slr_fit(1, 1, 1, 8, 8, 1, None, 1, None) == EINVAL                   # no workspace
+    assert L.residual_encode(None, 1, 1, 8, 8, 1, 1, 1, None, None) == EINVAL
+    assert L.residual_decode(1, 1, 1, 8, 8, 1, None, 1, None) == EINVAL
+    assert L.rgbe_key_scale(None, None, None) == EINVAL
+    buf = (ctypes.c_int64 * 2)(0, -5)
+    J, r = ctypes.c_int32(), ctypes.c_int32()
+    assert L.rgbe_key_scale(ctypes.addressof(buf), ctypes.addressof(J), ctypes.addressof(r)) == EINVAL
+    assert native.slr_fit_workspace_bytes() == 256 * 13 * 8
+
+
+def test_misaligned_typed_pointers_rejected():
+    # typed buffers must be naturally aligned; the check runs before any launch
+    L = native.lib()
+    EINVAL = -1
+    assert L.rgbe_split(0x1001, 4, 4, 0x2000, 0x3000, 0x4000, None) == EINVAL      # uint32 words at odd address
+    assert L.rgbe_split(0x1000, 4, 4, 0x2000, 0x3000, 0x4004, None) == EINVAL      # int64 stats at 4 mod 8
+    assert L.sdri_base_roundtrip(0x1000, 0x2000, 8, 8, 0x3002, 50, 0x4000, None, None) == EINVAL
+    assert L.slr_fit(0x1000, 0x2000, 0x3000, 8, 8, 1, 0x4004, 0x5000, None) == EINVAL
+    assert L.slr_fit(0x1000, 0x2000, 0x3000, 8, 8, 1, 0x4000, 0x5002, None) == EINVAL
+    assert L.residual_encode(0x1000, 0x2000, 0x3000, 8, 8, 1, 0x4000, 0x5001, None, None) == EINVAL
+    assert L.residual_encode(0x1000, 0x2000, 0x3000, 8, 8, 1, 0x4000, 0x5000, 0x6002, None) == EINVAL
+    assert L.residual_decode(0x1000, 0x2000, 0x3001, 8, 8, 1, 0x4000, 0x5000, None) == EINVAL
+    assert L.residual_decode(0x1000, 0x2000, 0x3000, 8, 8, 1, 0x4000, 0x5002, None) == EINVAL
+    assert "aligned" in native.last_error()
+
+
+def test_params_layout_roundtrip():
+    from paper_2309_11072_gb300 import codec
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal((3, 256)).astype(np.float32)
+    b = rng.standard_normal((3, 256)).astype(np.float32)
+    n = rng.integers(0, 5, 256).astype(np.int32)
+    import torch
+    p = codec.params_to_numpy(torch.from_numpy(codec.params_from_numpy(a, b, n)))
+    assert np.array_equal(p["a"], a) and np.array_equal(p["b"], b) and np.array_equal(p["n"], n)
+    assert p["n_used"] == int((n > 0).sum())
