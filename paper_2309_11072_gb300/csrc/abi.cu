@@ -10,6 +10,10 @@
 
 #include "slrme_internal.cuh"
 
+#define SLRME_TABLE static const
+#include "tables.inc"
+#undef SLRME_TABLE
+
 namespace slrme {
 
 static thread_local char g_err[512] = "";
@@ -31,31 +35,6 @@ int cuda_status(const char* what) {
 }
 
 // ---------------------------------------------------------------- tables
-
-static TmoTables g_tmo;
-static Log2Table g_log2;
-static std::once_flag g_tables_once;
-
-static void build_tables() {
-    g_tmo.gamma[0] = 0.0f;
-    for (int k = 1; k < 256; ++k) g_tmo.gamma[k] = (float)pow((k - 0.5) / 255.0, 2.2);
-    for (int r = 0; r < 16; ++r) {
-        double f = exp2(-(double)r / 16.0);
-        g_tmo.kr[r] = (float)(0.18 * f);
-        g_tmo.wr[r] = (float)(1800.0 * f);
-    }
-    for (int i = 0; i < 2048; ++i) g_log2.lut[i] = (int32_t)lrint(65536.0 * log2((double)(2048 + i)));
-}
-
-const TmoTables& tmo_tables() {
-    std::call_once(g_tables_once, build_tables);
-    return g_tmo;
-}
-
-const Log2Table& log2_table() {
-    std::call_once(g_tables_once, build_tables);
-    return g_log2;
-}
 
 // ITU-T T.81 Annex K, Table K.1 (luminance), row-major.
 static const int kAnnexK1[64] = {
@@ -220,11 +199,10 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
 
 int slrme_host_tables(int32_t* lut, float* gamma, float* kr, float* wr, int quality, int32_t* quant,
                       int32_t* dct) {
-    const TmoTables& t = tmo_tables();
-    if (lut) memcpy(lut, log2_table().lut, sizeof(int32_t) * 2048);
-    if (gamma) memcpy(gamma, t.gamma, sizeof(float) * 256);
-    if (kr) memcpy(kr, t.kr, sizeof(float) * 16);
-    if (wr) memcpy(wr, t.wr, sizeof(float) * 16);
+    if (lut) memcpy(lut, kLog2Lut, sizeof(int32_t) * 2048);
+    if (gamma) memcpy(gamma, kGammaBits, sizeof(float) * 256);
+    if (kr) memcpy(kr, kKrBits, sizeof(float) * 16);
+    if (wr) memcpy(wr, kWrBits, sizeof(float) * 16);
     if (quant) {
         QuantTable qt;
         REQUIRE(quant_table(quality, &qt), "slrme_host_tables: quality %d outside 1..100", quality);

@@ -19,6 +19,10 @@
 // the plain matrix products with the same rounding shifts.
 #include "slrme_internal.cuh"
 
+#define SLRME_TABLE static __device__ const
+#include "tables.inc"
+#undef SLRME_TABLE
+
 namespace slrme {
 
 namespace {
@@ -30,11 +34,6 @@ constexpr int kTileWords = 3 * 4 * 72;    // per warp: 3 planes x 4 blocks x (8 
 // Fixed-point DCT constants round(4096 * alpha_u * cos((2x+1) u pi / 16)).
 constexpr int C4 = 1448;   // alpha_0 * 4096 and cos(pi/4) / 2 * 4096
 constexpr int C1 = 2009, C2 = 1892, C3 = 1703, C5 = 1138, C6 = 784, C7 = 400;
-
-struct BaseParams {
-    TmoTables tmo;
-    QuantTable qt;
-};
 
 __device__ __forceinline__ int rshift_round(int v, int s) { return (v + (1 << (s - 1))) >> s; }
 
@@ -114,18 +113,18 @@ __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w
 __global__ void __launch_bounds__(kThreads) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
                                                    int h, int w, const int64_t* __restrict__ lum_stats,
                                                    uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3, int fast_io,
-                                                   const BaseParams P) {
+                                                   const QuantTable QT) {
     __shared__ float gam[256];
     __shared__ int tile[kWarps][kTileWords];
     __shared__ int keyJ, keyR;
-    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = P.tmo.gamma[i];
+    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = __uint_as_float(kGammaBits[i]);
     if (threadIdx.x == 0) key_from_stats(lum_stats, &keyJ, &keyR);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int blk = lane >> 3, sub = lane & 7;     // block in the band, row (phases 1, 3) or column (phase 2)
     const int J = keyJ;
-    const float kr = P.tmo.kr[keyR], wr = P.tmo.wr[keyR];
+    const float kr = __uint_as_float(kKrBits[keyR]), wr = __uint_as_float(kWrBits[keyR]);
     const int64_t n = (int64_t)h * w;
     const bool fast = fast_io != 0;
 
@@ -134,8 +133,8 @@ __global__ void __launch_bounds__(kThreads) k_base(const uint8_t* __restrict__ m
     uint32_t qmcol[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-        qcol[v] = P.qt.q[v * 8 + sub];
-        qmcol[v] = P.qt.qm[v * 8 + sub];
+        qcol[v] = QT.q[v * 8 + sub];
+        qmcol[v] = QT.qm[v * 8 + sub];
     }
 
     int* T = tile[warp];
@@ -242,9 +241,6 @@ __global__ void __launch_bounds__(kThreads) k_base(const uint8_t* __restrict__ m
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, const QuantTable& qt,
                 uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s) {
     const Geometry g = geometry();
-    BaseParams P;
-    P.tmo = tmo_tables();
-    P.qt = qt;
     const int64_t n = (int64_t)h * w;
     const bool fast = (w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
                       ((uintptr_t)s_dec3 % 8 == 0) && (!sdr3 || (uintptr_t)sdr3 % 8 == 0) && (n % 8 == 0);
@@ -253,7 +249,7 @@ int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t
     const int64_t cap = (int64_t)g.sms * 4;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_base<<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, fast ? 1 : 0, P);
+    k_base<<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, fast ? 1 : 0, qt);
     return cuda_status("sdri_base_roundtrip launch");
 }
 

@@ -1,0 +1,47 @@
+"""Writes tables.inc: the codec's constant tables as literals.
+
+Run from the repository root after changing a definition:
+    python paper_2309_11072_gb300/csrc/gen_tables.py
+
+Tables (all built in float64 and rounded once):
+  kLog2Lut[i]   = round(65536 * log2(2048 + i)),        i = 0..2047
+  kGammaBits[k] = float32 bits of ((k - 0.5) / 255)^2.2,  k = 1..255 (k = 0: 0.0)
+  kKrBits[r]    = float32 bits of 0.18 * 2^(-r/16),        r = 0..15
+  kWrBits[r]    = float32 bits of 1800 * 2^(-r/16),        r = 0..15
+The literals live in the library's device and host code, so no table has to
+be built or copied at run time.
+"""
+import math
+import os
+import struct
+
+
+def f32_bits(x: float) -> int:
+    return struct.unpack("<I", struct.pack("<f", x))[0]
+
+
+def main():
+    lut = [round(65536.0 * math.log2(2048 + i)) for i in range(2048)]
+    gamma = [0] + [f32_bits(((k - 0.5) / 255.0) ** 2.2) for k in range(1, 256)]
+    kr = [f32_bits(0.18 * 2.0 ** (-r / 16.0)) for r in range(16)]
+    wr = [f32_bits(1800.0 * 2.0 ** (-r / 16.0)) for r in range(16)]
+
+    def arr(ctype, name, vals, fmt, per_line):
+        lines = []
+        for i in range(0, len(vals), per_line):
+            lines.append("    " + ", ".join(fmt(v) for v in vals[i:i + per_line]) + ",")
+        return f"SLRME_TABLE {ctype} {name}[{len(vals)}] = {{\n" + "\n".join(lines) + "\n};\n"
+
+    out = ["// Generated by gen_tables.py -- do not edit.  Constant tables of the codec.",
+           "// Include after defining SLRME_TABLE (storage class / qualifiers).", ""]
+    out.append(arr("int32_t", "kLog2Lut", lut, str, 12))
+    out.append(arr("uint32_t", "kGammaBits", gamma, lambda v: f"0x{v:08x}u", 8))
+    out.append(arr("uint32_t", "kKrBits", kr, lambda v: f"0x{v:08x}u", 8))
+    out.append(arr("uint32_t", "kWrBits", wr, lambda v: f"0x{v:08x}u", 8))
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tables.inc")
+    with open(path, "w") as fh:
+        fh.write("\n".join(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -18,7 +18,7 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kStripRows = 16;
+constexpr int kStripRows = 8;
 constexpr int kStripCols = 256;
 // Per-lane run accumulators are 32-bit: a run holds at most 8 * kStripRows
 // pixels, and 8 * kStripRows * 4080^2 must stay below 2^32.
@@ -104,6 +104,42 @@ __device__ __forceinline__ void gf_pairs(const Row10& a, const Row10& b, const R
     X[3] = L3 + 2u * V[3] + R3;
 }
 
+// Sliding 3-row window of the three S planes down one strip.  With the
+// filter on, rows y-1, y, y+1 are held and one new row is fetched per step;
+// with it off only row y is needed.  All 32 lanes must call together.
+struct GfWindow {
+    const uint8_t* s3;
+    int64_t n;
+    int h, w, xs, lane;
+    bool fast, gf;
+    Row10 prv[3], cur[3];
+
+    __device__ __forceinline__ void start(int y0) {
+        if (!gf) return;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            prv[c] = fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane);
+            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
+        }
+    }
+
+    // x values of row y (which must follow the previous call's row) as 16-bit pairs.
+    __device__ __forceinline__ void row(int y, uint32_t (&X)[3][4]) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (gf) {
+                const Row10 nxt = fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane);
+                gf_pairs(prv[c], cur[c], nxt, true, X[c]);
+                prv[c] = cur[c];
+                cur[c] = nxt;
+            } else {
+                const Row10 r = fetch_row(s3 + c * n, h, w, y, xs, fast, lane);
+                gf_pairs(r, r, r, false, X[c]);
+            }
+        }
+    }
+};
+
 __device__ __forceinline__ int half_of(const uint32_t (&X)[4], int i) {
     return (int)((X[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
 }
@@ -148,24 +184,79 @@ __device__ __forceinline__ void run_reset(RunAcc& a, int E) {
     for (int c = 0; c < 3; ++c) a.sx[c] = a.sy[c] = a.sxy[c] = a.sxx[c] = 0;
 }
 
-__device__ __forceinline__ void run_flush(const RunAcc& a, unsigned long long* bins) {
-    if (a.E < 0 || a.n == 0) return;
-    unsigned long long* b = bins + a.E * kNsum;
-    atomicAdd(b, (unsigned long long)a.n);
+// Exact 64-bit add into a (lo, hi) pair of 32-bit shared words with native
+// 32-bit atomics: the old low word returned by the atomic tells whether this
+// addition wrapped, and each wrap carries exactly once into the high word.
+__device__ __forceinline__ void add_u64(uint32_t* lo, uint32_t* hi, unsigned long long v) {
+    const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
+    if (vl) {
+        const uint32_t old = atomicAdd(lo, vl);
+        const uint32_t carry = (old + vl) < old ? 1u : 0u;
+        if (vh + carry) atomicAdd(hi, vh + carry);
+    } else if (vh) {
+        atomicAdd(hi, vh);
+    }
+}
+
+// Bins in shared memory: low words then high words, [E][13] each.
+struct SmemBins {
+    uint32_t lo[kNbin * kNsum];
+    uint32_t hi[kNbin * kNsum];
+};
+
+__device__ __forceinline__ void bins_add(SmemBins& B, int E, const unsigned long long (&v)[kNsum]) {
+#pragma unroll
+    for (int j = 0; j < kNsum; ++j) add_u64(&B.lo[E * kNsum + j], &B.hi[E * kNsum + j], v[j]);
+}
+
+__device__ __forceinline__ void run_values(const RunAcc& a, unsigned long long (&v)[kNsum]) {
+    v[0] = a.n;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        atomicAdd(b + 1 + 4 * c, (unsigned long long)a.sx[c]);
-        atomicAdd(b + 2 + 4 * c, (unsigned long long)a.sy[c]);
-        atomicAdd(b + 3 + 4 * c, (unsigned long long)a.sxy[c]);
-        atomicAdd(b + 4 + 4 * c, (unsigned long long)a.sxx[c]);
+        v[1 + 4 * c] = a.sx[c];
+        v[2 + 4 * c] = a.sy[c];
+        v[3 + 4 * c] = a.sxy[c];
+        v[4 + 4 * c] = a.sxx[c];
+    }
+}
+
+// Flush of one lane's run (divergent call sites).
+__device__ __forceinline__ void run_flush(const RunAcc& a, SmemBins& B) {
+    if (a.E < 0 || a.n == 0) return;
+    unsigned long long v[kNsum];
+    run_values(a, v);
+    bins_add(B, a.E, v);
+}
+
+// Flush of all lanes' runs at a warp-uniform point: when every non-empty run
+// is in the same region the warp reduces them first and one lane adds.
+__device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lane) {
+    const bool live = a.E >= 0 && a.n != 0;
+    const unsigned liveMask = __ballot_sync(0xffffffffu, live);
+    if (!liveMask) return;
+    const int E0 = __shfl_sync(0xffffffffu, a.E, __ffs(liveMask) - 1);
+    if (__all_sync(0xffffffffu, !live || a.E == E0)) {
+        unsigned long long v[kNsum];
+        run_values(a, v);
+        if (!live) {
+#pragma unroll
+            for (int j = 0; j < kNsum; ++j) v[j] = 0ull;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < kNsum; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+        if (lane == 0) bins_add(B, E0, v);
+    } else {
+        run_flush(a, B);
     }
 }
 
 __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
                                                   const uint8_t* __restrict__ e, int h, int w, int gf_on, int fast_io,
                                                   unsigned long long* __restrict__ gbins) {
-    __shared__ unsigned long long bins[kNbin * kNsum];
-    for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins[i] = 0ull;
+    __shared__ SmemBins bins;
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins.lo[i] = bins.hi[i] = 0u;
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -180,19 +271,11 @@ __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3
         const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
         const int y1 = min(y0 + kStripRows, h);
-        Row10 prv[3], cur[3], nxt[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
-            prv[c] = gf ? fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane) : cur[c];
-        }
+        GfWindow win{s3, n, h, w, xs, lane, fast, gf};
+        win.start(y0);
         for (int y = y0; y < y1; ++y) {
             uint32_t X[3][4];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                nxt[c] = gf ? fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane) : cur[c];
-                gf_pairs(prv[c], cur[c], nxt[c], gf, X[c]);
-            }
+            win.row(y, X);
             if (x0 < w) {
                 uint32_t mlo[3], mhi[3], elo, ehi;
 #pragma unroll
@@ -245,22 +328,15 @@ __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3
                     }
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                prv[c] = cur[c];
-                cur[c] = nxt[c];
-            }
         }
-        // keep every run within one strip so the 32-bit accumulators cannot overflow
-        run_flush(acc, bins);
+        // every run ends with its strip, so the 32-bit run accumulators cannot overflow
+        warp_flush(acc, bins, lane);
         run_reset(acc, -1);
     }
     __syncthreads();
-    for (int E = threadIdx.x; E < kNbin; E += kThreads) {
-        const unsigned long long* b = bins + E * kNsum;
-        if (b[0] == 0ull) continue;
-#pragma unroll
-        for (int j = 0; j < kNsum; ++j) atomicAdd(gbins + E * kNsum + j, b[j]);
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) {
+        const unsigned long long v = ((unsigned long long)bins.hi[i] << 32) | bins.lo[i];
+        if (v) atomicAdd(gbins + i, v);
     }
 }
 
@@ -343,19 +419,11 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
         const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
         const int y1 = min(y0 + kStripRows, h);
-        Row10 prv[3], cur[3], nxt[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
-            prv[c] = gf ? fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane) : cur[c];
-        }
+        GfWindow win{s3, n, h, w, xs, lane, fast, gf};
+        win.start(y0);
         for (int y = y0; y < y1; ++y) {
             uint32_t X[3][4];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                nxt[c] = gf ? fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane) : cur[c];
-                gf_pairs(prv[c], cur[c], nxt[c], gf, X[c]);
-            }
+            win.row(y, X);
             if (x0 < w) {
                 uint32_t elo, ehi;
                 load_bytes8(e, w, y, x0, fast, elo, ehi);
@@ -391,11 +459,6 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
                     }
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                prv[c] = cur[c];
-                cur[c] = nxt[c];
-            }
         }
     }
     if (ghist) {
@@ -424,19 +487,11 @@ __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__
         const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
         const int y1 = min(y0 + kStripRows, h);
-        Row10 prv[3], cur[3], nxt[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cur[c] = fetch_row(s3 + c * n, h, w, y0, xs, fast, lane);
-            prv[c] = gf ? fetch_row(s3 + c * n, h, w, y0 - 1, xs, fast, lane) : cur[c];
-        }
+        GfWindow win{s3, n, h, w, xs, lane, fast, gf};
+        win.start(y0);
         for (int y = y0; y < y1; ++y) {
             uint32_t X[3][4];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                nxt[c] = gf ? fetch_row(s3 + c * n, h, w, y + 1, xs, fast, lane) : cur[c];
-                gf_pairs(prv[c], cur[c], nxt[c], gf, X[c]);
-            }
+            win.row(y, X);
             if (x0 < w) {
                 uint32_t elo, ehi;
                 load_bytes8(e, w, y, x0, fast, elo, ehi);
@@ -475,11 +530,6 @@ __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__
                     const int cnt = min(8, w - x0);
                     for (int i = 0; i < cnt; ++i) orow[i] = word[i];
                 }
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                prv[c] = cur[c];
-                cur[c] = nxt[c];
             }
         }
     }

@@ -15,12 +15,8 @@ constexpr int kNsum = SLRME_NSUM;
 constexpr int kNres = SLRME_NRES;
 
 // ---------------------------------------------------------------- tables
-// Tone-mapping constants, built once on the host (tables.cu).
-struct TmoTables {
-    float gamma[256];   // gamma[k] = float(((k - 0.5) / 255)^2.2), gamma[0] = 0
-    float kr[16];       // float(0.18 * 2^(-r/16))
-    float wr[16];       // float(1800 * 2^(-r/16))
-};
+// The constant tables (log2 LUT, gamma thresholds, key scales) are literals
+// in tables.inc, included by each translation unit that reads them.
 
 // Quantiser for one quality: steps q[v*8+u] and the reciprocal multipliers
 // qm = ceil(2^24 / q), so floor(n / q) == umulhi(n << 8, qm) for 0 <= n < 4096.
@@ -29,12 +25,6 @@ struct QuantTable {
     uint32_t qm[64];
 };
 
-struct Log2Table {
-    int32_t lut[2048];  // round(65536 * log2(2048 + i))
-};
-
-const TmoTables& tmo_tables();
-const Log2Table& log2_table();
 bool quant_table(int quality, QuantTable* out);
 
 // ---------------------------------------------------------------- launch geometry

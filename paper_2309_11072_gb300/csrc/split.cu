@@ -8,6 +8,10 @@
 // int64, then per warp and block, with one 64-bit atomic per block.
 #include "slrme_internal.cuh"
 
+#define SLRME_TABLE static __device__ const
+#include "tables.inc"
+#undef SLRME_TABLE
+
 namespace slrme {
 
 namespace {
@@ -63,9 +67,9 @@ __device__ __forceinline__ void block_reduce_add(int64_t s, int64_t c, int64_t* 
 __global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict__ rgbe4, int64_t nv,
                                                         uint32_t* __restrict__ mR, uint32_t* __restrict__ mG,
                                                         uint32_t* __restrict__ mB, uint32_t* __restrict__ eP,
-                                                        int64_t* __restrict__ stats, const Log2Table tab) {
+                                                        int64_t* __restrict__ stats) {
     __shared__ int32_t lut[2048];
-    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = tab.lut[i];
+    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = kLog2Lut[i];
     __syncthreads();
 
     int64_t s = 0, c = 0;
@@ -108,9 +112,9 @@ __global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict_
 // Scalar path: any size and alignment, one word per thread per step.
 __global__ void __launch_bounds__(kThreads) k_split_scalar(const uint32_t* __restrict__ rgbe, int64_t n,
                                                            uint8_t* __restrict__ m3, uint8_t* __restrict__ e,
-                                                           int64_t* __restrict__ stats, const Log2Table tab) {
+                                                           int64_t* __restrict__ stats) {
     __shared__ int32_t lut[2048];
-    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = tab.lut[i];
+    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = kLog2Lut[i];
     __syncthreads();
     int64_t s = 0, c = 0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -134,7 +138,7 @@ int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e, int64
                      ((uintptr_t)e % 4 == 0);
     const int64_t units = vec ? n / 4 : n;
     int64_t blocks = (units + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)g.sms * 8;   // 8 resident blocks of 256 threads per SM
+    const int64_t cap = (int64_t)g.sms * 4;   // 4 resident blocks of 256 threads per SM
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     if (vec) {
@@ -142,9 +146,9 @@ int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e, int64
         k_split_vec<<<(unsigned)blocks, kThreads, 0, s>>>(
             reinterpret_cast<const uint4*>(rgbe), nv, reinterpret_cast<uint32_t*>(m3),
             reinterpret_cast<uint32_t*>(m3 + n), reinterpret_cast<uint32_t*>(m3 + 2 * n),
-            reinterpret_cast<uint32_t*>(e), lum_stats, log2_table());
+            reinterpret_cast<uint32_t*>(e), lum_stats);
     } else {
-        k_split_scalar<<<(unsigned)blocks, kThreads, 0, s>>>(rgbe, n, m3, e, lum_stats, log2_table());
+        k_split_scalar<<<(unsigned)blocks, kThreads, 0, s>>>(rgbe, n, m3, e, lum_stats);
     }
     return cuda_status("rgbe_split launch");
 }
