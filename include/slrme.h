@@ -113,6 +113,25 @@ int slr_fit(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, i
 /* Bytes of the bin_sums workspace slr_fit needs (256 * 13 * 8). */
 size_t slr_fit_workspace_bytes(void);
 
+/* slr_fit for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment variant).  Some callers hold no device
+ * allocator of their own: a plugin whose host application owns all device
+ * memory, a fixed-budget service that allocates nothing after start-up, or
+ * C code that only receives device pointers from another framework.  They
+ * cannot provide the bin_sums workspace, so this entry point keeps it in a
+ * library-owned static device array of 26,624 bytes (256 regions x 13 int64
+ * sums) that every GPU loading the library holds until exit.  It computes the
+ * same params as slr_fit and calls no cudaMalloc / cudaFree.
+ * - Sizes: the same as slr_fit (h, w >= 0, h*w < 2^31, the range in which the
+ *   int64 sums are exact); anything else is rejected with SLRME_EINVAL.
+ * - The first call on a device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ * - All calls share the one array: each call clears it on `stream` before
+ *   use, and calls whose GPU work overlaps (other streams, other threads)
+ *   race on it and give wrong parameters.  Serialise them. */
+int slr_fit_noalloc(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w,
+                    int gf_on, slrme_params* params, slrme_stream_t stream);
+
 /* Residual formation (Eq. 8, Sec. III-C): M*(q) = round(a_E S*(q) + b_E)
  * clipped to [0, 255] (float32 multiply then add, round half away from zero),
  * R = M - M* (r3, int16 [3][h][w]).  hist (uint32 [3][511], device, may be

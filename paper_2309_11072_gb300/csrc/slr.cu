@@ -10,6 +10,8 @@
 // of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
 // them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
 // 32-bit add (values stay <= 4080).
+#include <mutex>
+
 #include "slrme_internal.cuh"
 
 namespace slrme {
@@ -579,3 +581,91 @@ int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r
 }
 
 }  // namespace slrme
+
+// ====================================================================== slr_fit_noalloc
+//
+// The same fit as slr_fit for callers that cannot allocate device memory:
+// the bin sums live in this file-scope array instead of a caller workspace.
+// Every GPU that loads the library holds these 26,624 bytes until exit.
+
+namespace slrme {
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) unsigned long long g_fit_scratch[kNbin * kNsum];
+static std::mutex g_scratch_mu;
+static void* g_scratch_addr[kMaxDevices];
+
+// Device address of g_fit_scratch on the current device, looked up once per
+// device (with that device current).  In host code the array's name is only a
+// host-side stand-in, so kernels must be given this address, never the name.
+int scratch_address(void** out) {
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) {
+        set_error("slr_fit_noalloc: cudaGetDevice: %s", cudaGetErrorString(err));
+        return SLRME_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("slr_fit_noalloc: device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
+        return SLRME_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_fit_scratch);
+        if (err != cudaSuccess || !p) {
+            set_error("slr_fit_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(err));
+            return SLRME_ECUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return SLRME_OK;
+}
+
+}  // namespace
+
+}  // namespace slrme
+
+extern "C" int slr_fit_noalloc(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w,
+                               int gf_on, slrme_params* params, slrme_stream_t stream) {
+    using namespace slrme;
+    if (h < 0 || w < 0 || (int64_t)h * (int64_t)w >= ((int64_t)1 << 31)) {
+        set_error("slr_fit_noalloc: image %d x %d outside the supported size (h, w >= 0, h*w < 2^31): "
+                  "the fixed %d-byte scratch holds exact sums only up to that size",
+                  h, w, (int)sizeof(g_fit_scratch));
+        return SLRME_EINVAL;
+    }
+    if (gf_on != 0 && gf_on != 1) {
+        set_error("slr_fit_noalloc: gf_on must be 0 or 1");
+        return SLRME_EINVAL;
+    }
+    if (!params || (uintptr_t)params % 4 != 0) {
+        set_error("slr_fit_noalloc: params must be a non-null, 4-byte aligned device pointer");
+        return SLRME_EINVAL;
+    }
+    const int64_t n = (int64_t)h * w;
+    if (n > 0 && !(s_dec3 && m3 && e)) {
+        set_error("slr_fit_noalloc: null image pointer");
+        return SLRME_EINVAL;
+    }
+    void* scratch = nullptr;
+    int st = scratch_address(&scratch);
+    if (st != SLRME_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's sums: clear it before accumulating
+    if (cudaMemsetAsync(scratch, 0, sizeof(g_fit_scratch), s) != cudaSuccess)
+        return cuda_status("slr_fit_noalloc memset");
+    unsigned long long* bins = static_cast<unsigned long long*>(scratch);
+    if (n > 0) {
+        const bool fast = (w % 8 == 0) && ((uintptr_t)s_dec3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
+                          ((uintptr_t)e % 8 == 0);
+        k_fit<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s_dec3, m3, e, h, w, gf_on, fast ? 1 : 0, bins);
+        st = cuda_status("slr_fit_noalloc launch");
+        if (st != SLRME_OK) return st;
+    }
+    k_solve<<<1, 768, 0, s>>>(reinterpret_cast<const int64_t*>(bins), params);
+    return cuda_status("slr_fit_noalloc solve launch");
+}

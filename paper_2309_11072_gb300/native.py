@@ -36,6 +36,7 @@ _SIGS = {
     "rgbe_key_scale": [_vp, _vp, _vp],
     "sdri_base_roundtrip": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp],
     "slr_fit": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
+    "slr_fit_noalloc": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp],
     "residual_encode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "residual_decode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
     "slrme_host_tables": [_vp, _vp, _vp, _vp, _i32, _vp, _vp],
@@ -115,6 +116,13 @@ def sdri_base_roundtrip(m3, e, h: int, w: int, lum_stats, quality: int, s_dec3, 
 def slr_fit(s_dec3, m3, e, h: int, w: int, gf_on: int, bin_sums, params, stream=None) -> None:
     _check("slr_fit", lib().slr_fit(_ptr(s_dec3), _ptr(m3), _ptr(e), h, w, int(gf_on), _ptr(bin_sums),
                                     _ptr(params), _stream(stream)))
+
+
+def slr_fit_noalloc(s_dec3, m3, e, h: int, w: int, gf_on: int, params, stream=None) -> None:
+    """slr_fit without a caller workspace: the library's static device scratch
+    holds the bin sums (for callers that cannot allocate device memory)."""
+    _check("slr_fit_noalloc", lib().slr_fit_noalloc(_ptr(s_dec3), _ptr(m3), _ptr(e), h, w, int(gf_on),
+                                                    _ptr(params), _stream(stream)))
 
 
 def slr_fit_workspace_bytes() -> int:
