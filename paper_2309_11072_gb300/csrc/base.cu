@@ -69,12 +69,28 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8]) {
     x[3] = E3 + O3; x[4] = E3 - O3;
 }
 
-// 8-bit display value: #{k in 1..255 : v >= gamma[k]} by bisection.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 8-bit display value: #{k in 1..255 : v >= gamma[k]} for the increasing
+// threshold table.  A hardware-approximate 255 v^(1/2.2) seeds k; the two
+// loops then move k to the unique value with gamma[k] <= v < gamma[k+1]
+// (k = 0 below gamma[1], k = 255 at or above gamma[255]), so the result is
+// exactly the table count whatever the seed's error.
 __device__ __forceinline__ int gamma_code(float v, const float* g) {
-    int k = 0;
-#pragma unroll
-    for (int step = 128; step > 0; step >>= 1)
-        if (v >= g[k + step]) k += step;
+    const float seed = 255.0f * ex2_approx(lg2_approx(v) * (1.0f / 2.2f)) + 0.5f;
+    int k = seed >= 255.0f ? 255 : (seed > 0.0f ? (int)seed : 0);
+    while (k < 255 && v >= g[k + 1]) ++k;
+    while (k > 0 && v < g[k]) --k;
     return k;
 }
 

@@ -5,7 +5,7 @@
 //   k_decode     restoration + Eq. (8) prediction + M = R + M* + repack
 //
 // Shared structure: a warp owns a strip 256 columns wide (8 per lane) and
-// kStripRows rows tall and slides a 3-row window of S down it, so every row
+// 4, 8 or 16 rows tall and slides a 3-row window of S down it, so every row
 // of S is loaded once per strip.  The neighbours a lane needs left and right
 // of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
 // them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
@@ -20,11 +20,11 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kStripRows = 8;
+constexpr int kMaxStripRows = 16;   // strip height is chosen per launch: 4, 8 or 16 rows
 constexpr int kStripCols = 256;
-// Per-lane run accumulators are 32-bit: a run holds at most 8 * kStripRows
-// pixels, and 8 * kStripRows * 4080^2 must stay below 2^32.
-static_assert(8ull * kStripRows * 4080ull * 4080ull < (1ull << 32), "run accumulators would overflow");
+// Per-lane run accumulators are 32-bit: a run holds at most 8 * kMaxStripRows
+// pixels, and 8 * kMaxStripRows * 4080^2 must stay below 2^32.
+static_assert(8ull * kMaxStripRows * 4080ull * 4080ull < (1ull << 32), "run accumulators would overflow");
 
 struct Row10 {
     uint32_t lo, hi;   // bytes at x0 .. x0+7
@@ -254,9 +254,78 @@ __device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lan
     }
 }
 
+// Accumulate one full uniform row segment (8 pixels of one region) into a run.
+__device__ __forceinline__ void run_add8(RunAcc& a, const uint32_t (&X)[3][4], const uint32_t (&mlo)[3],
+                                         const uint32_t (&mhi)[3]) {
+    a.n += 8;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t ps = X[c][0] + X[c][1] + X[c][2] + X[c][3];
+        a.sx[c] += (ps & 0xFFFFu) + (ps >> 16);
+        a.sy[c] = __dp4a(mlo[c], 0x01010101u, __dp4a(mhi[c], 0x01010101u, a.sy[c]));
+        a.sxy[c] = __dp2a_lo(X[c][0], mlo[c], a.sxy[c]);
+        a.sxy[c] = __dp2a_hi(X[c][1], mlo[c], a.sxy[c]);
+        a.sxy[c] = __dp2a_lo(X[c][2], mhi[c], a.sxy[c]);
+        a.sxy[c] = __dp2a_hi(X[c][3], mhi[c], a.sxy[c]);
+        uint32_t q = a.sxx[c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t lo16 = X[c][k] & 0xFFFFu, hi16 = X[c][k] >> 16;
+            q += lo16 * lo16 + hi16 * hi16;
+        }
+        a.sxx[c] = q;
+    }
+}
+
+__device__ __forceinline__ void run_add1(RunAcc& a, const uint32_t (&x)[3], const uint32_t (&y)[3]) {
+    a.n += 1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.sx[c] += x[c];
+        a.sy[c] += y[c];
+        a.sxy[c] += x[c] * y[c];
+        a.sxx[c] += x[c] * x[c];
+    }
+}
+
+__device__ __forceinline__ void run_swap(RunAcc& a, RunAcc& b) {
+    const RunAcc t = a;
+    a = b;
+    b = t;
+}
+
+// Two runs per lane: a region boundary through the lane's 8-pixel column
+// costs no flush; a third region evicts the less recently used run.
+struct RunCache {
+    RunAcc A, B;
+    bool lastA;   // A was used more recently than B
+
+    __device__ __forceinline__ void reset() {
+        run_reset(A, -1);
+        run_reset(B, -1);
+        lastA = true;
+    }
+
+    // Run to accumulate region E into: 0 = A, 1 = B (evicting one if needed).
+    __device__ __forceinline__ int pick(int E, SmemBins& bins) {
+        if (E == A.E) { lastA = true; return 0; }
+        if (E == B.E) { lastA = false; return 1; }
+        if (lastA) {
+            run_flush(B, bins);
+            run_reset(B, E);
+            lastA = false;
+            return 1;
+        }
+        run_flush(A, bins);
+        run_reset(A, E);
+        lastA = true;
+        return 0;
+    }
+};
+
 __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
                                                   const uint8_t* __restrict__ e, int h, int w, int gf_on, int fast_io,
-                                                  unsigned long long* __restrict__ gbins) {
+                                                  int strip_rows, unsigned long long* __restrict__ gbins) {
     __shared__ SmemBins bins;
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins.lo[i] = bins.hi[i] = 0u;
     __syncthreads();
@@ -264,15 +333,15 @@ __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = (int64_t)h * w;
     const bool fast = fast_io != 0, gf = gf_on != 0;
-    const int bands = (h + kStripRows - 1) / kStripRows, cols = (w + kStripCols - 1) / kStripCols;
+    const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
     const int64_t tasks = (int64_t)bands * cols;
 
-    RunAcc acc;
-    run_reset(acc, -1);
+    RunCache rc;
+    rc.reset();
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
+        const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
-        const int y1 = min(y0 + kStripRows, h);
+        const int y1 = min(y0 + strip_rows, h);
         GfWindow win{s3, n, h, w, xs, lane, fast, gf};
         win.start(y0);
         for (int y = y0; y < y1; ++y) {
@@ -286,54 +355,30 @@ __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3
                 const bool full = x0 + 8 <= w;
                 const bool uniform = full && elo == ehi && elo == __byte_perm(elo, 0, 0x0000);
                 if (uniform) {
-                    const int E = (int)(elo & 255u);
-                    if (E != acc.E) {
-                        run_flush(acc, bins);
-                        run_reset(acc, E);
-                    }
-                    acc.n += 8;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const uint32_t ps = X[c][0] + X[c][1] + X[c][2] + X[c][3];
-                        acc.sx[c] += (ps & 0xFFFFu) + (ps >> 16);
-                        acc.sy[c] = __dp4a(mlo[c], 0x01010101u, __dp4a(mhi[c], 0x01010101u, acc.sy[c]));
-                        acc.sxy[c] = __dp2a_lo(X[c][0], mlo[c], acc.sxy[c]);
-                        acc.sxy[c] = __dp2a_hi(X[c][1], mlo[c], acc.sxy[c]);
-                        acc.sxy[c] = __dp2a_lo(X[c][2], mhi[c], acc.sxy[c]);
-                        acc.sxy[c] = __dp2a_hi(X[c][3], mhi[c], acc.sxy[c]);
-                        uint32_t q = acc.sxx[c];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint32_t lo16 = X[c][k] & 0xFFFFu, hi16 = X[c][k] >> 16;
-                            q += lo16 * lo16 + hi16 * hi16;
-                        }
-                        acc.sxx[c] = q;
-                    }
+                    if (rc.pick((int)(elo & 255u), bins) == 0) run_add8(rc.A, X, mlo, mhi);
+                    else run_add8(rc.B, X, mlo, mhi);
                 } else {
                     const int cnt = min(8, w - x0);
                     for (int i = 0; i < cnt; ++i) {
-                        const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
-                        if (E != acc.E) {
-                            run_flush(acc, bins);
-                            run_reset(acc, E);
-                        }
-                        acc.n += 1;
+                        uint32_t x[3], yv[3];
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            const uint32_t x = (uint32_t)half_of(X[c], i);
-                            const uint32_t yv = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
-                            acc.sx[c] += x;
-                            acc.sy[c] += yv;
-                            acc.sxy[c] += x * yv;
-                            acc.sxx[c] += x * x;
+                            x[c] = (uint32_t)half_of(X[c], i);
+                            yv[c] = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
                         }
+                        if (rc.pick((int)byte_of(i < 4 ? elo : ehi, i & 3), bins) == 0) run_add1(rc.A, x, yv);
+                        else run_add1(rc.B, x, yv);
                     }
                 }
             }
         }
-        // every run ends with its strip, so the 32-bit run accumulators cannot overflow
-        warp_flush(acc, bins, lane);
-        run_reset(acc, -1);
+        // Every run ends with its strip, so the 32-bit run accumulators cannot
+        // overflow.  Order the two runs by region so lanes that saw the same
+        // two regions flush them in the same warp-wide step.
+        if ((unsigned)rc.A.E > (unsigned)rc.B.E) run_swap(rc.A, rc.B);
+        warp_flush(rc.A, bins, lane);
+        warp_flush(rc.B, bins, lane);
+        rc.reset();
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) {
@@ -403,7 +448,7 @@ __device__ __forceinline__ void load_params(const slrme_params* __restrict__ P, 
 
 __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
                                                        const uint8_t* __restrict__ e, int h, int w, int gf_on,
-                                                       int fast_io, const slrme_params* __restrict__ P,
+                                                       int fast_io, int strip_rows, const slrme_params* __restrict__ P,
                                                        int16_t* __restrict__ r3, uint32_t* __restrict__ ghist) {
     __shared__ float sa[3 * kNbin], sb[3 * kNbin];
     __shared__ uint32_t hist[3 * kNres];
@@ -415,12 +460,12 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = (int64_t)h * w;
     const bool fast = fast_io != 0, gf = gf_on != 0;
-    const int bands = (h + kStripRows - 1) / kStripRows, cols = (w + kStripCols - 1) / kStripCols;
+    const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
     const int64_t tasks = (int64_t)bands * cols;
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
+        const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
-        const int y1 = min(y0 + kStripRows, h);
+        const int y1 = min(y0 + strip_rows, h);
         GfWindow win{s3, n, h, w, xs, lane, fast, gf};
         win.start(y0);
         for (int y = y0; y < y1; ++y) {
@@ -474,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
 
 __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ e,
                                                      const int16_t* __restrict__ r3, int h, int w, int gf_on,
-                                                     int fast_io, const slrme_params* __restrict__ P,
+                                                     int fast_io, int strip_rows, const slrme_params* __restrict__ P,
                                                      uint32_t* __restrict__ out) {
     __shared__ float sa[3 * kNbin], sb[3 * kNbin];
     load_params(P, sa, sb);
@@ -483,12 +528,12 @@ __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = (int64_t)h * w;
     const bool fast = fast_io != 0, gf = gf_on != 0;
-    const int bands = (h + kStripRows - 1) / kStripRows, cols = (w + kStripCols - 1) / kStripCols;
+    const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
     const int64_t tasks = (int64_t)bands * cols;
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * kStripRows, xs = (int)(t % cols) * kStripCols;
+        const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
-        const int y1 = min(y0 + kStripRows, h);
+        const int y1 = min(y0 + strip_rows, h);
         GfWindow win{s3, n, h, w, xs, lane, fast, gf};
         win.start(y0);
         for (int y = y0; y < y1; ++y) {
@@ -537,12 +582,23 @@ __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__
     }
 }
 
-int strip_blocks(int h, int w, int per_sm) {
-    const int64_t tasks = (int64_t)((h + kStripRows - 1) / kStripRows) * ((w + kStripCols - 1) / kStripCols);
+struct StripLaunch {
+    int rows;     // strip height
+    int blocks;   // CTAs
+};
+
+// Strip height: the tallest of 16, 8, 4 rows that still gives about 32 warps
+// of work per SM (short strips re-read two halo rows of S per strip).
+StripLaunch strip_launch(int h, int w, int per_sm) {
+    const int sms = geometry().sms;
+    const int64_t cols = (w + kStripCols - 1) / kStripCols;
+    int rows = kMaxStripRows;
+    while (rows > 4 && (int64_t)((h + rows - 1) / rows) * cols < (int64_t)sms * 32) rows >>= 1;
+    const int64_t tasks = (int64_t)((h + rows - 1) / rows) * cols;
     int64_t blocks = (tasks + kWarps - 1) / kWarps;
-    const int64_t cap = (int64_t)geometry().sms * per_sm;
+    const int64_t cap = (int64_t)sms * per_sm;
     if (blocks > cap) blocks = cap;
-    return (int)(blocks < 1 ? 1 : blocks);
+    return StripLaunch{rows, (int)(blocks < 1 ? 1 : blocks)};
 }
 
 }  // namespace
@@ -555,8 +611,9 @@ int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, in
     if (n > 0) {
         const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                           ((uintptr_t)e % 8 == 0);
-        k_fit<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0,
-                                                         reinterpret_cast<unsigned long long*>(bin_sums));
+        const StripLaunch L = strip_launch(h, w, 2);
+        k_fit<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
+                                            reinterpret_cast<unsigned long long*>(bin_sums));
         int st = cuda_status("slr_fit launch");
         if (st != SLRME_OK) return st;
     }
@@ -568,7 +625,8 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
                            const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                       ((uintptr_t)e % 8 == 0) && ((uintptr_t)r3 % 16 == 0);
-    k_residual<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, params, r3, hist);
+    const StripLaunch L = strip_launch(h, w, 2);
+    k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
     return cuda_status("residual_encode launch");
 }
 
@@ -576,7 +634,8 @@ int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r
                            const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
                       ((uintptr_t)r3 % 16 == 0) && ((uintptr_t)rgbe_out % 16 == 0);
-    k_decode<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, params, rgbe_out);
+    const StripLaunch L = strip_launch(h, w, 2);
+    k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
     return cuda_status("residual_decode launch");
 }
 
@@ -662,7 +721,8 @@ extern "C" int slr_fit_noalloc(const uint8_t* s_dec3, const uint8_t* m3, const u
     if (n > 0) {
         const bool fast = (w % 8 == 0) && ((uintptr_t)s_dec3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                           ((uintptr_t)e % 8 == 0);
-        k_fit<<<strip_blocks(h, w, 4), kThreads, 0, s>>>(s_dec3, m3, e, h, w, gf_on, fast ? 1 : 0, bins);
+        const StripLaunch L = strip_launch(h, w, 2);
+        k_fit<<<L.blocks, kThreads, 0, s>>>(s_dec3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, bins);
         st = cuda_status("slr_fit_noalloc launch");
         if (st != SLRME_OK) return st;
     }
