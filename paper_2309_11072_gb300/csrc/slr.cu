@@ -294,36 +294,7 @@ __device__ __forceinline__ void run_swap(RunAcc& a, RunAcc& b) {
     b = t;
 }
 
-// Two runs per lane: a region boundary through the lane's 8-pixel column
-// costs no flush; a third region evicts the less recently used run.
-struct RunCache {
-    RunAcc A, B;
-    bool lastA;   // A was used more recently than B
-
-    __device__ __forceinline__ void reset() {
-        run_reset(A, -1);
-        run_reset(B, -1);
-        lastA = true;
-    }
-
-    // Run to accumulate region E into: 0 = A, 1 = B (evicting one if needed).
-    __device__ __forceinline__ int pick(int E, SmemBins& bins) {
-        if (E == A.E) { lastA = true; return 0; }
-        if (E == B.E) { lastA = false; return 1; }
-        if (lastA) {
-            run_flush(B, bins);
-            run_reset(B, E);
-            lastA = false;
-            return 1;
-        }
-        run_flush(A, bins);
-        run_reset(A, E);
-        lastA = true;
-        return 0;
-    }
-};
-
-__global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
+__global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
                                                   const uint8_t* __restrict__ e, int h, int w, int gf_on, int fast_io,
                                                   int strip_rows, unsigned long long* __restrict__ gbins) {
     __shared__ SmemBins bins;
@@ -336,8 +307,12 @@ __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3
     const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
     const int64_t tasks = (int64_t)bands * cols;
 
-    RunCache rc;
-    rc.reset();
+    // Two runs per lane: `cur` accumulates, `vic` holds the previous region,
+    // so a region boundary through the lane's 8-pixel column costs a swap, not
+    // a flush.  A third region flushes `vic`.
+    RunAcc cur, vic;
+    run_reset(cur, -1);
+    run_reset(vic, -1);
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
         const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
@@ -352,33 +327,54 @@ __global__ void __launch_bounds__(kThreads) k_fit(const uint8_t* __restrict__ s3
 #pragma unroll
                 for (int c = 0; c < 3; ++c) load_bytes8(m3 + c * n, w, y, x0, fast, mlo[c], mhi[c]);
                 load_bytes8(e, w, y, x0, fast, elo, ehi);
-                const bool full = x0 + 8 <= w;
-                const bool uniform = full && elo == ehi && elo == __byte_perm(elo, 0, 0x0000);
-                if (uniform) {
-                    if (rc.pick((int)(elo & 255u), bins) == 0) run_add8(rc.A, X, mlo, mhi);
-                    else run_add8(rc.B, X, mlo, mhi);
-                } else {
-                    const int cnt = min(8, w - x0);
-                    for (int i = 0; i < cnt; ++i) {
+                const bool uniform = x0 + 8 <= w && elo == ehi && elo == __byte_perm(elo, 0, 0x0000);
+                // one segment of 8 pixels, or one segment per pixel; in the
+                // per-pixel case the packed pixel words are shifted down after
+                // each pixel, so no register array is indexed
+                const int segs = uniform ? 1 : min(8, w - x0);
+#pragma unroll 1
+                for (int sgi = 0; sgi < segs; ++sgi) {
+                    const int E = (int)(elo & 255u);
+                    elo = __funnelshift_r(elo, ehi, 8);
+                    ehi >>= 8;
+                    if (E != cur.E) {
+                        if (E != vic.E) {
+                            run_flush(vic, bins);
+                            run_reset(vic, E);
+                        }
+                        run_swap(cur, vic);
+                    }
+                    if (uniform) {
+                        run_add8(cur, X, mlo, mhi);
+                    } else {
                         uint32_t x[3], yv[3];
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            x[c] = (uint32_t)half_of(X[c], i);
-                            yv[c] = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
+                            x[c] = X[c][0] & 0xFFFFu;
+                            yv[c] = mlo[c] & 255u;
+                            mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
+                            mhi[c] >>= 8;
+                            X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
+                            X[c][1] = __funnelshift_r(X[c][1], X[c][2], 16);
+                            X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
+                            X[c][3] >>= 16;
                         }
-                        if (rc.pick((int)byte_of(i < 4 ? elo : ehi, i & 3), bins) == 0) run_add1(rc.A, x, yv);
-                        else run_add1(rc.B, x, yv);
+                        run_add1(cur, x, yv);
                     }
                 }
             }
         }
         // Every run ends with its strip, so the 32-bit run accumulators cannot
-        // overflow.  Order the two runs by region so lanes that saw the same
-        // two regions flush them in the same warp-wide step.
-        if ((unsigned)rc.A.E > (unsigned)rc.B.E) run_swap(rc.A, rc.B);
-        warp_flush(rc.A, bins, lane);
-        warp_flush(rc.B, bins, lane);
-        rc.reset();
+        // overflow.  Lanes order their two runs by region so lanes that saw the
+        // same two regions flush them in the same warp-wide step.
+        if ((unsigned)cur.E > (unsigned)vic.E) run_swap(cur, vic);
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            warp_flush(cur, bins, lane);
+            run_swap(cur, vic);
+        }
+        run_reset(cur, -1);
+        run_reset(vic, -1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) {
