@@ -126,7 +126,7 @@ __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
+__global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
                                                    int h, int w, const int64_t* __restrict__ lum_stats,
                                                    uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3, int fast_io,
                                                    const QuantTable QT) {

@@ -294,9 +294,82 @@ __device__ __forceinline__ void run_swap(RunAcc& a, RunAcc& b) {
     b = t;
 }
 
+// Sums of one 8-pixel segment, restricted to the pixels whose byte of `mlo/mhi`
+// mask is 0xFF (mask = ~0 for all pixels).  x pairs are masked with the
+// 16-bit expansion of the byte mask.
+__device__ __forceinline__ void seg_sums(const uint32_t (&X)[3][4], const uint32_t (&mlo)[3], const uint32_t (&mhi)[3],
+                                         uint32_t klo, uint32_t khi, RunAcc& a) {
+    const uint32_t k16[4] = {__byte_perm(klo, 0, 0x1100), __byte_perm(klo, 0, 0x3322),
+                             __byte_perm(khi, 0, 0x1100), __byte_perm(khi, 0, 0x3322)};
+    a.n = (uint32_t)(__popc(klo) + __popc(khi)) >> 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        uint32_t x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = X[c][k] & k16[k];
+        const uint32_t yl = mlo[c] & klo, yh = mhi[c] & khi;
+        const uint32_t ps = x[0] + x[1] + x[2] + x[3];
+        a.sx[c] = (ps & 0xFFFFu) + (ps >> 16);
+        a.sy[c] = __dp4a(yl, 0x01010101u, __dp4a(yh, 0x01010101u, 0u));
+        uint32_t q = __dp2a_lo(x[0], yl, 0u);
+        q = __dp2a_hi(x[1], yl, q);
+        q = __dp2a_lo(x[2], yh, q);
+        a.sxy[c] = __dp2a_hi(x[3], yh, q);
+        uint32_t r = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t lo16 = x[k] & 0xFFFFu, hi16 = x[k] >> 16;
+            r += lo16 * lo16 + hi16 * hi16;
+        }
+        a.sxx[c] = r;
+    }
+}
+
+__device__ __forceinline__ void run_merge(RunAcc& a, const RunAcc& b) {
+    a.n += b.n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.sx[c] += b.sx[c];
+        a.sy[c] += b.sy[c];
+        a.sxy[c] += b.sxy[c];
+        a.sxx[c] += b.sxx[c];
+    }
+}
+
+__device__ __forceinline__ void run_minus(RunAcc& a, const RunAcc& b) {   // a -= b
+    a.n -= b.n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.sx[c] -= b.sx[c];
+        a.sy[c] -= b.sy[c];
+        a.sxy[c] -= b.sxy[c];
+        a.sxx[c] -= b.sxx[c];
+    }
+}
+
+// Largest byte of a pair of words.
+__device__ __forceinline__ uint32_t max_byte(uint32_t lo, uint32_t hi) {
+    uint32_t m = __vmaxu4(lo, hi);
+    m = __vmaxu4(m, m >> 16);
+    m = __vmaxu4(m, m >> 8);
+    return m & 255u;
+}
+
+// Add a segment's sums for region E to the run of E's parity, flushing the
+// run first when it holds another region of that parity.
+__device__ __forceinline__ void run_feed(RunAcc& run, int E, const RunAcc& part, SmemBins& bins) {
+    if (part.n == 0) return;
+    if (E != run.E) {
+        run_flush(run, bins);
+        run_reset(run, E);
+    }
+    run_merge(run, part);
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
-                                                  const uint8_t* __restrict__ e, int h, int w, int gf_on, int fast_io,
-                                                  int strip_rows, unsigned long long* __restrict__ gbins) {
+                                                     const uint8_t* __restrict__ e, int h, int w, int gf_on,
+                                                     int fast_io, int strip_rows,
+                                                     unsigned long long* __restrict__ gbins) {
     __shared__ SmemBins bins;
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins.lo[i] = bins.hi[i] = 0u;
     __syncthreads();
@@ -307,12 +380,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
     const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
     const int64_t tasks = (int64_t)bands * cols;
 
-    // Two runs per lane: `cur` accumulates, `vic` holds the previous region,
-    // so a region boundary through the lane's 8-pixel column costs a swap, not
-    // a flush.  A third region flushes `vic`.
-    RunAcc cur, vic;
-    run_reset(cur, -1);
-    run_reset(vic, -1);
+    // One run per exponent parity.  Adjacent regions of a smooth exponent
+    // field differ by one, so a boundary through a lane's column feeds the
+    // two runs without flushing either.
+    RunAcc even, odd;
+    run_reset(even, -1);
+    run_reset(odd, -1);
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
         const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
         const int x0 = xs + 8 * lane;
@@ -327,31 +400,48 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
 #pragma unroll
                 for (int c = 0; c < 3; ++c) load_bytes8(m3 + c * n, w, y, x0, fast, mlo[c], mhi[c]);
                 load_bytes8(e, w, y, x0, fast, elo, ehi);
-                const bool uniform = x0 + 8 <= w && elo == ehi && elo == __byte_perm(elo, 0, 0x0000);
-                // one segment of 8 pixels, or one segment per pixel; in the
-                // per-pixel case the packed pixel words are shifted down after
-                // each pixel, so no register array is indexed
-                const int segs = uniform ? 1 : min(8, w - x0);
-#pragma unroll 1
-                for (int sgi = 0; sgi < segs; ++sgi) {
-                    const int E = (int)(elo & 255u);
-                    elo = __funnelshift_r(elo, ehi, 8);
-                    ehi >>= 8;
-                    if (E != cur.E) {
-                        if (E != vic.E) {
-                            run_flush(vic, bins);
-                            run_reset(vic, E);
-                        }
-                        run_swap(cur, vic);
-                    }
-                    if (uniform) {
-                        run_add8(cur, X, mlo, mhi);
+                // byte masks of the odd-exponent pixels and the two exponents
+                const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+                const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
+                const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
+                const bool two = x0 + 8 <= w && ((elo ^ (Eo * 0x01010101u)) & olo) == 0 &&
+                                 ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
+                                 ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
+                                 ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
+                if (two) {
+                    // at most one even and one odd exponent in the segment
+                    RunAcc pe, po;
+                    seg_sums(X, mlo, mhi, 0xFFFFFFFFu, 0xFFFFFFFFu, pe);
+                    if ((olo | ohi) == 0u) {
+                        run_reset(po, -1);
+                    } else if ((olo & ohi) == 0xFFFFFFFFu) {
+                        po = pe;
+                        run_reset(pe, -1);
                     } else {
-                        uint32_t x[3], yv[3];
+                        seg_sums(X, mlo, mhi, olo, ohi, po);
+                        run_minus(pe, po);
+                    }
+                    run_feed(even, (int)Ee, pe, bins);
+                    run_feed(odd, (int)Eo, po, bins);
+                } else {
+                    // three or more exponents, or a ragged segment: pixel by pixel;
+                    // the packed words are shifted down so no register array is indexed
+                    const int cnt = min(8, w - x0);
+#pragma unroll 1
+                    for (int i = 0; i < cnt; ++i) {
+                        const int E = (int)(elo & 255u);
+                        elo = __funnelshift_r(elo, ehi, 8);
+                        ehi >>= 8;
+                        RunAcc one;
+                        one.E = E;
+                        one.n = 1;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            x[c] = X[c][0] & 0xFFFFu;
-                            yv[c] = mlo[c] & 255u;
+                            const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
+                            one.sx[c] = x;
+                            one.sy[c] = yv;
+                            one.sxy[c] = x * yv;
+                            one.sxx[c] = x * x;
                             mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
                             mhi[c] >>= 8;
                             X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
@@ -359,22 +449,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
                             X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
                             X[c][3] >>= 16;
                         }
-                        run_add1(cur, x, yv);
+                        if (E & 1) run_feed(odd, E, one, bins);
+                        else run_feed(even, E, one, bins);
                     }
                 }
             }
         }
         // Every run ends with its strip, so the 32-bit run accumulators cannot
-        // overflow.  Lanes order their two runs by region so lanes that saw the
-        // same two regions flush them in the same warp-wide step.
-        if ((unsigned)cur.E > (unsigned)vic.E) run_swap(cur, vic);
-#pragma unroll 1
-        for (int k = 0; k < 2; ++k) {
-            warp_flush(cur, bins, lane);
-            run_swap(cur, vic);
-        }
-        run_reset(cur, -1);
-        run_reset(vic, -1);
+        // overflow; lanes hold their runs by parity, so equal regions flush in
+        // the same warp-wide step.
+        warp_flush(even, bins, lane);
+        warp_flush(odd, bins, lane);
+        run_reset(even, -1);
+        run_reset(odd, -1);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) {
