@@ -366,11 +366,58 @@ __device__ __forceinline__ void run_feed(RunAcc& run, int E, const RunAcc& part,
     run_merge(run, part);
 }
 
+// Segments with three or more exponents (or ragged ones) are queued per warp
+// and drained 32 at a time, one per lane, so the rare per-pixel work does not
+// make every lane of the warp wait on it.  An entry is 21 words: the exponent
+// bytes, the mantissa bytes of the three planes, the x pairs and the count;
+// the odd stride keeps the lanes' accesses on distinct banks.
+constexpr int kQueueStride = 21;
+
+__device__ __forceinline__ void add_u32_exact(SmemBins& B, int idx, uint32_t v) {
+    const uint32_t old = atomicAdd(&B.lo[idx], v);
+    if (old + v < old) atomicAdd(&B.hi[idx], 1u);
+}
+
+// Adds every pixel of one queued segment straight into the bins.
+__device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
+    uint32_t elo = q[0], ehi = q[1];
+    uint32_t mlo[3] = {q[2], q[3], q[4]}, mhi[3] = {q[5], q[6], q[7]};
+    uint32_t X[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) X[c][k] = q[8 + 4 * c + k];
+    const int cnt = (int)q[20];
+#pragma unroll 1
+    for (int i = 0; i < cnt; ++i) {
+        const int E = (int)(elo & 255u);
+        elo = __funnelshift_r(elo, ehi, 8);
+        ehi >>= 8;
+        const int base = E * kNsum;
+        add_u32_exact(B, base, 1u);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
+            add_u32_exact(B, base + 1 + 4 * c, x);
+            add_u32_exact(B, base + 2 + 4 * c, yv);
+            add_u32_exact(B, base + 3 + 4 * c, x * yv);
+            add_u32_exact(B, base + 4 + 4 * c, x * x);
+            mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
+            mhi[c] >>= 8;
+            X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
+            X[c][1] = __funnelshift_r(X[c][1], X[c][2], 16);
+            X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
+            X[c][3] >>= 16;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
                                                      const uint8_t* __restrict__ e, int h, int w, int gf_on,
                                                      int fast_io, int strip_rows,
                                                      unsigned long long* __restrict__ gbins) {
     __shared__ SmemBins bins;
+    __shared__ uint32_t queue[kWarps][32 * kQueueStride];
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins.lo[i] = bins.hi[i] = 0u;
     __syncthreads();
 
@@ -379,6 +426,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
     const bool fast = fast_io != 0, gf = gf_on != 0;
     const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
     const int64_t tasks = (int64_t)bands * cols;
+    uint32_t* Q = queue[warp];
+    int queued = 0;   // entries in this warp's queue (warp-uniform)
 
     // One run per exponent parity.  Adjacent regions of a smooth exponent
     // field differ by one, so a boundary through a lane's column feeds the
@@ -395,8 +444,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
         for (int y = y0; y < y1; ++y) {
             uint32_t X[3][4];
             win.row(y, X);
+            uint32_t mlo[3] = {0u, 0u, 0u}, mhi[3] = {0u, 0u, 0u}, elo = 0u, ehi = 0u;
+            bool slow = false;
             if (x0 < w) {
-                uint32_t mlo[3], mhi[3], elo, ehi;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) load_bytes8(m3 + c * n, w, y, x0, fast, mlo[c], mhi[c]);
                 load_bytes8(e, w, y, x0, fast, elo, ehi);
@@ -424,35 +474,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
                     run_feed(even, (int)Ee, pe, bins);
                     run_feed(odd, (int)Eo, po, bins);
                 } else {
-                    // three or more exponents, or a ragged segment: pixel by pixel;
-                    // the packed words are shifted down so no register array is indexed
-                    const int cnt = min(8, w - x0);
-#pragma unroll 1
-                    for (int i = 0; i < cnt; ++i) {
-                        const int E = (int)(elo & 255u);
-                        elo = __funnelshift_r(elo, ehi, 8);
-                        ehi >>= 8;
-                        RunAcc one;
-                        one.E = E;
-                        one.n = 1;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
-                            one.sx[c] = x;
-                            one.sy[c] = yv;
-                            one.sxy[c] = x * yv;
-                            one.sxx[c] = x * x;
-                            mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
-                            mhi[c] >>= 8;
-                            X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
-                            X[c][1] = __funnelshift_r(X[c][1], X[c][2], 16);
-                            X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
-                            X[c][3] >>= 16;
-                        }
-                        if (E & 1) run_feed(odd, E, one, bins);
-                        else run_feed(even, E, one, bins);
-                    }
+                    slow = true;
                 }
+            }
+            // queue the segments with three or more exponents and the ragged ones
+            const unsigned want = __ballot_sync(0xffffffffu, slow);
+            if (want) {
+                if (queued + __popc(want) > 32) {
+                    if (lane < queued) drain_entry(Q + lane * kQueueStride, bins);
+                    __syncwarp();
+                    queued = 0;
+                }
+                if (slow) {
+                    uint32_t* q = Q + (queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+                    q[0] = elo;
+                    q[1] = ehi;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        q[2 + c] = mlo[c];
+                        q[5 + c] = mhi[c];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) q[8 + 4 * c + k] = X[c][k];
+                    }
+                    q[20] = (uint32_t)min(8, w - x0);
+                }
+                __syncwarp();
+                queued += __popc(want);
             }
         }
         // Every run ends with its strip, so the 32-bit run accumulators cannot
@@ -463,6 +510,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
         run_reset(even, -1);
         run_reset(odd, -1);
     }
+    if (lane < queued) drain_entry(Q + lane * kQueueStride, bins);
     __syncthreads();
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) {
         const unsigned long long v = ((unsigned long long)bins.hi[i] << 32) | bins.lo[i];
