@@ -149,6 +149,96 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
                     int gf_on, const slrme_params* params, uint32_t* rgbe_out,
                     slrme_stream_t stream);
 
+/* ===================================================================== batch form
+ * Many images of uneven sizes coded together: one persistent launch per stage
+ * (split, base round trip, fit + solve, residual; decode), tiles chosen by an
+ * autotuner, and the whole chain capturable as one CUDA graph.  The paper
+ * codes one image at a time; the batch form computes, image by image, exactly
+ * what the single-image entry points compute.
+ *
+ * Layout: all images share batch planes.  Image i occupies pixels
+ * [px_offset_i, px_offset_i + h_i w_i) of the word planes (rgbe, e, rgbe_out)
+ * and [3 px_offset_i, 3 px_offset_i + 3 h_i w_i) of the three-plane buffers
+ * (m3, s3, r3: planes c = 0, 1, 2 of the image at 3 px_offset_i + c h_i w_i).
+ * params[i] and hist[i * 3 * 511 ...] hold image i's parameters and histograms. */
+typedef struct slrme_batch_image {
+    int32_t h, w;         /* size: h, w >= 0, h*w < 2^31 */
+    int32_t quality;      /* base-layer quality 1..100 */
+    int32_t gf_on;        /* Gaussian restoration, 0 or 1 */
+    int64_t px_offset;    /* OUT (slrme_batch_plan_init): first pixel of the image in the batch planes,
+                             a multiple of 16 */
+} slrme_batch_image;
+
+typedef struct slrme_batch_tiles {
+    int32_t strip_rows;         /* rows per strip of fit / residual / decode: 4, 8 or 16 */
+    int32_t split_ctas_per_sm;  /* persistent CTAs per SM: split 1..8 */
+    int32_t base_ctas_per_sm;   /* base round trip 1..3 */
+    int32_t fit_ctas_per_sm;    /* fit 1..2 */
+    int32_t res_ctas_per_sm;    /* residual and decode 1..2 */
+} slrme_batch_tiles;
+
+/* Host-side plan; the caller owns the struct, the images array (kept alive
+ * while the plan is used) and the device workspace. */
+typedef struct slrme_batch_plan {
+    int32_t n_images;
+    int64_t total_px;                   /* pixels of a word plane (images + alignment padding) */
+    const slrme_batch_image* images;
+    void* workspace;                    /* device, slrme_batch_workspace_bytes(n_images), 256-byte aligned */
+    slrme_batch_tiles tiles;
+    int64_t split_chunks, base_tasks, strip_tasks;   /* task counts for the current tiles */
+    void* graph;                        /* instantiated CUDA graph (cudaGraphExec_t) or NULL */
+} slrme_batch_plan;
+
+/* Device buffers of one batch (all device pointers, caller-owned).  rgbe,
+ * r3 and rgbe_out must be 16-byte aligned, params and hist 4-byte aligned.
+ * Sizes: rgbe, e, rgbe_out: total_px elements; m3, s3, r3: 3 total_px;
+ * params: n_images; hist: n_images * 3 * 511 (or NULL). */
+typedef struct slrme_batch_buffers {
+    const uint32_t* rgbe;
+    uint8_t* m3;
+    uint8_t* e;
+    uint8_t* s3;
+    int16_t* r3;
+    slrme_params* params;
+    uint32_t* hist;
+    uint32_t* rgbe_out;
+} slrme_batch_buffers;
+
+/* Workspace bytes for n_images images (descriptors, quantiser tables, task
+ * tables, per-image statistics and bin sums). */
+size_t slrme_batch_workspace_bytes(int n_images);
+
+/* Lays the images out (sets images[i].px_offset), uploads descriptors and task
+ * tables to the workspace with default tiles.  Synchronises `stream`. */
+int slrme_batch_plan_init(slrme_batch_plan* plan, slrme_batch_image* images, int n_images, void* workspace,
+                          slrme_stream_t stream);
+
+/* Sets the tiles (validated) and re-uploads the task tables.  Synchronises `stream`. */
+int slrme_batch_set_tiles(slrme_batch_plan* plan, const slrme_batch_tiles* tiles, slrme_stream_t stream);
+
+/* Encoder over the batch: split, base round trip, fit + solve, residual
+ * (hist may be NULL); asynchronous on `stream`. */
+int slrme_batch_encode(const slrme_batch_plan* plan, const slrme_batch_buffers* bufs, slrme_stream_t stream);
+
+/* Decoder over the batch (reads s3, e, r3, params; writes rgbe_out). */
+int slrme_batch_decode(const slrme_batch_plan* plan, const slrme_batch_buffers* bufs, slrme_stream_t stream);
+
+/* Times each stage over candidate tiles on this batch (`reps` runs each, best
+ * time) and keeps the fastest; synchronous, overwrites the buffers' outputs.
+ * The coded results never depend on the tiles. */
+int slrme_batch_autotune(slrme_batch_plan* plan, const slrme_batch_buffers* bufs, int reps, slrme_stream_t stream);
+
+/* Captures encode + decode on `stream` (a created stream, not the legacy
+ * default stream) into a CUDA graph bound to these buffers and instantiates
+ * it into plan->graph, replacing any previous graph. */
+int slrme_batch_graph_build(slrme_batch_plan* plan, const slrme_batch_buffers* bufs, slrme_stream_t stream);
+
+/* Launches plan->graph on `stream`. */
+int slrme_batch_graph_launch(const slrme_batch_plan* plan, slrme_stream_t stream);
+
+/* Destroys plan->graph (if any). */
+int slrme_batch_graph_destroy(slrme_batch_plan* plan);
+
 /* Host, no GPU: copies the library's own constant tables (built by the
  * library's host code) for inspection: log2_lut[2048] = round(65536 log2(2048+i)),
  * gamma[256] thresholds (gamma[k] = float(((k-0.5)/255)^2.2), gamma[0] = 0),

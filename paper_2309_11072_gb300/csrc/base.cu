@@ -126,129 +126,176 @@ __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
-                                                   int h, int w, const int64_t* __restrict__ lum_stats,
-                                                   uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3, int fast_io,
-                                                   const QuantTable QT) {
-    __shared__ float gam[256];
-    __shared__ int tile[kWarps][kTileWords];
-    __shared__ int keyJ, keyR;
-    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = __uint_as_float(kGammaBits[i]);
-    if (threadIdx.x == 0) key_from_stats(lum_stats, &keyJ, &keyR);
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int blk = lane >> 3, sub = lane & 7;     // block in the band, row (phases 1, 3) or column (phase 2)
-    const int J = keyJ;
-    const float kr = __uint_as_float(kKrBits[keyR]), wr = __uint_as_float(kWrBits[keyR]);
-    const int64_t n = (int64_t)h * w;
-    const bool fast = fast_io != 0;
-
-    // quantiser column `sub` of the block: q[v][sub], v = 0..7
-    int qcol[8];
+// Key and quantiser state of one image, as a lane needs it.
+struct BaseKey {
+    int J;
+    float kr, wr;
+    int qcol[8];        // quantiser column `sub` of the block: q[v][sub], v = 0..7
     uint32_t qmcol[8];
+};
+
+__device__ __forceinline__ void base_key(const int64_t* __restrict__ stats, const QuantTable& QT, int sub,
+                                         BaseKey& K) {
+    int r;
+    key_from_stats(stats, &K.J, &r);
+    K.kr = __uint_as_float(kKrBits[r]);
+    K.wr = __uint_as_float(kWrBits[r]);
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-        qcol[v] = QT.q[v * 8 + sub];
-        qmcol[v] = QT.qm[v * 8 + sub];
+        K.qcol[v] = QT.q[v * 8 + sub];
+        K.qmcol[v] = QT.qm[v * 8 + sub];
     }
+}
 
-    int* T = tile[warp];
-    const int bands = (h + 7) >> 3, cols = (w + 31) >> 5;
-    const int64_t tasks = (int64_t)bands * cols;
-    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * 8, xb = (int)(t % cols) * 32;
-        const int x0 = xb + 8 * blk;          // first column of this lane's block
-        const int y = y0 + sub;               // this lane's row in phases 1 and 3
-
-        // ---------------- phase 1: tone map and forward DCT along x
-        {
-            uint8_t mr[8], mg[8], mb[8], ee[8];
-            // rows past the bottom and columns past the right edge replicate the last row/column
-            load8(m3, h, w, y, x0, fast, mr);
-            load8(m3 + n, h, w, y, x0, fast, mg);
-            load8(m3 + 2 * n, h, w, y, x0, fast, mb);
-            load8(e, h, w, y, x0, fast, ee);
-            int sdr[3][8];
+// One band task of one image (all 32 lanes): rows y0 .. y0+7, columns xb .. xb+31.
+__device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h, int w,
+                                          bool fast, int y0, int xb, int lane, const BaseKey& K, const float* gam,
+                                          int* T, uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3) {
+    const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
+    const int64_t n = (int64_t)h * w;
+    const int J = K.J;
+    const float kr = K.kr, wr = K.wr;
+    const int x0 = xb + 8 * blk;                 // first column of this lane's block
+    const int y = y0 + sub;                      // this lane's row in phases 1 and 3
+    // ---------------- phase 1: tone map and forward DCT along x
+    {
+        uint8_t mr[8], mg[8], mb[8], ee[8];
+        // rows past the bottom and columns past the right edge replicate the last row/column
+        load8(m3, h, w, y, x0, fast, mr);
+        load8(m3 + n, h, w, y, x0, fast, mg);
+        load8(m3 + 2 * n, h, w, y, x0, fast, mb);
+        load8(e, h, w, y, x0, fast, ee);
+        int sdr[3][8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int E = ee[i];
-                if (E == 0) {
-                    sdr[0][i] = sdr[1][i] = sdr[2][i] = 0;
-                    continue;
-                }
-                const int yq = 2126 * (2 * mr[i] + 1) + 7152 * (2 * mg[i] + 1) + 722 * (2 * mb[i] + 1);
-                int d = E - 137 - J;
-                d = d < -100 ? -100 : (d > 100 ? 100 : d);
-                const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
-                const float L = __fmul_rn(__fmul_rn(kr, __int2float_rn(yq)), p2d);
-                const float den = __fadd_rn(1.0f, L);
-                const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
-                sdr[0][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mr[i] + 1)), gam);
-                sdr[1][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mg[i] + 1)), gam);
-                sdr[2][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mb[i] + 1)), gam);
+        for (int i = 0; i < 8; ++i) {
+            const int E = ee[i];
+            if (E == 0) {
+                sdr[0][i] = sdr[1][i] = sdr[2][i] = 0;
+                continue;
             }
-            if (sdr3 && x0 < w) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const uint32_t lo = sdr[c][0] | (sdr[c][1] << 8) | (sdr[c][2] << 16) | (sdr[c][3] << 24);
-                    const uint32_t hi = sdr[c][4] | (sdr[c][5] << 8) | (sdr[c][6] << 16) | (sdr[c][7] << 24);
-                    store8(sdr3 + c * n, h, w, y, x0, fast, lo, hi);
-                }
-            }
+            const int yq = 2126 * (2 * mr[i] + 1) + 7152 * (2 * mg[i] + 1) + 722 * (2 * mb[i] + 1);
+            int d = E - 137 - J;
+            d = d < -100 ? -100 : (d > 100 ? 100 : d);
+            const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
+            const float L = __fmul_rn(__fmul_rn(kr, __int2float_rn(yq)), p2d);
+            const float den = __fadd_rn(1.0f, L);
+            const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
+            sdr[0][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mr[i] + 1)), gam);
+            sdr[1][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mg[i] + 1)), gam);
+            sdr[2][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mb[i] + 1)), gam);
+        }
+        if (sdr3 && x0 < w) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                int X[8], F[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) X[i] = sdr[c][i] - 128;
-                fdct8(X, F);
-                int* row = T + (c * 4 + blk) * 72 + sub * 9;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) row[u] = rshift_round(F[u], 9);
+                const uint32_t lo = sdr[c][0] | (sdr[c][1] << 8) | (sdr[c][2] << 16) | (sdr[c][3] << 24);
+                const uint32_t hi = sdr[c][4] | (sdr[c][5] << 8) | (sdr[c][6] << 16) | (sdr[c][7] << 24);
+                store8(sdr3 + c * n, h, w, y, x0, fast, lo, hi);
             }
         }
-        __syncwarp();
-
-        // ---------------- phase 2: along y: forward DCT, quantiser, inverse DCT
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            int* col = T + (c * 4 + blk) * 72 + sub;
-            int Tc[8], F[8], G[8];
+            int X[8], F[8];
 #pragma unroll
-            for (int yy = 0; yy < 8; ++yy) Tc[yy] = col[yy * 9];
-            fdct8(Tc, F);
+            for (int i = 0; i < 8; ++i) X[i] = sdr[c][i] - 128;
+            fdct8(X, F);
+            int* row = T + (c * 4 + blk) * 72 + sub * 9;
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const int f = rshift_round(F[v], 15);
-                const uint32_t a = (uint32_t)(f < 0 ? -f : f);
-                const int lvl = (int)__umulhi((a + (uint32_t)(qcol[v] >> 1)) << 8, qmcol[v]);
-                F[v] = (f < 0 ? -lvl : lvl) * qcol[v];
-            }
-            idct8(F, G);
-#pragma unroll
-            for (int yy = 0; yy < 8; ++yy) col[yy * 9] = rshift_round(G[yy], 9);
+            for (int u = 0; u < 8; ++u) row[u] = rshift_round(F[u], 9);
         }
-        __syncwarp();
+    }
+    __syncwarp();
 
-        // ---------------- phase 3: inverse DCT along x, store S
+    // ---------------- phase 2: along y: forward DCT, quantiser, inverse DCT
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int* row = T + (c * 4 + blk) * 72 + sub * 9;
-            int G[8], X[8];
+    for (int c = 0; c < 3; ++c) {
+        int* col = T + (c * 4 + blk) * 72 + sub;
+        int Tc[8], F[8], G[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) G[u] = row[u];
-            idct8(G, X);
-            uint32_t lo = 0, hi = 0;
+        for (int yy = 0; yy < 8; ++yy) Tc[yy] = col[yy * 9];
+        fdct8(Tc, F);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                int s = rshift_round(X[i], 15) + 128;
-                s = s < 0 ? 0 : (s > 255 ? 255 : s);
-                if (i < 4) lo |= (uint32_t)s << (8 * i);
-                else hi |= (uint32_t)s << (8 * (i - 4));
-            }
-            if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi);
+        for (int v = 0; v < 8; ++v) {
+            const int f = rshift_round(F[v], 15);
+            const uint32_t a = (uint32_t)(f < 0 ? -f : f);
+            const int lvl = (int)__umulhi((a + (uint32_t)(K.qcol[v] >> 1)) << 8, K.qmcol[v]);
+            F[v] = (f < 0 ? -lvl : lvl) * K.qcol[v];
         }
-        __syncwarp();
+        idct8(F, G);
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) col[yy * 9] = rshift_round(G[yy], 9);
+    }
+    __syncwarp();
+
+    // ---------------- phase 3: inverse DCT along x, store S
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int* row = T + (c * 4 + blk) * 72 + sub * 9;
+        int G[8], X[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) G[u] = row[u];
+        idct8(G, X);
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int s = rshift_round(X[i], 15) + 128;
+            s = s < 0 ? 0 : (s > 255 ? 255 : s);
+            if (i < 4) lo |= (uint32_t)s << (8 * i);
+            else hi |= (uint32_t)s << (8 * (i - 4));
+        }
+        if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
+                                                      int h, int w, const int64_t* __restrict__ lum_stats,
+                                                      uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3,
+                                                      int fast_io, const QuantTable QT) {
+    __shared__ float gam[256];
+    __shared__ int tile[kWarps][kTileWords];
+    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = __uint_as_float(kGammaBits[i]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BaseKey K;
+    base_key(lum_stats, QT, lane & 7, K);
+    const int cols = (w + 31) >> 5;
+    const int64_t tasks = (int64_t)((h + 7) >> 3) * cols;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
+        base_band(m3, e, h, w, fast_io != 0, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, tile[warp], s3,
+                  sdr3);
+}
+
+// Batch: CTA tasks of 8 band tasks of one image, contiguous ranges per CTA.
+__global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, int64_t cta_tasks,
+                                                            const uint8_t* __restrict__ m3b,
+                                                            const uint8_t* __restrict__ eb, uint8_t* __restrict__ s3b) {
+    __shared__ float gam[256];
+    __shared__ int tile[kWarps][kTileWords];
+    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = __uint_as_float(kGammaBits[i]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
+    int cur = -1;
+    BaseKey K;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int i = batch_image_of(B.base_prefix, B.n, k);
+        if (i != cur) {
+            base_key(B.lum_stats + 2 * i, B.quant[i], lane & 7, K);
+            cur = i;
+        }
+        const BatchImage im = B.img[i];
+        const uint8_t* m3 = m3b + 3 * im.px;
+        const uint8_t* e = eb + im.px;
+        uint8_t* s3 = s3b + 3 * im.px;
+        const int cols = (im.w + 31) >> 5;
+        const int64_t bands = (int64_t)((im.h + 7) >> 3) * cols;
+        const int64_t t = (k - B.base_prefix[i]) * kWarps + warp;
+        const bool fast = (im.w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
+                          ((uintptr_t)s3 % 8 == 0);
+        if ((int64_t)im.h * im.w > 0 && t < bands)
+            base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, tile[warp],
+                      s3, nullptr);
     }
 }
 
@@ -267,6 +314,19 @@ int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t
     if (blocks < 1) blocks = 1;
     k_base<<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, fast ? 1 : 0, qt);
     return cuda_status("sdri_base_roundtrip launch");
+}
+
+}  // namespace slrme
+
+namespace slrme {
+
+int launch_base_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* m3, const uint8_t* e,
+                      uint8_t* s3, cudaStream_t s) {
+    if (cta_tasks == 0) return SLRME_OK;
+    const int64_t cap = (int64_t)geometry().sms * (ctas_per_sm < 3 ? ctas_per_sm : 3);
+    const int64_t g = cta_tasks < cap ? cta_tasks : cap;
+    k_base_batch<<<(unsigned)(g < 1 ? 1 : g), kThreads, 0, s>>>(B, cta_tasks, m3, e, s3);
+    return cuda_status("batch base launch");
 }
 
 }  // namespace slrme

@@ -254,46 +254,6 @@ __device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lan
     }
 }
 
-// Accumulate one full uniform row segment (8 pixels of one region) into a run.
-__device__ __forceinline__ void run_add8(RunAcc& a, const uint32_t (&X)[3][4], const uint32_t (&mlo)[3],
-                                         const uint32_t (&mhi)[3]) {
-    a.n += 8;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const uint32_t ps = X[c][0] + X[c][1] + X[c][2] + X[c][3];
-        a.sx[c] += (ps & 0xFFFFu) + (ps >> 16);
-        a.sy[c] = __dp4a(mlo[c], 0x01010101u, __dp4a(mhi[c], 0x01010101u, a.sy[c]));
-        a.sxy[c] = __dp2a_lo(X[c][0], mlo[c], a.sxy[c]);
-        a.sxy[c] = __dp2a_hi(X[c][1], mlo[c], a.sxy[c]);
-        a.sxy[c] = __dp2a_lo(X[c][2], mhi[c], a.sxy[c]);
-        a.sxy[c] = __dp2a_hi(X[c][3], mhi[c], a.sxy[c]);
-        uint32_t q = a.sxx[c];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t lo16 = X[c][k] & 0xFFFFu, hi16 = X[c][k] >> 16;
-            q += lo16 * lo16 + hi16 * hi16;
-        }
-        a.sxx[c] = q;
-    }
-}
-
-__device__ __forceinline__ void run_add1(RunAcc& a, const uint32_t (&x)[3], const uint32_t (&y)[3]) {
-    a.n += 1;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        a.sx[c] += x[c];
-        a.sy[c] += y[c];
-        a.sxy[c] += x[c] * y[c];
-        a.sxx[c] += x[c] * x[c];
-    }
-}
-
-__device__ __forceinline__ void run_swap(RunAcc& a, RunAcc& b) {
-    const RunAcc t = a;
-    a = b;
-    b = t;
-}
-
 // Sums of one 8-pixel segment, restricted to the pixels whose byte of `mlo/mhi`
 // mask is 0xFF (mask = ~0 for all pixels).  x pairs are masked with the
 // 16-bit expansion of the byte mask.
@@ -412,110 +372,187 @@ __device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
     }
 }
 
+// Per-warp state of the fit: one run per exponent parity (adjacent regions
+// of a smooth exponent field differ by one, so a boundary through a lane's
+// column feeds the two runs without flushing either) and the queue of
+// segments that need per-pixel work.
+struct FitWarp {
+    RunAcc even, odd;
+    uint32_t* Q;
+    int queued;   // entries in the queue (warp-uniform)
+};
+
+__device__ __forceinline__ void fit_drain(FitWarp& st, SmemBins& bins, int lane) {
+    if (lane < st.queued) drain_entry(st.Q + lane * kQueueStride, bins);
+    __syncwarp();
+    st.queued = 0;
+}
+
+// One strip of one image (all 32 lanes): rows y0 .. y0 + rows - 1, columns xs .. xs + 255.
+__device__ __forceinline__ void fit_strip(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
+                                          const uint8_t* __restrict__ e, int h, int w, bool gf, bool fast, int y0,
+                                          int rows, int xs, int lane, FitWarp& st, SmemBins& bins) {
+    const int64_t n = (int64_t)h * w;
+    const int x0 = xs + 8 * lane;
+    const int y1 = min(y0 + rows, h);
+    GfWindow win{s3, n, h, w, xs, lane, fast, gf};
+    win.start(y0);
+    for (int y = y0; y < y1; ++y) {
+        uint32_t X[3][4];
+        win.row(y, X);
+        uint32_t mlo[3] = {0u, 0u, 0u}, mhi[3] = {0u, 0u, 0u}, elo = 0u, ehi = 0u;
+        bool slow = false;
+        if (x0 < w) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) load_bytes8(m3 + c * n, w, y, x0, fast, mlo[c], mhi[c]);
+            load_bytes8(e, w, y, x0, fast, elo, ehi);
+            // byte masks of the odd-exponent pixels and the two exponents
+            const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+            const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
+            const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
+            const bool two = x0 + 8 <= w && ((elo ^ (Eo * 0x01010101u)) & olo) == 0 &&
+                             ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
+                             ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
+                             ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
+            if (two) {
+                // at most one even and one odd exponent in the segment
+                RunAcc pe, po;
+                seg_sums(X, mlo, mhi, 0xFFFFFFFFu, 0xFFFFFFFFu, pe);
+                if ((olo | ohi) == 0u) {
+                    run_reset(po, -1);
+                } else if ((olo & ohi) == 0xFFFFFFFFu) {
+                    po = pe;
+                    run_reset(pe, -1);
+                } else {
+                    seg_sums(X, mlo, mhi, olo, ohi, po);
+                    run_minus(pe, po);
+                }
+                run_feed(st.even, (int)Ee, pe, bins);
+                run_feed(st.odd, (int)Eo, po, bins);
+            } else {
+                slow = true;
+            }
+        }
+        // queue the segments with three or more exponents and the ragged ones
+        const unsigned want = __ballot_sync(0xffffffffu, slow);
+        if (want) {
+            if (st.queued + __popc(want) > 32) fit_drain(st, bins, lane);
+            if (slow) {
+                uint32_t* q = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+                q[0] = elo;
+                q[1] = ehi;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    q[2 + c] = mlo[c];
+                    q[5 + c] = mhi[c];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) q[8 + 4 * c + k] = X[c][k];
+                }
+                q[20] = (uint32_t)min(8, w - x0);
+            }
+            __syncwarp();
+            st.queued += __popc(want);
+        }
+    }
+    // Every run ends with its strip, so the 32-bit run accumulators cannot
+    // overflow; lanes hold their runs by parity, so equal regions flush in
+    // the same warp-wide step.
+    warp_flush(st.even, bins, lane);
+    warp_flush(st.odd, bins, lane);
+    run_reset(st.even, -1);
+    run_reset(st.odd, -1);
+}
+
+__device__ __forceinline__ void bins_clear(SmemBins& bins) {
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += blockDim.x) bins.lo[i] = bins.hi[i] = 0u;
+}
+
+// Adds the block's bins to global int64 sums (and clears them when asked).
+__device__ __forceinline__ void bins_to_global(SmemBins& bins, unsigned long long* __restrict__ g, bool clear) {
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += blockDim.x) {
+        const unsigned long long v = ((unsigned long long)bins.hi[i] << 32) | bins.lo[i];
+        if (v) {
+            atomicAdd(g + i, v);
+            if (clear) bins.lo[i] = bins.hi[i] = 0u;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
                                                      const uint8_t* __restrict__ e, int h, int w, int gf_on,
                                                      int fast_io, int strip_rows,
                                                      unsigned long long* __restrict__ gbins) {
     __shared__ SmemBins bins;
     __shared__ uint32_t queue[kWarps][32 * kQueueStride];
-    for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) bins.lo[i] = bins.hi[i] = 0u;
+    bins_clear(bins);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t n = (int64_t)h * w;
-    const bool fast = fast_io != 0, gf = gf_on != 0;
-    const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
-    const int64_t tasks = (int64_t)bands * cols;
-    uint32_t* Q = queue[warp];
-    int queued = 0;   // entries in this warp's queue (warp-uniform)
-
-    // One run per exponent parity.  Adjacent regions of a smooth exponent
-    // field differ by one, so a boundary through a lane's column feeds the
-    // two runs without flushing either.
-    RunAcc even, odd;
-    run_reset(even, -1);
-    run_reset(odd, -1);
-    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
-        const int x0 = xs + 8 * lane;
-        const int y1 = min(y0 + strip_rows, h);
-        GfWindow win{s3, n, h, w, xs, lane, fast, gf};
-        win.start(y0);
-        for (int y = y0; y < y1; ++y) {
-            uint32_t X[3][4];
-            win.row(y, X);
-            uint32_t mlo[3] = {0u, 0u, 0u}, mhi[3] = {0u, 0u, 0u}, elo = 0u, ehi = 0u;
-            bool slow = false;
-            if (x0 < w) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) load_bytes8(m3 + c * n, w, y, x0, fast, mlo[c], mhi[c]);
-                load_bytes8(e, w, y, x0, fast, elo, ehi);
-                // byte masks of the odd-exponent pixels and the two exponents
-                const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
-                const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
-                const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
-                const bool two = x0 + 8 <= w && ((elo ^ (Eo * 0x01010101u)) & olo) == 0 &&
-                                 ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
-                                 ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
-                                 ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
-                if (two) {
-                    // at most one even and one odd exponent in the segment
-                    RunAcc pe, po;
-                    seg_sums(X, mlo, mhi, 0xFFFFFFFFu, 0xFFFFFFFFu, pe);
-                    if ((olo | ohi) == 0u) {
-                        run_reset(po, -1);
-                    } else if ((olo & ohi) == 0xFFFFFFFFu) {
-                        po = pe;
-                        run_reset(pe, -1);
-                    } else {
-                        seg_sums(X, mlo, mhi, olo, ohi, po);
-                        run_minus(pe, po);
-                    }
-                    run_feed(even, (int)Ee, pe, bins);
-                    run_feed(odd, (int)Eo, po, bins);
-                } else {
-                    slow = true;
-                }
-            }
-            // queue the segments with three or more exponents and the ragged ones
-            const unsigned want = __ballot_sync(0xffffffffu, slow);
-            if (want) {
-                if (queued + __popc(want) > 32) {
-                    if (lane < queued) drain_entry(Q + lane * kQueueStride, bins);
-                    __syncwarp();
-                    queued = 0;
-                }
-                if (slow) {
-                    uint32_t* q = Q + (queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
-                    q[0] = elo;
-                    q[1] = ehi;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        q[2 + c] = mlo[c];
-                        q[5 + c] = mhi[c];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) q[8 + 4 * c + k] = X[c][k];
-                    }
-                    q[20] = (uint32_t)min(8, w - x0);
-                }
-                __syncwarp();
-                queued += __popc(want);
-            }
-        }
-        // Every run ends with its strip, so the 32-bit run accumulators cannot
-        // overflow; lanes hold their runs by parity, so equal regions flush in
-        // the same warp-wide step.
-        warp_flush(even, bins, lane);
-        warp_flush(odd, bins, lane);
-        run_reset(even, -1);
-        run_reset(odd, -1);
-    }
-    if (lane < queued) drain_entry(Q + lane * kQueueStride, bins);
+    const int cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)((h + strip_rows - 1) / strip_rows) * cols;
+    FitWarp st;
+    run_reset(st.even, -1);
+    run_reset(st.odd, -1);
+    st.Q = queue[warp];
+    st.queued = 0;
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
+        fit_strip(s3, m3, e, h, w, gf_on != 0, fast_io != 0, (int)(t / cols) * strip_rows, strip_rows,
+                  (int)(t % cols) * kStripCols, lane, st, bins);
+    fit_drain(st, bins, lane);
     __syncthreads();
-    for (int i = threadIdx.x; i < kNbin * kNsum; i += kThreads) {
-        const unsigned long long v = ((unsigned long long)bins.hi[i] << 32) | bins.lo[i];
-        if (v) atomicAdd(gbins + i, v);
+    bins_to_global(bins, gbins, false);
+}
+
+// Vector loads need 8-byte aligned rows of every plane.
+__device__ __forceinline__ bool planes_fast(int w, const void* a, const void* b, const void* c) {
+    return (w % 8 == 0) && ((uintptr_t)a % 8 == 0) && ((uintptr_t)b % 8 == 0) && ((uintptr_t)c % 8 == 0);
+}
+
+// Batch: each CTA task is 8 strips of one image; a CTA works through a
+// contiguous range of tasks, so its bins change image rarely.
+__global__ void __launch_bounds__(kThreads, 2) k_fit_batch(const BatchDev B, int64_t cta_tasks,
+                                                           const uint8_t* __restrict__ s3b,
+                                                           const uint8_t* __restrict__ m3b,
+                                                           const uint8_t* __restrict__ eb) {
+    __shared__ SmemBins bins;
+    __shared__ uint32_t queue[kWarps][32 * kQueueStride];
+    bins_clear(bins);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    FitWarp st;
+    run_reset(st.even, -1);
+    run_reset(st.odd, -1);
+    st.Q = queue[warp];
+    st.queued = 0;
+    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
+    int cur = -1;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int i = batch_image_of(B.strip_prefix, B.n, k);
+        if (i != cur) {
+            if (cur >= 0) {
+                fit_drain(st, bins, lane);
+                __syncthreads();
+                bins_to_global(bins, B.sums + (int64_t)cur * kNbin * kNsum, true);
+                __syncthreads();
+            }
+            cur = i;
+        }
+        const BatchImage im = B.img[i];
+        const int64_t n = (int64_t)im.h * im.w;
+        const uint8_t* s3 = s3b + 3 * im.px;
+        const uint8_t* m3 = m3b + 3 * im.px;
+        const uint8_t* e = eb + im.px;
+        const int cols = (im.w + kStripCols - 1) / kStripCols;
+        const int64_t strips = (int64_t)((im.h + B.strip_rows - 1) / B.strip_rows) * cols;
+        const int64_t t = (k - B.strip_prefix[i]) * kWarps + warp;
+        if (n > 0 && t < strips)
+            fit_strip(s3, m3, e, im.h, im.w, im.gf_on != 0, planes_fast(im.w, s3, m3, e),
+                      (int)(t / cols) * B.strip_rows, B.strip_rows, (int)(t % cols) * kStripCols, lane, st, bins);
     }
+    fit_drain(st, bins, lane);
+    __syncthreads();
+    if (cur >= 0) bins_to_global(bins, B.sums + (int64_t)cur * kNbin * kNsum, false);
 }
 
 // ====================================================================== solve
@@ -541,7 +578,9 @@ __device__ __forceinline__ double i128_to_f64(__int128 v) {
     return neg ? -r : r;
 }
 
-__global__ void __launch_bounds__(768) k_solve(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
+// Slope and intercept of every (channel, region) of one image from its sums
+// (768 threads: channel = thread / 256, region E = thread % 256).
+__device__ __forceinline__ void solve_image(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
     const int c = threadIdx.x >> 8, E = threadIdx.x & 255;
     const int64_t* s = sums + E * kNsum;
     const int64_t N = s[0];
@@ -568,12 +607,73 @@ __global__ void __launch_bounds__(768) k_solve(const int64_t* __restrict__ sums,
     }
 }
 
+__global__ void __launch_bounds__(768) k_solve(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
+    solve_image(sums, P);
+}
+
+// one block per image of a batch
+__global__ void __launch_bounds__(768) k_solve_batch(const unsigned long long* __restrict__ sums,
+                                                      slrme_params* __restrict__ P) {
+    solve_image(reinterpret_cast<const int64_t*>(sums) + (int64_t)blockIdx.x * kNbin * kNsum, P + blockIdx.x);
+}
+
 // ====================================================================== residual
 
 __device__ __forceinline__ void load_params(const slrme_params* __restrict__ P, float* sa, float* sb) {
     for (int i = threadIdx.x; i < 3 * kNbin; i += blockDim.x) {
         sa[i] = (&P->a[0][0])[i];
         sb[i] = (&P->b[0][0])[i];
+    }
+}
+
+// One strip: R = M - M* for rows y0 .. y0 + rows - 1, columns xs .. xs + 255;
+// `hist` (shared, may be null) counts the residual values.
+__device__ __forceinline__ void residual_strip(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ m3,
+                                               const uint8_t* __restrict__ e, int h, int w, bool gf, bool fast,
+                                               bool vec_r, int y0, int rows, int xs, int lane, const float* sa,
+                                               const float* sb, int16_t* __restrict__ r3, uint32_t* hist) {
+    const int64_t n = (int64_t)h * w;
+    const int x0 = xs + 8 * lane;
+    const int y1 = min(y0 + rows, h);
+    GfWindow win{s3, n, h, w, xs, lane, fast, gf};
+    win.start(y0);
+    for (int y = y0; y < y1; ++y) {
+        uint32_t X[3][4];
+        win.row(y, X);
+        if (x0 >= w) continue;
+        uint32_t elo, ehi;
+        load_bytes8(e, w, y, x0, fast, elo, ehi);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            uint32_t mlo, mhi;
+            load_bytes8(m3 + c * n, w, y, x0, fast, mlo, mhi);
+            int r[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
+                const int M = (int)byte_of(i < 4 ? mlo : mhi, i & 3);
+                r[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
+            }
+            int16_t* row = r3 + c * n + (int64_t)y * w + x0;
+            if (vec_r && x0 + 8 <= w) {
+                uint4 v;
+                v.x = (uint32_t)(r[0] & 0xFFFF) | ((uint32_t)r[1] << 16);
+                v.y = (uint32_t)(r[2] & 0xFFFF) | ((uint32_t)r[3] << 16);
+                v.z = (uint32_t)(r[4] & 0xFFFF) | ((uint32_t)r[5] << 16);
+                v.w = (uint32_t)(r[6] & 0xFFFF) | ((uint32_t)r[7] << 16);
+                *reinterpret_cast<uint4*>(row) = v;
+                if (hist) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + r[i] + 255], 1u);
+                }
+            } else {
+                const int cnt = min(8, w - x0);
+                for (int i = 0; i < cnt; ++i) {
+                    row[i] = (int16_t)r[i];
+                    if (hist) atomicAdd(&hist[c * kNres + r[i] + 255], 1u);
+                }
+            }
+        }
     }
 }
 
@@ -587,58 +687,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
     if (ghist)
         for (int i = threadIdx.x; i < 3 * kNres; i += kThreads) hist[i] = 0u;
     __syncthreads();
-
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t n = (int64_t)h * w;
-    const bool fast = fast_io != 0, gf = gf_on != 0;
-    const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
-    const int64_t tasks = (int64_t)bands * cols;
-    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
-        const int x0 = xs + 8 * lane;
-        const int y1 = min(y0 + strip_rows, h);
-        GfWindow win{s3, n, h, w, xs, lane, fast, gf};
-        win.start(y0);
-        for (int y = y0; y < y1; ++y) {
-            uint32_t X[3][4];
-            win.row(y, X);
-            if (x0 < w) {
-                uint32_t elo, ehi;
-                load_bytes8(e, w, y, x0, fast, elo, ehi);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint32_t mlo, mhi;
-                    load_bytes8(m3 + c * n, w, y, x0, fast, mlo, mhi);
-                    int r[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
-                        const int M = (int)byte_of(i < 4 ? mlo : mhi, i & 3);
-                        r[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
-                    }
-                    int16_t* row = r3 + c * n + (int64_t)y * w + x0;
-                    if (fast && x0 + 8 <= w) {
-                        uint4 v;
-                        v.x = (uint32_t)(r[0] & 0xFFFF) | ((uint32_t)r[1] << 16);
-                        v.y = (uint32_t)(r[2] & 0xFFFF) | ((uint32_t)r[3] << 16);
-                        v.z = (uint32_t)(r[4] & 0xFFFF) | ((uint32_t)r[5] << 16);
-                        v.w = (uint32_t)(r[6] & 0xFFFF) | ((uint32_t)r[7] << 16);
-                        *reinterpret_cast<uint4*>(row) = v;
-                        if (ghist) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + r[i] + 255], 1u);
-                        }
-                    } else {
-                        const int cnt = min(8, w - x0);
-                        for (int i = 0; i < cnt; ++i) {
-                            row[i] = (int16_t)r[i];
-                            if (ghist) atomicAdd(&hist[c * kNres + r[i] + 255], 1u);
-                        }
-                    }
-                }
-            }
-        }
-    }
+    const int cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)((h + strip_rows - 1) / strip_rows) * cols;
+    const bool vec_r = fast_io != 0 && ((uintptr_t)r3 % 16 == 0);
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
+        residual_strip(s3, m3, e, h, w, gf_on != 0, fast_io != 0, vec_r, (int)(t / cols) * strip_rows, strip_rows,
+                       (int)(t % cols) * kStripCols, lane, sa, sb, r3, ghist ? hist : nullptr);
     if (ghist) {
         __syncthreads();
         for (int i = threadIdx.x; i < 3 * kNres; i += kThreads)
@@ -646,7 +701,107 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
     }
 }
 
+// Batch: CTA tasks of 8 strips of one image; parameters and histogram of the
+// current image stay in shared memory until the CTA moves to the next image.
+__global__ void __launch_bounds__(kThreads) k_residual_batch(const BatchDev B, int64_t cta_tasks,
+                                                             const uint8_t* __restrict__ s3b,
+                                                             const uint8_t* __restrict__ m3b,
+                                                             const uint8_t* __restrict__ eb,
+                                                             const slrme_params* __restrict__ P,
+                                                             int16_t* __restrict__ r3b, uint32_t* __restrict__ ghist) {
+    __shared__ float sa[3 * kNbin], sb[3 * kNbin];
+    __shared__ uint32_t hist[3 * kNres];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
+    int cur = -1;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int i = batch_image_of(B.strip_prefix, B.n, k);
+        if (i != cur) {
+            __syncthreads();
+            if (cur >= 0 && ghist)
+                for (int j = threadIdx.x; j < 3 * kNres; j += kThreads)
+                    if (hist[j]) atomicAdd(ghist + (int64_t)cur * 3 * kNres + j, hist[j]);
+            load_params(P + i, sa, sb);
+            for (int j = threadIdx.x; j < 3 * kNres; j += kThreads) hist[j] = 0u;
+            __syncthreads();
+            cur = i;
+        }
+        const BatchImage im = B.img[i];
+        const uint8_t* s3 = s3b + 3 * im.px;
+        const uint8_t* m3 = m3b + 3 * im.px;
+        const uint8_t* e = eb + im.px;
+        int16_t* r3 = r3b + 3 * im.px;
+        const int cols = (im.w + kStripCols - 1) / kStripCols;
+        const int64_t strips = (int64_t)((im.h + B.strip_rows - 1) / B.strip_rows) * cols;
+        const int64_t t = (k - B.strip_prefix[i]) * kWarps + warp;
+        const bool fast = planes_fast(im.w, s3, m3, e);
+        if ((int64_t)im.h * im.w > 0 && t < strips)
+            residual_strip(s3, m3, e, im.h, im.w, im.gf_on != 0, fast, fast && ((uintptr_t)r3 % 16 == 0),
+                           (int)(t / cols) * B.strip_rows, B.strip_rows, (int)(t % cols) * kStripCols, lane, sa, sb,
+                           r3, ghist ? hist : nullptr);
+    }
+    __syncthreads();
+    if (cur >= 0 && ghist)
+        for (int j = threadIdx.x; j < 3 * kNres; j += kThreads)
+            if (hist[j]) atomicAdd(ghist + (int64_t)cur * 3 * kNres + j, hist[j]);
+}
+
 // ====================================================================== decode
+
+// One strip: M = R + M*, repacked with E into RGBE words.
+__device__ __forceinline__ void decode_strip(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ e,
+                                             const int16_t* __restrict__ r3, int h, int w, bool gf, bool fast,
+                                             bool vec, int y0, int rows, int xs, int lane, const float* sa,
+                                             const float* sb, uint32_t* __restrict__ out) {
+    const int64_t n = (int64_t)h * w;
+    const int x0 = xs + 8 * lane;
+    const int y1 = min(y0 + rows, h);
+    GfWindow win{s3, n, h, w, xs, lane, fast, gf};
+    win.start(y0);
+    for (int y = y0; y < y1; ++y) {
+        uint32_t X[3][4];
+        win.row(y, X);
+        if (x0 >= w) continue;
+        uint32_t elo, ehi;
+        load_bytes8(e, w, y, x0, fast, elo, ehi);
+        uint32_t word[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? elo : ehi, i & 3) << 24;
+        const bool v8 = vec && x0 + 8 <= w;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int16_t* row = r3 + c * n + (int64_t)y * w + x0;
+            int r[8];
+            if (v8) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(row));
+                const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    r[2 * k] = (int)(int16_t)(q[k] & 0xFFFFu);
+                    r[2 * k + 1] = (int)(int16_t)(q[k] >> 16);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) r[i] = (x0 + i < w) ? (int)__ldg(row + i) : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int E = (int)(word[i] >> 24);
+                const int M = r[i] + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
+                word[i] |= ((uint32_t)M & 255u) << (8 * c);
+            }
+        }
+        uint32_t* orow = out + (int64_t)y * w + x0;
+        if (v8) {
+            reinterpret_cast<uint4*>(orow)[0] = make_uint4(word[0], word[1], word[2], word[3]);
+            reinterpret_cast<uint4*>(orow)[1] = make_uint4(word[4], word[5], word[6], word[7]);
+        } else {
+            const int cnt = min(8, w - x0);
+            for (int i = 0; i < cnt; ++i) orow[i] = word[i];
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__ s3, const uint8_t* __restrict__ e,
                                                      const int16_t* __restrict__ r3, int h, int w, int gf_on,
@@ -655,62 +810,54 @@ __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__
     __shared__ float sa[3 * kNbin], sb[3 * kNbin];
     load_params(P, sa, sb);
     __syncthreads();
-
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t n = (int64_t)h * w;
-    const bool fast = fast_io != 0, gf = gf_on != 0;
-    const int bands = (h + strip_rows - 1) / strip_rows, cols = (w + kStripCols - 1) / kStripCols;
-    const int64_t tasks = (int64_t)bands * cols;
-    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
-        const int y0 = (int)(t / cols) * strip_rows, xs = (int)(t % cols) * kStripCols;
-        const int x0 = xs + 8 * lane;
-        const int y1 = min(y0 + strip_rows, h);
-        GfWindow win{s3, n, h, w, xs, lane, fast, gf};
-        win.start(y0);
-        for (int y = y0; y < y1; ++y) {
-            uint32_t X[3][4];
-            win.row(y, X);
-            if (x0 < w) {
-                uint32_t elo, ehi;
-                load_bytes8(e, w, y, x0, fast, elo, ehi);
-                uint32_t word[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? elo : ehi, i & 3) << 24;
-                const bool vec = fast && x0 + 8 <= w;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int16_t* row = r3 + c * n + (int64_t)y * w + x0;
-                    int r[8];
-                    if (vec) {
-                        const uint4 v = __ldg(reinterpret_cast<const uint4*>(row));
-                        const uint32_t q[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            r[2 * k] = (int)(int16_t)(q[k] & 0xFFFFu);
-                            r[2 * k + 1] = (int)(int16_t)(q[k] >> 16);
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) r[i] = (x0 + i < w) ? (int)__ldg(row + i) : 0;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int E = (int)(word[i] >> 24);
-                        const int M = r[i] + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
-                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
-                    }
-                }
-                uint32_t* orow = out + (int64_t)y * w + x0;
-                if (vec) {
-                    reinterpret_cast<uint4*>(orow)[0] = make_uint4(word[0], word[1], word[2], word[3]);
-                    reinterpret_cast<uint4*>(orow)[1] = make_uint4(word[4], word[5], word[6], word[7]);
-                } else {
-                    const int cnt = min(8, w - x0);
-                    for (int i = 0; i < cnt; ++i) orow[i] = word[i];
-                }
-            }
+    const int cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)((h + strip_rows - 1) / strip_rows) * cols;
+    const bool vec = fast_io != 0 && ((uintptr_t)r3 % 16 == 0) && ((uintptr_t)out % 16 == 0);
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
+        decode_strip(s3, e, r3, h, w, gf_on != 0, fast_io != 0, vec, (int)(t / cols) * strip_rows, strip_rows,
+                     (int)(t % cols) * kStripCols, lane, sa, sb, out);
+}
+
+__global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int64_t cta_tasks,
+                                                           const uint8_t* __restrict__ s3b,
+                                                           const uint8_t* __restrict__ eb,
+                                                           const int16_t* __restrict__ r3b,
+                                                           const slrme_params* __restrict__ P,
+                                                           uint32_t* __restrict__ outb) {
+    __shared__ float sa[3 * kNbin], sb[3 * kNbin];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
+    int cur = -1;
+    for (int64_t k = k0; k < k1; ++k) {
+        const int i = batch_image_of(B.strip_prefix, B.n, k);
+        if (i != cur) {
+            __syncthreads();
+            load_params(P + i, sa, sb);
+            __syncthreads();
+            cur = i;
         }
+        const BatchImage im = B.img[i];
+        const uint8_t* s3 = s3b + 3 * im.px;
+        const uint8_t* e = eb + im.px;
+        const int16_t* r3 = r3b + 3 * im.px;
+        uint32_t* out = outb + im.px;
+        const int cols = (im.w + kStripCols - 1) / kStripCols;
+        const int64_t strips = (int64_t)((im.h + B.strip_rows - 1) / B.strip_rows) * cols;
+        const int64_t t = (k - B.strip_prefix[i]) * kWarps + warp;
+        const bool fast = (im.w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
+        const bool vec = fast && ((uintptr_t)r3 % 16 == 0) && ((uintptr_t)out % 16 == 0);
+        if ((int64_t)im.h * im.w > 0 && t < strips)
+            decode_strip(s3, e, r3, im.h, im.w, im.gf_on != 0, fast, vec, (int)(t / cols) * B.strip_rows,
+                         B.strip_rows, (int)(t % cols) * kStripCols, lane, sa, sb, out);
     }
+}
+
+int strip_ctas(int64_t cta_tasks, int per_sm) {
+    const int64_t cap = (int64_t)geometry().sms * per_sm;
+    int64_t g = cta_tasks < cap ? cta_tasks : cap;
+    return (int)(g < 1 ? 1 : g);
 }
 
 struct StripLaunch {
@@ -755,7 +902,7 @@ int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, in
 int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
                            const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
-                      ((uintptr_t)e % 8 == 0) && ((uintptr_t)r3 % 16 == 0);
+                      ((uintptr_t)e % 8 == 0);
     const StripLaunch L = strip_launch(h, w, 2);
     k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
     return cuda_status("residual_encode launch");
@@ -763,11 +910,45 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
 
 int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w, int gf_on,
                            const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s) {
-    const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
-                      ((uintptr_t)r3 % 16 == 0) && ((uintptr_t)rgbe_out % 16 == 0);
+    const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
     const StripLaunch L = strip_launch(h, w, 2);
     k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
     return cuda_status("residual_decode launch");
+}
+
+
+// ---------------------------------------------------------------- batch launchers
+
+int launch_fit_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3, const uint8_t* m3,
+                     const uint8_t* e, slrme_params* params, cudaStream_t s) {
+    if (cudaMemsetAsync(B.sums, 0, sizeof(unsigned long long) * kNbin * kNsum * (size_t)B.n, s) != cudaSuccess)
+        return cuda_status("batch fit memset");
+    if (cta_tasks > 0) {
+        k_fit_batch<<<strip_ctas(cta_tasks, ctas_per_sm < 2 ? ctas_per_sm : 2), kThreads, 0, s>>>(B, cta_tasks, s3,
+                                                                                                 m3, e);
+        const int st = cuda_status("batch fit launch");
+        if (st != SLRME_OK) return st;
+    }
+    k_solve_batch<<<B.n, 768, 0, s>>>(B.sums, params);
+    return cuda_status("batch solve launch");
+}
+
+int launch_residual_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3,
+                          const uint8_t* m3, const uint8_t* e, const slrme_params* params, int16_t* r3,
+                          uint32_t* hist, cudaStream_t s) {
+    if (hist && cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 3 * kNres * (size_t)B.n, s) != cudaSuccess)
+        return cuda_status("batch residual memset");
+    if (cta_tasks == 0) return SLRME_OK;
+    k_residual_batch<<<strip_ctas(cta_tasks, ctas_per_sm), kThreads, 0, s>>>(B, cta_tasks, s3, m3, e, params, r3,
+                                                                             hist);
+    return cuda_status("batch residual launch");
+}
+
+int launch_decode_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3, const uint8_t* e,
+                        const int16_t* r3, const slrme_params* params, uint32_t* out, cudaStream_t s) {
+    if (cta_tasks == 0) return SLRME_OK;
+    k_decode_batch<<<strip_ctas(cta_tasks, ctas_per_sm), kThreads, 0, s>>>(B, cta_tasks, s3, e, r3, params, out);
+    return cuda_status("batch decode launch");
 }
 
 }  // namespace slrme

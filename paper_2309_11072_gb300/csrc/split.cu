@@ -61,6 +61,7 @@ __device__ __forceinline__ void block_reduce_add(int64_t s, int64_t c, int64_t* 
             atomicAdd(reinterpret_cast<unsigned long long*>(stats + 1), (unsigned long long)tc);
         }
     }
+    __syncthreads();   // `red` may be reused by the next call
 }
 
 // Vector path: n % 4 == 0, rgbe 16-byte aligned, planes 4-byte aligned.
@@ -130,6 +131,60 @@ __global__ void __launch_bounds__(kThreads) k_split_scalar(const uint32_t* __res
     block_reduce_add(s, c, stats);
 }
 
+
+// Batch: one task per chunk of 4096 words of one image; a CTA works through a
+// contiguous range of chunks and adds each chunk's statistic to its image.
+__global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int64_t chunks,
+                                                          const uint32_t* __restrict__ rgbeb,
+                                                          uint8_t* __restrict__ m3b, uint8_t* __restrict__ eb) {
+    __shared__ int32_t lut[2048];
+    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = kLog2Lut[i];
+    __syncthreads();
+    const int64_t per = (chunks + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, chunks);
+    for (int64_t k = k0; k < k1; ++k) {
+        const int i = batch_image_of(B.split_prefix, B.n, k);
+        const BatchImage im = B.img[i];
+        const int64_t n = (int64_t)im.h * im.w;
+        const int64_t w0 = (k - B.split_prefix[i]) * kSplitChunk, w1 = min(w0 + kSplitChunk, n);
+        const uint32_t* rgbe = rgbeb + im.px;
+        uint8_t* m3 = m3b + 3 * im.px;
+        uint8_t* e = eb + im.px;
+        int64_t s = 0, c = 0;
+        const bool vec = (n % 4 == 0) && ((uintptr_t)rgbe % 16 == 0) && ((uintptr_t)m3 % 4 == 0) &&
+                         ((uintptr_t)e % 4 == 0);
+        if (vec) {
+            const uint4* r4 = reinterpret_cast<const uint4*>(rgbe);
+            uint32_t* mR = reinterpret_cast<uint32_t*>(m3);
+            uint32_t* mG = reinterpret_cast<uint32_t*>(m3 + n);
+            uint32_t* mB = reinterpret_cast<uint32_t*>(m3 + 2 * n);
+            uint32_t* eP = reinterpret_cast<uint32_t*>(e);
+            for (int64_t j = w0 / 4 + threadIdx.x; j < w1 / 4; j += kThreads) {
+                const uint4 v = ld_stream(r4 + j);
+                const uint32_t lo01 = __byte_perm(v.x, v.y, 0x5140), hi01 = __byte_perm(v.x, v.y, 0x7362);
+                const uint32_t lo23 = __byte_perm(v.z, v.w, 0x5140), hi23 = __byte_perm(v.z, v.w, 0x7362);
+                mR[j] = __byte_perm(lo01, lo23, 0x5410);
+                mG[j] = __byte_perm(lo01, lo23, 0x7632);
+                mB[j] = __byte_perm(hi01, hi23, 0x5410);
+                eP[j] = __byte_perm(hi01, hi23, 0x7632);
+                s += (int64_t)log_lum(v.x, lut) + log_lum(v.y, lut) + log_lum(v.z, lut) + log_lum(v.w, lut);
+                c += (v.x >> 24 != 0) + (v.y >> 24 != 0) + (v.z >> 24 != 0) + (v.w >> 24 != 0);
+            }
+        } else {
+            for (int64_t j = w0 + threadIdx.x; j < w1; j += kThreads) {
+                const uint32_t wd = __ldg(rgbe + j);
+                m3[j] = (uint8_t)(wd & 255u);
+                m3[n + j] = (uint8_t)((wd >> 8) & 255u);
+                m3[2 * n + j] = (uint8_t)((wd >> 16) & 255u);
+                e[j] = (uint8_t)(wd >> 24);
+                s += log_lum(wd, lut);
+                c += (wd >> 24) != 0;
+            }
+        }
+        block_reduce_add(s, c, B.lum_stats + 2 * i);
+    }
+}
+
 }  // namespace
 
 int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e, int64_t* lum_stats, cudaStream_t s) {
@@ -151,6 +206,21 @@ int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e, int64
         k_split_scalar<<<(unsigned)blocks, kThreads, 0, s>>>(rgbe, n, m3, e, lum_stats);
     }
     return cuda_status("rgbe_split launch");
+}
+
+}  // namespace slrme
+
+namespace slrme {
+
+int launch_split_batch(const BatchDev& B, int64_t chunks, int ctas_per_sm, const uint32_t* rgbe, uint8_t* m3,
+                       uint8_t* e, cudaStream_t s) {
+    if (cudaMemsetAsync(B.lum_stats, 0, sizeof(int64_t) * 2 * (size_t)B.n, s) != cudaSuccess)
+        return cuda_status("batch split memset");
+    if (chunks == 0) return SLRME_OK;
+    const int64_t cap = (int64_t)geometry().sms * ctas_per_sm;
+    const int64_t g = chunks < cap ? chunks : cap;
+    k_split_batch<<<(unsigned)(g < 1 ? 1 : g), kThreads, 0, s>>>(B, chunks, rgbe, m3, e);
+    return cuda_status("batch split launch");
 }
 
 }  // namespace slrme

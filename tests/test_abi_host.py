@@ -110,3 +110,19 @@ def test_params_layout_roundtrip():
     p = codec.params_to_numpy(torch.from_numpy(codec.params_from_numpy(a, b, n)))
     assert np.array_equal(p["a"], a) and np.array_equal(p["b"], b) and np.array_equal(p["n"], n)
     assert p["n_used"] == int((n > 0).sum())
+
+
+def test_batch_struct_layouts_and_argument_checks():
+    import ctypes as C
+    from paper_2309_11072_gb300 import batch as B
+    assert C.sizeof(B.BatchImage) == 24 and C.sizeof(B.BatchTiles) == 20
+    assert C.sizeof(B.BatchPlan) == 88 and C.sizeof(B.BatchBuffers) == 64
+    L = B._lib()
+    assert L.slrme_batch_workspace_bytes(0) == 0
+    assert L.slrme_batch_workspace_bytes(64) > 64 * 256 * 13 * 8
+    imgs = (B.BatchImage * 2)(B.BatchImage(8, 8, 90, 1, 0), B.BatchImage(8, 8, 0, 1, 0))   # quality 0
+    plan = B.BatchPlan()
+    assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 2, 0x100000, None) == -1
+    assert "quality" in native.last_error()
+    assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 2, 0x100010, None) == -1   # unaligned
+    assert L.slrme_batch_graph_launch(C.addressof(plan), None) == -1
