@@ -149,6 +149,82 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
                     int gf_on, const slrme_params* params, uint32_t* rgbe_out,
                     slrme_stream_t stream);
 
+/* ===================================================================== learned estimator
+ * A small integer CNN that predicts the mantissas from the decoded SDRI and
+ * the exponent plane, a learned alternative to Eq. (8) (the paper's estimator
+ * is the regression; this one is chosen per image only where its residuals
+ * cost fewer bits, and the residual / lossless decoding of Sec. III-C is
+ * unchanged).  Definition:
+ *   input a0 (4 planes, int8): S_c - 128 (c = R, G, B) and
+ *     clamp(E - 137 - J, -128, 127), J the image's tone-mapping key
+ *     (rgbe_key_scale), sent as side information with the network's residuals;
+ *   layers l = 1..4: 3x3 convolution with zero padding, channels
+ *     4 -> 16 -> 16 -> 16 -> 3, acc = b + sum w a (exact integer),
+ *     a' = clamp(floor((acc * m + 2^(shift-1)) / 2^shift), 0, hi) with hi = 127
+ *     for layers 1-3 and 255 for layer 4, whose planes are M^_R, M^_G, M^_B.
+ * Weights are int8 in [-127, 127]; m > 0 and 1 <= shift <= 30 (checked by the
+ * caller); |acc| stays below 2^24. */
+typedef struct slrme_cnn_net {
+    int8_t  w1[16][4][9];      /* [out][in][3x3 tap, row-major] */
+    int8_t  w2[16][16][9];
+    int8_t  w3[16][16][9];
+    int8_t  w4[3][16][9];
+    int32_t b1[16], b2[16], b3[16], b4[3];
+    int32_t m1[16], m2[16], m3[16], m4[3];
+    int32_t shift[4];
+    int32_t reserved;
+} slrme_cnn_net;   /* 6044 bytes, 4-byte aligned (device memory) */
+
+/* Predicted mantissas M^ (uint8 [3][h][w]) of the network for one image. */
+int cnn_infer(const uint8_t* s_dec3, const uint8_t* e, int h, int w, int32_t J, const slrme_cnn_net* net,
+              uint8_t* mhat3, slrme_stream_t stream);
+
+/* Residuals R = M - M^ (int16 [3][h][w]) and, if hist is not NULL, their
+ * histograms (cleared first), as residual_encode does for Eq. (8). */
+int cnn_residual_encode(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w, int32_t J,
+                        const slrme_cnn_net* net, int16_t* r3, uint32_t* hist, slrme_stream_t stream);
+
+/* Decoder of the network's residuals: M = R + M^, repacked with E into RGBE words. */
+int cnn_residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, int h, int w, int32_t J,
+                        const slrme_cnn_net* net, uint32_t* rgbe_out, slrme_stream_t stream);
+
+/* Training of the network (float32, on the device), used to produce its
+ * weights from (decoded SDRI, exponent, mantissa) triples of the codec itself.
+ * Tensors are [B][C][H][W] float32 (B crops of H x W); theta is the flat
+ * parameter vector: for l = 1..4, w_l[out][in][3][3] then b_l[out] (5667
+ * floats).  quant = 1 trains with fake quantisation (weights to int8 steps per
+ * output channel, hidden activations to multiples of 1/8 in [0, 127/8],
+ * straight-through gradients); quant = 0 is the plain ReLU network.  All
+ * reductions run in a fixed order (no float atomics): results are
+ * reproducible bit for bit.  ws: device workspace of
+ * cnn_train_workspace_bytes(B, H, W) bytes shared by forward and backward. */
+size_t cnn_train_workspace_bytes(int B, int H, int W);
+
+/* Forward pass: x [B][4][H][W] -> out [B][3][H][W]; keeps activations in ws. */
+int cnn_train_forward(const float* theta, const float* x, int B, int H, int W, int quant, float* ws, float* out,
+                      slrme_stream_t stream);
+
+/* Backward pass after cnn_train_forward on the same ws: grad (5667 floats) of
+ * the loss whose gradient w.r.t. out is dout [B][3][H][W]. */
+int cnn_train_backward(const float* x, const float* dout, int B, int H, int W, int quant, float* ws, float* grad,
+                       slrme_stream_t stream);
+
+/* Mean absolute error of out against target (n values): *loss (device float)
+ * and dout = sign(out - target) / n.  ws: ceil(n / 256) floats. */
+int cnn_loss_l1(const float* out, const float* target, int64_t n, float* dout, float* loss, float* ws,
+                slrme_stream_t stream);
+
+/* One bias-corrected Adam update of theta (n values) at step >= 1. */
+int cnn_adam_step(float* theta, const float* grad, float* m, float* v, int n, float lr, float b1, float b2, float eps,
+                  int step, slrme_stream_t stream);
+
+/* Training crops from coded images: crops[6 k ..] = (pixel offset of the
+ * image's planes as in the batch layout, h, w, y0, x0, J) for crop k;
+ * writes x[k] = (S - 128, clamp(E - 137 - J, -128, 127)) and target[k] = M,
+ * as floats of CH x CW. */
+int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const uint8_t* m3, const int64_t* crops, int ncrops, int CH,
+                     int CW, float* x, float* target, slrme_stream_t stream);
+
 /* ===================================================================== batch form
  * Many images of uneven sizes coded together: one persistent launch per stage
  * (split, base round trip, fit + solve, residual; decode), tiles chosen by an
@@ -227,6 +303,10 @@ int slrme_batch_decode(const slrme_batch_plan* plan, const slrme_batch_buffers* 
  * time) and keeps the fastest; synchronous, overwrites the buffers' outputs.
  * The coded results never depend on the tiles. */
 int slrme_batch_autotune(slrme_batch_plan* plan, const slrme_batch_buffers* bufs, int reps, slrme_stream_t stream);
+
+/* Copies the per-image log-average statistics of the last encode (int64
+ * [n_images][2], as rgbe_split defines them) to host memory; synchronous. */
+int slrme_batch_lum_stats(const slrme_batch_plan* plan, int64_t* stats_host, slrme_stream_t stream);
 
 /* Captures encode + decode on `stream` (a created stream, not the legacy
  * default stream) into a CUDA graph bound to these buffers and instantiates

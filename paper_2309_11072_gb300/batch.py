@@ -54,6 +54,7 @@ _BATCH_SIGS = {
     "slrme_batch_graph_build": [_vp, _vp, _vp],
     "slrme_batch_graph_launch": [_vp, _vp],
     "slrme_batch_graph_destroy": [_vp],
+    "slrme_batch_lum_stats": [_vp, _vp, _vp],
 }
 
 
@@ -166,6 +167,16 @@ class BatchCodec:
 
     def graph_launch(self, stream=None) -> None:
         _call("slrme_batch_graph_launch", ctypes.addressof(self.plan), self._stream(stream))
+
+    def lum_stats(self) -> np.ndarray:
+        """Per-image log-average statistics of the last encode (int64 [n, 2])."""
+        out = np.zeros((self.n, 2), np.int64)
+        _call("slrme_batch_lum_stats", ctypes.addressof(self.plan), out.ctypes.data, self._stream())
+        return out
+
+    def keys(self) -> list:
+        """Tone-mapping key J of every image (from the last encode)."""
+        return [native.rgbe_key_scale(st)[0] for st in self.lum_stats()]
 
     def close(self) -> None:
         if self.plan.graph:

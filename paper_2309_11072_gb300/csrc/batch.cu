@@ -301,6 +301,20 @@ done:
     return st;
 }
 
+int slrme_batch_lum_stats(const slrme_batch_plan* plan, int64_t* stats_host, slrme_stream_t stream) {
+    if (!plan || !plan->workspace || !stats_host) {
+        set_error("slrme_batch_lum_stats: null pointer");
+        return SLRME_EINVAL;
+    }
+    const BatchDev B = device_view(plan);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(stats_host, B.lum_stats, sizeof(int64_t) * 2 * (size_t)plan->n_images, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return cuda_status("slrme_batch_lum_stats");
+    return SLRME_OK;
+}
+
 // Captures encode + decode of the batch on `stream` (which must not be the
 // legacy default stream) into a CUDA graph and instantiates it.
 int slrme_batch_graph_build(slrme_batch_plan* plan, const slrme_batch_buffers* bufs, slrme_stream_t stream) {
