@@ -58,7 +58,7 @@ def test_cnn_infer_matches_integer_oracle(h, w, kind):
     got = _host(mh, np.uint8).reshape(3, h, w)
     assert np.array_equal(got, ref)
     if kind == "mild" and h * w > 100:
-        assert len(np.unique(ref)) > 20          # the test exercises unsaturated values
+        assert len(np.unique(ref)) > 8           # the test exercises unsaturated values
 
 
 @pytest.mark.parametrize("h,w", [(9, 17), (48, 80), (130, 70)])
