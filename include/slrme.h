@@ -161,7 +161,8 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
  *   layers l = 1..4: 3x3 convolution with zero padding, channels
  *     4 -> 16 -> 16 -> 16 -> 3, acc = b + sum w a (exact integer),
  *     a' = clamp(floor((acc * m + 2^(shift-1)) / 2^shift), 0, hi) with hi = 127
- *     for layers 1-3 and 255 for layer 4, whose planes are M^_R, M^_G, M^_B.
+ *     for layers 1-3 and 255 for layer 4, whose planes y_R, y_G, y_B correct the
+ *     regression: M^_c = clamp(M*_c + y_c - 128, 0, 255), M* from Eq. (8).
  * Weights are int8 in [-127, 127]; m > 0 and 1 <= shift <= 30 (checked by the
  * caller); |acc| stays below 2^24. */
 typedef struct slrme_cnn_net {
@@ -175,18 +176,21 @@ typedef struct slrme_cnn_net {
     int32_t reserved;
 } slrme_cnn_net;   /* 6044 bytes, 4-byte aligned (device memory) */
 
-/* Predicted mantissas M^ (uint8 [3][h][w]) of the network for one image. */
+/* Output planes y (uint8 [3][h][w]) of the network for one image. */
 int cnn_infer(const uint8_t* s_dec3, const uint8_t* e, int h, int w, int32_t J, const slrme_cnn_net* net,
               uint8_t* mhat3, slrme_stream_t stream);
 
-/* Residuals R = M - M^ (int16 [3][h][w]) and, if hist is not NULL, their
- * histograms (cleared first), as residual_encode does for Eq. (8). */
+/* Residuals R = M - M^ (int16 [3][h][w]) of the refined estimate M^ (the
+ * image's regression `params` with restoration gf_on, corrected by the
+ * network) and, if hist is not NULL, their histograms (cleared first). */
 int cnn_residual_encode(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w, int32_t J,
-                        const slrme_cnn_net* net, int16_t* r3, uint32_t* hist, slrme_stream_t stream);
+                        const slrme_cnn_net* net, const slrme_params* params, int gf_on, int16_t* r3,
+                        uint32_t* hist, slrme_stream_t stream);
 
-/* Decoder of the network's residuals: M = R + M^, repacked with E into RGBE words. */
+/* Decoder of those residuals: M = R + M^, repacked with E into RGBE words. */
 int cnn_residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, int h, int w, int32_t J,
-                        const slrme_cnn_net* net, uint32_t* rgbe_out, slrme_stream_t stream);
+                        const slrme_cnn_net* net, const slrme_params* params, int gf_on, uint32_t* rgbe_out,
+                        slrme_stream_t stream);
 
 /* Training of the network (float32, on the device), used to produce its
  * weights from (decoded SDRI, exponent, mantissa) triples of the codec itself.
@@ -220,9 +224,9 @@ int cnn_adam_step(float* theta, const float* grad, float* m, float* v, int n, fl
 
 /* Training crops from coded images: crops[6 k ..] = (pixel offset of the
  * image's planes as in the batch layout, h, w, y0, x0, J) for crop k;
- * writes x[k] = (S - 128, clamp(E - 137 - J, -128, 127)) and target[k] = M,
- * as floats of CH x CW. */
-int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const uint8_t* m3, const int64_t* crops, int ncrops, int CH,
+ * writes x[k] = (S - 128, clamp(E - 137 - J, -128, 127)) and target[k] =
+ * R + 128 with R = M - M* the regression's residual, as floats of CH x CW. */
+int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const int16_t* r3, const int64_t* crops, int ncrops, int CH,
                      int CW, float* x, float* target, slrme_stream_t stream);
 
 /* ===================================================================== batch form

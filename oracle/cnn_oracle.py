@@ -12,18 +12,22 @@ residuals cost fewer bits, with the same residual / lossless decoding
 Input (4 int8 planes, per pixel):  S_c - 128 (c = R, G, B) and
     clamp(E - 137 - J, -128, 127), the exponent relative to the image's
     tone-mapping key J (Sec. II-B's operator uses the same d = E - 137 - J).
+Output: three planes y_c in [0, 255] that correct the regression's estimate
+    (Eq. 8): M^_c = clamp(M*_c + y_c - 128, 0, 255).  (READING: the network
+    refines the regression rather than replacing it; a network that knows
+    only the integer part of the key cannot place the mantissas alone.)
 Layers l = 1..4: 3x3 convolution, zero padding, stride 1, channels
     4 -> 16 -> 16 -> 16 -> 3; weights int8 in [-127, 127], bias int32,
     per-output-channel multiplier int32 and per-layer shift.
     acc = bias + sum w * a  (exact integer);
     y   = clamp(floor(((acc) * mult + 2^(shift-1)) / 2^shift), lo, hi)
     with [lo, hi] = [0, 127] for layers 1-3 (ReLU) and [0, 255] for layer 4,
-    whose three planes are the predicted mantissas M^_R, M^_G, M^_B.
+    whose three planes are the corrections y_R, y_G, y_B.
 
 Training (float): the same network with fake quantisation (weights per
 output channel to int8 steps, hidden activations to multiples of SCALE_A in
 [0, 127 SCALE_A]; straight-through gradients inside the range) and an L1
-loss on M^ - M.
+loss between y and the regression's residual plus 128, (M - M*) + 128.
 """
 from __future__ import annotations
 
@@ -69,12 +73,17 @@ def requant(acc: np.ndarray, mult: np.ndarray, shift: int, lo: int, hi: int) -> 
 
 
 def infer(s3: np.ndarray, e: np.ndarray, J: int, net: dict) -> np.ndarray:
-    """Predicted mantissas M^ (uint8 [3, h, w]) of the integer network."""
+    """Output planes y (uint8 [3, h, w]) of the integer network."""
     a = cnn_input(s3, e, J)
     for l in range(4):
         acc = conv3x3_int(a, net["w"][l]) + np.asarray(net["b"][l], np.int64).reshape(-1, 1, 1)
         a = requant(acc, net["m"][l], int(net["sh"][l]), 0, 127 if l < 3 else 255)
     return a.astype(np.uint8)
+
+
+def refine(mstar3: np.ndarray, y3: np.ndarray) -> np.ndarray:
+    """M^ = clamp(M* + y - 128, 0, 255)."""
+    return np.clip(np.asarray(mstar3, np.int64) + np.asarray(y3, np.int64) - 128, 0, 255).astype(np.uint8)
 
 
 def residual(m3: np.ndarray, mhat3: np.ndarray):

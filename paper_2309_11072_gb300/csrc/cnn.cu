@@ -28,7 +28,7 @@ constexpr int H3 = TH + 2, W3 = TW + 2;
 constexpr int kThreadsC = 256, kWarpsC = 8;
 constexpr int kBufAPx = H0 * W0;                // holds the input and layer-2 activations
 constexpr int kBufBPx = H1 * W1;                // holds layer-1 and layer-3 activations
-constexpr int kSmemBytes = (kBufAPx + kBufBPx) * 32 + 3 * TH * TW + 3 * kNres * 4;
+constexpr int kSmemBytes = (kBufAPx + kBufBPx) * 32 + 3 * TH * TW + 3 * kNres * 4 + 2 * 3 * kNbin * 4;
 
 enum Mode { kInfer = 0, kEncode = 1, kDecode = 2 };
 
@@ -154,8 +154,25 @@ struct CnnArgs {
     uint32_t* hist;        // encode: histograms (may be null)
     uint32_t* rgbe_out;    // decode: words
     const slrme_cnn_net* net;
-    int h, w, J, mode;
+    const slrme_params* params;   // encode / decode: the regression being refined
+    int h, w, J, mode, gf_on;
 };
+
+// x = 16 S* (3x3 binomial, edge replicated) or 16 S at one pixel of one plane.
+__device__ __forceinline__ int gf_at(const uint8_t* __restrict__ S, int h, int w, int y, int x, bool gf) {
+    if (!gf) return 16 * (int)S[(int64_t)y * w + x];
+    int acc = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = min(max(y + dy, 0), h - 1);
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int xx = min(max(x + dx, 0), w - 1);
+            acc += (2 - (dy != 0)) * (2 - (dx != 0)) * (int)S[(int64_t)yy * w + xx];
+        }
+    }
+    return acc;
+}
 
 __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
     extern __shared__ __align__(128) char smem[];
@@ -163,12 +180,19 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
     char* bufB = smem + kBufAPx * 32;
     uint8_t* mh = reinterpret_cast<uint8_t*>(bufB + kBufBPx * 32);
     uint32_t* hist = reinterpret_cast<uint32_t*>(mh + 3 * TH * TW);
+    float* pa = reinterpret_cast<float*>(hist + 3 * kNres);      // regression slopes [3][256]
+    float* pb = pa + 3 * kNbin;                                   // intercepts [3][256]
     const uint32_t sA = (uint32_t)__cvta_generic_to_shared(bufA), sB = (uint32_t)__cvta_generic_to_shared(bufB);
     const int h = A.h, w = A.w;
     const int64_t n = (int64_t)h * w;
     const bool want_hist = A.mode == kEncode && A.hist;
     if (want_hist)
         for (int i = threadIdx.x; i < 3 * kNres; i += kThreadsC) hist[i] = 0u;
+    if (A.mode != kInfer)
+        for (int i = threadIdx.x; i < 3 * kNbin; i += kThreadsC) {
+            pa[i] = (&A.params->a[0][0])[i];
+            pb[i] = (&A.params->b[0][0])[i];
+        }
 
     const slrme_cnn_net* N = A.net;
     const LayerRef L1{&N->w1[0][0][0], N->b1, N->m1, 4, 16, N->shift[0], 127};
@@ -209,26 +233,34 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
             const int gy = oy + p / TW, gx = ox + p % TW;
             if (gy >= h || gx >= w) continue;
             const int64_t o = (int64_t)gy * w + gx;
-            const int mr = mh[p], mg = mh[TH * TW + p], mb = mh[2 * TH * TW + p];
+            int y3[3] = {mh[p], mh[TH * TW + p], mh[2 * TH * TW + p]};
             if (A.mode == kInfer) {
-                A.mhat3[o] = (uint8_t)mr;
-                A.mhat3[n + o] = (uint8_t)mg;
-                A.mhat3[2 * n + o] = (uint8_t)mb;
-            } else if (A.mode == kEncode) {
-                const int r0 = (int)A.m3[o] - mr, r1 = (int)A.m3[n + o] - mg, r2 = (int)A.m3[2 * n + o] - mb;
-                A.r3_out[o] = (int16_t)r0;
-                A.r3_out[n + o] = (int16_t)r1;
-                A.r3_out[2 * n + o] = (int16_t)r2;
-                if (want_hist) {
-                    atomicAdd(&hist[r0 + 255], 1u);
-                    atomicAdd(&hist[kNres + r1 + 255], 1u);
-                    atomicAdd(&hist[2 * kNres + r2 + 255], 1u);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) A.mhat3[c * n + o] = (uint8_t)y3[c];
+                continue;
+            }
+            // refined estimate: M^ = clamp(M* + y - 128, 0, 255), M* from Eq. (8)
+            const int E = A.e[o];
+            int mhat[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int ms = predict(pa[c * kNbin + E], pb[c * kNbin + E], gf_at(A.s3 + c * n, h, w, gy, gx,
+                                                                                    A.gf_on != 0));
+                const int v = ms + y3[c] - 128;
+                mhat[c] = v < 0 ? 0 : (v > 255 ? 255 : v);
+            }
+            if (A.mode == kEncode) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int r = (int)A.m3[c * n + o] - mhat[c];
+                    A.r3_out[c * n + o] = (int16_t)r;
+                    if (want_hist) atomicAdd(&hist[c * kNres + r + 255], 1u);
                 }
             } else {
-                const uint32_t R = (uint32_t)((int)A.r3[o] + mr) & 255u;
-                const uint32_t G = (uint32_t)((int)A.r3[n + o] + mg) & 255u;
-                const uint32_t B = (uint32_t)((int)A.r3[2 * n + o] + mb) & 255u;
-                A.rgbe_out[o] = R | (G << 8) | (B << 16) | ((uint32_t)A.e[o] << 24);
+                uint32_t wd = (uint32_t)E << 24;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) wd |= ((uint32_t)((int)A.r3[c * n + o] + mhat[c]) & 255u) << (8 * c);
+                A.rgbe_out[o] = wd;
             }
         }
     }
@@ -276,14 +308,15 @@ int cnn_infer(const uint8_t* s_dec3, const uint8_t* e, int h, int w, int32_t J, 
         set_error("cnn_infer: null pointer");
         return SLRME_EINVAL;
     }
-    CnnArgs A{s_dec3, e, nullptr, nullptr, mhat3, nullptr, nullptr, nullptr, net, h, w, J, kInfer};
+    CnnArgs A{s_dec3, e, nullptr, nullptr, mhat3, nullptr, nullptr, nullptr, net, nullptr, h, w, J, kInfer, 0};
     return launch_cnn(A, (cudaStream_t)stream);
 }
 
 int cnn_residual_encode(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w, int32_t J,
-                        const slrme_cnn_net* net, int16_t* r3, uint32_t* hist, slrme_stream_t stream) {
+                        const slrme_cnn_net* net, const slrme_params* params, int gf_on, int16_t* r3, uint32_t* hist,
+                        slrme_stream_t stream) {
     if (h < 0 || w < 0 || (int64_t)h * w >= ((int64_t)1 << 31) || !net_ok(net) || (uintptr_t)r3 % 2 ||
-        (uintptr_t)hist % 4) {
+        (uintptr_t)hist % 4 || !params || (uintptr_t)params % 4 || (gf_on != 0 && gf_on != 1)) {
         set_error("cnn_residual_encode: bad size, alignment or network pointer");
         return SLRME_EINVAL;
     }
@@ -295,14 +328,15 @@ int cnn_residual_encode(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t*
         set_error("cnn_residual_encode: null pointer");
         return SLRME_EINVAL;
     }
-    CnnArgs A{s_dec3, e, m3, nullptr, nullptr, r3, hist, nullptr, net, h, w, J, kEncode};
+    CnnArgs A{s_dec3, e, m3, nullptr, nullptr, r3, hist, nullptr, net, params, h, w, J, kEncode, gf_on};
     return launch_cnn(A, s);
 }
 
 int cnn_residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, int h, int w, int32_t J,
-                        const slrme_cnn_net* net, uint32_t* rgbe_out, slrme_stream_t stream) {
+                        const slrme_cnn_net* net, const slrme_params* params, int gf_on, uint32_t* rgbe_out,
+                        slrme_stream_t stream) {
     if (h < 0 || w < 0 || (int64_t)h * w >= ((int64_t)1 << 31) || !net_ok(net) || (uintptr_t)r3 % 2 ||
-        (uintptr_t)rgbe_out % 4) {
+        (uintptr_t)rgbe_out % 4 || !params || (uintptr_t)params % 4 || (gf_on != 0 && gf_on != 1)) {
         set_error("cnn_residual_decode: bad size, alignment or network pointer");
         return SLRME_EINVAL;
     }
@@ -311,7 +345,7 @@ int cnn_residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* 
         set_error("cnn_residual_decode: null pointer");
         return SLRME_EINVAL;
     }
-    CnnArgs A{s_dec3, e, nullptr, r3, nullptr, nullptr, nullptr, rgbe_out, net, h, w, J, kDecode};
+    CnnArgs A{s_dec3, e, nullptr, r3, nullptr, nullptr, nullptr, rgbe_out, net, params, h, w, J, kDecode, gf_on};
     return launch_cnn(A, (cudaStream_t)stream);
 }
 

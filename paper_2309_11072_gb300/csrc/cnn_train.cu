@@ -236,9 +236,9 @@ __global__ void k_adam(float* __restrict__ theta, const float* __restrict__ grad
 
 // Training crops: for crop k with origin (y0, x0) in image planes at pixel
 // offset px (h x w, key J), x[k] = (S - 128, clamp(E - 137 - J)) and
-// t[k] = M, as floats, CH x CW each.
+// t[k] = R + 128 (the regression's residual, centred), as floats, CH x CW each.
 __global__ void k_gather(const uint8_t* __restrict__ s3b, const uint8_t* __restrict__ eb,
-                         const uint8_t* __restrict__ m3b, const int64_t* __restrict__ crops, int ncrops, int CH,
+                         const int16_t* __restrict__ r3b, const int64_t* __restrict__ crops, int ncrops, int CH,
                          int CW, float* __restrict__ x, float* __restrict__ t) {
     const int64_t hw = (int64_t)CH * CW;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,14 +249,14 @@ __global__ void k_gather(const uint8_t* __restrict__ s3b, const uint8_t* __restr
     const int64_t px = c[0], h = c[1], w = c[2];
     const int64_t n = h * w, o = (c[3] + yy) * w + c[4] + xx;
     const uint8_t* s3 = s3b + 3 * px;
-    const uint8_t* m3 = m3b + 3 * px;
+    const int16_t* r3 = r3b + 3 * px;
     int d = (int)eb[px + o] - 137 - (int)c[5];
     d = d < -128 ? -128 : (d > 127 ? 127 : d);
     float* xk = x + (int64_t)k * 4 * hw + (int64_t)yy * CW + xx;
     float* tk = t + (int64_t)k * 3 * hw + (int64_t)yy * CW + xx;
     for (int ch = 0; ch < 3; ++ch) {
         xk[ch * hw] = (float)((int)s3[ch * n + o] - 128);
-        tk[ch * hw] = (float)m3[ch * n + o];
+        tk[ch * hw] = (float)((int)r3[ch * n + o] + 128);
     }
     xk[3 * hw] = (float)d;
 }
@@ -376,14 +376,14 @@ int cnn_adam_step(float* theta, const float* grad, float* m, float* v, int n, fl
     return cuda_status("cnn_adam_step launch");
 }
 
-int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const uint8_t* m3, const int64_t* crops, int ncrops, int CH,
+int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const int16_t* r3, const int64_t* crops, int ncrops, int CH,
                      int CW, float* x, float* target, slrme_stream_t stream) {
-    if (!s3 || !e || !m3 || !crops || !x || !target || ncrops < 1 || CH < 1 || CW < 1 ||
+    if (!s3 || !e || !r3 || (uintptr_t)r3 % 2 || !crops || !x || !target || ncrops < 1 || CH < 1 || CW < 1 ||
         (int64_t)ncrops * CH * CW >= ((int64_t)1 << 31)) {
         set_error("cnn_gather_crops: bad arguments");
         return SLRME_EINVAL;
     }
-    k_gather<<<blocks_for((int64_t)ncrops * CH * CW), kThreadsT, 0, (cudaStream_t)stream>>>(s3, e, m3, crops, ncrops,
+    k_gather<<<blocks_for((int64_t)ncrops * CH * CW), kThreadsT, 0, (cudaStream_t)stream>>>(s3, e, r3, crops, ncrops,
                                                                                            CH, CW, x, target);
     return cuda_status("cnn_gather_crops launch");
 }

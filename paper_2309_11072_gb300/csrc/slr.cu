@@ -162,15 +162,6 @@ __device__ __forceinline__ void load_bytes8(const uint8_t* __restrict__ plane, i
     }
 }
 
-// Eq. (8): round(a x + b) clipped to [0, 255]; float32 multiply then add,
-// half away from zero.  NaN and t <= 0 give 0.
-__device__ __forceinline__ int predict(float a, float b, int x) {
-    float t = __fadd_rn(__fmul_rn(a, __int2float_rn(x)), b);
-    t = fminf(fmaxf(t, 0.0f), 255.0f);
-    const int r = __float2int_rz(t);
-    return r + (__fsub_rn(t, __int2float_rn(r)) >= 0.5f ? 1 : 0);
-}
-
 // ====================================================================== fit
 
 struct RunAcc {

@@ -30,8 +30,10 @@ _I32_OFF = 5616                                         # b1, b2, b3, b4, m1, ..
 _vp = ctypes.c_void_p
 _SIGS = {
     "cnn_infer": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _vp, _vp, _vp],
-    "cnn_residual_encode": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _vp, _vp, _vp, _vp],
-    "cnn_residual_decode": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _vp, _vp, _vp],
+    "cnn_residual_encode": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _vp, _vp, ctypes.c_int, _vp,
+                            _vp, _vp],
+    "cnn_residual_decode": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _vp, _vp, ctypes.c_int, _vp,
+                            _vp],
     "cnn_train_forward": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "cnn_train_backward": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "cnn_loss_l1": [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp],
@@ -129,14 +131,14 @@ def cnn_infer(s3, e, h, w, J, net_dev, mhat3, stream=None):
     _call("cnn_infer", _ptr(s3), _ptr(e), h, w, int(J), _ptr(net_dev), _ptr(mhat3), _stream(stream))
 
 
-def cnn_residual_encode(s3, m3, e, h, w, J, net_dev, r3, hist=None, stream=None):
-    _call("cnn_residual_encode", _ptr(s3), _ptr(m3), _ptr(e), h, w, int(J), _ptr(net_dev), _ptr(r3), _ptr(hist),
-          _stream(stream))
+def cnn_residual_encode(s3, m3, e, h, w, J, net_dev, params, gf_on, r3, hist=None, stream=None):
+    _call("cnn_residual_encode", _ptr(s3), _ptr(m3), _ptr(e), h, w, int(J), _ptr(net_dev), _ptr(params),
+          int(gf_on), _ptr(r3), _ptr(hist), _stream(stream))
 
 
-def cnn_residual_decode(s3, e, r3, h, w, J, net_dev, out, stream=None):
-    _call("cnn_residual_decode", _ptr(s3), _ptr(e), _ptr(r3), h, w, int(J), _ptr(net_dev), _ptr(out),
-          _stream(stream))
+def cnn_residual_decode(s3, e, r3, h, w, J, net_dev, params, gf_on, out, stream=None):
+    _call("cnn_residual_decode", _ptr(s3), _ptr(e), _ptr(r3), h, w, int(J), _ptr(net_dev), _ptr(params),
+          int(gf_on), _ptr(out), _stream(stream))
 
 
 # ------------------------------------------------------------------ training
@@ -155,6 +157,8 @@ class Trainer:
             ci, co = CHANNELS[l], CHANNELS[l + 1]
             fan_in = ci * 9
             scale = math.sqrt(2.0 / fan_in) if l < 3 else math.sqrt(1.0 / fan_in)
+            if l == 0:
+                scale /= 64.0     # raw int8 inputs span +-128: keep first activations inside [0, 127/8]
             theta[o:o + co * ci * 9] = rng.normal(0, scale, co * ci * 9)
             o += co * ci * 9
             theta[o:o + co] = 1.0 if l < 3 else 128.0        # hidden units start active; output near mid-range
@@ -196,9 +200,10 @@ class Trainer:
         _call("cnn_adam_step", _ptr(self.theta), _ptr(self.grad), _ptr(self.m), _ptr(self.v), N_PARAMS,
               float(self.lr), 0.9, 0.999, 1e-8, self.step_no, _stream(stream))
 
-    def step(self, crops_dev, s3, e, m3, stream=None):
-        """One training step on the crops (int64 [B, 6] on the device)."""
-        _call("cnn_gather_crops", _ptr(s3), _ptr(e), _ptr(m3), _ptr(crops_dev), self.B, self.H, self.W,
+    def step(self, crops_dev, s3, e, r3, stream=None):
+        """One training step on the crops (int64 [B, 6] on the device) of coded
+        images: decoded SDRI s3, exponents e and the regression's residuals r3."""
+        _call("cnn_gather_crops", _ptr(s3), _ptr(e), _ptr(r3), _ptr(crops_dev), self.B, self.H, self.W,
               _ptr(self.x), _ptr(self.t), _stream(stream))
         self.forward(stream=stream)
         self.loss_l1(stream=stream)
@@ -239,7 +244,7 @@ def train(bc, keys: Sequence[int], steps: int, B: int = 32, H: int = 64, W: int 
     crops = torch.zeros((B, 6), dtype=torch.int64, device=bc.device)
     for k in range(steps):
         crops.copy_(torch.from_numpy(crop_table(bc, keys, B, H, W, rng)))
-        tr.step(crops, bc.s3, bc.e, bc.m3)
+        tr.step(crops, bc.s3, bc.e, bc.r3)
         if log_every and (k == 0 or (k + 1) % log_every == 0):
             loss = float(tr.loss.item())
             if history is not None:
@@ -267,8 +272,10 @@ def rate(hist3: np.ndarray, side_bits: float, n_px: int) -> float:
 
 def pick_image(hist_slr: np.ndarray, n_used: int, hist_cnn: np.ndarray, n_px: int) -> Pick:
     """The 1-bit per-image choice: the network only where its residuals cost
-    fewer bits than the regression's (side information included; the flag
-    itself costs one bit either way)."""
-    b_slr = rate(hist_slr, 256 + 3 * 64 * n_used + 1, n_px)
-    b_cnn = rate(hist_cnn, 32 + 1, n_px)          # the key J travels with the network's residuals
+    fewer bits than the regression's.  Both carry the regression's parameters
+    (the network refines that estimate); the network's residuals also carry
+    the key J; the flag costs one bit either way."""
+    side = 256 + 3 * 64 * n_used + 1
+    b_slr = rate(hist_slr, side, n_px)
+    b_cnn = rate(hist_cnn, side + 32, n_px)
     return Pick(b_slr, b_cnn, b_cnn < b_slr)

@@ -91,9 +91,9 @@ def main(argv=None):
             out = torch.empty(h * w, dtype=torch.int32, device=dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            Lr.cnn_residual_encode(L["s3"], L["m3"], L["e"], h, w, tkeys[i], net_dev, r3, hist)
+            Lr.cnn_residual_encode(L["s3"], L["m3"], L["e"], h, w, tkeys[i], net_dev, L["params"], 1, r3, hist)
             e1.record()
-            Lr.cnn_residual_decode(L["s3"], L["e"], r3, h, w, tkeys[i], net_dev, out)
+            Lr.cnn_residual_decode(L["s3"], L["e"], r3, h, w, tkeys[i], net_dev, L["params"], 1, out)
             torch.cuda.synchronize()
             cnn_ms += e0.elapsed_time(e1)
             cnn_px += h * w

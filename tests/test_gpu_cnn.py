@@ -62,20 +62,28 @@ def test_cnn_infer_matches_integer_oracle(h, w, kind):
 
 
 @pytest.mark.parametrize("h,w", [(9, 17), (48, 80), (130, 70)])
-def test_cnn_residual_roundtrip(h, w):
+@pytest.mark.parametrize("gf_on", [0, 1])
+def test_cnn_residual_roundtrip(h, w, gf_on):
+    from oracle import oracle as O
+    from paper_2309_11072_gb300 import codec
     img = synth.make_rgbe(h, w, seed=h + w, lo=-3.0, hi=5.0)
     m3 = np.stack([(img >> (8 * c)) & 255 for c in range(3)]).astype(np.uint8)
     e = (img >> 24).astype(np.uint8)
     s3, _ = _inputs(h, w, seed=7)
+    rng = np.random.default_rng(h * w)
+    a = rng.uniform(-0.1, 0.1, (3, 256)).astype(np.float32)
+    b = rng.uniform(0, 255, (3, 256)).astype(np.float32)
+    params = _dev(codec.params_from_numpy(a, b), torch.int32)
     net = _mild_net(3)
     nd = Lr.upload_net(net)
     r3 = torch.empty(3 * h * w, dtype=torch.int16, device=DEV)
     hist = torch.empty(3 * 511, dtype=torch.int32, device=DEV)
-    Lr.cnn_residual_encode(_dev(s3), _dev(m3), _dev(e), h, w, 4, nd, r3, hist)
+    Lr.cnn_residual_encode(_dev(s3), _dev(m3), _dev(e), h, w, 4, nd, params, gf_on, r3, hist)
     out = torch.empty(h * w, dtype=torch.int32, device=DEV)
-    Lr.cnn_residual_decode(_dev(s3), _dev(e), r3, h, w, 4, nd, out)
+    Lr.cnn_residual_decode(_dev(s3), _dev(e), r3, h, w, 4, nd, params, gf_on, out)
     torch.cuda.synchronize()
-    r_ref, h_ref = C.residual(m3, C.infer(s3, e, 4, net))
+    mhat = C.refine(O.predict(O.gf(s3, bool(gf_on)), e, a, b), C.infer(s3, e, 4, net))
+    r_ref, h_ref = C.residual(m3, mhat)
     assert np.array_equal(_host(r3, np.int16).reshape(3, h, w), r_ref)
     assert np.array_equal(_host(hist, np.uint32).reshape(3, 511), h_ref)
     assert np.array_equal(_host(out, np.uint32).reshape(h, w), img)
@@ -162,7 +170,7 @@ def test_training_is_reproducible_and_resumable():
         tab = Lr.crop_table(bc, keys, 4, 32, 32, rng)
         if k >= 3:
             crops.copy_(torch.from_numpy(tab))
-            c.step(crops, bc.s3, bc.e, bc.m3)
+            c.step(crops, bc.s3, bc.e, bc.r3)
     assert torch.equal(a.theta, c.theta)
 
 
@@ -170,7 +178,7 @@ def test_learned_estimator_pick_is_lossless_and_never_worse():
     train_bc, _, train_keys = _coded_set(12, 128, 41000)
     hist_loss = []
     tr = Lr.train(train_bc, train_keys, steps=150, B=16, H=48, W=48, seed=5, log_every=50, history=hist_loss)
-    assert hist_loss[-1][1] < 0.7 * hist_loss[0][1]          # training lowers the L1 loss
+    assert hist_loss[-1][1] < 0.9 * hist_loss[0][1]          # training lowers the L1 loss
     net = Lr.upload_net(Lr.export_int_net(tr.theta.cpu().numpy()))
     test_bc, test_imgs, test_keys = _coded_set(3, 160, 42000)
     for i, img in enumerate(test_imgs):
@@ -178,9 +186,9 @@ def test_learned_estimator_pick_is_lossless_and_never_worse():
         h, w = img.shape
         r3 = torch.empty(3 * h * w, dtype=torch.int16, device=DEV)
         hist = torch.empty(3 * 511, dtype=torch.int32, device=DEV)
-        Lr.cnn_residual_encode(L["s3"], L["m3"], L["e"], h, w, test_keys[i], net, r3, hist)
+        Lr.cnn_residual_encode(L["s3"], L["m3"], L["e"], h, w, test_keys[i], net, L["params"], 1, r3, hist)
         out = torch.empty(h * w, dtype=torch.int32, device=DEV)
-        Lr.cnn_residual_decode(L["s3"], L["e"], r3, h, w, test_keys[i], net, out)
+        Lr.cnn_residual_decode(L["s3"], L["e"], r3, h, w, test_keys[i], net, L["params"], 1, out)
         torch.cuda.synchronize()
         assert np.array_equal(_host(out, np.uint32).reshape(h, w), img)
         pk = Lr.pick_image(_host(L["hist"], np.uint32).reshape(3, 511), test_bc.image_params(i)["n_used"],

@@ -136,3 +136,22 @@ def test_fake_quantisers():
     a, mask = C.fq_act(z)
     assert a.tolist() == [0.0, 0.0, 0.0, 0.125, 3.0, 15.875, 15.875, 15.875]
     assert mask.tolist() == [0, 0, 1, 1, 1, 1, 0, 0]
+
+
+def test_neutral_correction_keeps_the_regression_estimate():
+    # a network whose output is 128 everywhere leaves M* unchanged
+    from oracle import oracle as O
+    net = C.random_net(7)
+    for l in range(4):
+        net["w"][l][:] = 0
+        net["m"][l][:] = 1 << 10
+        net["sh"][l] = 10
+    net["b"][3][:] = 128
+    rng = np.random.default_rng(8)
+    s3 = rng.integers(0, 256, size=(3, 6, 9)).astype(np.uint8)
+    e = rng.integers(120, 140, size=(6, 9)).astype(np.uint8)
+    a = rng.uniform(-0.1, 0.1, (3, 256)).astype(np.float32)
+    b = rng.uniform(0, 255, (3, 256)).astype(np.float32)
+    ms = O.predict(O.gf(s3), e, a, b)
+    assert np.array_equal(C.refine(ms, C.infer(s3, e, 0, net)), ms)
+    assert C.refine(np.array([[[250, 3]]]), np.array([[[200, 10]]])).tolist() == [[[255, 0]]]
