@@ -166,6 +166,8 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
 
     # bit-exact check and rates at each quality (outside the timed region)
+    from paper_2309_11072_gb300 import learned as Lr
+    net_dev = Lr.upload_net(Lr.load_net(Lr.default_weights())) if os.path.exists(Lr.default_weights()) else None
     bit_exact = True
     bpp = {}
     ident = torch.from_numpy(codec.params_from_numpy(np.full((3, 256), 1 / 16, np.float32),
@@ -179,6 +181,24 @@ def run_ours(args) -> None:
         # without SLRME nothing but the residual planes is sent (M* = S)
         plain = enhancement_bits_per_pixel(c.hist.view(3, 511).cpu().numpy().view(np.uint32), 0, n) - 256.0 / n
         bpp[str(q)] = {"slr": round(slr, 4), "without_slrme": round(plain, 4), "learned": None}
+        if net_dev is not None:
+            # the learned estimator (refining this image's regression), picked only if cheaper
+            native.residual_encode(c.s3, c.m3, c.e, h, w, 1, c.params, c.r3, c.hist, stream)
+            hist_slr = c.hist.view(3, 511).cpu().numpy().view(np.uint32).copy()
+            J = native.rgbe_key_scale(c.stats.cpu().numpy())[0]
+            r3c = torch.empty_like(c.r3)
+            hc = torch.empty_like(c.hist)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Lr.cnn_residual_encode(c.s3, c.m3, c.e, h, w, J, net_dev, c.params, 1, r3c, hc, stream)
+            e1.record(stream)
+            Lr.cnn_residual_decode(c.s3, c.e, r3c, h, w, J, net_dev, c.params, 1, c.out, stream)
+            torch.cuda.synchronize()
+            bit_exact &= bool(torch.equal(c.out, rgbe))
+            pk = Lr.pick_image(hist_slr, codec.params_to_numpy(c.params)["n_used"],
+                               hc.view(3, 511).cpu().numpy().view(np.uint32), n)
+            bpp[str(q)].update(learned=round(pk.bits_cnn, 4), picked="learned" if pk.use_cnn else "slr",
+                               with_pick=round(pk.bits, 4), learned_encode_us=round(1e3 * e0.elapsed_time(e1), 1))
     torch.cuda.synchronize()
 
     if dist is not None:

@@ -333,6 +333,11 @@ int slrme_batch_graph_destroy(slrme_batch_plan* plan);
 int slrme_host_tables(int32_t* log2_lut, float* gamma, float* kr, float* wr,
                       int quality, int32_t* quant, int32_t* dct);
 
+/* Device status word of the current device (synchronous): 0, or
+ * 1 when a kernel's wait for its own bulk copies gave up after its bound (the
+ * kernel then stopped and its outputs are incomplete).  clear != 0 resets it. */
+int slrme_device_status(int* status, int clear);
+
 /* Text of the last error reported to the calling thread ("" if none). */
 const char* slrme_last_error(void);
 

@@ -10,11 +10,18 @@
 // of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
 // them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
 // 32-bit add (values stay <= 4080).
+#include <initializer_list>
 #include <mutex>
 
 #include "slrme_internal.cuh"
+#include "tma.cuh"
 
 namespace slrme {
+
+// Device status word of the TMA-staged kernels (0 = fine); read and cleared
+// by slrme_device_status().
+__device__ int g_slrme_status;
+
 
 namespace {
 
@@ -845,6 +852,338 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
     }
 }
 
+// ====================================================================== TMA-staged kernels
+//
+// The same computations as k_fit / k_residual / k_decode for images whose
+// rows are 16-byte aligned (w % 16 == 0, 16-byte aligned planes).  A CTA owns
+// a 256-column strip of a band of rows and streams it through a ring of
+// kStages shared-memory slots of kRB rows each: one warp issues 1-D bulk
+// copies (cp.async.bulk, completion counted on the slot's mbarrier) of every
+// plane's row segments, including the restoration's halo rows (clamped to the
+// image) and 16 halo columns on each side; all 8 warps then compute one row
+// each from shared memory.  Data in flight lives in shared memory, not in
+// registers, so far more bytes are outstanding per SM than with the
+// register window.
+
+constexpr int kRB = 8;          // rows per slot (one per warp)
+constexpr int kStages = 3;
+constexpr int kSW = 288;        // S row segment: 16 halo + 256 + 16 halo bytes
+constexpr int kBandChunks = 4;  // slots per band: bands of kRB * kBandChunks rows
+// fit runs end with their band: at most kRB * kBandChunks rows of 8 pixels per lane
+static_assert(8ull * kRB * kBandChunks * 4080ull * 4080ull < (1ull << 32), "run accumulators would overflow");
+
+enum class TmaMode { kResidual = 0, kDecode = 1, kFit = 2 };
+
+template <TmaMode MODE>
+struct TmaSlot {
+    static constexpr int kPlanes8 = MODE == TmaMode::kDecode ? 1 : 4;   // M_R, M_G, M_B, E  or  E
+    static constexpr int kPlanes16 = MODE == TmaMode::kDecode ? 3 : 0;  // R planes (int16)
+    uint8_t S[3][kRB + 2][kSW];
+    uint8_t B[kPlanes8][kRB][256];
+    int16_t R[kPlanes16 > 0 ? kPlanes16 : 1][kPlanes16 > 0 ? kRB : 1][256];
+};
+
+struct TmaImage {
+    const uint8_t* s3;
+    const uint8_t* m3;
+    const uint8_t* e;
+    const int16_t* r3_in;
+    int16_t* r3_out;
+    uint32_t* out;
+    int h, w;
+    bool gf;
+};
+
+// Copies of one slot: chunk (band y0, strip xs, stage k).  Lane i of the
+// issuing warp issues copies i, i + 32, ...; lane 0 first announces the
+// slot's byte count on its barrier.
+template <TmaMode MODE>
+__device__ __forceinline__ void tma_issue(const TmaImage& im, TmaSlot<MODE>& sl, uint32_t bar, int yf, int nr,
+                                          int xs, int lane) {
+    const int64_t n = (int64_t)im.h * im.w;
+    const int padl = xs >= 16 ? 16 : 0;
+    const int s_bytes = min(xs + 256 + 16, im.w) - (xs - padl);
+    const int b_bytes = min(256, im.w - xs);
+    constexpr int P8 = TmaSlot<MODE>::kPlanes8, P16 = TmaSlot<MODE>::kPlanes16;
+    const int ns = nr > 0 ? 3 * (nr + 2) : 0, nb = P8 * nr, nrr = P16 * nr;
+    if (lane == 0)
+        mbar_arrive_expect_tx(bar, (uint32_t)(ns * s_bytes + nb * b_bytes + nrr * 2 * b_bytes));
+    __syncwarp();
+    for (int k = lane; k < ns + nb + nrr; k += 32) {
+        if (k < ns) {
+            const int c = k / (nr + 2), r = k % (nr + 2);
+            const int y = min(max(yf - 1 + r, 0), im.h - 1);
+            tma_load_1d(smem_addr(&sl.S[c][r][16 - padl]), im.s3 + c * n + (int64_t)y * im.w + xs - padl,
+                        (uint32_t)s_bytes, bar);
+        } else if (k < ns + nb) {
+            const int q = k - ns, p = q / nr, r = q % nr;
+            const uint8_t* src = (MODE == TmaMode::kDecode || p == 3) ? im.e : im.m3 + p * n;
+            tma_load_1d(smem_addr(&sl.B[p][r][0]), src + (int64_t)(yf + r) * im.w + xs, (uint32_t)b_bytes, bar);
+        } else {
+            const int q = k - ns - nb, p = q / nr, r = q % nr;
+            tma_load_1d(smem_addr(&sl.R[p][r][0]), im.r3_in + p * n + (int64_t)(yf + r) * im.w + xs,
+                        (uint32_t)(2 * b_bytes), bar);
+        }
+    }
+}
+
+// One lane's row segment of S (8 bytes and the two neighbours) from a slot row.
+__device__ __forceinline__ Row10 slot_row(const uint8_t* row, int xs, int x0, int w) {
+    Row10 R;
+    const uint2 v = *reinterpret_cast<const uint2*>(row + 16 + (x0 - xs));
+    R.lo = v.x;
+    R.hi = v.y;
+    R.l = row[16 + (x0 > 0 ? x0 - 1 : 0) - xs];
+    R.r = row[16 + (x0 + 8 < w ? x0 + 8 : w - 1) - xs];
+    return R;
+}
+
+template <TmaMode MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_tma(const TmaImage im, const slrme_params* __restrict__ P,
+                                                     uint32_t* __restrict__ ghist,
+                                                     unsigned long long* __restrict__ gbins, int max_spins) {
+    extern __shared__ __align__(128) char dyn[];
+    TmaSlot<MODE>* slots = reinterpret_cast<TmaSlot<MODE>*>(dyn);
+    char* tail = dyn + sizeof(TmaSlot<MODE>) * kStages;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tail);
+    tail += 8 * kStages;
+    float* sa = reinterpret_cast<float*>(tail);                    // residual / decode: parameters
+    float* sb = sa + 3 * kNbin;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(sb + 3 * kNbin);  // residual: histograms
+    SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);            // fit: bins (instead of params)
+    uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = im.h, w = im.w;
+    const int64_t n = (int64_t)h * w;
+    if (MODE == TmaMode::kFit) {
+        bins_clear(bins);
+    } else {
+        load_params(P, sa, sb);
+        if (MODE == TmaMode::kResidual && ghist)
+            for (int i = threadIdx.x; i < 3 * kNres; i += kThreads) hist[i] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; ++k) mbar_init(smem_addr(&bars[k]), 1);
+        fence_async_shared();
+    }
+    __syncthreads();
+
+    const int cols = (w + 255) / 256;
+    const int band_rows = kRB * kBandChunks;
+    const int64_t tiles = (int64_t)((h + band_rows - 1) / band_rows) * cols;
+    const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nchunks = my_tiles * kBandChunks;
+    auto chunk_geom = [&](int64_t q, int& yf, int& nr, int& xs) {
+        const int64_t t = blockIdx.x + (q / kBandChunks) * gridDim.x;
+        const int k = (int)(q % kBandChunks);
+        yf = (int)(t / cols) * band_rows + k * kRB;
+        xs = (int)(t % cols) * 256;
+        nr = max(0, min(kRB, h - yf));   // rows of this slot (0 past the image's last row)
+    };
+    FitWarp st;
+    run_reset(st.even, -1);
+    run_reset(st.odd, -1);
+    st.Q = queue + warp * 32 * kQueueStride;
+    st.queued = 0;
+    bool ok = true;
+
+    if (warp == 0)
+        for (int64_t q = 0; q < kStages - 1 && q < nchunks; ++q) {
+            int yf, nr, xs;
+            chunk_geom(q, yf, nr, xs);
+            tma_issue<MODE>(im, slots[q % kStages], smem_addr(&bars[q % kStages]), yf, nr, xs, lane);
+        }
+    for (int64_t q = 0; q < nchunks && ok; ++q) {
+        if (warp == 0 && q + kStages - 1 < nchunks) {
+            const int64_t qn = q + kStages - 1;
+            int yf, nr, xs;
+            chunk_geom(qn, yf, nr, xs);
+            fence_async_shared();   // the slot's previous readers are done (barrier below)
+            tma_issue<MODE>(im, slots[qn % kStages], smem_addr(&bars[qn % kStages]), yf, nr, xs, lane);
+        }
+        const int slot = (int)(q % kStages);
+        ok = mbar_wait(smem_addr(&bars[slot]), (uint32_t)((q / kStages) & 1), &g_slrme_status, max_spins);
+        int yf, nr, xs;
+        chunk_geom(q, yf, nr, xs);
+        const TmaSlot<MODE>& sl = slots[slot];
+        const int x0 = xs + 8 * lane;
+        if (ok && warp < nr) {
+            const int r = warp, y = yf + r;
+            uint32_t X[3][4];
+            if (x0 < w) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const Row10 a = slot_row(sl.S[c][r], xs, x0, w);
+                    const Row10 b = slot_row(sl.S[c][r + 1], xs, x0, w);
+                    const Row10 cc = slot_row(sl.S[c][r + 2], xs, x0, w);
+                    gf_pairs(a, b, cc, im.gf, X[c]);
+                }
+            }
+            if (MODE == TmaMode::kResidual && x0 < w) {
+                const uint2 ev = *reinterpret_cast<const uint2*>(&sl.B[3][r][x0 - xs]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const uint2 mv = *reinterpret_cast<const uint2*>(&sl.B[c][r][x0 - xs]);
+                    int rr[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
+                        const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
+                        rr[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
+                    }
+                    uint4 v;
+                    v.x = (uint32_t)(rr[0] & 0xFFFF) | ((uint32_t)rr[1] << 16);
+                    v.y = (uint32_t)(rr[2] & 0xFFFF) | ((uint32_t)rr[3] << 16);
+                    v.z = (uint32_t)(rr[4] & 0xFFFF) | ((uint32_t)rr[5] << 16);
+                    v.w = (uint32_t)(rr[6] & 0xFFFF) | ((uint32_t)rr[7] << 16);
+                    *reinterpret_cast<uint4*>(im.r3_out + c * n + (int64_t)y * w + x0) = v;
+                    if (ghist) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
+                    }
+                }
+            }
+            if (MODE == TmaMode::kDecode && x0 < w) {
+                const uint2 ev = *reinterpret_cast<const uint2*>(&sl.B[0][r][x0 - xs]);
+                uint32_t word[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? ev.x : ev.y, i & 3) << 24;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(&sl.R[c][r][x0 - xs]);
+                    const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                        const int E = (int)(word[i] >> 24);
+                        const int M = rv + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
+                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
+                    }
+                }
+                uint4* o4 = reinterpret_cast<uint4*>(im.out + (int64_t)y * w + x0);
+                o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
+                o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
+            }
+            if (MODE == TmaMode::kFit) {
+                uint32_t mlo[3] = {0u, 0u, 0u}, mhi[3] = {0u, 0u, 0u}, elo = 0u, ehi = 0u;
+                bool slow = false;
+                if (x0 < w) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const uint2 mv = *reinterpret_cast<const uint2*>(&sl.B[c][r][x0 - xs]);
+                        mlo[c] = mv.x;
+                        mhi[c] = mv.y;
+                    }
+                    const uint2 ev = *reinterpret_cast<const uint2*>(&sl.B[3][r][x0 - xs]);
+                    elo = ev.x;
+                    ehi = ev.y;
+                    const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+                    const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
+                    const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
+                    const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 &&
+                                     ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
+                                     ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
+                                     ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
+                    if (two) {
+                        RunAcc pe, po;
+                        seg_sums(X, mlo, mhi, 0xFFFFFFFFu, 0xFFFFFFFFu, pe);
+                        if ((olo | ohi) == 0u) {
+                            run_reset(po, -1);
+                        } else if ((olo & ohi) == 0xFFFFFFFFu) {
+                            po = pe;
+                            run_reset(pe, -1);
+                        } else {
+                            seg_sums(X, mlo, mhi, olo, ohi, po);
+                            run_minus(pe, po);
+                        }
+                        run_feed(st.even, (int)Ee, pe, bins);
+                        run_feed(st.odd, (int)Eo, po, bins);
+                    } else {
+                        slow = true;
+                    }
+                }
+                const unsigned want = __ballot_sync(0xffffffffu, slow);
+                if (want) {
+                    if (st.queued + __popc(want) > 32) fit_drain(st, bins, lane);
+                    if (slow) {
+                        uint32_t* qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+                        qe[0] = elo;
+                        qe[1] = ehi;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            qe[2 + c] = mlo[c];
+                            qe[5 + c] = mhi[c];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[c][k];
+                        }
+                        qe[20] = 8u;
+                    }
+                    __syncwarp();
+                    st.queued += __popc(want);
+                }
+            }
+        }
+        if (MODE == TmaMode::kFit && (q % kBandChunks) == kBandChunks - 1) {
+            // end of a band: runs cover at most kRB * kBandChunks rows of 8 pixels
+            warp_flush(st.even, bins, lane);
+            warp_flush(st.odd, bins, lane);
+            run_reset(st.even, -1);
+            run_reset(st.odd, -1);
+        }
+        __syncthreads();   // the slot is free for the copy issued at the next step
+        ok = __syncthreads_and(ok);
+    }
+    if (!ok) {
+        // a copy did not arrive in time: drain what is in flight (bounded) and stop
+        for (int k = 0; k < kStages; ++k) mbar_wait(smem_addr(&bars[k]), 0u, &g_slrme_status, 1 << 10);
+        return;
+    }
+    if (MODE == TmaMode::kFit) {
+        fit_drain(st, bins, lane);
+        __syncthreads();
+        bins_to_global(bins, gbins, false);
+    }
+    if (MODE == TmaMode::kResidual && ghist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * kNres; i += kThreads)
+            if (hist[i]) atomicAdd(ghist + i, hist[i]);
+    }
+}
+
+template <TmaMode MODE>
+constexpr size_t tma_smem_bytes() {
+    return sizeof(TmaSlot<MODE>) * kStages + 8 * kStages +
+           (MODE == TmaMode::kFit ? sizeof(SmemBins) + sizeof(uint32_t) * kWarps * 32 * kQueueStride
+                                  : sizeof(float) * 6 * kNbin + sizeof(uint32_t) * 3 * kNres);
+}
+
+bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
+    if (w % 16 != 0) return false;
+    for (const void* p : ptrs)
+        if ((uintptr_t)p % 16 != 0) return false;
+    return true;
+}
+
+template <TmaMode MODE>
+int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, unsigned long long* bins, cudaStream_t s) {
+    static bool attr_set[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("tma device");
+    constexpr size_t smem = tma_smem_bytes<MODE>();
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return cuda_status("tma smem attribute");
+        attr_set[dev] = true;
+    }
+    const int band_rows = kRB * kBandChunks;
+    const int64_t tiles = (int64_t)((im.h + band_rows - 1) / band_rows) * ((im.w + 255) / 256);
+    const int64_t cap = (int64_t)geometry().sms * 2;
+    const int64_t g = tiles < cap ? tiles : cap;
+    k_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kThreads, smem, s>>>(im, P, hist, bins, kMaxSpins);
+    return cuda_status("tma stage launch");
+}
+
 int strip_ctas(int64_t cta_tasks, int per_sm) {
     const int64_t cap = (int64_t)geometry().sms * per_sm;
     int64_t g = cta_tasks < cap ? cta_tasks : cap;
@@ -880,10 +1219,16 @@ int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, in
     if (n > 0) {
         const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                           ((uintptr_t)e % 8 == 0);
-        const StripLaunch L = strip_launch(h, w, 2);
-        k_fit<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
-                                            reinterpret_cast<unsigned long long*>(bin_sums));
-        int st = cuda_status("slr_fit launch");
+        int st;
+        if (tma_eligible(w, {s3, m3, e})) {
+            const TmaImage im{s3, m3, e, nullptr, nullptr, nullptr, h, w, gf_on != 0};
+            st = launch_tma<TmaMode::kFit>(im, nullptr, nullptr, reinterpret_cast<unsigned long long*>(bin_sums), s);
+        } else {
+            const StripLaunch L = strip_launch(h, w, 2);
+            k_fit<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
+                                                reinterpret_cast<unsigned long long*>(bin_sums));
+            st = cuda_status("slr_fit launch");
+        }
         if (st != SLRME_OK) return st;
     }
     k_solve<<<1, 768, 0, s>>>(bin_sums, params);
@@ -894,6 +1239,10 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
                            const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                       ((uintptr_t)e % 8 == 0);
+    if (tma_eligible(w, {s3, m3, e, r3})) {
+        const TmaImage im{s3, m3, e, nullptr, r3, nullptr, h, w, gf_on != 0};
+        return launch_tma<TmaMode::kResidual>(im, params, hist, nullptr, s);
+    }
     const StripLaunch L = strip_launch(h, w, 2);
     k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
     return cuda_status("residual_encode launch");
@@ -902,6 +1251,10 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
 int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w, int gf_on,
                            const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
+    if (tma_eligible(w, {s3, e, r3, rgbe_out})) {
+        const TmaImage im{s3, nullptr, e, r3, nullptr, rgbe_out, h, w, gf_on != 0};
+        return launch_tma<TmaMode::kDecode>(im, params, nullptr, nullptr, s);
+    }
     const StripLaunch L = strip_launch(h, w, 2);
     k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
     return cuda_status("residual_decode launch");
@@ -1031,4 +1384,20 @@ extern "C" int slr_fit_noalloc(const uint8_t* s_dec3, const uint8_t* m3, const u
     }
     k_solve<<<1, 768, 0, s>>>(reinterpret_cast<const int64_t*>(bins), params);
     return cuda_status("slr_fit_noalloc solve launch");
+}
+
+extern "C" int slrme_device_status(int* status, int clear) {
+    using namespace slrme;
+    if (!status) {
+        set_error("slrme_device_status: null pointer");
+        return SLRME_EINVAL;
+    }
+    if (cudaMemcpyFromSymbol(status, g_slrme_status, sizeof(int)) != cudaSuccess)
+        return cuda_status("slrme_device_status read");
+    if (clear) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_slrme_status, &zero, sizeof(int)) != cudaSuccess)
+            return cuda_status("slrme_device_status clear");
+    }
+    return SLRME_OK;
 }

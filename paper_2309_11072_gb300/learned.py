@@ -121,6 +121,18 @@ def export_int_net(theta: np.ndarray) -> dict:
     return net
 
 
+def load_net(path: str) -> dict:
+    """Integer network saved by learned_eval (--weights)."""
+    z = np.load(path)
+    return {"w": [z[f"w{l}"] for l in range(4)], "b": [z[f"b{l}"] for l in range(4)],
+            "m": [z[f"m{l}"] for l in range(4)], "sh": [int(v) for v in z["sh"]]}
+
+
+def default_weights() -> str:
+    import os
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "cnn_refine_q90.npz")
+
+
 def upload_net(net: dict, device="cuda") -> torch.Tensor:
     return torch.from_numpy(pack_net(net).view(np.int32).copy()).to(device)
 

@@ -40,6 +40,7 @@ _SIGS = {
     "residual_encode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "residual_decode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
     "slrme_host_tables": [_vp, _vp, _vp, _vp, _i32, _vp, _vp],
+    "slrme_device_status": [_vp, _i32],
 }
 
 
@@ -137,6 +138,13 @@ def residual_encode(s_dec3, m3, e, h: int, w: int, gf_on: int, params, r3, hist=
 def residual_decode(s_dec3, e, r3, h: int, w: int, gf_on: int, params, rgbe_out, stream=None) -> None:
     _check("residual_decode", lib().residual_decode(_ptr(s_dec3), _ptr(e), _ptr(r3), h, w, int(gf_on),
                                                     _ptr(params), _ptr(rgbe_out), _stream(stream)))
+
+
+def device_status(clear: bool = True) -> int:
+    """The library's device status word (0 = fine); see include/slrme.h."""
+    v = ctypes.c_int(-1)
+    _check("slrme_device_status", lib().slrme_device_status(ctypes.addressof(v), int(clear)))
+    return v.value
 
 
 def host_tables(quality: int = 50) -> dict:

@@ -326,3 +326,21 @@ def test_pipeline_8k_workload_full_size():
     g, o = assert_matches_oracle(img, 90)
     e = g["e"]
     assert e.min() >= 100 and e.max() <= 150
+
+
+def _device_status():
+    import ctypes
+    v = ctypes.c_int(-1)
+    L = native.lib()
+    assert L.slrme_device_status(ctypes.addressof(v), 1) == 0
+    return v.value
+
+
+@pytest.mark.parametrize("h,w", [(1, 16), (8, 16), (33, 256), (70, 512), (45, 784), (100, 1040)])
+@pytest.mark.parametrize("gf_on", [True, False])
+def test_tma_staged_path_matches_oracle(h, w, gf_on):
+    # rows of 16-byte multiples take the bulk-copy (TMA) kernels of fit, residual and decode
+    _device_status()
+    assert_matches_oracle(make_img(h, w, "scene", seed=h + 3 * w), 80, gf_on)
+    assert_matches_oracle(make_img(h, w, "noise", seed=h + 5 * w), 80, gf_on)
+    assert _device_status() == 0
