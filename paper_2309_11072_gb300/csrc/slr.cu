@@ -855,32 +855,30 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
 // ====================================================================== TMA-staged kernels
 //
 // The same computations as k_fit / k_residual / k_decode for images whose
-// rows are 16-byte aligned (w % 16 == 0, 16-byte aligned planes).  A CTA owns
-// a 256-column strip of a band of rows and streams it through a ring of
-// kStages shared-memory slots of kRB rows each: one warp issues 1-D bulk
-// copies (cp.async.bulk, completion counted on the slot's mbarrier) of every
-// plane's row segments, including the restoration's halo rows (clamped to the
-// image) and 16 halo columns on each side; all 8 warps then compute one row
-// each from shared memory.  Data in flight lives in shared memory, not in
-// registers, so far more bytes are outstanding per SM than with the
-// register window.
+// rows are 16-byte aligned (w % 16 == 0, 16-byte aligned planes).  Each warp
+// streams its own strip tasks (256 columns x strip_rows rows) through its own
+// ring of kSlots shared-memory slots: a slot holds one row "item", the S row
+// of all three planes with 16 halo columns on each side (rows clamped to the
+// image) and, for output rows, the M / E (or R / E) row segments.  Lanes
+// issue the item's 1-D bulk copies (cp.async.bulk, completion counted on the
+// slot's mbarrier); output row j of a task needs items j, j+1, j+2, so up to
+// kSlots - 3 items are in flight while a row is computed, and a slot is
+// refilled as soon as its row leaves the 3-row window.  No CTA-wide barrier
+// is involved; data in flight costs shared memory, not registers.
 
-constexpr int kRB = 8;          // rows per slot (one per warp)
-constexpr int kStages = 3;
-constexpr int kSW = 288;        // S row segment: 16 halo + 256 + 16 halo bytes
-constexpr int kBandChunks = 4;  // slots per band: bands of kRB * kBandChunks rows
-// fit runs end with their band: at most kRB * kBandChunks rows of 8 pixels per lane
-static_assert(8ull * kRB * kBandChunks * 4080ull * 4080ull < (1ull << 32), "run accumulators would overflow");
+constexpr int kSlots = 6;
+constexpr int kSW = 288;         // S row segment: 16 halo + 256 + 16 halo bytes
+constexpr int kTmaWarps = 4;     // warps per CTA (independent pipelines)
 
 enum class TmaMode { kResidual = 0, kDecode = 1, kFit = 2 };
 
 template <TmaMode MODE>
 struct TmaSlot {
     static constexpr int kPlanes8 = MODE == TmaMode::kDecode ? 1 : 4;   // M_R, M_G, M_B, E  or  E
-    static constexpr int kPlanes16 = MODE == TmaMode::kDecode ? 3 : 0;  // R planes (int16)
-    uint8_t S[3][kRB + 2][kSW];
-    uint8_t B[kPlanes8][kRB][256];
-    int16_t R[kPlanes16 > 0 ? kPlanes16 : 1][kPlanes16 > 0 ? kRB : 1][256];
+    static constexpr bool kR = MODE == TmaMode::kDecode;                  // R planes (int16)
+    uint8_t S[3][kSW];
+    uint8_t B[kPlanes8][256];
+    int16_t R[kR ? 3 : 1][kR ? 256 : 8];
 };
 
 struct TmaImage {
@@ -894,40 +892,38 @@ struct TmaImage {
     bool gf;
 };
 
-// Copies of one slot: chunk (band y0, strip xs, stage k).  Lane i of the
-// issuing warp issues copies i, i + 32, ...; lane 0 first announces the
-// slot's byte count on its barrier.
+// Issue the copies of item k of the strip task (y0, rows, xs): the S rows
+// y0 - 1 + k (clamped), and for 1 <= k <= rows the output row y0 + k - 1.
+// Lane 0 announces the byte count first.
 template <TmaMode MODE>
-__device__ __forceinline__ void tma_issue(const TmaImage& im, TmaSlot<MODE>& sl, uint32_t bar, int yf, int nr,
-                                          int xs, int lane) {
+__device__ __forceinline__ void tma_item(const TmaImage& im, TmaSlot<MODE>& sl, uint32_t bar, int y0, int rows,
+                                         int xs, int k, int lane) {
     const int64_t n = (int64_t)im.h * im.w;
     const int padl = xs >= 16 ? 16 : 0;
     const int s_bytes = min(xs + 256 + 16, im.w) - (xs - padl);
     const int b_bytes = min(256, im.w - xs);
-    constexpr int P8 = TmaSlot<MODE>::kPlanes8, P16 = TmaSlot<MODE>::kPlanes16;
-    const int ns = nr > 0 ? 3 * (nr + 2) : 0, nb = P8 * nr, nrr = P16 * nr;
-    if (lane == 0)
-        mbar_arrive_expect_tx(bar, (uint32_t)(ns * s_bytes + nb * b_bytes + nrr * 2 * b_bytes));
+    const bool out_row = k >= 1 && k <= rows;
+    constexpr int P8 = TmaSlot<MODE>::kPlanes8;
+    constexpr int NR = TmaSlot<MODE>::kR ? 3 : 0;
+    const uint32_t bytes = 3u * s_bytes + (out_row ? (uint32_t)(P8 * b_bytes + NR * 2 * b_bytes) : 0u);
+    if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
     __syncwarp();
-    for (int k = lane; k < ns + nb + nrr; k += 32) {
-        if (k < ns) {
-            const int c = k / (nr + 2), r = k % (nr + 2);
-            const int y = min(max(yf - 1 + r, 0), im.h - 1);
-            tma_load_1d(smem_addr(&sl.S[c][r][16 - padl]), im.s3 + c * n + (int64_t)y * im.w + xs - padl,
-                        (uint32_t)s_bytes, bar);
-        } else if (k < ns + nb) {
-            const int q = k - ns, p = q / nr, r = q % nr;
-            const uint8_t* src = (MODE == TmaMode::kDecode || p == 3) ? im.e : im.m3 + p * n;
-            tma_load_1d(smem_addr(&sl.B[p][r][0]), src + (int64_t)(yf + r) * im.w + xs, (uint32_t)b_bytes, bar);
-        } else {
-            const int q = k - ns - nb, p = q / nr, r = q % nr;
-            tma_load_1d(smem_addr(&sl.R[p][r][0]), im.r3_in + p * n + (int64_t)(yf + r) * im.w + xs,
-                        (uint32_t)(2 * b_bytes), bar);
-        }
+    const int ys = min(max(y0 - 1 + k, 0), im.h - 1);
+    if (lane < 3) {
+        tma_load_1d(smem_addr(&sl.S[lane][16 - padl]), im.s3 + lane * n + (int64_t)ys * im.w + xs - padl,
+                    (uint32_t)s_bytes, bar);
+    } else if (out_row && lane < 3 + P8) {
+        const int p = lane - 3;
+        const uint8_t* src = (MODE == TmaMode::kDecode || p == 3) ? im.e : im.m3 + p * n;
+        tma_load_1d(smem_addr(&sl.B[p][0]), src + (int64_t)(y0 + k - 1) * im.w + xs, (uint32_t)b_bytes, bar);
+    } else if (out_row && lane < 3 + P8 + NR) {
+        const int p = lane - 3 - P8;
+        tma_load_1d(smem_addr(&sl.R[p][0]), im.r3_in + p * n + (int64_t)(y0 + k - 1) * im.w + xs,
+                    (uint32_t)(2 * b_bytes), bar);
     }
 }
 
-// One lane's row segment of S (8 bytes and the two neighbours) from a slot row.
+// One lane's row segment of S (8 bytes and the two neighbours) from a slot.
 __device__ __forceinline__ Row10 slot_row(const uint8_t* row, int xs, int x0, int w) {
     Row10 R;
     const uint2 v = *reinterpret_cast<const uint2*>(row + 16 + (x0 - xs));
@@ -938,22 +934,45 @@ __device__ __forceinline__ Row10 slot_row(const uint8_t* row, int xs, int x0, in
     return R;
 }
 
+// The warp's strip tasks in issue order (the same order they are consumed).
+struct TaskCursor {
+    int64_t t, stride, tasks;
+    int cols, rows_per, h;
+    int y0, rows, xs, k;   // current task and item within it
+    __device__ __forceinline__ bool valid() const { return t < tasks; }
+    __device__ __forceinline__ void load() {
+        if (t < tasks) {
+            y0 = (int)(t / cols) * rows_per;
+            xs = (int)(t % cols) * 256;
+            rows = min(rows_per, h - y0);
+        }
+        k = 0;
+    }
+    __device__ __forceinline__ void next_item() {
+        if (++k == rows + 2) {
+            t += stride;
+            load();
+        }
+    }
+};
+
 template <TmaMode MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_tma(const TmaImage im, const slrme_params* __restrict__ P,
-                                                     uint32_t* __restrict__ ghist,
-                                                     unsigned long long* __restrict__ gbins, int max_spins) {
+__global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, const slrme_params* __restrict__ P,
+                                                            uint32_t* __restrict__ ghist,
+                                                            unsigned long long* __restrict__ gbins, int rows_per,
+                                                            int max_spins) {
     extern __shared__ __align__(128) char dyn[];
-    TmaSlot<MODE>* slots = reinterpret_cast<TmaSlot<MODE>*>(dyn);
-    char* tail = dyn + sizeof(TmaSlot<MODE>) * kStages;
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tail);
-    tail += 8 * kStages;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TmaSlot<MODE>* ring = reinterpret_cast<TmaSlot<MODE>*>(dyn) + warp * kSlots;
+    char* tail = dyn + sizeof(TmaSlot<MODE>) * kSlots * kTmaWarps;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tail) + warp * kSlots;
+    tail += 8 * kSlots * kTmaWarps;
     float* sa = reinterpret_cast<float*>(tail);                    // residual / decode: parameters
     float* sb = sa + 3 * kNbin;
     uint32_t* hist = reinterpret_cast<uint32_t*>(sb + 3 * kNbin);  // residual: histograms
     SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);            // fit: bins (instead of params)
     uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int h = im.h, w = im.w;
     const int64_t n = (int64_t)h * w;
     if (MODE == TmaMode::kFit) {
@@ -961,70 +980,67 @@ __global__ void __launch_bounds__(kThreads, 2) k_tma(const TmaImage im, const sl
     } else {
         load_params(P, sa, sb);
         if (MODE == TmaMode::kResidual && ghist)
-            for (int i = threadIdx.x; i < 3 * kNres; i += kThreads) hist[i] = 0u;
+            for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
     }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < kStages; ++k) mbar_init(smem_addr(&bars[k]), 1);
+    if (lane == 0) {
+        for (int k = 0; k < kSlots; ++k) mbar_init(smem_addr(&bars[k]), 1);
         fence_async_shared();
     }
     __syncthreads();
 
     const int cols = (w + 255) / 256;
-    const int band_rows = kRB * kBandChunks;
-    const int64_t tiles = (int64_t)((h + band_rows - 1) / band_rows) * cols;
-    const int64_t my_tiles = tiles > blockIdx.x ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nchunks = my_tiles * kBandChunks;
-    auto chunk_geom = [&](int64_t q, int& yf, int& nr, int& xs) {
-        const int64_t t = blockIdx.x + (q / kBandChunks) * gridDim.x;
-        const int k = (int)(q % kBandChunks);
-        yf = (int)(t / cols) * band_rows + k * kRB;
-        xs = (int)(t % cols) * 256;
-        nr = max(0, min(kRB, h - yf));   // rows of this slot (0 past the image's last row)
-    };
+    const int64_t tasks = (int64_t)((h + rows_per - 1) / rows_per) * cols;
+    const int64_t first = (int64_t)blockIdx.x * kTmaWarps + warp, stride = (int64_t)gridDim.x * kTmaWarps;
+    TaskCursor issue{first, stride, tasks, cols, rows_per, h, 0, 0, 0, 0};
+    issue.load();
+    TaskCursor cons = issue;
+    int64_t g_issue = 0, g_cons = 0;   // items issued / first item of the consumer's current task
+    bool ok = true;
     FitWarp st;
     run_reset(st.even, -1);
     run_reset(st.odd, -1);
     st.Q = queue + warp * 32 * kQueueStride;
     st.queued = 0;
-    bool ok = true;
 
-    if (warp == 0)
-        for (int64_t q = 0; q < kStages - 1 && q < nchunks; ++q) {
-            int yf, nr, xs;
-            chunk_geom(q, yf, nr, xs);
-            tma_issue<MODE>(im, slots[q % kStages], smem_addr(&bars[q % kStages]), yf, nr, xs, lane);
+    // keep the ring full: items up to g_lo + kSlots - 1 may be in flight
+    auto refill = [&](int64_t g_lo) {
+        while (issue.valid() && g_issue < g_lo + kSlots) {
+            const int slot = (int)(g_issue % kSlots);
+            fence_async_shared();
+            tma_item<MODE>(im, ring[slot], smem_addr(&bars[slot]), issue.y0, issue.rows, issue.xs, issue.k, lane);
+            ++g_issue;
+            issue.next_item();
         }
-    for (int64_t q = 0; q < nchunks && ok; ++q) {
-        if (warp == 0 && q + kStages - 1 < nchunks) {
-            const int64_t qn = q + kStages - 1;
-            int yf, nr, xs;
-            chunk_geom(qn, yf, nr, xs);
-            fence_async_shared();   // the slot's previous readers are done (barrier below)
-            tma_issue<MODE>(im, slots[qn % kStages], smem_addr(&bars[qn % kStages]), yf, nr, xs, lane);
-        }
-        const int slot = (int)(q % kStages);
-        ok = mbar_wait(smem_addr(&bars[slot]), (uint32_t)((q / kStages) & 1), &g_slrme_status, max_spins);
-        int yf, nr, xs;
-        chunk_geom(q, yf, nr, xs);
-        const TmaSlot<MODE>& sl = slots[slot];
+    };
+    refill(0);
+    while (cons.valid() && ok) {
+        const int y0 = cons.y0, rows = cons.rows, xs = cons.xs;
         const int x0 = xs + 8 * lane;
-        if (ok && warp < nr) {
-            const int r = warp, y = yf + r;
+        // the first two items of the task
+        for (int k = 0; k < 2 && ok; ++k)
+            ok = mbar_wait(smem_addr(&bars[(g_cons + k) % kSlots]), (uint32_t)(((g_cons + k) / kSlots) & 1),
+                           &g_slrme_status, max_spins);
+        for (int j = 0; j < rows && ok; ++j) {
+            const int64_t gi = g_cons + j + 2;
+            ok = mbar_wait(smem_addr(&bars[gi % kSlots]), (uint32_t)((gi / kSlots) & 1), &g_slrme_status,
+                           max_spins);
+            if (!ok) break;
+            const TmaSlot<MODE>& s0 = ring[(g_cons + j) % kSlots];
+            const TmaSlot<MODE>& s1 = ring[(g_cons + j + 1) % kSlots];
+            const TmaSlot<MODE>& s2 = ring[gi % kSlots];
+            const int y = y0 + j;
             uint32_t X[3][4];
             if (x0 < w) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const Row10 a = slot_row(sl.S[c][r], xs, x0, w);
-                    const Row10 b = slot_row(sl.S[c][r + 1], xs, x0, w);
-                    const Row10 cc = slot_row(sl.S[c][r + 2], xs, x0, w);
-                    gf_pairs(a, b, cc, im.gf, X[c]);
-                }
+                for (int c = 0; c < 3; ++c)
+                    gf_pairs(slot_row(s0.S[c], xs, x0, w), slot_row(s1.S[c], xs, x0, w),
+                             slot_row(s2.S[c], xs, x0, w), im.gf, X[c]);
             }
             if (MODE == TmaMode::kResidual && x0 < w) {
-                const uint2 ev = *reinterpret_cast<const uint2*>(&sl.B[3][r][x0 - xs]);
+                const uint2 ev = *reinterpret_cast<const uint2*>(&s1.B[3][x0 - xs]);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const uint2 mv = *reinterpret_cast<const uint2*>(&sl.B[c][r][x0 - xs]);
+                    const uint2 mv = *reinterpret_cast<const uint2*>(&s1.B[c][x0 - xs]);
                     int rr[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -1045,13 +1061,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_tma(const TmaImage im, const sl
                 }
             }
             if (MODE == TmaMode::kDecode && x0 < w) {
-                const uint2 ev = *reinterpret_cast<const uint2*>(&sl.B[0][r][x0 - xs]);
+                const uint2 ev = *reinterpret_cast<const uint2*>(&s1.B[0][x0 - xs]);
                 uint32_t word[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? ev.x : ev.y, i & 3) << 24;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(&sl.R[c][r][x0 - xs]);
+                    const uint4 v = *reinterpret_cast<const uint4*>(&s1.R[c][x0 - xs]);
                     const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -1071,11 +1087,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tma(const TmaImage im, const sl
                 if (x0 < w) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const uint2 mv = *reinterpret_cast<const uint2*>(&sl.B[c][r][x0 - xs]);
+                        const uint2 mv = *reinterpret_cast<const uint2*>(&s1.B[c][x0 - xs]);
                         mlo[c] = mv.x;
                         mhi[c] = mv.y;
                     }
-                    const uint2 ev = *reinterpret_cast<const uint2*>(&sl.B[3][r][x0 - xs]);
+                    const uint2 ev = *reinterpret_cast<const uint2*>(&s1.B[3][x0 - xs]);
                     elo = ev.x;
                     ehi = ev.y;
                     const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
@@ -1123,38 +1139,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_tma(const TmaImage im, const sl
                     st.queued += __popc(want);
                 }
             }
+            __syncwarp();          // every lane is done with item g_cons + j
+            refill(g_cons + j + 1);
         }
-        if (MODE == TmaMode::kFit && (q % kBandChunks) == kBandChunks - 1) {
-            // end of a band: runs cover at most kRB * kBandChunks rows of 8 pixels
+        if (MODE == TmaMode::kFit) {
+            // every run ends with its strip task (bounded: see kMaxStripRows)
             warp_flush(st.even, bins, lane);
             warp_flush(st.odd, bins, lane);
             run_reset(st.even, -1);
             run_reset(st.odd, -1);
         }
-        __syncthreads();   // the slot is free for the copy issued at the next step
-        ok = __syncthreads_and(ok);
+        g_cons += rows + 2;
+        cons.t += cons.stride;
+        cons.load();
+        if (ok) refill(g_cons);
     }
     if (!ok) {
-        // a copy did not arrive in time: drain what is in flight (bounded) and stop
-        for (int k = 0; k < kStages; ++k) mbar_wait(smem_addr(&bars[k]), 0u, &g_slrme_status, 1 << 10);
-        return;
+        // a copy did not arrive in time: give what is in flight a bounded wait and stop
+        for (int64_t g = g_cons; g < g_issue; ++g)
+            mbar_wait(smem_addr(&bars[g % kSlots]), (uint32_t)((g / kSlots) & 1), &g_slrme_status, 1 << 10);
     }
     if (MODE == TmaMode::kFit) {
-        fit_drain(st, bins, lane);
+        if (ok) fit_drain(st, bins, lane);
         __syncthreads();
         bins_to_global(bins, gbins, false);
     }
     if (MODE == TmaMode::kResidual && ghist) {
         __syncthreads();
-        for (int i = threadIdx.x; i < 3 * kNres; i += kThreads)
+        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x)
             if (hist[i]) atomicAdd(ghist + i, hist[i]);
     }
 }
 
 template <TmaMode MODE>
 constexpr size_t tma_smem_bytes() {
-    return sizeof(TmaSlot<MODE>) * kStages + 8 * kStages +
-           (MODE == TmaMode::kFit ? sizeof(SmemBins) + sizeof(uint32_t) * kWarps * 32 * kQueueStride
+    return sizeof(TmaSlot<MODE>) * kSlots * kTmaWarps + 8 * kSlots * kTmaWarps +
+           (MODE == TmaMode::kFit ? sizeof(SmemBins) + sizeof(uint32_t) * kTmaWarps * 32 * kQueueStride
                                   : sizeof(float) * 6 * kNbin + sizeof(uint32_t) * 3 * kNres);
 }
 
@@ -1176,11 +1196,16 @@ int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, unsign
             return cuda_status("tma smem attribute");
         attr_set[dev] = true;
     }
-    const int band_rows = kRB * kBandChunks;
-    const int64_t tiles = (int64_t)((im.h + band_rows - 1) / band_rows) * ((im.w + 255) / 256);
-    const int64_t cap = (int64_t)geometry().sms * 2;
-    const int64_t g = tiles < cap ? tiles : cap;
-    k_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kThreads, smem, s>>>(im, P, hist, bins, kMaxSpins);
+    // strip height: the tallest of 16, 8, 4 rows giving about 24 warps of work per SM
+    const int sms = geometry().sms;
+    const int64_t cols = (im.w + 255) / 256;
+    int rows = kMaxStripRows;
+    while (rows > 4 && (int64_t)((im.h + rows - 1) / rows) * cols < (int64_t)sms * 24) rows >>= 1;
+    const int64_t tasks = (int64_t)((im.h + rows - 1) / rows) * cols;
+    int64_t g = (tasks + kTmaWarps - 1) / kTmaWarps;
+    const int64_t cap = (int64_t)sms * (MODE == TmaMode::kFit ? 2 : 3);
+    if (g > cap) g = cap;
+    k_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kTmaWarps * 32, smem, s>>>(im, P, hist, bins, rows, kMaxSpins);
     return cuda_status("tma stage launch");
 }
 
