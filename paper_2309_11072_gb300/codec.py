@@ -116,35 +116,55 @@ class HostCodec:
 
     Each call copies the words host -> device, encodes and decodes on the
     device, and copies the enhancement layer (R, E, parameters, histograms),
-    the base layer S and the decoded words back to pinned host buffers.
+    the base layer S and the decoded words back to pinned host buffers.  Two
+    device codecs on two streams alternate between calls, so the copies of one
+    call overlap the coding of the next; host buffers are per call slot.
     """
 
-    def __init__(self, h: int, w: int, device: str | torch.device = "cuda", gf_on: bool = True):
-        self.codec = Codec(h, w, device, gf_on)
+    def __init__(self, h: int, w: int, device: str | torch.device = "cuda", gf_on: bool = True, slots: int = 2):
+        self.slots = []
         n = h * w
-        self.d_rgbe = torch.empty(n, dtype=torch.int32, device=self.codec.device)
-        self.h_s3 = torch.empty(3 * n, dtype=torch.uint8).pin_memory()
-        self.h_e = torch.empty(n, dtype=torch.uint8).pin_memory()
-        self.h_r3 = torch.empty(3 * n, dtype=torch.int16).pin_memory()
-        self.h_params = torch.empty(native.PARAMS_BYTES // 4, dtype=torch.int32).pin_memory()
-        self.h_hist = torch.empty(3 * native.SLRME_NRES, dtype=torch.int32).pin_memory()
-        self.h_out = torch.empty(n, dtype=torch.int32).pin_memory()
+        for _ in range(slots):
+            c = Codec(h, w, device, gf_on)
+            self.slots.append(dict(
+                codec=c, stream=torch.cuda.Stream(device=c.device),
+                d_rgbe=torch.empty(n, dtype=torch.int32, device=c.device),
+                h_s3=torch.empty(3 * n, dtype=torch.uint8).pin_memory(),
+                h_e=torch.empty(n, dtype=torch.uint8).pin_memory(),
+                h_r3=torch.empty(3 * n, dtype=torch.int16).pin_memory(),
+                h_params=torch.empty(native.PARAMS_BYTES // 4, dtype=torch.int32).pin_memory(),
+                h_hist=torch.empty(3 * native.SLRME_NRES, dtype=torch.int32).pin_memory(),
+                h_out=torch.empty(n, dtype=torch.int32).pin_memory()))
+        self.turn = 0
+
+    @property
+    def h_out(self) -> torch.Tensor:
+        return self.slots[(self.turn - 1) % len(self.slots)]["h_out"]
 
     def h2d_bytes(self) -> int:
-        return self.d_rgbe.numel() * 4
+        return self.slots[0]["d_rgbe"].numel() * 4
 
     def d2h_bytes(self) -> int:
-        return sum(t.numel() * t.element_size() for t in
-                   (self.h_s3, self.h_e, self.h_r3, self.h_params, self.h_hist, self.h_out))
+        sl = self.slots[0]
+        return sum(sl[k].numel() * sl[k].element_size() for k in ("h_s3", "h_e", "h_r3", "h_params", "h_hist", "h_out"))
 
     def roundtrip(self, rgbe_host: torch.Tensor, quality: int) -> None:
-        c = self.codec
-        self.d_rgbe.copy_(rgbe_host, non_blocking=True)
-        L = c.encode(self.d_rgbe, quality)
-        out = c.decode(L.s3, L.e, L.r3, L.params)
-        self.h_s3.copy_(c.s3, non_blocking=True)
-        self.h_e.copy_(c.e, non_blocking=True)
-        self.h_r3.copy_(c.r3, non_blocking=True)
-        self.h_params.copy_(c.params, non_blocking=True)
-        self.h_hist.copy_(c.hist, non_blocking=True)
-        self.h_out.copy_(out, non_blocking=True)
+        """Enqueue one call on the next slot's stream (asynchronous; the slot's
+        previous call, two calls back, is complete before its buffers are reused
+        because its stream runs in order)."""
+        sl = self.slots[self.turn % len(self.slots)]
+        self.turn += 1
+        c, s = sl["codec"], sl["stream"]
+        with torch.cuda.stream(s):
+            sl["d_rgbe"].copy_(rgbe_host, non_blocking=True)
+            L = c.encode(sl["d_rgbe"], quality, stream=s)
+            out = c.decode(L.s3, L.e, L.r3, L.params, stream=s)
+            sl["h_s3"].copy_(c.s3, non_blocking=True)
+            sl["h_e"].copy_(c.e, non_blocking=True)
+            sl["h_r3"].copy_(c.r3, non_blocking=True)
+            sl["h_params"].copy_(c.params, non_blocking=True)
+            sl["h_hist"].copy_(c.hist, non_blocking=True)
+            sl["h_out"].copy_(out, non_blocking=True)
+
+    def streams(self):
+        return [sl["stream"] for sl in self.slots]

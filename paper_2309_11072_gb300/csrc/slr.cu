@@ -229,7 +229,12 @@ __device__ __forceinline__ void run_flush(const RunAcc& a, SmemBins& B) {
 }
 
 // Flush of all lanes' runs at a warp-uniform point: when every non-empty run
-// is in the same region the warp reduces them first and one lane adds.
+// is in the same region the warp reduces them first and one lane adds.  A
+// lane's run holds at most 8 * kMaxStripRows = 128 pixels, so warp totals of
+// N, sum x, sum y and sum xy stay below 2^32 (4096 * 4080 * 255 < 2^32) and
+// use the 32-bit warp reduction; sum xx needs 64 bits.
+static_assert(32ull * 8 * kMaxStripRows * 4080ull * 255ull < (1ull << 32), "warp sums of x y exceed 32 bits");
+
 __device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lane) {
     const bool live = a.E >= 0 && a.n != 0;
     const unsigned liveMask = __ballot_sync(0xffffffffu, live);
@@ -237,15 +242,17 @@ __device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lan
     const int E0 = __shfl_sync(0xffffffffu, a.E, __ffs(liveMask) - 1);
     if (__all_sync(0xffffffffu, !live || a.E == E0)) {
         unsigned long long v[kNsum];
-        run_values(a, v);
-        if (!live) {
+        v[0] = __reduce_add_sync(0xffffffffu, live ? a.n : 0u);
 #pragma unroll
-            for (int j = 0; j < kNsum; ++j) v[j] = 0ull;
+        for (int c = 0; c < 3; ++c) {
+            v[1 + 4 * c] = __reduce_add_sync(0xffffffffu, live ? a.sx[c] : 0u);
+            v[2 + 4 * c] = __reduce_add_sync(0xffffffffu, live ? a.sy[c] : 0u);
+            v[3 + 4 * c] = __reduce_add_sync(0xffffffffu, live ? a.sxy[c] : 0u);
+            unsigned long long q = live ? a.sxx[c] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+            v[4 + 4 * c] = q;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int j = 0; j < kNsum; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
         if (lane == 0) bins_add(B, E0, v);
     } else {
         run_flush(a, B);
