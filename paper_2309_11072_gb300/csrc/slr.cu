@@ -259,35 +259,46 @@ __device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lan
     }
 }
 
-// Sums of one 8-pixel segment, restricted to the pixels whose byte of `mlo/mhi`
-// mask is 0xFF (mask = ~0 for all pixels).  x pairs are masked with the
-// 16-bit expansion of the byte mask.
+// Sums of one channel of an 8-pixel segment over the pixels whose byte of
+// `klo/khi` is 0xFF; k16 is the mask expanded to the 16-bit x pairs.
+__device__ __forceinline__ void chan_sums(const uint32_t (&X)[4], uint32_t ml, uint32_t mh, uint32_t klo,
+                                          uint32_t khi, const uint32_t (&k16)[4], RunAcc& a, int c) {
+    uint32_t x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = X[k] & k16[k];
+    const uint32_t yl = ml & klo, yh = mh & khi;
+    const uint32_t ps = x[0] + x[1] + x[2] + x[3];
+    a.sx[c] = (ps & 0xFFFFu) + (ps >> 16);
+    a.sy[c] = __dp4a(yl, 0x01010101u, __dp4a(yh, 0x01010101u, 0u));
+    uint32_t q = __dp2a_lo(x[0], yl, 0u);
+    q = __dp2a_hi(x[1], yl, q);
+    q = __dp2a_lo(x[2], yh, q);
+    a.sxy[c] = __dp2a_hi(x[3], yh, q);
+    uint32_t r = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t lo16 = x[k] & 0xFFFFu, hi16 = x[k] >> 16;
+        r += lo16 * lo16 + hi16 * hi16;
+    }
+    a.sxx[c] = r;
+}
+
+__device__ __forceinline__ void mask16(uint32_t klo, uint32_t khi, uint32_t (&k16)[4]) {
+    k16[0] = __byte_perm(klo, 0, 0x1100);
+    k16[1] = __byte_perm(klo, 0, 0x3322);
+    k16[2] = __byte_perm(khi, 0, 0x1100);
+    k16[3] = __byte_perm(khi, 0, 0x3322);
+}
+
+// Sums of one 8-pixel segment, restricted to the pixels whose byte of `klo/khi`
+// is 0xFF (all ones for all pixels).
 __device__ __forceinline__ void seg_sums(const uint32_t (&X)[3][4], const uint32_t (&mlo)[3], const uint32_t (&mhi)[3],
                                          uint32_t klo, uint32_t khi, RunAcc& a) {
-    const uint32_t k16[4] = {__byte_perm(klo, 0, 0x1100), __byte_perm(klo, 0, 0x3322),
-                             __byte_perm(khi, 0, 0x1100), __byte_perm(khi, 0, 0x3322)};
+    uint32_t k16[4];
+    mask16(klo, khi, k16);
     a.n = (uint32_t)(__popc(klo) + __popc(khi)) >> 3;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        uint32_t x[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) x[k] = X[c][k] & k16[k];
-        const uint32_t yl = mlo[c] & klo, yh = mhi[c] & khi;
-        const uint32_t ps = x[0] + x[1] + x[2] + x[3];
-        a.sx[c] = (ps & 0xFFFFu) + (ps >> 16);
-        a.sy[c] = __dp4a(yl, 0x01010101u, __dp4a(yh, 0x01010101u, 0u));
-        uint32_t q = __dp2a_lo(x[0], yl, 0u);
-        q = __dp2a_hi(x[1], yl, q);
-        q = __dp2a_lo(x[2], yh, q);
-        a.sxy[c] = __dp2a_hi(x[3], yh, q);
-        uint32_t r = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t lo16 = x[k] & 0xFFFFu, hi16 = x[k] >> 16;
-            r += lo16 * lo16 + hi16 * hi16;
-        }
-        a.sxx[c] = r;
-    }
+    for (int c = 0; c < 3; ++c) chan_sums(X[c], mlo[c], mhi[c], klo, khi, k16, a, c);
 }
 
 __device__ __forceinline__ void run_merge(RunAcc& a, const RunAcc& b) {
@@ -343,8 +354,18 @@ __device__ __forceinline__ void add_u32_exact(SmemBins& B, int idx, uint32_t v) 
     if (old + v < old) atomicAdd(&B.hi[idx], 1u);
 }
 
-// Adds every pixel of one queued segment straight into the bins.
+// Adds one queued entry to the bins: a flushed run (tag 256 + E; words 0-12
+// hold N and the channel sums in bin order) or a segment, pixel by pixel
+// (tag = pixel count).
 __device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
+    const uint32_t tag = q[20];
+    if (tag >= 256u) {
+        const int base = (int)(tag - 256u) * kNsum;
+#pragma unroll
+        for (int j = 0; j < kNsum; ++j)
+            if (q[j]) add_u32_exact(B, base + j, q[j]);
+        return;
+    }
     uint32_t elo = q[0], ehi = q[1];
     uint32_t mlo[3] = {q[2], q[3], q[4]}, mhi[3] = {q[5], q[6], q[7]};
     uint32_t X[3][4];
@@ -352,7 +373,7 @@ __device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int k = 0; k < 4; ++k) X[c][k] = q[8 + 4 * c + k];
-    const int cnt = (int)q[20];
+    const int cnt = (int)tag;
 #pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
         const int E = (int)(elo & 255u);
@@ -391,6 +412,29 @@ __device__ __forceinline__ void fit_drain(FitWarp& st, SmemBins& bins, int lane)
     if (lane < st.queued) drain_entry(st.Q + lane * kQueueStride, bins);
     __syncwarp();
     st.queued = 0;
+}
+
+// Queues the run of every lane with `want` set (a run that must leave its
+// accumulator in the middle of a strip); the warp drains them together later
+// instead of waiting on one lane's atomics.
+__device__ __forceinline__ void enqueue_run(FitWarp& st, bool want, const RunAcc& r, SmemBins& bins, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    if (st.queued + __popc(m) > 32) fit_drain(st, bins, lane);
+    if (want) {
+        uint32_t* q = st.Q + (st.queued + __popc(m & ((1u << lane) - 1u))) * kQueueStride;
+        q[0] = r.n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[1 + 4 * c] = r.sx[c];
+            q[2 + 4 * c] = r.sy[c];
+            q[3 + 4 * c] = r.sxy[c];
+            q[4 + 4 * c] = r.sxx[c];
+        }
+        q[20] = 256u + (uint32_t)r.E;
+    }
+    __syncwarp();
+    st.queued += __popc(m);
 }
 
 // One strip of one image (all 32 lanes): rows y0 .. y0 + rows - 1, columns xs .. xs + 255.
@@ -861,7 +905,7 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
 
 // ====================================================================== TMA-staged kernels
 //
-// The same computations as k_fit / k_residual / k_decode for images whose
+// The same computations as k_residual / k_decode for images whose
 // rows are 16-byte aligned (w % 16 == 0, 16-byte aligned planes).  Each warp
 // streams its own strip tasks (256 columns x strip_rows rows) through its own
 // ring of kSlots shared-memory slots: a slot holds one row "item", the S row
@@ -877,7 +921,7 @@ constexpr int kSlots = 6;
 constexpr int kSW = 288;         // S row segment: 16 halo + 256 + 16 halo bytes
 constexpr int kTmaWarps = 4;     // warps per CTA (independent pipelines)
 
-enum class TmaMode { kResidual = 0, kDecode = 1, kFit = 2 };
+enum class TmaMode { kResidual = 0, kDecode = 1 };
 
 template <TmaMode MODE>
 struct TmaSlot {
@@ -965,8 +1009,7 @@ struct TaskCursor {
 
 template <TmaMode MODE>
 __global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, const slrme_params* __restrict__ P,
-                                                            uint32_t* __restrict__ ghist,
-                                                            unsigned long long* __restrict__ gbins, int rows_per,
+                                                            uint32_t* __restrict__ ghist, int rows_per,
                                                             int max_spins) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -977,18 +1020,12 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, co
     float* sa = reinterpret_cast<float*>(tail);                    // residual / decode: parameters
     float* sb = sa + 3 * kNbin;
     uint32_t* hist = reinterpret_cast<uint32_t*>(sb + 3 * kNbin);  // residual: histograms
-    SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);            // fit: bins (instead of params)
-    uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
 
     const int h = im.h, w = im.w;
     const int64_t n = (int64_t)h * w;
-    if (MODE == TmaMode::kFit) {
-        bins_clear(bins);
-    } else {
-        load_params(P, sa, sb);
-        if (MODE == TmaMode::kResidual && ghist)
-            for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
-    }
+    load_params(P, sa, sb);
+    if (MODE == TmaMode::kResidual && ghist)
+        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
     if (lane == 0) {
         for (int k = 0; k < kSlots; ++k) mbar_init(smem_addr(&bars[k]), 1);
         fence_async_shared();
@@ -1003,11 +1040,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, co
     TaskCursor cons = issue;
     int64_t g_issue = 0, g_cons = 0;   // items issued / first item of the consumer's current task
     bool ok = true;
-    FitWarp st;
-    run_reset(st.even, -1);
-    run_reset(st.odd, -1);
-    st.Q = queue + warp * 32 * kQueueStride;
-    st.queued = 0;
 
     // keep the ring full: items up to g_lo + kSlots - 1 may be in flight
     auto refill = [&](int64_t g_lo) {
@@ -1088,73 +1120,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, co
                 o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
                 o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
             }
-            if (MODE == TmaMode::kFit) {
-                uint32_t mlo[3] = {0u, 0u, 0u}, mhi[3] = {0u, 0u, 0u}, elo = 0u, ehi = 0u;
-                bool slow = false;
-                if (x0 < w) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const uint2 mv = *reinterpret_cast<const uint2*>(&s1.B[c][x0 - xs]);
-                        mlo[c] = mv.x;
-                        mhi[c] = mv.y;
-                    }
-                    const uint2 ev = *reinterpret_cast<const uint2*>(&s1.B[3][x0 - xs]);
-                    elo = ev.x;
-                    ehi = ev.y;
-                    const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
-                    const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
-                    const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
-                    const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 &&
-                                     ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
-                                     ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
-                                     ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
-                    if (two) {
-                        RunAcc pe, po;
-                        seg_sums(X, mlo, mhi, 0xFFFFFFFFu, 0xFFFFFFFFu, pe);
-                        if ((olo | ohi) == 0u) {
-                            run_reset(po, -1);
-                        } else if ((olo & ohi) == 0xFFFFFFFFu) {
-                            po = pe;
-                            run_reset(pe, -1);
-                        } else {
-                            seg_sums(X, mlo, mhi, olo, ohi, po);
-                            run_minus(pe, po);
-                        }
-                        run_feed(st.even, (int)Ee, pe, bins);
-                        run_feed(st.odd, (int)Eo, po, bins);
-                    } else {
-                        slow = true;
-                    }
-                }
-                const unsigned want = __ballot_sync(0xffffffffu, slow);
-                if (want) {
-                    if (st.queued + __popc(want) > 32) fit_drain(st, bins, lane);
-                    if (slow) {
-                        uint32_t* qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
-                        qe[0] = elo;
-                        qe[1] = ehi;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            qe[2 + c] = mlo[c];
-                            qe[5 + c] = mhi[c];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[c][k];
-                        }
-                        qe[20] = 8u;
-                    }
-                    __syncwarp();
-                    st.queued += __popc(want);
-                }
-            }
             __syncwarp();          // every lane is done with item g_cons + j
             refill(g_cons + j + 1);
-        }
-        if (MODE == TmaMode::kFit) {
-            // every run ends with its strip task (bounded: see kMaxStripRows)
-            warp_flush(st.even, bins, lane);
-            warp_flush(st.odd, bins, lane);
-            run_reset(st.even, -1);
-            run_reset(st.odd, -1);
         }
         g_cons += rows + 2;
         cons.t += cons.stride;
@@ -1166,11 +1133,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, co
         for (int64_t g = g_cons; g < g_issue; ++g)
             mbar_wait(smem_addr(&bars[g % kSlots]), (uint32_t)((g / kSlots) & 1), &g_slrme_status, 1 << 10);
     }
-    if (MODE == TmaMode::kFit) {
-        if (ok) fit_drain(st, bins, lane);
-        __syncthreads();
-        bins_to_global(bins, gbins, false);
-    }
     if (MODE == TmaMode::kResidual && ghist) {
         __syncthreads();
         for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x)
@@ -1180,9 +1142,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, co
 
 template <TmaMode MODE>
 constexpr size_t tma_smem_bytes() {
-    return sizeof(TmaSlot<MODE>) * kSlots * kTmaWarps + 8 * kSlots * kTmaWarps +
-           (MODE == TmaMode::kFit ? sizeof(SmemBins) + sizeof(uint32_t) * kTmaWarps * 32 * kQueueStride
-                                  : sizeof(float) * 6 * kNbin + sizeof(uint32_t) * 3 * kNres);
+    return sizeof(TmaSlot<MODE>) * kSlots * kTmaWarps + 8 * kSlots * kTmaWarps + sizeof(float) * 6 * kNbin +
+           sizeof(uint32_t) * 3 * kNres;
 }
 
 bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
@@ -1193,7 +1154,7 @@ bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
 }
 
 template <TmaMode MODE>
-int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, unsigned long long* bins, cudaStream_t s) {
+int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, cudaStream_t s) {
     static bool attr_set[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("tma device");
@@ -1210,10 +1171,304 @@ int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, unsign
     while (rows > 4 && (int64_t)((im.h + rows - 1) / rows) * cols < (int64_t)sms * 24) rows >>= 1;
     const int64_t tasks = (int64_t)((im.h + rows - 1) / rows) * cols;
     int64_t g = (tasks + kTmaWarps - 1) / kTmaWarps;
-    const int64_t cap = (int64_t)sms * (MODE == TmaMode::kFit ? 2 : 3);
+    const int64_t cap = (int64_t)sms * 3;
     if (g > cap) g = cap;
-    k_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kTmaWarps * 32, smem, s>>>(im, P, hist, bins, rows, kMaxSpins);
+    k_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kTmaWarps * 32, smem, s>>>(im, P, hist, rows, kMaxSpins);
     return cuda_status("tma stage launch");
+}
+
+// ====================================================================== TMA-staged fit
+//
+// k_fit_tma: the fit for images whose rows are 16-byte aligned.  The rows of
+// all strips are taken in column-major order (strip, row) and cut into one
+// contiguous range per warp, so every warp does the same number of rows to
+// within one; a range becomes tasks of at most kMaxStripRows rows of one
+// strip.  Each warp streams its rows through two rings of shared-memory
+// slots filled by 1-D bulk copies that complete on the slot's mbarrier: S
+// rows of the three planes with 16 halo columns (row j of a task needs S rows
+// j - 1, j, j + 1) and, one row ahead, the M and E row segments.  A run that
+// has to leave its accumulator inside a strip goes to the warp's queue, with
+// the segments that hold three or more exponents, and the warp drains the
+// queue 32 entries at a time.
+
+constexpr int kFitWarps = 8;
+constexpr int kFitSlots = 6;     // S rows
+constexpr int kMeSlots = 2;      // M / E rows
+
+struct FitSlot {
+    uint8_t S[3][kSW];
+};
+
+struct MeSlot {
+    uint8_t M[3][kStripCols];
+    uint8_t E[kStripCols];
+};
+
+constexpr size_t kFitSmem = (sizeof(FitSlot) * kFitSlots + sizeof(MeSlot) * kMeSlots +
+                             8 * (kFitSlots + kMeSlots)) * kFitWarps +
+                            sizeof(SmemBins) + sizeof(uint32_t) * kFitWarps * 32 * kQueueStride;
+
+// A warp's rows r .. end - 1 in (strip, row) order and its current task.
+struct RowRange {
+    int r, end, h;
+    int y0, rows, xs;
+    // Takes the next task; false when the range is done.
+    __device__ __forceinline__ bool next() {
+        if (r >= end) return false;
+        const int c = r / h;
+        y0 = r - c * h;
+        rows = min(min(end - r, h - y0), kMaxStripRows);
+        xs = c * kStripCols;
+        r += rows;
+        return true;
+    }
+};
+
+// One lane's S row segment from a slot: 8 bytes plus the neighbours at the
+// precomputed offsets (which point at the lane's own edge byte where the
+// image ends, replicating it).
+__device__ __forceinline__ Row10 fit_row(const uint8_t* row, int own, int offl, int offr) {
+    Row10 R;
+    const uint2 v = *reinterpret_cast<const uint2*>(row + own);
+    R.lo = v.x;
+    R.hi = v.y;
+    R.l = row[offl];
+    R.r = row[offr];
+    return R;
+}
+
+// Copies the M and E row segments of row y, columns xs .. xs + 255 (lanes 0-3).
+__device__ __forceinline__ void issue_me(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int64_t n,
+                                         int w, int y, int xs, MeSlot& sl, uint32_t bar, int lane) {
+    const int bytes = min(kStripCols, w - xs);
+    fence_async_shared();
+    if (lane == 0) mbar_arrive_expect_tx(bar, 4u * (uint32_t)bytes);
+    __syncwarp();
+    if (lane < 4) {
+        const uint8_t* src = (lane < 3 ? m3 + lane * n : e) + (int64_t)y * w + xs;
+        tma_load_1d(smem_addr(lane < 3 ? &sl.M[lane][0] : &sl.E[0]), src, (uint32_t)bytes, bar);
+    }
+}
+
+__global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __restrict__ s3,
+                                                                const uint8_t* __restrict__ m3,
+                                                                const uint8_t* __restrict__ e, int h, int w, int gf_on,
+                                                                int64_t total_rows,
+                                                                unsigned long long* __restrict__ gbins, int max_spins) {
+    extern __shared__ __align__(128) char dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    FitSlot* ring = reinterpret_cast<FitSlot*>(dyn) + warp * kFitSlots;
+    char* tail = dyn + sizeof(FitSlot) * kFitSlots * kFitWarps;
+    MeSlot* me = reinterpret_cast<MeSlot*>(tail) + warp * kMeSlots;
+    tail += sizeof(MeSlot) * kMeSlots * kFitWarps;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kFitSlots + kMeSlots);
+    unsigned long long* me_bars = bars + kFitSlots;
+    tail += 8 * (kFitSlots + kMeSlots) * kFitWarps;
+    SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
+
+    bins_clear(bins);
+    if (lane == 0) {
+        for (int k = 0; k < kFitSlots + kMeSlots; ++k) mbar_init(smem_addr(&bars[k]), 1);
+        fence_async_shared();
+    }
+    __syncthreads();
+
+    const int64_t n = (int64_t)h * w;
+    const bool gf = gf_on != 0;
+    const int64_t warps = (int64_t)gridDim.x * kFitWarps, gw = (int64_t)blockIdx.x * kFitWarps + warp;
+    const int r0 = (int)(gw * total_rows / warps), r1 = (int)((gw + 1) * total_rows / warps);
+
+    // producer of S rows: the task and item (0 .. rows + 1) issued next
+    RowRange P{r0, r1, h, 0, 0, 0};
+    bool p_valid = P.next();
+    int pk = 0, p_slot = 0, issued = 0, released = 0;
+    auto refill = [&]() {
+        while (p_valid && issued < released + kFitSlots) {
+            const int padl = P.xs >= 16 ? 16 : 0;
+            const int s_bytes = min(P.xs + kStripCols + 16, w) - (P.xs - padl);
+            const uint32_t bar = smem_addr(&bars[p_slot]);
+            fence_async_shared();
+            if (lane == 0) mbar_arrive_expect_tx(bar, 3u * (uint32_t)s_bytes);
+            __syncwarp();
+            if (lane < 3) {
+                const int ys = min(max(P.y0 - 1 + pk, 0), h - 1);
+                tma_load_1d(smem_addr(&ring[p_slot].S[lane][16 - padl]),
+                            s3 + lane * n + (int64_t)ys * w + P.xs - padl, (uint32_t)s_bytes, bar);
+            }
+            ++issued;
+            p_slot = p_slot + 1 == kFitSlots ? 0 : p_slot + 1;
+            if (++pk == P.rows + 2) {
+                pk = 0;
+                p_valid = P.next();
+            }
+        }
+    };
+
+    FitWarp st;
+    run_reset(st.even, -1);
+    run_reset(st.odd, -1);
+    st.Q = queue + warp * 32 * kQueueStride;
+    st.queued = 0;
+
+    // consumer: current task, the next one (for the M / E copy a row ahead),
+    // slot of the task's first S item, the expected phase parity of every S
+    // slot, and the warp's row count q (M / E slot q % 2, parity (q / 2) % 2)
+    RowRange C{r0, r1, h, 0, 0, 0};
+    bool c_valid = C.next();
+    RowRange Cn = C;
+    bool n_valid = c_valid && Cn.next();
+    int c_slot = 0, q = 0;
+    uint32_t par = 0u;
+    bool ok = true;
+    if (c_valid) issue_me(m3, e, n, w, C.y0, C.xs, me[0], smem_addr(&me_bars[0]), lane);
+    refill();
+
+    while (c_valid && ok) {
+        const int x0 = C.xs + 8 * lane;
+        const int own = 16 + 8 * lane;
+        const int offl = x0 == 0 ? own : own - 1;
+        const int offr = x0 + 8 >= w ? own + 7 : own + 8;
+        const bool inside = x0 < w;
+        int a = c_slot, b = a + 1 == kFitSlots ? 0 : a + 1;
+        ok = mbar_wait(smem_addr(&bars[a]), (par >> a) & 1u, &g_slrme_status, max_spins) &&
+             mbar_wait(smem_addr(&bars[b]), (par >> b) & 1u, &g_slrme_status, max_spins);
+        for (int j = 0; j < C.rows && ok; ++j, ++q) {
+            const int c2 = b + 1 == kFitSlots ? 0 : b + 1;
+            // M / E of the next row (this task's, else the next task's first)
+            if (j + 1 < C.rows)
+                issue_me(m3, e, n, w, C.y0 + j + 1, C.xs, me[(q + 1) & 1], smem_addr(&me_bars[(q + 1) & 1]), lane);
+            else if (n_valid)
+                issue_me(m3, e, n, w, Cn.y0, Cn.xs, me[(q + 1) & 1], smem_addr(&me_bars[(q + 1) & 1]), lane);
+            ok = mbar_wait(smem_addr(&bars[c2]), (par >> c2) & 1u, &g_slrme_status, max_spins) &&
+                 mbar_wait(smem_addr(&me_bars[q & 1]), (uint32_t)(q >> 1) & 1u, &g_slrme_status, max_spins);
+            if (!ok) break;
+            const MeSlot& ms = me[q & 1];
+            const uint2 ev = *reinterpret_cast<const uint2*>(&ms.E[8 * lane]);
+            const uint32_t elo = ev.x, ehi = ev.y;
+            // byte masks of the odd-exponent pixels and the two exponents
+            const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+            const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
+            const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
+            const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 && ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
+                             ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
+                             ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
+            // segments with three or more exponents go to the queue pixel by pixel
+            const bool slow = inside && !two;
+            const unsigned want = __ballot_sync(0xffffffffu, slow);
+            uint32_t* qe = nullptr;
+            if (want) {
+                if (st.queued + __popc(want) > 32) fit_drain(st, bins, lane);
+                qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+            }
+            // channel by channel: x = 16 S* pairs, then the sums of the odd
+            // pixels (by mask) and of all pixels
+            RunAcc pe, po;
+            uint32_t k16[4];
+            mask16(olo, ohi, k16);
+            const uint32_t ones[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint32_t X[4];
+                gf_pairs(fit_row(ring[a].S[c], own, offl, offr), fit_row(ring[b].S[c], own, offl, offr),
+                         fit_row(ring[c2].S[c], own, offl, offr), gf, X);
+                const uint2 mv = *reinterpret_cast<const uint2*>(&ms.M[c][8 * lane]);
+                chan_sums(X, mv.x, mv.y, olo, ohi, k16, po, c);
+                chan_sums(X, mv.x, mv.y, 0xFFFFFFFFu, 0xFFFFFFFFu, ones, pe, c);
+                if (slow) {
+                    qe[2 + c] = mv.x;
+                    qe[5 + c] = mv.y;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[k];
+                }
+            }
+            po.n = (uint32_t)(__popc(olo) + __popc(ohi)) >> 3;
+            pe.n = 8u;
+            run_minus(pe, po);
+            if (!inside || slow) pe.n = po.n = 0u;
+            if (want) {
+                if (slow) {
+                    qe[0] = elo;
+                    qe[1] = ehi;
+                    qe[20] = 8u;
+                }
+                __syncwarp();
+                st.queued += __popc(want);
+            }
+            const bool fe = pe.n != 0u && (int)Ee != st.even.E && st.even.n != 0u;
+            const bool fo = po.n != 0u && (int)Eo != st.odd.E && st.odd.n != 0u;
+            enqueue_run(st, fe, st.even, bins, lane);
+            enqueue_run(st, fo, st.odd, bins, lane);
+            if (pe.n != 0u) {
+                if ((int)Ee != st.even.E) run_reset(st.even, (int)Ee);
+                run_merge(st.even, pe);
+            }
+            if (po.n != 0u) {
+                if ((int)Eo != st.odd.E) run_reset(st.odd, (int)Eo);
+                run_merge(st.odd, po);
+            }
+            // S item j (slot a) has left the window: release it and refill
+            par ^= 1u << a;
+            ++released;
+            a = b;
+            b = c2;
+            __syncwarp();
+            refill();
+        }
+        if (!ok) break;
+        // the last two S items of the task; every run ends with its task
+        // (bounded: a run holds at most 8 * kMaxStripRows pixels)
+        par ^= (1u << a) | (1u << b);
+        released += 2;
+        c_slot = b + 1 == kFitSlots ? 0 : b + 1;
+        warp_flush(st.even, bins, lane);
+        warp_flush(st.odd, bins, lane);
+        run_reset(st.even, -1);
+        run_reset(st.odd, -1);
+        __syncwarp();
+        refill();
+        C = Cn;
+        c_valid = n_valid;
+        n_valid = c_valid && Cn.next();
+    }
+    if (!ok) {
+        // a copy did not arrive in time: give what is in flight a bounded wait
+        // and stop (each unreleased S item has a slot of its own; the M / E
+        // copy of row q + 1 may be in flight too)
+        int s = p_slot;
+        for (int g = issued - 1; g >= released; --g) {
+            s = s == 0 ? kFitSlots - 1 : s - 1;
+            mbar_wait(smem_addr(&bars[s]), (par >> s) & 1u, &g_slrme_status, 1 << 10);
+        }
+        mbar_wait(smem_addr(&me_bars[q & 1]), (uint32_t)(q >> 1) & 1u, &g_slrme_status, 1 << 10);
+        mbar_wait(smem_addr(&me_bars[(q + 1) & 1]), (uint32_t)((q + 1) >> 1) & 1u, &g_slrme_status, 1 << 10);
+    } else {
+        fit_drain(st, bins, lane);
+    }
+    __syncthreads();
+    bins_to_global(bins, gbins, false);
+}
+
+int launch_fit_tma(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
+                   unsigned long long* bins, cudaStream_t s) {
+    static bool attr_set[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("fit device");
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_fit_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFitSmem) !=
+            cudaSuccess)
+            return cuda_status("fit smem attribute");
+        attr_set[dev] = true;
+    }
+    // every warp gets at least 4 rows; at most 2 CTAs of 8 warps per SM
+    const int64_t total_rows = (int64_t)((w + kStripCols - 1) / kStripCols) * h;
+    int64_t warps = (total_rows + 3) / 4;
+    const int64_t cap = (int64_t)geometry().sms * 2 * kFitWarps;
+    if (warps > cap) warps = cap;
+    const int64_t g = (warps + kFitWarps - 1) / kFitWarps;
+    k_fit_tma<<<(unsigned)(g < 1 ? 1 : g), kFitWarps * 32, kFitSmem, s>>>(s3, m3, e, h, w, gf_on, total_rows, bins,
+                                                                            kMaxSpins);
+    return cuda_status("slr_fit launch");
 }
 
 int strip_ctas(int64_t cta_tasks, int per_sm) {
@@ -1253,8 +1508,7 @@ int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, in
                           ((uintptr_t)e % 8 == 0);
         int st;
         if (tma_eligible(w, {s3, m3, e})) {
-            const TmaImage im{s3, m3, e, nullptr, nullptr, nullptr, h, w, gf_on != 0};
-            st = launch_tma<TmaMode::kFit>(im, nullptr, nullptr, reinterpret_cast<unsigned long long*>(bin_sums), s);
+            st = launch_fit_tma(s3, m3, e, h, w, gf_on, reinterpret_cast<unsigned long long*>(bin_sums), s);
         } else {
             const StripLaunch L = strip_launch(h, w, 2);
             k_fit<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
@@ -1273,7 +1527,7 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
                       ((uintptr_t)e % 8 == 0);
     if (tma_eligible(w, {s3, m3, e, r3})) {
         const TmaImage im{s3, m3, e, nullptr, r3, nullptr, h, w, gf_on != 0};
-        return launch_tma<TmaMode::kResidual>(im, params, hist, nullptr, s);
+        return launch_tma<TmaMode::kResidual>(im, params, hist, s);
     }
     const StripLaunch L = strip_launch(h, w, 2);
     k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
@@ -1285,7 +1539,7 @@ int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
     if (tma_eligible(w, {s3, e, r3, rgbe_out})) {
         const TmaImage im{s3, nullptr, e, r3, nullptr, rgbe_out, h, w, gf_on != 0};
-        return launch_tma<TmaMode::kDecode>(im, params, nullptr, nullptr, s);
+        return launch_tma<TmaMode::kDecode>(im, params, nullptr, s);
     }
     const StripLaunch L = strip_launch(h, w, 2);
     k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
