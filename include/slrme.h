@@ -288,8 +288,12 @@ typedef struct slrme_batch_buffers {
  * tables, per-image statistics and bin sums). */
 size_t slrme_batch_workspace_bytes(int n_images);
 
+/* Most images in one plan (the per-image solve runs as one grid row per image). */
+#define SLRME_BATCH_MAX_IMAGES 65535
+
 /* Lays the images out (sets images[i].px_offset), uploads descriptors and task
- * tables to the workspace with default tiles.  Synchronises `stream`. */
+ * tables to the workspace with default tiles.  Synchronises `stream`.
+ * SLRME_EINVAL for 1 > n_images or n_images > SLRME_BATCH_MAX_IMAGES. */
 int slrme_batch_plan_init(slrme_batch_plan* plan, slrme_batch_image* images, int n_images, void* workspace,
                           slrme_stream_t stream);
 

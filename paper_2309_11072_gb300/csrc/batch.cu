@@ -156,6 +156,10 @@ int slrme_batch_plan_init(slrme_batch_plan* plan, slrme_batch_image* images, int
         set_error("slrme_batch_plan_init: null pointer or no images");
         return SLRME_EINVAL;
     }
+    if (n_images > SLRME_BATCH_MAX_IMAGES) {
+        set_error("slrme_batch_plan_init: %d images, at most %d per plan", n_images, SLRME_BATCH_MAX_IMAGES);
+        return SLRME_EINVAL;
+    }
     if ((uintptr_t)workspace % kSection) {
         set_error("slrme_batch_plan_init: workspace must be 256-byte aligned");
         return SLRME_EINVAL;

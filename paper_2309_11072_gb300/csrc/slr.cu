@@ -184,29 +184,42 @@ __device__ __forceinline__ void run_reset(RunAcc& a, int E) {
     for (int c = 0; c < 3; ++c) a.sx[c] = a.sy[c] = a.sxy[c] = a.sxx[c] = 0;
 }
 
-// Exact 64-bit add into a (lo, hi) pair of 32-bit shared words with native
-// 32-bit atomics: the old low word returned by the atomic tells whether this
-// addition wrapped, and each wrap carries exactly once into the high word.
-__device__ __forceinline__ void add_u64(uint32_t* lo, uint32_t* hi, unsigned long long v) {
-    const uint32_t vl = (uint32_t)v, vh = (uint32_t)(v >> 32);
-    if (vl) {
-        const uint32_t old = atomicAdd(lo, vl);
-        const uint32_t carry = (old + vl) < old ? 1u : 0u;
-        if (vh + carry) atomicAdd(hi, vh + carry);
-    } else if (vh) {
-        atomicAdd(hi, vh);
-    }
-}
+// Bins in shared memory, [E][13] twice: a sum is hi * 2^12 + lo, and every
+// addend v goes in as v mod 2^12 (to lo) and v / 2^12 (to hi) with
+// fire-and-forget shared-memory reductions, so no thread waits for an atomic.
+// Exact while a block adds at most kMaxBlockPixels pixels between flushes to
+// global memory: each addition covers at least one pixel, so lo stays below
+// 2^20 (2^12 - 1) < 2^32, and hi below 2^20 * 4080^2 / 2^12 < 2^32.
+constexpr int64_t kMaxBlockPixels = (int64_t)1 << 20;
+static_assert((unsigned long long)kMaxBlockPixels * 4080ull * 4080ull / 4096ull < (1ull << 32), "hi words overflow");
 
-// Bins in shared memory: low words then high words, [E][13] each.
 struct SmemBins {
     uint32_t lo[kNbin * kNsum];
     uint32_t hi[kNbin * kNsum];
 };
 
-__device__ __forceinline__ void bins_add(SmemBins& B, int E, const unsigned long long (&v)[kNsum]) {
+__device__ __forceinline__ void red_add(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Adds the 13 sums of region E (values below 2^44) to the bins at shared
+// address `bins`.
+__device__ __forceinline__ void bins_add(uint32_t bins, int E, const unsigned long long (&v)[kNsum]) {
+    const uint32_t lo = bins + 4u * (uint32_t)(E * kNsum), hi = lo + 4u * kNbin * kNsum;
 #pragma unroll
-    for (int j = 0; j < kNsum; ++j) add_u64(&B.lo[E * kNsum + j], &B.hi[E * kNsum + j], v[j]);
+    for (int j = 0; j < kNsum; ++j) {
+        red_add(lo + 4u * j, (uint32_t)v[j] & 0xFFFu);
+        red_add(hi + 4u * j, (uint32_t)(v[j] >> 12));
+    }
+}
+
+__device__ __forceinline__ void bins_add32(uint32_t bins, int E, const uint32_t (&v)[kNsum]) {
+    const uint32_t lo = bins + 4u * (uint32_t)(E * kNsum), hi = lo + 4u * kNbin * kNsum;
+#pragma unroll
+    for (int j = 0; j < kNsum; ++j) {
+        red_add(lo + 4u * j, v[j] & 0xFFFu);
+        red_add(hi + 4u * j, v[j] >> 12);
+    }
 }
 
 __device__ __forceinline__ void run_values(const RunAcc& a, unsigned long long (&v)[kNsum]) {
@@ -225,7 +238,7 @@ __device__ __forceinline__ void run_flush(const RunAcc& a, SmemBins& B) {
     if (a.E < 0 || a.n == 0) return;
     unsigned long long v[kNsum];
     run_values(a, v);
-    bins_add(B, a.E, v);
+    bins_add(smem_addr(&B), a.E, v);
 }
 
 // Flush of all lanes' runs at a warp-uniform point: when every non-empty run
@@ -253,7 +266,7 @@ __device__ __forceinline__ void warp_flush(const RunAcc& a, SmemBins& B, int lan
             for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
             v[4 + 4 * c] = q;
         }
-        if (lane == 0) bins_add(B, E0, v);
+        if (lane == 0) bins_add(smem_addr(&B), E0, v);
     } else {
         run_flush(a, B);
     }
@@ -349,21 +362,17 @@ __device__ __forceinline__ void run_feed(RunAcc& run, int E, const RunAcc& part,
 // the odd stride keeps the lanes' accesses on distinct banks.
 constexpr int kQueueStride = 21;
 
-__device__ __forceinline__ void add_u32_exact(SmemBins& B, int idx, uint32_t v) {
-    const uint32_t old = atomicAdd(&B.lo[idx], v);
-    if (old + v < old) atomicAdd(&B.hi[idx], 1u);
-}
-
 // Adds one queued entry to the bins: a flushed run (tag 256 + E; words 0-12
-// hold N and the channel sums in bin order) or a segment, pixel by pixel
-// (tag = pixel count).
-__device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
+// hold N and the channel sums in bin order) or a segment (tag = pixel
+// count), whose pixels are summed in order and added once per stretch of
+// equal exponents.
+__device__ __forceinline__ void drain_entry(const uint32_t* q, uint32_t B) {
     const uint32_t tag = q[20];
+    uint32_t acc[kNsum];
     if (tag >= 256u) {
-        const int base = (int)(tag - 256u) * kNsum;
 #pragma unroll
-        for (int j = 0; j < kNsum; ++j)
-            if (q[j]) add_u32_exact(B, base + j, q[j]);
+        for (int j = 0; j < kNsum; ++j) acc[j] = q[j];
+        bins_add32(B, (int)(tag - 256u), acc);
         return;
     }
     uint32_t elo = q[0], ehi = q[1];
@@ -374,20 +383,28 @@ __device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) X[c][k] = q[8 + 4 * c + k];
     const int cnt = (int)tag;
+    int Ecur = (int)(elo & 255u);
+#pragma unroll
+    for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
 #pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
         const int E = (int)(elo & 255u);
         elo = __funnelshift_r(elo, ehi, 8);
         ehi >>= 8;
-        const int base = E * kNsum;
-        add_u32_exact(B, base, 1u);
+        if (E != Ecur) {
+            bins_add32(B, Ecur, acc);
+#pragma unroll
+            for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
+            Ecur = E;
+        }
+        acc[0] += 1u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
-            add_u32_exact(B, base + 1 + 4 * c, x);
-            add_u32_exact(B, base + 2 + 4 * c, yv);
-            add_u32_exact(B, base + 3 + 4 * c, x * yv);
-            add_u32_exact(B, base + 4 + 4 * c, x * x);
+            acc[1 + 4 * c] += x;
+            acc[2 + 4 * c] += yv;
+            acc[3 + 4 * c] += x * yv;
+            acc[4 + 4 * c] += x * x;
             mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
             mhi[c] >>= 8;
             X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
@@ -396,6 +413,7 @@ __device__ __forceinline__ void drain_entry(const uint32_t* q, SmemBins& B) {
             X[c][3] >>= 16;
         }
     }
+    bins_add32(B, Ecur, acc);
 }
 
 // Per-warp state of the fit: one run per exponent parity (adjacent regions
@@ -408,9 +426,14 @@ struct FitWarp {
     int queued;   // entries in the queue (warp-uniform)
 };
 
-__device__ __forceinline__ void fit_drain(FitWarp& st, SmemBins& bins, int lane) {
-    if (lane < st.queued) drain_entry(st.Q + lane * kQueueStride, bins);
+// Drains `queued` entries of a warp's queue, one per lane.
+__device__ __forceinline__ void drain_queue(const uint32_t* Q, int queued, uint32_t bins, int lane) {
+    if (lane < queued) drain_entry(Q + lane * kQueueStride, bins);
     __syncwarp();
+}
+
+__device__ __forceinline__ void fit_drain(FitWarp& st, SmemBins& bins, int lane) {
+    drain_queue(st.Q, st.queued, smem_addr(&bins), lane);
     st.queued = 0;
 }
 
@@ -519,7 +542,7 @@ __device__ __forceinline__ void bins_clear(SmemBins& bins) {
 // Adds the block's bins to global int64 sums (and clears them when asked).
 __device__ __forceinline__ void bins_to_global(SmemBins& bins, unsigned long long* __restrict__ g, bool clear) {
     for (int i = threadIdx.x; i < kNbin * kNsum; i += blockDim.x) {
-        const unsigned long long v = ((unsigned long long)bins.hi[i] << 32) | bins.lo[i];
+        const unsigned long long v = ((unsigned long long)bins.hi[i] << 12) + bins.lo[i];
         if (v) {
             atomicAdd(g + i, v);
             if (clear) bins.lo[i] = bins.hi[i] = 0u;
@@ -627,10 +650,11 @@ __device__ __forceinline__ double i128_to_f64(__int128 v) {
     return neg ? -r : r;
 }
 
-// Slope and intercept of every (channel, region) of one image from its sums
-// (768 threads: channel = thread / 256, region E = thread % 256).
-__device__ __forceinline__ void solve_image(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
-    const int c = threadIdx.x >> 8, E = threadIdx.x & 255;
+// Slope and intercept of one (channel c, region E) of an image from its sums.
+// FP64 work: a one-block solve would be bound by one SM's FP64 units, so the
+// 768 solves of an image are spread over 24 warps (blocks of 32 threads).
+__device__ __forceinline__ void solve_one(const int64_t* __restrict__ sums, slrme_params* __restrict__ P, int c,
+                                          int E) {
     const int64_t* s = sums + E * kNsum;
     const int64_t N = s[0];
     float a = 0.0f, b = 0.0f;
@@ -648,22 +672,36 @@ __device__ __forceinline__ void solve_image(const int64_t* __restrict__ sums, sl
     }
     P->a[c][E] = a;
     P->b[c][E] = b;
-    const int used = __syncthreads_count(c == 0 && N > 0);
     if (c == 0) P->n[E] = (int32_t)N;
-    if (threadIdx.x == 0) {
-        P->n_used = used;
-        P->reserved[0] = P->reserved[1] = P->reserved[2] = 0;
+}
+
+// Block b (32 threads) of an image solves channel b / 8, regions 32 (b % 8) ..
+// + 31; block 0 also counts the used regions.
+__device__ __forceinline__ void solve_block(const int64_t* __restrict__ sums, slrme_params* __restrict__ P, int b) {
+    const int lane = threadIdx.x;
+    solve_one(sums, P, b >> 3, ((b & 7) << 5) + lane);
+    if (b == 0) {
+        int used = 0;
+#pragma unroll
+        for (int k = 0; k < kNbin / 32; ++k) used += __popc(__ballot_sync(0xffffffffu, sums[(32 * k + lane) * kNsum] > 0));
+        if (lane == 0) {
+            P->n_used = used;
+            P->reserved[0] = P->reserved[1] = P->reserved[2] = 0;
+        }
     }
 }
 
-__global__ void __launch_bounds__(768) k_solve(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
-    solve_image(sums, P);
+constexpr int kSolveBlocks = 3 * kNbin / 32;
+
+__global__ void __launch_bounds__(32) k_solve(const int64_t* __restrict__ sums, slrme_params* __restrict__ P) {
+    solve_block(sums, P, blockIdx.x);
 }
 
-// one block per image of a batch
-__global__ void __launch_bounds__(768) k_solve_batch(const unsigned long long* __restrict__ sums,
-                                                      slrme_params* __restrict__ P) {
-    solve_image(reinterpret_cast<const int64_t*>(sums) + (int64_t)blockIdx.x * kNbin * kNsum, P + blockIdx.x);
+// grid (kSolveBlocks, images)
+__global__ void __launch_bounds__(32) k_solve_batch(const unsigned long long* __restrict__ sums,
+                                                     slrme_params* __restrict__ P) {
+    solve_block(reinterpret_cast<const int64_t*>(sums) + (int64_t)blockIdx.y * kNbin * kNsum, P + blockIdx.y,
+                blockIdx.x);
 }
 
 // ====================================================================== residual
@@ -1186,14 +1224,14 @@ int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, cudaSt
 // strip.  Each warp streams its rows through two rings of shared-memory
 // slots filled by 1-D bulk copies that complete on the slot's mbarrier: S
 // rows of the three planes with 16 halo columns (row j of a task needs S rows
-// j - 1, j, j + 1) and, one row ahead, the M and E row segments.  A run that
+// j - 1, j, j + 1) and, up to two rows ahead, the M and E row segments.  A run that
 // has to leave its accumulator inside a strip goes to the warp's queue, with
 // the segments that hold three or more exponents, and the warp drains the
 // queue 32 entries at a time.
 
 constexpr int kFitWarps = 8;
-constexpr int kFitSlots = 6;     // S rows
-constexpr int kMeSlots = 2;      // M / E rows
+constexpr int kFitSlots = 5;     // S rows
+constexpr int kMeSlots = 3;      // M / E rows
 
 struct FitSlot {
     uint8_t S[3][kSW];
@@ -1311,17 +1349,32 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
     st.Q = queue + warp * 32 * kQueueStride;
     st.queued = 0;
 
-    // consumer: current task, the next one (for the M / E copy a row ahead),
-    // slot of the task's first S item, the expected phase parity of every S
-    // slot, and the warp's row count q (M / E slot q % 2, parity (q / 2) % 2)
+    // producer of M / E rows: the warp's rows one by one, up to kMeSlots - 1
+    // rows ahead of the row being processed
+    RowRange MP{r0, r1, h, 0, 0, 0};
+    bool m_valid = MP.next();
+    int mj = 0, m_slot = 0, m_issued = 0;
+    auto refill_me = [&](int q_done) {
+        while (m_valid && m_issued < q_done + kMeSlots) {
+            issue_me(m3, e, n, w, MP.y0 + mj, MP.xs, me[m_slot], smem_addr(&me_bars[m_slot]), lane);
+            ++m_issued;
+            m_slot = m_slot + 1 == kMeSlots ? 0 : m_slot + 1;
+            if (++mj == MP.rows) {
+                mj = 0;
+                m_valid = MP.next();
+            }
+        }
+    };
+
+    // consumer: current task, slot of its first S item, the expected phase
+    // parity of every S and M / E slot, the warp's row count q and the
+    // M / E slot of row q
     RowRange C{r0, r1, h, 0, 0, 0};
     bool c_valid = C.next();
-    RowRange Cn = C;
-    bool n_valid = c_valid && Cn.next();
-    int c_slot = 0, q = 0;
-    uint32_t par = 0u;
+    int c_slot = 0, q = 0, mc = 0;
+    uint32_t par = 0u, mpar = 0u;
     bool ok = true;
-    if (c_valid) issue_me(m3, e, n, w, C.y0, C.xs, me[0], smem_addr(&me_bars[0]), lane);
+    refill_me(0);
     refill();
 
     while (c_valid && ok) {
@@ -1335,15 +1388,10 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
              mbar_wait(smem_addr(&bars[b]), (par >> b) & 1u, &g_slrme_status, max_spins);
         for (int j = 0; j < C.rows && ok; ++j, ++q) {
             const int c2 = b + 1 == kFitSlots ? 0 : b + 1;
-            // M / E of the next row (this task's, else the next task's first)
-            if (j + 1 < C.rows)
-                issue_me(m3, e, n, w, C.y0 + j + 1, C.xs, me[(q + 1) & 1], smem_addr(&me_bars[(q + 1) & 1]), lane);
-            else if (n_valid)
-                issue_me(m3, e, n, w, Cn.y0, Cn.xs, me[(q + 1) & 1], smem_addr(&me_bars[(q + 1) & 1]), lane);
             ok = mbar_wait(smem_addr(&bars[c2]), (par >> c2) & 1u, &g_slrme_status, max_spins) &&
-                 mbar_wait(smem_addr(&me_bars[q & 1]), (uint32_t)(q >> 1) & 1u, &g_slrme_status, max_spins);
+                 mbar_wait(smem_addr(&me_bars[mc]), (mpar >> mc) & 1u, &g_slrme_status, max_spins);
             if (!ok) break;
-            const MeSlot& ms = me[q & 1];
+            const MeSlot& ms = me[mc];
             const uint2 ev = *reinterpret_cast<const uint2*>(&ms.E[8 * lane]);
             const uint32_t elo = ev.x, ehi = ev.y;
             // byte masks of the odd-exponent pixels and the two exponents
@@ -1353,20 +1401,29 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
             const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 && ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
                              ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
                              ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
-            // segments with three or more exponents go to the queue pixel by pixel
+            // at most one even and one odd exponent: the odd pixels join the
+            // odd run, the rest the even run; other segments go to the queue
             const bool slow = inside && !two;
+            const bool take = inside && two;
+            const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
+            const uint32_t pe_n = take ? 8u - po_n : 0u;
+            // a run whose region changes leaves its accumulator first
+            enqueue_run(st, pe_n != 0u && (int)Ee != st.even.E && st.even.n != 0u, st.even, bins, lane);
+            enqueue_run(st, po_n != 0u && (int)Eo != st.odd.E && st.odd.n != 0u, st.odd, bins, lane);
+            if (pe_n != 0u && (int)Ee != st.even.E) run_reset(st.even, (int)Ee);
+            if (po_n != 0u && (int)Eo != st.odd.E) run_reset(st.odd, (int)Eo);
             const unsigned want = __ballot_sync(0xffffffffu, slow);
             uint32_t* qe = nullptr;
             if (want) {
                 if (st.queued + __popc(want) > 32) fit_drain(st, bins, lane);
                 qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
             }
-            // channel by channel: x = 16 S* pairs, then the sums of the odd
-            // pixels (by mask) and of all pixels
-            RunAcc pe, po;
+            // channel by channel: x = 16 S* pairs, the sums of the odd pixels
+            // (by mask) and of all pixels, added straight to the two runs
             uint32_t k16[4];
             mask16(olo, ohi, k16);
             const uint32_t ones[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+            RunAcc po, pa;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 uint32_t X[4];
@@ -1374,7 +1431,17 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
                          fit_row(ring[c2].S[c], own, offl, offr), gf, X);
                 const uint2 mv = *reinterpret_cast<const uint2*>(&ms.M[c][8 * lane]);
                 chan_sums(X, mv.x, mv.y, olo, ohi, k16, po, c);
-                chan_sums(X, mv.x, mv.y, 0xFFFFFFFFu, 0xFFFFFFFFu, ones, pe, c);
+                chan_sums(X, mv.x, mv.y, 0xFFFFFFFFu, 0xFFFFFFFFu, ones, pa, c);
+                if (take) {
+                    st.odd.sx[c] += po.sx[c];
+                    st.odd.sy[c] += po.sy[c];
+                    st.odd.sxy[c] += po.sxy[c];
+                    st.odd.sxx[c] += po.sxx[c];
+                    st.even.sx[c] += pa.sx[c] - po.sx[c];
+                    st.even.sy[c] += pa.sy[c] - po.sy[c];
+                    st.even.sxy[c] += pa.sxy[c] - po.sxy[c];
+                    st.even.sxx[c] += pa.sxx[c] - po.sxx[c];
+                }
                 if (slow) {
                     qe[2 + c] = mv.x;
                     qe[5 + c] = mv.y;
@@ -1382,10 +1449,8 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
                     for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[k];
                 }
             }
-            po.n = (uint32_t)(__popc(olo) + __popc(ohi)) >> 3;
-            pe.n = 8u;
-            run_minus(pe, po);
-            if (!inside || slow) pe.n = po.n = 0u;
+            st.odd.n += po_n;
+            st.even.n += pe_n;
             if (want) {
                 if (slow) {
                     qe[0] = elo;
@@ -1395,24 +1460,15 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
                 __syncwarp();
                 st.queued += __popc(want);
             }
-            const bool fe = pe.n != 0u && (int)Ee != st.even.E && st.even.n != 0u;
-            const bool fo = po.n != 0u && (int)Eo != st.odd.E && st.odd.n != 0u;
-            enqueue_run(st, fe, st.even, bins, lane);
-            enqueue_run(st, fo, st.odd, bins, lane);
-            if (pe.n != 0u) {
-                if ((int)Ee != st.even.E) run_reset(st.even, (int)Ee);
-                run_merge(st.even, pe);
-            }
-            if (po.n != 0u) {
-                if ((int)Eo != st.odd.E) run_reset(st.odd, (int)Eo);
-                run_merge(st.odd, po);
-            }
-            // S item j (slot a) has left the window: release it and refill
+            // S item j (slot a) and the M / E of row q are done: release and refill
             par ^= 1u << a;
             ++released;
             a = b;
             b = c2;
+            mpar ^= 1u << mc;
+            mc = mc + 1 == kMeSlots ? 0 : mc + 1;
             __syncwarp();
+            refill_me(q + 1);
             refill();
         }
         if (!ok) break;
@@ -1427,21 +1483,21 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
         run_reset(st.odd, -1);
         __syncwarp();
         refill();
-        C = Cn;
-        c_valid = n_valid;
-        n_valid = c_valid && Cn.next();
+        c_valid = C.next();
     }
     if (!ok) {
         // a copy did not arrive in time: give what is in flight a bounded wait
-        // and stop (each unreleased S item has a slot of its own; the M / E
-        // copy of row q + 1 may be in flight too)
+        // and stop (each unreleased item has a slot of its own)
         int s = p_slot;
         for (int g = issued - 1; g >= released; --g) {
             s = s == 0 ? kFitSlots - 1 : s - 1;
             mbar_wait(smem_addr(&bars[s]), (par >> s) & 1u, &g_slrme_status, 1 << 10);
         }
-        mbar_wait(smem_addr(&me_bars[q & 1]), (uint32_t)(q >> 1) & 1u, &g_slrme_status, 1 << 10);
-        mbar_wait(smem_addr(&me_bars[(q + 1) & 1]), (uint32_t)((q + 1) >> 1) & 1u, &g_slrme_status, 1 << 10);
+        s = m_slot;
+        for (int g = m_issued - 1; g >= q; --g) {
+            s = s == 0 ? kMeSlots - 1 : s - 1;
+            mbar_wait(smem_addr(&me_bars[s]), (mpar >> s) & 1u, &g_slrme_status, 1 << 10);
+        }
     } else {
         fit_drain(st, bins, lane);
     }
@@ -1460,11 +1516,15 @@ int launch_fit_tma(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h
             return cuda_status("fit smem attribute");
         attr_set[dev] = true;
     }
-    // every warp gets at least 4 rows; at most 2 CTAs of 8 warps per SM
+    // every warp gets at least 4 rows; at most 2 CTAs of 8 warps per SM,
+    // unless a block would then add more than kMaxBlockPixels pixels (a warp
+    // gets at most ceil(total_rows / warps) rows of at most 256 pixels)
     const int64_t total_rows = (int64_t)((w + kStripCols - 1) / kStripCols) * h;
     int64_t warps = (total_rows + 3) / 4;
     const int64_t cap = (int64_t)geometry().sms * 2 * kFitWarps;
     if (warps > cap) warps = cap;
+    const int64_t rows_max = kMaxBlockPixels / ((int64_t)kFitWarps * kStripCols);
+    if (warps < (total_rows + rows_max - 1) / rows_max) warps = (total_rows + rows_max - 1) / rows_max;
     const int64_t g = (warps + kFitWarps - 1) / kFitWarps;
     k_fit_tma<<<(unsigned)(g < 1 ? 1 : g), kFitWarps * 32, kFitSmem, s>>>(s3, m3, e, h, w, gf_on, total_rows, bins,
                                                                             kMaxSpins);
@@ -1496,6 +1556,19 @@ StripLaunch strip_launch(int h, int w, int per_sm) {
     return StripLaunch{rows, (int)(blocks < 1 ? 1 : blocks)};
 }
 
+// Blocks for the grid-stride strip fit: each block may add at most
+// kMaxBlockPixels pixels to its bins, and a warp of a grid of `blocks` gets at
+// most ceil(tasks / (kWarps blocks)) strips of rows x 256 pixels.
+int64_t fit_strips_per_warp(int rows) { return kMaxBlockPixels / ((int64_t)kWarps * rows * kStripCols); }
+
+int fit_strip_blocks(const StripLaunch& L, int h, int w) {
+    const int64_t cols = (w + kStripCols - 1) / kStripCols;
+    const int64_t tasks = (int64_t)((h + L.rows - 1) / L.rows) * cols;
+    const int64_t per = kWarps * fit_strips_per_warp(L.rows);
+    const int64_t need = (tasks + per - 1) / per;
+    return (int)(need > L.blocks ? need : L.blocks);
+}
+
 }  // namespace
 
 int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on, int64_t* bin_sums,
@@ -1511,13 +1584,13 @@ int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, in
             st = launch_fit_tma(s3, m3, e, h, w, gf_on, reinterpret_cast<unsigned long long*>(bin_sums), s);
         } else {
             const StripLaunch L = strip_launch(h, w, 2);
-            k_fit<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
-                                                reinterpret_cast<unsigned long long*>(bin_sums));
+            k_fit<<<fit_strip_blocks(L, h, w), kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
+                                                                 reinterpret_cast<unsigned long long*>(bin_sums));
             st = cuda_status("slr_fit launch");
         }
         if (st != SLRME_OK) return st;
     }
-    k_solve<<<1, 768, 0, s>>>(bin_sums, params);
+    k_solve<<<kSolveBlocks, 32, 0, s>>>(bin_sums, params);
     return cuda_status("slr_fit solve launch");
 }
 
@@ -1554,12 +1627,15 @@ int launch_fit_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, cons
     if (cudaMemsetAsync(B.sums, 0, sizeof(unsigned long long) * kNbin * kNsum * (size_t)B.n, s) != cudaSuccess)
         return cuda_status("batch fit memset");
     if (cta_tasks > 0) {
-        k_fit_batch<<<strip_ctas(cta_tasks, ctas_per_sm < 2 ? ctas_per_sm : 2), kThreads, 0, s>>>(B, cta_tasks, s3,
-                                                                                                 m3, e);
+        // each block adds at most kMaxBlockPixels pixels (a CTA task is kWarps strips)
+        const int64_t per = fit_strips_per_warp(B.strip_rows);
+        int64_t blocks = strip_ctas(cta_tasks, ctas_per_sm < 2 ? ctas_per_sm : 2);
+        if (blocks < (cta_tasks + per - 1) / per) blocks = (cta_tasks + per - 1) / per;
+        k_fit_batch<<<(unsigned)blocks, kThreads, 0, s>>>(B, cta_tasks, s3, m3, e);
         const int st = cuda_status("batch fit launch");
         if (st != SLRME_OK) return st;
     }
-    k_solve_batch<<<B.n, 768, 0, s>>>(B.sums, params);
+    k_solve_batch<<<dim3(kSolveBlocks, B.n), 32, 0, s>>>(B.sums, params);
     return cuda_status("batch solve launch");
 }
 
@@ -1664,11 +1740,11 @@ extern "C" int slr_fit_noalloc(const uint8_t* s_dec3, const uint8_t* m3, const u
         const bool fast = (w % 8 == 0) && ((uintptr_t)s_dec3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                           ((uintptr_t)e % 8 == 0);
         const StripLaunch L = strip_launch(h, w, 2);
-        k_fit<<<L.blocks, kThreads, 0, s>>>(s_dec3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, bins);
+        k_fit<<<fit_strip_blocks(L, h, w), kThreads, 0, s>>>(s_dec3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, bins);
         st = cuda_status("slr_fit_noalloc launch");
         if (st != SLRME_OK) return st;
     }
-    k_solve<<<1, 768, 0, s>>>(reinterpret_cast<const int64_t*>(bins), params);
+    k_solve<<<kSolveBlocks, 32, 0, s>>>(reinterpret_cast<const int64_t*>(bins), params);
     return cuda_status("slr_fit_noalloc solve launch");
 }
 

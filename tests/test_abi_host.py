@@ -125,4 +125,6 @@ def test_batch_struct_layouts_and_argument_checks():
     assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 2, 0x100000, None) == -1
     assert "quality" in native.last_error()
     assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 2, 0x100010, None) == -1   # unaligned
+    assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 65536, 0x100000, None) == -1
+    assert "at most 65535" in native.last_error()
     assert L.slrme_batch_graph_launch(C.addressof(plan), None) == -1
