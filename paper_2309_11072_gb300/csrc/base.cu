@@ -69,29 +69,22 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8]) {
     x[3] = E3 + O3; x[4] = E3 - O3;
 }
 
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // 8-bit display value: #{k in 1..255 : v >= gamma[k]} for the increasing
-// threshold table.  A hardware-approximate 255 v^(1/2.2) seeds k; the two
-// loops then move k to the unique value with gamma[k] <= v < gamma[k+1]
-// (k = 0 below gamma[1], k = 255 at or above gamma[255]), so the result is
-// exactly the table count whatever the seed's error.
-__device__ __forceinline__ int gamma_code(float v, const float* g) {
-    const float seed = 255.0f * ex2_approx(lg2_approx(v) * (1.0f / 2.2f)) + 0.5f;
-    int k = seed >= 255.0f ? 255 : (seed > 0.0f ? (int)seed : 0);
-    while (k < 255 && v >= g[k + 1]) ++k;
-    while (k > 0 && v < g[k]) --k;
-    return k;
+// threshold table (v >= 0).  Below 2^-20 (< gamma[1]) it is 0, from 1 up
+// (> gamma[255]) 255; in between the bucket of v (exponent and top 8 mantissa
+// bits) holds at most one threshold, so its start count plus one comparison
+// with the next threshold is the count.  `g` has g[256] = +inf.
+__device__ __forceinline__ int gamma_code(float v, const float* g, const uint8_t* start) {
+    const uint32_t bits = __float_as_uint(v);
+    if (bits < 0x35800000u) return 0;        // v < 2^-20
+    if (bits >= 0x3F800000u) return 255;     // v >= 1
+    const int k = start[(bits - 0x35800000u) >> 15];
+    return k + (v >= g[k + 1] ? 1 : 0);
+}
+
+// float(v) for 0 <= v < 2^23, exactly (the 2^23 bias).
+__device__ __forceinline__ float small_int_to_float(int v) {
+    return __fsub_rn(__int_as_float(0x4B000000 | v), 8388608.0f);
 }
 
 __device__ __forceinline__ void load8(const uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
@@ -126,6 +119,16 @@ __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w
     }
 }
 
+// The threshold table (with g[256] = +inf) and the bucket starts, into
+// shared memory; ends with a block barrier.
+__device__ __forceinline__ void load_gamma(float* gam, uint8_t* gstart) {
+    for (int i = threadIdx.x; i < 257; i += blockDim.x) gam[i] = i < 256 ? __uint_as_float(kGammaBits[i]) : INFINITY;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(kGammaStart);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(gstart);
+    for (int i = threadIdx.x; i < (int)sizeof(kGammaStart) / 4; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
 // Key and quantiser state of one image, as a lane needs it.
 struct BaseKey {
     int J;
@@ -150,7 +153,8 @@ __device__ __forceinline__ void base_key(const int64_t* __restrict__ stats, cons
 // One band task of one image (all 32 lanes): rows y0 .. y0+7, columns xb .. xb+31.
 __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h, int w,
                                           bool fast, int y0, int xb, int lane, const BaseKey& K, const float* gam,
-                                          int* T, uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3) {
+                                          const uint8_t* gstart, int* T, uint8_t* __restrict__ s3,
+                                          uint8_t* __restrict__ sdr3) {
     const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
     const int64_t n = (int64_t)h * w;
     const int J = K.J;
@@ -177,12 +181,12 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
             int d = E - 137 - J;
             d = d < -100 ? -100 : (d > 100 ? 100 : d);
             const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
-            const float L = __fmul_rn(__fmul_rn(kr, __int2float_rn(yq)), p2d);
+            const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float(yq)), p2d);
             const float den = __fadd_rn(1.0f, L);
             const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
-            sdr[0][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mr[i] + 1)), gam);
-            sdr[1][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mg[i] + 1)), gam);
-            sdr[2][i] = gamma_code(__fmul_rn(H, __int2float_rn(2 * mb[i] + 1)), gam);
+            sdr[0][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr[i] + 1)), gam, gstart);
+            sdr[1][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg[i] + 1)), gam, gstart);
+            sdr[2][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb[i] + 1)), gam, gstart);
         }
         if (sdr3 && x0 < w) {
 #pragma unroll
@@ -251,28 +255,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict_
                                                       int h, int w, const int64_t* __restrict__ lum_stats,
                                                       uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3,
                                                       int fast_io, const QuantTable QT) {
-    __shared__ float gam[256];
+    __shared__ float gam[257];
+    __shared__ __align__(16) uint8_t gstart[sizeof(kGammaStart)];
     __shared__ int tile[kWarps][kTileWords];
-    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = __uint_as_float(kGammaBits[i]);
-    __syncthreads();
+    load_gamma(gam, gstart);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BaseKey K;
     base_key(lum_stats, QT, lane & 7, K);
     const int cols = (w + 31) >> 5;
     const int64_t tasks = (int64_t)((h + 7) >> 3) * cols;
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
-        base_band(m3, e, h, w, fast_io != 0, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, tile[warp], s3,
-                  sdr3);
+        base_band(m3, e, h, w, fast_io != 0, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, gstart,
+                  tile[warp], s3, sdr3);
 }
 
 // Batch: CTA tasks of 8 band tasks of one image, contiguous ranges per CTA.
 __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, int64_t cta_tasks,
                                                             const uint8_t* __restrict__ m3b,
                                                             const uint8_t* __restrict__ eb, uint8_t* __restrict__ s3b) {
-    __shared__ float gam[256];
+    __shared__ float gam[257];
+    __shared__ __align__(16) uint8_t gstart[sizeof(kGammaStart)];
     __shared__ int tile[kWarps][kTileWords];
-    for (int i = threadIdx.x; i < 256; i += kThreads) gam[i] = __uint_as_float(kGammaBits[i]);
-    __syncthreads();
+    load_gamma(gam, gstart);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
@@ -294,8 +298,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
         const bool fast = (im.w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
                           ((uintptr_t)s3 % 8 == 0);
         if ((int64_t)im.h * im.w > 0 && t < bands)
-            base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, tile[warp],
-                      s3, nullptr);
+            base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, gstart,
+                      tile[warp], s3, nullptr);
     }
 }
 

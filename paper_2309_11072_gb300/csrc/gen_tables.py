@@ -8,6 +8,11 @@ Tables (all built in float64 and rounded once):
   kGammaBits[k] = float32 bits of ((k - 0.5) / 255)^2.2,  k = 1..255 (k = 0: 0.0)
   kKrBits[r]    = float32 bits of 0.18 * 2^(-r/16),        r = 0..15
   kWrBits[r]    = float32 bits of 1800 * 2^(-r/16),        r = 0..15
+  kGammaStart[b] = #{k in 1..255 : gamma[k] <= start of bucket b}, where
+                  bucket b = 256 (e - 107) + m holds the float32 values with
+                  biased exponent e in 107..126 and top 8 mantissa bits m
+                  (v in [2^-20, 1)); no bucket holds more than one threshold,
+                  so the display code of v is start + (v >= gamma[start + 1]).
 The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
 """
@@ -24,6 +29,17 @@ def main():
     lut = [round(65536.0 * math.log2(2048 + i)) for i in range(2048)]
     gamma = [0] + [f32_bits(((k - 0.5) / 255.0) ** 2.2) for k in range(1, 256)]
     kr = [f32_bits(0.18 * 2.0 ** (-r / 16.0)) for r in range(16)]
+    # buckets of [2^-20, 1) by exponent and top 8 mantissa bits; thresholds as
+    # bit patterns (positive floats order like their bits)
+    assert gamma[1] > (107 << 23) and gamma[255] < (127 << 23)
+    start = []
+    for b in range(20 * 256):
+        lo = (107 << 23) + (b << 15)
+        hi = lo + (1 << 15)
+        k = sum(1 for t in gamma[1:] if t <= lo)
+        inside = [t for t in gamma[1:] if lo < t < hi]
+        assert len(inside) <= 1 and (k == 255 or k + 2 > 255 or gamma[k + 2] >= hi), b
+        start.append(k)
     wr = [f32_bits(1800.0 * 2.0 ** (-r / 16.0)) for r in range(16)]
 
     def arr(ctype, name, vals, fmt, per_line):
@@ -38,6 +54,7 @@ def main():
     out.append(arr("uint32_t", "kGammaBits", gamma, lambda v: f"0x{v:08x}u", 8))
     out.append(arr("uint32_t", "kKrBits", kr, lambda v: f"0x{v:08x}u", 8))
     out.append(arr("uint32_t", "kWrBits", wr, lambda v: f"0x{v:08x}u", 8))
+    out.append(arr("uint8_t", "kGammaStart", start, str, 24))
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tables.inc")
     with open(path, "w") as fh:
         fh.write("\n".join(out))
