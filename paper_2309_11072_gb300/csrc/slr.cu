@@ -941,33 +941,42 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
     }
 }
 
-// ====================================================================== TMA-staged kernels
+// ====================================================================== TMA-staged row pipelines
 //
-// The same computations as k_residual / k_decode for images whose
-// rows are 16-byte aligned (w % 16 == 0, 16-byte aligned planes).  Each warp
-// streams its own strip tasks (256 columns x strip_rows rows) through its own
-// ring of kSlots shared-memory slots: a slot holds one row "item", the S row
-// of all three planes with 16 halo columns on each side (rows clamped to the
-// image) and, for output rows, the M / E (or R / E) row segments.  Lanes
-// issue the item's 1-D bulk copies (cp.async.bulk, completion counted on the
-// slot's mbarrier); output row j of a task needs items j, j+1, j+2, so up to
-// kSlots - 3 items are in flight while a row is computed, and a slot is
-// refilled as soon as its row leaves the 3-row window.  No CTA-wide barrier
-// is involved; data in flight costs shared memory, not registers.
+// For images whose rows are 16-byte aligned (w % 16 == 0, 16-byte aligned
+// planes).  The rows of all 256-column strips are taken in column-major
+// order (strip, row) and cut into one contiguous range per warp, so every
+// warp does the same number of rows to within one; a range becomes tasks of
+// at most kMaxStripRows rows of one strip.  Each warp streams its rows
+// through two rings of shared-memory slots filled by 1-D bulk copies
+// (cp.async.bulk) that complete on the slot's mbarrier: S rows of the three
+// planes with 16 halo columns (row j of a task needs S rows j - 1, j, j + 1,
+// clamped to the image) and, up to two rows ahead, the row's other planes
+// (M and E for the fit and the residual, R and E for the decoder).  No
+// CTA-wide barrier is involved; data in flight costs shared memory, not
+// registers.  Every wait is bounded (see tma.cuh).
 
-constexpr int kSlots = 6;
-constexpr int kSW = 288;         // S row segment: 16 halo + 256 + 16 halo bytes
-constexpr int kTmaWarps = 4;     // warps per CTA (independent pipelines)
+constexpr int kSW = 288;          // S row segment: 16 halo + 256 + 16 halo bytes
+constexpr int kRowWarps = 8;      // warps per CTA (independent pipelines)
+constexpr int kSSlots = 5;        // S rows
+constexpr int kAuxSlots = 3;      // M / E (or R / E) rows
 
-enum class TmaMode { kResidual = 0, kDecode = 1 };
+enum class TmaMode { kResidual = 0, kDecode = 1, kFit = 2 };
+
+struct SRow {
+    uint8_t S[3][kSW];
+};
 
 template <TmaMode MODE>
-struct TmaSlot {
-    static constexpr int kPlanes8 = MODE == TmaMode::kDecode ? 1 : 4;   // M_R, M_G, M_B, E  or  E
-    static constexpr bool kR = MODE == TmaMode::kDecode;                  // R planes (int16)
-    uint8_t S[3][kSW];
-    uint8_t B[kPlanes8][256];
-    int16_t R[kR ? 3 : 1][kR ? 256 : 8];
+struct AuxSlot {                  // fit and residual: M and E
+    uint8_t M[3][kStripCols];
+    uint8_t E[kStripCols];
+};
+
+template <>
+struct AuxSlot<TmaMode::kDecode> {
+    int16_t R[3][kStripCols];
+    uint8_t E[kStripCols];
 };
 
 struct TmaImage {
@@ -980,271 +989,6 @@ struct TmaImage {
     int h, w;
     bool gf;
 };
-
-// Issue the copies of item k of the strip task (y0, rows, xs): the S rows
-// y0 - 1 + k (clamped), and for 1 <= k <= rows the output row y0 + k - 1.
-// Lane 0 announces the byte count first.
-template <TmaMode MODE>
-__device__ __forceinline__ void tma_item(const TmaImage& im, TmaSlot<MODE>& sl, uint32_t bar, int y0, int rows,
-                                         int xs, int k, int lane) {
-    const int64_t n = (int64_t)im.h * im.w;
-    const int padl = xs >= 16 ? 16 : 0;
-    const int s_bytes = min(xs + 256 + 16, im.w) - (xs - padl);
-    const int b_bytes = min(256, im.w - xs);
-    const bool out_row = k >= 1 && k <= rows;
-    constexpr int P8 = TmaSlot<MODE>::kPlanes8;
-    constexpr int NR = TmaSlot<MODE>::kR ? 3 : 0;
-    const uint32_t bytes = 3u * s_bytes + (out_row ? (uint32_t)(P8 * b_bytes + NR * 2 * b_bytes) : 0u);
-    if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
-    __syncwarp();
-    const int ys = min(max(y0 - 1 + k, 0), im.h - 1);
-    if (lane < 3) {
-        tma_load_1d(smem_addr(&sl.S[lane][16 - padl]), im.s3 + lane * n + (int64_t)ys * im.w + xs - padl,
-                    (uint32_t)s_bytes, bar);
-    } else if (out_row && lane < 3 + P8) {
-        const int p = lane - 3;
-        const uint8_t* src = (MODE == TmaMode::kDecode || p == 3) ? im.e : im.m3 + p * n;
-        tma_load_1d(smem_addr(&sl.B[p][0]), src + (int64_t)(y0 + k - 1) * im.w + xs, (uint32_t)b_bytes, bar);
-    } else if (out_row && lane < 3 + P8 + NR) {
-        const int p = lane - 3 - P8;
-        tma_load_1d(smem_addr(&sl.R[p][0]), im.r3_in + p * n + (int64_t)(y0 + k - 1) * im.w + xs,
-                    (uint32_t)(2 * b_bytes), bar);
-    }
-}
-
-// One lane's row segment of S (8 bytes and the two neighbours) from a slot.
-__device__ __forceinline__ Row10 slot_row(const uint8_t* row, int xs, int x0, int w) {
-    Row10 R;
-    const uint2 v = *reinterpret_cast<const uint2*>(row + 16 + (x0 - xs));
-    R.lo = v.x;
-    R.hi = v.y;
-    R.l = row[16 + (x0 > 0 ? x0 - 1 : 0) - xs];
-    R.r = row[16 + (x0 + 8 < w ? x0 + 8 : w - 1) - xs];
-    return R;
-}
-
-// The warp's strip tasks in issue order (the same order they are consumed).
-struct TaskCursor {
-    int64_t t, stride, tasks;
-    int cols, rows_per, h;
-    int y0, rows, xs, k;   // current task and item within it
-    __device__ __forceinline__ bool valid() const { return t < tasks; }
-    __device__ __forceinline__ void load() {
-        if (t < tasks) {
-            y0 = (int)(t / cols) * rows_per;
-            xs = (int)(t % cols) * 256;
-            rows = min(rows_per, h - y0);
-        }
-        k = 0;
-    }
-    __device__ __forceinline__ void next_item() {
-        if (++k == rows + 2) {
-            t += stride;
-            load();
-        }
-    }
-};
-
-template <TmaMode MODE>
-__global__ void __launch_bounds__(kTmaWarps * 32, 3) k_tma(const TmaImage im, const slrme_params* __restrict__ P,
-                                                            uint32_t* __restrict__ ghist, int rows_per,
-                                                            int max_spins) {
-    extern __shared__ __align__(128) char dyn[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    TmaSlot<MODE>* ring = reinterpret_cast<TmaSlot<MODE>*>(dyn) + warp * kSlots;
-    char* tail = dyn + sizeof(TmaSlot<MODE>) * kSlots * kTmaWarps;
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tail) + warp * kSlots;
-    tail += 8 * kSlots * kTmaWarps;
-    float* sa = reinterpret_cast<float*>(tail);                    // residual / decode: parameters
-    float* sb = sa + 3 * kNbin;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(sb + 3 * kNbin);  // residual: histograms
-
-    const int h = im.h, w = im.w;
-    const int64_t n = (int64_t)h * w;
-    load_params(P, sa, sb);
-    if (MODE == TmaMode::kResidual && ghist)
-        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
-    if (lane == 0) {
-        for (int k = 0; k < kSlots; ++k) mbar_init(smem_addr(&bars[k]), 1);
-        fence_async_shared();
-    }
-    __syncthreads();
-
-    const int cols = (w + 255) / 256;
-    const int64_t tasks = (int64_t)((h + rows_per - 1) / rows_per) * cols;
-    const int64_t first = (int64_t)blockIdx.x * kTmaWarps + warp, stride = (int64_t)gridDim.x * kTmaWarps;
-    TaskCursor issue{first, stride, tasks, cols, rows_per, h, 0, 0, 0, 0};
-    issue.load();
-    TaskCursor cons = issue;
-    int64_t g_issue = 0, g_cons = 0;   // items issued / first item of the consumer's current task
-    bool ok = true;
-
-    // keep the ring full: items up to g_lo + kSlots - 1 may be in flight
-    auto refill = [&](int64_t g_lo) {
-        while (issue.valid() && g_issue < g_lo + kSlots) {
-            const int slot = (int)(g_issue % kSlots);
-            fence_async_shared();
-            tma_item<MODE>(im, ring[slot], smem_addr(&bars[slot]), issue.y0, issue.rows, issue.xs, issue.k, lane);
-            ++g_issue;
-            issue.next_item();
-        }
-    };
-    refill(0);
-    while (cons.valid() && ok) {
-        const int y0 = cons.y0, rows = cons.rows, xs = cons.xs;
-        const int x0 = xs + 8 * lane;
-        // the first two items of the task
-        for (int k = 0; k < 2 && ok; ++k)
-            ok = mbar_wait(smem_addr(&bars[(g_cons + k) % kSlots]), (uint32_t)(((g_cons + k) / kSlots) & 1),
-                           &g_slrme_status, max_spins);
-        for (int j = 0; j < rows && ok; ++j) {
-            const int64_t gi = g_cons + j + 2;
-            ok = mbar_wait(smem_addr(&bars[gi % kSlots]), (uint32_t)((gi / kSlots) & 1), &g_slrme_status,
-                           max_spins);
-            if (!ok) break;
-            const TmaSlot<MODE>& s0 = ring[(g_cons + j) % kSlots];
-            const TmaSlot<MODE>& s1 = ring[(g_cons + j + 1) % kSlots];
-            const TmaSlot<MODE>& s2 = ring[gi % kSlots];
-            const int y = y0 + j;
-            uint32_t X[3][4];
-            if (x0 < w) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    gf_pairs(slot_row(s0.S[c], xs, x0, w), slot_row(s1.S[c], xs, x0, w),
-                             slot_row(s2.S[c], xs, x0, w), im.gf, X[c]);
-            }
-            if (MODE == TmaMode::kResidual && x0 < w) {
-                const uint2 ev = *reinterpret_cast<const uint2*>(&s1.B[3][x0 - xs]);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const uint2 mv = *reinterpret_cast<const uint2*>(&s1.B[c][x0 - xs]);
-                    int rr[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
-                        const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
-                        rr[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
-                    }
-                    uint4 v;
-                    v.x = (uint32_t)(rr[0] & 0xFFFF) | ((uint32_t)rr[1] << 16);
-                    v.y = (uint32_t)(rr[2] & 0xFFFF) | ((uint32_t)rr[3] << 16);
-                    v.z = (uint32_t)(rr[4] & 0xFFFF) | ((uint32_t)rr[5] << 16);
-                    v.w = (uint32_t)(rr[6] & 0xFFFF) | ((uint32_t)rr[7] << 16);
-                    *reinterpret_cast<uint4*>(im.r3_out + c * n + (int64_t)y * w + x0) = v;
-                    if (ghist) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
-                    }
-                }
-            }
-            if (MODE == TmaMode::kDecode && x0 < w) {
-                const uint2 ev = *reinterpret_cast<const uint2*>(&s1.B[0][x0 - xs]);
-                uint32_t word[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? ev.x : ev.y, i & 3) << 24;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(&s1.R[c][x0 - xs]);
-                    const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
-                        const int E = (int)(word[i] >> 24);
-                        const int M = rv + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X[c], i));
-                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
-                    }
-                }
-                uint4* o4 = reinterpret_cast<uint4*>(im.out + (int64_t)y * w + x0);
-                o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
-                o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
-            }
-            __syncwarp();          // every lane is done with item g_cons + j
-            refill(g_cons + j + 1);
-        }
-        g_cons += rows + 2;
-        cons.t += cons.stride;
-        cons.load();
-        if (ok) refill(g_cons);
-    }
-    if (!ok) {
-        // a copy did not arrive in time: give what is in flight a bounded wait and stop
-        for (int64_t g = g_cons; g < g_issue; ++g)
-            mbar_wait(smem_addr(&bars[g % kSlots]), (uint32_t)((g / kSlots) & 1), &g_slrme_status, 1 << 10);
-    }
-    if (MODE == TmaMode::kResidual && ghist) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x)
-            if (hist[i]) atomicAdd(ghist + i, hist[i]);
-    }
-}
-
-template <TmaMode MODE>
-constexpr size_t tma_smem_bytes() {
-    return sizeof(TmaSlot<MODE>) * kSlots * kTmaWarps + 8 * kSlots * kTmaWarps + sizeof(float) * 6 * kNbin +
-           sizeof(uint32_t) * 3 * kNres;
-}
-
-bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
-    if (w % 16 != 0) return false;
-    for (const void* p : ptrs)
-        if ((uintptr_t)p % 16 != 0) return false;
-    return true;
-}
-
-template <TmaMode MODE>
-int launch_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, cudaStream_t s) {
-    static bool attr_set[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("tma device");
-    constexpr size_t smem = tma_smem_bytes<MODE>();
-    if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return cuda_status("tma smem attribute");
-        attr_set[dev] = true;
-    }
-    // strip height: the tallest of 16, 8, 4 rows giving about 24 warps of work per SM
-    const int sms = geometry().sms;
-    const int64_t cols = (im.w + 255) / 256;
-    int rows = kMaxStripRows;
-    while (rows > 4 && (int64_t)((im.h + rows - 1) / rows) * cols < (int64_t)sms * 24) rows >>= 1;
-    const int64_t tasks = (int64_t)((im.h + rows - 1) / rows) * cols;
-    int64_t g = (tasks + kTmaWarps - 1) / kTmaWarps;
-    const int64_t cap = (int64_t)sms * 3;
-    if (g > cap) g = cap;
-    k_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kTmaWarps * 32, smem, s>>>(im, P, hist, rows, kMaxSpins);
-    return cuda_status("tma stage launch");
-}
-
-// ====================================================================== TMA-staged fit
-//
-// k_fit_tma: the fit for images whose rows are 16-byte aligned.  The rows of
-// all strips are taken in column-major order (strip, row) and cut into one
-// contiguous range per warp, so every warp does the same number of rows to
-// within one; a range becomes tasks of at most kMaxStripRows rows of one
-// strip.  Each warp streams its rows through two rings of shared-memory
-// slots filled by 1-D bulk copies that complete on the slot's mbarrier: S
-// rows of the three planes with 16 halo columns (row j of a task needs S rows
-// j - 1, j, j + 1) and, up to two rows ahead, the M and E row segments.  A run that
-// has to leave its accumulator inside a strip goes to the warp's queue, with
-// the segments that hold three or more exponents, and the warp drains the
-// queue 32 entries at a time.
-
-constexpr int kFitWarps = 8;
-constexpr int kFitSlots = 5;     // S rows
-constexpr int kMeSlots = 3;      // M / E rows
-
-struct FitSlot {
-    uint8_t S[3][kSW];
-};
-
-struct MeSlot {
-    uint8_t M[3][kStripCols];
-    uint8_t E[kStripCols];
-};
-
-constexpr size_t kFitSmem = (sizeof(FitSlot) * kFitSlots + sizeof(MeSlot) * kMeSlots +
-                             8 * (kFitSlots + kMeSlots)) * kFitWarps +
-                            sizeof(SmemBins) + sizeof(uint32_t) * kFitWarps * 32 * kQueueStride;
 
 // A warp's rows r .. end - 1 in (strip, row) order and its current task.
 struct RowRange {
@@ -1262,10 +1006,18 @@ struct RowRange {
     }
 };
 
+// The warp's range of rows: warp gw of `warps` gets rows
+// [gw total / warps, (gw + 1) total / warps).
+__device__ __forceinline__ RowRange warp_rows(int64_t total_rows, int h, int per_block) {
+    const int64_t warps = (int64_t)gridDim.x * per_block;
+    const int64_t gw = (int64_t)blockIdx.x * per_block + (threadIdx.x >> 5);
+    return RowRange{(int)(gw * total_rows / warps), (int)((gw + 1) * total_rows / warps), h, 0, 0, 0};
+}
+
 // One lane's S row segment from a slot: 8 bytes plus the neighbours at the
 // precomputed offsets (which point at the lane's own edge byte where the
 // image ends, replicating it).
-__device__ __forceinline__ Row10 fit_row(const uint8_t* row, int own, int offl, int offr) {
+__device__ __forceinline__ Row10 seg_row(const uint8_t* row, int own, int offl, int offr) {
     Row10 R;
     const uint2 v = *reinterpret_cast<const uint2*>(row + own);
     R.lo = v.x;
@@ -1275,73 +1027,314 @@ __device__ __forceinline__ Row10 fit_row(const uint8_t* row, int own, int offl, 
     return R;
 }
 
-// Copies the M and E row segments of row y, columns xs .. xs + 255 (lanes 0-3).
-__device__ __forceinline__ void issue_me(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int64_t n,
-                                         int w, int y, int xs, MeSlot& sl, uint32_t bar, int lane) {
-    const int bytes = min(kStripCols, w - xs);
+// Copies S row ys, columns xs - 16 .. xs + 271 (clipped to the image), of the
+// three planes (lanes 0-2).
+__device__ __forceinline__ void issue_s(const TmaImage& im, int64_t n, int ys, int xs, SRow& sl, uint32_t bar,
+                                        int lane) {
+    const int padl = xs >= 16 ? 16 : 0;
+    const int bytes = min(xs + kStripCols + 16, im.w) - (xs - padl);
     fence_async_shared();
-    if (lane == 0) mbar_arrive_expect_tx(bar, 4u * (uint32_t)bytes);
+    if (lane == 0) mbar_arrive_expect_tx(bar, 3u * (uint32_t)bytes);
     __syncwarp();
-    if (lane < 4) {
-        const uint8_t* src = (lane < 3 ? m3 + lane * n : e) + (int64_t)y * w + xs;
-        tma_load_1d(smem_addr(lane < 3 ? &sl.M[lane][0] : &sl.E[0]), src, (uint32_t)bytes, bar);
+    if (lane < 3)
+        tma_load_1d(smem_addr(&sl.S[lane][16 - padl]), im.s3 + lane * n + (int64_t)ys * im.w + xs - padl,
+                    (uint32_t)bytes, bar);
+}
+
+// Copies the other planes of row y, columns xs .. xs + 255 (lanes 0-3).
+template <TmaMode MODE>
+__device__ __forceinline__ void issue_aux(const TmaImage& im, int64_t n, int y, int xs, AuxSlot<MODE>& sl,
+                                          uint32_t bar, int lane) {
+    const int bytes = min(kStripCols, im.w - xs);
+    constexpr int kRb = MODE == TmaMode::kDecode ? 2 : 1;   // bytes per element of planes 0-2
+    fence_async_shared();
+    if (lane == 0) mbar_arrive_expect_tx(bar, (3u * kRb + 1u) * (uint32_t)bytes);
+    __syncwarp();
+    const int64_t off = (int64_t)y * im.w + xs;
+    if (lane < 3) {
+        if constexpr (MODE == TmaMode::kDecode)
+            tma_load_1d(smem_addr(&sl.R[lane][0]), im.r3_in + lane * n + off, 2u * (uint32_t)bytes, bar);
+        else
+            tma_load_1d(smem_addr(&sl.M[lane][0]), im.m3 + lane * n + off, (uint32_t)bytes, bar);
+    } else if (lane == 3) {
+        tma_load_1d(smem_addr(&sl.E[0]), im.e + off, (uint32_t)bytes, bar);
     }
 }
 
-__global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __restrict__ s3,
-                                                                const uint8_t* __restrict__ m3,
-                                                                const uint8_t* __restrict__ e, int h, int w, int gf_on,
-                                                                int64_t total_rows,
-                                                                unsigned long long* __restrict__ gbins, int max_spins) {
-    extern __shared__ __align__(128) char dyn[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    FitSlot* ring = reinterpret_cast<FitSlot*>(dyn) + warp * kFitSlots;
-    char* tail = dyn + sizeof(FitSlot) * kFitSlots * kFitWarps;
-    MeSlot* me = reinterpret_cast<MeSlot*>(tail) + warp * kMeSlots;
-    tail += sizeof(MeSlot) * kMeSlots * kFitWarps;
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kFitSlots + kMeSlots);
-    unsigned long long* me_bars = bars + kFitSlots;
-    tail += 8 * (kFitSlots + kMeSlots) * kFitWarps;
-    SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);
-    uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
+// The two producers and the consumer's bookkeeping of one warp's rings.
+template <TmaMode MODE>
+struct RowPipe {
+    SRow* ring;
+    AuxSlot<MODE>* aux;
+    unsigned long long* bars;    // kSSlots S barriers, then kAuxSlots aux barriers
+    // S producer: task and item (0 .. rows + 1) issued next
+    RowRange P;
+    bool p_valid;
+    int pk, p_slot, issued, released;
+    // aux producer: the warp's rows one by one
+    RowRange A;
+    bool a_valid;
+    int aj, a_slot, a_issued;
+    // consumer: S slot of the task's first item, expected phase parities, the
+    // warp's row count q and the aux slot of row q
+    int c_slot, q, mc;
+    uint32_t par, mpar;
 
-    bins_clear(bins);
-    if (lane == 0) {
-        for (int k = 0; k < kFitSlots + kMeSlots; ++k) mbar_init(smem_addr(&bars[k]), 1);
-        fence_async_shared();
+    __device__ __forceinline__ void init(const RowRange& R) {
+        P = R;
+        p_valid = P.next();
+        pk = p_slot = issued = released = 0;
+        A = R;
+        a_valid = A.next();
+        aj = a_slot = a_issued = 0;
+        c_slot = q = mc = 0;
+        par = mpar = 0u;
     }
-    __syncthreads();
+    __device__ __forceinline__ uint32_t sbar(int s) const { return smem_addr(&bars[s]); }
+    __device__ __forceinline__ uint32_t abar(int s) const { return smem_addr(&bars[kSSlots + s]); }
 
-    const int64_t n = (int64_t)h * w;
-    const bool gf = gf_on != 0;
-    const int64_t warps = (int64_t)gridDim.x * kFitWarps, gw = (int64_t)blockIdx.x * kFitWarps + warp;
-    const int r0 = (int)(gw * total_rows / warps), r1 = (int)((gw + 1) * total_rows / warps);
-
-    // producer of S rows: the task and item (0 .. rows + 1) issued next
-    RowRange P{r0, r1, h, 0, 0, 0};
-    bool p_valid = P.next();
-    int pk = 0, p_slot = 0, issued = 0, released = 0;
-    auto refill = [&]() {
-        while (p_valid && issued < released + kFitSlots) {
-            const int padl = P.xs >= 16 ? 16 : 0;
-            const int s_bytes = min(P.xs + kStripCols + 16, w) - (P.xs - padl);
-            const uint32_t bar = smem_addr(&bars[p_slot]);
-            fence_async_shared();
-            if (lane == 0) mbar_arrive_expect_tx(bar, 3u * (uint32_t)s_bytes);
-            __syncwarp();
-            if (lane < 3) {
-                const int ys = min(max(P.y0 - 1 + pk, 0), h - 1);
-                tma_load_1d(smem_addr(&ring[p_slot].S[lane][16 - padl]),
-                            s3 + lane * n + (int64_t)ys * w + P.xs - padl, (uint32_t)s_bytes, bar);
-            }
+    // keep kSSlots S items in flight or unreleased
+    __device__ __forceinline__ void refill_s(const TmaImage& im, int64_t n, int lane) {
+        while (p_valid && issued < released + kSSlots) {
+            issue_s(im, n, min(max(P.y0 - 1 + pk, 0), im.h - 1), P.xs, ring[p_slot], sbar(p_slot), lane);
             ++issued;
-            p_slot = p_slot + 1 == kFitSlots ? 0 : p_slot + 1;
+            p_slot = p_slot + 1 == kSSlots ? 0 : p_slot + 1;
             if (++pk == P.rows + 2) {
                 pk = 0;
                 p_valid = P.next();
             }
         }
-    };
+    }
+    // keep rows q_done .. q_done + kAuxSlots - 1 in flight or ready
+    __device__ __forceinline__ void refill_aux(const TmaImage& im, int64_t n, int q_done, int lane) {
+        while (a_valid && a_issued < q_done + kAuxSlots) {
+            issue_aux<MODE>(im, n, A.y0 + aj, A.xs, aux[a_slot], abar(a_slot), lane);
+            ++a_issued;
+            a_slot = a_slot + 1 == kAuxSlots ? 0 : a_slot + 1;
+            if (++aj == A.rows) {
+                aj = 0;
+                a_valid = A.next();
+            }
+        }
+    }
+    // after a wait gave up: a bounded wait for every unreleased copy (each
+    // has a slot of its own)
+    __device__ __forceinline__ void drain_in_flight() {
+        int s = p_slot;
+        for (int g = issued - 1; g >= released; --g) {
+            s = s == 0 ? kSSlots - 1 : s - 1;
+            mbar_wait(sbar(s), (par >> s) & 1u, &g_slrme_status, 1 << 10);
+        }
+        s = a_slot;
+        for (int g = a_issued - 1; g >= q; --g) {
+            s = s == 0 ? kAuxSlots - 1 : s - 1;
+            mbar_wait(abar(s), (mpar >> s) & 1u, &g_slrme_status, 1 << 10);
+        }
+    }
+};
+
+template <TmaMode MODE>
+constexpr size_t rows_smem_bytes(int warps) {
+    return (sizeof(SRow) * kSSlots + sizeof(AuxSlot<MODE>) * kAuxSlots + 8 * (kSSlots + kAuxSlots)) * warps;
+}
+
+// k_rows_tma<kResidual>: R = M - M* and histograms; k_rows_tma<kDecode>:
+// M = R + M*, repacked with E.
+template <TmaMode MODE>
+__global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage im, const slrme_params* __restrict__ P,
+                                                                uint32_t* __restrict__ ghist, int64_t total_rows,
+                                                                int max_spins) {
+    extern __shared__ __align__(128) char dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RowPipe<MODE> pp;
+    pp.ring = reinterpret_cast<SRow*>(dyn) + warp * kSSlots;
+    char* tail = dyn + sizeof(SRow) * kSSlots * kRowWarps;
+    pp.aux = reinterpret_cast<AuxSlot<MODE>*>(tail) + warp * kAuxSlots;
+    tail += sizeof(AuxSlot<MODE>) * kAuxSlots * kRowWarps;
+    pp.bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kSSlots + kAuxSlots);
+    tail += 8 * (kSSlots + kAuxSlots) * kRowWarps;
+    float* sa = reinterpret_cast<float*>(tail);
+    float* sb = sa + 3 * kNbin;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(sb + 3 * kNbin);
+
+    load_params(P, sa, sb);
+    if (MODE == TmaMode::kResidual && ghist)
+        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
+    if (lane == 0) {
+        for (int k = 0; k < kSSlots + kAuxSlots; ++k) mbar_init(smem_addr(&pp.bars[k]), 1);
+        fence_async_shared();
+    }
+    __syncthreads();
+
+    const int h = im.h, w = im.w;
+    const int64_t n = (int64_t)h * w;
+    const RowRange R0 = warp_rows(total_rows, h, kRowWarps);
+    pp.init(R0);
+    RowRange C = R0;
+    bool c_valid = C.next();
+    bool ok = true;
+    pp.refill_aux(im, n, 0, lane);
+    pp.refill_s(im, n, lane);
+
+    while (c_valid && ok) {
+        const int x0 = C.xs + 8 * lane;
+        const int own = 16 + 8 * lane;
+        const int offl = x0 == 0 ? own : own - 1;
+        const int offr = x0 + 8 >= w ? own + 7 : own + 8;
+        int a = pp.c_slot, b = a + 1 == kSSlots ? 0 : a + 1;
+        ok = mbar_wait(pp.sbar(a), (pp.par >> a) & 1u, &g_slrme_status, max_spins) &&
+             mbar_wait(pp.sbar(b), (pp.par >> b) & 1u, &g_slrme_status, max_spins);
+        for (int j = 0; j < C.rows && ok; ++j, ++pp.q) {
+            const int c2 = b + 1 == kSSlots ? 0 : b + 1;
+            ok = mbar_wait(pp.sbar(c2), (pp.par >> c2) & 1u, &g_slrme_status, max_spins) &&
+                 mbar_wait(pp.abar(pp.mc), (pp.mpar >> pp.mc) & 1u, &g_slrme_status, max_spins);
+            if (!ok) break;
+            const AuxSlot<MODE>& as = pp.aux[pp.mc];
+            const int y = C.y0 + j;
+            if (x0 < w) {
+                const uint2 ev = *reinterpret_cast<const uint2*>(&as.E[8 * lane]);
+                if constexpr (MODE == TmaMode::kResidual) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        uint32_t X[4];
+                        gf_pairs(seg_row(pp.ring[a].S[c], own, offl, offr), seg_row(pp.ring[b].S[c], own, offl, offr),
+                                 seg_row(pp.ring[c2].S[c], own, offl, offr), im.gf, X);
+                        const uint2 mv = *reinterpret_cast<const uint2*>(&as.M[c][8 * lane]);
+                        int rr[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
+                            const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
+                            rr[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X, i));
+                        }
+                        uint4 v;
+                        v.x = (uint32_t)(rr[0] & 0xFFFF) | ((uint32_t)rr[1] << 16);
+                        v.y = (uint32_t)(rr[2] & 0xFFFF) | ((uint32_t)rr[3] << 16);
+                        v.z = (uint32_t)(rr[4] & 0xFFFF) | ((uint32_t)rr[5] << 16);
+                        v.w = (uint32_t)(rr[6] & 0xFFFF) | ((uint32_t)rr[7] << 16);
+                        *reinterpret_cast<uint4*>(im.r3_out + c * n + (int64_t)y * w + x0) = v;
+                        if (ghist) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
+                        }
+                    }
+                } else {
+                    uint32_t word[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? ev.x : ev.y, i & 3) << 24;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        uint32_t X[4];
+                        gf_pairs(seg_row(pp.ring[a].S[c], own, offl, offr), seg_row(pp.ring[b].S[c], own, offl, offr),
+                                 seg_row(pp.ring[c2].S[c], own, offl, offr), im.gf, X);
+                        const uint4 v = *reinterpret_cast<const uint4*>(&as.R[c][8 * lane]);
+                        const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                            const int E = (int)(word[i] >> 24);
+                            const int M = rv + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X, i));
+                            word[i] |= ((uint32_t)M & 255u) << (8 * c);
+                        }
+                    }
+                    uint4* o4 = reinterpret_cast<uint4*>(im.out + (int64_t)y * w + x0);
+                    o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
+                    o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                }
+            }
+            // S item j (slot a) and the aux row q are done: release and refill
+            pp.par ^= 1u << a;
+            ++pp.released;
+            a = b;
+            b = c2;
+            pp.mpar ^= 1u << pp.mc;
+            pp.mc = pp.mc + 1 == kAuxSlots ? 0 : pp.mc + 1;
+            __syncwarp();
+            pp.refill_aux(im, n, pp.q + 1, lane);
+            pp.refill_s(im, n, lane);
+        }
+        if (!ok) break;
+        // the last two S items of the task
+        pp.par ^= (1u << a) | (1u << b);
+        pp.released += 2;
+        pp.c_slot = b + 1 == kSSlots ? 0 : b + 1;
+        __syncwarp();
+        pp.refill_s(im, n, lane);
+        c_valid = C.next();
+    }
+    if (!ok) pp.drain_in_flight();
+    if (MODE == TmaMode::kResidual && ghist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x)
+            if (hist[i]) atomicAdd(ghist + i, hist[i]);
+    }
+}
+
+bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
+    if (w % 16 != 0) return false;
+    for (const void* p : ptrs)
+        if ((uintptr_t)p % 16 != 0) return false;
+    return true;
+}
+
+template <TmaMode MODE>
+int launch_rows_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, cudaStream_t s) {
+    static bool attr_set[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("row pipeline device");
+    constexpr size_t smem = rows_smem_bytes<MODE>(kRowWarps) + sizeof(float) * 6 * kNbin + sizeof(uint32_t) * 3 * kNres;
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_rows_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return cuda_status("row pipeline smem attribute");
+        attr_set[dev] = true;
+    }
+    // every warp gets at least 4 rows; at most 2 CTAs of 8 warps per SM
+    const int64_t total_rows = (int64_t)((im.w + kStripCols - 1) / kStripCols) * im.h;
+    int64_t warps = (total_rows + 3) / 4;
+    const int64_t cap = (int64_t)geometry().sms * 2 * kRowWarps;
+    if (warps > cap) warps = cap;
+    const int64_t g = (warps + kRowWarps - 1) / kRowWarps;
+    k_rows_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kRowWarps * 32, smem, s>>>(im, P, hist, total_rows, kMaxSpins);
+    return cuda_status(MODE == TmaMode::kResidual ? "residual_encode launch" : "residual_decode launch");
+}
+
+// ====================================================================== TMA-staged fit
+//
+// k_fit_tma: the fit on the row pipelines above (M / E as the other planes).
+// Per lane one run per exponent parity is fed with the SIMD byte-mask sums of
+// its 8-pixel segments; a run that has to leave its accumulator inside a
+// strip goes to the warp's queue, with the segments that hold more exponents,
+// and the warp drains the queue 32 entries at a time.
+
+constexpr size_t kFitSmem = rows_smem_bytes<TmaMode::kFit>(kRowWarps) + sizeof(SmemBins) +
+                            sizeof(uint32_t) * kRowWarps * 32 * kQueueStride;
+
+__global__ void __launch_bounds__(kRowWarps * 32, 2) k_fit_tma(const TmaImage im, int64_t total_rows,
+                                                                unsigned long long* __restrict__ gbins, int max_spins) {
+    extern __shared__ __align__(128) char dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RowPipe<TmaMode::kFit> pp;
+    pp.ring = reinterpret_cast<SRow*>(dyn) + warp * kSSlots;
+    char* tail = dyn + sizeof(SRow) * kSSlots * kRowWarps;
+    pp.aux = reinterpret_cast<AuxSlot<TmaMode::kFit>*>(tail) + warp * kAuxSlots;
+    tail += sizeof(AuxSlot<TmaMode::kFit>) * kAuxSlots * kRowWarps;
+    pp.bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kSSlots + kAuxSlots);
+    tail += 8 * (kSSlots + kAuxSlots) * kRowWarps;
+    SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
+
+    bins_clear(bins);
+    if (lane == 0) {
+        for (int k = 0; k < kSSlots + kAuxSlots; ++k) mbar_init(smem_addr(&pp.bars[k]), 1);
+        fence_async_shared();
+    }
+    __syncthreads();
+
+    const int h = im.h, w = im.w;
+    const int64_t n = (int64_t)h * w;
+    const RowRange R0 = warp_rows(total_rows, h, kRowWarps);
+    pp.init(R0);
 
     FitWarp st;
     run_reset(st.even, -1);
@@ -1349,33 +1342,11 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
     st.Q = queue + warp * 32 * kQueueStride;
     st.queued = 0;
 
-    // producer of M / E rows: the warp's rows one by one, up to kMeSlots - 1
-    // rows ahead of the row being processed
-    RowRange MP{r0, r1, h, 0, 0, 0};
-    bool m_valid = MP.next();
-    int mj = 0, m_slot = 0, m_issued = 0;
-    auto refill_me = [&](int q_done) {
-        while (m_valid && m_issued < q_done + kMeSlots) {
-            issue_me(m3, e, n, w, MP.y0 + mj, MP.xs, me[m_slot], smem_addr(&me_bars[m_slot]), lane);
-            ++m_issued;
-            m_slot = m_slot + 1 == kMeSlots ? 0 : m_slot + 1;
-            if (++mj == MP.rows) {
-                mj = 0;
-                m_valid = MP.next();
-            }
-        }
-    };
-
-    // consumer: current task, slot of its first S item, the expected phase
-    // parity of every S and M / E slot, the warp's row count q and the
-    // M / E slot of row q
-    RowRange C{r0, r1, h, 0, 0, 0};
+    RowRange C = R0;
     bool c_valid = C.next();
-    int c_slot = 0, q = 0, mc = 0;
-    uint32_t par = 0u, mpar = 0u;
     bool ok = true;
-    refill_me(0);
-    refill();
+    pp.refill_aux(im, n, 0, lane);
+    pp.refill_s(im, n, lane);
 
     while (c_valid && ok) {
         const int x0 = C.xs + 8 * lane;
@@ -1383,15 +1354,15 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
         const int offl = x0 == 0 ? own : own - 1;
         const int offr = x0 + 8 >= w ? own + 7 : own + 8;
         const bool inside = x0 < w;
-        int a = c_slot, b = a + 1 == kFitSlots ? 0 : a + 1;
-        ok = mbar_wait(smem_addr(&bars[a]), (par >> a) & 1u, &g_slrme_status, max_spins) &&
-             mbar_wait(smem_addr(&bars[b]), (par >> b) & 1u, &g_slrme_status, max_spins);
-        for (int j = 0; j < C.rows && ok; ++j, ++q) {
-            const int c2 = b + 1 == kFitSlots ? 0 : b + 1;
-            ok = mbar_wait(smem_addr(&bars[c2]), (par >> c2) & 1u, &g_slrme_status, max_spins) &&
-                 mbar_wait(smem_addr(&me_bars[mc]), (mpar >> mc) & 1u, &g_slrme_status, max_spins);
+        int a = pp.c_slot, b = a + 1 == kSSlots ? 0 : a + 1;
+        ok = mbar_wait(pp.sbar(a), (pp.par >> a) & 1u, &g_slrme_status, max_spins) &&
+             mbar_wait(pp.sbar(b), (pp.par >> b) & 1u, &g_slrme_status, max_spins);
+        for (int j = 0; j < C.rows && ok; ++j, ++pp.q) {
+            const int c2 = b + 1 == kSSlots ? 0 : b + 1;
+            ok = mbar_wait(pp.sbar(c2), (pp.par >> c2) & 1u, &g_slrme_status, max_spins) &&
+                 mbar_wait(pp.abar(pp.mc), (pp.mpar >> pp.mc) & 1u, &g_slrme_status, max_spins);
             if (!ok) break;
-            const MeSlot& ms = me[mc];
+            const AuxSlot<TmaMode::kFit>& ms = pp.aux[pp.mc];
             const uint2 ev = *reinterpret_cast<const uint2*>(&ms.E[8 * lane]);
             const uint32_t elo = ev.x, ehi = ev.y;
             // byte masks of the odd-exponent pixels and the two exponents
@@ -1427,8 +1398,8 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 uint32_t X[4];
-                gf_pairs(fit_row(ring[a].S[c], own, offl, offr), fit_row(ring[b].S[c], own, offl, offr),
-                         fit_row(ring[c2].S[c], own, offl, offr), gf, X);
+                gf_pairs(seg_row(pp.ring[a].S[c], own, offl, offr), seg_row(pp.ring[b].S[c], own, offl, offr),
+                         seg_row(pp.ring[c2].S[c], own, offl, offr), im.gf, X);
                 const uint2 mv = *reinterpret_cast<const uint2*>(&ms.M[c][8 * lane]);
                 chan_sums(X, mv.x, mv.y, olo, ohi, k16, po, c);
                 chan_sums(X, mv.x, mv.y, 0xFFFFFFFFu, 0xFFFFFFFFu, ones, pa, c);
@@ -1461,46 +1432,32 @@ __global__ void __launch_bounds__(kFitWarps * 32, 2) k_fit_tma(const uint8_t* __
                 st.queued += __popc(want);
             }
             // S item j (slot a) and the M / E of row q are done: release and refill
-            par ^= 1u << a;
-            ++released;
+            pp.par ^= 1u << a;
+            ++pp.released;
             a = b;
             b = c2;
-            mpar ^= 1u << mc;
-            mc = mc + 1 == kMeSlots ? 0 : mc + 1;
+            pp.mpar ^= 1u << pp.mc;
+            pp.mc = pp.mc + 1 == kAuxSlots ? 0 : pp.mc + 1;
             __syncwarp();
-            refill_me(q + 1);
-            refill();
+            pp.refill_aux(im, n, pp.q + 1, lane);
+            pp.refill_s(im, n, lane);
         }
         if (!ok) break;
         // the last two S items of the task; every run ends with its task
         // (bounded: a run holds at most 8 * kMaxStripRows pixels)
-        par ^= (1u << a) | (1u << b);
-        released += 2;
-        c_slot = b + 1 == kFitSlots ? 0 : b + 1;
+        pp.par ^= (1u << a) | (1u << b);
+        pp.released += 2;
+        pp.c_slot = b + 1 == kSSlots ? 0 : b + 1;
         warp_flush(st.even, bins, lane);
         warp_flush(st.odd, bins, lane);
         run_reset(st.even, -1);
         run_reset(st.odd, -1);
         __syncwarp();
-        refill();
+        pp.refill_s(im, n, lane);
         c_valid = C.next();
     }
-    if (!ok) {
-        // a copy did not arrive in time: give what is in flight a bounded wait
-        // and stop (each unreleased item has a slot of its own)
-        int s = p_slot;
-        for (int g = issued - 1; g >= released; --g) {
-            s = s == 0 ? kFitSlots - 1 : s - 1;
-            mbar_wait(smem_addr(&bars[s]), (par >> s) & 1u, &g_slrme_status, 1 << 10);
-        }
-        s = m_slot;
-        for (int g = m_issued - 1; g >= q; --g) {
-            s = s == 0 ? kMeSlots - 1 : s - 1;
-            mbar_wait(smem_addr(&me_bars[s]), (mpar >> s) & 1u, &g_slrme_status, 1 << 10);
-        }
-    } else {
-        fit_drain(st, bins, lane);
-    }
+    if (!ok) pp.drain_in_flight();   // a copy did not arrive in time: stop
+    else fit_drain(st, bins, lane);
     __syncthreads();
     bins_to_global(bins, gbins, false);
 }
@@ -1521,13 +1478,13 @@ int launch_fit_tma(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h
     // gets at most ceil(total_rows / warps) rows of at most 256 pixels)
     const int64_t total_rows = (int64_t)((w + kStripCols - 1) / kStripCols) * h;
     int64_t warps = (total_rows + 3) / 4;
-    const int64_t cap = (int64_t)geometry().sms * 2 * kFitWarps;
+    const int64_t cap = (int64_t)geometry().sms * 2 * kRowWarps;
     if (warps > cap) warps = cap;
-    const int64_t rows_max = kMaxBlockPixels / ((int64_t)kFitWarps * kStripCols);
+    const int64_t rows_max = kMaxBlockPixels / ((int64_t)kRowWarps * kStripCols);
     if (warps < (total_rows + rows_max - 1) / rows_max) warps = (total_rows + rows_max - 1) / rows_max;
-    const int64_t g = (warps + kFitWarps - 1) / kFitWarps;
-    k_fit_tma<<<(unsigned)(g < 1 ? 1 : g), kFitWarps * 32, kFitSmem, s>>>(s3, m3, e, h, w, gf_on, total_rows, bins,
-                                                                            kMaxSpins);
+    const int64_t g = (warps + kRowWarps - 1) / kRowWarps;
+    const TmaImage im{s3, m3, e, nullptr, nullptr, nullptr, h, w, gf_on != 0};
+    k_fit_tma<<<(unsigned)(g < 1 ? 1 : g), kRowWarps * 32, kFitSmem, s>>>(im, total_rows, bins, kMaxSpins);
     return cuda_status("slr_fit launch");
 }
 
@@ -1600,7 +1557,7 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
                       ((uintptr_t)e % 8 == 0);
     if (tma_eligible(w, {s3, m3, e, r3})) {
         const TmaImage im{s3, m3, e, nullptr, r3, nullptr, h, w, gf_on != 0};
-        return launch_tma<TmaMode::kResidual>(im, params, hist, s);
+        return launch_rows_tma<TmaMode::kResidual>(im, params, hist, s);
     }
     const StripLaunch L = strip_launch(h, w, 2);
     k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
@@ -1612,7 +1569,7 @@ int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
     if (tma_eligible(w, {s3, e, r3, rgbe_out})) {
         const TmaImage im{s3, nullptr, e, r3, nullptr, rgbe_out, h, w, gf_on != 0};
-        return launch_tma<TmaMode::kDecode>(im, params, nullptr, s);
+        return launch_rows_tma<TmaMode::kDecode>(im, params, nullptr, s);
     }
     const StripLaunch L = strip_launch(h, w, 2);
     k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
