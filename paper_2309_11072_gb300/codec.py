@@ -116,18 +116,21 @@ class HostCodec:
 
     Each call copies the words host -> device, encodes and decodes on the
     device, and copies the enhancement layer (R, E, parameters, histograms),
-    the base layer S and the decoded words back to pinned host buffers.  Two
-    device codecs on two streams alternate between calls, so the copies of one
-    call overlap the coding of the next; host buffers are per call slot.
+    the base layer S and the decoded words back to pinned host buffers.
+    Device codecs on separate streams take the calls in turn (slots), so the
+    copies of one call overlap the coding of the next; within a call the
+    encoder's outputs go back on a second stream while the decoder runs.
+    Host buffers are per slot.
     """
 
-    def __init__(self, h: int, w: int, device: str | torch.device = "cuda", gf_on: bool = True, slots: int = 2):
+    def __init__(self, h: int, w: int, device: str | torch.device = "cuda", gf_on: bool = True, slots: int = 3):
         self.slots = []
         n = h * w
         for _ in range(slots):
             c = Codec(h, w, device, gf_on)
             self.slots.append(dict(
-                codec=c, stream=torch.cuda.Stream(device=c.device),
+                codec=c, stream=torch.cuda.Stream(device=c.device), out_stream=torch.cuda.Stream(device=c.device),
+                done=None,
                 d_rgbe=torch.empty(n, dtype=torch.int32, device=c.device),
                 h_s3=torch.empty(3 * n, dtype=torch.uint8).pin_memory(),
                 h_e=torch.empty(n, dtype=torch.uint8).pin_memory(),
@@ -149,22 +152,34 @@ class HostCodec:
         return sum(sl[k].numel() * sl[k].element_size() for k in ("h_s3", "h_e", "h_r3", "h_params", "h_hist", "h_out"))
 
     def roundtrip(self, rgbe_host: torch.Tensor, quality: int) -> None:
-        """Enqueue one call on the next slot's stream (asynchronous; the slot's
-        previous call, two calls back, is complete before its buffers are reused
-        because its stream runs in order)."""
+        """Enqueue one call on the next slot's streams (asynchronous).  The
+        slot's previous call is complete before its buffers are reused: the
+        coding stream waits for the slot's last copy back."""
         sl = self.slots[self.turn % len(self.slots)]
         self.turn += 1
-        c, s = sl["codec"], sl["stream"]
+        c, s, so = sl["codec"], sl["stream"], sl["out_stream"]
+        if sl["done"] is not None:
+            s.wait_event(sl["done"])
         with torch.cuda.stream(s):
             sl["d_rgbe"].copy_(rgbe_host, non_blocking=True)
             L = c.encode(sl["d_rgbe"], quality, stream=s)
+            encoded = torch.cuda.Event()
+            encoded.record(s)
             out = c.decode(L.s3, L.e, L.r3, L.params, stream=s)
+            decoded = torch.cuda.Event()
+            decoded.record(s)
+        with torch.cuda.stream(so):
+            so.wait_event(encoded)
             sl["h_s3"].copy_(c.s3, non_blocking=True)
             sl["h_e"].copy_(c.e, non_blocking=True)
             sl["h_r3"].copy_(c.r3, non_blocking=True)
             sl["h_params"].copy_(c.params, non_blocking=True)
             sl["h_hist"].copy_(c.hist, non_blocking=True)
+            so.wait_event(decoded)
             sl["h_out"].copy_(out, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(so)
+        sl["done"] = done
 
     def streams(self):
-        return [sl["stream"] for sl in self.slots]
+        return [st for sl in self.slots for st in (sl["stream"], sl["out_stream"])]

@@ -344,3 +344,23 @@ def test_tma_staged_path_matches_oracle(h, w, gf_on):
     assert_matches_oracle(make_img(h, w, "scene", seed=h + 3 * w), 80, gf_on)
     assert_matches_oracle(make_img(h, w, "noise", seed=h + 5 * w), 80, gf_on)
     assert _device_status() == 0
+
+
+def test_host_codec_slots_match_oracle():
+    # calls queued back to back on the rotating slots (copies of one call
+    # overlapping the next one's coding) leave each call's layers intact
+    h, w = 96, 144
+    hc = codec.HostCodec(h, w, DEV)
+    nslots = len(hc.slots)
+    calls = [(make_img(h, w, "scene", seed=10 + i), [50, 75, 90, 60, 85][i]) for i in range(nslots + 2)]
+    hosts = [torch.from_numpy(img.view(np.int32).reshape(-1).copy()).pin_memory() for img, _ in calls]
+    for host, (_, q) in zip(hosts, calls):
+        hc.roundtrip(host, q)
+    torch.cuda.synchronize()
+    for i in range(len(calls) - nslots, len(calls)):
+        img, q = calls[i]
+        sl = hc.slots[i % nslots]
+        o = O.encode(img, q)
+        assert np.array_equal(sl["h_out"].numpy().view(np.uint32).reshape(h, w), img)
+        assert np.array_equal(sl["h_r3"].numpy().reshape(3, h, w), o["r3"])
+        assert np.array_equal(sl["h_s3"].numpy().reshape(3, h, w), o["s3"])
