@@ -366,6 +366,7 @@ constexpr int kQueueStride = 21;
 // hold N and the channel sums in bin order) or a segment (tag = pixel
 // count), whose pixels are summed in order and added once per stretch of
 // equal exponents.
+template <bool kUnroll>
 __device__ __forceinline__ void drain_entry(const uint32_t* q, uint32_t B) {
     const uint32_t tag = q[20];
     uint32_t acc[kNsum];
@@ -386,31 +387,58 @@ __device__ __forceinline__ void drain_entry(const uint32_t* q, uint32_t B) {
     int Ecur = (int)(elo & 255u);
 #pragma unroll
     for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
-#pragma unroll 1
-    for (int i = 0; i < cnt; ++i) {
-        const int E = (int)(elo & 255u);
-        elo = __funnelshift_r(elo, ehi, 8);
-        ehi >>= 8;
-        if (E != Ecur) {
-            bins_add32(B, Ecur, acc);
+    if constexpr (kUnroll) {
+        // fully unrolled: every byte and pair is picked with a constant index
 #pragma unroll
-            for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
-            Ecur = E;
+        for (int i = 0; i < 8; ++i) {
+            if (i < cnt) {
+                const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
+                if (E != Ecur) {
+                    bins_add32(B, Ecur, acc);
+#pragma unroll
+                    for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
+                    Ecur = E;
+                }
+                acc[0] += 1u;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const uint32_t x = (X[c][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                    const uint32_t yv = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
+                    acc[1 + 4 * c] += x;
+                    acc[2 + 4 * c] += yv;
+                    acc[3 + 4 * c] += x * yv;
+                    acc[4 + 4 * c] += x * x;
+                }
+            }
         }
-        acc[0] += 1u;
+    } else {
+        // compact loop (fewer registers): shift the next pixel into place
+#pragma unroll 1
+        for (int i = 0; i < cnt; ++i) {
+            const int E = (int)(elo & 255u);
+            elo = __funnelshift_r(elo, ehi, 8);
+            ehi >>= 8;
+            if (E != Ecur) {
+                bins_add32(B, Ecur, acc);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
-            acc[1 + 4 * c] += x;
-            acc[2 + 4 * c] += yv;
-            acc[3 + 4 * c] += x * yv;
-            acc[4 + 4 * c] += x * x;
-            mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
-            mhi[c] >>= 8;
-            X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
-            X[c][1] = __funnelshift_r(X[c][1], X[c][2], 16);
-            X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
-            X[c][3] >>= 16;
+                for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
+                Ecur = E;
+            }
+            acc[0] += 1u;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
+                acc[1 + 4 * c] += x;
+                acc[2 + 4 * c] += yv;
+                acc[3 + 4 * c] += x * yv;
+                acc[4 + 4 * c] += x * x;
+                mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
+                mhi[c] >>= 8;
+                X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
+                X[c][1] = __funnelshift_r(X[c][1], X[c][2], 16);
+                X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
+                X[c][3] >>= 16;
+            }
         }
     }
     bins_add32(B, Ecur, acc);
@@ -426,24 +454,23 @@ struct FitWarp {
     int queued;   // entries in the queue (warp-uniform)
 };
 
-// Drains `queued` entries of a warp's queue, one per lane.
-__device__ __forceinline__ void drain_queue(const uint32_t* Q, int queued, uint32_t bins, int lane) {
-    if (lane < queued) drain_entry(Q + lane * kQueueStride, bins);
-    __syncwarp();
-}
-
+// Drains the warp's queue, one entry per lane (kUnroll: the faster drain
+// that needs more registers).
+template <bool kUnroll = false>
 __device__ __forceinline__ void fit_drain(FitWarp& st, SmemBins& bins, int lane) {
-    drain_queue(st.Q, st.queued, smem_addr(&bins), lane);
+    if (lane < st.queued) drain_entry<kUnroll>(st.Q + lane * kQueueStride, smem_addr(&bins));
+    __syncwarp();
     st.queued = 0;
 }
 
 // Queues the run of every lane with `want` set (a run that must leave its
 // accumulator in the middle of a strip); the warp drains them together later
 // instead of waiting on one lane's atomics.
+template <bool kUnroll = false>
 __device__ __forceinline__ void enqueue_run(FitWarp& st, bool want, const RunAcc& r, SmemBins& bins, int lane) {
     const unsigned m = __ballot_sync(0xffffffffu, want);
     if (!m) return;
-    if (st.queued + __popc(m) > 32) fit_drain(st, bins, lane);
+    if (st.queued + __popc(m) > 32) fit_drain<kUnroll>(st, bins, lane);
     if (want) {
         uint32_t* q = st.Q + (st.queued + __popc(m & ((1u << lane) - 1u))) * kQueueStride;
         q[0] = r.n;
@@ -711,6 +738,11 @@ __device__ __forceinline__ void load_params(const slrme_params* __restrict__ P, 
         sa[i] = (&P->a[0][0])[i];
         sb[i] = (&P->b[0][0])[i];
     }
+}
+
+// The parameters as (a, b) pairs, [c][E], so one 8-byte load gets both.
+__device__ __forceinline__ void load_params_ab(const slrme_params* __restrict__ P, float2* ab) {
+    for (int i = threadIdx.x; i < 3 * kNbin; i += blockDim.x) ab[i] = make_float2((&P->a[0][0])[i], (&P->b[0][0])[i]);
 }
 
 // One strip: R = M - M* for rows y0 .. y0 + rows - 1, columns xs .. xs + 255;
@@ -1153,11 +1185,10 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage i
     tail += sizeof(AuxSlot<MODE>) * kAuxSlots * kRowWarps;
     pp.bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kSSlots + kAuxSlots);
     tail += 8 * (kSSlots + kAuxSlots) * kRowWarps;
-    float* sa = reinterpret_cast<float*>(tail);
-    float* sb = sa + 3 * kNbin;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(sb + 3 * kNbin);
+    float2* ab = reinterpret_cast<float2*>(tail);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ab + 3 * kNbin);
 
-    load_params(P, sa, sb);
+    load_params_ab(P, ab);
     if (MODE == TmaMode::kResidual && ghist)
         for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
     if (lane == 0) {
@@ -1205,7 +1236,8 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage i
                         for (int i = 0; i < 8; ++i) {
                             const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
                             const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
-                            rr[i] = M - predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X, i));
+                            const float2 p = ab[c * kNbin + E];
+                            rr[i] = M - predict(p.x, p.y, half_of(X, i));
                         }
                         uint4 v;
                         v.x = (uint32_t)(rr[0] & 0xFFFF) | ((uint32_t)rr[1] << 16);
@@ -1233,7 +1265,8 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage i
                         for (int i = 0; i < 8; ++i) {
                             const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
                             const int E = (int)(word[i] >> 24);
-                            const int M = rv + predict(sa[c * kNbin + E], sb[c * kNbin + E], half_of(X, i));
+                            const float2 p = ab[c * kNbin + E];
+                            const int M = rv + predict(p.x, p.y, half_of(X, i));
                             word[i] |= ((uint32_t)M & 255u) << (8 * c);
                         }
                     }
@@ -1379,14 +1412,14 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_fit_tma(const TmaImage im
             const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
             const uint32_t pe_n = take ? 8u - po_n : 0u;
             // a run whose region changes leaves its accumulator first
-            enqueue_run(st, pe_n != 0u && (int)Ee != st.even.E && st.even.n != 0u, st.even, bins, lane);
-            enqueue_run(st, po_n != 0u && (int)Eo != st.odd.E && st.odd.n != 0u, st.odd, bins, lane);
+            enqueue_run<true>(st, pe_n != 0u && (int)Ee != st.even.E && st.even.n != 0u, st.even, bins, lane);
+            enqueue_run<true>(st, po_n != 0u && (int)Eo != st.odd.E && st.odd.n != 0u, st.odd, bins, lane);
             if (pe_n != 0u && (int)Ee != st.even.E) run_reset(st.even, (int)Ee);
             if (po_n != 0u && (int)Eo != st.odd.E) run_reset(st.odd, (int)Eo);
             const unsigned want = __ballot_sync(0xffffffffu, slow);
             uint32_t* qe = nullptr;
             if (want) {
-                if (st.queued + __popc(want) > 32) fit_drain(st, bins, lane);
+                if (st.queued + __popc(want) > 32) fit_drain<true>(st, bins, lane);
                 qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
             }
             // channel by channel: x = 16 S* pairs, the sums of the odd pixels
@@ -1457,7 +1490,7 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_fit_tma(const TmaImage im
         c_valid = C.next();
     }
     if (!ok) pp.drain_in_flight();   // a copy did not arrive in time: stop
-    else fit_drain(st, bins, lane);
+    else fit_drain<true>(st, bins, lane);
     __syncthreads();
     bins_to_global(bins, gbins, false);
 }

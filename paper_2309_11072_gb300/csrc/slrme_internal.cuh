@@ -123,20 +123,18 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t w, int i) { return (w >> (8
 // Eq. (8): round(a x + b) clipped to [0, 255]; float32 multiply then add,
 // half away from zero.  NaN and t <= 0 give 0.
 //
-// The integer <-> float conversions use the 2^23 bias: for 0 <= v < 2^23,
-// float(v) = bits(0x4B000000 | v) - 2^23 exactly, and adding 2^23 to a float
-// t in [0, 255] rounds it to the nearest integer (ties to even) in the low
-// mantissa bits.  A tie that went to the even neighbour below is moved up, so
-// the result is round-half-away-from-zero, as with truncation and a
-// comparison of the fraction, without the slower conversion instructions.
+// float(x) for 0 <= x < 2^23 is bits(0x4B000000 | x) - 2^23 exactly (the 2^23
+// bias).  For the clipped t in [0, 255], round half away from zero is
+// floor(t + 0.5); the sum rounded down keeps that floor exact (the exact sum
+// is at least the rounded one, and an integer in between would have to be the
+// rounded value itself), and adding 2^23 rounded down leaves floor(v) in the
+// low mantissa bits.
 __device__ __forceinline__ int predict(float a, float b, int x) {
     const float xf = __fsub_rn(__int_as_float(0x4B000000 | x), 8388608.0f);
     float t = __fadd_rn(__fmul_rn(a, xf), b);
     t = fminf(fmaxf(t, 0.0f), 255.0f);
-    const float u = __fadd_rn(t, 8388608.0f);               // 2^23 + rn(t)
-    const int r = __float_as_int(u) - 0x4B000000;           // rn(t), ties to even
-    const float d = __fsub_rn(t, __fsub_rn(u, 8388608.0f)); // t - rn(t), exact
-    return r + (d == 0.5f ? 1 : 0);
+    const float v = __fadd_rd(t, 0.5f);
+    return __float_as_int(__fadd_rd(v, 8388608.0f)) - 0x4B000000;
 }
 
 }  // namespace slrme

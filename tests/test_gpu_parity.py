@@ -247,6 +247,32 @@ def test_decode_parity_any_params(h, w, gf_on):
     assert np.array_equal(got, img)
 
 
+@pytest.mark.parametrize("w", [64, 72])
+def test_prediction_ties_round_half_away(w):
+    # slopes and intercepts that put a * x + b exactly on .5 for many x: the
+    # residuals (and the decoder) follow Eq. 8's round half away from zero
+    h = 40
+    img = make_img(h, w, "noise", seed=w)
+    om3, oe = O.rgbe_split(img)
+    s3 = np.random.default_rng(w).integers(0, 256, size=(3, h, w)).astype(np.uint8)
+    a = np.zeros((3, 256), np.float32)
+    b = np.zeros((3, 256), np.float32)
+    a[0], b[0] = 1.0 / 32.0, 0.0          # x = 16 (2k + 1): t = k + 0.5
+    a[1], b[1] = 1.0 / 16.0, 0.5          # every x: t = S* + 0.5 on integer S*
+    a[2], b[2] = 1.0 / 64.0, 0.25         # x = 16 (2k + 1): t = k / 2 + 0.5 (every other one a tie)
+    for gf_on in (0, 1):
+        x3 = O.gf(s3, bool(gf_on))
+        ms = O.predict(x3, oe, a, b)
+        r3, hist = run_residual(s3, om3, oe, a, b, gf_on)
+        or3, ohist = O.residual(om3, ms)
+        assert np.array_equal(r3, or3) and np.array_equal(hist, ohist)
+        out = torch.empty(h * w, dtype=torch.int32, device=DEV)
+        native.residual_decode(dev(s3), dev(oe), dev(or3, torch.int16), h, w, gf_on,
+                               dev(codec.params_from_numpy(a, b), torch.int32), out)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(out, np.uint32).reshape(h, w), img)
+
+
 # ------------------------------------------------------------------ chained
 
 def encode_gpu(img, quality, gf_on=True):
