@@ -7,10 +7,11 @@ Workload (one "step"): the 2048x1536 synthetic RGBE image (fBm luminance over
 at base qualities 50, 75 and 90: per quality rgbe_split, sdri_base_roundtrip,
 slr_fit, residual_encode, then residual_decode, with the decoded words
 checked against the input.  The step's 15 C-ABI calls are captured once as
-a CUDA graph and the timed steps replay it; per-call times come from a
-separate call-by-call pass with events between the calls.  The input is
-resident in HBM when timing starts; L2 is flushed (a 256 MiB write) between
-timed steps, outside the step events.
+a CUDA graph and the timed steps replay it; per-call times come from
+event-record nodes between the calls inside the same timed replays.  The
+input is resident in HBM when timing starts; L2 is flushed (a 256 MiB write)
+between timed steps, outside the step events.  ``--workload 8k`` runs the
+same step on the 7680x4320 image (fBm over 8 decades with a sky band, q 90).
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead
 (rank 0 only) on the same workload, one quality per step.
@@ -40,7 +41,7 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # DRAM bytes per pixel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
-TRAFFIC = {}
+TRAFFIC = {"slr_fit": {"bytes_per_px": 22116864 / (2048 * 1536), "sha": "250a995f0fe557ad"}}
 KERNEL_SOURCE = {"rgbe_split": "split.cu", "sdri_base_roundtrip": "base.cu", "slr_fit": "slr.cu",
                  "residual_encode": "slr.cu", "residual_decode": "slr.cu"}
 
@@ -132,7 +133,7 @@ def run_ours(args) -> None:
         dist.init_process_group("nccl")
     native.lib()
 
-    wl = synth.workload_2k()
+    wl = synth.workload_8k() if args.workload == "8k" else synth.workload_2k()
     (h, w), = wl.sizes
     img = synth.make_workload_images(wl)[0]
     n = h * w
@@ -205,12 +206,18 @@ def run_ours(args) -> None:
                                with_pick=round(pk.bits, 4), learned_encode_us=round(1e3 * e0.elapsed_time(e1), 1))
     torch.cuda.synchronize()
 
-    # the step's 15 C-ABI calls, captured once into a CUDA graph and replayed
+    # the step's C-ABI calls, captured once into a CUDA graph and replayed;
+    # event-record nodes between the calls time each call inside the timed
+    # replays (external events, where this torch has them)
+    try:
+        gev = {q: [torch.cuda.Event(enable_timing=True, external=True) for _ in range(6)] for q in qualities}
+    except TypeError:
+        gev = None
     graph = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream()
     cap.wait_stream(stream)
     with torch.cuda.graph(graph, stream=cap, capture_error_mode="thread_local"):
-        step(None, torch.cuda.current_stream())
+        step(gev, torch.cuda.current_stream())
     stream.wait_stream(cap)
     for _ in range(args.warmup):
         graph.replay()
@@ -221,6 +228,7 @@ def run_ours(args) -> None:
         dist.barrier()
     torch.cuda.synchronize()
     step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    per_call = {name: [] for name in calls}
     with ClockSampler(local) as clocks:
         wall0 = time.perf_counter()
         for k in range(args.steps):
@@ -228,6 +236,13 @@ def run_ours(args) -> None:
             graph.replay()
             step_ev[k][1].record(stream)
             flush.zero_()
+            if gev is not None:
+                # the in-graph events are rewritten by every replay: read them now
+                # (the wait is outside the step's events)
+                stream.synchronize()
+                for q in qualities:
+                    for i, name in enumerate(calls):
+                        per_call[name].append(gev[q][i].elapsed_time(gev[q][i + 1]))
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     if dist is not None:
@@ -236,20 +251,22 @@ def run_ours(args) -> None:
     total_ms = sum(step_ms)
     out_ok = bool(torch.equal(c.out, rgbe))
 
-    # per-call times: the same step launched call by call with events between
-    # the calls (not part of the timed steps above)
-    call_ev = [{q: [torch.cuda.Event(enable_timing=True) for _ in range(6)] for q in qualities}
-               for _ in range(args.steps)]
-    for k in range(args.steps):
-        step(call_ev[k])
-        flush.zero_()
-    torch.cuda.synchronize()
-    per_call = {name: [] for name in calls}
-    for k in range(args.steps):
-        for q in qualities:
-            ev = call_ev[k][q]
-            for i, name in enumerate(calls):
-                per_call[name].append(ev[i].elapsed_time(ev[i + 1]))
+    call_timing = "event-record nodes inside the timed graph replays"
+    if gev is None:
+        # no external events in this torch: the same step launched call by call
+        # with events between the calls (not part of the timed steps above)
+        call_timing = "separate call-by-call pass (no in-graph events in this torch)"
+        call_ev = [{q: [torch.cuda.Event(enable_timing=True) for _ in range(6)] for q in qualities}
+                   for _ in range(args.steps)]
+        for k in range(args.steps):
+            step(call_ev[k])
+            flush.zero_()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            for q in qualities:
+                ev = call_ev[k][q]
+                for i, name in enumerate(calls):
+                    per_call[name].append(ev[i].elapsed_time(ev[i + 1]))
     if dist is not None:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -269,7 +286,8 @@ def run_ours(args) -> None:
         traffic = tr["bytes_per_px"] * n
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": dom,
-                "algorithmic_bytes": BYTES_PER_PX[dom] * n, "peak_source": peaks["src"]}
+                "algorithmic_bytes": BYTES_PER_PX[dom] * n, "peak_source": peaks["src"],
+                "timing": call_timing}
     stage_us = {name: round(v, 2) for name, v in avg_us.items()}
     stage_frac = {name: round(BYTES_PER_PX[name] * n / (avg_us[name] * 1e-6) / 1e9 / peaks["hbm_gbs"], 4)
                   for name in calls}
@@ -312,7 +330,8 @@ def run_ours(args) -> None:
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"{wl.name} q{{50,75,90}} encode+decode, SLR, gaussian restoration on",
+            "config": {"workload": f"{wl.name} q{{{','.join(map(str, qualities))}}} encode+decode, SLR, "
+                                   "gaussian restoration on",
                        "pixels_per_step": px_per_step, "image": f"{w}x{h}", "qualities": list(qualities),
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{world}",
                        "launch": "the step's 15 C-ABI calls captured once as a CUDA graph, replayed per step"},
@@ -406,7 +425,7 @@ def run_reference(args) -> None:
     from oracle import oracle as O
     from paper_2309_11072_gb300 import synth
     O.build()
-    wl = synth.workload_2k()
+    wl = synth.workload_8k() if args.workload == "8k" else synth.workload_2k()
     img = synth.make_workload_images(wl)[0]
     qualities = wl.qualities
 
@@ -445,8 +464,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["2k", "batch64"], default="2k",
-                    help="2k: the benchmark line; batch64: the batch form on 64 uneven images")
+    ap.add_argument("--workload", choices=["2k", "8k", "batch64"], default="2k",
+                    help="2k: the benchmark line; 8k: the 7680x4320 image (q90); "
+                         "batch64: the batch form on 64 uneven images")
     args = ap.parse_args()
     if args.impl == "ours":
         args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps on the GPU
