@@ -8,7 +8,8 @@ at base qualities 50, 75 and 90: per quality rgbe_split, sdri_base_roundtrip,
 slr_fit, residual_encode, then residual_decode, with the decoded words
 checked against the input.  The step's 15 C-ABI calls are captured once as
 a CUDA graph and the timed steps replay it; per-call times come from
-event-record nodes between the calls inside the same timed replays.  The
+replays of a copy of that graph with event-record nodes between the calls
+(timed apart, since each node adds a few microseconds to the step).  The
 input is resident in HBM when timing starts; L2 is flushed (a 256 MiB write)
 between timed steps, outside the step events.  ``--workload 8k`` runs the
 same step on the 7680x4320 image (fBm over 8 decades with a sky band, q 90).
@@ -206,18 +207,25 @@ def run_ours(args) -> None:
                                with_pick=round(pk.bits, 4), learned_encode_us=round(1e3 * e0.elapsed_time(e1), 1))
     torch.cuda.synchronize()
 
-    # the step's C-ABI calls, captured once into a CUDA graph and replayed;
-    # event-record nodes between the calls time each call inside the timed
-    # replays (external events, where this torch has them)
+    # the step's C-ABI calls, captured once into a CUDA graph and replayed.
+    # A second graph of the same calls carries event-record nodes between the
+    # calls (external events, where this torch has them) and times each call;
+    # event nodes add a few microseconds each, so the step time comes from the
+    # graph without them.
     try:
         gev = {q: [torch.cuda.Event(enable_timing=True, external=True) for _ in range(6)] for q in qualities}
     except TypeError:
         gev = None
-    graph = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream()
     cap.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=cap, capture_error_mode="thread_local"):
-        step(gev, torch.cuda.current_stream())
+        step(None, torch.cuda.current_stream())
+    egraph = None
+    if gev is not None:
+        egraph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(egraph, stream=cap, capture_error_mode="thread_local"):
+            step(gev, torch.cuda.current_stream())
     stream.wait_stream(cap)
     for _ in range(args.warmup):
         graph.replay()
@@ -236,22 +244,29 @@ def run_ours(args) -> None:
             graph.replay()
             step_ev[k][1].record(stream)
             flush.zero_()
-            if gev is not None:
-                # the in-graph events are rewritten by every replay: read them now
-                # (the wait is outside the step's events)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if egraph is not None:
+            # per-call times: the same steps replayed with event nodes between
+            # the calls, L2 flushed between steps as above; the in-graph events
+            # are rewritten by every replay, so they are read after each one
+            for _ in range(args.warmup):
+                egraph.replay()
+                flush.zero_()
+            for k in range(args.steps):
+                egraph.replay()
+                flush.zero_()
                 stream.synchronize()
                 for q in qualities:
                     for i, name in enumerate(calls):
                         per_call[name].append(gev[q][i].elapsed_time(gev[q][i + 1]))
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
     if dist is not None:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     total_ms = sum(step_ms)
     out_ok = bool(torch.equal(c.out, rgbe))
 
-    call_timing = "event-record nodes inside the timed graph replays"
+    call_timing = "event-record nodes between the calls in replays of the same step graph (L2 flushed between steps)"
     if gev is None:
         # no external events in this torch: the same step launched call by call
         # with events between the calls (not part of the timed steps above)
