@@ -10,6 +10,8 @@
 // of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
 // them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
 // 32-bit add (values stay <= 4080).
+#include <cuda.h>
+
 #include <initializer_list>
 #include <mutex>
 
@@ -973,264 +975,518 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
     }
 }
 
-// ====================================================================== TMA-staged row pipelines
+// ====================================================================== tensor-map row pipeline
 //
 // For images whose rows are 16-byte aligned (w % 16 == 0, 16-byte aligned
-// planes).  The rows of all 256-column strips are taken in column-major
-// order (strip, row) and cut into one contiguous range per warp, so every
-// warp does the same number of rows to within one; a range becomes tasks of
-// at most kMaxStripRows rows of one strip.  Each warp streams its rows
-// through two rings of shared-memory slots filled by 1-D bulk copies
-// (cp.async.bulk) that complete on the slot's mbarrier: S rows of the three
-// planes with 16 halo columns (row j of a task needs S rows j - 1, j, j + 1,
-// clamped to the image) and, up to two rows ahead, the row's other planes
-// (M and E for the fit and the residual, R and E for the decoder).  No
-// CTA-wide barrier is involved; data in flight costs shared memory, not
-// registers.  Every wait is bounded (see tma.cuh).
+// planes).  The image is cut into strips of kTileCols = 2048 columns, one
+// 256-column slice per consumer warp (kTileWarps = 8 per CTA).  The rows of
+// all strips, strip after strip, are split into one contiguous range per
+// CTA, and a range becomes tasks of at most kTaskRows rows of one strip.
+// A producer warp streams the range through two shared-memory rings with
+// tensor-map bulk copies (cp.async.bulk.tensor): per S item, the S row of the
+// three planes with 16 halo columns on each side (one 4-D box); per row, its
+// other planes (M and E for the fit and the residual, R and E for the
+// decoder: one 4-D box and one 4-D box of a single plane).  Row j of a task
+// needs S items j, j + 1, j + 2 (rows y - 1, y, y + 1, clamped to the image
+// by the producer, which replicates the edge rows).  A slot's full barrier
+// completes on the bytes of its copies; its empty barrier completes when all
+// consumer warps have arrived.  Box columns past the image are zero-filled by
+// the copy and never read as pixels: edge columns replicate through the
+// neighbour offsets.  Every wait is bounded (see tma.cuh).
 
-constexpr int kSW = 288;          // S row segment: 16 halo + 256 + 16 halo bytes
-constexpr int kRowWarps = 8;      // warps per CTA (independent pipelines)
-constexpr int kSSlots = 5;        // S rows
-constexpr int kAuxSlots = 3;      // M / E (or R / E) rows
+constexpr int kTileWarps = 8;                              // consumer warps
+constexpr int kTileThreads = (kTileWarps + 1) * 32;        // + one producer warp
+constexpr int kTileCols = kTileWarps * kStripCols;         // 2048
+constexpr int kTileSW = kTileCols + 32;                    // S row with halos, per plane
+constexpr int kTaskRows = 256;
+constexpr int kTileS = 5;                                  // S ring slots
+constexpr int kTileA = 3;                                  // M / E (or R / E) ring slots
+constexpr uint32_t kTileSBytes = 3u * kTileSW;             // 6240
+constexpr uint32_t kTileSStride = 6272;                    // slot stride, multiple of 128
+static_assert(kTileSStride >= kTileSBytes && kTileSStride % 128 == 0, "S slot");
+// Flush every run this often: a run then holds at most 8 * 16 pixels, which
+// keeps its 32-bit sums exact (see kMaxStripRows).
+constexpr int kRunRows = kMaxStripRows;
 
 enum class TmaMode { kResidual = 0, kDecode = 1, kFit = 2 };
 
-struct SRow {
-    uint8_t S[3][kSW];
-};
-
+// Aux slot: planes 0-2 (1 or 2 bytes per pixel) then E.
 template <TmaMode MODE>
-struct AuxSlot {                  // fit and residual: M and E
-    uint8_t M[3][kStripCols];
-    uint8_t E[kStripCols];
+struct TileAux {
+    static constexpr uint32_t kElem = MODE == TmaMode::kDecode ? 2 : 1;
+    static constexpr uint32_t kPlane = kElem * kTileCols;          // bytes per plane row
+    static constexpr uint32_t kE = 3 * kPlane;                     // offset of the E row
+    static constexpr uint32_t kBytes = kE + kTileCols;
+    static constexpr uint32_t kStride = kBytes;                    // multiple of 128
+    static_assert(kStride % 128 == 0, "aux slot");
 };
 
-template <>
-struct AuxSlot<TmaMode::kDecode> {
-    int16_t R[3][kStripCols];
-    uint8_t E[kStripCols];
+struct TileMaps {
+    CUtensorMap s;   // u8 (16, w/16, h, 3): S planes
+    CUtensorMap a;   // u8 (16, w/16, h, 3) M planes, or u16 (8, w/8, h, 3) R planes
+    CUtensorMap e;   // u8 (16, w/16, h, 1): E plane
 };
 
-struct TmaImage {
-    const uint8_t* s3;
-    const uint8_t* m3;
-    const uint8_t* e;
-    const int16_t* r3_in;
-    int16_t* r3_out;
-    uint32_t* out;
+struct TileArgs {
     int h, w;
-    bool gf;
+    int gf;
+    int64_t total_rows;                      // strips * h
+    int max_spins;
+    const slrme_params* params;              // residual / decode
+    int16_t* r3_out;                         // residual
+    uint32_t* hist;                          // residual (may be null)
+    uint32_t* out;                           // decode
+    unsigned long long* gbins;               // fit
 };
 
-// A warp's rows r .. end - 1 in (strip, row) order and its current task.
-struct RowRange {
-    int r, end, h;
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Barrier among the consumer warps only (the producer warp may have left).
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kTileWarps * 32) : "memory");
+}
+
+// The CTA's rows r .. end - 1 in (strip, row) order and its current task.
+struct TileRange {
+    int64_t r, end;
+    int h;
     int y0, rows, xs;
-    // Takes the next task; false when the range is done.
     __device__ __forceinline__ bool next() {
         if (r >= end) return false;
-        const int c = r / h;
-        y0 = r - c * h;
-        rows = min(min(end - r, h - y0), kMaxStripRows);
-        xs = c * kStripCols;
+        const int64_t c = r / h;
+        y0 = (int)(r - c * h);
+        rows = (int)min(min(end - r, (int64_t)(h - y0)), (int64_t)kTaskRows);
+        xs = (int)c * kTileCols;
         r += rows;
         return true;
     }
 };
 
-// The warp's range of rows: warp gw of `warps` gets rows
-// [gw total / warps, (gw + 1) total / warps).
-__device__ __forceinline__ RowRange warp_rows(int64_t total_rows, int h, int per_block) {
-    const int64_t warps = (int64_t)gridDim.x * per_block;
-    const int64_t gw = (int64_t)blockIdx.x * per_block + (threadIdx.x >> 5);
-    return RowRange{(int)(gw * total_rows / warps), (int)((gw + 1) * total_rows / warps), h, 0, 0, 0};
+__device__ __forceinline__ TileRange tile_range(int64_t total_rows, int h) {
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    return TileRange{b * total_rows / G, (b + 1) * total_rows / G, h, 0, 0, 0};
 }
 
-// One lane's S row segment from a slot: 8 bytes plus the neighbours at the
-// precomputed offsets (which point at the lane's own edge byte where the
-// image ends, replicating it).
-__device__ __forceinline__ Row10 seg_row(const uint8_t* row, int own, int offl, int offr) {
-    Row10 R;
-    const uint2 v = *reinterpret_cast<const uint2*>(row + own);
-    R.lo = v.x;
-    R.hi = v.y;
-    R.l = row[offl];
-    R.r = row[offr];
-    return R;
-}
-
-// Copies S row ys, columns xs - 16 .. xs + 271 (clipped to the image), of the
-// three planes (lanes 0-2).
-__device__ __forceinline__ void issue_s(const TmaImage& im, int64_t n, int ys, int xs, SRow& sl, uint32_t bar,
-                                        int lane) {
-    const int padl = xs >= 16 ? 16 : 0;
-    const int bytes = min(xs + kStripCols + 16, im.w) - (xs - padl);
-    fence_async_shared();
-    if (lane == 0) mbar_arrive_expect_tx(bar, 3u * (uint32_t)bytes);
-    __syncwarp();
-    if (lane < 3)
-        tma_load_1d(smem_addr(&sl.S[lane][16 - padl]), im.s3 + lane * n + (int64_t)ys * im.w + xs - padl,
-                    (uint32_t)bytes, bar);
-}
-
-// Copies the other planes of row y, columns xs .. xs + 255 (lanes 0-3).
+// Shared-memory layout of a tile kernel: the two rings, then four barrier
+// arrays, then the mode's own data at `extra`.
 template <TmaMode MODE>
-__device__ __forceinline__ void issue_aux(const TmaImage& im, int64_t n, int y, int xs, AuxSlot<MODE>& sl,
-                                          uint32_t bar, int lane) {
-    const int bytes = min(kStripCols, im.w - xs);
-    constexpr int kRb = MODE == TmaMode::kDecode ? 2 : 1;   // bytes per element of planes 0-2
-    fence_async_shared();
-    if (lane == 0) mbar_arrive_expect_tx(bar, (3u * kRb + 1u) * (uint32_t)bytes);
-    __syncwarp();
-    const int64_t off = (int64_t)y * im.w + xs;
-    if (lane < 3) {
-        if constexpr (MODE == TmaMode::kDecode)
-            tma_load_1d(smem_addr(&sl.R[lane][0]), im.r3_in + lane * n + off, 2u * (uint32_t)bytes, bar);
-        else
-            tma_load_1d(smem_addr(&sl.M[lane][0]), im.m3 + lane * n + off, (uint32_t)bytes, bar);
-    } else if (lane == 3) {
-        tma_load_1d(smem_addr(&sl.E[0]), im.e + off, (uint32_t)bytes, bar);
+struct TileSmem {
+    uint32_t s_ring, a_ring, bars, extra;
+    __device__ __forceinline__ uint32_t sfull(int k) const { return bars + 8u * k; }
+    __device__ __forceinline__ uint32_t sempty(int k) const { return bars + 8u * (kTileS + k); }
+    __device__ __forceinline__ uint32_t afull(int k) const { return bars + 8u * (2 * kTileS + k); }
+    __device__ __forceinline__ uint32_t aempty(int k) const { return bars + 8u * (2 * kTileS + kTileA + k); }
+    __device__ __forceinline__ uint32_t sslot(uint32_t i) const { return s_ring + (i % kTileS) * kTileSStride; }
+    __device__ __forceinline__ uint32_t aslot(uint32_t i) const {
+        return a_ring + (i % kTileA) * TileAux<MODE>::kStride;
     }
-}
-
-// The two producers and the consumer's bookkeeping of one warp's rings.
-template <TmaMode MODE>
-struct RowPipe {
-    SRow* ring;
-    AuxSlot<MODE>* aux;
-    unsigned long long* bars;    // kSSlots S barriers, then kAuxSlots aux barriers
-    // S producer: task and item (0 .. rows + 1) issued next
-    RowRange P;
-    bool p_valid;
-    int pk, p_slot, issued, released;
-    // aux producer: the warp's rows one by one
-    RowRange A;
-    bool a_valid;
-    int aj, a_slot, a_issued;
-    // consumer: S slot of the task's first item, expected phase parities, the
-    // warp's row count q and the aux slot of row q
-    int c_slot, q, mc;
-    uint32_t par, mpar;
-
-    __device__ __forceinline__ void init(const RowRange& R) {
-        P = R;
-        p_valid = P.next();
-        pk = p_slot = issued = released = 0;
-        A = R;
-        a_valid = A.next();
-        aj = a_slot = a_issued = 0;
-        c_slot = q = mc = 0;
-        par = mpar = 0u;
-    }
-    __device__ __forceinline__ uint32_t sbar(int s) const { return smem_addr(&bars[s]); }
-    __device__ __forceinline__ uint32_t abar(int s) const { return smem_addr(&bars[kSSlots + s]); }
-
-    // keep kSSlots S items in flight or unreleased
-    __device__ __forceinline__ void refill_s(const TmaImage& im, int64_t n, int lane) {
-        while (p_valid && issued < released + kSSlots) {
-            issue_s(im, n, min(max(P.y0 - 1 + pk, 0), im.h - 1), P.xs, ring[p_slot], sbar(p_slot), lane);
-            ++issued;
-            p_slot = p_slot + 1 == kSSlots ? 0 : p_slot + 1;
-            if (++pk == P.rows + 2) {
-                pk = 0;
-                p_valid = P.next();
-            }
-        }
-    }
-    // keep rows q_done .. q_done + kAuxSlots - 1 in flight or ready
-    __device__ __forceinline__ void refill_aux(const TmaImage& im, int64_t n, int q_done, int lane) {
-        while (a_valid && a_issued < q_done + kAuxSlots) {
-            issue_aux<MODE>(im, n, A.y0 + aj, A.xs, aux[a_slot], abar(a_slot), lane);
-            ++a_issued;
-            a_slot = a_slot + 1 == kAuxSlots ? 0 : a_slot + 1;
-            if (++aj == A.rows) {
-                aj = 0;
-                a_valid = A.next();
-            }
-        }
-    }
-    // after a wait gave up: a bounded wait for every unreleased copy (each
-    // has a slot of its own)
-    __device__ __forceinline__ void drain_in_flight() {
-        int s = p_slot;
-        for (int g = issued - 1; g >= released; --g) {
-            s = s == 0 ? kSSlots - 1 : s - 1;
-            mbar_wait(sbar(s), (par >> s) & 1u, &g_slrme_status, 1 << 10);
-        }
-        s = a_slot;
-        for (int g = a_issued - 1; g >= q; --g) {
-            s = s == 0 ? kAuxSlots - 1 : s - 1;
-            mbar_wait(abar(s), (mpar >> s) & 1u, &g_slrme_status, 1 << 10);
-        }
-    }
+    static constexpr uint32_t kRings = kTileS * kTileSStride + kTileA * TileAux<MODE>::kStride;
+    static constexpr uint32_t kHead = kRings + 8u * 2 * (kTileS + kTileA);   // multiple of 16
 };
 
 template <TmaMode MODE>
-constexpr size_t rows_smem_bytes(int warps) {
-    return (sizeof(SRow) * kSSlots + sizeof(AuxSlot<MODE>) * kAuxSlots + 8 * (kSSlots + kAuxSlots)) * warps;
+__device__ __forceinline__ TileSmem<MODE> tile_smem(char* dyn) {
+    const uint32_t base = (smem_addr(dyn) + 127u) & ~127u;
+    TileSmem<MODE> L;
+    L.s_ring = base;
+    L.a_ring = base + kTileS * kTileSStride;
+    L.bars = base + TileSmem<MODE>::kRings;
+    L.extra = base + TileSmem<MODE>::kHead;
+    return L;
 }
 
-// k_rows_tma<kResidual>: R = M - M* and histograms; k_rows_tma<kDecode>:
-// M = R + M*, repacked with E.
 template <TmaMode MODE>
-__global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage im, const slrme_params* __restrict__ P,
-                                                                uint32_t* __restrict__ ghist, int64_t total_rows,
-                                                                int max_spins) {
-    extern __shared__ __align__(128) char dyn[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    RowPipe<MODE> pp;
-    pp.ring = reinterpret_cast<SRow*>(dyn) + warp * kSSlots;
-    char* tail = dyn + sizeof(SRow) * kSSlots * kRowWarps;
-    pp.aux = reinterpret_cast<AuxSlot<MODE>*>(tail) + warp * kAuxSlots;
-    tail += sizeof(AuxSlot<MODE>) * kAuxSlots * kRowWarps;
-    pp.bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kSSlots + kAuxSlots);
-    tail += 8 * (kSSlots + kAuxSlots) * kRowWarps;
-    float2* ab = reinterpret_cast<float2*>(tail);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(ab + 3 * kNbin);
-
-    load_params_ab(P, ab);
-    if (MODE == TmaMode::kResidual && ghist)
-        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
-    if (lane == 0) {
-        for (int k = 0; k < kSSlots + kAuxSlots; ++k) mbar_init(smem_addr(&pp.bars[k]), 1);
+__device__ __forceinline__ void tile_init_barriers(const TileSmem<MODE>& L) {
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kTileS; ++k) {
+            mbar_init(L.sfull(k), 1);
+            mbar_init(L.sempty(k), kTileWarps);
+        }
+        for (int k = 0; k < kTileA; ++k) {
+            mbar_init(L.afull(k), 1);
+            mbar_init(L.aempty(k), kTileWarps);
+        }
         fence_async_shared();
     }
+}
+
+// The producer (one thread): items in the order the consumers use them.
+// Returns false if a wait for a free slot gave up.
+template <TmaMode MODE>
+__device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const CUtensorMap* tm_s, const CUtensorMap* tm_a,
+                                          const CUtensorMap* tm_e, const TileArgs& A) {
+    TileRange P = tile_range(A.total_rows, A.h);
+    uint32_t si = 0, ai = 0;
+    bool ok = true;
+    while (ok && P.next()) {
+        for (int k = 0; k < P.rows + 2 && ok; ++k) {
+            // S item k: row y0 - 1 + k, clamped (edge rows replicate)
+            {
+                const int slot = (int)(si % kTileS);
+                if (si >= (uint32_t)kTileS)
+                    ok = mbar_wait(L.sempty(slot), ((si / kTileS) - 1u) & 1u, &g_slrme_status, A.max_spins);
+                if (!ok) break;
+                const int ys = min(max(P.y0 - 1 + k, 0), A.h - 1);
+                fence_async_shared();
+                mbar_arrive_expect_tx(L.sfull(slot), kTileSBytes);
+                tma_load_4d(L.sslot(si), tm_s, 0, P.xs / 16 - 1, ys, 0, L.sfull(slot));
+                ++si;
+            }
+            if (k >= 2) {   // the other planes of row y0 + k - 2
+                const int slot = (int)(ai % kTileA);
+                if (ai >= (uint32_t)kTileA)
+                    ok = mbar_wait(L.aempty(slot), ((ai / kTileA) - 1u) & 1u, &g_slrme_status, A.max_spins);
+                if (!ok) break;
+                const int y = P.y0 + k - 2;
+                const uint32_t dst = L.aslot(ai);
+                fence_async_shared();
+                mbar_arrive_expect_tx(L.afull(slot), TileAux<MODE>::kBytes);
+                if constexpr (MODE == TmaMode::kDecode)
+                    tma_load_4d(dst, tm_a, 0, P.xs / 8, y, 0, L.afull(slot));
+                else
+                    tma_load_4d(dst, tm_a, 0, P.xs / 16, y, 0, L.afull(slot));
+                tma_load_4d(dst + TileAux<MODE>::kE, tm_e, 0, P.xs / 16, y, 0, L.afull(slot));
+                ++ai;
+            }
+        }
+    }
+    // before leaving, wait (bounded) for the last copy into every slot, so
+    // no copy is in flight if the consumers stopped early
+    const int spins = ok ? A.max_spins : (1 << 10);
+    for (uint32_t k = si > (uint32_t)kTileS ? si - kTileS : 0; k < si; ++k)
+        mbar_wait(L.sfull((int)(k % kTileS)), (k / kTileS) & 1u, &g_slrme_status, spins);
+    for (uint32_t k = ai > (uint32_t)kTileA ? ai - kTileA : 0; k < ai; ++k)
+        mbar_wait(L.afull((int)(k % kTileA)), (k / kTileA) & 1u, &g_slrme_status, spins);
+}
+
+// A consumer warp is done with a slot (all lanes call after their last read).
+__device__ __forceinline__ void tile_release(uint32_t empty_bar, int lane) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty_bar);
+}
+
+// One consumer warp's view of the rings: waits and releases by item index.
+template <TmaMode MODE>
+struct TileConsumer {
+    TileSmem<MODE> L;
+    int max_spins;
+    __device__ __forceinline__ bool wait_s(uint32_t i) const {
+        return mbar_wait(L.sfull((int)(i % kTileS)), (i / kTileS) & 1u, &g_slrme_status, max_spins);
+    }
+    __device__ __forceinline__ bool wait_a(uint32_t i) const {
+        return mbar_wait(L.afull((int)(i % kTileA)), (i / kTileA) & 1u, &g_slrme_status, max_spins);
+    }
+    // all lanes call after their last read of the items
+    __device__ __forceinline__ void release_s(uint32_t i, int lane) const {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(L.sempty((int)(i % kTileS)));
+    }
+    __device__ __forceinline__ void release_a(uint32_t i, int lane) const {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(L.aempty((int)(i % kTileA)));
+    }
+};
+
+// One lane's S row segment from an S slot (shared address): 8 bytes plus the
+// neighbours at the given offsets.
+__device__ __forceinline__ Row10 tile_seg(uint32_t row, int own, int offl, int offr) {
+    Row10 R;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(R.lo), "=r"(R.hi) : "r"(row + own));
+    uint32_t l, r;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(l) : "r"(row + offl));
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(r) : "r"(row + offr));
+    R.l = l;
+    R.r = r;
+    return R;
+}
+
+__device__ __forceinline__ uint2 lds64(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+// Per-lane geometry of a task: the lane's 8 columns and its S byte offsets.
+struct LaneCols {
+    int x0, own, offl, offr;
+    bool inside;
+    __device__ __forceinline__ LaneCols(int xs, int w, int warp, int lane) {
+        x0 = xs + kStripCols * warp + 8 * lane;
+        own = 16 + kStripCols * warp + 8 * lane;
+        offl = x0 == 0 ? own : own - 1;
+        offr = x0 + 8 >= w ? own + 7 : own + 8;
+        inside = x0 < w;
+    }
+};
+
+// x = 16 S* of channel c for the lane's 8 pixels, as 16-bit pairs.
+__device__ __forceinline__ void tile_x(uint32_t sa, uint32_t sb, uint32_t sc, int c, const LaneCols& lc, bool gf,
+                                       uint32_t (&X)[4]) {
+    const uint32_t po = (uint32_t)c * kTileSW;
+    if (gf) {
+        gf_pairs(tile_seg(sa + po, lc.own, lc.offl, lc.offr), tile_seg(sb + po, lc.own, lc.offl, lc.offr),
+                 tile_seg(sc + po, lc.own, lc.offl, lc.offr), true, X);
+    } else {
+        const Row10 r = tile_seg(sb + po, lc.own, lc.offl, lc.offr);
+        gf_pairs(r, r, r, false, X);
+    }
+}
+
+// ---------------------------------------------------------------- fit on the tile pipeline
+
+// One channel of an 8-pixel segment added to a run: x pairs and y bytes
+// already masked to the run's pixels.
+__device__ __forceinline__ void chan_accum(const uint32_t (&x)[4], uint32_t yl, uint32_t yh, RunAcc& a, int c) {
+    uint32_t sx = a.sx[c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sx = __dp2a_lo(x[k], 0x0101u, sx);
+    a.sx[c] = sx;
+    a.sy[c] = __dp4a(yl, 0x01010101u, __dp4a(yh, 0x01010101u, a.sy[c]));
+    uint32_t q = __dp2a_lo(x[0], yl, a.sxy[c]);
+    q = __dp2a_hi(x[1], yl, q);
+    q = __dp2a_lo(x[2], yh, q);
+    a.sxy[c] = __dp2a_hi(x[3], yh, q);
+    uint32_t r = a.sxx[c];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t lo16 = x[k] & 0xFFFFu, hi16 = x[k] >> 16;
+        r += lo16 * lo16 + hi16 * hi16;
+    }
+    a.sxx[c] = r;
+}
+
+constexpr uint32_t kFitExtra = sizeof(SmemBins) + sizeof(uint32_t) * kTileWarps * 32 * kQueueStride;
+constexpr size_t kTileFitSmem = 128 + TileSmem<TmaMode::kFit>::kHead + kFitExtra;
+
+// Queues the even run (all - odd, region all.E) of every lane with `want` set.
+__device__ __forceinline__ void enqueue_even(FitWarp& st, bool want, const RunAcc& all, const RunAcc& odd,
+                                             SmemBins& bins, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    if (st.queued + __popc(m) > 32) fit_drain<true>(st, bins, lane);
+    if (want) {
+        uint32_t* q = st.Q + (st.queued + __popc(m & ((1u << lane) - 1u))) * kQueueStride;
+        q[0] = all.n - odd.n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[1 + 4 * c] = all.sx[c] - odd.sx[c];
+            q[2 + 4 * c] = all.sy[c] - odd.sy[c];
+            q[3 + 4 * c] = all.sxy[c] - odd.sxy[c];
+            q[4 + 4 * c] = all.sxx[c] - odd.sxx[c];
+        }
+        q[20] = 256u + (uint32_t)all.E;
+    }
+    __syncwarp();
+    st.queued += __popc(m);
+}
+
+// Per lane: `all` holds the sums of both runs, `odd` those of the odd run;
+// the even run is all - odd.  A run that changes region leaves through the
+// warp's queue; a task's runs are flushed every kRunRows rows and at its end.
+__global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_constant__ CUtensorMap tm_s,
+                                                               const __grid_constant__ CUtensorMap tm_a,
+                                                               const __grid_constant__ CUtensorMap tm_e,
+                                                               const TileArgs A) {
+    extern __shared__ __align__(128) char dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TileSmem<TmaMode::kFit> L = tile_smem<TmaMode::kFit>(dyn);
+    char* extra = dyn + (L.extra - smem_addr(dyn));
+    SmemBins& bins = *reinterpret_cast<SmemBins*>(extra);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(extra + sizeof(SmemBins));
+    bins_clear(bins);
+    tile_init_barriers(L);
     __syncthreads();
 
-    const int h = im.h, w = im.w;
-    const int64_t n = (int64_t)h * w;
-    const RowRange R0 = warp_rows(total_rows, h, kRowWarps);
-    pp.init(R0);
-    RowRange C = R0;
-    bool c_valid = C.next();
+    if (warp == kTileWarps) {
+        if (lane == 0) tile_produce(L, &tm_s, &tm_a, &tm_e, A);
+        return;
+    }
+    const TileConsumer<TmaMode::kFit> C{L, A.max_spins};
+    const int w = A.w;
+    const bool gf = A.gf != 0;
+    FitWarp st;
+    st.Q = queue + warp * 32 * kQueueStride;
+    st.queued = 0;
+    RunAcc all, odd;
+    TileRange T = tile_range(A.total_rows, A.h);
+    uint32_t si = 0, ai = 0;
     bool ok = true;
-    pp.refill_aux(im, n, 0, lane);
-    pp.refill_s(im, n, lane);
-
-    while (c_valid && ok) {
-        const int x0 = C.xs + 8 * lane;
-        const int own = 16 + 8 * lane;
-        const int offl = x0 == 0 ? own : own - 1;
-        const int offr = x0 + 8 >= w ? own + 7 : own + 8;
-        int a = pp.c_slot, b = a + 1 == kSSlots ? 0 : a + 1;
-        ok = mbar_wait(pp.sbar(a), (pp.par >> a) & 1u, &g_slrme_status, max_spins) &&
-             mbar_wait(pp.sbar(b), (pp.par >> b) & 1u, &g_slrme_status, max_spins);
-        for (int j = 0; j < C.rows && ok; ++j, ++pp.q) {
-            const int c2 = b + 1 == kSSlots ? 0 : b + 1;
-            ok = mbar_wait(pp.sbar(c2), (pp.par >> c2) & 1u, &g_slrme_status, max_spins) &&
-                 mbar_wait(pp.abar(pp.mc), (pp.mpar >> pp.mc) & 1u, &g_slrme_status, max_spins);
+    while (ok && T.next()) {
+        const LaneCols lc(T.xs, w, warp, lane);
+        run_reset(all, -1);
+        run_reset(odd, -1);
+        ok = C.wait_s(si) && C.wait_s(si + 1);
+        for (int j = 0; j < T.rows && ok; ++j) {
+            ok = C.wait_s(si + j + 2) && C.wait_a(ai + j);
             if (!ok) break;
-            const AuxSlot<MODE>& as = pp.aux[pp.mc];
-            const int y = C.y0 + j;
-            if (x0 < w) {
-                const uint2 ev = *reinterpret_cast<const uint2*>(&as.E[8 * lane]);
+            const uint32_t sa = L.sslot(si + j), sb = L.sslot(si + j + 1), sc = L.sslot(si + j + 2);
+            const uint32_t as = L.aslot(ai + j) + kStripCols * warp + 8 * lane;
+            const uint2 ev = lds64(as + TileAux<TmaMode::kFit>::kE);
+            const uint32_t elo = ev.x, ehi = ev.y;
+            // byte masks of the odd-exponent pixels and the two exponents
+            const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+            const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
+            const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
+            const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 && ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
+                             ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
+                             ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
+            const bool slow = lc.inside && !two;
+            const bool take = lc.inside && two;
+            const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
+            const bool chg_o = po_n != 0u && (int)Eo != odd.E;
+            const bool chg_e = take && po_n != 8u && (int)Ee != all.E;
+            // a run whose region changes leaves first (the even run is all - odd)
+            enqueue_even(st, chg_e && all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
+            enqueue_run<true>(st, chg_o && odd.E >= 0 && odd.n != 0u, odd, bins, lane);
+            if (chg_e) {
+                const int keep = odd.E;
+                all = odd;        // the even part leaves: all - odd = 0
+                all.E = (int)Ee;
+                odd.E = keep;
+            }
+            if (chg_o) {
+                const int keep = all.E;
+                run_minus(all, odd);
+                all.E = keep;
+                run_reset(odd, (int)Eo);
+            }
+            const unsigned want = __ballot_sync(0xffffffffu, slow);
+            uint32_t* qe = nullptr;
+            if (want) {
+                if (st.queued + __popc(want) > 32) fit_drain<true>(st, bins, lane);
+                qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+            }
+            uint32_t k16[4];
+            mask16(olo, ohi, k16);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint32_t X[4];
+                tile_x(sa, sb, sc, c, lc, gf, X);
+                const uint2 mv = lds64(as + (uint32_t)c * TileAux<TmaMode::kFit>::kPlane);
+                if (take) {
+                    uint32_t xo[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xo[k] = X[k] & k16[k];
+                    chan_accum(xo, mv.x & olo, mv.y & ohi, odd, c);
+                    chan_accum(X, mv.x, mv.y, all, c);
+                }
+                if (slow) {
+                    qe[2 + c] = mv.x;
+                    qe[5 + c] = mv.y;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[k];
+                }
+            }
+            odd.n += po_n;
+            all.n += take ? 8u : 0u;
+            if (want) {
+                if (slow) {
+                    qe[0] = elo;
+                    qe[1] = ehi;
+                    qe[20] = 8u;
+                }
+                __syncwarp();
+                st.queued += __popc(want);
+            }
+            tile_release(L.sempty((int)((si + j) % kTileS)), lane);
+            tile_release(L.aempty((int)((ai + j) % kTileA)), lane);
+            if ((j + 1) % kRunRows == 0 || j + 1 == T.rows) {
+                // bounded runs: flush both (the even run is all - odd)
+                RunAcc e = all;
+                run_minus(e, odd);
+                e.E = all.E;
+                warp_flush(e, bins, lane);
+                warp_flush(odd, bins, lane);
+                run_reset(all, -1);
+                run_reset(odd, -1);
+            }
+        }
+        if (!ok) break;
+        tile_release(L.sempty((int)((si + T.rows) % kTileS)), lane);
+        tile_release(L.sempty((int)((si + T.rows + 1) % kTileS)), lane);
+        si += T.rows + 2;
+        ai += T.rows;
+    }
+    if (ok) fit_drain<true>(st, bins, lane);
+    consumers_sync();
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += kTileWarps * 32) {
+        const unsigned long long v = ((unsigned long long)bins.hi[i] << 12) + bins.lo[i];
+        if (v) atomicAdd(A.gbins + i, v);
+    }
+}
+
+// ---------------------------------------------------------------- residual / decode on the tile pipeline
+
+template <TmaMode MODE>
+constexpr size_t tile_rows_smem() {
+    return 128 + TileSmem<MODE>::kHead + sizeof(float2) * 3 * kNbin +
+           (MODE == TmaMode::kResidual ? sizeof(uint32_t) * 3 * kNres : 0);
+}
+
+// k_rows_tile<kResidual>: R = M - M* and histograms; k_rows_tile<kDecode>:
+// M = R + M*, repacked with E.
+template <TmaMode MODE>
+__global__ void __launch_bounds__(kTileThreads, 2) k_rows_tile(const __grid_constant__ CUtensorMap tm_s,
+                                                                const __grid_constant__ CUtensorMap tm_a,
+                                                                const __grid_constant__ CUtensorMap tm_e,
+                                                                const TileArgs A) {
+    extern __shared__ __align__(128) char dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TileSmem<MODE> L = tile_smem<MODE>(dyn);
+    char* extra = dyn + (L.extra - smem_addr(dyn));
+    float2* ab = reinterpret_cast<float2*>(extra);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ab + 3 * kNbin);
+    load_params_ab(A.params, ab);
+    if (MODE == TmaMode::kResidual && A.hist)
+        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
+    tile_init_barriers(L);
+    __syncthreads();
+
+    if (warp == kTileWarps) {
+        if (lane == 0) tile_produce(L, &tm_s, &tm_a, &tm_e, A);
+        return;
+    }
+    const TileConsumer<MODE> C{L, A.max_spins};
+    const int w = A.w;
+    const int64_t n = (int64_t)A.h * w;
+    const bool gf = A.gf != 0;
+    TileRange T = tile_range(A.total_rows, A.h);
+    uint32_t si = 0, ai = 0;
+    bool ok = true;
+    while (ok && T.next()) {
+        const LaneCols lc(T.xs, w, warp, lane);
+        ok = C.wait_s(si) && C.wait_s(si + 1);
+        for (int j = 0; j < T.rows && ok; ++j) {
+            ok = C.wait_s(si + j + 2) && C.wait_a(ai + j);
+            if (!ok) break;
+            const uint32_t sa = L.sslot(si + j), sb = L.sslot(si + j + 1), sc = L.sslot(si + j + 2);
+            const uint32_t as = L.aslot(ai + j);
+            const int y = T.y0 + j;
+            if (lc.inside) {
+                const uint2 ev = lds64(as + TileAux<MODE>::kE + kStripCols * warp + 8 * lane);
                 if constexpr (MODE == TmaMode::kResidual) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         uint32_t X[4];
-                        gf_pairs(seg_row(pp.ring[a].S[c], own, offl, offr), seg_row(pp.ring[b].S[c], own, offl, offr),
-                                 seg_row(pp.ring[c2].S[c], own, offl, offr), im.gf, X);
-                        const uint2 mv = *reinterpret_cast<const uint2*>(&as.M[c][8 * lane]);
+                        tile_x(sa, sb, sc, c, lc, gf, X);
+                        const uint2 mv = lds64(as + (uint32_t)c * TileAux<MODE>::kPlane + kStripCols * warp + 8 * lane);
                         int rr[8];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -1244,8 +1500,8 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage i
                         v.y = (uint32_t)(rr[2] & 0xFFFF) | ((uint32_t)rr[3] << 16);
                         v.z = (uint32_t)(rr[4] & 0xFFFF) | ((uint32_t)rr[5] << 16);
                         v.w = (uint32_t)(rr[6] & 0xFFFF) | ((uint32_t)rr[7] << 16);
-                        *reinterpret_cast<uint4*>(im.r3_out + c * n + (int64_t)y * w + x0) = v;
-                        if (ghist) {
+                        *reinterpret_cast<uint4*>(A.r3_out + c * n + (int64_t)y * w + lc.x0) = v;
+                        if (A.hist) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
                         }
@@ -1257,9 +1513,9 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage i
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         uint32_t X[4];
-                        gf_pairs(seg_row(pp.ring[a].S[c], own, offl, offr), seg_row(pp.ring[b].S[c], own, offl, offr),
-                                 seg_row(pp.ring[c2].S[c], own, offl, offr), im.gf, X);
-                        const uint4 v = *reinterpret_cast<const uint4*>(&as.R[c][8 * lane]);
+                        tile_x(sa, sb, sc, c, lc, gf, X);
+                        const uint4 v =
+                            lds128(as + (uint32_t)c * TileAux<MODE>::kPlane + 2u * (kStripCols * warp + 8 * lane));
                         const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -1270,36 +1526,24 @@ __global__ void __launch_bounds__(kRowWarps * 32, 2) k_rows_tma(const TmaImage i
                             word[i] |= ((uint32_t)M & 255u) << (8 * c);
                         }
                     }
-                    uint4* o4 = reinterpret_cast<uint4*>(im.out + (int64_t)y * w + x0);
+                    uint4* o4 = reinterpret_cast<uint4*>(A.out + (int64_t)y * w + lc.x0);
                     o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
                     o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
                 }
             }
-            // S item j (slot a) and the aux row q are done: release and refill
-            pp.par ^= 1u << a;
-            ++pp.released;
-            a = b;
-            b = c2;
-            pp.mpar ^= 1u << pp.mc;
-            pp.mc = pp.mc + 1 == kAuxSlots ? 0 : pp.mc + 1;
-            __syncwarp();
-            pp.refill_aux(im, n, pp.q + 1, lane);
-            pp.refill_s(im, n, lane);
+            C.release_s(si + j, lane);
+            C.release_a(ai + j, lane);
         }
         if (!ok) break;
-        // the last two S items of the task
-        pp.par ^= (1u << a) | (1u << b);
-        pp.released += 2;
-        pp.c_slot = b + 1 == kSSlots ? 0 : b + 1;
-        __syncwarp();
-        pp.refill_s(im, n, lane);
-        c_valid = C.next();
+        C.release_s(si + T.rows, lane);
+        C.release_s(si + T.rows + 1, lane);
+        si += T.rows + 2;
+        ai += T.rows;
     }
-    if (!ok) pp.drain_in_flight();
-    if (MODE == TmaMode::kResidual && ghist) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x)
-            if (hist[i]) atomicAdd(ghist + i, hist[i]);
+    if (MODE == TmaMode::kResidual && A.hist) {
+        consumers_sync();
+        for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32)
+            if (hist[i]) atomicAdd(A.hist + i, hist[i]);
     }
 }
 
@@ -1310,214 +1554,107 @@ bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
     return true;
 }
 
-template <TmaMode MODE>
-int launch_rows_tma(const TmaImage& im, const slrme_params* P, uint32_t* hist, cudaStream_t s) {
-    static bool attr_set[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("row pipeline device");
-    constexpr size_t smem = rows_smem_bytes<MODE>(kRowWarps) + sizeof(float) * 6 * kNbin + sizeof(uint32_t) * 3 * kNres;
-    if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_rows_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return cuda_status("row pipeline smem attribute");
-        attr_set[dev] = true;
+// ---------------------------------------------------------------- tensor maps (host)
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map of `planes` planes of h x w pixels of `esize` bytes, viewed as
+// (16-byte chunk, chunk, row, plane); a box is one row of `box_chunks` chunks
+// of every plane.
+bool plane_map(CUtensorMap* tm, const void* base, int esize, int h, int w, int planes, int box_chunks) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return false;
     }
-    // every warp gets at least 4 rows; at most 2 CTAs of 8 warps per SM
-    const int64_t total_rows = (int64_t)((im.w + kStripCols - 1) / kStripCols) * im.h;
-    int64_t warps = (total_rows + 3) / 4;
-    const int64_t cap = (int64_t)geometry().sms * 2 * kRowWarps;
-    if (warps > cap) warps = cap;
-    const int64_t g = (warps + kRowWarps - 1) / kRowWarps;
-    k_rows_tma<MODE><<<(unsigned)(g < 1 ? 1 : g), kRowWarps * 32, smem, s>>>(im, P, hist, total_rows, kMaxSpins);
+    const cuuint64_t row = (cuuint64_t)w * esize;
+    const cuuint64_t dims[4] = {(cuuint64_t)(16 / esize), row / 16, (cuuint64_t)h, (cuuint64_t)planes};
+    const cuuint64_t strides[3] = {16, row, row * (cuuint64_t)h};
+    const cuuint32_t box[4] = {(cuuint32_t)(16 / esize), (cuuint32_t)box_chunks, 1, (cuuint32_t)planes};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(tm, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 4,
+                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d plane map", (int)r, h, w);
+        return false;
+    }
+    return true;
+}
+
+template <TmaMode MODE>
+bool tile_maps(TileMaps& M, const uint8_t* s3, const void* aux, const uint8_t* e, int h, int w) {
+    return plane_map(&M.s, s3, 1, h, w, 3, kTileSW / 16) &&
+           plane_map(&M.a, aux, (int)TileAux<MODE>::kElem, h, w, 3, (int)(TileAux<MODE>::kElem * kTileCols / 16)) &&
+           plane_map(&M.e, e, 1, h, w, 1, kTileCols / 16);
+}
+
+// Grid of a tile kernel: two CTAs per SM at most, at least four rows per
+// CTA, and for the fit at least total_rows / rows_max CTAs.
+int64_t tile_grid(int64_t total_rows, int64_t rows_max) {
+    int64_t g = (total_rows + 3) / 4;
+    const int64_t cap = (int64_t)geometry().sms * 2;
+    if (g > cap) g = cap;
+    if (rows_max > 0 && g < (total_rows + rows_max - 1) / rows_max) g = (total_rows + rows_max - 1) / rows_max;
+    return g < 1 ? 1 : g;
+}
+
+template <typename K>
+int tile_smem_attr(K kernel, size_t bytes, bool* set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("tile kernel device");
+    if (!set[dev]) {
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+            return cuda_status("tile kernel shared memory attribute");
+        set[dev] = true;
+    }
+    return SLRME_OK;
+}
+
+template <TmaMode MODE>
+int launch_rows_tile(const uint8_t* s3, const void* aux, const uint8_t* e, int h, int w, int gf_on,
+                     const slrme_params* P, int16_t* r3_out, uint32_t* hist, uint32_t* out, cudaStream_t s) {
+    static bool attr_set[64];
+    constexpr size_t smem = tile_rows_smem<MODE>();
+    int st = tile_smem_attr(k_rows_tile<MODE>, smem, attr_set);
+    if (st != SLRME_OK) return st;
+    TileMaps M;
+    if (!tile_maps<MODE>(M, s3, aux, e, h, w)) return SLRME_ECUDA;
+    const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
+    TileArgs A{h, w, gf_on, total_rows, kMaxSpins, P, r3_out, hist, out, nullptr};
+    k_rows_tile<MODE><<<(unsigned)tile_grid(total_rows, 0), kTileThreads, smem, s>>>(M.s, M.a, M.e, A);
     return cuda_status(MODE == TmaMode::kResidual ? "residual_encode launch" : "residual_decode launch");
 }
 
-// ====================================================================== TMA-staged fit
-//
-// k_fit_tma: the fit on the row pipelines above (M / E as the other planes).
-// Per lane one run per exponent parity is fed with the SIMD byte-mask sums of
-// its 8-pixel segments; a run that has to leave its accumulator inside a
-// strip goes to the warp's queue, with the segments that hold more exponents,
-// and the warp drains the queue 32 entries at a time.
-
-constexpr size_t kFitSmem = rows_smem_bytes<TmaMode::kFit>(kRowWarps) + sizeof(SmemBins) +
-                            sizeof(uint32_t) * kRowWarps * 32 * kQueueStride;
-
-__global__ void __launch_bounds__(kRowWarps * 32, 2) k_fit_tma(const TmaImage im, int64_t total_rows,
-                                                                unsigned long long* __restrict__ gbins, int max_spins) {
-    extern __shared__ __align__(128) char dyn[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    RowPipe<TmaMode::kFit> pp;
-    pp.ring = reinterpret_cast<SRow*>(dyn) + warp * kSSlots;
-    char* tail = dyn + sizeof(SRow) * kSSlots * kRowWarps;
-    pp.aux = reinterpret_cast<AuxSlot<TmaMode::kFit>*>(tail) + warp * kAuxSlots;
-    tail += sizeof(AuxSlot<TmaMode::kFit>) * kAuxSlots * kRowWarps;
-    pp.bars = reinterpret_cast<unsigned long long*>(tail) + warp * (kSSlots + kAuxSlots);
-    tail += 8 * (kSSlots + kAuxSlots) * kRowWarps;
-    SmemBins& bins = *reinterpret_cast<SmemBins*>(tail);
-    uint32_t* queue = reinterpret_cast<uint32_t*>(tail + sizeof(SmemBins));
-
-    bins_clear(bins);
-    if (lane == 0) {
-        for (int k = 0; k < kSSlots + kAuxSlots; ++k) mbar_init(smem_addr(&pp.bars[k]), 1);
-        fence_async_shared();
-    }
-    __syncthreads();
-
-    const int h = im.h, w = im.w;
-    const int64_t n = (int64_t)h * w;
-    const RowRange R0 = warp_rows(total_rows, h, kRowWarps);
-    pp.init(R0);
-
-    FitWarp st;
-    run_reset(st.even, -1);
-    run_reset(st.odd, -1);
-    st.Q = queue + warp * 32 * kQueueStride;
-    st.queued = 0;
-
-    RowRange C = R0;
-    bool c_valid = C.next();
-    bool ok = true;
-    pp.refill_aux(im, n, 0, lane);
-    pp.refill_s(im, n, lane);
-
-    while (c_valid && ok) {
-        const int x0 = C.xs + 8 * lane;
-        const int own = 16 + 8 * lane;
-        const int offl = x0 == 0 ? own : own - 1;
-        const int offr = x0 + 8 >= w ? own + 7 : own + 8;
-        const bool inside = x0 < w;
-        int a = pp.c_slot, b = a + 1 == kSSlots ? 0 : a + 1;
-        ok = mbar_wait(pp.sbar(a), (pp.par >> a) & 1u, &g_slrme_status, max_spins) &&
-             mbar_wait(pp.sbar(b), (pp.par >> b) & 1u, &g_slrme_status, max_spins);
-        for (int j = 0; j < C.rows && ok; ++j, ++pp.q) {
-            const int c2 = b + 1 == kSSlots ? 0 : b + 1;
-            ok = mbar_wait(pp.sbar(c2), (pp.par >> c2) & 1u, &g_slrme_status, max_spins) &&
-                 mbar_wait(pp.abar(pp.mc), (pp.mpar >> pp.mc) & 1u, &g_slrme_status, max_spins);
-            if (!ok) break;
-            const AuxSlot<TmaMode::kFit>& ms = pp.aux[pp.mc];
-            const uint2 ev = *reinterpret_cast<const uint2*>(&ms.E[8 * lane]);
-            const uint32_t elo = ev.x, ehi = ev.y;
-            // byte masks of the odd-exponent pixels and the two exponents
-            const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
-            const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
-            const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
-            const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 && ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
-                             ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
-                             ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
-            // at most one even and one odd exponent: the odd pixels join the
-            // odd run, the rest the even run; other segments go to the queue
-            const bool slow = inside && !two;
-            const bool take = inside && two;
-            const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
-            const uint32_t pe_n = take ? 8u - po_n : 0u;
-            // a run whose region changes leaves its accumulator first
-            enqueue_run<true>(st, pe_n != 0u && (int)Ee != st.even.E && st.even.n != 0u, st.even, bins, lane);
-            enqueue_run<true>(st, po_n != 0u && (int)Eo != st.odd.E && st.odd.n != 0u, st.odd, bins, lane);
-            if (pe_n != 0u && (int)Ee != st.even.E) run_reset(st.even, (int)Ee);
-            if (po_n != 0u && (int)Eo != st.odd.E) run_reset(st.odd, (int)Eo);
-            const unsigned want = __ballot_sync(0xffffffffu, slow);
-            uint32_t* qe = nullptr;
-            if (want) {
-                if (st.queued + __popc(want) > 32) fit_drain<true>(st, bins, lane);
-                qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
-            }
-            // channel by channel: x = 16 S* pairs, the sums of the odd pixels
-            // (by mask) and of all pixels, added straight to the two runs
-            uint32_t k16[4];
-            mask16(olo, ohi, k16);
-            const uint32_t ones[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-            RunAcc po, pa;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uint32_t X[4];
-                gf_pairs(seg_row(pp.ring[a].S[c], own, offl, offr), seg_row(pp.ring[b].S[c], own, offl, offr),
-                         seg_row(pp.ring[c2].S[c], own, offl, offr), im.gf, X);
-                const uint2 mv = *reinterpret_cast<const uint2*>(&ms.M[c][8 * lane]);
-                chan_sums(X, mv.x, mv.y, olo, ohi, k16, po, c);
-                chan_sums(X, mv.x, mv.y, 0xFFFFFFFFu, 0xFFFFFFFFu, ones, pa, c);
-                if (take) {
-                    st.odd.sx[c] += po.sx[c];
-                    st.odd.sy[c] += po.sy[c];
-                    st.odd.sxy[c] += po.sxy[c];
-                    st.odd.sxx[c] += po.sxx[c];
-                    st.even.sx[c] += pa.sx[c] - po.sx[c];
-                    st.even.sy[c] += pa.sy[c] - po.sy[c];
-                    st.even.sxy[c] += pa.sxy[c] - po.sxy[c];
-                    st.even.sxx[c] += pa.sxx[c] - po.sxx[c];
-                }
-                if (slow) {
-                    qe[2 + c] = mv.x;
-                    qe[5 + c] = mv.y;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[k];
-                }
-            }
-            st.odd.n += po_n;
-            st.even.n += pe_n;
-            if (want) {
-                if (slow) {
-                    qe[0] = elo;
-                    qe[1] = ehi;
-                    qe[20] = 8u;
-                }
-                __syncwarp();
-                st.queued += __popc(want);
-            }
-            // S item j (slot a) and the M / E of row q are done: release and refill
-            pp.par ^= 1u << a;
-            ++pp.released;
-            a = b;
-            b = c2;
-            pp.mpar ^= 1u << pp.mc;
-            pp.mc = pp.mc + 1 == kAuxSlots ? 0 : pp.mc + 1;
-            __syncwarp();
-            pp.refill_aux(im, n, pp.q + 1, lane);
-            pp.refill_s(im, n, lane);
-        }
-        if (!ok) break;
-        // the last two S items of the task; every run ends with its task
-        // (bounded: a run holds at most 8 * kMaxStripRows pixels)
-        pp.par ^= (1u << a) | (1u << b);
-        pp.released += 2;
-        pp.c_slot = b + 1 == kSSlots ? 0 : b + 1;
-        warp_flush(st.even, bins, lane);
-        warp_flush(st.odd, bins, lane);
-        run_reset(st.even, -1);
-        run_reset(st.odd, -1);
-        __syncwarp();
-        pp.refill_s(im, n, lane);
-        c_valid = C.next();
-    }
-    if (!ok) pp.drain_in_flight();   // a copy did not arrive in time: stop
-    else fit_drain<true>(st, bins, lane);
-    __syncthreads();
-    bins_to_global(bins, gbins, false);
-}
-
-int launch_fit_tma(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
-                   unsigned long long* bins, cudaStream_t s) {
+int launch_fit_tile(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
+                    unsigned long long* bins, cudaStream_t s) {
     static bool attr_set[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("fit device");
-    if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(k_fit_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFitSmem) !=
-            cudaSuccess)
-            return cuda_status("fit smem attribute");
-        attr_set[dev] = true;
-    }
-    // every warp gets at least 4 rows; at most 2 CTAs of 8 warps per SM,
-    // unless a block would then add more than kMaxBlockPixels pixels (a warp
-    // gets at most ceil(total_rows / warps) rows of at most 256 pixels)
-    const int64_t total_rows = (int64_t)((w + kStripCols - 1) / kStripCols) * h;
-    int64_t warps = (total_rows + 3) / 4;
-    const int64_t cap = (int64_t)geometry().sms * 2 * kRowWarps;
-    if (warps > cap) warps = cap;
-    const int64_t rows_max = kMaxBlockPixels / ((int64_t)kRowWarps * kStripCols);
-    if (warps < (total_rows + rows_max - 1) / rows_max) warps = (total_rows + rows_max - 1) / rows_max;
-    const int64_t g = (warps + kRowWarps - 1) / kRowWarps;
-    const TmaImage im{s3, m3, e, nullptr, nullptr, nullptr, h, w, gf_on != 0};
-    k_fit_tma<<<(unsigned)(g < 1 ? 1 : g), kRowWarps * 32, kFitSmem, s>>>(im, total_rows, bins, kMaxSpins);
+    int st = tile_smem_attr(k_fit_tile, kTileFitSmem, attr_set);
+    if (st != SLRME_OK) return st;
+    TileMaps M;
+    if (!tile_maps<TmaMode::kFit>(M, s3, m3, e, h, w)) return SLRME_ECUDA;
+    const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
+    // a CTA adds at most kMaxBlockPixels pixels to its bins
+    const int64_t rows_max = kMaxBlockPixels / kTileCols;
+    TileArgs A{h, w, gf_on, total_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr, bins};
+    k_fit_tile<<<(unsigned)tile_grid(total_rows, rows_max), kTileThreads, kTileFitSmem, s>>>(M.s, M.a, M.e, A);
     return cuda_status("slr_fit launch");
 }
 
@@ -1571,7 +1708,7 @@ int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, in
                           ((uintptr_t)e % 8 == 0);
         int st;
         if (tma_eligible(w, {s3, m3, e})) {
-            st = launch_fit_tma(s3, m3, e, h, w, gf_on, reinterpret_cast<unsigned long long*>(bin_sums), s);
+            st = launch_fit_tile(s3, m3, e, h, w, gf_on, reinterpret_cast<unsigned long long*>(bin_sums), s);
         } else {
             const StripLaunch L = strip_launch(h, w, 2);
             k_fit<<<fit_strip_blocks(L, h, w), kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows,
@@ -1588,10 +1725,8 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
                            const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                       ((uintptr_t)e % 8 == 0);
-    if (tma_eligible(w, {s3, m3, e, r3})) {
-        const TmaImage im{s3, m3, e, nullptr, r3, nullptr, h, w, gf_on != 0};
-        return launch_rows_tma<TmaMode::kResidual>(im, params, hist, s);
-    }
+    if (tma_eligible(w, {s3, m3, e, r3}))
+        return launch_rows_tile<TmaMode::kResidual>(s3, m3, e, h, w, gf_on, params, r3, hist, nullptr, s);
     const StripLaunch L = strip_launch(h, w, 2);
     k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
     return cuda_status("residual_encode launch");
@@ -1600,10 +1735,8 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
 int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w, int gf_on,
                            const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
-    if (tma_eligible(w, {s3, e, r3, rgbe_out})) {
-        const TmaImage im{s3, nullptr, e, r3, nullptr, rgbe_out, h, w, gf_on != 0};
-        return launch_rows_tma<TmaMode::kDecode>(im, params, nullptr, s);
-    }
+    if (tma_eligible(w, {s3, e, r3, rgbe_out}))
+        return launch_rows_tile<TmaMode::kDecode>(s3, r3, e, h, w, gf_on, params, nullptr, nullptr, rgbe_out, s);
     const StripLaunch L = strip_launch(h, w, 2);
     k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
     return cuda_status("residual_decode launch");

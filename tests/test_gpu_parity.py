@@ -362,10 +362,13 @@ def _device_status():
     return v.value
 
 
-@pytest.mark.parametrize("h,w", [(1, 16), (8, 16), (33, 256), (70, 512), (45, 784), (100, 1040)])
+@pytest.mark.parametrize("h,w", [(1, 16), (8, 16), (33, 256), (70, 512), (45, 784), (100, 1040), (5, 2064),
+                                 (3, 4096), (21, 2560), (80000, 16)])
 @pytest.mark.parametrize("gf_on", [True, False])
 def test_tma_staged_path_matches_oracle(h, w, gf_on):
-    # rows of 16-byte multiples take the bulk-copy (TMA) kernels of fit, residual and decode
+    # rows of 16-byte multiples take the tensor-map (TMA) kernels of fit, residual
+    # and decode: 2048-column strips (one or several, the last one partial), CTA
+    # row ranges that cross from one strip to the next, tasks longer than 256 rows
     _device_status()
     assert_matches_oracle(make_img(h, w, "scene", seed=h + 3 * w), 80, gf_on)
     assert_matches_oracle(make_img(h, w, "noise", seed=h + 5 * w), 80, gf_on)
