@@ -9,14 +9,19 @@
 //   phase 2  (lane = column):  forward 1-D DCT along y, quantise/dequantise,
 //                              inverse 1-D DCT along y; G -> shared
 //   phase 3  (lane = row):     inverse 1-D DCT along x, +128, clamp, store S
-// Only __syncwarp is needed between phases.  The shared tile of a block is
-// 8 rows of stride 9 words and blocks are 72 words apart, which makes both
-// the row-wise and the column-wise accesses of a warp conflict-free.
+// Only __syncwarp is needed between phases.  A block's tile is 8 lines of 8
+// words, blocks 72 words apart: phase 1 writes its row transposed (word
+// 8u + r for coefficient u of row r) and phase 2 writes its column
+// transposed (word 8y + u), so each phase reads its own line as two 16-byte
+// loads, and every scattered 4-byte store of a warp hits 32 distinct banks
+// (lanes differ in 8 * block + line index).
 //
 // Exactness: every product and sum is an exact int32 (worst cases: 2^21
 // after pass 1, 2^25.1 before the second shift, 2^24 and 2^28.2 in the
 // inverse), so the even/odd factorisation below yields the same integers as
-// the plain matrix products with the same rounding shifts.
+// the plain matrix products with the same rounding shifts; the rounding
+// term of each shift (and the +128 of the last one) is added before the
+// shift as part of the sums, which changes no integer.
 #include "slrme_internal.cuh"
 
 #define SLRME_TABLE static __device__ const
@@ -29,34 +34,34 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kTileWords = 3 * 4 * 72;    // per warp: 3 planes x 4 blocks x (8 x 9)
+constexpr int kTileWords = 3 * 4 * 72;    // per warp: 3 planes x 4 blocks x 72 words (64 used)
 
 // Fixed-point DCT constants round(4096 * alpha_u * cos((2x+1) u pi / 16)).
 constexpr int C4 = 1448;   // alpha_0 * 4096 and cos(pi/4) / 2 * 4096
 constexpr int C1 = 2009, C2 = 1892, C3 = 1703, C5 = 1138, C6 = 784, C7 = 400;
 
-__device__ __forceinline__ int rshift_round(int v, int s) { return (v + (1 << (s - 1))) >> s; }
-
-// Forward 8-point transform along one line: out[u] = sum_x D[u][x] in[x].
-__device__ __forceinline__ void fdct8(const int (&x)[8], int (&F)[8]) {
+// Forward 8-point transform along one line: out[u] = sum_x D[u][x] in[x] + r
+// (r, the rounding term of the shift that follows, enters each output's
+// first multiply-add).
+__device__ __forceinline__ void fdct8(const int (&x)[8], int (&F)[8], int r) {
     const int s07 = x[0] + x[7], d07 = x[0] - x[7];
     const int s16 = x[1] + x[6], d16 = x[1] - x[6];
     const int s25 = x[2] + x[5], d25 = x[2] - x[5];
     const int s34 = x[3] + x[4], d34 = x[3] - x[4];
     const int e0 = s07 + s34, e1 = s16 + s25, e2 = s07 - s34, e3 = s16 - s25;
-    F[0] = C4 * (e0 + e1);
-    F[4] = C4 * (e0 - e1);
-    F[2] = C2 * e2 + C6 * e3;
-    F[6] = C6 * e2 - C2 * e3;
-    F[1] = C1 * d07 + C3 * d16 + C5 * d25 + C7 * d34;
-    F[3] = C3 * d07 - C7 * d16 - C1 * d25 - C5 * d34;
-    F[5] = C5 * d07 - C1 * d16 + C7 * d25 + C3 * d34;
-    F[7] = C7 * d07 - C5 * d16 + C3 * d25 - C1 * d34;
+    F[0] = C4 * (e0 + e1) + r;
+    F[4] = C4 * (e0 - e1) + r;
+    F[2] = C2 * e2 + r + C6 * e3;
+    F[6] = C6 * e2 + r - C2 * e3;
+    F[1] = C1 * d07 + r + C3 * d16 + C5 * d25 + C7 * d34;
+    F[3] = C3 * d07 + r - C7 * d16 - C1 * d25 - C5 * d34;
+    F[5] = C5 * d07 + r - C1 * d16 + C7 * d25 + C3 * d34;
+    F[7] = C7 * d07 + r - C5 * d16 + C3 * d25 - C1 * d34;
 }
 
-// Inverse 8-point transform along one line: out[x] = sum_u D[u][x] in[u].
-__device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8]) {
-    const int a = C4 * (F[0] + F[4]), b = C4 * (F[0] - F[4]);
+// Inverse 8-point transform along one line: out[x] = sum_u D[u][x] in[u] + r.
+__device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8], int r) {
+    const int a = C4 * (F[0] + F[4]) + r, b = C4 * (F[0] - F[4]) + r;
     const int c = C2 * F[2] + C6 * F[6], d = C6 * F[2] - C2 * F[6];
     const int E0 = a + c, E3 = a - c, E1 = b + d, E2 = b - d;
     const int O0 = C1 * F[1] + C3 * F[3] + C5 * F[5] + C7 * F[7];
@@ -70,16 +75,17 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8]) {
 }
 
 // 8-bit display value: #{k in 1..255 : v >= gamma[k]} for the increasing
-// threshold table (v >= 0).  Below 2^-20 (< gamma[1]) it is 0, from 1 up
-// (> gamma[255]) 255; in between the bucket of v (exponent and top 8 mantissa
-// bits) holds at most one threshold, so its start count plus one comparison
-// with the next threshold is the count.  `g` has g[256] = +inf.
-__device__ __forceinline__ int gamma_code(float v, const float* g, const uint8_t* start) {
-    const uint32_t bits = __float_as_uint(v);
-    if (bits < 0x35800000u) return 0;        // v < 2^-20
-    if (bits >= 0x3F800000u) return 255;     // v >= 1
-    const int k = start[(bits - 0x35800000u) >> 15];
-    return k + (v >= g[k + 1] ? 1 : 0);
+// threshold table (v >= 0).  The float bits of v pick a bucket (exponent and
+// top 8 mantissa bits over [2^-20, 1), plus one bucket below and one above);
+// a bucket holds at most one threshold, and its word is the count below the
+// bucket plus, from bit 8, the low 15 bits of that threshold (0x8000 when
+// there is none), so the count is one lookup and one integer comparison
+// (positive floats order like their bits).  No branch.
+__device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {
+    const int bits = __float_as_int(v);
+    const int b = min(max((bits - 0x35800000) >> 15, -1), 5120) + 1;
+    const uint32_t e = code[b];
+    return (int)(e & 255u) + ((uint32_t)(bits & 0x7FFF) >= (e >> 8) ? 1 : 0);
 }
 
 // float(v) for 0 <= v < 2^23, exactly (the 2^23 bias).
@@ -119,13 +125,11 @@ __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w
     }
 }
 
-// The threshold table (with g[256] = +inf) and the bucket starts, into
-// shared memory; ends with a block barrier.
-__device__ __forceinline__ void load_gamma(float* gam, uint8_t* gstart) {
-    for (int i = threadIdx.x; i < 257; i += blockDim.x) gam[i] = i < 256 ? __uint_as_float(kGammaBits[i]) : INFINITY;
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(kGammaStart);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(gstart);
-    for (int i = threadIdx.x; i < (int)sizeof(kGammaStart) / 4; i += blockDim.x) dst[i] = src[i];
+// The bucket words of the display code into shared memory; ends with a
+// block barrier.
+constexpr int kGammaWords = 5122;
+__device__ __forceinline__ void load_gamma(uint32_t* code) {
+    for (int i = threadIdx.x; i < kGammaWords; i += blockDim.x) code[i] = kGammaCode[i];
     __syncthreads();
 }
 
@@ -152,8 +156,8 @@ __device__ __forceinline__ void base_key(const int64_t* __restrict__ stats, cons
 
 // One band task of one image (all 32 lanes): rows y0 .. y0+7, columns xb .. xb+31.
 __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h, int w,
-                                          bool fast, int y0, int xb, int lane, const BaseKey& K, const float* gam,
-                                          const uint8_t* gstart, int* T, uint8_t* __restrict__ s3,
+                                          bool fast, int y0, int xb, int lane, const BaseKey& K,
+                                          const uint32_t* gcode, int* T, uint8_t* __restrict__ s3,
                                           uint8_t* __restrict__ sdr3) {
     const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
     const int64_t n = (int64_t)h * w;
@@ -172,11 +176,8 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         int sdr[3][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
+            // computed for every pixel, then zeroed where E = 0 (no branch)
             const int E = ee[i];
-            if (E == 0) {
-                sdr[0][i] = sdr[1][i] = sdr[2][i] = 0;
-                continue;
-            }
             const int yq = 2126 * (2 * mr[i] + 1) + 7152 * (2 * mg[i] + 1) + 722 * (2 * mb[i] + 1);
             int d = E - 137 - J;
             d = d < -100 ? -100 : (d > 100 ? 100 : d);
@@ -184,9 +185,10 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
             const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float(yq)), p2d);
             const float den = __fadd_rn(1.0f, L);
             const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
-            sdr[0][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr[i] + 1)), gam, gstart);
-            sdr[1][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg[i] + 1)), gam, gstart);
-            sdr[2][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb[i] + 1)), gam, gstart);
+            const int keep = E == 0 ? 0 : -1;
+            sdr[0][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr[i] + 1)), gcode) & keep;
+            sdr[1][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg[i] + 1)), gcode) & keep;
+            sdr[2][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb[i] + 1)), gcode) & keep;
         }
         if (sdr3 && x0 < w) {
 #pragma unroll
@@ -201,10 +203,10 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
             int X[8], F[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) X[i] = sdr[c][i] - 128;
-            fdct8(X, F);
-            int* row = T + (c * 4 + blk) * 72 + sub * 9;
+            fdct8(X, F, 1 << 8);
+            int* tile = T + (c * 4 + blk) * 72 + sub;   // coefficient u of row sub at word 8u + sub
 #pragma unroll
-            for (int u = 0; u < 8; ++u) row[u] = rshift_round(F[u], 9);
+            for (int u = 0; u < 8; ++u) tile[8 * u] = F[u] >> 9;
         }
     }
     __syncwarp();
@@ -212,40 +214,40 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
     // ---------------- phase 2: along y: forward DCT, quantiser, inverse DCT
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        int* col = T + (c * 4 + blk) * 72 + sub;
-        int Tc[8], F[8], G[8];
-#pragma unroll
-        for (int yy = 0; yy < 8; ++yy) Tc[yy] = col[yy * 9];
-        fdct8(Tc, F);
+        int* tile = T + (c * 4 + blk) * 72;
+        const int4 c0 = *reinterpret_cast<const int4*>(tile + 8 * sub);       // column sub, rows 0-3
+        const int4 c1 = *reinterpret_cast<const int4*>(tile + 8 * sub + 4);   // rows 4-7
+        const int Tc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        int F[8], G[8];
+        fdct8(Tc, F, 1 << 14);
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            const int f = rshift_round(F[v], 15);
+            const int f = F[v] >> 15;
             const uint32_t a = (uint32_t)(f < 0 ? -f : f);
             const int lvl = (int)__umulhi((a + (uint32_t)(K.qcol[v] >> 1)) << 8, K.qmcol[v]);
             F[v] = (f < 0 ? -lvl : lvl) * K.qcol[v];
         }
-        idct8(F, G);
+        idct8(F, G, 1 << 8);
+        __syncwarp();   // every lane has read its column before the rows are written
 #pragma unroll
-        for (int yy = 0; yy < 8; ++yy) col[yy * 9] = rshift_round(G[yy], 9);
+        for (int yy = 0; yy < 8; ++yy) tile[8 * yy + sub] = G[yy] >> 9;   // row yy, column sub
     }
     __syncwarp();
 
     // ---------------- phase 3: inverse DCT along x, store S
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const int* row = T + (c * 4 + blk) * 72 + sub * 9;
-        int G[8], X[8];
+        const int* tile = T + (c * 4 + blk) * 72 + 8 * sub;   // row sub
+        const int4 g0 = *reinterpret_cast<const int4*>(tile);
+        const int4 g1 = *reinterpret_cast<const int4*>(tile + 4);
+        const int G[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        int X[8];
+        idct8(G, X, (1 << 14) + (128 << 15));
+        uint32_t q[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) G[u] = row[u];
-        idct8(G, X);
-        uint32_t lo = 0, hi = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            int s = rshift_round(X[i], 15) + 128;
-            s = s < 0 ? 0 : (s > 255 ? 255 : s);
-            if (i < 4) lo |= (uint32_t)s << (8 * i);
-            else hi |= (uint32_t)s << (8 * (i - 4));
-        }
+        for (int i = 0; i < 8; ++i) q[i] = (uint32_t)min(max(X[i] >> 15, 0), 255);
+        const uint32_t lo = __byte_perm(__byte_perm(q[0], q[1], 0x0040), __byte_perm(q[2], q[3], 0x0040), 0x5410);
+        const uint32_t hi = __byte_perm(__byte_perm(q[4], q[5], 0x0040), __byte_perm(q[6], q[7], 0x0040), 0x5410);
         if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi);
     }
     __syncwarp();
@@ -255,17 +257,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict_
                                                       int h, int w, const int64_t* __restrict__ lum_stats,
                                                       uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3,
                                                       int fast_io, const QuantTable QT) {
-    __shared__ float gam[257];
-    __shared__ __align__(16) uint8_t gstart[sizeof(kGammaStart)];
-    __shared__ int tile[kWarps][kTileWords];
-    load_gamma(gam, gstart);
+    __shared__ uint32_t gcode[kGammaWords];
+    __shared__ __align__(16) int tile[kWarps][kTileWords];
+    load_gamma(gcode);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BaseKey K;
     base_key(lum_stats, QT, lane & 7, K);
     const int cols = (w + 31) >> 5;
     const int64_t tasks = (int64_t)((h + 7) >> 3) * cols;
     for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
-        base_band(m3, e, h, w, fast_io != 0, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, gstart,
+        base_band(m3, e, h, w, fast_io != 0, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
                   tile[warp], s3, sdr3);
 }
 
@@ -273,10 +274,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict_
 __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, int64_t cta_tasks,
                                                             const uint8_t* __restrict__ m3b,
                                                             const uint8_t* __restrict__ eb, uint8_t* __restrict__ s3b) {
-    __shared__ float gam[257];
-    __shared__ __align__(16) uint8_t gstart[sizeof(kGammaStart)];
-    __shared__ int tile[kWarps][kTileWords];
-    load_gamma(gam, gstart);
+    __shared__ uint32_t gcode[kGammaWords];
+    __shared__ __align__(16) int tile[kWarps][kTileWords];
+    load_gamma(gcode);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
         const bool fast = (im.w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
                           ((uintptr_t)s3 % 8 == 0);
         if ((int64_t)im.h * im.w > 0 && t < bands)
-            base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gam, gstart,
+            base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
                       tile[warp], s3, nullptr);
     }
 }

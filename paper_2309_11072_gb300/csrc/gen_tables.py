@@ -13,6 +13,12 @@ Tables (all built in float64 and rounded once):
                   biased exponent e in 107..126 and top 8 mantissa bits m
                   (v in [2^-20, 1)); no bucket holds more than one threshold,
                   so the display code of v is start + (v >= gamma[start + 1]).
+  kGammaCode[i] = the same as one word per bucket, i = 0 .. 5121: bucket
+                  i - 1 for i = 1 .. 5120, i = 0 for v < 2^-20 and i = 5121
+                  for v >= 1; the word is start | (t << 8) with t the low 15
+                  bits of the one threshold inside the bucket, or 0x8000 (no
+                  15-bit value reaches it) when the bucket holds none, so the
+                  code of v is start + ((bits(v) & 0x7FFF) >= t).
 The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
 """
@@ -41,6 +47,13 @@ def main():
         assert len(inside) <= 1 and (k == 255 or k + 2 > 255 or gamma[k + 2] >= hi), b
         start.append(k)
     wr = [f32_bits(1800.0 * 2.0 ** (-r / 16.0)) for r in range(16)]
+    code = [0 | (0x8000 << 8)]
+    for b, k in enumerate(start):
+        lo = (107 << 23) + (b << 15)
+        t = gamma[k + 1] if k < 255 else None
+        inside = t is not None and (t >> 15) == (lo >> 15)
+        code.append(k | ((t & 0x7FFF) if inside else 0x8000) << 8)
+    code.append(255 | (0x8000 << 8))
 
     def arr(ctype, name, vals, fmt, per_line):
         lines = []
@@ -55,6 +68,7 @@ def main():
     out.append(arr("uint32_t", "kKrBits", kr, lambda v: f"0x{v:08x}u", 8))
     out.append(arr("uint32_t", "kWrBits", wr, lambda v: f"0x{v:08x}u", 8))
     out.append(arr("uint8_t", "kGammaStart", start, str, 24))
+    out.append(arr("uint32_t", "kGammaCode", code, lambda v: f"0x{v:08x}u", 8))
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tables.inc")
     with open(path, "w") as fh:
         fh.write("\n".join(out))
