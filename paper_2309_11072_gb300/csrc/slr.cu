@@ -1272,30 +1272,85 @@ __device__ __forceinline__ void chan_accum(const uint32_t (&x)[4], uint32_t yl, 
     a.sxx[c] = r;
 }
 
-constexpr uint32_t kFitExtra = sizeof(SmemBins) + sizeof(uint32_t) * kTileWarps * 32 * kQueueStride;
-constexpr size_t kTileFitSmem = 128 + TileSmem<TmaMode::kFit>::kHead + kFitExtra;
+// Two per-warp queues: flushed runs (their sums) and segments that need
+// per-pixel work (their pixels).  Each is drained by its own code path, one
+// entry per lane, so draining runs -- the common case -- never pays for the
+// per-pixel segment path.  A row queues at most one segment per lane, so the
+// segment queue holds 32 (a row's segments are written piece by piece while
+// the row is processed); runs, complete when queued, go in chunks that fit
+// the 16-entry run queue, draining it in between.
+constexpr int kRunQ = 16;
+constexpr int kRunStride = 15;   // 13 sums, the region, a pad word (odd stride: distinct banks)
+constexpr int kSegQ = 32;        // segment entries of kQueueStride words
+struct FitQueues {
+    uint32_t* R;   // run entries
+    uint32_t* Q;   // segment entries
+    int nr, nq;    // entries queued (warp-uniform)
+};
 
-// Queues the even run (all - odd, region all.E) of every lane with `want` set.
-__device__ __forceinline__ void enqueue_even(FitWarp& st, bool want, const RunAcc& all, const RunAcc& odd,
-                                             SmemBins& bins, int lane) {
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (!m) return;
-    if (st.queued + __popc(m) > 32) fit_drain<true>(st, bins, lane);
-    if (want) {
-        uint32_t* q = st.Q + (st.queued + __popc(m & ((1u << lane) - 1u))) * kQueueStride;
-        q[0] = all.n - odd.n;
+__device__ __forceinline__ void drain_runs(FitQueues& fq, SmemBins& bins, int lane) {
+    if (lane < fq.nr) {
+        const uint32_t* q = fq.R + lane * kRunStride;
+        uint32_t acc[kNsum];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            q[1 + 4 * c] = all.sx[c] - odd.sx[c];
-            q[2 + 4 * c] = all.sy[c] - odd.sy[c];
-            q[3 + 4 * c] = all.sxy[c] - odd.sxy[c];
-            q[4 + 4 * c] = all.sxx[c] - odd.sxx[c];
-        }
-        q[20] = 256u + (uint32_t)all.E;
+        for (int j = 0; j < kNsum; ++j) acc[j] = q[j];
+        bins_add32(smem_addr(&bins), (int)q[kNsum], acc);
     }
     __syncwarp();
-    st.queued += __popc(m);
+    fq.nr = 0;
 }
+
+__device__ __forceinline__ void drain_segs(FitQueues& fq, SmemBins& bins, int lane) {
+    if (lane < fq.nq) drain_entry<true>(fq.Q + lane * kQueueStride, smem_addr(&bins));
+    __syncwarp();
+    fq.nq = 0;
+}
+
+// Queues the run of every lane with `want` set: the even run (all - odd,
+// region all.E) or the odd run (odd, region odd.E), in chunks that fit.
+template <bool kEven>
+__device__ __forceinline__ void push_run(FitQueues& fq, bool want, const RunAcc& all, const RunAcc& odd,
+                                         SmemBins& bins, int lane) {
+    unsigned m = __ballot_sync(0xffffffffu, want);
+    while (m) {
+        if (fq.nr == kRunQ) drain_runs(fq, bins, lane);
+        // the first kRunQ - nr lanes of m go now
+        unsigned take = m;
+        while (__popc(take) > kRunQ - fq.nr) take &= ~(1u << (31 - __clz(take)));
+        if (take & (1u << lane)) {
+            uint32_t* q = fq.R + (fq.nr + __popc(take & ((1u << lane) - 1u))) * kRunStride;
+            if constexpr (kEven) {
+                q[0] = all.n - odd.n;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    q[1 + 4 * c] = all.sx[c] - odd.sx[c];
+                    q[2 + 4 * c] = all.sy[c] - odd.sy[c];
+                    q[3 + 4 * c] = all.sxy[c] - odd.sxy[c];
+                    q[4 + 4 * c] = all.sxx[c] - odd.sxx[c];
+                }
+                q[kNsum] = (uint32_t)all.E;
+            } else {
+                q[0] = odd.n;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    q[1 + 4 * c] = odd.sx[c];
+                    q[2 + 4 * c] = odd.sy[c];
+                    q[3 + 4 * c] = odd.sxy[c];
+                    q[4 + 4 * c] = odd.sxx[c];
+                }
+                q[kNsum] = (uint32_t)odd.E;
+            }
+        }
+        __syncwarp();
+        fq.nr += __popc(take);
+        m &= ~take;
+    }
+}
+
+constexpr uint32_t kFitQueueBytes = sizeof(uint32_t) * kTileWarps * (kRunQ * kRunStride + kSegQ * kQueueStride);
+constexpr uint32_t kFitExtra = sizeof(SmemBins) + kFitQueueBytes;
+constexpr size_t kTileFitSmem = 128 + TileSmem<TmaMode::kFit>::kHead + kFitExtra;
+static_assert(2 * (kTileFitSmem + 1024) <= 228 * 1024, "two fit CTAs per SM");
 
 // Per lane: `all` holds the sums of both runs, `odd` those of the odd run;
 // the even run is all - odd.  A run that changes region leaves through the
@@ -1321,9 +1376,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_const
     const TileConsumer<TmaMode::kFit> C{L, A.max_spins};
     const int w = A.w;
     const bool gf = A.gf != 0;
-    FitWarp st;
-    st.Q = queue + warp * 32 * kQueueStride;
-    st.queued = 0;
+    FitQueues fq;
+    fq.R = queue + warp * (kRunQ * kRunStride + kSegQ * kQueueStride);
+    fq.Q = fq.R + kRunQ * kRunStride;
+    fq.nr = fq.nq = 0;
     RunAcc all, odd;
     TileRange T = tile_range(A.total_rows, A.h);
     uint32_t si = 0, ai = 0;
@@ -1353,8 +1409,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_const
             const bool chg_o = po_n != 0u && (int)Eo != odd.E;
             const bool chg_e = take && po_n != 8u && (int)Ee != all.E;
             // a run whose region changes leaves first (the even run is all - odd)
-            enqueue_even(st, chg_e && all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
-            enqueue_run<true>(st, chg_o && odd.E >= 0 && odd.n != 0u, odd, bins, lane);
+            push_run<true>(fq, chg_e && all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
+            push_run<false>(fq, chg_o && odd.E >= 0 && odd.n != 0u, all, odd, bins, lane);
             if (chg_e) {
                 const int keep = odd.E;
                 all = odd;        // the even part leaves: all - odd = 0
@@ -1370,8 +1426,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_const
             const unsigned want = __ballot_sync(0xffffffffu, slow);
             uint32_t* qe = nullptr;
             if (want) {
-                if (st.queued + __popc(want) > 32) fit_drain<true>(st, bins, lane);
-                qe = st.Q + (st.queued + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+                if (fq.nq + __popc(want) > kSegQ) drain_segs(fq, bins, lane);
+                qe = fq.Q + (fq.nq + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
             }
             uint32_t k16[4];
             mask16(olo, ohi, k16);
@@ -1403,7 +1459,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_const
                     qe[20] = 8u;
                 }
                 __syncwarp();
-                st.queued += __popc(want);
+                fq.nq += __popc(want);
             }
             tile_release(L.sempty((int)((si + j) % kTileS)), lane);
             tile_release(L.aempty((int)((ai + j) % kTileA)), lane);
@@ -1424,7 +1480,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_const
         si += T.rows + 2;
         ai += T.rows;
     }
-    if (ok) fit_drain<true>(st, bins, lane);
+    if (ok) {
+        drain_runs(fq, bins, lane);
+        drain_segs(fq, bins, lane);
+    }
     consumers_sync();
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kTileWarps * 32) {
         const unsigned long long v = ((unsigned long long)bins.hi[i] << 12) + bins.lo[i];
