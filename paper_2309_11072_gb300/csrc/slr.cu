@@ -1000,7 +1000,7 @@ constexpr int kTileCols = kTileWarps * kStripCols;         // 2048
 constexpr int kTileSW = kTileCols + 32;                    // S row with halos, per plane
 constexpr int kTaskRows = 256;
 constexpr int kTileS = 5;                                  // S ring slots
-constexpr int kTileA = 3;                                  // M / E (or R / E) ring slots
+constexpr int kTileA = 3;                                  // M / E ring slots (fit, residual)
 constexpr uint32_t kTileSBytes = 3u * kTileSW;             // 6240
 constexpr uint32_t kTileSStride = 6272;                    // slot stride, multiple of 128
 static_assert(kTileSStride >= kTileSBytes && kTileSStride % 128 == 0, "S slot");
@@ -1019,6 +1019,10 @@ struct TileAux {
     static constexpr uint32_t kBytes = kE + kTileCols;
     static constexpr uint32_t kStride = kBytes;                    // multiple of 128
     static_assert(kStride % 128 == 0, "aux slot");
+    static constexpr int kSlots = kTileA;   // ring slots
+    // CTAs per SM the kernel is built for (the residual kernel's registers
+    // and shared memory allow three; the launch uses three on large images)
+    static constexpr int kCtas = MODE == TmaMode::kResidual ? 3 : 2;
 };
 
 struct TileMaps {
@@ -1086,13 +1090,15 @@ struct TileSmem {
     __device__ __forceinline__ uint32_t sfull(int k) const { return bars + 8u * k; }
     __device__ __forceinline__ uint32_t sempty(int k) const { return bars + 8u * (kTileS + k); }
     __device__ __forceinline__ uint32_t afull(int k) const { return bars + 8u * (2 * kTileS + k); }
-    __device__ __forceinline__ uint32_t aempty(int k) const { return bars + 8u * (2 * kTileS + kTileA + k); }
+    __device__ __forceinline__ uint32_t aempty(int k) const {
+        return bars + 8u * (2 * kTileS + TileAux<MODE>::kSlots + k);
+    }
     __device__ __forceinline__ uint32_t sslot(uint32_t i) const { return s_ring + (i % kTileS) * kTileSStride; }
     __device__ __forceinline__ uint32_t aslot(uint32_t i) const {
-        return a_ring + (i % kTileA) * TileAux<MODE>::kStride;
+        return a_ring + (i % TileAux<MODE>::kSlots) * TileAux<MODE>::kStride;
     }
-    static constexpr uint32_t kRings = kTileS * kTileSStride + kTileA * TileAux<MODE>::kStride;
-    static constexpr uint32_t kHead = kRings + 8u * 2 * (kTileS + kTileA);   // multiple of 16
+    static constexpr uint32_t kRings = kTileS * kTileSStride + TileAux<MODE>::kSlots * TileAux<MODE>::kStride;
+    static constexpr uint32_t kHead = kRings + 8u * 2 * (kTileS + TileAux<MODE>::kSlots);   // multiple of 16
 };
 
 template <TmaMode MODE>
@@ -1113,7 +1119,7 @@ __device__ __forceinline__ void tile_init_barriers(const TileSmem<MODE>& L) {
             mbar_init(L.sfull(k), 1);
             mbar_init(L.sempty(k), kTileWarps);
         }
-        for (int k = 0; k < kTileA; ++k) {
+        for (int k = 0; k < TileAux<MODE>::kSlots; ++k) {
             mbar_init(L.afull(k), 1);
             mbar_init(L.aempty(k), kTileWarps);
         }
@@ -1144,9 +1150,9 @@ __device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const CUtenso
                 ++si;
             }
             if (k >= 2) {   // the other planes of row y0 + k - 2
-                const int slot = (int)(ai % kTileA);
-                if (ai >= (uint32_t)kTileA)
-                    ok = mbar_wait(L.aempty(slot), ((ai / kTileA) - 1u) & 1u, &g_slrme_status, A.max_spins);
+                constexpr uint32_t KA = TileAux<MODE>::kSlots;
+                const int slot = (int)(ai % KA);
+                if (ai >= KA) ok = mbar_wait(L.aempty(slot), ((ai / KA) - 1u) & 1u, &g_slrme_status, A.max_spins);
                 if (!ok) break;
                 const int y = P.y0 + k - 2;
                 const uint32_t dst = L.aslot(ai);
@@ -1166,8 +1172,9 @@ __device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const CUtenso
     const int spins = ok ? A.max_spins : (1 << 10);
     for (uint32_t k = si > (uint32_t)kTileS ? si - kTileS : 0; k < si; ++k)
         mbar_wait(L.sfull((int)(k % kTileS)), (k / kTileS) & 1u, &g_slrme_status, spins);
-    for (uint32_t k = ai > (uint32_t)kTileA ? ai - kTileA : 0; k < ai; ++k)
-        mbar_wait(L.afull((int)(k % kTileA)), (k / kTileA) & 1u, &g_slrme_status, spins);
+    constexpr uint32_t KA = TileAux<MODE>::kSlots;
+    for (uint32_t k = ai > KA ? ai - KA : 0; k < ai; ++k)
+        mbar_wait(L.afull((int)(k % KA)), (k / KA) & 1u, &g_slrme_status, spins);
 }
 
 // A consumer warp is done with a slot (all lanes call after their last read).
@@ -1185,7 +1192,8 @@ struct TileConsumer {
         return mbar_wait(L.sfull((int)(i % kTileS)), (i / kTileS) & 1u, &g_slrme_status, max_spins);
     }
     __device__ __forceinline__ bool wait_a(uint32_t i) const {
-        return mbar_wait(L.afull((int)(i % kTileA)), (i / kTileA) & 1u, &g_slrme_status, max_spins);
+        constexpr uint32_t KA = TileAux<MODE>::kSlots;
+        return mbar_wait(L.afull((int)(i % KA)), (i / KA) & 1u, &g_slrme_status, max_spins);
     }
     // all lanes call after their last read of the items
     __device__ __forceinline__ void release_s(uint32_t i, int lane) const {
@@ -1194,7 +1202,7 @@ struct TileConsumer {
     }
     __device__ __forceinline__ void release_a(uint32_t i, int lane) const {
         __syncwarp();
-        if (lane == 0) mbar_arrive(L.aempty((int)(i % kTileA)));
+        if (lane == 0) mbar_arrive(L.aempty((int)(i % TileAux<MODE>::kSlots)));
     }
 };
 
@@ -1355,7 +1363,7 @@ static_assert(2 * (kTileFitSmem + 1024) <= 228 * 1024, "two fit CTAs per SM");
 // Per lane: `all` holds the sums of both runs, `odd` those of the odd run;
 // the even run is all - odd.  A run that changes region leaves through the
 // warp's queue; a task's runs are flushed every kRunRows rows and at its end.
-__global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_constant__ CUtensorMap tm_s,
+__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile(const __grid_constant__ CUtensorMap tm_s,
                                                                const __grid_constant__ CUtensorMap tm_a,
                                                                const __grid_constant__ CUtensorMap tm_e,
                                                                const TileArgs A) {
@@ -1462,7 +1470,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fit_tile(const __grid_const
                 fq.nq += __popc(want);
             }
             tile_release(L.sempty((int)((si + j) % kTileS)), lane);
-            tile_release(L.aempty((int)((ai + j) % kTileA)), lane);
+            tile_release(L.aempty((int)((ai + j) % TileAux<TmaMode::kFit>::kSlots)), lane);
             if ((j + 1) % kRunRows == 0 || j + 1 == T.rows) {
                 // bounded runs: flush both (the even run is all - odd)
                 RunAcc e = all;
@@ -1498,11 +1506,13 @@ constexpr size_t tile_rows_smem() {
     return 128 + TileSmem<MODE>::kHead + sizeof(float2) * 3 * kNbin +
            (MODE == TmaMode::kResidual ? sizeof(uint32_t) * 3 * kNres : 0);
 }
+static_assert(3 * (tile_rows_smem<TmaMode::kResidual>() + 1024) <= 228 * 1024, "three residual CTAs per SM");
+static_assert(2 * (tile_rows_smem<TmaMode::kDecode>() + 1024) <= 228 * 1024, "two decode CTAs per SM");
 
 // k_rows_tile<kResidual>: R = M - M* and histograms; k_rows_tile<kDecode>:
 // M = R + M*, repacked with E.
 template <TmaMode MODE>
-__global__ void __launch_bounds__(kTileThreads, 2) k_rows_tile(const __grid_constant__ CUtensorMap tm_s,
+__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile(const __grid_constant__ CUtensorMap tm_s,
                                                                 const __grid_constant__ CUtensorMap tm_a,
                                                                 const __grid_constant__ CUtensorMap tm_e,
                                                                 const TileArgs A) {
@@ -1665,11 +1675,14 @@ bool tile_maps(TileMaps& M, const uint8_t* s3, const void* aux, const uint8_t* e
            plane_map(&M.e, e, 1, h, w, 1, kTileCols / 16);
 }
 
-// Grid of a tile kernel: two CTAs per SM at most, at least four rows per
-// CTA, and for the fit at least total_rows / rows_max CTAs.
-int64_t tile_grid(int64_t total_rows, int64_t rows_max) {
+// Grid of a tile kernel: at least four rows per CTA; at most two CTAs per SM,
+// or `per_sm` when every CTA still gets 16 rows or more (a short range
+// spends proportionally more of its time filling the rings); for the fit at
+// least total_rows / rows_max CTAs.
+int64_t tile_grid(int64_t total_rows, int64_t rows_max, int per_sm) {
+    if (total_rows < (int64_t)16 * per_sm * geometry().sms) per_sm = 2;
     int64_t g = (total_rows + 3) / 4;
-    const int64_t cap = (int64_t)geometry().sms * 2;
+    const int64_t cap = (int64_t)geometry().sms * per_sm;
     if (g > cap) g = cap;
     if (rows_max > 0 && g < (total_rows + rows_max - 1) / rows_max) g = (total_rows + rows_max - 1) / rows_max;
     return g < 1 ? 1 : g;
@@ -1698,7 +1711,8 @@ int launch_rows_tile(const uint8_t* s3, const void* aux, const uint8_t* e, int h
     if (!tile_maps<MODE>(M, s3, aux, e, h, w)) return SLRME_ECUDA;
     const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
     TileArgs A{h, w, gf_on, total_rows, kMaxSpins, P, r3_out, hist, out, nullptr};
-    k_rows_tile<MODE><<<(unsigned)tile_grid(total_rows, 0), kTileThreads, smem, s>>>(M.s, M.a, M.e, A);
+    k_rows_tile<MODE><<<(unsigned)tile_grid(total_rows, 0, TileAux<MODE>::kCtas), kTileThreads, smem, s>>>(M.s, M.a,
+                                                                                                    M.e, A);
     return cuda_status(MODE == TmaMode::kResidual ? "residual_encode launch" : "residual_decode launch");
 }
 
@@ -1713,7 +1727,8 @@ int launch_fit_tile(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int 
     // a CTA adds at most kMaxBlockPixels pixels to its bins
     const int64_t rows_max = kMaxBlockPixels / kTileCols;
     TileArgs A{h, w, gf_on, total_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr, bins};
-    k_fit_tile<<<(unsigned)tile_grid(total_rows, rows_max), kTileThreads, kTileFitSmem, s>>>(M.s, M.a, M.e, A);
+    k_fit_tile<<<(unsigned)tile_grid(total_rows, rows_max, TileAux<TmaMode::kFit>::kCtas), kTileThreads, kTileFitSmem,
+                 s>>>(M.s, M.a, M.e, A);
     return cuda_status("slr_fit launch");
 }
 

@@ -64,59 +64,49 @@ __device__ __forceinline__ void block_reduce_add(int64_t s, int64_t c, int64_t* 
     __syncthreads();   // `red` may be reused by the next call
 }
 
-// Splits four words (one 16-byte load) into the four planes at vector index j.
-__device__ __forceinline__ void split4(const uint4 v, int64_t j, uint32_t* __restrict__ mR, uint32_t* __restrict__ mG,
-                                       uint32_t* __restrict__ mB, uint32_t* __restrict__ eP, const int32_t* lut,
-                                       int64_t& s, int64_t& c) {
-    const uint32_t lo01 = __byte_perm(v.x, v.y, 0x5140), hi01 = __byte_perm(v.x, v.y, 0x7362);
-    const uint32_t lo23 = __byte_perm(v.z, v.w, 0x5140), hi23 = __byte_perm(v.z, v.w, 0x7362);
-    mR[j] = __byte_perm(lo01, lo23, 0x5410);
-    mG[j] = __byte_perm(lo01, lo23, 0x7632);
-    mB[j] = __byte_perm(hi01, hi23, 0x5410);
-    eP[j] = __byte_perm(hi01, hi23, 0x7632);
-    const int32_t part = log_lum(v.x, lut) + log_lum(v.y, lut);
-    const int32_t part2 = log_lum(v.z, lut) + log_lum(v.w, lut);
-    s += (int64_t)part + part2;
-    c += (v.x >> 24 != 0) + (v.y >> 24 != 0) + (v.z >> 24 != 0) + (v.w >> 24 != 0);
-}
-
 // Vector path: n % 4 == 0, rgbe 16-byte aligned, planes 4-byte aligned.
-// Software-pipelined: each thread keeps its next U loads in flight while it
-// splits the current ones, and the first loads are issued before the log
-// table is staged in shared memory.
-__global__ void __launch_bounds__(kThreads, 4) k_split_vec(const uint4* __restrict__ rgbe4, int64_t nv,
+__global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict__ rgbe4, int64_t nv,
                                                         uint32_t* __restrict__ mR, uint32_t* __restrict__ mG,
                                                         uint32_t* __restrict__ mB, uint32_t* __restrict__ eP,
                                                         int64_t* __restrict__ stats) {
     __shared__ int32_t lut[2048];
-    constexpr int U = 4;   // independent 16-byte loads in flight per thread
-    const int64_t stride = (int64_t)gridDim.x * kThreads;
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    uint4 v[U];
-    bool more = i + (U - 1) * stride < nv;
-    if (more) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = ld_stream(rgbe4 + i + u * stride);
-    }
-    for (int k = threadIdx.x; k < 2048; k += kThreads) lut[k] = kLog2Lut[k];
+    for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = kLog2Lut[i];
     __syncthreads();
 
     int64_t s = 0, c = 0;
-    while (more) {
-        uint4 cur[U];
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    constexpr int U = 4;   // independent 16-byte loads in flight per thread
+    for (; i + (U - 1) * stride < nv; i += U * stride) {
+        uint4 v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) cur[u] = v[u];
-        const int64_t j0 = i;
-        i += U * stride;
-        more = i + (U - 1) * stride < nv;
-        if (more) {
+        for (int u = 0; u < U; ++u) v[u] = ld_stream(rgbe4 + i + u * stride);
 #pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = ld_stream(rgbe4 + i + u * stride);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t lo01 = __byte_perm(v[u].x, v[u].y, 0x5140), hi01 = __byte_perm(v[u].x, v[u].y, 0x7362);
+            const uint32_t lo23 = __byte_perm(v[u].z, v[u].w, 0x5140), hi23 = __byte_perm(v[u].z, v[u].w, 0x7362);
+            const int64_t j = i + u * stride;
+            mR[j] = __byte_perm(lo01, lo23, 0x5410);
+            mG[j] = __byte_perm(lo01, lo23, 0x7632);
+            mB[j] = __byte_perm(hi01, hi23, 0x5410);
+            eP[j] = __byte_perm(hi01, hi23, 0x7632);
+            int32_t part = log_lum(v[u].x, lut) + log_lum(v[u].y, lut);
+            int32_t part2 = log_lum(v[u].z, lut) + log_lum(v[u].w, lut);
+            s += (int64_t)part + part2;
+            c += (v[u].x >> 24 != 0) + (v[u].y >> 24 != 0) + (v[u].z >> 24 != 0) + (v[u].w >> 24 != 0);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) split4(cur[u], j0 + u * stride, mR, mG, mB, eP, lut, s, c);
     }
-    for (; i < nv; i += stride) split4(ld_stream(rgbe4 + i), i, mR, mG, mB, eP, lut, s, c);
+    for (; i < nv; i += stride) {
+        const uint4 v = ld_stream(rgbe4 + i);
+        const uint32_t lo01 = __byte_perm(v.x, v.y, 0x5140), hi01 = __byte_perm(v.x, v.y, 0x7362);
+        const uint32_t lo23 = __byte_perm(v.z, v.w, 0x5140), hi23 = __byte_perm(v.z, v.w, 0x7362);
+        mR[i] = __byte_perm(lo01, lo23, 0x5410);
+        mG[i] = __byte_perm(lo01, lo23, 0x7632);
+        mB[i] = __byte_perm(hi01, hi23, 0x5410);
+        eP[i] = __byte_perm(hi01, hi23, 0x7632);
+        s += (int64_t)log_lum(v.x, lut) + log_lum(v.y, lut) + log_lum(v.z, lut) + log_lum(v.w, lut);
+        c += (v.x >> 24 != 0) + (v.y >> 24 != 0) + (v.z >> 24 != 0) + (v.w >> 24 != 0);
+    }
     block_reduce_add(s, c, stats);
 }
 
