@@ -76,17 +76,23 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8], int r) {
 
 // 8-bit display value: #{k in 1..255 : v >= gamma[k]} for the increasing
 // threshold table (v >= 0).  The float bits of v pick a bucket (exponent and
-// top 8 mantissa bits over [2^-20, 1), plus one bucket below and one above);
+// top 7 mantissa bits over [2^-20, 1), plus one bucket below and one above);
 // a bucket holds at most one threshold, and its word is the count below the
-// bucket plus, from bit 8, the low 15 bits of that threshold (0x8000 when
+// bucket plus, from bit 8, the low 16 bits of that threshold (0x10000 when
 // there is none), so the count is one lookup and one integer comparison
 // (positive floats order like their bits).  No branch.
 __device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {
     const int bits = __float_as_int(v);
-    const int b = min(max((bits - 0x35800000) >> 15, -1), 5120) + 1;
+    const int b = min(max((bits - 0x35800000) >> 16, -1), 2560) + 1;
     const uint32_t e = code[b];
-    return (int)(e & 255u) + ((uint32_t)(bits & 0x7FFF) >= (e >> 8) ? 1 : 0);
+    return (int)(e & 255u) + ((uint32_t)(bits & 0xFFFF) >= (e >> 8) ? 1 : 0);
 }
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // float(v) for 0 <= v < 2^23, exactly (the 2^23 bias).
 __device__ __forceinline__ float small_int_to_float(int v) {
@@ -113,6 +119,14 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ plane, int h, 
     }
 }
 
+__device__ __forceinline__ void unpack8(const uint2 v, uint8_t (&out)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        out[i] = (uint8_t)byte_of(v.x, i);
+        out[4 + i] = (uint8_t)byte_of(v.y, i);
+    }
+}
+
 __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
                                        const uint32_t lo, const uint32_t hi) {
     if (y >= h) return;
@@ -127,7 +141,7 @@ __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w
 
 // The bucket words of the display code into shared memory; ends with a
 // block barrier.
-constexpr int kGammaWords = 5122;
+constexpr int kGammaWords = 2562;
 __device__ __forceinline__ void load_gamma(uint32_t* code) {
     for (int i = threadIdx.x; i < kGammaWords; i += blockDim.x) code[i] = kGammaCode[i];
     __syncthreads();
@@ -158,7 +172,7 @@ __device__ __forceinline__ void base_key(const int64_t* __restrict__ stats, cons
 __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h, int w,
                                           bool fast, int y0, int xb, int lane, const BaseKey& K,
                                           const uint32_t* gcode, int* T, uint8_t* __restrict__ s3,
-                                          uint8_t* __restrict__ sdr3) {
+                                          uint8_t* __restrict__ sdr3, const uint2* pre) {
     const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
     const int64_t n = (int64_t)h * w;
     const int J = K.J;
@@ -168,11 +182,19 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
     // ---------------- phase 1: tone map and forward DCT along x
     {
         uint8_t mr[8], mg[8], mb[8], ee[8];
-        // rows past the bottom and columns past the right edge replicate the last row/column
-        load8(m3, h, w, y, x0, fast, mr);
-        load8(m3 + n, h, w, y, x0, fast, mg);
-        load8(m3 + 2 * n, h, w, y, x0, fast, mb);
-        load8(e, h, w, y, x0, fast, ee);
+        if (pre) {
+            // the band's bytes, copied to shared memory while the previous band was processed
+            unpack8(pre[0], mr);
+            unpack8(pre[32], mg);
+            unpack8(pre[64], mb);
+            unpack8(pre[96], ee);
+        } else {
+            // rows past the bottom and columns past the right edge replicate the last row/column
+            load8(m3, h, w, y, x0, fast, mr);
+            load8(m3 + n, h, w, y, x0, fast, mg);
+            load8(m3 + 2 * n, h, w, y, x0, fast, mb);
+            load8(e, h, w, y, x0, fast, ee);
+        }
         int sdr[3][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -253,21 +275,60 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
     __syncwarp();
 }
 
+// Copies this lane's bytes of band t (M_R, M_G, M_B, E: 8 each) into its
+// prefetch slot and commits the copies as one group (an empty group when
+// the band is not whole -- the right edge of a ragged image -- or the image
+// has no 8-byte rows); false when nothing was copied.
+__device__ __forceinline__ bool prefetch_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h,
+                                              int w, bool fast, int cols, int64_t t, int lane, uint2* slot) {
+    bool ok = false;
+    if (fast) {
+        const int y0 = (int)(t / cols) * 8, xb = (int)(t % cols) * 32;
+        if (xb + 32 <= w) {
+            const int y = min(y0 + (lane & 7), h - 1), x0 = xb + 8 * (lane >> 3);
+            const int64_t n = (int64_t)h * w, off = (int64_t)y * w + x0;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot);
+            cp_async8(dst, m3 + off);
+            cp_async8(dst + 256, m3 + n + off);
+            cp_async8(dst + 512, m3 + 2 * n + off);
+            cp_async8(dst + 768, e + off);
+            ok = true;
+        }
+    }
+    cp_async_commit();
+    return ok;
+}
+
 __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
                                                       int h, int w, const int64_t* __restrict__ lum_stats,
                                                       uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3,
                                                       int fast_io, const QuantTable QT) {
     __shared__ uint32_t gcode[kGammaWords];
     __shared__ __align__(16) int tile[kWarps][kTileWords];
+    __shared__ __align__(16) uint2 pre[kWarps][2][4][32];   // [warp][slot][plane][lane]
     load_gamma(gcode);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BaseKey K;
     base_key(lum_stats, QT, lane & 7, K);
     const int cols = (w + 31) >> 5;
     const int64_t tasks = (int64_t)((h + 7) >> 3) * cols;
-    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps)
-        base_band(m3, e, h, w, fast_io != 0, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
-                  tile[warp], s3, sdr3);
+    const int64_t step = (int64_t)gridDim.x * kWarps;
+    const bool fast = fast_io != 0;
+    int64_t t = (int64_t)blockIdx.x * kWarps + warp;
+    int slot = 0;
+    bool have = t < tasks && prefetch_band(m3, e, h, w, fast, cols, t, lane, &pre[warp][0][0][lane]);
+    while (t < tasks) {
+        // the next band's copies go out before this band is processed
+        const int64_t tn = t + step;
+        const bool next = tn < tasks && prefetch_band(m3, e, h, w, fast, cols, tn, lane, &pre[warp][slot ^ 1][0][lane]);
+        if (!next) cp_async_commit();   // keep one group per band, so "all but the newest" is this band's
+        cp_async_wait_prev();
+        base_band(m3, e, h, w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode, tile[warp], s3,
+                  sdr3, have ? &pre[warp][slot][0][lane] : nullptr);
+        t = tn;
+        slot ^= 1;
+        have = next;
+    }
 }
 
 // Batch: CTA tasks of 8 band tasks of one image, contiguous ranges per CTA.
@@ -299,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
                           ((uintptr_t)s3 % 8 == 0);
         if ((int64_t)im.h * im.w > 0 && t < bands)
             base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
-                      tile[warp], s3, nullptr);
+                      tile[warp], s3, nullptr, nullptr);
     }
 }
 

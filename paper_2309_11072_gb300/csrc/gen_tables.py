@@ -13,12 +13,15 @@ Tables (all built in float64 and rounded once):
                   biased exponent e in 107..126 and top 8 mantissa bits m
                   (v in [2^-20, 1)); no bucket holds more than one threshold,
                   so the display code of v is start + (v >= gamma[start + 1]).
-  kGammaCode[i] = the same as one word per bucket, i = 0 .. 5121: bucket
-                  i - 1 for i = 1 .. 5120, i = 0 for v < 2^-20 and i = 5121
-                  for v >= 1; the word is start | (t << 8) with t the low 15
-                  bits of the one threshold inside the bucket, or 0x8000 (no
-                  15-bit value reaches it) when the bucket holds none, so the
-                  code of v is start + ((bits(v) & 0x7FFF) >= t).
+  kGammaCode[i] = the display code as one word per coarser bucket, i = 0 ..
+                  2561: bucket i - 1 (biased exponent e in 107..126 and top 7
+                  mantissa bits) for i = 1 .. 2560, i = 0 for v < 2^-20 and
+                  i = 2561 for v >= 1; no such bucket holds more than one
+                  threshold either, and the word is start | (t << 8) with
+                  start the count of thresholds below the bucket and t the low
+                  16 bits of the one threshold inside it, or 0x10000 (no
+                  16-bit value reaches it) when there is none, so the code of
+                  v is start + ((bits(v) & 0xFFFF) >= t).
 The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
 """
@@ -47,14 +50,15 @@ def main():
         assert len(inside) <= 1 and (k == 255 or k + 2 > 255 or gamma[k + 2] >= hi), b
         start.append(k)
     wr = [f32_bits(1800.0 * 2.0 ** (-r / 16.0)) for r in range(16)]
-    code = [0 | (0x8000 << 8)]
-    for b, k in enumerate(start):
-        lo = (107 << 23) + (b << 15)
-        t = gamma[k + 1] if k < 255 else None
-        inside = t is not None and (t >> 15) == (lo >> 15)
-        code.append(k | ((t & 0x7FFF) if inside else 0x8000) << 8)
-    code.append(255 | (0x8000 << 8))
-
+    code = [0 | (0x10000 << 8)]
+    for b in range(20 * 128):
+        lo = (107 << 23) + (b << 16)
+        hi = lo + (1 << 16)
+        k = sum(1 for t in gamma[1:] if t < lo)
+        inside = [t for t in gamma[1:] if lo <= t < hi]
+        assert len(inside) <= 1, b
+        code.append(k | ((inside[0] & 0xFFFF) if inside else 0x10000) << 8)
+    code.append(255 | (0x10000 << 8))
     def arr(ctype, name, vals, fmt, per_line):
         lines = []
         for i in range(0, len(vals), per_line):
