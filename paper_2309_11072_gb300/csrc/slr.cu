@@ -1308,8 +1308,40 @@ __device__ __forceinline__ void drain_runs(FitQueues& fq, SmemBins& bins, int la
     fq.nr = 0;
 }
 
+// Adds the eight pixels of a queued segment to their bins one by one, without
+// branches: per pixel 19 reductions (the count, x and y are below 2^12 and
+// have no high part under the split rule; x y and x x take two words).
+__device__ __forceinline__ void drain_segment_pixels(const uint32_t* q, uint32_t B) {
+    const uint32_t elo = q[0], ehi = q[1];
+    uint32_t mlo[3] = {q[2], q[3], q[4]}, mhi[3] = {q[5], q[6], q[7]};
+    uint32_t X[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) X[c][k] = q[8 + 4 * c + k];
+    constexpr uint32_t kHi = 4u * kNbin * kNsum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t lo = B + 4u * kNsum * byte_of(i < 4 ? elo : ehi, i & 3);
+        red_add(lo, 1u);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t x = (X[c][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+            const uint32_t y = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
+            const uint32_t xy = x * y, xx = x * x;
+            const uint32_t a = lo + 4u * (1 + 4 * c);
+            red_add(a, x);
+            red_add(a + 4u, y);
+            red_add(a + 8u, xy & 0xFFFu);
+            red_add(a + 8u + kHi, xy >> 12);
+            red_add(a + 12u, xx & 0xFFFu);
+            red_add(a + 12u + kHi, xx >> 12);
+        }
+    }
+}
+
 __device__ __forceinline__ void drain_segs(FitQueues& fq, SmemBins& bins, int lane) {
-    if (lane < fq.nq) drain_entry<true>(fq.Q + lane * kQueueStride, smem_addr(&bins));
+    if (lane < fq.nq) drain_segment_pixels(fq.Q + lane * kQueueStride, smem_addr(&bins));
     __syncwarp();
     fq.nq = 0;
 }
