@@ -44,7 +44,15 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # DRAM bytes per pixel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
-TRAFFIC = {"slr_fit": {"bytes_per_px": 22090240 / (2048 * 1536), "sha": "9febd5c5a761ec31"}}
+TRAFFIC = {"slr_fit": {"bytes_per_px": 22090240 / (2048 * 1536), "sha": "9febd5c5a761ec31"},
+           "sdri_base_roundtrip": {"bytes_per_px": 12650496 / (2048 * 1536), "sha": "351ed30ae469b5ac"}}
+# The base round trip is bound by instruction issue, not by memory: its
+# roofline counts the arithmetic operations its definition needs per pixel
+# (tone mapping 24; four 8-point integer DCT passes per channel, 36 butterfly
+# operations and 8 rounding shifts per 8 values and pass, 66; quantiser 15;
+# clamp and pack 3) against the issue peak of the GPU's SMs x 128 lanes x the
+# maximum SM clock.
+ALU_OPS_PER_PX = {"sdri_base_roundtrip": 108}
 KERNEL_SOURCE = {"rgbe_split": "split.cu", "sdri_base_roundtrip": "base.cu", "slr_fit": "slr.cu",
                  "residual_encode": "slr.cu", "residual_decode": "slr.cu"}
 
@@ -58,8 +66,8 @@ def load_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
-    return {"hbm_gbs": 6800.0, "src": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
 
 
 class ClockSampler:
@@ -313,19 +321,31 @@ def run_ours(args) -> None:
     px_per_step = n * len(qualities)
     value = world * px_per_step * args.steps / (total_ms / 1e3) / 1e6
 
-    # roofline of the dominant call
+    # roofline of the dominant call (its own bound: HBM bytes, or ALU operations)
     peaks = load_peaks()
     avg_us = {name: 1e3 * statistics.mean(v) for name, v in per_call.items()}
+    alu_peak = torch.cuda.get_device_properties(local).multi_processor_count * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12
+
+    def call_roofline(name):
+        t = avg_us[name] * 1e-6
+        if name in ALU_OPS_PER_PX:
+            a = ALU_OPS_PER_PX[name] * n / t / 1e12
+            return {"bound": "alu", "achieved": round(a, 2), "peak": round(alu_peak, 2), "unit": "Tops/s",
+                    "frac": round(a / alu_peak, 4), "algorithmic_ops": ALU_OPS_PER_PX[name] * n,
+                    "peak_source": "SMs x 128 lanes x max SM clock"}
+        a = BYTES_PER_PX[name] * n / t / 1e9
+        return {"bound": "hbm", "achieved": round(a, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(a / peaks["hbm_gbs"], 4), "algorithmic_bytes": BYTES_PER_PX[name] * n,
+                "peak_source": peaks["src"]}
+
     dom = max(avg_us, key=lambda k: avg_us[k])
-    achieved = BYTES_PER_PX[dom] * n / (avg_us[dom] * 1e-6) / 1e9
+    roofline = call_roofline(dom)
     tr = TRAFFIC.get(dom)
-    traffic = None
-    if tr and tr["sha"] == _sha(KERNEL_SOURCE[dom]):
-        traffic = tr["bytes_per_px"] * n
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic, "kernel": dom,
-                "algorithmic_bytes": BYTES_PER_PX[dom] * n, "peak_source": peaks["src"],
-                "timing": call_timing}
+    roofline["traffic"] = tr["bytes_per_px"] * n if tr and tr["sha"] == _sha(KERNEL_SOURCE[dom]) else None
+    roofline["kernel"] = dom
+    roofline["timing"] = call_timing
+    stage_roofline = {name: {k: v for k, v in call_roofline(name).items() if k in ("bound", "achieved", "unit", "frac")}
+                      for name in calls}
     stage_us = {name: round(v, 2) for name, v in avg_us.items()}
     stage_frac = {name: round(BYTES_PER_PX[name] * n / (avg_us[name] * 1e-6) / 1e9 / peaks["hbm_gbs"], 4)
                   for name in calls}
@@ -380,7 +400,8 @@ def run_ours(args) -> None:
                     "h2d_bytes_per_step": hc.h2d_bytes() * len(qualities),
                     "d2h_bytes_per_step": hc.d2h_bytes() * len(qualities)},
             "gpu_launches": args.steps * len(qualities) * 6,
-            "roofline": roofline, "stage_us": stage_us, "stage_hbm_frac": stage_frac,
+            "roofline": roofline, "stage_us": stage_us, "stage_roofline": stage_roofline,
+            "stage_hbm_frac": stage_frac,
             "clocks": clocks.summary(), "cpu_baseline": cpu, "wall_s_timed": round(wall, 3),
         }
         print(json.dumps(line), flush=True)

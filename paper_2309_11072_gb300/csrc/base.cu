@@ -81,10 +81,9 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8], int r) {
 // bucket plus, from bit 8, the low 16 bits of that threshold (0x10000 when
 // there is none), so the count is one lookup and one integer comparison
 // (positive floats order like their bits).  No branch.
-__device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {
+__device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {   // code = table + 1
     const int bits = __float_as_int(v);
-    const int b = min(max((bits - 0x35800000) >> 16, -1), 2560) + 1;
-    const uint32_t e = code[b];
+    const uint32_t e = code[min(max((bits - 0x35800000) >> 16, -1), 2560)];   // `code` points at bucket 0
     return (int)(e & 255u) + ((uint32_t)(bits & 0xFFFF) >= (e >> 8) ? 1 : 0);
 }
 
@@ -208,9 +207,9 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
             const float den = __fadd_rn(1.0f, L);
             const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
             const int keep = E == 0 ? 0 : -1;
-            sdr[0][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr[i] + 1)), gcode) & keep;
-            sdr[1][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg[i] + 1)), gcode) & keep;
-            sdr[2][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb[i] + 1)), gcode) & keep;
+            sdr[0][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr[i] + 1)), gcode + 1) & keep;
+            sdr[1][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg[i] + 1)), gcode + 1) & keep;
+            sdr[2][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb[i] + 1)), gcode + 1) & keep;
         }
         if (sdr3 && x0 < w) {
 #pragma unroll
@@ -222,10 +221,11 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            int X[8], F[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) X[i] = sdr[c][i] - 128;
-            fdct8(X, F, 1 << 8);
+            // the transform of (sdr - 128): only F[0] sees the level shift
+            // (every other output's coefficients sum to zero), by -1024 C4
+            int F[8];
+            fdct8(sdr[c], F, 1 << 8);
+            F[0] -= 1024 * C4;
             int* tile = T + (c * 4 + blk) * 72 + sub;   // coefficient u of row sub at word 8u + sub
 #pragma unroll
             for (int u = 0; u < 8; ++u) tile[8 * u] = F[u] >> 9;
