@@ -360,91 +360,10 @@ __device__ __forceinline__ void run_feed(RunAcc& run, int E, const RunAcc& part,
 // Segments with three or more exponents (or ragged ones) are queued per warp
 // and drained 32 at a time, one per lane, so the rare per-pixel work does not
 // make every lane of the warp wait on it.  An entry is 21 words: the exponent
-// bytes, the mantissa bytes of the three planes, the x pairs and the count;
-// the odd stride keeps the lanes' accesses on distinct banks.
+// bytes, the mantissa bytes of the three planes, the x pairs and the count
+// (or, for a flushed run, its 13 sums and the tag 256 + E); the odd stride
+// keeps the lanes' accesses on distinct banks.
 constexpr int kQueueStride = 21;
-
-// Adds one queued entry to the bins: a flushed run (tag 256 + E; words 0-12
-// hold N and the channel sums in bin order) or a segment (tag = pixel
-// count), whose pixels are summed in order and added once per stretch of
-// equal exponents.
-template <bool kUnroll>
-__device__ __forceinline__ void drain_entry(const uint32_t* q, uint32_t B) {
-    const uint32_t tag = q[20];
-    uint32_t acc[kNsum];
-    if (tag >= 256u) {
-#pragma unroll
-        for (int j = 0; j < kNsum; ++j) acc[j] = q[j];
-        bins_add32(B, (int)(tag - 256u), acc);
-        return;
-    }
-    uint32_t elo = q[0], ehi = q[1];
-    uint32_t mlo[3] = {q[2], q[3], q[4]}, mhi[3] = {q[5], q[6], q[7]};
-    uint32_t X[3][4];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) X[c][k] = q[8 + 4 * c + k];
-    const int cnt = (int)tag;
-    int Ecur = (int)(elo & 255u);
-#pragma unroll
-    for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
-    if constexpr (kUnroll) {
-        // fully unrolled: every byte and pair is picked with a constant index
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (i < cnt) {
-                const int E = (int)byte_of(i < 4 ? elo : ehi, i & 3);
-                if (E != Ecur) {
-                    bins_add32(B, Ecur, acc);
-#pragma unroll
-                    for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
-                    Ecur = E;
-                }
-                acc[0] += 1u;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const uint32_t x = (X[c][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-                    const uint32_t yv = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
-                    acc[1 + 4 * c] += x;
-                    acc[2 + 4 * c] += yv;
-                    acc[3 + 4 * c] += x * yv;
-                    acc[4 + 4 * c] += x * x;
-                }
-            }
-        }
-    } else {
-        // compact loop (fewer registers): shift the next pixel into place
-#pragma unroll 1
-        for (int i = 0; i < cnt; ++i) {
-            const int E = (int)(elo & 255u);
-            elo = __funnelshift_r(elo, ehi, 8);
-            ehi >>= 8;
-            if (E != Ecur) {
-                bins_add32(B, Ecur, acc);
-#pragma unroll
-                for (int j = 0; j < kNsum; ++j) acc[j] = 0u;
-                Ecur = E;
-            }
-            acc[0] += 1u;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const uint32_t x = X[c][0] & 0xFFFFu, yv = mlo[c] & 255u;
-                acc[1 + 4 * c] += x;
-                acc[2 + 4 * c] += yv;
-                acc[3 + 4 * c] += x * yv;
-                acc[4 + 4 * c] += x * x;
-                mlo[c] = __funnelshift_r(mlo[c], mhi[c], 8);
-                mhi[c] >>= 8;
-                X[c][0] = __funnelshift_r(X[c][0], X[c][1], 16);
-                X[c][1] = __funnelshift_r(X[c][1], X[c][2], 16);
-                X[c][2] = __funnelshift_r(X[c][2], X[c][3], 16);
-                X[c][3] >>= 16;
-            }
-        }
-    }
-    bins_add32(B, Ecur, acc);
-}
 
 // Per-warp state of the fit: one run per exponent parity (adjacent regions
 // of a smooth exponent field differ by one, so a boundary through a lane's
@@ -456,11 +375,47 @@ struct FitWarp {
     int queued;   // entries in the queue (warp-uniform)
 };
 
-// Drains the warp's queue, one entry per lane (kUnroll: the faster drain
-// that needs more registers).
+// Adds one queued entry to the bins without branches on the exponents: a
+// flushed run (tag 256 + E) as its 13 sums, or a segment (tag = pixel count,
+// 1 .. 8) pixel by pixel, 19 reductions each (the count, x and y are below
+// 2^12 and go to the low words alone; x y and x x take two words).
+__device__ __noinline__ void drain_entry_flat(const uint32_t* q, uint32_t B) {
+    const uint32_t tag = q[20];
+    if (tag >= 256u) {
+        uint32_t acc[kNsum];
+#pragma unroll
+        for (int j = 0; j < kNsum; ++j) acc[j] = q[j];
+        bins_add32(B, (int)(tag - 256u), acc);
+        return;
+    }
+    const uint32_t elo = q[0], ehi = q[1];
+    const uint32_t mlo[3] = {q[2], q[3], q[4]}, mhi[3] = {q[5], q[6], q[7]};
+    constexpr uint32_t kHi = 4u * kNbin * kNsum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < (int)tag) {
+            const uint32_t lo = B + 4u * kNsum * byte_of(i < 4 ? elo : ehi, i & 3);
+            red_add(lo, 1u);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const uint32_t x = (q[8 + 4 * c + (i >> 1)] >> (16 * (i & 1))) & 0xFFFFu;
+                const uint32_t y = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
+                const uint32_t xy = x * y, xx = x * x, a = lo + 4u * (1 + 4 * c);
+                red_add(a, x);
+                red_add(a + 4u, y);
+                red_add(a + 8u, xy & 0xFFFu);
+                red_add(a + 8u + kHi, xy >> 12);
+                red_add(a + 12u, xx & 0xFFFu);
+                red_add(a + 12u + kHi, xx >> 12);
+            }
+        }
+    }
+}
+
+// Drains the warp's queue, one entry per lane.
 template <bool kUnroll = false>
 __device__ __forceinline__ void fit_drain(FitWarp& st, SmemBins& bins, int lane) {
-    if (lane < st.queued) drain_entry<kUnroll>(st.Q + lane * kQueueStride, smem_addr(&bins));
+    if (lane < st.queued) drain_entry_flat(st.Q + lane * kQueueStride, smem_addr(&bins));
     __syncwarp();
     st.queued = 0;
 }
