@@ -22,8 +22,11 @@
  *   call only clears the outputs it documents as cleared.
  * - Typed buffers must be naturally aligned (uint32/float/int32: 4 bytes,
  *   int16: 2, int64: 8); a misaligned one is rejected with SLRME_EINVAL.
- *   Byte planes may start anywhere.  Buffers aligned to 16 bytes with
- *   w % 8 == 0 take the vectorised path, others a scalar path.
+ *   Byte planes may start anywhere.  Planes aligned to 16 bytes with
+ *   w % 16 == 0 take the tensor-map (TMA) kernels of slr_fit,
+ *   residual_encode and residual_decode; 8-byte aligned planes with
+ *   w % 8 == 0 take vectorised loads; others a scalar path.  Every path
+ *   gives the same results.
  * - Return value: SLRME_OK, or a negative SLRME_E* code; the text of the
  *   last error of the calling thread is in slrme_last_error().
  *   SLRME_EINVAL is returned before anything is enqueued.  SLRME_ECUDA
