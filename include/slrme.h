@@ -345,6 +345,15 @@ int slrme_host_tables(int32_t* log2_lut, float* gamma, float* kr, float* wr,
  * kernel then stopped and its outputs are incomplete).  clear != 0 resets it. */
 int slrme_device_status(int* status, int clear);
 
+/* Self-test of the bounded waits the TMA-staged kernels use (the paper has
+ * no counterpart): launches one warp that waits on a shared-memory mbarrier
+ * for at most max_spins polls (1 .. 2^20).  arrive = 0: nothing arrives, so
+ * the wait gives up, sets the device status word to 1 (see
+ * slrme_device_status) and the kernel returns, leaving the context usable;
+ * arrive = 1: the barrier completes and the status word is untouched.
+ * Asynchronous on `stream`; SLRME_EINVAL for arguments out of range. */
+int slrme_wait_probe(int max_spins, int arrive, slrme_stream_t stream);
+
 /* Text of the last error reported to the calling thread ("" if none). */
 const char* slrme_last_error(void);
 

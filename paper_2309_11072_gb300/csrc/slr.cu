@@ -1932,6 +1932,41 @@ extern "C" int slr_fit_noalloc(const uint8_t* s_dec3, const uint8_t* m3, const u
     return cuda_status("slr_fit_noalloc solve launch");
 }
 
+namespace slrme {
+namespace {
+
+// Self-test of the bounded waits: one warp waits for phase 0 of a
+// shared-memory mbarrier with room for one arrival.  With `arrive` = 0
+// nothing ever arrives: the wait gives up after max_spins polls, records
+// the timeout in the device status word and the kernel returns (no copy is
+// in flight, so nothing is left behind).  With arrive = 1 lane 0 arrives
+// first and the wait completes.
+__global__ void __launch_bounds__(32) k_wait_probe(int max_spins, int arrive) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        fence_async_shared();
+    }
+    __syncwarp();
+    if (arrive && threadIdx.x == 0) mbar_arrive(b);
+    __syncwarp();
+    mbar_wait(b, 0u, &g_slrme_status, max_spins);
+}
+
+}  // namespace
+}  // namespace slrme
+
+extern "C" int slrme_wait_probe(int max_spins, int arrive, slrme_stream_t stream) {
+    using namespace slrme;
+    if (max_spins < 1 || max_spins > (1 << 20) || (arrive != 0 && arrive != 1)) {
+        set_error("slrme_wait_probe: max_spins must be in 1..2^20 and arrive 0 or 1");
+        return SLRME_EINVAL;
+    }
+    k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(max_spins, arrive);
+    return cuda_status("slrme_wait_probe launch");
+}
+
 extern "C" int slrme_device_status(int* status, int clear) {
     using namespace slrme;
     if (!status) {

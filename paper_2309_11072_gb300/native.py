@@ -41,6 +41,7 @@ _SIGS = {
     "residual_decode": [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp],
     "slrme_host_tables": [_vp, _vp, _vp, _vp, _i32, _vp, _vp],
     "slrme_device_status": [_vp, _i32],
+    "slrme_wait_probe": [_i32, _i32, _vp],
 }
 
 
@@ -145,6 +146,11 @@ def device_status(clear: bool = True) -> int:
     v = ctypes.c_int(-1)
     _check("slrme_device_status", lib().slrme_device_status(ctypes.addressof(v), int(clear)))
     return v.value
+
+
+def wait_probe(max_spins: int, arrive: bool, stream=None) -> None:
+    """Launches the library's bounded-wait self-test (see slrme_wait_probe)."""
+    _check("slrme_wait_probe", lib().slrme_wait_probe(int(max_spins), int(bool(arrive)), _stream(stream)))
 
 
 def host_tables(quality: int = 50) -> dict:
