@@ -45,6 +45,12 @@ def lib():
             _lib.oracle_i128_to_double_parts.argtypes = [ctypes.c_int64, ctypes.c_uint64]
             _lib.oracle_rgbe_from_float.restype = ctypes.c_int
             _lib.oracle_base_roundtrip.restype = ctypes.c_int
+            _lib.oracle_rans_table.restype = ctypes.c_int
+            _lib.oracle_rans_encode.restype = ctypes.c_int
+            _lib.oracle_rans_encode.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]
+            _lib.oracle_rans_decode.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_void_p]
     return _lib
 
 
@@ -241,3 +247,42 @@ def entropy_bits(hist: np.ndarray) -> float:
         return 0.0
     p = h[h > 0] / tot
     return float(-(p * np.log2(p)).sum())
+
+
+# ---------------------------------------------------------------- enhancement-layer coder (rANS)
+RANS_CHUNK, RANS_LANES, RANS_CAP = 8192, 32, 8192 // 32 + 2
+
+
+def rans_table(counts: np.ndarray) -> np.ndarray:
+    """Frequency table (total 2^14) of one channel from its residual histogram."""
+    c = np.ascontiguousarray(counts, dtype=np.uint32).reshape(NRES)
+    f = np.zeros(NRES, np.uint32)
+    lib().oracle_rans_table(_p(c), _p(f))
+    return f
+
+
+def rans_layout(n: int):
+    chunks = (n + RANS_CHUNK - 1) // RANS_CHUNK
+    return chunks, 3 * chunks * RANS_LANES * RANS_CAP, 3 * chunks * RANS_LANES
+
+
+def rans_encode(r3: np.ndarray, freq3: np.ndarray):
+    """Words ([3][chunks][32][258] uint16) and counts ([3][chunks][32]) of the residual planes."""
+    r = np.ascontiguousarray(r3, dtype=np.int16).reshape(-1)
+    n = r.size // 3
+    _, nw, nc = rans_layout(n)
+    words = np.zeros(nw, np.uint16)
+    counts = np.zeros(nc, np.uint32)
+    f = np.ascontiguousarray(freq3, dtype=np.uint32).reshape(3 * NRES)
+    rc = lib().oracle_rans_encode(_p(r), n, _p(f), _p(words), _p(counts))
+    if rc != 0:
+        raise ValueError("a residual has a zero frequency in its channel's table")
+    return words, counts
+
+
+def rans_decode(words: np.ndarray, counts: np.ndarray, n: int, freq3: np.ndarray) -> np.ndarray:
+    out = np.zeros(3 * n, np.int16)
+    f = np.ascontiguousarray(freq3, dtype=np.uint32).reshape(3 * NRES)
+    lib().oracle_rans_decode(_p(np.ascontiguousarray(words, dtype=np.uint16)),
+                             _p(np.ascontiguousarray(counts, dtype=np.uint32)), n, _p(f), _p(out))
+    return out

@@ -530,3 +530,147 @@ void oracle_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h
     free(x3);
     free(ms);
 }
+
+/* ===================================================================== enhancement-layer coder
+ * The reversible coder of the residual planes (Sec. III-C sends R to a
+ * lossless coder; the paper uses JPEG 2000 lossless, Sec. IV).  Here: a
+ * static rANS coder with one frequency table per channel, written from the
+ * published rANS construction (J. Duda, "Asymmetric numeral systems", 2013)
+ * as specified for this library:
+ *   symbols s = R + 255 in 0..510; table total M = 2^14;
+ *   state x in [L, 2^32) with L = 2^16; 16-bit words in and out;
+ *   encode s (f, c): if floor(x / 2^18) >= f, emit x mod 2^16, x = floor(x / 2^16);
+ *                    then x = floor(x / f) M + (x mod f) + c;
+ *   decode: slot = x mod M, s the symbol with c <= slot < c + f,
+ *           x = f floor(x / M) + slot - c; if x < L, x = 2^16 x + next word.
+ * A plane's symbols (raster order) are cut into chunks of 8192; stream l
+ * (0..31) of chunk k codes symbols k 8192 + l + 32 j in increasing j.  A
+ * stream's words sit at the end of its region of 258 words, in decoding
+ * order: the final encoder state (high word, low word), then the
+ * renormalisation words; counts[] holds the words used per stream. */
+
+#define RANS_BITS 14
+#define RANS_M (1u << RANS_BITS)
+#define RANS_L (1u << 16)
+#define RANS_CHUNK 8192
+#define RANS_LANES 32
+#define RANS_CAP (RANS_CHUNK / RANS_LANES + 2)
+
+/* Frequency table of one channel from its residual histogram: every symbol
+ * that occurs gets max(1, floor(count M / N)); the shortfall to M goes to the
+ * most frequent symbol (smallest on ties), an excess is taken one at a time
+ * from the largest entry above 1 (smallest symbol on ties).  Returns the
+ * number of symbols that occur (0: an empty histogram, all entries 0). */
+int oracle_rans_table(const uint32_t* counts, uint32_t* freq)
+{
+    uint64_t N = 0;
+    int used = 0;
+    for (int s = 0; s < NRES; ++s) {
+        N += counts[s];
+        used += counts[s] != 0;
+    }
+    for (int s = 0; s < NRES; ++s) freq[s] = 0;
+    if (N == 0) return 0;
+    int64_t sum = 0;
+    for (int s = 0; s < NRES; ++s)
+        if (counts[s]) {
+            uint64_t f = (uint64_t)counts[s] * RANS_M / N;
+            freq[s] = (uint32_t)(f < 1 ? 1 : f);
+            sum += freq[s];
+        }
+    int64_t diff = (int64_t)RANS_M - sum;
+    if (diff > 0) {
+        int best = 0;
+        for (int s = 1; s < NRES; ++s)
+            if (counts[s] > counts[best]) best = s;
+        freq[best] += (uint32_t)diff;
+    }
+    while (diff < 0) {
+        int best = -1;
+        for (int s = 0; s < NRES; ++s)
+            if (freq[s] > 1 && (best < 0 || freq[s] > freq[best])) best = s;
+        freq[best] -= 1;
+        diff += 1;
+    }
+    return used;
+}
+
+static void rans_cum(const uint32_t* freq, uint32_t* cum)
+{
+    uint32_t c = 0;
+    for (int s = 0; s < NRES; ++s) {
+        cum[s] = c;
+        c += freq[s];
+    }
+}
+
+/* Symbols of stream l of chunk k of a plane of n symbols. */
+static int64_t rans_stream_len(int64_t n, int64_t k, int l)
+{
+    int64_t end = (k + 1) * RANS_CHUNK < n ? (k + 1) * RANS_CHUNK : n;
+    int64_t first = k * RANS_CHUNK + l;
+    return first < end ? (end - 1 - first) / RANS_LANES + 1 : 0;
+}
+
+/* Encodes the three residual planes (int16 [3][n]) with the channels'
+ * tables freq3 ([3][511]).  words: [3][chunks][32][258] uint16, counts:
+ * [3][chunks][32]; chunks = ceil(n / 8192).  Returns 0, or -1 when a
+ * residual has a zero frequency (the table does not cover the data). */
+int oracle_rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts)
+{
+    int64_t chunks = (n + RANS_CHUNK - 1) / RANS_CHUNK;
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t* freq = freq3 + c * NRES;
+        uint32_t cum[NRES];
+        rans_cum(freq, cum);
+        for (int64_t k = 0; k < chunks; ++k)
+            for (int l = 0; l < RANS_LANES; ++l) {
+                uint16_t* region = words + ((c * chunks + k) * RANS_LANES + l) * RANS_CAP;
+                int64_t len = rans_stream_len(n, k, l);
+                uint32_t x = RANS_L;
+                int p = RANS_CAP;
+                for (int64_t j = len - 1; j >= 0; --j) {
+                    int s = r3[c * n + k * RANS_CHUNK + l + RANS_LANES * j] + 255;
+                    uint32_t f = freq[s];
+                    if (f == 0) return -1;
+                    if ((x >> 18) >= f) {
+                        region[--p] = (uint16_t)(x & 0xFFFFu);
+                        x >>= 16;
+                    }
+                    x = (x / f) * RANS_M + (x % f) + cum[s];
+                }
+                region[--p] = (uint16_t)(x & 0xFFFFu);
+                region[--p] = (uint16_t)(x >> 16);
+                counts[(c * chunks + k) * RANS_LANES + l] = (uint32_t)(RANS_CAP - p);
+            }
+    }
+    return 0;
+}
+
+/* Decodes what oracle_rans_encode wrote back into the residual planes. */
+void oracle_rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3,
+                        int16_t* r3)
+{
+    int64_t chunks = (n + RANS_CHUNK - 1) / RANS_CHUNK;
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t* freq = freq3 + c * NRES;
+        uint32_t cum[NRES];
+        rans_cum(freq, cum);
+        for (int64_t k = 0; k < chunks; ++k)
+            for (int l = 0; l < RANS_LANES; ++l) {
+                const uint16_t* region = words + ((c * chunks + k) * RANS_LANES + l) * RANS_CAP;
+                int64_t len = rans_stream_len(n, k, l);
+                int p = RANS_CAP - (int)counts[(c * chunks + k) * RANS_LANES + l];
+                uint32_t x = ((uint32_t)region[p] << 16) | region[p + 1];
+                p += 2;
+                for (int64_t j = 0; j < len; ++j) {
+                    uint32_t slot = x & (RANS_M - 1);
+                    int s = 0;
+                    while (!(cum[s] <= slot && slot < cum[s] + freq[s])) ++s;
+                    x = freq[s] * (x >> RANS_BITS) + slot - cum[s];
+                    if (x < RANS_L) x = (x << 16) | region[p++];
+                    r3[c * n + k * RANS_CHUNK + l + RANS_LANES * j] = (int16_t)(s - 255);
+                }
+            }
+    }
+}
