@@ -152,6 +152,70 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
                     int gf_on, const slrme_params* params, uint32_t* rgbe_out,
                     slrme_stream_t stream);
 
+/* ===================================================================== enhancement-layer entropy coder
+ * The enhancement layer carries the residuals R to the decoder through a
+ * reversible coder (Sec. II-A: the enhancement layer's coders must be
+ * reversible for lossless decoding; Sec. IV codes it with JPEG 2000's
+ * lossless mode).  This coder is interleaved range asymmetric numeral
+ * systems (rANS, Duda 2013) with one static frequency table per colour
+ * channel:
+ *   M = 2^14 (table total), state x in [2^16, 2^32), 16-bit words;
+ *   symbol s = R + 255 (0..510), frequency f_s, cumulative c_s = sum_{t<s} f_t;
+ *   encode, symbols of a stream in reverse order, from x = 2^16:
+ *     if floor(x / 2^18) >= f_s: emit x mod 2^16, x = floor(x / 2^16);
+ *     x = floor(x / f_s) M + (x mod f_s) + c_s;
+ *   finally emit x mod 2^16, then floor(x / 2^16);
+ *   decode: slot = x mod M, s with c_s <= slot < c_s + f_s,
+ *     x = f_s floor(x / M) + slot - c_s, and if x < 2^16, x = 2^16 x + next word;
+ *   the decoder reads the words in the reverse of their emission order and
+ *   ends in the state 2^16 with every word read.
+ * Layout for three residual planes of n symbols each (int16 [3][n], the
+ * planes of residual_encode with n = h*w): chunks = ceil(n / 8192); chunk k
+ * of plane c is coded as 32 streams, stream l taking symbols k*8192 + l + 32 j
+ * (j = 0, 1, ...) of the plane.  Stream l of chunk k of plane c owns the
+ * region of SLRME_RANS_CAP (258) uint16 words starting at word
+ * ((c*chunks + k)*32 + l)*258 of `words`; its used words sit at the end of
+ * the region in decoding order (the state's high word, its low word, then the
+ * renormalisation words) and the words before them are 0.
+ * counts[(c*chunks + k)*32 + l] (uint32) is the number of words the stream
+ * used (2..258, or 0 for a stream that could not be coded).
+ * Errors found while a kernel runs (a residual outside -255..255 or with a
+ * zero frequency, a table whose entries exceed M or do not sum to M, a stream
+ * whose words do not decode back to the initial state) set bit 1 (value 2) of
+ * the device status word (slrme_device_status); the affected outputs are then
+ * unspecified but every access stays inside the documented buffers. */
+#define SLRME_RANS_CHUNK  8192   /* symbols per chunk of a plane                 */
+#define SLRME_RANS_LANES  32     /* interleaved streams per chunk                */
+#define SLRME_RANS_CAP    258    /* uint16 words per stream region (256 + 2)     */
+#define SLRME_RANS_M      16384  /* table total                                  */
+
+/* Host, no GPU: uint16 words of `words` and uint32 entries of `counts` for
+ * three planes of n symbols (0 for n <= 0). */
+int64_t rans_words_capacity(int64_t n);
+int64_t rans_counts_capacity(int64_t n);
+
+/* Frequency tables freq3 (uint32 [3][511], device) from the residual
+ * histograms hist3 (uint32 [3][511], device, as residual_encode writes them):
+ * per channel with N = sum of its counts n_s > 0, f_s = max(1, floor(n_s M / N))
+ * for every s with n_s > 0 and 0 otherwise; a shortfall M - sum f is added to
+ * the most frequent symbol (smallest s on ties); an excess is removed one
+ * unit at a time from the largest entry above 1 (smallest s on ties).  A
+ * channel with N = 0 gets an all-zero table.  Asynchronous on `stream`. */
+int rans_tables(const uint32_t* hist3, uint32_t* freq3, slrme_stream_t stream);
+
+/* Encodes the residual planes r3 (int16 [3][n], device, 2-byte aligned) with
+ * the tables freq3 (device) into words (device, rans_words_capacity(n) uint16,
+ * 16-byte aligned; every word is written) and counts (device,
+ * rans_counts_capacity(n) uint32).  0 <= n < 2^31; n = 0 enqueues nothing.
+ * The table total M must hold for every channel with n > 0 symbols. */
+int rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts,
+                slrme_stream_t stream);
+
+/* Decodes words/counts (as rans_encode writes them; words 2-byte aligned)
+ * with the same tables back into the residual planes r3 (int16 [3][n]). */
+int rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3, int16_t* r3,
+                slrme_stream_t stream);
+
 /* ===================================================================== learned estimator
  * A small integer CNN that predicts the mantissas from the decoded SDRI and
  * the exponent plane, a learned alternative to Eq. (8) (the paper's estimator
@@ -340,15 +404,17 @@ int slrme_batch_graph_destroy(slrme_batch_plan* plan);
 int slrme_host_tables(int32_t* log2_lut, float* gamma, float* kr, float* wr,
                       int quality, int32_t* quant, int32_t* dct);
 
-/* Device status word of the current device (synchronous): 0, or
- * 1 when a kernel's wait for its own bulk copies gave up after its bound (the
- * kernel then stopped and its outputs are incomplete).  clear != 0 resets it. */
+/* Device status word of the current device (synchronous): 0, or a mask of
+ * bit 0 (1): a kernel's wait for its own bulk copies gave up after its bound
+ *   (the kernel then stopped and its outputs are incomplete);
+ * bit 1 (2): the rANS coder met input outside its table or a corrupt stream.
+ * clear != 0 resets it. */
 int slrme_device_status(int* status, int clear);
 
 /* Self-test of the bounded waits the TMA-staged kernels use (the paper has
  * no counterpart): launches one warp that waits on a shared-memory mbarrier
  * for at most max_spins polls (1 .. 2^20).  arrive = 0: nothing arrives, so
- * the wait gives up, sets the device status word to 1 (see
+ * the wait gives up, sets bit 0 of the device status word (see
  * slrme_device_status) and the kernel returns, leaving the context usable;
  * arrive = 1: the barrier completes and the status word is untouched.
  * Asynchronous on `stream`; SLRME_EINVAL for arguments out of range. */

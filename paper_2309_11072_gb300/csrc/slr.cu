@@ -1857,6 +1857,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned long long g_fit_scratch[kNbin * kNsum];
 static std::mutex g_scratch_mu;
 static void* g_scratch_addr[kMaxDevices];
+static void* g_status_addr[kMaxDevices];
 
 // Device address of g_fit_scratch on the current device, looked up once per
 // device (with that device current).  In host code the array's name is only a
@@ -1887,6 +1888,33 @@ int scratch_address(void** out) {
 }
 
 }  // namespace
+
+// Device address of the status word g_slrme_status on the current device,
+// looked up once per device, for kernels of other translation units.
+int status_word_address(int** out) {
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) {
+        set_error("status word: cudaGetDevice: %s", cudaGetErrorString(err));
+        return SLRME_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("status word: device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
+        return SLRME_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_status_addr[dev]) {
+        void* p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_slrme_status);
+        if (err != cudaSuccess || !p) {
+            set_error("status word: cudaGetSymbolAddress: %s", cudaGetErrorString(err));
+            return SLRME_ECUDA;
+        }
+        g_status_addr[dev] = p;
+    }
+    *out = (int*)g_status_addr[dev];
+    return SLRME_OK;
+}
 
 }  // namespace slrme
 

@@ -87,6 +87,10 @@ Geometry geometry();
 void set_error(const char* fmt, ...);
 int cuda_status(const char* what);   // SLRME_OK or SLRME_ECUDA after a launch
 
+// Device address of the library's status word (see slrme_device_status) on
+// the current device; kernels OR their error bits into it.
+int status_word_address(int** out);
+
 // ---------------------------------------------------------------- launchers
 int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e,
                  int64_t* lum_stats, cudaStream_t s);

@@ -11,7 +11,7 @@
 
 namespace slrme {
 
-constexpr int kStatusWaitTimeout = 1;   // an mbarrier wait gave up
+constexpr int kStatusWaitTimeout = 1;   // bit 0: an mbarrier wait gave up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -55,7 +55,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
             : "memory");
         if (done) return true;
     }
-    atomicExch(status, kStatusWaitTimeout);
+    atomicOr(status, kStatusWaitTimeout);
     return false;
 }
 

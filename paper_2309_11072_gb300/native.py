@@ -42,6 +42,9 @@ _SIGS = {
     "slrme_host_tables": [_vp, _vp, _vp, _vp, _i32, _vp, _vp],
     "slrme_device_status": [_vp, _i32],
     "slrme_wait_probe": [_i32, _i32, _vp],
+    "rans_tables": [_vp, _vp, _vp],
+    "rans_encode": [_vp, _i64, _vp, _vp, _vp, _vp],
+    "rans_decode": [_vp, _vp, _i64, _vp, _vp, _vp],
 }
 
 
@@ -66,6 +69,10 @@ def lib() -> ctypes.CDLL:
             L.slrme_last_error.argtypes = []
             L.slr_fit_workspace_bytes.restype = ctypes.c_size_t
             L.slr_fit_workspace_bytes.argtypes = []
+            for name in ("rans_words_capacity", "rans_counts_capacity"):
+                fn = getattr(L, name)
+                fn.restype = ctypes.c_int64
+                fn.argtypes = [_i64]
             _lib = L
     return _lib
 
@@ -139,6 +146,28 @@ def residual_encode(s_dec3, m3, e, h: int, w: int, gf_on: int, params, r3, hist=
 def residual_decode(s_dec3, e, r3, h: int, w: int, gf_on: int, params, rgbe_out, stream=None) -> None:
     _check("residual_decode", lib().residual_decode(_ptr(s_dec3), _ptr(e), _ptr(r3), h, w, int(gf_on),
                                                     _ptr(params), _ptr(rgbe_out), _stream(stream)))
+
+
+def rans_words_capacity(n: int) -> int:
+    return int(lib().rans_words_capacity(int(n)))
+
+
+def rans_counts_capacity(n: int) -> int:
+    return int(lib().rans_counts_capacity(int(n)))
+
+
+def rans_tables(hist3, freq3, stream=None) -> None:
+    _check("rans_tables", lib().rans_tables(_ptr(hist3), _ptr(freq3), _stream(stream)))
+
+
+def rans_encode(r3, n: int, freq3, words, counts, stream=None) -> None:
+    _check("rans_encode", lib().rans_encode(_ptr(r3), int(n), _ptr(freq3), _ptr(words), _ptr(counts),
+                                            _stream(stream)))
+
+
+def rans_decode(words, counts, n: int, freq3, r3, stream=None) -> None:
+    _check("rans_decode", lib().rans_decode(_ptr(words), _ptr(counts), int(n), _ptr(freq3), _ptr(r3),
+                                            _stream(stream)))
 
 
 def device_status(clear: bool = True) -> int:

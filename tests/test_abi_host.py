@@ -128,3 +128,27 @@ def test_batch_struct_layouts_and_argument_checks():
     assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 65536, 0x100000, None) == -1
     assert "at most 65535" in native.last_error()
     assert L.slrme_batch_graph_launch(C.addressof(plan), None) == -1
+
+
+def test_rans_capacity_matches_the_oracle_layout():
+    for n in (0, 1, 31, 8192, 8193, 2048 * 1536, 7680 * 4320):
+        _, nw, nc = O.rans_layout(n)
+        assert native.rans_words_capacity(n) == nw
+        assert native.rans_counts_capacity(n) == nc
+    assert native.rans_words_capacity(-5) == 0 and native.rans_counts_capacity(-5) == 0
+
+
+def test_rans_bad_arguments_rejected_before_any_gpu_work():
+    L = native.lib()
+    EINVAL = -1
+    assert L.rans_tables(None, 64, None) == EINVAL
+    assert L.rans_tables(66, 64, None) == EINVAL                     # hist3 not 4-byte aligned
+    assert L.rans_encode(None, 10, 64, 64, 64, None) == EINVAL
+    assert L.rans_encode(64, 10, 64, 72, 64, None) == EINVAL          # words not 16-byte aligned
+    assert L.rans_encode(65, 10, 64, 64, 64, None) == EINVAL          # r3 not 2-byte aligned
+    assert L.rans_encode(64, -1, 64, 64, 64, None) == EINVAL
+    assert L.rans_encode(64, 1 << 31, 64, 64, 64, None) == EINVAL
+    assert L.rans_decode(64, 66, 10, 64, 64, None) == EINVAL          # counts not 4-byte aligned
+    assert L.rans_decode(64, 64, 10, 64, None, None) == EINVAL
+    assert "rans_decode" in native.last_error()
+    assert L.rans_encode(None, 0, None, None, None, None) == 0        # empty planes: nothing to do
