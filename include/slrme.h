@@ -172,11 +172,12 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
  * Layout for three residual planes of n symbols each (int16 [3][n], the
  * planes of residual_encode with n = h*w): chunks = ceil(n / 8192); chunk k
  * of plane c is coded as 32 streams, stream l taking symbols k*8192 + l + 32 j
- * (j = 0, 1, ...) of the plane.  Stream l of chunk k of plane c owns the
- * region of SLRME_RANS_CAP (258) uint16 words starting at word
- * ((c*chunks + k)*32 + l)*258 of `words`; its used words sit at the end of
- * the region in decoding order (the state's high word, its low word, then the
- * renormalisation words) and the words before them are 0.
+ * (j = 0, 1, ...) of the plane.  Chunk k of plane c owns the block of
+ * 32 * SLRME_RANS_CAP (258) uint16 words starting at word (c*chunks + k)*32*258
+ * of `words`; its streams' words are packed from the start of the block,
+ * stream l from the sum of the word counts of streams 0..l-1, each in decoding
+ * order (the state's high word, its low word, then the renormalisation
+ * words).  rans_encode writes nothing else of a block.
  * counts[(c*chunks + k)*32 + l] (uint32) is the number of words the stream
  * used (2..258, or 0 for a stream that could not be coded).
  * Errors found while a kernel runs (a residual outside -255..255 or with a
@@ -205,14 +206,16 @@ int rans_tables(const uint32_t* hist3, uint32_t* freq3, slrme_stream_t stream);
 
 /* Encodes the residual planes r3 (int16 [3][n], device, 2-byte aligned) with
  * the tables freq3 (device) into words (device, rans_words_capacity(n) uint16,
- * 16-byte aligned; every word is written) and counts (device,
- * rans_counts_capacity(n) uint32).  0 <= n < 2^31; n = 0 enqueues nothing.
+ * 16-byte aligned) and counts (device, rans_counts_capacity(n) uint32).  0 <= n < 2^31; n = 0 enqueues nothing.
  * The table total M must hold for every channel with n > 0 symbols. */
 int rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts,
                 slrme_stream_t stream);
 
-/* Decodes words/counts (as rans_encode writes them; words 2-byte aligned)
- * with the same tables back into the residual planes r3 (int16 [3][n]). */
+/* Decodes words/counts (as rans_encode writes them; words 16-byte aligned)
+ * with the same tables back into the residual planes r3 (int16 [3][n]).
+ * Each chunk's packed words are read with one bulk copy whose wait is
+ * bounded: a wait that gives up sets bit 0 of the status word and the kernel
+ * stops. */
 int rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3, int16_t* r3,
                 slrme_stream_t stream);
 

@@ -267,7 +267,8 @@ def rans_layout(n: int):
 
 
 def rans_encode(r3: np.ndarray, freq3: np.ndarray):
-    """Words ([3][chunks][32][258] uint16) and counts ([3][chunks][32]) of the residual planes."""
+    """Words ([3][chunks] blocks of 32 x 258 uint16, each chunk's streams packed from the start of
+    its block) and counts ([3][chunks][32]) of the residual planes; the rest of a block is 0."""
     r = np.ascontiguousarray(r3, dtype=np.int16).reshape(-1)
     n = r.size // 3
     _, nw, nc = rans_layout(n)

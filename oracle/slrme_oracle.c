@@ -544,10 +544,12 @@ void oracle_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h
  *   decode: slot = x mod M, s the symbol with c <= slot < c + f,
  *           x = f floor(x / M) + slot - c; if x < L, x = 2^16 x + next word.
  * A plane's symbols (raster order) are cut into chunks of 8192; stream l
- * (0..31) of chunk k codes symbols k 8192 + l + 32 j in increasing j.  A
- * stream's words sit at the end of its region of 258 words, in decoding
- * order: the final encoder state (high word, low word), then the
- * renormalisation words; counts[] holds the words used per stream. */
+ * (0..31) of chunk k codes symbols k 8192 + l + 32 j in increasing j.  Each
+ * chunk owns a block of 32 x 258 words; its streams' words are packed from
+ * the start of the block, stream after stream (stream l from the sum of the
+ * word counts of streams 0..l-1), each in decoding order: the final encoder
+ * state (high word, low word), then the renormalisation words.  counts[]
+ * holds the words used per stream; the rest of the block is left as it was. */
 
 #define RANS_BITS 14
 #define RANS_M (1u << RANS_BITS)
@@ -613,7 +615,7 @@ static int64_t rans_stream_len(int64_t n, int64_t k, int l)
 }
 
 /* Encodes the three residual planes (int16 [3][n]) with the channels'
- * tables freq3 ([3][511]).  words: [3][chunks][32][258] uint16, counts:
+ * tables freq3 ([3][511]).  words: [3][chunks] blocks of 32 x 258 uint16, counts:
  * [3][chunks][32]; chunks = ceil(n / 8192).  Returns 0, or -1 when a
  * residual has a zero frequency (the table does not cover the data). */
 int oracle_rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts)
@@ -623,9 +625,13 @@ int oracle_rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint
         const uint32_t* freq = freq3 + c * NRES;
         uint32_t cum[NRES];
         rans_cum(freq, cum);
-        for (int64_t k = 0; k < chunks; ++k)
+        for (int64_t k = 0; k < chunks; ++k) {
+            uint16_t* block = words + (c * chunks + k) * RANS_LANES * RANS_CAP;
+            int64_t at = 0;   /* where the next stream starts in the block */
             for (int l = 0; l < RANS_LANES; ++l) {
-                uint16_t* region = words + ((c * chunks + k) * RANS_LANES + l) * RANS_CAP;
+                /* the words are produced last-first: build them at the end of
+                 * a scratch region, then copy them to the block */
+                uint16_t region[RANS_CAP];
                 int64_t len = rans_stream_len(n, k, l);
                 uint32_t x = RANS_L;
                 int p = RANS_CAP;
@@ -641,8 +647,12 @@ int oracle_rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint
                 }
                 region[--p] = (uint16_t)(x & 0xFFFFu);
                 region[--p] = (uint16_t)(x >> 16);
-                counts[(c * chunks + k) * RANS_LANES + l] = (uint32_t)(RANS_CAP - p);
+                int used = RANS_CAP - p;
+                memcpy(block + at, region + p, (size_t)used * sizeof(uint16_t));
+                at += used;
+                counts[(c * chunks + k) * RANS_LANES + l] = (uint32_t)used;
             }
+        }
     }
     return 0;
 }
@@ -656,21 +666,24 @@ void oracle_rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n
         const uint32_t* freq = freq3 + c * NRES;
         uint32_t cum[NRES];
         rans_cum(freq, cum);
-        for (int64_t k = 0; k < chunks; ++k)
+        for (int64_t k = 0; k < chunks; ++k) {
+            const uint16_t* block = words + (c * chunks + k) * RANS_LANES * RANS_CAP;
+            int64_t at = 0;
             for (int l = 0; l < RANS_LANES; ++l) {
-                const uint16_t* region = words + ((c * chunks + k) * RANS_LANES + l) * RANS_CAP;
+                const uint16_t* stream = block + at;
+                at += counts[(c * chunks + k) * RANS_LANES + l];
                 int64_t len = rans_stream_len(n, k, l);
-                int p = RANS_CAP - (int)counts[(c * chunks + k) * RANS_LANES + l];
-                uint32_t x = ((uint32_t)region[p] << 16) | region[p + 1];
-                p += 2;
+                uint32_t x = ((uint32_t)stream[0] << 16) | stream[1];
+                int p = 2;
                 for (int64_t j = 0; j < len; ++j) {
                     uint32_t slot = x & (RANS_M - 1);
                     int s = 0;
                     while (!(cum[s] <= slot && slot < cum[s] + freq[s])) ++s;
                     x = freq[s] * (x >> RANS_BITS) + slot - cum[s];
-                    if (x < RANS_L) x = (x << 16) | region[p++];
+                    if (x < RANS_L) x = (x << 16) | stream[p++];
                     r3[c * n + k * RANS_CHUNK + l + RANS_LANES * j] = (int16_t)(s - 255);
                 }
             }
+        }
     }
 }

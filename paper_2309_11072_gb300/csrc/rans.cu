@@ -17,16 +17,18 @@
 //   then emit the final state's low word, then its high word;
 //   decode: slot = x mod M, s the symbol with c_s <= slot < c_s + f_s,
 //     x = f_s floor(x / M) + slot - c_s; if x < L: x = 2^16 x + next word.
-// Stream l of chunk k of plane c owns the region of 258 words at word
-// ((c chunks + k) 32 + l) 258; its words fill the end of the region in
-// decoding order (high word, low word, then renormalisation words), the
-// words before them are zero, and counts[(c chunks + k) 32 + l] is the
-// number of words used.
+// Chunk k of plane c owns the block of 32 x 258 words at word
+// (c chunks + k) 32 258; its streams' words are packed from the start of the
+// block, stream l from the sum of the word counts of streams 0..l-1, each in
+// decoding order (high word, low word, then renormalisation words), and
+// counts[(c chunks + k) 32 + l] is the number of words of stream l.  The
+// rest of a block is not written.
 #include <stdint.h>
 
 #include <algorithm>
 
 #include "slrme_internal.cuh"
+#include "tma.cuh"
 
 namespace slrme {
 namespace {
@@ -85,20 +87,27 @@ __global__ void __launch_bounds__(32) k_rans_tables(const uint32_t* __restrict__
             if (lane + 32 * i < kNres) out[lane + 32 * i] = 0u;
         return;
     }
-    long long sum = 0;
+    // floor(n_s M / N) from a double estimate (relative error below 2^-51, so
+    // at most one off, and only next to an integer) and one exact correction;
+    // q N < 2^56 since q <= 2^14 and N < 2^41.
+    const double invN = 1.0 / (double)N;
+    int sum = 0;   // at most 511 x 2^14
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
         uint32_t v = 0;
         if (cnt[i]) {
-            const unsigned long long q = (unsigned long long)cnt[i] * kRansM / N;
+            const unsigned long long a = (unsigned long long)cnt[i] << kRansBits;
+            unsigned long long q = (unsigned long long)((double)a * invN);
+            if (q * N > a) --q;
+            else if ((q + 1) * N <= a) ++q;
             v = q < 1 ? 1u : (uint32_t)q;
         }
         f[i] = v;
-        sum += v;
+        sum += (int)v;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    const long long diff = (long long)kRansM - sum;
+    const int diff = (int)kRansM - sum;
     if (diff > 0) {
         // most frequent symbol, smallest index on ties: key = (count, -s)
         uint32_t bc = 0;
@@ -124,38 +133,39 @@ __global__ void __launch_bounds__(32) k_rans_tables(const uint32_t* __restrict__
         for (int i = 0; i < kPer; ++i)
             if (lane + 32 * i == bs) f[i] += (uint32_t)diff;
     } else if (diff < 0) {
-        const long long D = -diff;
+        const int D = -diff;   // at most 511
         uint32_t fmax = 0;
 #pragma unroll
         for (int i = 0; i < kPer; ++i) fmax = max(fmax, f[i]);
 #pragma unroll
         for (int o = 16; o; o >>= 1) fmax = max(fmax, __shfl_xor_sync(kFull, fmax, o));
-        // smallest T in [1, fmax] with E(T) <= D (E(fmax) = 0)
-        uint32_t lo = 1, hi = fmax;
+        // smallest T with E(T) <= D: E(fmax) = 0, and E(fmax - D - 1) > D
+        // because the largest entry alone contributes D + 1 there
+        uint32_t lo = fmax > (uint32_t)D ? fmax - (uint32_t)D : 1u, hi = fmax;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            long long e = 0;
+            int e = 0;
 #pragma unroll
-            for (int i = 0; i < kPer; ++i) e += f[i] > mid ? (long long)(f[i] - mid) : 0;
+            for (int i = 0; i < kPer; ++i) e += f[i] > mid ? (int)(f[i] - mid) : 0;
 #pragma unroll
             for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
             if (e <= D) hi = mid;
             else lo = mid + 1;
         }
         const uint32_t T = lo;
-        long long e = 0;
+        int e = 0;
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) e += f[i] > T ? (long long)(f[i] - T) : 0;
+        for (int i = 0; i < kPer; ++i) e += f[i] > T ? (int)(f[i] - T) : 0;
 #pragma unroll
         for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
-        const long long r = D - e;
+        const int r = D - e;
         // rank of each entry with f >= T in symbol order s = lane + 32 i
-        long long before = 0;
+        int before = 0;
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
             const bool cand = f[i] >= T;
             const unsigned m = __ballot_sync(kFull, cand);
-            const long long rank = before + __popc(m & ((1u << lane) - 1u));
+            const int rank = before + __popc(m & ((1u << lane) - 1u));
             if (cand) f[i] = (rank < r) ? T - 1 : T;
             before += __popc(m);
         }
@@ -229,6 +239,27 @@ __device__ __forceinline__ uint32_t div_by_magic(uint32_t x, uint32_t ml, uint32
     return (uint32_t)(t >> 14);
 }
 
+// One encoder step for residual value v, without branches: the low word of
+// x is stored at the next free position every step, and the position moves
+// only when the word is emitted (a word stored without moving is overwritten
+// by the next emitted word or by the final state, so it never survives).
+// Each step emits at most one word, so the positions stay in 1..257.  A value
+// outside -255..255 reads entry 511, whose frequency is 0 like that of any
+// symbol the table leaves out; fmin records it (the stream is then
+// reported).
+__device__ __forceinline__ void enc_step(uint32_t& x, int& p, uint32_t& fmin, uint16_t* st, const EncSym* tab,
+                                         int16_t v) {
+    const uint32_t s = min((uint32_t)((int)v + 255), (uint32_t)kNres);
+    const EncSym e = tab[s];
+    fmin = min(fmin, e.f);
+    const bool emit = (x >> 18) >= e.f;
+    st[p - 1] = (uint16_t)(x & 0xffffu);
+    p -= emit ? 1 : 0;
+    x = emit ? (x >> 16) : x;
+    const uint32_t q = div_by_magic(x, e.ml, e.mh);
+    x += q * (kRansM - e.f) + e.cum;
+}
+
 __global__ void __launch_bounds__(kEncWarps * 32, 1)
     k_rans_encode(const int16_t* __restrict__ r3, int64_t n, int64_t chunks, const uint32_t* __restrict__ freq3,
                   uint16_t* __restrict__ words, uint32_t* __restrict__ counts, int* status) {
@@ -256,72 +287,100 @@ __global__ void __launch_bounds__(kEncWarps * 32, 1)
     if (bad_table && threadIdx.x == 0) atomicOr(status, kStatusRans);
 
     uint16_t* stage = S.stage[warp];
-    uint4* stage4 = reinterpret_cast<uint4*>(stage);
-    constexpr int kVec = kLanes * kCap * 2 / 16;   // uint4 per chunk block
     for (int64_t k = (int64_t)blockIdx.x * kEncWarps + warp; k < chunks; k += (int64_t)gridDim.x * kEncWarps) {
         const int64_t blk = (int64_t)c * chunks + k;
         if (bad_table) {
             counts[blk * kLanes + lane] = 0u;
             continue;
         }
-        for (int i = lane; i < kVec; i += 32) stage4[i] = make_uint4(0u, 0u, 0u, 0u);
-        __syncwarp();
+        // The lanes' streams differ in length by at most one symbol (lane 0's
+        // is the longest): the top step is taken by the lanes that have it,
+        // every step below it by all lanes, without per-step conditions.
         const int len = stream_len(n, k, lane);
-        const int J = __shfl_sync(kFull, len, 0);   // lane 0 has the longest stream
+        const int J = __shfl_sync(kFull, len, 0);
         const int16_t* src = r3 + (int64_t)c * n + k * kChunk + lane;
         uint16_t* st = stage + lane * kCap;
-        uint32_t x = kRansL;
+        uint32_t x = kRansL, fmin = kRansM;
         int p = kCap;
-        bool ok = true;
-        // symbols are loaded one block of 8 ahead of the state chain
-        constexpr int kB = 8;
-        int16_t cur[kB], nxt[kB];
+        if ((k + 1) * kChunk <= n) {
+            // a full chunk: 256 steps per lane in blocks of 32, the symbols of
+            // the next block loaded while the current block runs
+            constexpr int kF = 32;
+            constexpr int kPerLane = kChunk / kLanes;
+            int16_t cur[kF];
 #pragma unroll
-        for (int u = 0; u < kB; ++u) {
-            const int j = J - 1 - u;
-            cur[u] = (j >= 0 && j < len) ? src[(int64_t)kLanes * j] : (int16_t)0;
-        }
-        for (int j0 = J; j0 > 0; j0 -= kB) {
+            for (int u = 0; u < kF; ++u) cur[u] = src[(int64_t)kLanes * (kPerLane - 1 - u)];
+#pragma unroll 1
+            for (int b = 0; b < kPerLane / kF; ++b) {
+                const int jtop = kPerLane - 1 - kF * b;
+                int16_t nxt[kF];
+                const int16_t* sp = src + (int64_t)kLanes * (jtop - kF);
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int j = j0 - kB - 1 - u;
-                nxt[u] = (j >= 0 && j < len) ? src[(int64_t)kLanes * j] : (int16_t)0;
+                for (int u = 0; u < kF; ++u) nxt[u] = b + 1 < kPerLane / kF ? sp[-kLanes * u] : (int16_t)0;
+#pragma unroll
+                for (int u = 0; u < kF; ++u) enc_step(x, p, fmin, st, S.sym, cur[u]);
+#pragma unroll
+                for (int u = 0; u < kF; ++u) cur[u] = nxt[u];
             }
+        } else {
+            // the plane's last, partial chunk
+            if (J > 0 && len == J) enc_step(x, p, fmin, st, S.sym, src[(int64_t)kLanes * (J - 1)]);
+            int j = J - 2;
+            // symbols are loaded one block of 8 steps ahead of the state chain
+            constexpr int kB = 8;
+            if (j >= kB - 1) {
+                int16_t cur[kB];
+                const int16_t* sp = src + (int64_t)kLanes * j;
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                const int j = j0 - 1 - u;
-                if (j >= 0 && j < len && ok) {
-                    const uint32_t s = (uint32_t)((int)cur[u] + 255);
-                    if (s >= (uint32_t)kNres) {
-                        ok = false;
-                    } else {
-                        const EncSym e = S.sym[s];
-                        if (e.f == 0u) {
-                            ok = false;
-                        } else {
-                            if ((x >> 18) >= e.f) {
-                                st[--p] = (uint16_t)(x & 0xffffu);
-                                x >>= 16;
-                            }
-                            const uint32_t q = div_by_magic(x, e.ml, e.mh);
-                            x += q * (kRansM - e.f) + e.cum;
-                        }
-                    }
+                for (int u = 0; u < kB; ++u) cur[u] = sp[-kLanes * u];
+                for (; j >= kB - 1; j -= kB) {
+                    int16_t nxt[kB];
+                    const bool more = j - kB >= kB - 1;
+                    sp = src + (int64_t)kLanes * (j - kB);
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) nxt[u] = more ? sp[-kLanes * u] : (int16_t)0;
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) enc_step(x, p, fmin, st, S.sym, cur[u]);
+#pragma unroll
+                    for (int u = 0; u < kB; ++u) cur[u] = nxt[u];
                 }
             }
+            for (; j >= 0; --j) enc_step(x, p, fmin, st, S.sym, src[(int64_t)kLanes * j]);
+        }
+        // at most one word per symbol and two for the state: p stays >= 0
+        st[--p] = (uint16_t)(x & 0xffffu);
+        st[--p] = (uint16_t)(x >> 16);
+        const bool ok = fmin != 0u;
+        if (!ok) atomicOr(status, kStatusRans);
+        const int used = kCap - p;
+        counts[blk * kLanes + lane] = ok ? (uint32_t)used : 0u;
+        // the streams go to the block packed, stream after stream: the warp
+        // copies one stream at a time (coalesced stores), stream r from the
+        // sum of the word counts of streams 0..r-1
+        int incl = used;
 #pragma unroll
-            for (int u = 0; u < kB; ++u) cur[u] = nxt[u];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
         }
-        if (ok) {
-            st[--p] = (uint16_t)(x & 0xffffu);
-            st[--p] = (uint16_t)(x >> 16);
-        } else {
-            atomicOr(status, kStatusRans);
-        }
-        counts[blk * kLanes + lane] = ok ? (uint32_t)(kCap - p) : 0u;
+        const int off = incl - used;
         __syncwarp();
-        uint4* dst = reinterpret_cast<uint4*>(words + blk * (int64_t)(kLanes * kCap));
-        for (int i = lane; i < kVec; i += 32) dst[i] = stage4[i];
+        // Each stream takes a fixed nine rounds of 32 words (258 at most),
+        // predicated, so the loads of several rounds and streams are in
+        // flight together.
+        uint16_t* dst = words + blk * (int64_t)(kLanes * kCap);
+        constexpr int kRounds = (kCap + 31) / 32;
+#pragma unroll 2
+        for (int r = 0; r < kLanes; ++r) {
+            const int cr = __shfl_sync(kFull, used, r), orr = __shfl_sync(kFull, off, r);
+            const uint16_t* from = stage + r * kCap + (kCap - cr);
+            uint16_t v[kRounds];
+#pragma unroll
+            for (int i = 0; i < kRounds; ++i) v[i] = (32 * i + lane < cr) ? from[32 * i + lane] : (uint16_t)0;
+#pragma unroll
+            for (int i = 0; i < kRounds; ++i)
+                if (32 * i + lane < cr) dst[orr + 32 * i + lane] = v[i];
+        }
         __syncwarp();
     }
 }
@@ -329,19 +388,46 @@ __global__ void __launch_bounds__(kEncWarps * 32, 1)
 // ---------------------------------------------------------------- decoder
 // Slot tables: fb[slot] = f_s << 16 | (slot - c_s) (f_s <= 2^14, slot - c_s
 // < f_s), sym[slot] = s, for the symbol s whose range holds the slot.  The
-// state update reads fb only; the symbol is fetched beside it.
+// state update reads fb only; the symbol is fetched beside it.  Each warp
+// stages its chunk's 32 stream regions (16,512 bytes, contiguous) in shared
+// memory with one bulk copy, so the word reads of the state chain are
+// shared-memory loads; the staging buffers share their space with the scan
+// arrays, which are dead once the slot tables are built.
 constexpr int kDecWarps = 8;
+constexpr uint32_t kBlockBytes = kLanes * kCap * 2;
 
 struct DecSmem {
     uint32_t fb[kRansM];
     uint16_t sym[kRansM];
-    uint32_t fr[512];
-    uint32_t cum[513];
+    unsigned long long bar[kDecWarps];
     int bad_table;
+    __align__(16) union {
+        struct {
+            uint32_t fr[512];
+            uint32_t cum[513];
+        } t;
+        uint16_t stage[kDecWarps][kLanes * kCap];
+    } u;
 };
+static_assert(sizeof(DecSmem) <= 232448, "decoder shared memory exceeds the 227 KB a CTA may use");
 
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+// One decoder step: the symbol of the state's slot, the state update, one
+// word taken when the state falls below L (reads are clamped to the staging
+// buffer: a corrupt stream runs past its words only in p, which is checked
+// at the end).
+__device__ __forceinline__ void dec_step(uint32_t& x, int& p, const uint32_t* fb, const uint16_t* sym,
+                                         const uint16_t* st, int16_t* out) {
+    // the next word is read every step (its address does not depend on x)
+    // and taken only when the state falls below L
+    const uint32_t w = st[min(p, kLanes * kCap - 1)];
+    const uint32_t slot = x & (kRansM - 1u);
+    const uint32_t e = fb[slot];
+    const int s = sym[slot];
+    x = (e >> 16) * (x >> kRansBits) + (e & 0xffffu);
+    const bool take = x < kRansL;
+    x = take ? ((x << 16) | w) : x;
+    p += take ? 1 : 0;
+    *out = (int16_t)(s - 255);
 }
 
 __global__ void __launch_bounds__(kDecWarps * 32, 1)
@@ -350,64 +436,120 @@ __global__ void __launch_bounds__(kDecWarps * 32, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DecSmem& S = *reinterpret_cast<DecSmem*>(smem_raw);
     const int c = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) table_scan(freq3 + c * kNres, S.fr, S.cum, &S.bad_table);
+    if (warp == 0) table_scan(freq3 + c * kNres, S.u.t.fr, S.u.t.cum, &S.bad_table);
+    if (lane == 0) mbar_init(smem_addr(&S.bar[warp]), 1);
     __syncthreads();
     if (S.bad_table) {
         if (threadIdx.x == 0) atomicOr(status, kStatusRans);
         return;
     }
-    // Each thread fills a run of consecutive slots: the symbol of its first
-    // slot is the largest s with cum[s] <= slot (that symbol has f > 0, as
-    // cum[s + 1] > slot), then it walks forward.
-    constexpr int kRun = kRansM / (kDecWarps * 32);
-    static_assert(kRansM % (kDecWarps * 32) == 0, "slot runs must tile the table");
+    // The symbol of each slot: every symbol with f > 0 marks the first slot
+    // of its range (cum[s]) in sym[], and a running maximum over the slots
+    // carries each mark to the end of its range (the marks grow with the
+    // slot).  Warp w takes slots w*2048 .. w*2048+2047, 32 consecutive slots
+    // per step (conflict-free), starting from the symbol of the slot before
+    // its range (the largest s with cum[s] at or below it; that s has f > 0).
+    constexpr int kRange = kRansM / kDecWarps;
+    static_assert(kRansM % (kDecWarps * 32) == 0, "slot ranges must tile the table");
     {
-        const uint32_t first = threadIdx.x * kRun;
-        int lo = 0, hi = kNres - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (S.cum[mid] <= first) lo = mid;
-            else hi = mid - 1;
+        const uint32_t* cum = S.u.t.cum;
+        const uint32_t* fr = S.u.t.fr;
+        uint32_t* sym32 = reinterpret_cast<uint32_t*>(S.sym);
+        for (int i = threadIdx.x; i < kRansM / 2; i += blockDim.x) sym32[i] = 0u;
+        __syncthreads();
+        for (int t = threadIdx.x; t < kNres; t += blockDim.x)
+            if (fr[t]) S.sym[cum[t]] = (uint16_t)t;
+        __syncthreads();
+        uint32_t carry = 0;
+        if (warp > 0) {
+            const uint32_t before = warp * kRange - 1;
+            int lo = 0, hi = kNres - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cum[mid] <= before) lo = mid;
+                else hi = mid - 1;
+            }
+            carry = lo;
         }
-        int s = lo;
-        for (uint32_t slot = first; slot < first + kRun; ++slot) {
-            while (slot >= S.cum[s + 1]) ++s;
-            S.fb[slot] = (S.fr[s] << 16) | (slot - S.cum[s]);
-            S.sym[slot] = (uint16_t)s;
+        // eight rows of 32 slots at a time: their scans are independent, the
+        // carry into each row is the maximum of the carry and the rows before it
+        constexpr int kG = 8;
+        for (int row = 0; row < kRange / 32; row += kG) {
+            uint32_t v[kG];
+#pragma unroll
+            for (int u = 0; u < kG; ++u) v[u] = S.sym[warp * kRange + (row + u) * 32 + lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int u = 0; u < kG; ++u) v[u] = max(v[u], __shfl_up_sync(kFull, v[u], o));
+            }
+            uint32_t top[kG];
+#pragma unroll
+            for (int u = 0; u < kG; ++u) top[u] = __shfl_sync(kFull, v[u], 31);
+#pragma unroll
+            for (int u = 0; u < kG; ++u) {
+                const uint32_t sv = max(v[u], carry);
+                carry = max(carry, top[u]);
+                const uint32_t slot = warp * kRange + (row + u) * 32 + lane;
+                S.fb[slot] = (fr[sv] << 16) | (slot - cum[sv]);
+                S.sym[slot] = (uint16_t)sv;
+            }
         }
     }
-    __syncthreads();
+    __syncthreads();   // the scan arrays are dead from here: the staging buffers reuse them
 
+    const uint32_t bar = smem_addr(&S.bar[warp]);
+    const uint32_t stage_addr = smem_addr(S.u.stage[warp]);
+    uint32_t phase = 0;
     for (int64_t k = (int64_t)blockIdx.x * kDecWarps + warp; k < chunks; k += (int64_t)gridDim.x * kDecWarps) {
         const int64_t blk = (int64_t)c * chunks + k;
-        const int len = stream_len(n, k, lane);
         const uint32_t cnt = counts[blk * kLanes + lane];
-        const uint16_t* reg = words + (blk * kLanes + lane) * (int64_t)kCap;
+        // stream offsets in the packed block; a count outside 2..258 (or a
+        // sum beyond the block) is reported, and the whole block is copied
+        const bool cnt_ok = cnt >= 2u && cnt <= (uint32_t)kCap;
+        uint32_t incl = cnt_ok ? cnt : 2u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        const bool ok = __all_sync(kFull, cnt_ok);
+        const uint32_t off = incl - (cnt_ok ? cnt : 2u);
+        const uint32_t bytes = ok ? ((total * 2u + 15u) & ~15u) : kBlockBytes;
+        if (lane == 0) {
+            fence_async_shared();   // earlier generic accesses of the buffer before the copy overwrites it
+            mbar_arrive_expect_tx(bar, bytes);
+            tma_load_1d(stage_addr, words + blk * (int64_t)(kLanes * kCap), bytes, bar);
+        }
+        const int len = stream_len(n, k, lane);
         int16_t* dst = r3 + (int64_t)c * n + k * kChunk + lane;
-        bool ok = cnt >= 2u && cnt <= (uint32_t)kCap;
-        int p = kCap - (ok ? (int)cnt : 2);
-        uint32_t x = kRansL;
-        if (ok) {
-            for (int q = (p & ~63); q < kCap; q += 64) prefetch_l1(reg + q);
-            x = ((uint32_t)__ldg(reg + p) << 16) | __ldg(reg + p + 1);
-            p += 2;
+        if (!mbar_wait(bar, phase, status)) {
+            // the copy did not land within the bound: wait once more (bounded)
+            // so that no copy is left in flight, then stop
+            mbar_wait(bar, phase, status);
+            return;
         }
-        for (int j = 0; j < len; ++j) {
-            int16_t v = 0;
-            if (ok) {
-                const uint32_t slot = x & (kRansM - 1u);
-                const uint32_t e = S.fb[slot];
-                v = (int16_t)((int)S.sym[slot] - 255);
-                x = (e >> 16) * (x >> kRansBits) + (e & 0xffffu);
-                if (x < kRansL) {
-                    if (p < kCap) x = (x << 16) | __ldg(reg + p++);
-                    else ok = false;
-                }
-            }
-            dst[(int64_t)kLanes * j] = v;
+        phase ^= 1u;
+        // every read is clamped to the buffer (a corrupt count or stream only
+        // decodes garbage, reported below)
+        const uint16_t* sw = S.u.stage[warp];
+        const uint32_t base = min(off, (uint32_t)(kLanes * kCap - 2));
+        uint32_t x = ((uint32_t)sw[base] << 16) | sw[base + 1];
+        int p = (int)base + 2;
+        // steps 0 .. J-2 for every lane, step J-1 for the lanes that have it
+        const int J = __shfl_sync(kFull, len, 0);
+        int j = 0;
+        for (; j + 4 <= J - 1; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dec_step(x, p, S.fb, S.sym, sw, dst + (int64_t)kLanes * (j + u));
         }
+        for (; j < J - 1; ++j) dec_step(x, p, S.fb, S.sym, sw, dst + (int64_t)kLanes * j);
+        if (J > 0 && len == J) dec_step(x, p, S.fb, S.sym, sw, dst + (int64_t)kLanes * (J - 1));
         // the decoder ends in the encoder's initial state with every word read
-        if (!ok || p != kCap || x != kRansL) atomicOr(status, kStatusRans);
+        if (!ok || total > (uint32_t)(kLanes * kCap) || p != (int)(off + cnt) || x != kRansL)
+            atomicOr(status, kStatusRans);
+        __syncwarp();   // every lane is done with the buffer before the next copy
     }
 }
 
@@ -417,11 +559,19 @@ int grid_x(int64_t chunks, int warps) {
     return (int)std::min<int64_t>(need, cap);
 }
 
-int set_smem(const void* fn, size_t bytes, const char* what) {
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-        return cuda_status(what);
+// Raises the kernel's dynamic shared-memory limit once per device.
+int set_smem(const void* fn, size_t bytes, bool* done, const char* what) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status(what);
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+            return cuda_status(what);
+        done[dev] = true;
+    }
     return SLRME_OK;
 }
+
+bool g_enc_attr[64], g_dec_attr[64];
 
 bool aligned(const void* p, size_t a) {
     return ((uintptr_t)p % a) == 0;
@@ -474,7 +624,7 @@ extern "C" int rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, 
     int* status = nullptr;
     if ((rc = status_word_address(&status))) return rc;
     const size_t smem = sizeof(EncSmem);
-    if ((rc = set_smem((const void*)k_rans_encode, smem, "rans_encode smem"))) return rc;
+    if ((rc = set_smem((const void*)k_rans_encode, smem, g_enc_attr, "rans_encode smem"))) return rc;
     const int64_t chunks = (n + kChunk - 1) / kChunk;
     const dim3 grid(grid_x(chunks, kEncWarps), 3);
     k_rans_encode<<<grid, kEncWarps * 32, smem, (cudaStream_t)stream>>>(r3, n, chunks, freq3, words, counts, status);
@@ -487,15 +637,15 @@ extern "C" int rans_decode(const uint16_t* words, const uint32_t* counts, int64_
     int rc = check_n("rans_decode", n);
     if (rc) return rc;
     if (n == 0) return SLRME_OK;
-    if (!r3 || !freq3 || !words || !counts || !aligned(r3, 2) || !aligned(freq3, 4) || !aligned(words, 2) ||
+    if (!r3 || !freq3 || !words || !counts || !aligned(r3, 2) || !aligned(freq3, 4) || !aligned(words, 16) ||
         !aligned(counts, 4)) {
-        set_error("rans_decode: null or misaligned pointer (words 2, counts 4, freq3 4, r3 2 bytes)");
+        set_error("rans_decode: null or misaligned pointer (words 16, counts 4, freq3 4, r3 2 bytes)");
         return SLRME_EINVAL;
     }
     int* status = nullptr;
     if ((rc = status_word_address(&status))) return rc;
     const size_t smem = sizeof(DecSmem);
-    if ((rc = set_smem((const void*)k_rans_decode, smem, "rans_decode smem"))) return rc;
+    if ((rc = set_smem((const void*)k_rans_decode, smem, g_dec_attr, "rans_decode smem"))) return rc;
     const int64_t chunks = (n + kChunk - 1) / kChunk;
     const dim3 grid(grid_x(chunks, kDecWarps), 3);
     k_rans_decode<<<grid, kDecWarps * 32, smem, (cudaStream_t)stream>>>(words, counts, n, chunks, freq3, r3, status);

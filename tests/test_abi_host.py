@@ -149,6 +149,7 @@ def test_rans_bad_arguments_rejected_before_any_gpu_work():
     assert L.rans_encode(64, -1, 64, 64, 64, None) == EINVAL
     assert L.rans_encode(64, 1 << 31, 64, 64, 64, None) == EINVAL
     assert L.rans_decode(64, 66, 10, 64, 64, None) == EINVAL          # counts not 4-byte aligned
+    assert L.rans_decode(72, 64, 10, 64, 64, None) == EINVAL          # words not 16-byte aligned
     assert L.rans_decode(64, 64, 10, 64, None, None) == EINVAL
     assert "rans_decode" in native.last_error()
     assert L.rans_encode(None, 0, None, None, None, None) == 0        # empty planes: nothing to do

@@ -61,6 +61,10 @@ def test_single_symbol_costs_nothing():
     assert (f3[:, 251] == M).all() and (f3.sum(1) == M).all()
     w, cn = O.rans_encode(r3, f3)
     assert (cn == 2).all()                       # only the final states
+    # the state never leaves L = 2^16: every stream is the word pair (1, 0),
+    # packed stream after stream from the start of its chunk's block
+    blocks = w.reshape(-1, 32 * 258)
+    assert (blocks[:, :64] == np.tile([1, 0], 32)).all() and (blocks[:, 64:] == 0).all()
     assert np.array_equal(O.rans_decode(w, cn, n, f3), r3)
 
 
