@@ -51,6 +51,14 @@ def lib():
                                                 ctypes.c_void_p]
             _lib.oracle_rans_decode.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                                 ctypes.c_void_p]
+            _lib.oracle_rans_encode_segments.restype = ctypes.c_int
+            _lib.oracle_rans_encode_segments.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            _lib.oracle_rans_decode_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            _lib.oracle_dwt53_bands.restype = ctypes.c_int
+            _lib.oracle_dwt53_forward.restype = ctypes.c_int
+            _lib.oracle_dwt53_inverse.restype = ctypes.c_int
     return _lib
 
 
@@ -286,4 +294,87 @@ def rans_decode(words: np.ndarray, counts: np.ndarray, n: int, freq3: np.ndarray
     f = np.ascontiguousarray(freq3, dtype=np.uint32).reshape(3 * NRES)
     lib().oracle_rans_decode(_p(np.ascontiguousarray(words, dtype=np.uint16)),
                              _p(np.ascontiguousarray(counts, dtype=np.uint32)), n, _p(f), _p(out))
+    return out
+
+
+RANS_RAW = 0xFFFFFFFF
+
+
+def rans_segment_layout(lengths):
+    """Chunks per segment and the words / counts sizes of a run of segments."""
+    chunks = [(int(n) + RANS_CHUNK - 1) // RANS_CHUNK for n in lengths]
+    total = sum(chunks)
+    return chunks, total * RANS_LANES * RANS_CAP, total * RANS_LANES
+
+
+def rans_encode_segments(sym: np.ndarray, lengths, freq: np.ndarray):
+    """Words and counts of a run of segments (segment g: `lengths[g]` symbols, table freq[g]);
+    chunks with a value outside -255..255 are stored raw."""
+    v = np.ascontiguousarray(sym, dtype=np.int16).reshape(-1)
+    ln = np.ascontiguousarray(lengths, dtype=np.int64)
+    assert v.size == int(ln.sum())
+    _, nw, nc = rans_segment_layout(ln)
+    words = np.zeros(nw, np.uint16)
+    counts = np.zeros(nc, np.uint32)
+    f = np.ascontiguousarray(freq, dtype=np.uint32).reshape(-1)
+    assert f.size == NRES * ln.size
+    rc = lib().oracle_rans_encode_segments(_p(v), int(ln.size), _p(ln), _p(f), _p(words), _p(counts))
+    if rc != 0:
+        raise ValueError("a value has a zero frequency in its segment's table")
+    return words, counts
+
+
+def rans_decode_segments(words: np.ndarray, counts: np.ndarray, lengths, freq: np.ndarray) -> np.ndarray:
+    ln = np.ascontiguousarray(lengths, dtype=np.int64)
+    out = np.zeros(int(ln.sum()), np.int16)
+    f = np.ascontiguousarray(freq, dtype=np.uint32).reshape(-1)
+    lib().oracle_rans_decode_segments(_p(np.ascontiguousarray(words, dtype=np.uint16)),
+                                      _p(np.ascontiguousarray(counts, dtype=np.uint32)), int(ln.size), _p(ln),
+                                      _p(f), _p(out))
+    return out
+
+
+def segment_hist(sym: np.ndarray, lengths) -> np.ndarray:
+    """Histogram (511 bins, value + 255) of the values inside -255..255 of each segment."""
+    v = np.asarray(sym, dtype=np.int64).reshape(-1)
+    out, at = [], 0
+    for n in lengths:
+        seg = v[at:at + int(n)]
+        seg = seg[(seg >= -255) & (seg <= 255)] + 255
+        out.append(np.bincount(seg, minlength=NRES))
+        at += int(n)
+    return np.array(out, dtype=np.uint32).reshape(len(out), NRES)
+
+
+DWT_MAX_LEVELS = 3
+
+
+def dwt53_bands(h: int, w: int, levels: int):
+    """(rows, columns) of each band in output order: LL_L, then HL, LH, HH from level L down to 1."""
+    dims = np.zeros(2 * (1 + 3 * DWT_MAX_LEVELS), np.int32)
+    nb = lib().oracle_dwt53_bands(ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(levels), _p(dims))
+    return [(int(dims[2 * b]), int(dims[2 * b + 1])) for b in range(nb)]
+
+
+def dwt53_forward(planes: np.ndarray, levels: int) -> np.ndarray:
+    """Reversible 5/3 transform of each plane ([P][h][w] int16) into its subband-major order ([P][h*w])."""
+    x = np.ascontiguousarray(planes, dtype=np.int16)
+    P, h, w = x.shape
+    out = np.zeros((P, h * w), np.int16)
+    for c in range(P):
+        rc = lib().oracle_dwt53_forward(_p(x[c]), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(levels),
+                                        _p(out[c]))
+        if rc != 0:
+            raise ValueError("levels must be in 0..3")
+    return out
+
+
+def dwt53_inverse(coef: np.ndarray, h: int, w: int, levels: int) -> np.ndarray:
+    cf = np.ascontiguousarray(coef, dtype=np.int16).reshape(-1, h * w)
+    out = np.zeros((cf.shape[0], h, w), np.int16)
+    for c in range(cf.shape[0]):
+        rc = lib().oracle_dwt53_inverse(_p(cf[c]), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(levels),
+                                        _p(out[c]))
+        if rc != 0:
+            raise ValueError("levels must be in 0..3")
     return out

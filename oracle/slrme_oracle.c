@@ -614,76 +614,310 @@ static int64_t rans_stream_len(int64_t n, int64_t k, int l)
     return first < end ? (end - 1 - first) / RANS_LANES + 1 : 0;
 }
 
-/* Encodes the three residual planes (int16 [3][n]) with the channels'
- * tables freq3 ([3][511]).  words: [3][chunks] blocks of 32 x 258 uint16, counts:
- * [3][chunks][32]; chunks = ceil(n / 8192).  Returns 0, or -1 when a
- * residual has a zero frequency (the table does not cover the data). */
-int oracle_rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts)
+/* Segments: the symbol array is a run of segments, each with its own table
+ * (freq[g * 511 ...]) and cut into its own chunks; segment g's chunks follow
+ * those of segments 0..g-1 in `words` and `counts`.  A chunk holding a value
+ * outside -255..255 is stored raw: its block holds the chunk's values (the
+ * int16 bit patterns, in order) and all 32 of its counts are RANS_RAW. */
+#define RANS_RAW 0xFFFFFFFFu
+
+static int64_t rans_chunks(int64_t len) { return (len + RANS_CHUNK - 1) / RANS_CHUNK; }
+
+/* Returns 0, or -1 when a value inside -255..255 has a zero frequency. */
+int oracle_rans_encode_segments(const int16_t* sym, int nseg, const int64_t* len, const uint32_t* freq,
+                                uint16_t* words, uint32_t* counts)
 {
-    int64_t chunks = (n + RANS_CHUNK - 1) / RANS_CHUNK;
-    for (int c = 0; c < 3; ++c) {
-        const uint32_t* freq = freq3 + c * NRES;
+    int64_t sym_at = 0, chunk_at = 0;
+    for (int g = 0; g < nseg; ++g) {
+        const uint32_t* f = freq + (int64_t)g * NRES;
         uint32_t cum[NRES];
-        rans_cum(freq, cum);
+        rans_cum(f, cum);
+        int64_t chunks = rans_chunks(len[g]);
         for (int64_t k = 0; k < chunks; ++k) {
-            uint16_t* block = words + (c * chunks + k) * RANS_LANES * RANS_CAP;
+            const int16_t* src = sym + sym_at + k * RANS_CHUNK;
+            int64_t m = len[g] - k * RANS_CHUNK < RANS_CHUNK ? len[g] - k * RANS_CHUNK : RANS_CHUNK;
+            uint16_t* block = words + (chunk_at + k) * RANS_LANES * RANS_CAP;
+            uint32_t* cnt = counts + (chunk_at + k) * RANS_LANES;
+            int raw = 0;
+            for (int64_t i = 0; i < m; ++i)
+                if (src[i] < -255 || src[i] > 255) raw = 1;
+            if (raw) {
+                for (int64_t i = 0; i < m; ++i) block[i] = (uint16_t)src[i];
+                for (int l = 0; l < RANS_LANES; ++l) cnt[l] = RANS_RAW;
+                continue;
+            }
             int64_t at = 0;   /* where the next stream starts in the block */
             for (int l = 0; l < RANS_LANES; ++l) {
                 /* the words are produced last-first: build them at the end of
                  * a scratch region, then copy them to the block */
                 uint16_t region[RANS_CAP];
-                int64_t len = rans_stream_len(n, k, l);
+                int64_t slen = rans_stream_len(m, 0, l);
                 uint32_t x = RANS_L;
                 int p = RANS_CAP;
-                for (int64_t j = len - 1; j >= 0; --j) {
-                    int s = r3[c * n + k * RANS_CHUNK + l + RANS_LANES * j] + 255;
-                    uint32_t f = freq[s];
-                    if (f == 0) return -1;
-                    if ((x >> 18) >= f) {
+                for (int64_t j = slen - 1; j >= 0; --j) {
+                    int s = src[l + RANS_LANES * j] + 255;
+                    uint32_t fs = f[s];
+                    if (fs == 0) return -1;
+                    if ((x >> 18) >= fs) {
                         region[--p] = (uint16_t)(x & 0xFFFFu);
                         x >>= 16;
                     }
-                    x = (x / f) * RANS_M + (x % f) + cum[s];
+                    x = (x / fs) * RANS_M + (x % fs) + cum[s];
                 }
                 region[--p] = (uint16_t)(x & 0xFFFFu);
                 region[--p] = (uint16_t)(x >> 16);
                 int used = RANS_CAP - p;
                 memcpy(block + at, region + p, (size_t)used * sizeof(uint16_t));
                 at += used;
-                counts[(c * chunks + k) * RANS_LANES + l] = (uint32_t)used;
+                cnt[l] = (uint32_t)used;
             }
         }
+        sym_at += len[g];
+        chunk_at += chunks;
     }
     return 0;
 }
 
-/* Decodes what oracle_rans_encode wrote back into the residual planes. */
-void oracle_rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3,
-                        int16_t* r3)
+/* Decodes what oracle_rans_encode_segments wrote. */
+void oracle_rans_decode_segments(const uint16_t* words, const uint32_t* counts, int nseg, const int64_t* len,
+                                 const uint32_t* freq, int16_t* sym)
 {
-    int64_t chunks = (n + RANS_CHUNK - 1) / RANS_CHUNK;
-    for (int c = 0; c < 3; ++c) {
-        const uint32_t* freq = freq3 + c * NRES;
+    int64_t sym_at = 0, chunk_at = 0;
+    for (int g = 0; g < nseg; ++g) {
+        const uint32_t* f = freq + (int64_t)g * NRES;
         uint32_t cum[NRES];
-        rans_cum(freq, cum);
+        rans_cum(f, cum);
+        int64_t chunks = rans_chunks(len[g]);
         for (int64_t k = 0; k < chunks; ++k) {
-            const uint16_t* block = words + (c * chunks + k) * RANS_LANES * RANS_CAP;
+            int16_t* dst = sym + sym_at + k * RANS_CHUNK;
+            int64_t m = len[g] - k * RANS_CHUNK < RANS_CHUNK ? len[g] - k * RANS_CHUNK : RANS_CHUNK;
+            const uint16_t* block = words + (chunk_at + k) * RANS_LANES * RANS_CAP;
+            const uint32_t* cnt = counts + (chunk_at + k) * RANS_LANES;
+            if (cnt[0] == RANS_RAW) {
+                for (int64_t i = 0; i < m; ++i) dst[i] = (int16_t)block[i];
+                continue;
+            }
             int64_t at = 0;
             for (int l = 0; l < RANS_LANES; ++l) {
                 const uint16_t* stream = block + at;
-                at += counts[(c * chunks + k) * RANS_LANES + l];
-                int64_t len = rans_stream_len(n, k, l);
+                at += cnt[l];
+                int64_t slen = rans_stream_len(m, 0, l);
                 uint32_t x = ((uint32_t)stream[0] << 16) | stream[1];
                 int p = 2;
-                for (int64_t j = 0; j < len; ++j) {
+                for (int64_t j = 0; j < slen; ++j) {
                     uint32_t slot = x & (RANS_M - 1);
                     int s = 0;
-                    while (!(cum[s] <= slot && slot < cum[s] + freq[s])) ++s;
-                    x = freq[s] * (x >> RANS_BITS) + slot - cum[s];
+                    while (!(cum[s] <= slot && slot < cum[s] + f[s])) ++s;
+                    x = f[s] * (x >> RANS_BITS) + slot - cum[s];
                     if (x < RANS_L) x = (x << 16) | stream[p++];
-                    r3[c * n + k * RANS_CHUNK + l + RANS_LANES * j] = (int16_t)(s - 255);
+                    dst[l + RANS_LANES * j] = (int16_t)(s - 255);
                 }
             }
         }
+        sym_at += len[g];
+        chunk_at += chunks;
     }
+}
+
+/* The three residual planes (int16 [3][n]) as three segments of n symbols
+ * with the channels' tables freq3 ([3][511]).  words: [3][chunks] blocks of
+ * 32 x 258 uint16, counts: [3][chunks][32]; chunks = ceil(n / 8192). */
+int oracle_rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts)
+{
+    const int64_t len[3] = {n, n, n};
+    return oracle_rans_encode_segments(r3, 3, len, freq3, words, counts);
+}
+
+void oracle_rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3,
+                        int16_t* r3)
+{
+    const int64_t len[3] = {n, n, n};
+    oracle_rans_decode_segments(words, counts, 3, len, freq3, r3);
+}
+
+/* ------------------------------------------------------------------ reversible 5/3 wavelet
+ * The enhancement layer of Sec. IV is coded by JPEG 2000's lossless mode,
+ * whose transform is the reversible LeGall 5/3 wavelet: integer lifting with
+ * whole-sample symmetric extension (x[-k] = x[k], x[n-1+k] = x[n-1-k]).
+ * For n >= 2 samples, nH = floor(n / 2) high-pass and nL = ceil(n / 2)
+ * low-pass values:
+ *   d[i] = x[2i+1] - floor((x[2i] + x[2i+2]) / 2),        i < nH
+ *   s[i] = x[2i]   + floor((d[i-1] + d[i] + 2) / 4),       i < nL
+ * where the extension gives x[n] = x[n-2], d[-1] = d[0] and, for odd n,
+ * d[nL-1] = d[nL-2].  A single sample is its own low-pass value.  The
+ * inverse runs the two steps backwards.  One 2-D level transforms every row,
+ * then every column of the row-transformed array; the next level transforms
+ * the low-low band.  Each pass at most doubles the largest magnitude, so
+ * three levels of residuals in -255..255 stay within +-16320 (int16).
+ * Output order per plane (subband-major, each band row-major):
+ *   LL_L, HL_L, LH_L, HH_L, HL_(L-1), LH_(L-1), HH_(L-1), ..., HL_1, LH_1, HH_1
+ * with HL high-pass along rows (columns nL..n-1 of a row), LH along columns. */
+
+#define DWT_MAX_LEVELS 3
+
+static int64_t floor_div2(int64_t a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+static int64_t floor_div4(int64_t a) { return a >= 0 ? a / 4 : -((-a + 3) / 4); }
+
+/* one 1-D forward step over n samples read with stride `step`: low-pass
+ * values to lo[0..nL), high-pass to hi[0..nH) */
+static void dwt53_fwd_1d(const int32_t* x, int n, int step, int32_t* lo, int32_t* hi)
+{
+    if (n == 1) {
+        lo[0] = x[0];
+        return;
+    }
+    int nH = n / 2, nL = n - nH;
+    for (int i = 0; i < nH; ++i) {
+        int64_t left = x[(2 * i) * step];
+        int64_t right = (2 * i + 2 <= n - 1) ? x[(2 * i + 2) * step] : x[(2 * i) * step];
+        hi[i] = (int32_t)(x[(2 * i + 1) * step] - floor_div2(left + right));
+    }
+    for (int i = 0; i < nL; ++i) {
+        int64_t dl = hi[i >= 1 ? i - 1 : 0];
+        int64_t dr = hi[i < nH ? i : nH - 1];
+        lo[i] = (int32_t)(x[(2 * i) * step] + floor_div4(dl + dr + 2));
+    }
+}
+
+static void dwt53_inv_1d(const int32_t* lo, const int32_t* hi, int n, int32_t* x, int step)
+{
+    if (n == 1) {
+        x[0] = lo[0];
+        return;
+    }
+    int nH = n / 2, nL = n - nH;
+    for (int i = 0; i < nL; ++i) {
+        int64_t dl = hi[i >= 1 ? i - 1 : 0];
+        int64_t dr = hi[i < nH ? i : nH - 1];
+        x[(2 * i) * step] = (int32_t)(lo[i] - floor_div4(dl + dr + 2));
+    }
+    for (int i = 0; i < nH; ++i) {
+        int64_t left = x[(2 * i) * step];
+        int64_t right = (2 * i + 2 <= n - 1) ? x[(2 * i + 2) * step] : x[(2 * i) * step];
+        x[(2 * i + 1) * step] = (int32_t)(hi[i] + floor_div2(left + right));
+    }
+}
+
+/* Band sizes in output order: dims[2 b] = rows, dims[2 b + 1] = columns of
+ * band b; returns the number of bands (1 + 3 levels). */
+int oracle_dwt53_bands(int h, int w, int levels, int32_t* dims)
+{
+    int hs[DWT_MAX_LEVELS + 1], ws[DWT_MAX_LEVELS + 1];
+    hs[0] = h;
+    ws[0] = w;
+    for (int l = 1; l <= levels; ++l) {
+        hs[l] = (hs[l - 1] + 1) / 2;
+        ws[l] = (ws[l - 1] + 1) / 2;
+    }
+    int b = 0;
+    dims[2 * b] = hs[levels];
+    dims[2 * b + 1] = ws[levels];
+    ++b;
+    for (int l = levels; l >= 1; --l) {
+        int H = hs[l - 1], W = ws[l - 1];
+        int HL = (H + 1) / 2, HH = H / 2, WL = (W + 1) / 2, WH = W / 2;
+        dims[2 * b] = HL; dims[2 * b + 1] = WH; ++b;   /* HL: rows low, columns high */
+        dims[2 * b] = HH; dims[2 * b + 1] = WL; ++b;   /* LH */
+        dims[2 * b] = HH; dims[2 * b + 1] = WH; ++b;   /* HH */
+    }
+    return b;
+}
+
+/* Forward transform of one plane (h x w, row-major) into the subband-major
+ * order above.  0 on success, -1 for levels outside 0..3. */
+int oracle_dwt53_forward(const int16_t* r, int h, int w, int levels, int16_t* coef)
+{
+    if (levels < 0 || levels > DWT_MAX_LEVELS) return -1;
+    int64_t n = (int64_t)h * w;
+    if (n == 0) return 0;
+    int32_t* cur = malloc(sizeof(int32_t) * n);     /* the band being split, H x W */
+    int32_t* tmp = malloc(sizeof(int32_t) * n);
+    int32_t* col = malloc(sizeof(int32_t) * (h > w ? h : w) * 2);
+    for (int64_t i = 0; i < n; ++i) cur[i] = r[i];
+    int32_t dims[2 * (1 + 3 * DWT_MAX_LEVELS)];
+    int nb = oracle_dwt53_bands(h, w, levels, dims);
+    /* band offsets in output order */
+    int64_t off[1 + 3 * DWT_MAX_LEVELS];
+    int64_t at = 0;
+    for (int b = 0; b < nb; ++b) {
+        off[b] = at;
+        at += (int64_t)dims[2 * b] * dims[2 * b + 1];
+    }
+    int H = h, W = w;
+    for (int l = 1; l <= levels; ++l) {
+        int WL = (W + 1) / 2, WH = W / 2, HL = (H + 1) / 2, HH = H / 2;
+        /* rows: tmp[y][0..WL) low, tmp[y][WL..W) high */
+        for (int y = 0; y < H; ++y) dwt53_fwd_1d(cur + (int64_t)y * W, W, 1, tmp + (int64_t)y * W, tmp + (int64_t)y * W + WL);
+        /* columns */
+        int bHL = 1 + 3 * (levels - l), bLH = bHL + 1, bHH = bHL + 2;
+        for (int x = 0; x < W; ++x) {
+            int32_t* lo = col;
+            int32_t* hi = col + H;
+            dwt53_fwd_1d(tmp + x, H, W, lo, hi);
+            for (int y = 0; y < HL; ++y) {
+                if (x < WL) cur[(int64_t)y * WL + x] = lo[y];           /* next level's input, HL x WL */
+                else coef[off[bHL] + (int64_t)y * WH + (x - WL)] = (int16_t)lo[y];
+            }
+            for (int y = 0; y < HH; ++y) {
+                if (x < WL) coef[off[bLH] + (int64_t)y * WL + x] = (int16_t)hi[y];
+                else coef[off[bHH] + (int64_t)y * WH + (x - WL)] = (int16_t)hi[y];
+            }
+        }
+        H = HL;
+        W = WL;
+    }
+    for (int64_t i = 0; i < (int64_t)H * W; ++i) coef[i] = (int16_t)cur[i];   /* LL_L (band 0 at offset 0) */
+    free(cur);
+    free(tmp);
+    free(col);
+    return 0;
+}
+
+/* Inverse of oracle_dwt53_forward. */
+int oracle_dwt53_inverse(const int16_t* coef, int h, int w, int levels, int16_t* r)
+{
+    if (levels < 0 || levels > DWT_MAX_LEVELS) return -1;
+    int64_t n = (int64_t)h * w;
+    if (n == 0) return 0;
+    int32_t dims[2 * (1 + 3 * DWT_MAX_LEVELS)];
+    int nb = oracle_dwt53_bands(h, w, levels, dims);
+    int64_t off[1 + 3 * DWT_MAX_LEVELS];
+    int64_t at = 0;
+    for (int b = 0; b < nb; ++b) {
+        off[b] = at;
+        at += (int64_t)dims[2 * b] * dims[2 * b + 1];
+    }
+    int hs[DWT_MAX_LEVELS + 1], ws[DWT_MAX_LEVELS + 1];
+    hs[0] = h;
+    ws[0] = w;
+    for (int l = 1; l <= levels; ++l) {
+        hs[l] = (hs[l - 1] + 1) / 2;
+        ws[l] = (ws[l - 1] + 1) / 2;
+    }
+    int32_t* cur = malloc(sizeof(int32_t) * n);
+    int32_t* tmp = malloc(sizeof(int32_t) * n);
+    int32_t* col = malloc(sizeof(int32_t) * (h > w ? h : w) * 2);
+    for (int64_t i = 0; i < (int64_t)hs[levels] * ws[levels]; ++i) cur[i] = coef[i];
+    for (int l = levels; l >= 1; --l) {
+        int H = hs[l - 1], W = ws[l - 1];
+        int WL = (W + 1) / 2, WH = W / 2, HL = (H + 1) / 2, HH = H / 2;
+        int bHL = 1 + 3 * (levels - l), bLH = bHL + 1, bHH = bHL + 2;
+        /* columns back into tmp (H x W, row-transformed layout) */
+        for (int x = 0; x < W; ++x) {
+            int32_t* lo = col;
+            int32_t* hi = col + H;
+            for (int y = 0; y < HL; ++y)
+                lo[y] = x < WL ? cur[(int64_t)y * WL + x] : coef[off[bHL] + (int64_t)y * WH + (x - WL)];
+            for (int y = 0; y < HH; ++y)
+                hi[y] = x < WL ? coef[off[bLH] + (int64_t)y * WL + x] : coef[off[bHH] + (int64_t)y * WH + (x - WL)];
+            dwt53_inv_1d(lo, hi, H, tmp + x, W);
+        }
+        /* rows back into cur (H x W) */
+        for (int y = 0; y < H; ++y) dwt53_inv_1d(tmp + (int64_t)y * W, tmp + (int64_t)y * W + WL, W, cur + (int64_t)y * W, 1);
+    }
+    for (int64_t i = 0; i < n; ++i) r[i] = (int16_t)cur[i];
+    free(cur);
+    free(tmp);
+    free(col);
+    return 0;
 }
