@@ -180,8 +180,8 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
  * words).  rans_encode writes nothing else of a block.
  * counts[(c*chunks + k)*32 + l] (uint32) is the number of words the stream
  * used (2..258, or 0 for a stream that could not be coded).
- * Errors found while a kernel runs (a residual outside -255..255 or with a
- * zero frequency, a table whose entries exceed M or do not sum to M, a stream
+ * Errors found while a kernel runs (a value inside -255..255 with a zero
+ * frequency, a table whose entries exceed M or do not sum to M, a stream
  * whose words do not decode back to the initial state) set bit 1 (value 2) of
  * the device status word (slrme_device_status); the affected outputs are then
  * unspecified but every access stays inside the documented buffers. */
@@ -218,6 +218,69 @@ int rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* w
  * stops. */
 int rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3, int16_t* r3,
                 slrme_stream_t stream);
+
+/* Segments: a run of symbol arrays coded each with its own table, for the
+ * wavelet coefficients below (one segment per plane and band).  The symbols
+ * of segment g follow those of segments 0..g-1 in `sym`; freq holds one
+ * table of 511 entries per segment (from rans_tables_n); segment g is cut
+ * into ceil(len[g] / 8192) chunks whose blocks and counts follow those of
+ * the segments before it.  A chunk holding a value outside -255..255 is
+ * stored raw: its block holds the chunk's values (int16 bit patterns, in
+ * order) and all 32 of its counts are SLRME_RANS_RAW.  The three-plane
+ * calls above are this form with three segments of n symbols (a residual
+ * outside -255..255 makes its chunk raw).  1 <= nseg <= SLRME_RANS_MAX_SEGMENTS,
+ * len (host array) >= 0, total symbols < 2^31. */
+#define SLRME_RANS_MAX_SEGMENTS 64
+#define SLRME_RANS_RAW          0xFFFFFFFFu
+
+/* Host: uint16 words and uint32 counts of a run of segments (0 on bad arguments). */
+int64_t rans_segments_words_capacity(int nseg, const int64_t* len);
+int64_t rans_segments_counts_capacity(int nseg, const int64_t* len);
+
+/* rans_tables for `ntables` histograms (uint32 [ntables][511]) -> freq
+ * (uint32 [ntables][511]); 1 <= ntables <= 65535. */
+int rans_tables_n(const uint32_t* hist, int ntables, uint32_t* freq, slrme_stream_t stream);
+
+int rans_encode_segments(const int16_t* sym, int nseg, const int64_t* len, const uint32_t* freq, uint16_t* words,
+                         uint32_t* counts, slrme_stream_t stream);
+int rans_decode_segments(const uint16_t* words, const uint32_t* counts, int nseg, const int64_t* len,
+                         const uint32_t* freq, int16_t* sym, slrme_stream_t stream);
+
+/* ===================================================================== reversible 5/3 wavelet
+ * The transform of JPEG 2000's lossless mode, which codes the enhancement
+ * layer in Sec. IV: integer lifting with whole-sample symmetric extension.
+ * For a row or column of n >= 2 samples (nH = floor(n/2), nL = ceil(n/2)):
+ *   d[i] = x[2i+1] - floor((x[2i] + x[2i+2]) / 2),   i < nH   (x[n] = x[n-2])
+ *   s[i] = x[2i]   + floor((d[i-1] + d[i] + 2) / 4), i < nL   (d[-1] = d[0];
+ *                                                  odd n: d[nL-1] = d[nL-2])
+ * and a single sample is its own low-pass value.  One level transforms the
+ * rows, then the columns; level l + 1 transforms level l's low-low band.
+ * Output per plane, subband-major, each band row-major: LL_L, then HL, LH,
+ * HH of level L, ..., of level 1 (HL: high-pass along the rows, low along
+ * the columns; LH the reverse), 1 + 3L bands.  Each pass at most doubles the
+ * largest magnitude: inputs in -255..255 stay within +-16320 at L = 3. */
+#define SLRME_DWT_MAX_LEVELS 3
+
+/* Host: band sizes in output order, dims[2b] rows and dims[2b+1] columns of
+ * band b; returns the number of bands (1 + 3 levels) or SLRME_EINVAL. */
+int dwt53_bands(int h, int w, int levels, int32_t* dims);
+
+/* Device workspace bytes for nplanes planes of h x w. */
+size_t dwt53_workspace_bytes(int nplanes, int h, int w);
+
+/* Forward transform of nplanes planes (int16 [nplanes][h][w], device) into
+ * coef (int16 [nplanes][h*w], device, each plane subband-major) and, if hist
+ * is not NULL, the histograms of the values inside -255..255 of every band
+ * (uint32 [nplanes][1 + 3 levels][511], value + 255; cleared first), the
+ * tables' input for the segment coder.  1 <= levels <= 3, 1 <= nplanes <=
+ * 65535, h <= 65535, h*w < 2^31; ws: dwt53_workspace_bytes, 256-byte
+ * aligned.  Planes and coef must not overlap. */
+int dwt53_forward(const int16_t* planes, int nplanes, int h, int w, int levels, int16_t* coef, uint32_t* hist,
+                  void* ws, slrme_stream_t stream);
+
+/* Inverse of dwt53_forward (coef -> planes). */
+int dwt53_inverse(const int16_t* coef, int nplanes, int h, int w, int levels, int16_t* planes, void* ws,
+                  slrme_stream_t stream);
 
 /* ===================================================================== learned estimator
  * A small integer CNN that predicts the mantissas from the decoded SDRI and

@@ -52,6 +52,25 @@ __device__ __forceinline__ int stream_len(int64_t n, int64_t k, int l) {
     return first < end ? (int)((end - 1 - first) / kLanes) + 1 : 0;
 }
 
+// A run of segments, each with its own table and its own chunks.
+constexpr int kMaxSeg = SLRME_RANS_MAX_SEGMENTS;
+struct SegPlan {
+    int n;
+    int64_t sym_off[kMaxSeg];     // first symbol of each segment
+    int64_t len[kMaxSeg];         // symbols of each segment
+    int64_t chunk_off[kMaxSeg];   // first chunk (block, 32 counts) of each segment
+};
+
+// Warp-wide: does the chunk hold a value outside -255..255 (a raw chunk)?
+__device__ __forceinline__ bool chunk_out_of_range(const int16_t* src, int64_t m, int lane) {
+    bool oor = false;
+    for (int64_t i = lane; i < m; i += 32) {
+        const int v = src[i];
+        oor |= v < -255 || v > 255;
+    }
+    return __any_sync(kFull, oor);
+}
+
 // ---------------------------------------------------------------- tables
 // Normalisation of one channel's residual histogram to a table of total M:
 //   f_s = max(1, floor(n_s M / N)) for every symbol that occurs (n_s > 0);
@@ -261,12 +280,15 @@ __device__ __forceinline__ void enc_step(uint32_t& x, int& p, uint32_t& fmin, ui
 }
 
 __global__ void __launch_bounds__(kEncWarps * 32, 1)
-    k_rans_encode(const int16_t* __restrict__ r3, int64_t n, int64_t chunks, const uint32_t* __restrict__ freq3,
+    k_rans_encode(const int16_t* __restrict__ sym, SegPlan P, const uint32_t* __restrict__ freq,
                   uint16_t* __restrict__ words, uint32_t* __restrict__ counts, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EncSmem& S = *reinterpret_cast<EncSmem*>(smem_raw);
-    const int c = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) table_scan(freq3 + c * kNres, S.fr, S.cum, &S.bad_table);
+    const int g = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t seg_len = P.len[g];
+    const int64_t chunks = (seg_len + kChunk - 1) / kChunk;
+    if ((int64_t)blockIdx.x * kEncWarps >= chunks) return;   // no chunk of this segment for this CTA
+    if (warp == 0) table_scan(freq + (int64_t)g * kNres, S.fr, S.cum, &S.bad_table);
     __syncthreads();
     for (int s = threadIdx.x; s < 512; s += blockDim.x) {
         const uint32_t f = S.fr[s];
@@ -284,25 +306,34 @@ __global__ void __launch_bounds__(kEncWarps * 32, 1)
     }
     __syncthreads();
     const bool bad_table = S.bad_table != 0;
-    if (bad_table && threadIdx.x == 0) atomicOr(status, kStatusRans);
 
     uint16_t* stage = S.stage[warp];
     for (int64_t k = (int64_t)blockIdx.x * kEncWarps + warp; k < chunks; k += (int64_t)gridDim.x * kEncWarps) {
-        const int64_t blk = (int64_t)c * chunks + k;
+        const int64_t blk = P.chunk_off[g] + k;
+        const int16_t* src0 = sym + P.sym_off[g] + k * kChunk;
+        const int64_t m = min((int64_t)kChunk, seg_len - k * kChunk);   // symbols of this chunk
         if (bad_table) {
-            counts[blk * kLanes + lane] = 0u;
+            // without a table only a raw chunk can be stored
+            if (chunk_out_of_range(src0, m, lane)) {
+                uint16_t* dst = words + blk * (int64_t)(kLanes * kCap);
+                for (int64_t i = lane; i < m; i += 32) dst[i] = (uint16_t)src0[i];
+                counts[blk * kLanes + lane] = SLRME_RANS_RAW;
+            } else {
+                if (lane == 0) atomicOr(status, kStatusRans);
+                counts[blk * kLanes + lane] = 0u;
+            }
             continue;
         }
         // The lanes' streams differ in length by at most one symbol (lane 0's
         // is the longest): the top step is taken by the lanes that have it,
         // every step below it by all lanes, without per-step conditions.
-        const int len = stream_len(n, k, lane);
+        const int len = stream_len(m, 0, lane);
         const int J = __shfl_sync(kFull, len, 0);
-        const int16_t* src = r3 + (int64_t)c * n + k * kChunk + lane;
+        const int16_t* src = src0 + lane;
         uint16_t* st = stage + lane * kCap;
         uint32_t x = kRansL, fmin = kRansM;
         int p = kCap;
-        if ((k + 1) * kChunk <= n) {
+        if (m == kChunk) {
             // a full chunk: 256 steps per lane in blocks of 32, the symbols of
             // the next block loaded while the current block runs
             constexpr int kF = 32;
@@ -350,6 +381,14 @@ __global__ void __launch_bounds__(kEncWarps * 32, 1)
         // at most one word per symbol and two for the state: p stays >= 0
         st[--p] = (uint16_t)(x & 0xffffu);
         st[--p] = (uint16_t)(x >> 16);
+        if (__any_sync(kFull, fmin == 0u) && chunk_out_of_range(src0, m, lane)) {
+            // a value outside the alphabet: the chunk is stored raw
+            uint16_t* dst = words + blk * (int64_t)(kLanes * kCap);
+            for (int64_t i = lane; i < m; i += 32) dst[i] = (uint16_t)src0[i];
+            counts[blk * kLanes + lane] = SLRME_RANS_RAW;
+            __syncwarp();
+            continue;
+        }
         const bool ok = fmin != 0u;
         if (!ok) atomicOr(status, kStatusRans);
         const int used = kCap - p;
@@ -431,18 +470,19 @@ __device__ __forceinline__ void dec_step(uint32_t& x, int& p, const uint32_t* fb
 }
 
 __global__ void __launch_bounds__(kDecWarps * 32, 1)
-    k_rans_decode(const uint16_t* __restrict__ words, const uint32_t* __restrict__ counts, int64_t n, int64_t chunks,
-                  const uint32_t* __restrict__ freq3, int16_t* __restrict__ r3, int* status) {
+    k_rans_decode(const uint16_t* __restrict__ words, const uint32_t* __restrict__ counts, SegPlan P,
+                  const uint32_t* __restrict__ freq, int16_t* __restrict__ sym, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DecSmem& S = *reinterpret_cast<DecSmem*>(smem_raw);
-    const int c = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) table_scan(freq3 + c * kNres, S.u.t.fr, S.u.t.cum, &S.bad_table);
+    const int g = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t seg_len = P.len[g];
+    const int64_t chunks = (seg_len + kChunk - 1) / kChunk;
+    if ((int64_t)blockIdx.x * kDecWarps >= chunks) return;   // no chunk of this segment for this CTA
+    if (warp == 0) table_scan(freq + (int64_t)g * kNres, S.u.t.fr, S.u.t.cum, &S.bad_table);
     if (lane == 0) mbar_init(smem_addr(&S.bar[warp]), 1);
     __syncthreads();
-    if (S.bad_table) {
-        if (threadIdx.x == 0) atomicOr(status, kStatusRans);
-        return;
-    }
+    const bool bad_table = S.bad_table != 0;
+    if (!bad_table) {
     // The symbol of each slot: every symbol with f > 0 marks the first slot
     // of its range (cum[s]) in sym[], and a running maximum over the slots
     // carries each mark to the end of its range (the marks grow with the
@@ -496,14 +536,29 @@ __global__ void __launch_bounds__(kDecWarps * 32, 1)
             }
         }
     }
+    }
     __syncthreads();   // the scan arrays are dead from here: the staging buffers reuse them
 
     const uint32_t bar = smem_addr(&S.bar[warp]);
     const uint32_t stage_addr = smem_addr(S.u.stage[warp]);
     uint32_t phase = 0;
     for (int64_t k = (int64_t)blockIdx.x * kDecWarps + warp; k < chunks; k += (int64_t)gridDim.x * kDecWarps) {
-        const int64_t blk = (int64_t)c * chunks + k;
+        const int64_t blk = P.chunk_off[g] + k;
+        const int64_t m = min((int64_t)kChunk, seg_len - k * kChunk);
+        int16_t* out0 = sym + P.sym_off[g] + k * kChunk;
         const uint32_t cnt = counts[blk * kLanes + lane];
+        const bool raw = cnt == SLRME_RANS_RAW;
+        if (__any_sync(kFull, raw)) {
+            // a raw chunk (all 32 counts say so) holds its values verbatim
+            const uint16_t* block = words + blk * (int64_t)(kLanes * kCap);
+            for (int64_t i = lane; i < m; i += 32) out0[i] = (int16_t)block[i];
+            if (!__all_sync(kFull, raw) && lane == 0) atomicOr(status, kStatusRans);
+            continue;
+        }
+        if (bad_table) {
+            if (lane == 0) atomicOr(status, kStatusRans);
+            continue;
+        }
         // stream offsets in the packed block; a count outside 2..258 (or a
         // sum beyond the block) is reported, and the whole block is copied
         const bool cnt_ok = cnt >= 2u && cnt <= (uint32_t)kCap;
@@ -522,8 +577,8 @@ __global__ void __launch_bounds__(kDecWarps * 32, 1)
             mbar_arrive_expect_tx(bar, bytes);
             tma_load_1d(stage_addr, words + blk * (int64_t)(kLanes * kCap), bytes, bar);
         }
-        const int len = stream_len(n, k, lane);
-        int16_t* dst = r3 + (int64_t)c * n + k * kChunk + lane;
+        const int len = stream_len(m, 0, lane);
+        int16_t* dst = out0 + lane;
         if (!mbar_wait(bar, phase, status)) {
             // the copy did not land within the bound: wait once more (bounded)
             // so that no copy is left in flight, then stop
@@ -553,12 +608,6 @@ __global__ void __launch_bounds__(kDecWarps * 32, 1)
     }
 }
 
-int grid_x(int64_t chunks, int warps) {
-    const int64_t need = (chunks + warps - 1) / warps;
-    const int64_t cap = std::max(1, geometry().sms / 3);
-    return (int)std::min<int64_t>(need, cap);
-}
-
 // Raises the kernel's dynamic shared-memory limit once per device.
 int set_smem(const void* fn, size_t bytes, bool* done, const char* what) {
     int dev = 0;
@@ -572,6 +621,81 @@ int set_smem(const void* fn, size_t bytes, bool* done, const char* what) {
 }
 
 bool g_enc_attr[64], g_dec_attr[64];
+
+// CTAs per segment: enough for every warp of the largest segment to take a
+// chunk, at most a third of the SMs (then the CTAs loop over their chunks).
+int grid_x(const SegPlan& P, int warps) {
+    int64_t need = 1;
+    for (int g = 0; g < P.n; ++g) need = std::max(need, ((P.len[g] + kChunk - 1) / kChunk + warps - 1) / warps);
+    const int64_t cap = std::max(1, geometry().sms / 3);
+    return (int)std::min<int64_t>(need, cap);
+}
+
+// Validates a run of segments and lays out its symbols and chunks.
+int seg_plan(const char* who, int nseg, const int64_t* len, SegPlan* P, int64_t* total_chunks) {
+    if (nseg < 1 || nseg > kMaxSeg || !len) {
+        set_error("%s: need 1 <= nseg <= %d and the segment lengths", who, kMaxSeg);
+        return SLRME_EINVAL;
+    }
+    P->n = nseg;
+    int64_t at = 0, chunk = 0;
+    for (int g = 0; g < nseg; ++g) {
+        if (len[g] < 0) {
+            set_error("%s: segment %d has a negative length", who, g);
+            return SLRME_EINVAL;
+        }
+        P->sym_off[g] = at;
+        P->len[g] = len[g];
+        P->chunk_off[g] = chunk;
+        at += len[g];
+        chunk += (len[g] + kChunk - 1) / kChunk;
+        if (at >= (int64_t(1) << 31)) {
+            set_error("%s: the segments hold 2^31 symbols or more", who);
+            return SLRME_EINVAL;
+        }
+    }
+    for (int g = nseg; g < kMaxSeg; ++g) P->sym_off[g] = P->len[g] = P->chunk_off[g] = 0;
+    *total_chunks = chunk;
+    return SLRME_OK;
+}
+
+int encode_plan(const int16_t* sym, const SegPlan& P, int64_t chunks, const uint32_t* freq, uint16_t* words,
+                uint32_t* counts, cudaStream_t s, const char* who) {
+    if (chunks == 0) return SLRME_OK;
+    if (!sym || !freq || !words || !counts || ((uintptr_t)sym & 1u) || ((uintptr_t)freq & 3u) ||
+        ((uintptr_t)words & 15u) || ((uintptr_t)counts & 3u)) {
+        set_error("%s: null or misaligned pointer (symbols 2, tables 4, words 16, counts 4 bytes)", who);
+        return SLRME_EINVAL;
+    }
+    int* status = nullptr;
+    int rc = status_word_address(&status);
+    if (rc) return rc;
+    const size_t smem = sizeof(EncSmem);
+    if ((rc = set_smem((const void*)k_rans_encode, smem, g_enc_attr, "rans encoder shared memory"))) return rc;
+    const dim3 grid(grid_x(P, kEncWarps), P.n);
+    k_rans_encode<<<grid, kEncWarps * 32, smem, s>>>(sym, P, freq, words, counts, status);
+    return cuda_status(who);
+}
+
+int decode_plan(const uint16_t* words, const uint32_t* counts, const SegPlan& P, int64_t chunks,
+                const uint32_t* freq, int16_t* sym, cudaStream_t s, const char* who) {
+    if (chunks == 0) return SLRME_OK;
+    if (!sym || !freq || !words || !counts || ((uintptr_t)sym & 1u) || ((uintptr_t)freq & 3u) ||
+        ((uintptr_t)words & 15u) || ((uintptr_t)counts & 3u)) {
+        set_error("%s: null or misaligned pointer (words 16, counts 4, tables 4, symbols 2 bytes)", who);
+        return SLRME_EINVAL;
+    }
+    int* status = nullptr;
+    int rc = status_word_address(&status);
+    if (rc) return rc;
+    const size_t smem = sizeof(DecSmem);
+    if ((rc = set_smem((const void*)k_rans_decode, smem, g_dec_attr, "rans decoder shared memory"))) return rc;
+    const dim3 grid(grid_x(P, kDecWarps), P.n);
+    k_rans_decode<<<grid, kDecWarps * 32, smem, s>>>(words, counts, P, freq, sym, status);
+    return cuda_status(who);
+}
+
+
 
 bool aligned(const void* p, size_t a) {
     return ((uintptr_t)p % a) == 0;
@@ -600,6 +724,32 @@ extern "C" int64_t rans_counts_capacity(int64_t n) {
     return 3 * chunks * SLRME_RANS_LANES;
 }
 
+extern "C" int64_t rans_segments_words_capacity(int nseg, const int64_t* len) {
+    using namespace slrme;
+    SegPlan P;
+    int64_t chunks = 0;
+    if (seg_plan("rans_segments_words_capacity", nseg, len, &P, &chunks)) return 0;
+    return chunks * kLanes * kCap;
+}
+
+extern "C" int64_t rans_segments_counts_capacity(int nseg, const int64_t* len) {
+    using namespace slrme;
+    SegPlan P;
+    int64_t chunks = 0;
+    if (seg_plan("rans_segments_counts_capacity", nseg, len, &P, &chunks)) return 0;
+    return chunks * kLanes;
+}
+
+extern "C" int rans_tables_n(const uint32_t* hist, int ntables, uint32_t* freq, slrme_stream_t stream) {
+    using namespace slrme;
+    if (!hist || !freq || !aligned(hist, 4) || !aligned(freq, 4) || ntables < 1 || ntables > 65535) {
+        set_error("rans_tables_n: need 4-byte aligned hist and freq and 1 <= ntables <= 65535");
+        return SLRME_EINVAL;
+    }
+    k_rans_tables<<<ntables, 32, 0, (cudaStream_t)stream>>>(hist, freq);
+    return cuda_status("rans_tables_n launch");
+}
+
 extern "C" int rans_tables(const uint32_t* hist3, uint32_t* freq3, slrme_stream_t stream) {
     using namespace slrme;
     if (!hist3 || !freq3 || !aligned(hist3, 4) || !aligned(freq3, 4)) {
@@ -610,25 +760,36 @@ extern "C" int rans_tables(const uint32_t* hist3, uint32_t* freq3, slrme_stream_
     return cuda_status("rans_tables launch");
 }
 
+extern "C" int rans_encode_segments(const int16_t* sym, int nseg, const int64_t* len, const uint32_t* freq,
+                                    uint16_t* words, uint32_t* counts, slrme_stream_t stream) {
+    using namespace slrme;
+    SegPlan P;
+    int64_t chunks = 0;
+    int rc = seg_plan("rans_encode_segments", nseg, len, &P, &chunks);
+    if (rc) return rc;
+    return encode_plan(sym, P, chunks, freq, words, counts, (cudaStream_t)stream, "rans_encode_segments");
+}
+
+extern "C" int rans_decode_segments(const uint16_t* words, const uint32_t* counts, int nseg, const int64_t* len,
+                                    const uint32_t* freq, int16_t* sym, slrme_stream_t stream) {
+    using namespace slrme;
+    SegPlan P;
+    int64_t chunks = 0;
+    int rc = seg_plan("rans_decode_segments", nseg, len, &P, &chunks);
+    if (rc) return rc;
+    return decode_plan(words, counts, P, chunks, freq, sym, (cudaStream_t)stream, "rans_decode_segments");
+}
+
 extern "C" int rans_encode(const int16_t* r3, int64_t n, const uint32_t* freq3, uint16_t* words, uint32_t* counts,
                            slrme_stream_t stream) {
     using namespace slrme;
     int rc = check_n("rans_encode", n);
     if (rc) return rc;
-    if (n == 0) return SLRME_OK;
-    if (!r3 || !freq3 || !words || !counts || !aligned(r3, 2) || !aligned(freq3, 4) || !aligned(words, 16) ||
-        !aligned(counts, 4)) {
-        set_error("rans_encode: null or misaligned pointer (r3 2, freq3 4, words 16, counts 4 bytes)");
-        return SLRME_EINVAL;
-    }
-    int* status = nullptr;
-    if ((rc = status_word_address(&status))) return rc;
-    const size_t smem = sizeof(EncSmem);
-    if ((rc = set_smem((const void*)k_rans_encode, smem, g_enc_attr, "rans_encode smem"))) return rc;
-    const int64_t chunks = (n + kChunk - 1) / kChunk;
-    const dim3 grid(grid_x(chunks, kEncWarps), 3);
-    k_rans_encode<<<grid, kEncWarps * 32, smem, (cudaStream_t)stream>>>(r3, n, chunks, freq3, words, counts, status);
-    return cuda_status("rans_encode launch");
+    const int64_t len[3] = {n, n, n};
+    SegPlan P;
+    int64_t chunks = 0;
+    if ((rc = seg_plan("rans_encode", 3, len, &P, &chunks))) return rc;
+    return encode_plan(r3, P, chunks, freq3, words, counts, (cudaStream_t)stream, "rans_encode");
 }
 
 extern "C" int rans_decode(const uint16_t* words, const uint32_t* counts, int64_t n, const uint32_t* freq3,
@@ -636,18 +797,9 @@ extern "C" int rans_decode(const uint16_t* words, const uint32_t* counts, int64_
     using namespace slrme;
     int rc = check_n("rans_decode", n);
     if (rc) return rc;
-    if (n == 0) return SLRME_OK;
-    if (!r3 || !freq3 || !words || !counts || !aligned(r3, 2) || !aligned(freq3, 4) || !aligned(words, 16) ||
-        !aligned(counts, 4)) {
-        set_error("rans_decode: null or misaligned pointer (words 16, counts 4, freq3 4, r3 2 bytes)");
-        return SLRME_EINVAL;
-    }
-    int* status = nullptr;
-    if ((rc = status_word_address(&status))) return rc;
-    const size_t smem = sizeof(DecSmem);
-    if ((rc = set_smem((const void*)k_rans_decode, smem, g_dec_attr, "rans_decode smem"))) return rc;
-    const int64_t chunks = (n + kChunk - 1) / kChunk;
-    const dim3 grid(grid_x(chunks, kDecWarps), 3);
-    k_rans_decode<<<grid, kDecWarps * 32, smem, (cudaStream_t)stream>>>(words, counts, n, chunks, freq3, r3, status);
-    return cuda_status("rans_decode launch");
+    const int64_t len[3] = {n, n, n};
+    SegPlan P;
+    int64_t chunks = 0;
+    if ((rc = seg_plan("rans_decode", 3, len, &P, &chunks))) return rc;
+    return decode_plan(words, counts, P, chunks, freq3, r3, (cudaStream_t)stream, "rans_decode");
 }

@@ -45,6 +45,12 @@ _SIGS = {
     "rans_tables": [_vp, _vp, _vp],
     "rans_encode": [_vp, _i64, _vp, _vp, _vp, _vp],
     "rans_decode": [_vp, _vp, _i64, _vp, _vp, _vp],
+    "rans_tables_n": [_vp, _i32, _vp, _vp],
+    "rans_encode_segments": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
+    "rans_decode_segments": [_vp, _vp, _i32, _vp, _vp, _vp, _vp],
+    "dwt53_bands": [_i32, _i32, _i32, _vp],
+    "dwt53_forward": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
+    "dwt53_inverse": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp],
 }
 
 
@@ -73,6 +79,12 @@ def lib() -> ctypes.CDLL:
                 fn = getattr(L, name)
                 fn.restype = ctypes.c_int64
                 fn.argtypes = [_i64]
+            for name in ("rans_segments_words_capacity", "rans_segments_counts_capacity"):
+                fn = getattr(L, name)
+                fn.restype = ctypes.c_int64
+                fn.argtypes = [_i32, _vp]
+            L.dwt53_workspace_bytes.restype = ctypes.c_size_t
+            L.dwt53_workspace_bytes.argtypes = [_i32, _i32, _i32]
             _lib = L
     return _lib
 
@@ -168,6 +180,60 @@ def rans_encode(r3, n: int, freq3, words, counts, stream=None) -> None:
 def rans_decode(words, counts, n: int, freq3, r3, stream=None) -> None:
     _check("rans_decode", lib().rans_decode(_ptr(words), _ptr(counts), int(n), _ptr(freq3), _ptr(r3),
                                             _stream(stream)))
+
+
+def _lengths(lengths):
+    """The segment lengths as a host int64 array (kept alive by the caller's reference)."""
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(lengths, dtype=np.int64).reshape(-1))
+
+
+def rans_segments_capacity(lengths) -> tuple:
+    """(uint16 words, uint32 counts) of a run of segments."""
+    ln = _lengths(lengths)
+    return (int(lib().rans_segments_words_capacity(int(ln.size), ln.ctypes.data)),
+            int(lib().rans_segments_counts_capacity(int(ln.size), ln.ctypes.data)))
+
+
+def rans_tables_n(hist, ntables: int, freq, stream=None) -> None:
+    _check("rans_tables_n", lib().rans_tables_n(_ptr(hist), int(ntables), _ptr(freq), _stream(stream)))
+
+
+def rans_encode_segments(sym, lengths, freq, words, counts, stream=None) -> None:
+    ln = _lengths(lengths)
+    _check("rans_encode_segments", lib().rans_encode_segments(_ptr(sym), int(ln.size), ln.ctypes.data, _ptr(freq),
+                                                              _ptr(words), _ptr(counts), _stream(stream)))
+
+
+def rans_decode_segments(words, counts, lengths, freq, sym, stream=None) -> None:
+    ln = _lengths(lengths)
+    _check("rans_decode_segments", lib().rans_decode_segments(_ptr(words), _ptr(counts), int(ln.size),
+                                                              ln.ctypes.data, _ptr(freq), _ptr(sym),
+                                                              _stream(stream)))
+
+
+def dwt53_bands(h: int, w: int, levels: int) -> list:
+    """(rows, columns) of each band of a plane in output order."""
+    import numpy as np
+    dims = np.zeros(2 * 10, np.int32)
+    nb = lib().dwt53_bands(int(h), int(w), int(levels), dims.ctypes.data)
+    if nb < 0:
+        raise SlrmeError("dwt53_bands", nb, last_error())
+    return [(int(dims[2 * b]), int(dims[2 * b + 1])) for b in range(nb)]
+
+
+def dwt53_workspace_bytes(nplanes: int, h: int, w: int) -> int:
+    return int(lib().dwt53_workspace_bytes(int(nplanes), int(h), int(w)))
+
+
+def dwt53_forward(planes, nplanes: int, h: int, w: int, levels: int, coef, hist, ws, stream=None) -> None:
+    _check("dwt53_forward", lib().dwt53_forward(_ptr(planes), int(nplanes), int(h), int(w), int(levels), _ptr(coef),
+                                                _ptr(hist), _ptr(ws), _stream(stream)))
+
+
+def dwt53_inverse(coef, nplanes: int, h: int, w: int, levels: int, planes, ws, stream=None) -> None:
+    _check("dwt53_inverse", lib().dwt53_inverse(_ptr(coef), int(nplanes), int(h), int(w), int(levels), _ptr(planes),
+                                                _ptr(ws), _stream(stream)))
 
 
 def device_status(clear: bool = True) -> int:

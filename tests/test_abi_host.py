@@ -153,3 +153,33 @@ def test_rans_bad_arguments_rejected_before_any_gpu_work():
     assert L.rans_decode(64, 64, 10, 64, None, None) == EINVAL
     assert "rans_decode" in native.last_error()
     assert L.rans_encode(None, 0, None, None, None, None) == 0        # empty planes: nothing to do
+
+
+def test_dwt_band_sizes_and_segment_capacities_match_the_oracle():
+    for h, w in [(1, 1), (1, 7), (7, 1), (5, 3), (33, 65), (1536, 2048), (4320, 7680)]:
+        for levels in (1, 2, 3):
+            assert native.dwt53_bands(h, w, levels) == O.dwt53_bands(h, w, levels)
+    for lengths in ([1], [8192, 8193, 0, 31], [n for n in range(0, 64 * 100, 100)]):
+        _, nw, nc = O.rans_segment_layout(lengths)
+        assert native.rans_segments_capacity(lengths) == (nw, nc)
+
+
+def test_dwt_and_segment_bad_arguments_rejected_before_any_gpu_work():
+    L = native.lib()
+    EINVAL = -1
+    import numpy as np
+    assert L.dwt53_forward(64, 3, 8, 8, 0, 128, None, 256, None) == EINVAL        # levels 0
+    assert L.dwt53_forward(64, 3, 8, 8, 4, 128, None, 256, None) == EINVAL        # levels 4
+    assert L.dwt53_forward(64, 3, 65536, 8, 1, 128, None, 256, None) == EINVAL    # h > 65535
+    assert L.dwt53_forward(64, 3, 8, 8, 1, 128, None, 272, None) == EINVAL        # ws not 256-byte aligned
+    assert L.dwt53_forward(65, 3, 8, 8, 1, 128, None, 256, None) == EINVAL        # planes misaligned
+    assert L.dwt53_inverse(64, 0, 8, 8, 1, 128, 256, None) == EINVAL              # no planes
+    assert L.dwt53_bands(8, 8, 0, 64) == EINVAL
+    ln = np.array([10, -1], np.int64)
+    assert L.rans_encode_segments(64, 2, ln.ctypes.data, 64, 64, 64, None) == EINVAL    # negative length
+    ln = np.zeros(65, np.int64)
+    assert L.rans_encode_segments(64, 65, ln.ctypes.data, 64, 64, 64, None) == EINVAL   # too many segments
+    ln = np.array([100], np.int64)
+    assert L.rans_decode_segments(72, 64, 1, ln.ctypes.data, 64, 64, None) == EINVAL    # words misaligned
+    assert L.rans_tables_n(64, 0, 64, None) == EINVAL
+    assert L.rans_segments_words_capacity(0, ln.ctypes.data) == 0
