@@ -413,13 +413,15 @@ def run_ours(args) -> None:
 
 
 def enhancement_coder(c, rgbe, qualities, n, args, flush, stream) -> dict:
-    """The enhancement layer's entropy coder (interleaved rANS) on this
-    image's residuals at each quality, outside the timed step: the coded size
-    against the histograms' zeroth-order entropy, the lossless round trip of
-    the residual planes, and the device time of each coder call.  The three
-    calls are captured once as a CUDA graph with event-record nodes between
-    them and replayed (L2 flushed between replays), so host submission gaps
-    do not enter the times."""
+    """The enhancement layer's entropy coding on this image's residuals at
+    each quality, outside the timed step, in two forms: interleaved rANS over
+    the residual planes (a table per channel), and the same coder over the
+    coefficients of a three-level reversible 5/3 wavelet (a table per band).
+    Reports the coded size against the zeroth-order entropy, the lossless
+    round trip, and the device time of each call: the calls of each form are
+    captured once as a CUDA graph with event-record nodes between them and
+    replayed (L2 flushed between replays), so host submission gaps do not
+    enter the times."""
     import numpy as np
     import torch
 
@@ -427,68 +429,117 @@ def enhancement_coder(c, rgbe, qualities, n, args, flush, stream) -> dict:
     from paper_2309_11072_gb300.metrics import entropy_bits
 
     nres = native.SLRME_NRES
+    h, w = c.h, c.w
+    levels = 3
+    nb = 1 + 3 * levels
+    bands = native.dwt53_bands(h, w, levels)
+    lengths = [a * b for a, b in bands] * 3
+    # plain form buffers
     freq = torch.empty(3 * nres, dtype=torch.int32, device="cuda")
     words = torch.empty(native.rans_words_capacity(n), dtype=torch.int16, device="cuda")
     counts = torch.empty(native.rans_counts_capacity(n), dtype=torch.int32, device="cuda")
     r_back = torch.empty_like(c.r3)
-    names = ("rans_tables", "rans_encode", "rans_decode")
+    # wavelet form buffers
+    coef = torch.empty(3 * n, dtype=torch.int16, device="cuda")
+    bhist = torch.empty(3 * nb * nres, dtype=torch.int32, device="cuda")
+    bfreq = torch.empty(3 * nb * nres, dtype=torch.int32, device="cuda")
+    ws = torch.empty(native.dwt53_workspace_bytes(3, h, w), dtype=torch.uint8, device="cuda")
+    nw, nc = native.rans_segments_capacity(lengths)
+    wwords = torch.empty(nw, dtype=torch.int16, device="cuda")
+    wcounts = torch.empty(nc, dtype=torch.int32, device="cuda")
+    coef_back = torch.empty_like(coef)
+    w_back = torch.empty_like(c.r3)
 
-    def calls(st, ev=None):
+    plain_names = ("rans_tables", "rans_encode", "rans_decode")
+    wave_names = ("dwt53_forward", "rans_tables_n", "rans_encode_segments", "rans_decode_segments", "dwt53_inverse")
+
+    def plain_calls(st, ev=None):
+        steps = [lambda: native.rans_tables(c.hist, freq, st),
+                 lambda: native.rans_encode(c.r3, n, freq, words, counts, st),
+                 lambda: native.rans_decode(words, counts, n, freq, r_back, st)]
+        for i, f in enumerate(steps):
+            if ev is not None:
+                ev[i].record(st)
+            f()
         if ev is not None:
-            ev[0].record(st)
-        native.rans_tables(c.hist, freq, st)
+            ev[len(steps)].record(st)
+
+    def wave_calls(st, ev=None):
+        steps = [lambda: native.dwt53_forward(c.r3, 3, h, w, levels, coef, bhist, ws, st),
+                 lambda: native.rans_tables_n(bhist, 3 * nb, bfreq, st),
+                 lambda: native.rans_encode_segments(coef, lengths, bfreq, wwords, wcounts, st),
+                 lambda: native.rans_decode_segments(wwords, wcounts, lengths, bfreq, coef_back, st),
+                 lambda: native.dwt53_inverse(coef_back, 3, h, w, levels, w_back, ws, st)]
+        for i, f in enumerate(steps):
+            if ev is not None:
+                ev[i].record(st)
+            f()
         if ev is not None:
-            ev[1].record(st)
-        native.rans_encode(c.r3, n, freq, words, counts, st)
-        if ev is not None:
-            ev[2].record(st)
-        native.rans_decode(words, counts, n, freq, r_back, st)
-        if ev is not None:
-            ev[3].record(st)
+            ev[len(steps)].record(st)
 
     c.encode(rgbe, qualities[0])
-    calls(stream)                      # first calls set up the kernels before capture
+    plain_calls(stream)                # first calls set up the kernels before capture
+    wave_calls(stream)
     torch.cuda.synchronize()
+    forms = {}
     try:
-        gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(4)]
-        cap = torch.cuda.Stream()
-        cap.wait_stream(stream)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=cap, capture_error_mode="thread_local"):
-            calls(torch.cuda.current_stream(), gev)
-        stream.wait_stream(cap)
-        timing = "event-record nodes between the three calls in replays of one CUDA graph, L2 flushed between replays"
+        for name, fn, k in (("plain", plain_calls, len(plain_names)), ("wavelet", wave_calls, len(wave_names))):
+            gev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(k + 1)]
+            cap = torch.cuda.Stream()
+            cap.wait_stream(stream)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=cap, capture_error_mode="thread_local"):
+                fn(torch.cuda.current_stream(), gev)
+            stream.wait_stream(cap)
+            forms[name] = (graph, gev)
+        timing = "event-record nodes between the calls in replays of one CUDA graph per form, L2 flushed between replays"
     except TypeError:
-        graph = None
+        forms = {}
         timing = "events between the calls launched one by one (host gaps included), L2 flushed between repetitions"
-    out = {"coder": "static per-channel rANS, M = 2^14, 32 interleaved 16-bit streams per 8192 symbols",
-           "timing": timing}
-    ok = True
-    for q in qualities:
-        c.encode(rgbe, q)
-        native.device_status(clear=True)
+
+    def timed(name, fn, names):
         t = {k: [] for k in names}
         for rep in range(args.warmup + args.steps):
-            if graph is not None:
-                graph.replay()
-                ev = gev
+            if name in forms:
+                forms[name][0].replay()
+                ev = forms[name][1]
             else:
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-                calls(stream, ev)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+                fn(stream, ev)
             flush.zero_()
             torch.cuda.synchronize()
             if rep >= args.warmup:
                 for i, k in enumerate(names):
                     t[k].append(ev[i].elapsed_time(ev[i + 1]) * 1e3)
-        ok &= bool(torch.equal(r_back, c.r3)) and native.device_status(clear=True) == 0
+        return {k: round(statistics.mean(v), 2) for k, v in t.items()}
+
+    out = {"coder": "static rANS, M = 2^14, 32 interleaved 16-bit streams per 8192 symbols; plain: a table per "
+                    "channel over the residual planes; wavelet: three-level reversible 5/3 transform, a table "
+                    "per band (30), chunks with values beyond +-255 stored raw",
+           "timing": timing}
+    ok = True
+    for q in qualities:
+        c.encode(rgbe, q)
+        native.device_status(clear=True)
+        us = timed("plain", plain_calls, plain_names)
+        ok &= bool(torch.equal(r_back, c.r3))
+        wus = timed("wavelet", wave_calls, wave_names)
+        ok &= bool(torch.equal(w_back, c.r3)) and native.device_status(clear=True) == 0
         cnt = counts.cpu().numpy().view(np.uint32).astype(np.int64)
         hist = c.hist.view(3, nres).cpu().numpy().view(np.uint32)
         h0 = sum(entropy_bits(hist[ch]) for ch in range(3))
-        us = {k: round(statistics.mean(v), 2) for k, v in t.items()}
+        wc = wcounts.cpu().numpy().view(np.uint32)
+        raw = wc == 0xFFFFFFFF
+        raw_chunks = int(raw.sum()) // 32
+        wbits = 16.0 * wc[~raw].astype(np.int64).sum() + 16.0 * 8192 * raw_chunks
+        bh = bhist.view(3 * nb, nres).cpu().numpy().view(np.uint32)
+        wh0 = sum(entropy_bits(bh[i]) * bh[i].sum() for i in range(3 * nb)) / n
         out[str(q)] = {"coded_bits_per_px": round(16.0 * cnt.sum() / n, 4), "h0_bits_per_px": round(h0, 4),
                        "table_bits": 3 * nres * 15, "us": us,
                        "encode_msym_s": round(3 * n / us["rans_encode"], 1),
-                       "decode_msym_s": round(3 * n / us["rans_decode"], 1)}
+                       "decode_msym_s": round(3 * n / us["rans_decode"], 1),
+                       "wavelet": {"coded_bits_per_px": round(wbits / n, 4), "h0_bits_per_px": round(wh0, 4),
+                                   "raw_chunks": raw_chunks, "table_bits": 3 * nb * nres * 15, "us": wus}}
     out["lossless"] = ok
     return out
 
