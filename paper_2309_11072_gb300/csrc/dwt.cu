@@ -11,14 +11,15 @@
 // plane's output is subband-major: LL_L, then HL, LH, HH from level L down
 // to 1, each band row-major (HL: high-pass along the rows).
 //
-// Kernels: a row pass per level (one thread per output pair of a row) into
-// a workspace holding each row as [low | high]; a column pass (one thread
-// per output pair of a column, 32 adjacent columns per warp) that writes the
-// three detail bands to their places and the low-low band to the next
-// level's input (or, at the last level, to band 0), with per-band histograms
-// of the values inside -255..255 kept in shared memory and added to the
-// caller's array once per block.  The inverse runs the column pass, then
-// the row pass, level by level from the deepest.  Arithmetic shifts of
+// Kernels: a row pass per level (a CTA per 2,048-pair row segment, staged in
+// shared memory) into a workspace holding each row as [low | high]; a
+// column pass (a thread walks 64 pairs of one column, 32 adjacent columns
+// per warp) that writes the three detail bands to their places and the
+// low-low band to the next level's input (or, at the last level, to band 0),
+// with per-band histograms of the values inside -255..255 kept in shared
+// memory (one copy per warp) and added to the caller's array once per block.
+// The inverse runs the column pass, then the row pass, level by level from
+// the deepest.  Arithmetic shifts of
 // negative int are floors (two's complement, as nvcc compiles >>).
 #include <stdint.h>
 
@@ -65,32 +66,96 @@ void band_layout(int h, int w, int levels, Bands* B) {
     }
 }
 
-// The high-pass value j of a row or column of n >= 2 samples read through `at`.
-template <class F>
-__device__ __forceinline__ int hp(const F& at, int n, int j) {
-    const int l = at(2 * j);
-    const int r = (2 * j + 2 <= n - 1) ? at(2 * j + 2) : l;
-    return at(2 * j + 1) - ((l + r) >> 1);
-}
+// ---------------------------------------------------------------- row passes
+// A CTA takes kSeg pairs of one row (pairs i0 .. i0+kSeg-1): it stages the
+// samples they need (2 i0 - 2 .. 2 i0 + 2 kSeg) in shared memory with
+// coalesced loads, computes the high-pass values d_(i0-1) .. d_(i0+kSeg-1)
+// once each, then the low-pass values.
+constexpr int kRowThreads = 256;
+constexpr int kSeg = 2048;
 
-// ---------------------------------------------------------------- forward
-// Row pass: out row y = [s_0 .. s_{nL-1} | d_0 .. d_{nH-1}].
-__global__ void k_dwt_rows_fwd(const int16_t* __restrict__ in, int64_t in_plane, int H, int W,
-                               int16_t* __restrict__ out, int64_t out_plane) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kRowThreads) k_dwt_rows_fwd(const int16_t* __restrict__ in, int64_t in_plane,
+                                                              int H, int W, int16_t* __restrict__ out,
+                                                              int64_t out_plane) {
+    __shared__ int16_t xs[2 * kSeg + 3];
+    __shared__ int16_t ds[kSeg + 1];
     const int nH = W / 2, nL = W - nH;
-    if (i >= nL) return;
+    const int i0 = blockIdx.x * kSeg;
     const int16_t* x = in + blockIdx.z * in_plane + (int64_t)blockIdx.y * W;
     int16_t* o = out + blockIdx.z * out_plane + (int64_t)blockIdx.y * W;
     if (W == 1) {
-        o[0] = x[0];
+        if (threadIdx.x == 0) o[0] = x[0];
         return;
     }
-    auto at = [&](int k) { return (int)__ldg(x + k); };
-    const int dl = hp(at, W, i >= 1 ? i - 1 : 0);
-    const int dr = hp(at, W, i < nH ? i : nH - 1);
-    o[i] = (int16_t)(at(2 * i) + ((dl + dr + 2) >> 2));
-    if (i < nH) o[nL + i] = (int16_t)dr;
+    const int k0 = 2 * i0 - 2;                           // sample of xs[0]
+    const int k1 = min(W, 2 * (i0 + kSeg) + 1);         // one past the last sample needed
+    for (int k = max(k0, 0) + threadIdx.x; k < k1; k += kRowThreads) xs[k - k0] = x[k];
+    __syncthreads();
+    const int j0 = max(i0 - 1, 0), j1 = min(nH, i0 + kSeg);   // high-pass values to compute
+    for (int j = j0 + threadIdx.x; j < j1; j += kRowThreads) {
+        const int l = xs[2 * j - k0];
+        const int r = (2 * j + 2 <= W - 1) ? xs[2 * j + 2 - k0] : l;
+        const int d = xs[2 * j + 1 - k0] - ((l + r) >> 1);
+        ds[j - (i0 - 1)] = (int16_t)d;
+        if (j >= i0) o[nL + j] = (int16_t)d;
+    }
+    __syncthreads();
+    const int iend = min(nL, i0 + kSeg);
+    for (int i = i0 + threadIdx.x; i < iend; i += kRowThreads) {
+        const int dl = ds[max(i - 1, 0) - (i0 - 1)];
+        const int dr = ds[min(i, nH - 1) - (i0 - 1)];
+        o[i] = (int16_t)(xs[2 * i - k0] + ((dl + dr + 2) >> 2));
+    }
+}
+
+// Row inverse over the same segments: the CTA stages s_(i0) .. s_(i0+kSeg)
+// and d_(i0-1) .. d_(i0+kSeg), computes the even samples 2 i0 .. 2 (i0+kSeg)
+// once each, then the odd ones.
+__global__ void __launch_bounds__(kRowThreads) k_dwt_rows_inv(const int16_t* __restrict__ t, int64_t t_plane, int H,
+                                                              int W, int16_t* __restrict__ out, int64_t out_plane) {
+    __shared__ int16_t ss[kSeg + 1];
+    __shared__ int16_t dd[kSeg + 2];
+    __shared__ int16_t es[kSeg + 1];
+    const int nH = W / 2, nL = W - nH;
+    const int i0 = blockIdx.x * kSeg;
+    const int16_t* row = t + blockIdx.z * t_plane + (int64_t)blockIdx.y * W;
+    int16_t* o = out + blockIdx.z * out_plane + (int64_t)blockIdx.y * W;
+    if (W == 1) {
+        if (threadIdx.x == 0) o[0] = row[0];
+        return;
+    }
+    const int s1 = min(nL, i0 + kSeg + 1);
+    for (int i = i0 + threadIdx.x; i < s1; i += kRowThreads) ss[i - i0] = row[i];
+    const int dj0 = max(i0 - 1, 0), dj1 = min(nH, i0 + kSeg + 1);
+    for (int j = dj0 + threadIdx.x; j < dj1; j += kRowThreads) dd[j - (i0 - 1)] = row[nL + j];
+    __syncthreads();
+    for (int i = i0 + threadIdx.x; i < s1; i += kRowThreads) {
+        const int dl = dd[max(i - 1, 0) - (i0 - 1)];
+        const int dr = dd[min(i, nH - 1) - (i0 - 1)];
+        const int e = ss[i - i0] - ((dl + dr + 2) >> 2);
+        es[i - i0] = (int16_t)e;
+        if (i < i0 + kSeg) o[2 * i] = (int16_t)e;
+    }
+    __syncthreads();
+    const int oend = min(nH, i0 + kSeg);
+    for (int i = i0 + threadIdx.x; i < oend; i += kRowThreads) {
+        const int e0 = es[i - i0];
+        const int e1 = (2 * i + 2 <= W - 1) ? es[i + 1 - i0] : e0;
+        o[2 * i + 1] = (int16_t)(dd[i - (i0 - 1)] + ((e0 + e1) >> 1));
+    }
+}
+
+// ---------------------------------------------------------------- column passes
+// A thread walks `run` pairs of one column (32 adjacent columns per warp, so
+// every load and store of the warp is one contiguous 64-byte run), keeping
+// the previous even sample and high-pass value in registers: two loads and
+// one high-pass computation per pair.
+// Pairs per thread: up to 32, fewer on short columns so that every column
+// still has about two dozen walkers.
+int col_run(int pairs) {
+    int run = 32;
+    while (run > 4 && pairs < 24 * run) run >>= 1;
+    return run;
 }
 
 struct ColDst {
@@ -104,61 +169,96 @@ struct ColDst {
     int b_ll, b_hl;         // band of the low-low output (-1: not a band yet), of HL (LH, HH follow)
 };
 
-constexpr int kColPairs = 8;   // pairs per thread in the column pass
+// Each warp counts into its own copy of the four local histograms (band-major
+// key = band * 511 + value + 255), so only lanes of one warp meet on a bin.
+constexpr int kHistCopy = 4 * kNres;
 
-__device__ __forceinline__ void hist_add(uint32_t* h, int v) {
-    if (v >= -255 && v <= 255) atomicAdd(h + (v + 255), 1u);
+__device__ __forceinline__ void hist_add(uint32_t* sh, int key) {
+    if (key >= 0) atomicAdd(sh + key, 1u);
 }
 
-// Column pass over the row-transformed array t (H x W): thread (x, pairs).
 __global__ void __launch_bounds__(256) k_dwt_cols_fwd(const int16_t* __restrict__ t, int64_t t_plane, int H, int W,
-                                                      ColDst D) {
-    __shared__ uint32_t sh[4][kNres];   // local bands: 0 LL, 1 HL, 2 LH, 3 HH
+                                                      int run, ColDst D) {
+    extern __shared__ uint32_t hsm[];    // [8 warps][4 local bands: 0 LL, 1 HL, 2 LH, 3 HH][511]
     const bool want = D.hist != nullptr;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     if (want)
-        for (int k = threadIdx.y * 32 + threadIdx.x; k < 4 * kNres; k += 256) (&sh[0][0])[k] = 0u;
+        for (int k = tid; k < 8 * kHistCopy; k += 256) hsm[k] = 0u;
     __syncthreads();
+    uint32_t* sh = hsm + threadIdx.y * kHistCopy;
     const int p = blockIdx.z;
-    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int xr = blockIdx.x * 32 + threadIdx.x;
+    const bool live = xr < W;
+    const int x = live ? xr : W - 1;                     // lanes past the edge shadow the last column
     const int WL = (W + 1) / 2, WH = W / 2;
     const int nHc = H / 2, nLc = H - nHc;
-    const int16_t* tp = t + p * t_plane;
-    if (x < W) {
-        auto at = [&](int k) { return (int)__ldg(tp + (int64_t)k * W + x); };
-        const bool lowc = x < WL;
-        for (int r = 0; r < kColPairs; ++r) {
-            const int i = (blockIdx.y * kColPairs + r) * 8 + threadIdx.y;
-            if (i >= nLc) break;
-            int s, d = 0;
-            if (H == 1) {
-                s = at(0);
-            } else {
-                const int dl = hp(at, H, i >= 1 ? i - 1 : 0);
-                const int dr = hp(at, H, i < nHc ? i : nHc - 1);
-                s = at(2 * i) + ((dl + dr + 2) >> 2);
-                d = dr;
+    const bool lowc = x < WL;
+    const int16_t* col = t + p * t_plane + x;
+    auto at = [&](int k) { return (int)__ldg(col + (int64_t)k * W); };
+    int16_t* sdst = lowc ? D.ll + p * D.ll_plane + x : D.coef + p * D.coef_plane + D.off_hl + (x - WL);
+    int16_t* ddst = lowc ? D.coef + p * D.coef_plane + D.off_lh + x : D.coef + p * D.coef_plane + D.off_hh + (x - WL);
+    const int spitch = lowc ? WL : WH;
+    const int sband = lowc ? (D.b_ll >= 0 ? 0 : -1) : 1;
+    const int dband = lowc ? 2 : 3;
+    const int i0 = (blockIdx.y * 8 + threadIdx.y) * run;
+    const int i1 = min(nLc, i0 + run);
+    if (i0 < i1) {
+        if (H == 1) {
+            const int s = at(0);
+            if (live) sdst[0] = (int16_t)s;
+            if (want) hist_add(sh, (live && sband >= 0 && s >= -255 && s <= 255) ? sband * kNres + s + 255 : -1);
+        } else {
+            // the high-pass value before the run (d_(-1) = d_0 at the top)
+            int e = at(2 * i0);
+            int dprev = 0;
+            if (i0 >= 1) {
+                const int l = at(2 * i0 - 2);
+                dprev = at(2 * i0 - 1) - ((l + e) >> 1);
             }
-            if (lowc) {
-                D.ll[p * D.ll_plane + (int64_t)i * WL + x] = (int16_t)s;
-                if (want && D.b_ll >= 0) hist_add(sh[0], s);
-                if (i < nHc) {
-                    D.coef[p * D.coef_plane + D.off_lh + (int64_t)i * WL + x] = (int16_t)d;
-                    if (want) hist_add(sh[2], d);
+            // blocks of 8 pairs: the block's 16 samples are loaded before any
+            // arithmetic, so the walk waits for memory once per block
+            constexpr int kB = 8;
+            for (int ib = i0; ib < i1; ib += kB) {
+                int xo[kB], xe[kB];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int i = ib + u;
+                    xo[u] = (i < i1 && i < nHc) ? at(2 * i + 1) : 0;
+                    xe[u] = (i < i1 && 2 * i + 2 <= H - 1) ? at(2 * i + 2) : 0;
                 }
-            } else {
-                D.coef[p * D.coef_plane + D.off_hl + (int64_t)i * WH + (x - WL)] = (int16_t)s;
-                if (want) hist_add(sh[1], s);
-                if (i < nHc) {
-                    D.coef[p * D.coef_plane + D.off_hh + (int64_t)i * WH + (x - WL)] = (int16_t)d;
-                    if (want) hist_add(sh[3], d);
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int i = ib + u;
+                    if (i >= i1) break;
+                    int d, r = e;
+                    if (i < nHc) {
+                        if (2 * i + 2 <= H - 1) r = xe[u];
+                        d = xo[u] - ((e + r) >> 1);
+                    } else {
+                        d = dprev;                       // odd H: the last even sample mirrors d_(nH-1)
+                    }
+                    const int dl = i == 0 ? d : dprev;
+                    const int s = e + ((dl + d + 2) >> 2);
+                    if (live) {
+                        sdst[(int64_t)i * spitch] = (int16_t)s;
+                        if (i < nHc) ddst[(int64_t)i * spitch] = (int16_t)d;
+                    }
+                    if (want) {
+                        hist_add(sh, (live && sband >= 0 && s >= -255 && s <= 255) ? sband * kNres + s + 255 : -1);
+                        hist_add(sh, (live && i < nHc && d >= -255 && d <= 255) ? dband * kNres + d + 255 : -1);
+                    }
+                    e = r;
+                    dprev = d;
                 }
             }
         }
     }
     if (!want) return;
     __syncthreads();
-    for (int k = threadIdx.y * 32 + threadIdx.x; k < 4 * kNres; k += 256) {
-        const uint32_t v = (&sh[0][0])[k];
+    for (int k = tid; k < kHistCopy; k += 256) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int w8 = 0; w8 < 8; ++w8) v += hsm[w8 * kHistCopy + k];
         if (!v) continue;
         const int lb = k / kNres, bin = k - lb * kNres;
         const int band = lb == 0 ? D.b_ll : D.b_hl + (lb - 1);
@@ -166,7 +266,6 @@ __global__ void __launch_bounds__(256) k_dwt_cols_fwd(const int16_t* __restrict_
     }
 }
 
-// ---------------------------------------------------------------- inverse
 struct ColSrc {
     const int16_t* ll;      // low-low input, row pitch WL
     int64_t ll_plane;
@@ -175,14 +274,19 @@ struct ColSrc {
     int64_t off_hl, off_lh, off_hh;
 };
 
-// Column inverse into t (H x W, rows as [low | high]).
-__global__ void __launch_bounds__(256) k_dwt_cols_inv(ColSrc S, int H, int W, int16_t* __restrict__ t,
+// Column inverse into t (H x W, rows as [low | high]), walking `run` pairs:
+// the even sample of pair i + 1 is computed once and serves both odd
+// samples beside it.
+__global__ void __launch_bounds__(256) k_dwt_cols_inv(ColSrc S, int H, int W, int run, int16_t* __restrict__ t,
                                                       int64_t t_plane) {
     const int p = blockIdx.z;
     const int x = blockIdx.x * 32 + threadIdx.x;
     if (x >= W) return;
     const int WL = (W + 1) / 2, WH = W / 2;
     const int nHc = H / 2, nLc = H - nHc;
+    const int i0 = (blockIdx.y * 8 + threadIdx.y) * run;
+    const int i1 = min(nLc, i0 + run);
+    if (i0 >= i1) return;
     const bool lowc = x < WL;
     const int16_t* lo = lowc ? S.ll + p * S.ll_plane + x : S.coef + p * S.coef_plane + S.off_hl + (x - WL);
     const int16_t* hi = lowc ? S.coef + p * S.coef_plane + S.off_lh + x : S.coef + p * S.coef_plane + S.off_hh + (x - WL);
@@ -190,54 +294,46 @@ __global__ void __launch_bounds__(256) k_dwt_cols_inv(ColSrc S, int H, int W, in
     int16_t* tp = t + p * t_plane + x;
     auto s_at = [&](int k) { return (int)__ldg(lo + (int64_t)k * pitch); };
     auto d_at = [&](int k) { return (int)__ldg(hi + (int64_t)k * pitch); };
-    // even sample 2k from s_k and its two neighbouring high-pass values
-    auto even = [&](int k) {
-        const int dl = d_at(k >= 1 ? k - 1 : 0);
-        const int dr = d_at(k < nHc ? k : nHc - 1);
-        return s_at(k) - ((dl + dr + 2) >> 2);
-    };
-    for (int r = 0; r < kColPairs; ++r) {
-        const int i = (blockIdx.y * kColPairs + r) * 8 + threadIdx.y;
-        if (i >= nLc) break;
-        if (H == 1) {
-            tp[0] = (int16_t)s_at(0);
-            continue;
+    if (H == 1) {
+        tp[0] = (int16_t)s_at(0);
+        return;
+    }
+    // even sample 2k from s_k and d_(k-1), d_k (mirrored at both ends)
+    int dprev = d_at(i0 >= 1 ? i0 - 1 : 0);
+    int dcur = d_at(i0 < nHc ? i0 : nHc - 1);
+    int e = s_at(i0) - ((dprev + dcur + 2) >> 2);
+    constexpr int kB = 8;
+    for (int ib = i0; ib < i1; ib += kB) {
+        int sn[kB], dn[kB];   // s_(i+1), d_(i+1) (mirrored) of the block's pairs, loaded first
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int i = ib + u;
+            const bool more = i < i1 && i < nHc && 2 * i + 2 <= H - 1;
+            sn[u] = more ? s_at(i + 1) : 0;
+            dn[u] = more ? d_at(i + 1 < nHc ? i + 1 : nHc - 1) : 0;
         }
-        const int e0 = even(i);
-        tp[(int64_t)(2 * i) * W] = (int16_t)e0;
-        if (i < nHc) {
-            const int e1 = (2 * i + 2 <= H - 1) ? even(i + 1) : e0;
-            tp[(int64_t)(2 * i + 1) * W] = (int16_t)(d_at(i) + ((e0 + e1) >> 1));
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int i = ib + u;
+            if (i >= i1) break;
+            tp[(int64_t)(2 * i) * W] = (int16_t)e;
+            if (i < nHc) {
+                int en = e;
+                int dnext = dcur;
+                if (2 * i + 2 <= H - 1) {
+                    dnext = dn[u];
+                    en = sn[u] - ((dcur + dnext + 2) >> 2);
+                }
+                tp[(int64_t)(2 * i + 1) * W] = (int16_t)(dcur + ((e + en) >> 1));
+                e = en;
+                dcur = dnext;
+            }
         }
     }
 }
 
-// Row inverse: row y of t = [s | d] back to samples.
-__global__ void k_dwt_rows_inv(const int16_t* __restrict__ t, int64_t t_plane, int H, int W,
-                               int16_t* __restrict__ out, int64_t out_plane) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nH = W / 2, nL = W - nH;
-    if (i >= nL) return;
-    const int16_t* row = t + blockIdx.z * t_plane + (int64_t)blockIdx.y * W;
-    int16_t* o = out + blockIdx.z * out_plane + (int64_t)blockIdx.y * W;
-    if (W == 1) {
-        o[0] = row[0];
-        return;
-    }
-    auto s_at = [&](int k) { return (int)__ldg(row + k); };
-    auto d_at = [&](int k) { return (int)__ldg(row + nL + k); };
-    auto even = [&](int k) {
-        const int dl = d_at(k >= 1 ? k - 1 : 0);
-        const int dr = d_at(k < nH ? k : nH - 1);
-        return s_at(k) - ((dl + dr + 2) >> 2);
-    };
-    const int e0 = even(i);
-    o[2 * i] = (int16_t)e0;
-    if (i < nH) {
-        const int e1 = (2 * i + 2 <= W - 1) ? even(i + 1) : e0;
-        o[2 * i + 1] = (int16_t)(d_at(i) + ((e0 + e1) >> 1));
-    }
-}
+constexpr size_t kColFwdSmem = 8 * kHistCopy * sizeof(uint32_t);   // 65,408 bytes
+bool g_col_attr[64];
 
 bool aligned2(const void* p) {
     return ((uintptr_t)p & 1u) == 0;
@@ -294,6 +390,16 @@ extern "C" int dwt53_forward(const int16_t* planes, int nplanes, int h, int w, i
     if (hist && cudaMemsetAsync(hist, 0, (size_t)nplanes * B.n * kNres * sizeof(uint32_t), s) != cudaSuccess)
         return cuda_status("dwt53_forward hist clear");
     if ((int64_t)h * w == 0) return SLRME_OK;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_status("dwt53_forward device");
+        if (!g_col_attr[dev]) {
+            if (cudaFuncSetAttribute(k_dwt_cols_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColFwdSmem) !=
+                cudaSuccess)
+                return cuda_status("dwt53_forward shared memory attribute");
+            g_col_attr[dev] = true;
+        }
+    }
     const int64_t plane = (int64_t)h * w;
     const int64_t qplane = (int64_t)((h + 1) / 2) * ((w + 1) / 2);
     int16_t* tmp = (int16_t*)ws;
@@ -304,8 +410,8 @@ extern "C" int dwt53_forward(const int16_t* planes, int nplanes, int h, int w, i
     for (int l = 1; l <= levels; ++l) {
         const int WL = (W + 1) / 2, HL = (H + 1) / 2;
         {
-            const dim3 grid((unsigned)((WL + 255) / 256), (unsigned)H, (unsigned)nplanes);
-            k_dwt_rows_fwd<<<grid, 256, 0, s>>>(in, in_plane, H, W, tmp, plane);
+            const dim3 grid((unsigned)((WL + kSeg - 1) / kSeg), (unsigned)H, (unsigned)nplanes);
+            k_dwt_rows_fwd<<<grid, kRowThreads, 0, s>>>(in, in_plane, H, W, tmp, plane);
         }
         const int bHL = 1 + 3 * (levels - l);
         ColDst D;
@@ -321,9 +427,9 @@ extern "C" int dwt53_forward(const int16_t* planes, int nplanes, int h, int w, i
         D.nb = B.n;
         D.b_ll = last ? 0 : -1;
         D.b_hl = bHL;
-        const dim3 grid((unsigned)((W + 31) / 32), (unsigned)((HL + 8 * kColPairs - 1) / (8 * kColPairs)),
-                        (unsigned)nplanes);
-        k_dwt_cols_fwd<<<grid, dim3(32, 8), 0, s>>>(tmp, plane, H, W, D);
+        const int run = col_run(HL);
+        const dim3 grid((unsigned)((W + 31) / 32), (unsigned)((HL + 8 * run - 1) / (8 * run)), (unsigned)nplanes);
+        k_dwt_cols_fwd<<<grid, dim3(32, 8), hist ? kColFwdSmem : 0, s>>>(tmp, plane, H, W, run, D);
         in = A;
         in_plane = qplane;
         H = HL;
@@ -368,13 +474,13 @@ extern "C" int dwt53_inverse(const int16_t* coef, int nplanes, int h, int w, int
         S.off_hl = B.off[bHL];
         S.off_lh = B.off[bHL + 1];
         S.off_hh = B.off[bHL + 2];
-        const dim3 cgrid((unsigned)((W + 31) / 32), (unsigned)((HL + 8 * kColPairs - 1) / (8 * kColPairs)),
-                         (unsigned)nplanes);
-        k_dwt_cols_inv<<<cgrid, dim3(32, 8), 0, s>>>(S, H, W, tmp, plane);
+        const int run = col_run(HL);
+        const dim3 cgrid((unsigned)((W + 31) / 32), (unsigned)((HL + 8 * run - 1) / (8 * run)), (unsigned)nplanes);
+        k_dwt_cols_inv<<<cgrid, dim3(32, 8), 0, s>>>(S, H, W, run, tmp, plane);
         int16_t* out = l == 1 ? planes : A;
         const int64_t out_plane = l == 1 ? plane : qplane;
-        const dim3 rgrid((unsigned)((WL + 255) / 256), (unsigned)H, (unsigned)nplanes);
-        k_dwt_rows_inv<<<rgrid, 256, 0, s>>>(tmp, plane, H, W, out, out_plane);
+        const dim3 rgrid((unsigned)((WL + kSeg - 1) / kSeg), (unsigned)H, (unsigned)nplanes);
+        k_dwt_rows_inv<<<rgrid, kRowThreads, 0, s>>>(tmp, plane, H, W, out, out_plane);
     }
     return cuda_status("dwt53_inverse launch");
 }
