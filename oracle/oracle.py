@@ -56,6 +56,10 @@ def lib():
                                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             _lib.oracle_rans_decode_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            _lib.oracle_base_levels.restype = ctypes.c_int
+            _lib.oracle_jpeg_bits.restype = ctypes.c_int
+            _lib.oracle_jpeg_ac_len.restype = ctypes.c_int
+            _lib.oracle_jpeg_dc_len.restype = ctypes.c_int
             _lib.oracle_dwt53_bands.restype = ctypes.c_int
             _lib.oracle_dwt53_forward.restype = ctypes.c_int
             _lib.oracle_dwt53_inverse.restype = ctypes.c_int
@@ -378,3 +382,40 @@ def dwt53_inverse(coef: np.ndarray, h: int, w: int, levels: int) -> np.ndarray:
         if rc != 0:
             raise ValueError("levels must be in 0..3")
     return out
+
+
+# ---------------------------------------------------------------- base-layer entropy coding (JPEG baseline)
+def base_levels(sdr3: np.ndarray, quality: int) -> np.ndarray:
+    """Quantised levels of the base round trip: [3][bh*bw][64] int16, coefficient (v, u) at u*8 + v."""
+    s = np.ascontiguousarray(sdr3, dtype=np.uint8)
+    _, h, w = s.shape
+    bh, bw = (h + 7) // 8, (w + 7) // 8
+    out = np.zeros((3, bh * bw, 64), np.int16)
+    if lib().oracle_base_levels(_p(s), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(quality), _p(out)) != 0:
+        raise ValueError("quality must be in 1..100")
+    return out
+
+
+def jpeg_bits(levels3: np.ndarray, h: int, w: int):
+    """Entropy-coded bits per plane ([3] uint64) and per block ([3][bh*bw] uint32)."""
+    L = np.ascontiguousarray(levels3, dtype=np.int16)
+    bh, bw = (h + 7) // 8, (w + 7) // 8
+    bits = np.zeros(3, np.uint64)
+    blk = np.zeros((3, bh * bw), np.uint32)
+    if lib().oracle_jpeg_bits(_p(L), ctypes.c_int(h), ctypes.c_int(w), _p(bits), _p(blk)) != 0:
+        raise ValueError("a category exceeds the baseline Huffman tables")
+    return bits, blk
+
+
+def zigzag() -> np.ndarray:
+    zz = np.zeros(64, np.int32)
+    lib().oracle_zigzag(_p(zz))
+    return zz
+
+
+def jpeg_ac_len(sym: int) -> int:
+    return int(lib().oracle_jpeg_ac_len(ctypes.c_int(sym)))
+
+
+def jpeg_dc_len(cat: int) -> int:
+    return int(lib().oracle_jpeg_dc_len(ctypes.c_int(cat)))

@@ -921,3 +921,140 @@ int oracle_dwt53_inverse(const int16_t* coef, int h, int w, int levels, int16_t*
     free(col);
     return 0;
 }
+
+/* ------------------------------------------------------------------ base-layer entropy coding
+ * Sec. IV codes the base layer with JPEG.  The base round trip above models
+ * only what changes S; its quantised levels are also what a baseline JPEG
+ * encoder entropy-codes (T.81 Annex F.1.2), so their coded size gives the
+ * base layer's rate.  Each colour plane is its own single-component scan
+ * (reading 4), blocks in raster order, with the typical luminance Huffman
+ * tables of T.81 Annex K.3 (Tables K.3 and K.5):
+ *   DC: diff = level_DC - level_DC of the previous block of the plane (0
+ *       before the first); category SSSS = bit length of |diff|; cost =
+ *       length of the DC code of SSSS + SSSS extra bits;
+ *   AC: zigzag order k = 1..63; a run of r zeros before a nonzero level c
+ *       costs, for every 16 zeros beyond 15, one ZRL code (symbol 0xF0), then
+ *       the code of symbol (r mod 16) << 4 | SSSS(c) plus SSSS extra bits;
+ *       zeros after the last nonzero level cost one EOB code (symbol 0x00).
+ * The size is the sum of code lengths and extra bits: the entropy-coded
+ * data before byte stuffing, padding and markers.
+ * Levels layout: levels3[(c * bh + by) * bw + bx][64], bh = ceil(h / 8),
+ * bw = ceil(w / 8); within a block, coefficient (v vertical, u horizontal
+ * frequency) at u * 8 + v. */
+
+/* Code lengths of Table K.3 (DC luminance), by category 0..11. */
+static const int jpeg_dc_len[12] = {2, 3, 3, 3, 3, 3, 4, 5, 6, 7, 8, 9};
+
+/* Table K.5 (AC luminance): the symbols with codes shorter than 16 bits, in
+ * the table's order of increasing length, with their lengths; every other
+ * symbol (r << 4 | s, s = 1..10) has a 16-bit code. */
+static const uint8_t jpeg_ac_short_sym[37] = {
+    0x01, 0x02, 0x03, 0x00, 0x04, 0x11, 0x05, 0x12, 0x21, 0x31, 0x41, 0x06, 0x13,
+    0x51, 0x61, 0x07, 0x22, 0x71, 0x14, 0x32, 0x81, 0x91, 0xa1, 0x08, 0x23, 0x42,
+    0xb1, 0xc1, 0x15, 0x52, 0xd1, 0xf0, 0x24, 0x33, 0x62, 0x72, 0x82};
+static const uint8_t jpeg_ac_short_len[37] = {
+    2, 2, 3, 4, 4, 4, 5, 5, 5, 6, 6, 7, 7, 7, 7, 8, 8, 8, 9, 9, 9, 9, 9,
+    10, 10, 10, 10, 10, 11, 11, 11, 11, 12, 12, 12, 12, 15};
+
+/* Code length of AC symbol `sym`, 0 for a symbol the table does not have. */
+int oracle_jpeg_ac_len(int sym)
+{
+    for (int i = 0; i < 37; ++i)
+        if (jpeg_ac_short_sym[i] == sym) return jpeg_ac_short_len[i];
+    int s = sym & 15;
+    return (s >= 1 && s <= 10) ? 16 : 0;
+}
+
+int oracle_jpeg_dc_len(int cat) { return cat >= 0 && cat <= 11 ? jpeg_dc_len[cat] : 0; }
+
+/* Natural index (v * 8 + u) of zigzag position k (T.81 Figure A.6): the
+ * anti-diagonals s = u + v in turn, v rising on odd s and falling on even s. */
+void oracle_zigzag(int32_t* zz)
+{
+    int k = 0;
+    for (int s = 0; s <= 14; ++s) {
+        int vlo = s - 7 > 0 ? s - 7 : 0, vhi = s < 7 ? s : 7;
+        if (s & 1)
+            for (int v = vlo; v <= vhi; ++v) zz[k++] = v * 8 + (s - v);
+        else
+            for (int v = vhi; v >= vlo; --v) zz[k++] = v * 8 + (s - v);
+    }
+}
+
+static int bitlen(int a) { int n = 0; while (a) { ++n; a >>= 1; } return n; }
+
+/* The quantised levels of the base round trip (same blocks, transform and
+ * quantiser as oracle_base_roundtrip).  Returns -1 for a bad quality. */
+int oracle_base_levels(const uint8_t* sdr3, int h, int w, int quality, int16_t* levels3)
+{
+    if (quality < 1 || quality > 100) return -1;
+    int32_t Q[64];
+    oracle_quant_table(quality, Q);
+    int64_t n_px = (int64_t)h * w;
+    int bh = (h + 7) / 8, bw = (w + 7) / 8;
+    for (int c = 0; c < 3; ++c) {
+        const uint8_t* in = sdr3 + c * n_px;
+        for (int by = 0; by < bh; ++by)
+            for (int bx = 0; bx < bw; ++bx) {
+                int32_t X[64], F[64], Fq[64];
+                for (int y = 0; y < 8; ++y)
+                    for (int x = 0; x < 8; ++x) {
+                        int yy = 8 * by + y < h ? 8 * by + y : h - 1;
+                        int xx = 8 * bx + x < w ? 8 * bx + x : w - 1;
+                        X[y * 8 + x] = (int32_t)in[(int64_t)yy * w + xx] - 128;
+                    }
+                oracle_fdct_block(X, F);
+                oracle_quant_dequant_block(F, Q, Fq);
+                int16_t* L = levels3 + (((int64_t)c * bh + by) * bw + bx) * 64;
+                for (int v = 0; v < 8; ++v)
+                    for (int u = 0; u < 8; ++u) L[u * 8 + v] = (int16_t)(Fq[v * 8 + u] / Q[v * 8 + u]);
+            }
+    }
+    return 0;
+}
+
+/* Entropy-coded bits of each plane (bits3[3]) and of each block
+ * (block_bits[(c * bh + by) * bw + bx], may be NULL).  Returns -1 when a
+ * category exceeds the baseline tables (DC 11, AC 10). */
+int oracle_jpeg_bits(const int16_t* levels3, int h, int w, uint64_t* bits3, uint32_t* block_bits)
+{
+    int32_t zz[64];
+    oracle_zigzag(zz);
+    int bh = (h + 7) / 8, bw = (w + 7) / 8;
+    for (int c = 0; c < 3; ++c) {
+        uint64_t total = 0;
+        int pred = 0;
+        for (int64_t b = 0; b < (int64_t)bh * bw; ++b) {
+            const int16_t* L = levels3 + ((int64_t)c * bh * bw + b) * 64;
+            uint32_t bits = 0;
+            int diff = L[0] - pred;
+            pred = L[0];
+            int cat = bitlen(diff < 0 ? -diff : diff);
+            if (cat > 11) return -1;
+            bits += (uint32_t)(jpeg_dc_len[cat] + cat);
+            int run = 0;
+            for (int k = 1; k < 64; ++k) {
+                int nat = zz[k];
+                int v = nat / 8, u = nat % 8;
+                int lv = L[u * 8 + v];
+                if (lv == 0) {
+                    ++run;
+                    continue;
+                }
+                while (run > 15) {
+                    bits += (uint32_t)oracle_jpeg_ac_len(0xF0);
+                    run -= 16;
+                }
+                int s = bitlen(lv < 0 ? -lv : lv);
+                if (s > 10) return -1;
+                bits += (uint32_t)(oracle_jpeg_ac_len((run << 4) | s) + s);
+                run = 0;
+            }
+            if (run > 0) bits += (uint32_t)oracle_jpeg_ac_len(0x00);
+            if (block_bits) block_bits[(int64_t)c * bh * bw + b] = bits;
+            total += bits;
+        }
+        bits3[c] = total;
+    }
+    return 0;
+}
