@@ -45,7 +45,7 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
 TRAFFIC = {"slr_fit": {"bytes_per_px": 22093696 / (2048 * 1536), "sha": "b2c3817c7b238336"},
-           "sdri_base_roundtrip": {"bytes_per_px": 12650624 / (2048 * 1536), "sha": "1752dce12ad5ca2d"}}
+           "sdri_base_roundtrip": {"bytes_per_px": 12651136 / (2048 * 1536), "sha": "35ee295bb84d74b9"}}
 # The base round trip is bound by instruction issue, not by memory: its
 # roofline counts the arithmetic operations its definition needs per pixel
 # (tone mapping 24; four 8-point integer DCT passes per channel, 36 butterfly
@@ -541,6 +541,48 @@ def enhancement_coder(c, rgbe, qualities, n, args, flush, stream) -> dict:
                        "wavelet": {"coded_bits_per_px": round(wbits / n, 4), "h0_bits_per_px": round(wh0, 4),
                                    "raw_chunks": raw_chunks, "table_bits": 3 * nb * nres * 15, "us": wus}}
     out["lossless"] = ok
+    out["base_layer"] = base_layer_bits(c, rgbe, qualities, n, args, flush, stream, out)
+    return out
+
+
+def base_layer_bits(c, rgbe, qualities, n, args, flush, stream, enh) -> dict:
+    """The base layer's coded size at each quality: the quantised levels of
+    the round trip (sdri_base_levels) and the JPEG baseline Huffman size of
+    their coding (jpeg_huffman_bits, luminance tables of T.81 Annex K.3,
+    entropy-coded bits before byte stuffing and markers), and the total with
+    the enhancement layer's wavelet form, in bits per pixel; device times by
+    CUDA events around each call (L2 flushed between repetitions)."""
+    import numpy as np
+    import torch
+
+    from paper_2309_11072_gb300 import native
+
+    h, w = c.h, c.w
+    bh, bw = (h + 7) // 8, (w + 7) // 8
+    levels = torch.empty(3 * bh * bw * 64, dtype=torch.int16, device="cuda")
+    s3 = torch.empty_like(c.s3)
+    bits = torch.empty(3, dtype=torch.int64, device="cuda")
+    out = {"coder": "JPEG baseline Huffman (T.81 Annex K.3 luminance tables), each plane its own scan; "
+                    "entropy-coded bits without byte stuffing, markers or headers"}
+    for q in qualities:
+        c.encode(rgbe, q)
+        t = {"sdri_base_levels": [], "jpeg_huffman_bits": []}
+        for rep in range(args.warmup + args.steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            native.sdri_base_levels(c.m3, c.e, h, w, c.stats, q, s3, levels, stream)
+            ev[1].record(stream)
+            native.jpeg_huffman_bits(levels, h, w, bits, None, stream)
+            ev[2].record(stream)
+            flush.zero_()
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                t["sdri_base_levels"].append(ev[0].elapsed_time(ev[1]) * 1e3)
+                t["jpeg_huffman_bits"].append(ev[1].elapsed_time(ev[2]) * 1e3)
+        base = float(bits.cpu().numpy().sum()) / n
+        wav = enh[str(q)]["wavelet"]["coded_bits_per_px"]
+        out[str(q)] = {"base_bits_per_px": round(base, 4), "total_bits_per_px": round(base + wav, 4),
+                       "us": {k: round(statistics.mean(v), 2) for k, v in t.items()}}
     return out
 
 

@@ -152,6 +152,39 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
                     int gf_on, const slrme_params* params, uint32_t* rgbe_out,
                     slrme_stream_t stream);
 
+/* ===================================================================== base-layer entropy coding
+ * Sec. IV codes the base layer with JPEG.  sdri_base_roundtrip models only
+ * what changes S; these two calls give the base layer's coded size: the
+ * quantised levels the round trip computes, and the size of their JPEG
+ * baseline Huffman coding (T.81 Annex F.1.2) with the typical luminance
+ * tables of Annex K.3 (Tables K.3, K.5), each colour plane a single-
+ * component scan of its 8x8 blocks in raster order:
+ *   DC: diff = level_DC - level_DC of the plane's previous block (0 before
+ *       the first), category SSSS = bit length of |diff| (0..11), cost = DC
+ *       code length of SSSS + SSSS;
+ *   AC: zigzag positions 1..63 (T.81 Figure A.6); a nonzero level c after r
+ *       zeros costs floor(r / 16) ZRL codes (symbol 0xF0), then the code of
+ *       ((r mod 16) << 4) | SSSS(c) plus SSSS (1..10); trailing zeros cost
+ *       one EOB code (symbol 0x00).
+ * The size is the entropy-coded data in bits, before byte stuffing,
+ * padding, markers and headers.
+ * Levels layout: int16 [3][bh][bw][64], bh = ceil(h/8), bw = ceil(w/8);
+ * within a block, coefficient (v vertical, u horizontal frequency) at
+ * u*8 + v.  A level beyond the baseline categories (DC difference above
+ * 2047, AC level above 1023 in magnitude) sets bit 2 (value 4) of the
+ * status word and counts its size without a code. */
+
+/* sdri_base_roundtrip (without the SDRI output) that also writes the levels
+ * (levels3 device, 16-byte aligned). */
+int sdri_base_levels(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, int quality,
+                     uint8_t* s_dec3, int16_t* levels3, slrme_stream_t stream);
+
+/* Coded bits of each plane (bits3: uint64 [3], device, 8-byte aligned,
+ * cleared first) and, if block_bits is not NULL, of each block (uint32
+ * [3][bh*bw]).  Asynchronous on `stream`. */
+int jpeg_huffman_bits(const int16_t* levels3, int h, int w, unsigned long long* bits3, uint32_t* block_bits,
+                      slrme_stream_t stream);
+
 /* ===================================================================== enhancement-layer entropy coder
  * The enhancement layer carries the residuals R to the decoder through a
  * reversible coder (Sec. II-A: the enhancement layer's coders must be
@@ -473,7 +506,8 @@ int slrme_host_tables(int32_t* log2_lut, float* gamma, float* kr, float* wr,
 /* Device status word of the current device (synchronous): 0, or a mask of
  * bit 0 (1): a kernel's wait for its own bulk copies gave up after its bound
  *   (the kernel then stopped and its outputs are incomplete);
- * bit 1 (2): the rANS coder met input outside its table or a corrupt stream.
+ * bit 1 (2): the rANS coder met input outside its table or a corrupt stream;
+ * bit 2 (4): jpeg_huffman_bits met a level beyond the baseline categories.
  * clear != 0 resets it. */
 int slrme_device_status(int* status, int clear);
 

@@ -156,7 +156,21 @@ int sdri_base_roundtrip(const uint8_t* m3, const uint8_t* e, int h, int w, const
     if (n == 0) return SLRME_OK;
     REQUIRE(m3 && e && lum_stats && s_dec3, "sdri_base_roundtrip: null pointer");
     REQUIRE(aligned(lum_stats, 8), "sdri_base_roundtrip: lum_stats must be 8-byte aligned");
-    return launch_base(m3, e, h, w, lum_stats, qt, s_dec3, sdr3, (cudaStream_t)stream);
+    return launch_base(m3, e, h, w, lum_stats, qt, s_dec3, sdr3, nullptr, (cudaStream_t)stream);
+}
+
+int sdri_base_levels(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, int quality,
+                     uint8_t* s_dec3, int16_t* levels3, slrme_stream_t stream) {
+    if (!check_size(h, w)) return SLRME_EINVAL;
+    QuantTable qt;
+    REQUIRE(quality >= 1 && quality <= 100, "sdri_base_levels: quality %d outside 1..100", quality);
+    REQUIRE(quant_table(quality, &qt), "sdri_base_levels: quantiser table check failed");
+    const int64_t n = (int64_t)h * w;
+    if (n == 0) return SLRME_OK;
+    REQUIRE(m3 && e && lum_stats && s_dec3 && levels3, "sdri_base_levels: null pointer");
+    REQUIRE(aligned(lum_stats, 8) && aligned(levels3, 16),
+            "sdri_base_levels: lum_stats must be 8-byte and levels3 16-byte aligned");
+    return launch_base(m3, e, h, w, lum_stats, qt, s_dec3, nullptr, levels3, (cudaStream_t)stream);
 }
 
 int slr_fit(const uint8_t* s_dec3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,

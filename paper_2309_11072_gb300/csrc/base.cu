@@ -168,10 +168,15 @@ __device__ __forceinline__ void base_key(const int64_t* __restrict__ stats, cons
 }
 
 // One band task of one image (all 32 lanes): rows y0 .. y0+7, columns xb .. xb+31.
+// kLevels: also store the quantised levels to lv3, block (by, bx) of plane
+// c at ((c * bh + by) * bw + bx) * 64, coefficient (v, u) at u * 8 + v, so a
+// lane's column of a block is one 16-byte store (a separate instantiation,
+// so the plain round trip compiles without it).
+template <bool kLevels = false>
 __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h, int w,
                                           bool fast, int y0, int xb, int lane, const BaseKey& K,
                                           const uint32_t* gcode, int* T, uint8_t* __restrict__ s3,
-                                          uint8_t* __restrict__ sdr3, const uint2* pre) {
+                                          uint8_t* __restrict__ sdr3, const uint2* pre, int16_t* __restrict__ lv3) {
     const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
     const int64_t n = (int64_t)h * w;
     const int J = K.J;
@@ -242,12 +247,24 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         const int Tc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
         int F[8], G[8];
         fdct8(Tc, F, 1 << 14);
+        int L[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const int f = F[v] >> 15;
             const uint32_t a = (uint32_t)(f < 0 ? -f : f);
             const int lvl = (int)__umulhi((a + (uint32_t)(K.qcol[v] >> 1)) << 8, K.qmcol[v]);
-            F[v] = (f < 0 ? -lvl : lvl) * K.qcol[v];
+            L[v] = f < 0 ? -lvl : lvl;
+            F[v] = L[v] * K.qcol[v];
+        }
+        if (kLevels && x0 < w) {
+            const int bh = (h + 7) >> 3, bw = (w + 7) >> 3;
+            const int64_t blk_idx = ((int64_t)c * bh + (y0 >> 3)) * bw + (x0 >> 3);
+            int4 pk;
+            pk.x = (int)(((uint32_t)L[0] & 0xffffu) | ((uint32_t)L[1] << 16));
+            pk.y = (int)(((uint32_t)L[2] & 0xffffu) | ((uint32_t)L[3] << 16));
+            pk.z = (int)(((uint32_t)L[4] & 0xffffu) | ((uint32_t)L[5] << 16));
+            pk.w = (int)(((uint32_t)L[6] & 0xffffu) | ((uint32_t)L[7] << 16));
+            *reinterpret_cast<int4*>(lv3 + blk_idx * 64 + sub * 8) = pk;
         }
         idct8(F, G, 1 << 8);
         __syncwarp();   // every lane has read its column before the rows are written
@@ -299,10 +316,11 @@ __device__ __forceinline__ bool prefetch_band(const uint8_t* __restrict__ m3, co
     return ok;
 }
 
+template <bool kLevels>
 __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
                                                       int h, int w, const int64_t* __restrict__ lum_stats,
                                                       uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3,
-                                                      int fast_io, const QuantTable QT) {
+                                                      int16_t* __restrict__ lv3, int fast_io, const QuantTable QT) {
     __shared__ uint32_t gcode[kGammaWords];
     __shared__ __align__(16) int tile[kWarps][kTileWords];
     __shared__ __align__(16) uint2 pre[kWarps][2][4][32];   // [warp][slot][plane][lane]
@@ -323,8 +341,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict_
         const bool next = tn < tasks && prefetch_band(m3, e, h, w, fast, cols, tn, lane, &pre[warp][slot ^ 1][0][lane]);
         if (!next) cp_async_commit();   // keep one group per band, so "all but the newest" is this band's
         cp_async_wait_prev();
-        base_band(m3, e, h, w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode, tile[warp], s3,
-                  sdr3, have ? &pre[warp][slot][0][lane] : nullptr);
+        base_band<kLevels>(m3, e, h, w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode, tile[warp],
+                           s3, sdr3, have ? &pre[warp][slot][0][lane] : nullptr, lv3);
         t = tn;
         slot ^= 1;
         have = next;
@@ -360,14 +378,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
                           ((uintptr_t)s3 % 8 == 0);
         if ((int64_t)im.h * im.w > 0 && t < bands)
             base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
-                      tile[warp], s3, nullptr, nullptr);
+                      tile[warp], s3, nullptr, nullptr, nullptr);
     }
 }
 
 }  // namespace
 
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, const QuantTable& qt,
-                uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s) {
+                uint8_t* s_dec3, uint8_t* sdr3, int16_t* levels3, cudaStream_t s) {
     const Geometry g = geometry();
     const int64_t n = (int64_t)h * w;
     const bool fast = (w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
@@ -377,7 +395,12 @@ int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t
     const int64_t cap = (int64_t)g.sms * 4;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_base<<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, fast ? 1 : 0, qt);
+    if (levels3)
+        k_base<true><<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, levels3,
+                                                           fast ? 1 : 0, qt);
+    else
+        k_base<false><<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, nullptr,
+                                                            fast ? 1 : 0, qt);
     return cuda_status("sdri_base_roundtrip launch");
 }
 

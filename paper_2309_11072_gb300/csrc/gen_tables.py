@@ -24,6 +24,14 @@ Tables (all built in float64 and rounded once):
                   v is start + ((bits(v) & 0xFFFF) >= t).
 The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
+
+jpeg_tables.inc holds the Huffman code lengths of the base layer's entropy
+coding (T.81 Annex K.3, Tables K.3 and K.5, luminance):
+  kJpegDcLen[c]  = code length of DC category c (0..11; 0 for 12..15)
+  kJpegAcLen[rs] = code length of AC symbol rs = (run << 4) | size: the
+                   table's symbols with codes shorter than 16 bits take the
+                   lengths listed below, every other symbol with size 1..10
+                   (and ZRL, EOB when listed) a 16-bit code, all others 0.
 """
 import math
 import os
@@ -74,6 +82,29 @@ def main():
     out.append(arr("uint8_t", "kGammaStart", start, str, 24))
     out.append(arr("uint32_t", "kGammaCode", code, lambda v: f"0x{v:08x}u", 8))
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tables.inc")
+    with open(path, "w") as fh:
+        fh.write("\n".join(out))
+
+    # Table K.3: DC luminance, code lengths by category 0..11
+    dc = [2, 3, 3, 3, 3, 3, 4, 5, 6, 7, 8, 9] + [0] * 4
+    # Table K.5: AC luminance, the symbols of codes shorter than 16 bits by length
+    short = {2: [0x01, 0x02], 3: [0x03], 4: [0x00, 0x04, 0x11], 5: [0x05, 0x12, 0x21], 6: [0x31, 0x41],
+             7: [0x06, 0x13, 0x51, 0x61], 8: [0x07, 0x22, 0x71], 9: [0x14, 0x32, 0x81, 0x91, 0xa1],
+             10: [0x08, 0x23, 0x42, 0xb1, 0xc1], 11: [0x15, 0x52, 0xd1, 0xf0], 12: [0x24, 0x33, 0x62, 0x72],
+             15: [0x82]}
+    ac = [16 if 1 <= (rs & 15) <= 10 else 0 for rs in range(256)]
+    for length, syms in short.items():
+        for rs in syms:
+            ac[rs] = length
+    valid = {0x00, 0xF0} | {(r << 4) | z for r in range(16) for z in range(1, 11)}
+    assert {rs for rs in range(256) if ac[rs]} == valid
+    assert sum(2.0 ** -ac[rs] for rs in valid) == 1.0 - 2.0 ** -16
+    assert sum(2.0 ** -l for l in dc[:12]) == 1.0 - 2.0 ** -9
+    out = ["// Generated by gen_tables.py -- do not edit.  Huffman code lengths of JPEG's",
+           "// luminance tables (T.81 Annex K.3).  Include after defining SLRME_TABLE.", ""]
+    out.append(arr("uint8_t", "kJpegDcLen", dc, str, 16))
+    out.append(arr("uint8_t", "kJpegAcLen", ac, str, 16))
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "jpeg_tables.inc")
     with open(path, "w") as fh:
         fh.write("\n".join(out))
 

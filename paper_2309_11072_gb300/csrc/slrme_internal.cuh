@@ -95,7 +95,7 @@ int status_word_address(int** out);
 int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e,
                  int64_t* lum_stats, cudaStream_t s);
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
-                const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s);
+                const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, int16_t* levels3, cudaStream_t s);
 int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
                int64_t* bin_sums, slrme_params* params, cudaStream_t s);
 int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w,

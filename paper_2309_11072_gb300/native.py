@@ -48,6 +48,8 @@ _SIGS = {
     "rans_tables_n": [_vp, _i32, _vp, _vp],
     "rans_encode_segments": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
     "rans_decode_segments": [_vp, _vp, _i32, _vp, _vp, _vp, _vp],
+    "sdri_base_levels": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp],
+    "jpeg_huffman_bits": [_vp, _i32, _i32, _vp, _vp, _vp],
     "dwt53_bands": [_i32, _i32, _i32, _vp],
     "dwt53_forward": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "dwt53_inverse": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp],
@@ -180,6 +182,16 @@ def rans_encode(r3, n: int, freq3, words, counts, stream=None) -> None:
 def rans_decode(words, counts, n: int, freq3, r3, stream=None) -> None:
     _check("rans_decode", lib().rans_decode(_ptr(words), _ptr(counts), int(n), _ptr(freq3), _ptr(r3),
                                             _stream(stream)))
+
+
+def sdri_base_levels(m3, e, h: int, w: int, lum_stats, quality: int, s_dec3, levels3, stream=None) -> None:
+    _check("sdri_base_levels", lib().sdri_base_levels(_ptr(m3), _ptr(e), h, w, _ptr(lum_stats), quality, _ptr(s_dec3),
+                                                      _ptr(levels3), _stream(stream)))
+
+
+def jpeg_huffman_bits(levels3, h: int, w: int, bits3, block_bits=None, stream=None) -> None:
+    _check("jpeg_huffman_bits", lib().jpeg_huffman_bits(_ptr(levels3), h, w, _ptr(bits3), _ptr(block_bits),
+                                                        _stream(stream)))
 
 
 def _lengths(lengths):

@@ -183,3 +183,14 @@ def test_dwt_and_segment_bad_arguments_rejected_before_any_gpu_work():
     assert L.rans_decode_segments(72, 64, 1, ln.ctypes.data, 64, 64, None) == EINVAL    # words misaligned
     assert L.rans_tables_n(64, 0, 64, None) == EINVAL
     assert L.rans_segments_words_capacity(0, ln.ctypes.data) == 0
+
+
+def test_base_levels_and_jpeg_bits_reject_bad_arguments():
+    L = native.lib()
+    EINVAL = -1
+    assert L.sdri_base_levels(64, 64, 8, 8, 64, 0, 64, 64, None) == EINVAL      # quality 0
+    assert L.sdri_base_levels(64, 64, 8, 8, 64, 50, 64, None, None) == EINVAL   # no levels
+    assert L.sdri_base_levels(64, 64, 8, 8, 64, 50, 64, 72, None) == EINVAL     # levels not 16-byte aligned
+    assert L.jpeg_huffman_bits(64, 8, 8, None, None, None) == EINVAL           # no bits3
+    assert L.jpeg_huffman_bits(64, 8, 8, 68, None, None) == EINVAL             # bits3 not 8-byte aligned
+    assert L.jpeg_huffman_bits(64, -1, 8, 64, None, None) == EINVAL
