@@ -542,6 +542,62 @@ def enhancement_coder(c, rgbe, qualities, n, args, flush, stream) -> dict:
                                    "raw_chunks": raw_chunks, "table_bits": 3 * nb * nres * 15, "us": wus}}
     out["lossless"] = ok
     out["base_layer"] = base_layer_bits(c, rgbe, qualities, n, args, flush, stream, out)
+    out["quality_sweep"] = quality_sweep(c, rgbe, n, stream)
+    return out
+
+
+def quality_sweep(c, rgbe, n, stream) -> dict:
+    """Bits per pixel against the base layer's JPEG quality Q, in the manner of
+    Fig. 4: the base layer's Huffman-coded levels plus the enhancement layer
+    coded by the wavelet form, with the SLRME (the fitted parameters) and
+    without it (M* = S: slope 1/16 per grey level of x = 16 S*, intercept 0,
+    no restoration), at Q = 10, 20, ..., 100 and 85 (Table I's quality)."""
+    import numpy as np
+    import torch
+
+    from paper_2309_11072_gb300 import codec, native
+
+    h, w = c.h, c.w
+    levels_n = 3
+    nb = 1 + 3 * levels_n
+    lengths = [a * b for a, b in native.dwt53_bands(h, w, levels_n)] * 3
+    bh, bw = (h + 7) // 8, (w + 7) // 8
+    lv = torch.empty(3 * bh * bw * 64, dtype=torch.int16, device="cuda")
+    s3 = torch.empty_like(c.s3)
+    bits3 = torch.empty(3, dtype=torch.int64, device="cuda")
+    coef = torch.empty(3 * n, dtype=torch.int16, device="cuda")
+    bhist = torch.empty(3 * nb * 511, dtype=torch.int32, device="cuda")
+    bfreq = torch.empty_like(bhist)
+    ws = torch.empty(native.dwt53_workspace_bytes(3, h, w), dtype=torch.uint8, device="cuda")
+    nw, nc = native.rans_segments_capacity(lengths)
+    words = torch.empty(nw, dtype=torch.int16, device="cuda")
+    counts = torch.empty(nc, dtype=torch.int32, device="cuda")
+    r_plain = torch.empty_like(c.r3)
+    ident = torch.from_numpy(codec.params_from_numpy(np.full((3, 256), 1 / 16, np.float32),
+                                                     np.zeros((3, 256), np.float32))).cuda()
+
+    def enh_bits(r3):
+        native.dwt53_forward(r3, 3, h, w, levels_n, coef, bhist, ws, stream)
+        native.rans_tables_n(bhist, 3 * nb, bfreq, stream)
+        native.rans_encode_segments(coef, lengths, bfreq, words, counts, stream)
+        cnt = counts.cpu().numpy().view(np.uint32)
+        raw = cnt == 0xFFFFFFFF
+        return (16.0 * cnt[~raw].astype(np.int64).sum() + 16.0 * 8192 * (int(raw.sum()) // 32)) / n
+
+    out = {"form": "base: JPEG baseline Huffman of the quantised levels; enhancement: three-level 5/3 wavelet "
+                   "+ rANS (a table per band); bits per pixel"}
+    native.device_status(clear=True)
+    for q in list(range(10, 101, 10)) + [85]:
+        c.encode(rgbe, q)
+        native.sdri_base_levels(c.m3, c.e, h, w, c.stats, q, s3, lv, stream)
+        native.jpeg_huffman_bits(lv, h, w, bits3, None, stream)
+        base = float(bits3.cpu().numpy().sum()) / n
+        slr = enh_bits(c.r3)
+        native.residual_encode(c.s3, c.m3, c.e, h, w, 0, ident, r_plain, None, stream)
+        plain = enh_bits(r_plain)
+        out[str(q)] = {"base": round(base, 4), "enh_slr": round(slr, 4), "enh_without_slrme": round(plain, 4),
+                       "total_slr": round(base + slr, 4), "total_without_slrme": round(base + plain, 4)}
+    out["status"] = native.device_status(clear=True)
     return out
 
 
