@@ -60,6 +60,11 @@ def lib():
             _lib.oracle_jpeg_bits.restype = ctypes.c_int
             _lib.oracle_jpeg_ac_len.restype = ctypes.c_int
             _lib.oracle_jpeg_dc_len.restype = ctypes.c_int
+            _lib.oracle_jpeg_ac_len_c.restype = ctypes.c_int
+            _lib.oracle_jpeg_dc_len_c.restype = ctypes.c_int
+            _lib.oracle_jpeg_bits_planes.restype = ctypes.c_int
+            _lib.oracle_base_roundtrip_420.restype = ctypes.c_int
+            _lib.oracle_rgb_to_ycc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
             _lib.oracle_dwt53_bands.restype = ctypes.c_int
             _lib.oracle_dwt53_forward.restype = ctypes.c_int
             _lib.oracle_dwt53_inverse.restype = ctypes.c_int
@@ -419,3 +424,57 @@ def jpeg_ac_len(sym: int) -> int:
 
 def jpeg_dc_len(cat: int) -> int:
     return int(lib().oracle_jpeg_dc_len(ctypes.c_int(cat)))
+
+
+def jpeg_ac_len_c(sym: int) -> int:
+    return int(lib().oracle_jpeg_ac_len_c(ctypes.c_int(sym)))
+
+
+def jpeg_dc_len_c(cat: int) -> int:
+    return int(lib().oracle_jpeg_dc_len_c(ctypes.c_int(cat)))
+
+
+def jpeg_bits_planes(levels: np.ndarray, nblocks, chroma):
+    """Bits per plane and per block of planes with nblocks[p] blocks each, plane p with the chrominance
+    tables when chroma[p] (else luminance); levels: the planes' blocks one after another, 64 levels each."""
+    L = np.ascontiguousarray(levels, dtype=np.int16).reshape(-1)
+    nb = np.ascontiguousarray(nblocks, dtype=np.int64)
+    ch = np.ascontiguousarray(chroma, dtype=np.int32)
+    assert L.size == 64 * int(nb.sum())
+    bits = np.zeros(nb.size, np.uint64)
+    blk = np.zeros(int(nb.sum()), np.uint32)
+    if lib().oracle_jpeg_bits_planes(_p(L), ctypes.c_int(nb.size), _p(nb), _p(ch), _p(bits), _p(blk)) != 0:
+        raise ValueError("a category exceeds the baseline Huffman tables")
+    return bits, blk
+
+
+def quant_table_chroma(quality: int) -> np.ndarray:
+    q = np.zeros(64, np.int32)
+    lib().oracle_quant_table_chroma(ctypes.c_int(quality), _p(q))
+    return q.reshape(8, 8)
+
+
+def rgb_to_ycc(rgb3: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(rgb3, dtype=np.uint8)
+    out = np.zeros_like(x)
+    lib().oracle_rgb_to_ycc(_p(x), x[0].size, _p(out))
+    return out
+
+
+def blocks_420(h: int, w: int):
+    """Blocks of the Y plane and of each chroma plane of the 4:2:0 base layer."""
+    hc, wc = (h + 1) // 2, (w + 1) // 2
+    return ((h + 7) // 8) * ((w + 7) // 8), ((hc + 7) // 8) * ((wc + 7) // 8)
+
+
+def base_roundtrip_420(sdr3: np.ndarray, quality: int):
+    """The YCbCr 4:2:0 base layer: decoded RGB planes and the levels (Y blocks, Cb blocks, Cr blocks)."""
+    x = np.ascontiguousarray(sdr3, dtype=np.uint8)
+    _, h, w = x.shape
+    nbY, nbC = blocks_420(h, w)
+    s3 = np.zeros_like(x)
+    lv = np.zeros((nbY + 2 * nbC, 64), np.int16)
+    if lib().oracle_base_roundtrip_420(_p(x), ctypes.c_int(h), ctypes.c_int(w), ctypes.c_int(quality), _p(s3),
+                                       _p(lv)) != 0:
+        raise ValueError("quality must be in 1..100")
+    return s3, lv

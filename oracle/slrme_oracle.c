@@ -1013,48 +1013,222 @@ int oracle_base_levels(const uint8_t* sdr3, int h, int w, int quality, int16_t* 
     return 0;
 }
 
-/* Entropy-coded bits of each plane (bits3[3]) and of each block
- * (block_bits[(c * bh + by) * bw + bx], may be NULL).  Returns -1 when a
- * category exceeds the baseline tables (DC 11, AC 10). */
-int oracle_jpeg_bits(const int16_t* levels3, int h, int w, uint64_t* bits3, uint32_t* block_bits)
+/* Table K.4 (DC chrominance) code lengths by category, and Table K.6 (AC
+ * chrominance): its symbols with codes shorter than 16 bits, in the table's
+ * order, with their lengths; the other 119 symbols have 16-bit codes. */
+static const int jpeg_dc_len_c[12] = {2, 2, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11};
+static const uint8_t jpeg_ac_short_sym_c[43] = {
+    0x00, 0x01, 0x02, 0x03, 0x11, 0x04, 0x05, 0x21, 0x31, 0x06, 0x12, 0x41, 0x51, 0x07, 0x61,
+    0x71, 0x13, 0x22, 0x32, 0x81, 0x08, 0x14, 0x42, 0x91, 0xa1, 0xb1, 0xc1, 0x09, 0x23, 0x33,
+    0x52, 0xf0, 0x15, 0x62, 0x72, 0xd1, 0x0a, 0x16, 0x24, 0x34, 0xe1, 0x25, 0xf1};
+static const uint8_t jpeg_ac_short_len_c[43] = {
+    2, 2, 3, 4, 4, 5, 5, 5, 5, 6, 6, 6, 6, 7, 7, 7, 8, 8, 8, 8, 9, 9, 9, 9, 9, 9, 9, 10, 10, 10,
+    10, 10, 11, 11, 11, 11, 12, 12, 12, 12, 14, 15, 15};
+
+/* Code lengths of the chrominance tables (0 for a symbol or category they lack). */
+int oracle_jpeg_ac_len_c(int sym)
+{
+    for (int i = 0; i < 43; ++i)
+        if (jpeg_ac_short_sym_c[i] == sym) return jpeg_ac_short_len_c[i];
+    int s = sym & 15;
+    return (s >= 1 && s <= 10) ? 16 : 0;
+}
+
+int oracle_jpeg_dc_len_c(int cat) { return cat >= 0 && cat <= 11 ? jpeg_dc_len_c[cat] : 0; }
+
+/* Coded bits of one plane's nb blocks (64 levels each, raster order, one
+ * scan) with the luminance (chroma = 0) or chrominance tables.  Returns the
+ * total, or -1 when a category exceeds the baseline tables. */
+static int64_t jpeg_plane_bits(const int16_t* levels, int64_t nb, int chroma, uint32_t* block_bits)
 {
     int32_t zz[64];
     oracle_zigzag(zz);
-    int bh = (h + 7) / 8, bw = (w + 7) / 8;
-    for (int c = 0; c < 3; ++c) {
-        uint64_t total = 0;
-        int pred = 0;
-        for (int64_t b = 0; b < (int64_t)bh * bw; ++b) {
-            const int16_t* L = levels3 + ((int64_t)c * bh * bw + b) * 64;
-            uint32_t bits = 0;
-            int diff = L[0] - pred;
-            pred = L[0];
-            int cat = bitlen(diff < 0 ? -diff : diff);
-            if (cat > 11) return -1;
-            bits += (uint32_t)(jpeg_dc_len[cat] + cat);
-            int run = 0;
-            for (int k = 1; k < 64; ++k) {
-                int nat = zz[k];
-                int v = nat / 8, u = nat % 8;
-                int lv = L[u * 8 + v];
-                if (lv == 0) {
-                    ++run;
-                    continue;
-                }
-                while (run > 15) {
-                    bits += (uint32_t)oracle_jpeg_ac_len(0xF0);
-                    run -= 16;
-                }
-                int s = bitlen(lv < 0 ? -lv : lv);
-                if (s > 10) return -1;
-                bits += (uint32_t)(oracle_jpeg_ac_len((run << 4) | s) + s);
-                run = 0;
+    int64_t total = 0;
+    int pred = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int16_t* L = levels + b * 64;
+        uint32_t bits = 0;
+        int diff = L[0] - pred;
+        pred = L[0];
+        int cat = bitlen(diff < 0 ? -diff : diff);
+        if (cat > 11) return -1;
+        bits += (uint32_t)((chroma ? jpeg_dc_len_c[cat] : jpeg_dc_len[cat]) + cat);
+        int run = 0;
+        for (int k = 1; k < 64; ++k) {
+            int nat = zz[k];
+            int v = nat / 8, u = nat % 8;
+            int lv = L[u * 8 + v];
+            if (lv == 0) {
+                ++run;
+                continue;
             }
-            if (run > 0) bits += (uint32_t)oracle_jpeg_ac_len(0x00);
-            if (block_bits) block_bits[(int64_t)c * bh * bw + b] = bits;
-            total += bits;
+            while (run > 15) {
+                bits += (uint32_t)(chroma ? oracle_jpeg_ac_len_c(0xF0) : oracle_jpeg_ac_len(0xF0));
+                run -= 16;
+            }
+            int sz = bitlen(lv < 0 ? -lv : lv);
+            if (sz > 10) return -1;
+            int sym = (run << 4) | sz;
+            bits += (uint32_t)((chroma ? oracle_jpeg_ac_len_c(sym) : oracle_jpeg_ac_len(sym)) + sz);
+            run = 0;
         }
-        bits3[c] = total;
+        if (run > 0) bits += (uint32_t)(chroma ? oracle_jpeg_ac_len_c(0x00) : oracle_jpeg_ac_len(0x00));
+        if (block_bits) block_bits[b] = bits;
+        total += bits;
     }
+    return total;
+}
+
+/* Entropy-coded bits of each plane (bits3[3]) and of each block
+ * (block_bits[(c * bh + by) * bw + bx], may be NULL), three planes of the
+ * 4:4:4 base layer with the luminance tables.  Returns -1 when a category
+ * exceeds the baseline tables (DC 11, AC 10). */
+int oracle_jpeg_bits(const int16_t* levels3, int h, int w, uint64_t* bits3, uint32_t* block_bits)
+{
+    int64_t nb = (int64_t)((h + 7) / 8) * ((w + 7) / 8);
+    for (int c = 0; c < 3; ++c) {
+        int64_t t = jpeg_plane_bits(levels3 + c * nb * 64, nb, 0, block_bits ? block_bits + c * nb : NULL);
+        if (t < 0) return -1;
+        bits3[c] = (uint64_t)t;
+    }
+    return 0;
+}
+
+/* Planes of any block counts, each with its table class (chroma[p]). */
+int oracle_jpeg_bits_planes(const int16_t* levels, int np, const int64_t* nblocks, const int32_t* chroma,
+                            uint64_t* bits, uint32_t* block_bits)
+{
+    int64_t at = 0;
+    for (int p = 0; p < np; ++p) {
+        int64_t t = jpeg_plane_bits(levels + at * 64, nblocks[p], chroma[p], block_bits ? block_bits + at : NULL);
+        if (t < 0) return -1;
+        bits[p] = (uint64_t)t;
+        at += nblocks[p];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ YCbCr 4:2:0 base layer
+ * The base layer as a default JPEG encoder codes colour: the SDRI converted
+ * to YCbCr (T.871, the JFIF equations), chroma averaged over 2x2 pixels,
+ * each plane through the 8x8 round trip above (Y with the Annex K.1
+ * luminance table, Cb and Cr with the Annex K.2 chrominance table, both
+ * scaled by the IJG quality rule), chroma replicated back over its 2x2
+ * pixels, and converted back to RGB.  READING (fixed point, all rounding
+ * half up by adding half before an arithmetic right shift, then clamping
+ * to 0..255): with weights round(65536 c) of the T.871 coefficients c,
+ *   Y  = (19595 R + 38470 G + 7471 B + 32768) >> 16
+ *   Cb = ((-11058 R - 21710 G + 32768 B + 32768) >> 16) + 128
+ *   Cr = ((32768 R - 27439 G - 5329 B + 32768) >> 16) + 128
+ * chroma sample (i, j) = (sum of pixels (2i..2i+1, 2j..2j+1), edges
+ * replicated, + 2) >> 2, planes of ceil(h/2) x ceil(w/2); back:
+ *   R = Y + ((91881 (Cr - 128) + 32768) >> 16)
+ *   G = Y + ((-22554 (Cb - 128) - 46802 (Cr - 128) + 32768) >> 16)
+ *   B = Y + ((116130 (Cb - 128) + 32768) >> 16). */
+static const int32_t k_chroma_q50[64] = {
+    17, 18, 24, 47, 99, 99, 99, 99,
+    18, 21, 26, 66, 99, 99, 99, 99,
+    24, 26, 56, 99, 99, 99, 99, 99,
+    47, 66, 99, 99, 99, 99, 99, 99,
+    99, 99, 99, 99, 99, 99, 99, 99,
+    99, 99, 99, 99, 99, 99, 99, 99,
+    99, 99, 99, 99, 99, 99, 99, 99,
+    99, 99, 99, 99, 99, 99, 99, 99};
+
+void oracle_quant_table_chroma(int quality, int32_t* q)
+{
+    int s = quality < 50 ? 5000 / quality : 200 - 2 * quality;
+    for (int i = 0; i < 64; ++i) {
+        int v = (k_chroma_q50[i] * s + 50) / 100;
+        q[i] = v < 1 ? 1 : (v > 255 ? 255 : v);
+    }
+}
+
+static int clamp255(int v) { return v < 0 ? 0 : (v > 255 ? 255 : v); }
+
+void oracle_rgb_to_ycc(const uint8_t* rgb3, int64_t n, uint8_t* ycc3)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int r = rgb3[i], g = rgb3[n + i], b = rgb3[2 * n + i];
+        ycc3[i] = (uint8_t)clamp255((19595 * r + 38470 * g + 7471 * b + 32768) >> 16);
+        ycc3[n + i] = (uint8_t)clamp255(((-11058 * r - 21710 * g + 32768 * b + 32768) >> 16) + 128);
+        ycc3[2 * n + i] = (uint8_t)clamp255(((32768 * r - 27439 * g - 5329 * b + 32768) >> 16) + 128);
+    }
+}
+
+/* One plane (ph x pw) through the 8x8 round trip with steps Q; levels (may
+ * be NULL) as in oracle_base_levels for one plane. */
+static void plane_roundtrip(const uint8_t* in, int ph, int pw, const int32_t* Q, uint8_t* out, int16_t* levels)
+{
+    int bh = (ph + 7) / 8, bw = (pw + 7) / 8;
+    for (int by = 0; by < bh; ++by)
+        for (int bx = 0; bx < bw; ++bx) {
+            int32_t X[64], F[64], Fq[64], Y[64];
+            for (int y = 0; y < 8; ++y)
+                for (int x = 0; x < 8; ++x) {
+                    int yy = 8 * by + y < ph ? 8 * by + y : ph - 1;
+                    int xx = 8 * bx + x < pw ? 8 * bx + x : pw - 1;
+                    X[y * 8 + x] = (int32_t)in[(int64_t)yy * pw + xx] - 128;
+                }
+            oracle_fdct_block(X, F);
+            oracle_quant_dequant_block(F, Q, Fq);
+            if (levels) {
+                int16_t* L = levels + ((int64_t)by * bw + bx) * 64;
+                for (int v = 0; v < 8; ++v)
+                    for (int u = 0; u < 8; ++u) L[u * 8 + v] = (int16_t)(Fq[v * 8 + u] / Q[v * 8 + u]);
+            }
+            oracle_idct_block(Fq, Y);
+            for (int y = 0; y < 8 && 8 * by + y < ph; ++y)
+                for (int x = 0; x < 8 && 8 * bx + x < pw; ++x)
+                    out[(int64_t)(8 * by + y) * pw + 8 * bx + x] = (uint8_t)clamp255(Y[y * 8 + x] + 128);
+        }
+}
+
+/* The 4:2:0 base layer of the SDRI sdr3 (RGB planes) at `quality`: s3
+ * (RGB planes) and, if levels is not NULL, the levels of the Y blocks, then
+ * the Cb blocks, then the Cr blocks (each plane's blocks in raster order).
+ * Returns -1 for a bad quality. */
+int oracle_base_roundtrip_420(const uint8_t* sdr3, int h, int w, int quality, uint8_t* s3, int16_t* levels)
+{
+    if (quality < 1 || quality > 100) return -1;
+    int64_t n = (int64_t)h * w;
+    if (n == 0) return 0;
+    int hc = (h + 1) / 2, wc = (w + 1) / 2;
+    int64_t nc = (int64_t)hc * wc;
+    int32_t QY[64], QC[64];
+    oracle_quant_table(quality, QY);
+    oracle_quant_table_chroma(quality, QC);
+    uint8_t* ycc = malloc(3 * n);
+    uint8_t* cs = malloc(2 * nc);      /* subsampled Cb, Cr */
+    uint8_t* yd = malloc(n);
+    uint8_t* cd = malloc(2 * nc);
+    oracle_rgb_to_ycc(sdr3, n, ycc);
+    for (int c = 0; c < 2; ++c) {
+        const uint8_t* P = ycc + (1 + c) * n;
+        for (int i = 0; i < hc; ++i)
+            for (int j = 0; j < wc; ++j) {
+                int y0 = 2 * i, y1 = 2 * i + 1 < h ? 2 * i + 1 : h - 1;
+                int x0 = 2 * j, x1 = 2 * j + 1 < w ? 2 * j + 1 : w - 1;
+                int sum = P[(int64_t)y0 * w + x0] + P[(int64_t)y0 * w + x1] + P[(int64_t)y1 * w + x0] +
+                          P[(int64_t)y1 * w + x1];
+                cs[c * nc + (int64_t)i * wc + j] = (uint8_t)((sum + 2) >> 2);
+            }
+    }
+    int64_t nbY = (int64_t)((h + 7) / 8) * ((w + 7) / 8), nbC = (int64_t)((hc + 7) / 8) * ((wc + 7) / 8);
+    plane_roundtrip(ycc, h, w, QY, yd, levels);
+    for (int c = 0; c < 2; ++c)
+        plane_roundtrip(cs + c * nc, hc, wc, QC, cd + c * nc, levels ? levels + (nbY + c * nbC) * 64 : NULL);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int64_t i = (int64_t)y * w + x, k = (int64_t)(y / 2) * wc + x / 2;
+            int Y = yd[i], cb = cd[k] - 128, cr = cd[nc + k] - 128;
+            s3[i] = (uint8_t)clamp255(Y + ((91881 * cr + 32768) >> 16));
+            s3[n + i] = (uint8_t)clamp255(Y + ((-22554 * cb - 46802 * cr + 32768) >> 16));
+            s3[2 * n + i] = (uint8_t)clamp255(Y + ((116130 * cb + 32768) >> 16));
+        }
+    free(ycc);
+    free(cs);
+    free(yd);
+    free(cd);
     return 0;
 }
