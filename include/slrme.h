@@ -185,6 +185,36 @@ int sdri_base_levels(const uint8_t* m3, const uint8_t* e, int h, int w, const in
 int jpeg_huffman_bits(const int16_t* levels3, int h, int w, unsigned long long* bits3, uint32_t* block_bits,
                       slrme_stream_t stream);
 
+/* Sizes of any planes of levels (up to 4): plane p has nblocks[p] blocks
+ * (host array), its blocks following those of planes 0..p-1 in `levels`,
+ * coded with the chrominance tables of Annex K.3 (Tables K.4, K.6) when
+ * chroma[p] = 1 (host array) and the luminance tables when 0.  bits: uint64
+ * [nplanes] (device, cleared first); block_bits (may be NULL): uint32 per
+ * block in the same order. */
+int jpeg_huffman_bits_planes(const int16_t* levels, int nplanes, const int64_t* nblocks, const int32_t* chroma,
+                             unsigned long long* bits, uint32_t* block_bits, slrme_stream_t stream);
+
+/* The base layer with a default JPEG encoder's colour handling (YCbCr 4:2:0):
+ * the tone-mapped SDRI converted to YCbCr by T.871's equations in 16-bit
+ * fixed point (weights round(65536 c), rounded half up, clamped):
+ *   Y  = (19595 R + 38470 G + 7471 B + 32768) >> 16
+ *   Cb = ((-11058 R - 21710 G + 32768 B + 32768) >> 16) + 128
+ *   Cr = ((32768 R - 27439 G - 5329 B + 32768) >> 16) + 128,
+ * chroma averaged over 2x2 pixels ((sum + 2) >> 2, edges replicated) into
+ * planes of ceil(h/2) x ceil(w/2), each plane through the 8x8 round trip of
+ * sdri_base_roundtrip (Y with Table K.1, Cb and Cr with Table K.2, both
+ * IJG-scaled), chroma replicated back over its 2x2 pixels, and
+ *   R = Y + ((91881 (Cr - 128) + 32768) >> 16)
+ *   G = Y + ((-22554 (Cb - 128) - 46802 (Cr - 128) + 32768) >> 16)
+ *   B = Y + ((116130 (Cb - 128) + 32768) >> 16), clamped, into s_dec3.
+ * levels (may be NULL, 16-byte aligned): the Y plane's blocks, then Cb's,
+ * then Cr's (each in raster order, 64 levels per block as above), for
+ * jpeg_huffman_bits_planes with chroma = {0, 1, 1}.  ws: device workspace of
+ * sdri_base_420_workspace_bytes(h, w) bytes.  h <= 131070. */
+size_t sdri_base_420_workspace_bytes(int h, int w);
+int sdri_base_roundtrip_420(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                            int quality, uint8_t* s_dec3, int16_t* levels, void* ws, slrme_stream_t stream);
+
 /* ===================================================================== enhancement-layer entropy coder
  * The enhancement layer carries the residuals R to the decoder through a
  * reversible coder (Sec. II-A: the enhancement layer's coders must be

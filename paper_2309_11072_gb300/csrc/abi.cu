@@ -43,10 +43,17 @@ static const int kAnnexK1[64] = {
     18, 22, 37, 56, 68, 109, 103, 77,   24, 35, 55, 64, 81, 104, 113, 92,
     49, 64, 78, 87, 103, 121, 120, 101, 72, 92, 95, 98, 112, 100, 103, 99};
 
-static bool build_quant_table(int quality, QuantTable* out) {
+// ITU-T T.81 Annex K, Table K.2 (chrominance), row-major.
+static const int kAnnexK2[64] = {
+    17, 18, 24, 47, 99, 99, 99, 99,     18, 21, 26, 66, 99, 99, 99, 99,
+    24, 26, 56, 99, 99, 99, 99, 99,     47, 66, 99, 99, 99, 99, 99, 99,
+    99, 99, 99, 99, 99, 99, 99, 99,     99, 99, 99, 99, 99, 99, 99, 99,
+    99, 99, 99, 99, 99, 99, 99, 99,     99, 99, 99, 99, 99, 99, 99, 99};
+
+static bool build_quant_table(int quality, const int* base, QuantTable* out) {
     const int scale = quality < 50 ? 5000 / quality : 200 - 2 * quality;
     for (int i = 0; i < 64; ++i) {
-        int v = (kAnnexK1[i] * scale + 50) / 100;
+        int v = (base[i] * scale + 50) / 100;
         v = v < 1 ? 1 : (v > 255 ? 255 : v);
         out->q[i] = v;
         out->qm[i] = (uint32_t)(((1u << 24) + (uint32_t)v - 1u) / (uint32_t)v);   // ceil(2^24 / v)
@@ -60,16 +67,28 @@ static bool build_quant_table(int quality, QuantTable* out) {
     return true;
 }
 
+static bool cached_table(int quality, const int* base, QuantTable* cache, int* state, std::mutex& mu,
+                         QuantTable* out) {
+    if (quality < 1 || quality > 100) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (state[quality] == 0) state[quality] = build_quant_table(quality, base, &cache[quality]) ? 1 : -1;
+    if (state[quality] < 0) return false;
+    *out = cache[quality];
+    return true;
+}
+
 bool quant_table(int quality, QuantTable* out) {
     static QuantTable cache[101];
     static int state[101];   // 0 = not built, 1 = valid, -1 = failed check
     static std::mutex mu;
-    if (quality < 1 || quality > 100) return false;
-    std::lock_guard<std::mutex> lock(mu);
-    if (state[quality] == 0) state[quality] = build_quant_table(quality, &cache[quality]) ? 1 : -1;
-    if (state[quality] < 0) return false;
-    *out = cache[quality];
-    return true;
+    return cached_table(quality, kAnnexK1, cache, state, mu, out);
+}
+
+bool quant_table_chroma(int quality, QuantTable* out) {
+    static QuantTable cache[101];
+    static int state[101];
+    static std::mutex mu;
+    return cached_table(quality, kAnnexK2, cache, state, mu, out);
 }
 
 Geometry geometry() {
@@ -157,6 +176,28 @@ int sdri_base_roundtrip(const uint8_t* m3, const uint8_t* e, int h, int w, const
     REQUIRE(m3 && e && lum_stats && s_dec3, "sdri_base_roundtrip: null pointer");
     REQUIRE(aligned(lum_stats, 8), "sdri_base_roundtrip: lum_stats must be 8-byte aligned");
     return launch_base(m3, e, h, w, lum_stats, qt, s_dec3, sdr3, nullptr, (cudaStream_t)stream);
+}
+
+size_t sdri_base_420_workspace_bytes(int h, int w) {
+    if (h < 0 || w < 0) return 0;
+    const size_t n = (size_t)h * w, nc = (size_t)((h + 1) / 2) * ((w + 1) / 2);
+    return (n + 2 * nc + 255) & ~(size_t)255;
+}
+
+int sdri_base_roundtrip_420(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                            int quality, uint8_t* s_dec3, int16_t* levels, void* ws, slrme_stream_t stream) {
+    if (!check_size(h, w)) return SLRME_EINVAL;
+    REQUIRE(h <= 65535 * 2, "sdri_base_roundtrip_420: h must be at most 131070");
+    QuantTable qy, qc;
+    REQUIRE(quality >= 1 && quality <= 100, "sdri_base_roundtrip_420: quality %d outside 1..100", quality);
+    REQUIRE(quant_table(quality, &qy) && quant_table_chroma(quality, &qc),
+            "sdri_base_roundtrip_420: quantiser table check failed");
+    const int64_t n = (int64_t)h * w;
+    if (n == 0) return SLRME_OK;
+    REQUIRE(m3 && e && lum_stats && s_dec3 && ws, "sdri_base_roundtrip_420: null pointer");
+    REQUIRE(aligned(lum_stats, 8) && aligned(levels, 16),
+            "sdri_base_roundtrip_420: lum_stats must be 8-byte and levels 16-byte aligned");
+    return launch_base_420(m3, e, h, w, lum_stats, qy, qc, s_dec3, levels, (uint8_t*)ws, (cudaStream_t)stream);
 }
 
 int sdri_base_levels(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, int quality,

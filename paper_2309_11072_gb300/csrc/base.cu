@@ -146,6 +146,24 @@ __device__ __forceinline__ void load_gamma(uint32_t* code) {
     __syncthreads();
 }
 
+// The tone-mapping operator of one pixel (Sec. II-B with Sec. IV's
+// Reinhard operator): the three display codes of mantissas (mr, mg, mb) and
+// exponent E, computed for every pixel and zeroed where E = 0 (no branch).
+__device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, float kr, float wr,
+                                          const uint32_t* gcode, int& r, int& g, int& b) {
+    const int yq = 2126 * (2 * mr + 1) + 7152 * (2 * mg + 1) + 722 * (2 * mb + 1);
+    int d = E - 137 - J;
+    d = d < -100 ? -100 : (d > 100 ? 100 : d);
+    const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
+    const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float(yq)), p2d);
+    const float den = __fadd_rn(1.0f, L);
+    const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
+    const int keep = E == 0 ? 0 : -1;
+    r = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr + 1)), gcode + 1) & keep;
+    g = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg + 1)), gcode + 1) & keep;
+    b = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb + 1)), gcode + 1) & keep;
+}
+
 // Key and quantiser state of one image, as a lane needs it.
 struct BaseKey {
     int J;
@@ -201,21 +219,7 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         }
         int sdr[3][8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            // computed for every pixel, then zeroed where E = 0 (no branch)
-            const int E = ee[i];
-            const int yq = 2126 * (2 * mr[i] + 1) + 7152 * (2 * mg[i] + 1) + 722 * (2 * mb[i] + 1);
-            int d = E - 137 - J;
-            d = d < -100 ? -100 : (d > 100 ? 100 : d);
-            const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
-            const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float(yq)), p2d);
-            const float den = __fadd_rn(1.0f, L);
-            const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
-            const int keep = E == 0 ? 0 : -1;
-            sdr[0][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr[i] + 1)), gcode + 1) & keep;
-            sdr[1][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg[i] + 1)), gcode + 1) & keep;
-            sdr[2][i] = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb[i] + 1)), gcode + 1) & keep;
-        }
+        for (int i = 0; i < 8; ++i) tmo_pixel(mr[i], mg[i], mb[i], ee[i], J, kr, wr, gcode, sdr[0][i], sdr[1][i], sdr[2][i]);
         if (sdr3 && x0 < w) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -383,6 +387,196 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- YCbCr 4:2:0 base layer
+// The base layer with a default JPEG encoder's colour handling: the tone-
+// mapped SDRI in YCbCr (T.871's equations in 16-bit fixed point, rounded
+// half up, clamped), chroma averaged over 2x2 pixels (edges replicated,
+// rounded half up), each plane through the 8x8 round trip (Y with the K.1
+// table, Cb and Cr with K.2), chroma replicated back over its 2x2 pixels and
+// converted to RGB:
+//   Y  = (19595 R + 38470 G + 7471 B + 32768) >> 16
+//   Cb = ((-11058 R - 21710 G + 32768 B + 32768) >> 16) + 128
+//   Cr = ((32768 R - 27439 G - 5329 B + 32768) >> 16) + 128
+//   R = Y + ((91881 (Cr - 128) + 32768) >> 16)
+//   G = Y + ((-22554 (Cb - 128) - 46802 (Cr - 128) + 32768) >> 16)
+//   B = Y + ((116130 (Cb - 128) + 32768) >> 16)
+__device__ __forceinline__ int clamp255(int v) {
+    return min(max(v, 0), 255);
+}
+
+// One thread per 2x2 cell: tone mapping, the colour transform, Y of the
+// cell's pixels and the cell's chroma averages.
+__global__ void __launch_bounds__(256) k_ycc420_fwd(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
+                                                    int h, int w, const int64_t* __restrict__ lum_stats,
+                                                    uint8_t* __restrict__ yp, uint8_t* __restrict__ cbp,
+                                                    uint8_t* __restrict__ crp) {
+    __shared__ uint32_t gcode[kGammaWords];
+    load_gamma(gcode);
+    int J, r;
+    key_from_stats(lum_stats, &J, &r);
+    const float kr = __uint_as_float(kKrBits[r]), wr = __uint_as_float(kWrBits[r]);
+    const int hc = (h + 1) >> 1, wc = (w + 1) >> 1;
+    const int cj = blockIdx.x * 32 + threadIdx.x, ci = blockIdx.y * 8 + threadIdx.y;
+    if (ci >= hc || cj >= wc) return;
+    const int64_t n = (int64_t)h * w;
+    int sum_cb = 0, sum_cr = 0;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+            const int y = min(2 * ci + dy, h - 1), x = min(2 * cj + dx, w - 1);
+            const int64_t i = (int64_t)y * w + x;
+            int R, G, B;
+            tmo_pixel(__ldg(m3 + i), __ldg(m3 + n + i), __ldg(m3 + 2 * n + i), __ldg(e + i), J, kr, wr, gcode, R,
+                      G, B);
+            const int Y = clamp255((19595 * R + 38470 * G + 7471 * B + 32768) >> 16);
+            sum_cb += clamp255(((-11058 * R - 21710 * G + 32768 * B + 32768) >> 16) + 128);
+            sum_cr += clamp255(((32768 * R - 27439 * G - 5329 * B + 32768) >> 16) + 128);
+            if (2 * ci + dy < h && 2 * cj + dx < w) yp[i] = (uint8_t)Y;
+        }
+    cbp[(int64_t)ci * wc + cj] = (uint8_t)((sum_cb + 2) >> 2);
+    crp[(int64_t)ci * wc + cj] = (uint8_t)((sum_cr + 2) >> 2);
+}
+
+// The 8x8 round trip of single planes, in place: plane p (h[p] x w[p]) with
+// the luminance steps for p = 0 and the chrominance steps otherwise; one warp
+// per band of 8 rows x 32 columns as in base_band, without the tone mapping.
+// levels (may be null): plane p's blocks from block lv_off[p], 64 levels
+// each, coefficient (v, u) at u * 8 + v.
+struct Planes420 {
+    uint8_t* p[3];
+    int h[3], w[3];
+    int64_t lv_off[3];
+};
+
+__global__ void __launch_bounds__(kThreads) k_plane_rt(const Planes420 P, const QuantTable QY, const QuantTable QC,
+                                                       int16_t* __restrict__ levels) {
+    __shared__ __align__(16) int tiles[kWarps][4 * 72];
+    const int pl = blockIdx.y;
+    const QuantTable& Q = pl == 0 ? QY : QC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int blk = lane >> 3, sub = lane & 7;
+    int qcol[8];
+    uint32_t qmcol[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        qcol[v] = Q.q[v * 8 + sub];
+        qmcol[v] = Q.qm[v * 8 + sub];
+    }
+    uint8_t* plane = P.p[pl];
+    const int h = P.h[pl], w = P.w[pl];
+    const int cols = (w + 31) >> 5, bw = (w + 7) >> 3;
+    const int64_t tasks = (int64_t)((h + 7) >> 3) * cols;
+    int* T = tiles[warp];
+    for (int64_t t = (int64_t)blockIdx.x * kWarps + warp; t < tasks; t += (int64_t)gridDim.x * kWarps) {
+        const int y0 = (int)(t / cols) * 8, xb = (int)(t % cols) * 32;
+        const int x0 = xb + 8 * blk, y = y0 + sub;
+        {
+            uint8_t px[8];
+            load8(plane, h, w, y, x0, false, px);   // rows and columns past the edge replicate it
+            int X[8], F[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) X[i] = px[i];
+            fdct8(X, F, 1 << 8);
+            F[0] -= 1024 * C4;   // the level shift by -128 (only F[0] sees it)
+            int* tile = T + blk * 72 + sub;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) tile[8 * u] = F[u] >> 9;
+        }
+        __syncwarp();
+        {
+            int* tile = T + blk * 72;
+            const int4 c0 = *reinterpret_cast<const int4*>(tile + 8 * sub);
+            const int4 c1 = *reinterpret_cast<const int4*>(tile + 8 * sub + 4);
+            const int Tc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            int F[8], G[8], L[8];
+            fdct8(Tc, F, 1 << 14);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const int f = F[v] >> 15;
+                const uint32_t a = (uint32_t)(f < 0 ? -f : f);
+                const int lvl = (int)__umulhi((a + (uint32_t)(qcol[v] >> 1)) << 8, qmcol[v]);
+                L[v] = f < 0 ? -lvl : lvl;
+                F[v] = L[v] * qcol[v];
+            }
+            if (levels && x0 < w) {
+                const int64_t b = P.lv_off[pl] + (int64_t)(y0 >> 3) * bw + (x0 >> 3);
+                int4 pk;
+                pk.x = (int)(((uint32_t)L[0] & 0xffffu) | ((uint32_t)L[1] << 16));
+                pk.y = (int)(((uint32_t)L[2] & 0xffffu) | ((uint32_t)L[3] << 16));
+                pk.z = (int)(((uint32_t)L[4] & 0xffffu) | ((uint32_t)L[5] << 16));
+                pk.w = (int)(((uint32_t)L[6] & 0xffffu) | ((uint32_t)L[7] << 16));
+                *reinterpret_cast<int4*>(levels + b * 64 + sub * 8) = pk;
+            }
+            idct8(F, G, 1 << 8);
+            __syncwarp();
+#pragma unroll
+            for (int yy = 0; yy < 8; ++yy) tile[8 * yy + sub] = G[yy] >> 9;
+        }
+        __syncwarp();
+        {
+            const int* tile = T + blk * 72 + 8 * sub;
+            const int4 g0 = *reinterpret_cast<const int4*>(tile);
+            const int4 g1 = *reinterpret_cast<const int4*>(tile + 4);
+            const int G[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            int X[8];
+            idct8(G, X, (1 << 14) + (128 << 15));
+            uint32_t q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = (uint32_t)clamp255(X[i] >> 15);
+            const uint32_t lo = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
+            const uint32_t hi = q[4] | (q[5] << 8) | (q[6] << 16) | (q[7] << 24);
+            if (x0 < w) store8(plane, h, w, y, x0, false, lo, hi);
+        }
+        __syncwarp();
+    }
+}
+
+// Chroma back over its 2x2 pixels and the inverse colour transform.
+__global__ void __launch_bounds__(256) k_ycc420_inv(const uint8_t* __restrict__ yp, const uint8_t* __restrict__ cbp,
+                                                    const uint8_t* __restrict__ crp, int h, int w,
+                                                    uint8_t* __restrict__ s3) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= w || y >= h) return;
+    const int wc = (w + 1) >> 1;
+    const int64_t n = (int64_t)h * w, i = (int64_t)y * w + x, k = (int64_t)(y >> 1) * wc + (x >> 1);
+    const int Y = __ldg(yp + i), cb = (int)__ldg(cbp + k) - 128, cr = (int)__ldg(crp + k) - 128;
+    s3[i] = (uint8_t)clamp255(Y + ((91881 * cr + 32768) >> 16));
+    s3[n + i] = (uint8_t)clamp255(Y + ((-22554 * cb - 46802 * cr + 32768) >> 16));
+    s3[2 * n + i] = (uint8_t)clamp255(Y + ((116130 * cb + 32768) >> 16));
+}
+
+int launch_base_420(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, const QuantTable& qy,
+                    const QuantTable& qc, uint8_t* s_dec3, int16_t* levels, uint8_t* ws, cudaStream_t s) {
+    const int hc = (h + 1) / 2, wc = (w + 1) / 2;
+    const int64_t n = (int64_t)h * w, nc = (int64_t)hc * wc;
+    uint8_t* yp = ws;
+    uint8_t* cbp = ws + n;
+    uint8_t* crp = cbp + nc;
+    k_ycc420_fwd<<<dim3((unsigned)((wc + 31) / 32), (unsigned)((hc + 7) / 8)), dim3(32, 8), 0, s>>>(
+        m3, e, h, w, lum_stats, yp, cbp, crp);
+    Planes420 P;
+    P.p[0] = yp;
+    P.p[1] = cbp;
+    P.p[2] = crp;
+    P.h[0] = h;
+    P.w[0] = w;
+    P.h[1] = P.h[2] = hc;
+    P.w[1] = P.w[2] = wc;
+    const int64_t nbY = (int64_t)((h + 7) / 8) * ((w + 7) / 8), nbC = (int64_t)((hc + 7) / 8) * ((wc + 7) / 8);
+    P.lv_off[0] = 0;
+    P.lv_off[1] = nbY;
+    P.lv_off[2] = nbY + nbC;
+    const int64_t tasks = (int64_t)((h + 7) / 8) * ((w + 31) / 32);
+    int64_t gx = (tasks + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)geometry().sms * 4;
+    gx = gx < 1 ? 1 : (gx > cap ? cap : gx);
+    k_plane_rt<<<dim3((unsigned)gx, 3), kThreads, 0, s>>>(P, qy, qc, levels);
+    k_ycc420_inv<<<dim3((unsigned)((w + 31) / 32), (unsigned)((h + 7) / 8)), dim3(32, 8), 0, s>>>(yp, cbp, crp, h, w,
+                                                                                                  s_dec3);
+    return cuda_status("sdri_base_roundtrip_420 launch");
+}
 
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, const QuantTable& qt,
                 uint8_t* s_dec3, uint8_t* sdr3, int16_t* levels3, cudaStream_t s) {

@@ -26,7 +26,8 @@ The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
 
 jpeg_tables.inc holds the Huffman code lengths of the base layer's entropy
-coding (T.81 Annex K.3, Tables K.3 and K.5, luminance):
+coding (T.81 Annex K.3: Tables K.3 and K.5, luminance; K.4 and K.6,
+chrominance, as kJpegDcLenC and kJpegAcLenC):
   kJpegDcLen[c]  = code length of DC category c (0..11; 0 for 12..15)
   kJpegAcLen[rs] = code length of AC symbol rs = (run << 4) | size: the
                    table's symbols with codes shorter than 16 bits take the
@@ -100,10 +101,26 @@ def main():
     assert {rs for rs in range(256) if ac[rs]} == valid
     assert sum(2.0 ** -ac[rs] for rs in valid) == 1.0 - 2.0 ** -16
     assert sum(2.0 ** -l for l in dc[:12]) == 1.0 - 2.0 ** -9
+    # Table K.4: DC chrominance; Table K.6: AC chrominance (codes shorter than 16 bits by length)
+    dc_c = [2, 2, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11] + [0] * 4
+    short_c = {2: [0x00, 0x01], 3: [0x02], 4: [0x03, 0x11], 5: [0x04, 0x05, 0x21, 0x31],
+               6: [0x06, 0x12, 0x41, 0x51], 7: [0x07, 0x61, 0x71], 8: [0x13, 0x22, 0x32, 0x81],
+               9: [0x08, 0x14, 0x42, 0x91, 0xa1, 0xb1, 0xc1], 10: [0x09, 0x23, 0x33, 0x52, 0xf0],
+               11: [0x15, 0x62, 0x72, 0xd1], 12: [0x0a, 0x16, 0x24, 0x34], 14: [0xe1], 15: [0x25, 0xf1]}
+    ac_c = [16 if 1 <= (rs & 15) <= 10 else 0 for rs in range(256)]
+    for length, syms in short_c.items():
+        for rs in syms:
+            ac_c[rs] = length
+    assert {rs for rs in range(256) if ac_c[rs]} == valid
+    assert sum(2.0 ** -ac_c[rs] for rs in valid) == 1.0 - 2.0 ** -16
+    assert sum(2.0 ** -l for l in dc_c[:12]) == 1.0 - 2.0 ** -11
     out = ["// Generated by gen_tables.py -- do not edit.  Huffman code lengths of JPEG's",
-           "// luminance tables (T.81 Annex K.3).  Include after defining SLRME_TABLE.", ""]
+           "// typical tables (T.81 Annex K.3: luminance K.3, K.5; chrominance K.4, K.6).",
+           "// Include after defining SLRME_TABLE.", ""]
     out.append(arr("uint8_t", "kJpegDcLen", dc, str, 16))
     out.append(arr("uint8_t", "kJpegAcLen", ac, str, 16))
+    out.append(arr("uint8_t", "kJpegDcLenC", dc_c, str, 16))
+    out.append(arr("uint8_t", "kJpegAcLenC", ac_c, str, 16))
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "jpeg_tables.inc")
     with open(path, "w") as fh:
         fh.write("\n".join(out))

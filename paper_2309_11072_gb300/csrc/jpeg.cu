@@ -18,6 +18,7 @@
 // sums by warp reduction and one 64-bit atomic per warp.
 #include <stdint.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "slrme_internal.cuh"
@@ -53,6 +54,15 @@ __device__ __forceinline__ int bitlen(int a) {
 constexpr int kStatusJpeg = 4;   // bit 2 of the status word: a level beyond the baseline categories
 
 // AC position K (a compile-time index into the block's registers).
+// Planes to size: plane p has nblocks[p] blocks from block first[p] of the
+// levels array, coded with the chrominance tables when chroma[p].
+constexpr int kMaxPlanes = 4;
+struct JpegPlanes {
+    int n;
+    int64_t first[kMaxPlanes], nblocks[kMaxPlanes];
+    int chroma[kMaxPlanes];
+};
+
 template <int K>
 __device__ __forceinline__ void ac_step(const int16_t (&lv)[64], const uint8_t* aclen, int& run, uint32_t& bits,
                                         bool& bad) {
@@ -76,20 +86,22 @@ __device__ __forceinline__ void ac_steps(std::integer_sequence<int, K...>, const
     (ac_step<K + 1>(lv, aclen, run, bits, bad), ...);
 }
 
-__global__ void __launch_bounds__(256) k_jpeg_bits(const int16_t* __restrict__ lv3, int64_t blocks_per_plane,
+__global__ void __launch_bounds__(256) k_jpeg_bits(const int16_t* __restrict__ lv, const JpegPlanes P,
                                                    unsigned long long* __restrict__ bits3,
                                                    uint32_t* __restrict__ block_bits, int* status) {
     __shared__ uint8_t aclen[256];
     __shared__ uint8_t dclen[16];
-    aclen[threadIdx.x] = kJpegAcLen[threadIdx.x];
-    if (threadIdx.x < 16) dclen[threadIdx.x] = kJpegDcLen[threadIdx.x];
-    __syncthreads();
     const int c = blockIdx.y;
+    const bool chroma = P.chroma[c] != 0;
+    aclen[threadIdx.x] = chroma ? kJpegAcLenC[threadIdx.x] : kJpegAcLen[threadIdx.x];
+    if (threadIdx.x < 16) dclen[threadIdx.x] = chroma ? kJpegDcLenC[threadIdx.x] : kJpegDcLen[threadIdx.x];
+    __syncthreads();
+    const int64_t blocks_per_plane = P.nblocks[c];
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bits = 0;
     bool bad = false;
     if (b < blocks_per_plane) {
-        const int16_t* L = lv3 + ((int64_t)c * blocks_per_plane + b) * 64;
+        const int16_t* L = lv + (P.first[c] + b) * 64;
         int16_t lv[64];
         const int4* L4 = reinterpret_cast<const int4*>(L);
 #pragma unroll
@@ -110,13 +122,37 @@ __global__ void __launch_bounds__(256) k_jpeg_bits(const int16_t* __restrict__ l
         int run = 0;
         ac_steps(std::make_integer_sequence<int, 63>{}, lv, aclen, run, bits, bad);
         if (run > 0) bits += aclen[0x00];
-        if (block_bits) block_bits[(int64_t)c * blocks_per_plane + b] = bits;
+        if (block_bits) block_bits[P.first[c] + b] = bits;
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusJpeg);
     unsigned long long sum = bits;
 #pragma unroll
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if ((threadIdx.x & 31) == 0 && sum) atomicAdd(bits3 + c, sum);
+}
+
+}  // namespace
+}  // namespace slrme
+
+namespace slrme {
+namespace {
+
+int launch_jpeg(const int16_t* levels, const JpegPlanes& P, unsigned long long* bits, uint32_t* block_bits,
+                cudaStream_t s, const char* who) {
+    int64_t most = 0;
+    for (int p = 0; p < P.n; ++p) most = std::max(most, P.nblocks[p]);
+    if (most > 0 && (!levels || ((uintptr_t)levels & 15u))) {
+        set_error("%s: levels must be non-null and 16-byte aligned", who);
+        return SLRME_EINVAL;
+    }
+    int* status = nullptr;
+    int rc = status_word_address(&status);
+    if (rc) return rc;
+    if (cudaMemsetAsync(bits, 0, P.n * sizeof(unsigned long long), s) != cudaSuccess) return cuda_status(who);
+    if (most == 0) return SLRME_OK;
+    const dim3 grid((unsigned)((most + 255) / 256), (unsigned)P.n);
+    k_jpeg_bits<<<grid, 256, 0, s>>>(levels, P, bits, block_bits, status);
+    return cuda_status(who);
 }
 
 }  // namespace
@@ -130,20 +166,40 @@ extern "C" int jpeg_huffman_bits(const int16_t* levels3, int h, int w, unsigned 
         set_error("jpeg_huffman_bits: need 0 <= h, w, h*w < 2^31, an 8-byte aligned bits3 and 4-byte aligned block_bits");
         return SLRME_EINVAL;
     }
-    const int bh = (h + 7) / 8, bw = (w + 7) / 8;
-    const int64_t blocks = (int64_t)bh * bw;
-    if (blocks > 0 && (!levels3 || ((uintptr_t)levels3 & 15u))) {
-        set_error("jpeg_huffman_bits: levels3 must be non-null and 16-byte aligned");
+    const int64_t blocks = (int64_t)((h + 7) / 8) * ((w + 7) / 8);
+    JpegPlanes P;
+    P.n = 3;
+    for (int p = 0; p < kMaxPlanes; ++p) {
+        P.first[p] = p * blocks;
+        P.nblocks[p] = p < 3 ? blocks : 0;
+        P.chroma[p] = 0;
+    }
+    return launch_jpeg(levels3, P, bits3, block_bits, (cudaStream_t)stream, "jpeg_huffman_bits");
+}
+
+extern "C" int jpeg_huffman_bits_planes(const int16_t* levels, int nplanes, const int64_t* nblocks,
+                                        const int32_t* chroma, unsigned long long* bits, uint32_t* block_bits,
+                                        slrme_stream_t stream) {
+    using namespace slrme;
+    if (nplanes < 1 || nplanes > kMaxPlanes || !nblocks || !chroma || !bits || ((uintptr_t)bits & 7u) ||
+        (block_bits && ((uintptr_t)block_bits & 3u))) {
+        set_error("jpeg_huffman_bits_planes: need 1 <= nplanes <= %d, nblocks and chroma, an 8-byte aligned bits and "
+                  "4-byte aligned block_bits", kMaxPlanes);
         return SLRME_EINVAL;
     }
-    int* status = nullptr;
-    int rc = status_word_address(&status);
-    if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(bits3, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess)
-        return cuda_status("jpeg_huffman_bits clear");
-    if (blocks == 0) return SLRME_OK;
-    const dim3 grid((unsigned)((blocks + 255) / 256), 3);
-    k_jpeg_bits<<<grid, 256, 0, s>>>(levels3, blocks, bits3, block_bits, status);
-    return cuda_status("jpeg_huffman_bits launch");
+    JpegPlanes P;
+    P.n = nplanes;
+    int64_t at = 0;
+    for (int p = 0; p < kMaxPlanes; ++p) {
+        const bool in = p < nplanes;
+        if (in && (nblocks[p] < 0 || nblocks[p] >= (int64_t(1) << 31) / 64 + 1 || (chroma[p] != 0 && chroma[p] != 1))) {
+            set_error("jpeg_huffman_bits_planes: plane %d: bad block count or table class", p);
+            return SLRME_EINVAL;
+        }
+        P.first[p] = at;
+        P.nblocks[p] = in ? nblocks[p] : 0;
+        P.chroma[p] = in ? chroma[p] : 0;
+        at += P.nblocks[p];
+    }
+    return launch_jpeg(levels, P, bits, block_bits, (cudaStream_t)stream, "jpeg_huffman_bits_planes");
 }

@@ -25,7 +25,8 @@ struct QuantTable {
     uint32_t qm[64];
 };
 
-bool quant_table(int quality, QuantTable* out);
+bool quant_table(int quality, QuantTable* out);          // T.81 Table K.1 (luminance), IJG-scaled
+bool quant_table_chroma(int quality, QuantTable* out);   // T.81 Table K.2 (chrominance), IJG-scaled
 
 // ---------------------------------------------------------------- batch plan (device side)
 // One image of a batch.  Its planes start at pixel px of the batch planes:
@@ -96,6 +97,9 @@ int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e,
                  int64_t* lum_stats, cudaStream_t s);
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
                 const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, int16_t* levels3, cudaStream_t s);
+int launch_base_420(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                    const QuantTable& qy, const QuantTable& qc, uint8_t* s_dec3, int16_t* levels, uint8_t* ws,
+                    cudaStream_t s);
 int launch_fit(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
                int64_t* bin_sums, slrme_params* params, cudaStream_t s);
 int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w,

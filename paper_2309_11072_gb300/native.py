@@ -50,6 +50,8 @@ _SIGS = {
     "rans_decode_segments": [_vp, _vp, _i32, _vp, _vp, _vp, _vp],
     "sdri_base_levels": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp],
     "jpeg_huffman_bits": [_vp, _i32, _i32, _vp, _vp, _vp],
+    "jpeg_huffman_bits_planes": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
+    "sdri_base_roundtrip_420": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
     "dwt53_bands": [_i32, _i32, _i32, _vp],
     "dwt53_forward": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
     "dwt53_inverse": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp],
@@ -85,6 +87,8 @@ def lib() -> ctypes.CDLL:
                 fn = getattr(L, name)
                 fn.restype = ctypes.c_int64
                 fn.argtypes = [_i32, _vp]
+            L.sdri_base_420_workspace_bytes.restype = ctypes.c_size_t
+            L.sdri_base_420_workspace_bytes.argtypes = [_i32, _i32]
             L.dwt53_workspace_bytes.restype = ctypes.c_size_t
             L.dwt53_workspace_bytes.argtypes = [_i32, _i32, _i32]
             _lib = L
@@ -192,6 +196,25 @@ def sdri_base_levels(m3, e, h: int, w: int, lum_stats, quality: int, s_dec3, lev
 def jpeg_huffman_bits(levels3, h: int, w: int, bits3, block_bits=None, stream=None) -> None:
     _check("jpeg_huffman_bits", lib().jpeg_huffman_bits(_ptr(levels3), h, w, _ptr(bits3), _ptr(block_bits),
                                                         _stream(stream)))
+
+
+def jpeg_huffman_bits_planes(levels, nblocks, chroma, bits, block_bits=None, stream=None) -> None:
+    import numpy as np
+    nb = np.ascontiguousarray(nblocks, dtype=np.int64)
+    ch = np.ascontiguousarray(chroma, dtype=np.int32)
+    _check("jpeg_huffman_bits_planes", lib().jpeg_huffman_bits_planes(_ptr(levels), int(nb.size), nb.ctypes.data,
+                                                                      ch.ctypes.data, _ptr(bits), _ptr(block_bits),
+                                                                      _stream(stream)))
+
+
+def sdri_base_420_workspace_bytes(h: int, w: int) -> int:
+    return int(lib().sdri_base_420_workspace_bytes(int(h), int(w)))
+
+
+def sdri_base_roundtrip_420(m3, e, h: int, w: int, lum_stats, quality: int, s_dec3, levels, ws, stream=None) -> None:
+    _check("sdri_base_roundtrip_420", lib().sdri_base_roundtrip_420(_ptr(m3), _ptr(e), h, w, _ptr(lum_stats), quality,
+                                                                    _ptr(s_dec3), _ptr(levels), _ptr(ws),
+                                                                    _stream(stream)))
 
 
 def _lengths(lengths):

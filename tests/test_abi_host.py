@@ -194,3 +194,20 @@ def test_base_levels_and_jpeg_bits_reject_bad_arguments():
     assert L.jpeg_huffman_bits(64, 8, 8, None, None, None) == EINVAL           # no bits3
     assert L.jpeg_huffman_bits(64, 8, 8, 68, None, None) == EINVAL             # bits3 not 8-byte aligned
     assert L.jpeg_huffman_bits(64, -1, 8, 64, None, None) == EINVAL
+
+
+def test_420_and_plane_bits_reject_bad_arguments():
+    import numpy as np
+    L = native.lib()
+    EINVAL = -1
+    assert L.sdri_base_roundtrip_420(64, 64, 8, 8, 64, 0, 64, None, 256, None) == EINVAL    # quality 0
+    assert L.sdri_base_roundtrip_420(64, 64, 8, 8, 64, 50, 64, None, None, None) == EINVAL  # no workspace
+    assert L.sdri_base_roundtrip_420(64, 64, 8, 8, 64, 50, 64, 72, 256, None) == EINVAL    # levels misaligned
+    assert L.sdri_base_roundtrip_420(64, 64, 131071, 8, 64, 50, 64, None, 256, None) == EINVAL
+    nb = np.array([4, 1], np.int64)
+    ch = np.array([0, 2], np.int32)
+    assert L.jpeg_huffman_bits_planes(64, 2, nb.ctypes.data, ch.ctypes.data, 64, None, None) == EINVAL  # class 2
+    ch = np.array([0, 1], np.int32)
+    assert L.jpeg_huffman_bits_planes(64, 5, nb.ctypes.data, ch.ctypes.data, 64, None, None) == EINVAL  # 5 planes
+    assert L.jpeg_huffman_bits_planes(64, 2, nb.ctypes.data, ch.ctypes.data, 68, None, None) == EINVAL  # bits
+    assert native.sdri_base_420_workspace_bytes(1536, 2048) == 1536 * 2048 + 2 * 768 * 1024
