@@ -584,8 +584,19 @@ def quality_sweep(c, rgbe, n, stream) -> dict:
         raw = cnt == 0xFFFFFFFF
         return (16.0 * cnt[~raw].astype(np.int64).sum() + 16.0 * 8192 * (int(raw.sum()) // 32)) / n
 
-    out = {"form": "base: JPEG baseline Huffman of the quantised levels; enhancement: three-level 5/3 wavelet "
-                   "+ rANS (a table per band); bits per pixel"}
+    # the YCbCr 4:2:0 base layer: its own levels, sizes, fit and residuals
+    nbY = ((h + 7) // 8) * ((w + 7) // 8)
+    nbC = (((h + 1) // 2 + 7) // 8) * (((w + 1) // 2 + 7) // 8)
+    lv420 = torch.empty((nbY + 2 * nbC) * 64, dtype=torch.int16, device="cuda")
+    ws420 = torch.empty(native.sdri_base_420_workspace_bytes(h, w), dtype=torch.uint8, device="cuda")
+    s420 = torch.empty_like(c.s3)
+    r420 = torch.empty_like(c.r3)
+    sums = torch.empty_like(c.sums)
+    params = torch.empty_like(c.params)
+
+    out = {"form": "base: JPEG baseline Huffman of the quantised levels (4:4:4: each RGB plane with the luminance "
+                   "tables; 4:2:0: Y with the luminance, Cb and Cr with the chrominance tables); enhancement: "
+                   "three-level 5/3 wavelet + rANS (a table per band); bits per pixel"}
     native.device_status(clear=True)
     for q in list(range(10, 101, 10)) + [85]:
         c.encode(rgbe, q)
@@ -595,8 +606,16 @@ def quality_sweep(c, rgbe, n, stream) -> dict:
         slr = enh_bits(c.r3)
         native.residual_encode(c.s3, c.m3, c.e, h, w, 0, ident, r_plain, None, stream)
         plain = enh_bits(r_plain)
+        native.sdri_base_roundtrip_420(c.m3, c.e, h, w, c.stats, q, s420, lv420, ws420, stream)
+        native.jpeg_huffman_bits_planes(lv420, [nbY, nbC, nbC], [0, 1, 1], bits3, None, stream)
+        base420 = float(bits3.cpu().numpy().sum()) / n
+        native.slr_fit(s420, c.m3, c.e, h, w, 1, sums, params, stream)
+        native.residual_encode(s420, c.m3, c.e, h, w, 1, params, r420, None, stream)
+        slr420 = enh_bits(r420)
         out[str(q)] = {"base": round(base, 4), "enh_slr": round(slr, 4), "enh_without_slrme": round(plain, 4),
-                       "total_slr": round(base + slr, 4), "total_without_slrme": round(base + plain, 4)}
+                       "total_slr": round(base + slr, 4), "total_without_slrme": round(base + plain, 4),
+                       "base_420": round(base420, 4), "enh_slr_420": round(slr420, 4),
+                       "total_slr_420": round(base420 + slr420, 4)}
     out["status"] = native.device_status(clear=True)
     return out
 
@@ -605,9 +624,11 @@ def base_layer_bits(c, rgbe, qualities, n, args, flush, stream, enh) -> dict:
     """The base layer's coded size at each quality: the quantised levels of
     the round trip (sdri_base_levels) and the JPEG baseline Huffman size of
     their coding (jpeg_huffman_bits, luminance tables of T.81 Annex K.3,
-    entropy-coded bits before byte stuffing and markers), and the total with
-    the enhancement layer's wavelet form, in bits per pixel; device times by
-    CUDA events around each call (L2 flushed between repetitions)."""
+    entropy-coded bits before byte stuffing and markers), the total with the
+    enhancement layer's wavelet form, and the same base size for the YCbCr
+    4:2:0 layer (sdri_base_roundtrip_420, jpeg_huffman_bits_planes), in bits
+    per pixel; device times by CUDA events around each call (host gaps
+    included, L2 flushed between repetitions)."""
     import numpy as np
     import torch
 
@@ -620,24 +641,35 @@ def base_layer_bits(c, rgbe, qualities, n, args, flush, stream, enh) -> dict:
     bits = torch.empty(3, dtype=torch.int64, device="cuda")
     out = {"coder": "JPEG baseline Huffman (T.81 Annex K.3 luminance tables), each plane its own scan; "
                     "entropy-coded bits without byte stuffing, markers or headers"}
+    nbY = bh * bw
+    nbC = (((h + 1) // 2 + 7) // 8) * (((w + 1) // 2 + 7) // 8)
+    lv420 = torch.empty((nbY + 2 * nbC) * 64, dtype=torch.int16, device="cuda")
+    ws420 = torch.empty(native.sdri_base_420_workspace_bytes(h, w), dtype=torch.uint8, device="cuda")
+    bits420 = torch.empty(3, dtype=torch.int64, device="cuda")
+    names = ("sdri_base_levels", "jpeg_huffman_bits", "sdri_base_roundtrip_420", "jpeg_huffman_bits_planes")
     for q in qualities:
         c.encode(rgbe, q)
-        t = {"sdri_base_levels": [], "jpeg_huffman_bits": []}
+        t = {k: [] for k in names}
         for rep in range(args.warmup + args.steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             ev[0].record(stream)
             native.sdri_base_levels(c.m3, c.e, h, w, c.stats, q, s3, levels, stream)
             ev[1].record(stream)
             native.jpeg_huffman_bits(levels, h, w, bits, None, stream)
             ev[2].record(stream)
+            native.sdri_base_roundtrip_420(c.m3, c.e, h, w, c.stats, q, s3, lv420, ws420, stream)
+            ev[3].record(stream)
+            native.jpeg_huffman_bits_planes(lv420, [nbY, nbC, nbC], [0, 1, 1], bits420, None, stream)
+            ev[4].record(stream)
             flush.zero_()
             torch.cuda.synchronize()
             if rep >= args.warmup:
-                t["sdri_base_levels"].append(ev[0].elapsed_time(ev[1]) * 1e3)
-                t["jpeg_huffman_bits"].append(ev[1].elapsed_time(ev[2]) * 1e3)
+                for i, k in enumerate(names):
+                    t[k].append(ev[i].elapsed_time(ev[i + 1]) * 1e3)
         base = float(bits.cpu().numpy().sum()) / n
         wav = enh[str(q)]["wavelet"]["coded_bits_per_px"]
         out[str(q)] = {"base_bits_per_px": round(base, 4), "total_bits_per_px": round(base + wav, 4),
+                       "base_420_bits_per_px": round(float(bits420.cpu().numpy().sum()) / n, 4),
                        "us": {k: round(statistics.mean(v), 2) for k, v in t.items()}}
     return out
 
