@@ -56,6 +56,10 @@ def lib():
                                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             _lib.oracle_rans_decode_segments.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            _lib.oracle_white_point.restype = ctypes.c_float
+            _lib.oracle_white_point.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+            _lib.oracle_tmo_white.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_float, ctypes.c_void_p]
             _lib.oracle_base_levels.restype = ctypes.c_int
             _lib.oracle_jpeg_bits.restype = ctypes.c_int
             _lib.oracle_jpeg_ac_len.restype = ctypes.c_int
@@ -156,6 +160,22 @@ def tmo(rgbe: np.ndarray, J: int, r: int) -> np.ndarray:
     rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
     sdr3 = np.empty((3,) + rgbe.shape, dtype=np.uint8)
     lib().oracle_tmo(_p(rgbe), ctypes.c_int64(rgbe.size), ctypes.c_int32(J), ctypes.c_int32(r), _p(sdr3))
+    return sdr3
+
+
+def white_point(rgbe: np.ndarray, J: int, r: int) -> np.float32:
+    """The largest scaled luminance L of the image (the white point of the operator's Eq. 4 form)."""
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    return np.float32(lib().oracle_white_point(_p(rgbe), ctypes.c_int64(rgbe.size), ctypes.c_int32(J),
+                                               ctypes.c_int32(r)))
+
+
+def tmo_white(rgbe: np.ndarray, J: int, r: int, l_white: float) -> np.ndarray:
+    """Display codes of Reinhard's operator with white point l_white (float32)."""
+    rgbe = np.ascontiguousarray(rgbe, dtype=np.uint32)
+    sdr3 = np.empty((3,) + rgbe.shape, dtype=np.uint8)
+    lib().oracle_tmo_white(_p(rgbe), ctypes.c_int64(rgbe.size), ctypes.c_int32(J), ctypes.c_int32(r),
+                           ctypes.c_float(l_white), _p(sdr3))
     return sdr3
 
 

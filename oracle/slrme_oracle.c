@@ -208,6 +208,70 @@ void oracle_tmo(const uint32_t* rgbe, int64_t n_px, int32_t J, int32_t r, uint8_
     }
 }
 
+/* Reinhard's operator with a white point (his Eq. 4, the variant of Eq. 3
+ * that maps the luminance L_white to 1): L_d = L (1 + L / L_white^2) / (1 + L).
+ * READING: L_white is the largest scaled luminance L of the image (L as
+ * oracle_tmo computes it, over the pixels with E > 0; Reinhard's own
+ * suggestion), and per pixel, in float32 round-to-nearest,
+ *   H = ((num * (1 + L / (L_white * L_white))) / den)
+ * with num, den and L as in oracle_tmo, each operation rounded once in
+ * that order.  L_white = +inf gives oracle_tmo exactly. */
+static float tmo_L(uint32_t wd, int32_t J, float kr)
+{
+    int E = (int)(wd >> 24);
+    int d = E - 137 - J;
+    if (d < -100) d = -100;
+    if (d > 100) d = 100;
+    return ldexpf(kr * (float)yq_of(wd), d);
+}
+
+float oracle_white_point(const uint32_t* rgbe, int64_t n_px, int32_t J, int32_t r)
+{
+    float t[256], kr[16], wr[16];
+    (void)t;
+    oracle_key_tables(kr, wr);
+    float best = 0.0f;
+    for (int64_t p = 0; p < n_px; ++p) {
+        if ((rgbe[p] >> 24) == 0) continue;
+        float L = tmo_L(rgbe[p], J, kr[r]);
+        if (L > best) best = L;
+    }
+    return best;
+}
+
+void oracle_tmo_white(const uint32_t* rgbe, int64_t n_px, int32_t J, int32_t r, float l_white, uint8_t* sdr3)
+{
+    float t[256], kr[16], wr[16];
+    oracle_gamma_thresholds(t);
+    oracle_key_tables(kr, wr);
+    float lw2 = l_white * l_white;
+    for (int64_t p = 0; p < n_px; ++p) {
+        uint32_t wd = rgbe[p];
+        int E = (int)(wd >> 24);
+        if (E == 0) { sdr3[p] = sdr3[n_px + p] = sdr3[2 * n_px + p] = 0; continue; }
+        int d = E - 137 - J;
+        if (d < -100) d = -100;
+        if (d > 100) d = 100;
+        float L = tmo_L(wd, J, kr[r]);
+        float den = 1.0f + L;
+        float num = ldexpf(wr[r], d);
+        float q = L / lw2;
+        float f = 1.0f + q;
+        float nf = num * f;
+        float H = nf / den;
+        for (int c = 0; c < 3; ++c) {
+            int M = (int)((wd >> (8 * c)) & 255u);
+            float v = H * (float)(2 * M + 1);
+            int lo = 0, hi = 256;            /* count thresholds <= v */
+            while (hi - lo > 1) {
+                int mid = (lo + hi) / 2;
+                if (v >= t[mid]) lo = mid; else hi = mid;
+            }
+            sdr3[(int64_t)c * n_px + p] = (uint8_t)lo;
+        }
+    }
+}
+
 /* ======================================================================
  * Base layer, part 2: the lossy base coder round trip (Sec. IV uses JPEG
  * at quality Q).  Only the transform and quantiser change the decoded

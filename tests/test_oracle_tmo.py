@@ -139,3 +139,33 @@ def test_tmo_close_to_float64_reinhard():
     diff = np.abs(sdr.reshape(3, -1).astype(int) - ref)
     assert diff.max() <= 1
     assert (diff == 0).mean() > 0.99
+
+
+def test_white_point_operator_without_a_white_point_is_the_plain_operator():
+    img = synth.make_rgbe(40, 56, seed=21, lo=-3, hi=5, rects=3, highlights=4)
+    sdr, J, r = _tmo_image(img)
+    assert np.array_equal(O.tmo_white(img, J, r, np.inf), sdr)
+
+
+def test_white_point_operator_close_to_float64_reinhard_eq4_and_brighter():
+    img = synth.make_rgbe(64, 80, seed=13, lo=-3, hi=5, rects=4, highlights=6)
+    sdr, J, r = _tmo_image(img)
+    lw = O.white_point(img, J, r)
+    f = O.rgbe_to_float(img.reshape(-1))
+    y = 0.2126 * f[:, 0] + 0.7152 * f[:, 1] + 0.0722 * f[:, 2]
+    lav = 2.0 ** ((16 * J + r) / 16.0) / 1e4
+    nz = y > 0
+    L = np.where(nz, 0.18 * y / lav, 0.0)
+    # the white point is the largest scaled luminance (to float32 rounding of the operator's L)
+    assert abs(float(lw) / L.max() - 1.0) < 1e-4
+    Ld = L * (1 + L / L.max() ** 2) / (1 + L)
+    assert abs(Ld.max() - 1.0) < 1e-12                # the brightest pixel maps to white
+    ref = np.zeros((3, f.shape[0]))
+    for c in range(3):
+        v = np.where(nz, Ld * f[:, c] / np.where(nz, y, 1), 0.0)
+        ref[c] = np.clip(np.floor(255 * np.power(v, 1 / 2.2) + 0.5), 0, 255)
+    got = O.tmo_white(img, J, r, lw)
+    diff = np.abs(got.reshape(3, -1).astype(int) - ref)
+    assert diff.max() <= 1
+    assert (diff == 0).mean() > 0.99
+    assert (got >= sdr).all() and (got > sdr).any()   # the factor 1 + L / L_white^2 only brightens
