@@ -45,7 +45,7 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
 TRAFFIC = {"slr_fit": {"bytes_per_px": 22093696 / (2048 * 1536), "sha": "b2c3817c7b238336"},
-           "sdri_base_roundtrip": {"bytes_per_px": 12651136 / (2048 * 1536), "sha": "35ee295bb84d74b9"}}
+           "sdri_base_roundtrip": {"bytes_per_px": 12650496 / (2048 * 1536), "sha": "2400ac5ad38254ca"}}
 # The base round trip is bound by instruction issue, not by memory: its
 # roofline counts the arithmetic operations its definition needs per pixel
 # (tone mapping 24; four 8-point integer DCT passes per channel, 36 butterfly

@@ -152,6 +152,23 @@ int residual_decode(const uint8_t* s_dec3, const uint8_t* e, const int16_t* r3, 
                     int gf_on, const slrme_params* params, uint32_t* rgbe_out,
                     slrme_stream_t stream);
 
+/* Reinhard's operator with a white point (his Eq. 4 form: L_d = L (1 + L /
+ * L_white^2) / (1 + L)), a variant of the operator of sdri_base_roundtrip
+ * (Sec. IV names Reinhard's operator without its parameters).
+ * sdri_white_point writes L_white (float, device, 4-byte aligned): the
+ * largest scaled luminance L (as the operator computes it per pixel) over
+ * the pixels with E > 0, 0 for an image without such pixels.
+ * sdri_base_roundtrip_white is sdri_base_roundtrip with that operator: per
+ * pixel, in float32 round-to-nearest, H = (num * (1 + L / (L_white *
+ * L_white))) / den, each operation rounded once in that order (num, den and
+ * L as in the plain operator); an infinite L_white^2 gives the plain
+ * operator. */
+int sdri_white_point(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, float* l_white,
+                     slrme_stream_t stream);
+int sdri_base_roundtrip_white(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                              const float* l_white, int quality, uint8_t* s_dec3, uint8_t* sdr3,
+                              slrme_stream_t stream);
+
 /* ===================================================================== base-layer entropy coding
  * Sec. IV codes the base layer with JPEG.  sdri_base_roundtrip models only
  * what changes S; these two calls give the base layer's coded size: the

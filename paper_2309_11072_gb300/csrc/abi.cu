@@ -178,6 +178,29 @@ int sdri_base_roundtrip(const uint8_t* m3, const uint8_t* e, int h, int w, const
     return launch_base(m3, e, h, w, lum_stats, qt, s_dec3, sdr3, nullptr, (cudaStream_t)stream);
 }
 
+int sdri_white_point(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, float* l_white,
+                     slrme_stream_t stream) {
+    if (!check_size(h, w)) return SLRME_EINVAL;
+    REQUIRE(l_white && aligned(l_white, 4) && lum_stats && aligned(lum_stats, 8),
+            "sdri_white_point: need a 4-byte aligned l_white and 8-byte aligned lum_stats");
+    REQUIRE((int64_t)h * w == 0 || (m3 && e), "sdri_white_point: null image pointer");
+    return launch_white_point(m3, e, h, w, lum_stats, l_white, (cudaStream_t)stream);
+}
+
+int sdri_base_roundtrip_white(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                              const float* l_white, int quality, uint8_t* s_dec3, uint8_t* sdr3,
+                              slrme_stream_t stream) {
+    if (!check_size(h, w)) return SLRME_EINVAL;
+    QuantTable qt;
+    REQUIRE(quality >= 1 && quality <= 100, "sdri_base_roundtrip_white: quality %d outside 1..100", quality);
+    REQUIRE(quant_table(quality, &qt), "sdri_base_roundtrip_white: quantiser table check failed");
+    if ((int64_t)h * w == 0) return SLRME_OK;
+    REQUIRE(m3 && e && lum_stats && s_dec3 && l_white, "sdri_base_roundtrip_white: null pointer");
+    REQUIRE(aligned(lum_stats, 8) && aligned(l_white, 4),
+            "sdri_base_roundtrip_white: lum_stats must be 8-byte and l_white 4-byte aligned");
+    return launch_base_white(m3, e, h, w, lum_stats, l_white, qt, s_dec3, sdr3, (cudaStream_t)stream);
+}
+
 size_t sdri_base_420_workspace_bytes(int h, int w) {
     if (h < 0 || w < 0) return 0;
     const size_t n = (size_t)h * w, nc = (size_t)((h + 1) / 2) * ((w + 1) / 2);

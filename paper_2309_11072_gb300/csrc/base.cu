@@ -146,18 +146,30 @@ __device__ __forceinline__ void load_gamma(uint32_t* code) {
     __syncthreads();
 }
 
-// The tone-mapping operator of one pixel (Sec. II-B with Sec. IV's
-// Reinhard operator): the three display codes of mantissas (mr, mg, mb) and
-// exponent E, computed for every pixel and zeroed where E = 0 (no branch).
-__device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, float kr, float wr,
-                                          const uint32_t* gcode, int& r, int& g, int& b) {
+// The scaled luminance L of one pixel (the operator's input).
+__device__ __forceinline__ float tmo_L(int mr, int mg, int mb, int E, int J, float kr, float* p2d_out) {
     const int yq = 2126 * (2 * mr + 1) + 7152 * (2 * mg + 1) + 722 * (2 * mb + 1);
     int d = E - 137 - J;
     d = d < -100 ? -100 : (d > 100 ? 100 : d);
     const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
-    const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float(yq)), p2d);
+    *p2d_out = p2d;
+    return __fmul_rn(__fmul_rn(kr, small_int_to_float(yq)), p2d);
+}
+
+// The tone-mapping operator of one pixel (Sec. II-B with Sec. IV's
+// Reinhard operator): the three display codes of mantissas (mr, mg, mb) and
+// exponent E, computed for every pixel and zeroed where E = 0 (no branch).
+// kWhite: the operator with a white point (Reinhard's Eq. 4), lw2 = L_white^2:
+// the numerator is multiplied by 1 + L / lw2 before the division.
+template <bool kWhite = false>
+__device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, float kr, float wr,
+                                          const uint32_t* gcode, int& r, int& g, int& b, float lw2 = 0.0f) {
+    float p2d;
+    const float L = tmo_L(mr, mg, mb, E, J, kr, &p2d);
     const float den = __fadd_rn(1.0f, L);
-    const float H = __fdiv_rn(__fmul_rn(wr, p2d), den);
+    float num = __fmul_rn(wr, p2d);
+    if (kWhite) num = __fmul_rn(num, __fadd_rn(1.0f, __fdiv_rn(L, lw2)));
+    const float H = __fdiv_rn(num, den);
     const int keep = E == 0 ? 0 : -1;
     r = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr + 1)), gcode + 1) & keep;
     g = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg + 1)), gcode + 1) & keep;
@@ -190,11 +202,12 @@ __device__ __forceinline__ void base_key(const int64_t* __restrict__ stats, cons
 // c at ((c * bh + by) * bw + bx) * 64, coefficient (v, u) at u * 8 + v, so a
 // lane's column of a block is one 16-byte store (a separate instantiation,
 // so the plain round trip compiles without it).
-template <bool kLevels = false>
+template <bool kLevels = false, bool kWhite = false>
 __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h, int w,
                                           bool fast, int y0, int xb, int lane, const BaseKey& K,
                                           const uint32_t* gcode, int* T, uint8_t* __restrict__ s3,
-                                          uint8_t* __restrict__ sdr3, const uint2* pre, int16_t* __restrict__ lv3) {
+                                          uint8_t* __restrict__ sdr3, const uint2* pre, int16_t* __restrict__ lv3,
+                                          float lw2 = 0.0f) {
     const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
     const int64_t n = (int64_t)h * w;
     const int J = K.J;
@@ -219,7 +232,8 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         }
         int sdr[3][8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) tmo_pixel(mr[i], mg[i], mb[i], ee[i], J, kr, wr, gcode, sdr[0][i], sdr[1][i], sdr[2][i]);
+        for (int i = 0; i < 8; ++i)
+            tmo_pixel<kWhite>(mr[i], mg[i], mb[i], ee[i], J, kr, wr, gcode, sdr[0][i], sdr[1][i], sdr[2][i], lw2);
         if (sdr3 && x0 < w) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -320,11 +334,12 @@ __device__ __forceinline__ bool prefetch_band(const uint8_t* __restrict__ m3, co
     return ok;
 }
 
-template <bool kLevels>
+template <bool kLevels, bool kWhite = false>
 __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
                                                       int h, int w, const int64_t* __restrict__ lum_stats,
                                                       uint8_t* __restrict__ s3, uint8_t* __restrict__ sdr3,
-                                                      int16_t* __restrict__ lv3, int fast_io, const QuantTable QT) {
+                                                      int16_t* __restrict__ lv3, int fast_io, const QuantTable QT,
+                                                      const float* __restrict__ l_white = nullptr) {
     __shared__ uint32_t gcode[kGammaWords];
     __shared__ __align__(16) int tile[kWarps][kTileWords];
     __shared__ __align__(16) uint2 pre[kWarps][2][4][32];   // [warp][slot][plane][lane]
@@ -332,6 +347,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BaseKey K;
     base_key(lum_stats, QT, lane & 7, K);
+    float lw2 = 0.0f;
+    if (kWhite) {
+        const float lw = __ldg(l_white);
+        lw2 = __fmul_rn(lw, lw);
+    }
     const int cols = (w + 31) >> 5;
     const int64_t tasks = (int64_t)((h + 7) >> 3) * cols;
     const int64_t step = (int64_t)gridDim.x * kWarps;
@@ -345,8 +365,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_base(const uint8_t* __restrict_
         const bool next = tn < tasks && prefetch_band(m3, e, h, w, fast, cols, tn, lane, &pre[warp][slot ^ 1][0][lane]);
         if (!next) cp_async_commit();   // keep one group per band, so "all but the newest" is this band's
         cp_async_wait_prev();
-        base_band<kLevels>(m3, e, h, w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode, tile[warp],
-                           s3, sdr3, have ? &pre[warp][slot][0][lane] : nullptr, lv3);
+        base_band<kLevels, kWhite>(m3, e, h, w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
+                                   tile[warp], s3, sdr3, have ? &pre[warp][slot][0][lane] : nullptr, lv3, lw2);
         t = tn;
         slot ^= 1;
         have = next;
@@ -576,6 +596,54 @@ int launch_base_420(const uint8_t* m3, const uint8_t* e, int h, int w, const int
     k_ycc420_inv<<<dim3((unsigned)((w + 31) / 32), (unsigned)((h + 7) / 8)), dim3(32, 8), 0, s>>>(yp, cbp, crp, h, w,
                                                                                                   s_dec3);
     return cuda_status("sdri_base_roundtrip_420 launch");
+}
+
+// The white point: the largest scaled luminance L over the pixels with
+// E > 0, as the float bits (positive floats order like their bits), one
+// atomic per warp.
+__global__ void __launch_bounds__(256) k_white_point(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e,
+                                                     int64_t n, const int64_t* __restrict__ lum_stats,
+                                                     unsigned int* __restrict__ out) {
+    int J, r;
+    key_from_stats(lum_stats, &J, &r);
+    const float kr = __uint_as_float(kKrBits[r]);
+    unsigned int best = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int E = __ldg(e + i);
+        float p2d;
+        const float L = tmo_L(__ldg(m3 + i), __ldg(m3 + n + i), __ldg(m3 + 2 * n + i), E, J, kr, &p2d);
+        if (E != 0) best = max(best, __float_as_uint(L));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
+int launch_white_point(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, float* l_white,
+                       cudaStream_t s) {
+    if (cudaMemsetAsync(l_white, 0, sizeof(float), s) != cudaSuccess) return cuda_status("sdri_white_point clear");
+    const int64_t n = (int64_t)h * w;
+    if (n == 0) return SLRME_OK;
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)geometry().sms * 8;
+    blocks = blocks > cap ? cap : blocks;
+    k_white_point<<<(unsigned)blocks, 256, 0, s>>>(m3, e, n, lum_stats, reinterpret_cast<unsigned int*>(l_white));
+    return cuda_status("sdri_white_point launch");
+}
+
+int launch_base_white(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                      const float* l_white, const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s) {
+    const int64_t n = (int64_t)h * w;
+    const bool fast = (w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
+                      ((uintptr_t)s_dec3 % 8 == 0) && (!sdr3 || (uintptr_t)sdr3 % 8 == 0) && (n % 8 == 0);
+    const int64_t tasks = (int64_t)((h + 7) / 8) * ((w + 31) / 32);
+    int64_t blocks = (tasks + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)geometry().sms * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_base<false, true><<<(unsigned)blocks, kThreads, 0, s>>>(m3, e, h, w, lum_stats, s_dec3, sdr3, nullptr,
+                                                              fast ? 1 : 0, qt, l_white);
+    return cuda_status("sdri_base_roundtrip_white launch");
 }
 
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, const QuantTable& qt,

@@ -97,6 +97,10 @@ int launch_split(const uint32_t* rgbe, int64_t n, uint8_t* m3, uint8_t* e,
                  int64_t* lum_stats, cudaStream_t s);
 int launch_base(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
                 const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, int16_t* levels3, cudaStream_t s);
+int launch_white_point(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats, float* l_white,
+                       cudaStream_t s);
+int launch_base_white(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
+                      const float* l_white, const QuantTable& qt, uint8_t* s_dec3, uint8_t* sdr3, cudaStream_t s);
 int launch_base_420(const uint8_t* m3, const uint8_t* e, int h, int w, const int64_t* lum_stats,
                     const QuantTable& qy, const QuantTable& qc, uint8_t* s_dec3, int16_t* levels, uint8_t* ws,
                     cudaStream_t s);

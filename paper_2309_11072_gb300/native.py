@@ -51,6 +51,8 @@ _SIGS = {
     "sdri_base_levels": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp],
     "jpeg_huffman_bits": [_vp, _i32, _i32, _vp, _vp, _vp],
     "jpeg_huffman_bits_planes": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
+    "sdri_white_point": [_vp, _vp, _i32, _i32, _vp, _vp, _vp],
+    "sdri_base_roundtrip_white": [_vp, _vp, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp],
     "sdri_base_roundtrip_420": [_vp, _vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp],
     "dwt53_bands": [_i32, _i32, _i32, _vp],
     "dwt53_forward": [_vp, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp],
@@ -196,6 +198,18 @@ def sdri_base_levels(m3, e, h: int, w: int, lum_stats, quality: int, s_dec3, lev
 def jpeg_huffman_bits(levels3, h: int, w: int, bits3, block_bits=None, stream=None) -> None:
     _check("jpeg_huffman_bits", lib().jpeg_huffman_bits(_ptr(levels3), h, w, _ptr(bits3), _ptr(block_bits),
                                                         _stream(stream)))
+
+
+def sdri_white_point(m3, e, h: int, w: int, lum_stats, l_white, stream=None) -> None:
+    _check("sdri_white_point", lib().sdri_white_point(_ptr(m3), _ptr(e), h, w, _ptr(lum_stats), _ptr(l_white),
+                                                      _stream(stream)))
+
+
+def sdri_base_roundtrip_white(m3, e, h: int, w: int, lum_stats, l_white, quality: int, s_dec3, sdr3=None,
+                              stream=None) -> None:
+    _check("sdri_base_roundtrip_white", lib().sdri_base_roundtrip_white(_ptr(m3), _ptr(e), h, w, _ptr(lum_stats),
+                                                                        _ptr(l_white), quality, _ptr(s_dec3),
+                                                                        _ptr(sdr3), _stream(stream)))
 
 
 def jpeg_huffman_bits_planes(levels, nblocks, chroma, bits, block_bits=None, stream=None) -> None:

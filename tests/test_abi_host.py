@@ -211,3 +211,12 @@ def test_420_and_plane_bits_reject_bad_arguments():
     assert L.jpeg_huffman_bits_planes(64, 5, nb.ctypes.data, ch.ctypes.data, 64, None, None) == EINVAL  # 5 planes
     assert L.jpeg_huffman_bits_planes(64, 2, nb.ctypes.data, ch.ctypes.data, 68, None, None) == EINVAL  # bits
     assert native.sdri_base_420_workspace_bytes(1536, 2048) == 1536 * 2048 + 2 * 768 * 1024
+
+
+def test_white_point_calls_reject_bad_arguments():
+    L = native.lib()
+    EINVAL = -1
+    assert L.sdri_white_point(64, 64, 8, 8, 64, None, None) == EINVAL            # no output
+    assert L.sdri_white_point(64, 64, 8, 8, 66, 64, None) == EINVAL              # stats misaligned
+    assert L.sdri_base_roundtrip_white(64, 64, 8, 8, 64, None, 50, 64, None, None) == EINVAL   # no white point
+    assert L.sdri_base_roundtrip_white(64, 64, 8, 8, 64, 64, 0, 64, None, None) == EINVAL     # quality 0
