@@ -84,114 +84,83 @@ __device__ __forceinline__ bool chunk_out_of_range(const int16_t* src, int64_t m
 // Each level the removal passes through has all entries above it already cut
 // to it, and at the level T itself it walks the tied entries in symbol order.
 // Since sum f <= M + 511 over at most 511 symbols, T > 32, so no entry
-// reaches 0.  One warp per channel; lane t holds symbols t + 32 i.
-__global__ void __launch_bounds__(32) k_rans_tables(const uint32_t* __restrict__ hist3, uint32_t* __restrict__ freq3) {
-    constexpr int kPer = 16;   // 16 x 32 = 512 >= 511 symbols
-    const int c = blockIdx.x, lane = threadIdx.x;
-    const uint32_t* h = hist3 + c * kNres;
-    uint32_t cnt[kPer], f[kPer];
-    unsigned long long N = 0;
+// reaches 0.  One CTA of 512 threads per table, thread s holding symbol s: every sum,
+// maximum and rank is a block reduction (warp shuffles, then one warp over
+// the 16 warp results).
+constexpr int kTabThreads = 512;
+
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int s = lane + 32 * i;
-        cnt[i] = s < kNres ? h[s] : 0u;
-        N += cnt[i];
-    }
+    for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(kFull, v, o));
+    __syncthreads();   // the previous reduction's readers are done with red
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    v = red[lane & 15];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) N += __shfl_xor_sync(kFull, N, o);
+    for (int o = 8; o; o >>= 1) v = op(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(kTabThreads) k_rans_tables(const uint32_t* __restrict__ hist3,
+                                                             uint32_t* __restrict__ freq3) {
+    __shared__ unsigned long long red64[16];
+    __shared__ int red32[16];
+    const int c = blockIdx.x, s = threadIdx.x, lane = s & 31, warp = s >> 5;
+    auto add64 = [](unsigned long long a, unsigned long long b) { return a + b; };
+    auto max64 = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
+    auto add32 = [](int a, int b) { return a + b; };
+    auto max32 = [](int a, int b) { return a > b ? a : b; };
+    const uint32_t cnt = s < kNres ? hist3[c * kNres + s] : 0u;
     uint32_t* out = freq3 + c * kNres;
+    const unsigned long long N = block_reduce<unsigned long long>(cnt, add64, red64);
     if (N == 0) {
-#pragma unroll
-        for (int i = 0; i < kPer; ++i)
-            if (lane + 32 * i < kNres) out[lane + 32 * i] = 0u;
+        if (s < kNres) out[s] = 0u;
         return;
     }
     // floor(n_s M / N) from a double estimate (relative error below 2^-51, so
     // at most one off, and only next to an integer) and one exact correction;
     // q N < 2^56 since q <= 2^14 and N < 2^41.
-    const double invN = 1.0 / (double)N;
-    int sum = 0;   // at most 511 x 2^14
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        uint32_t v = 0;
-        if (cnt[i]) {
-            const unsigned long long a = (unsigned long long)cnt[i] << kRansBits;
-            unsigned long long q = (unsigned long long)((double)a * invN);
-            if (q * N > a) --q;
-            else if ((q + 1) * N <= a) ++q;
-            v = q < 1 ? 1u : (uint32_t)q;
-        }
-        f[i] = v;
-        sum += (int)v;
+    int f = 0;
+    if (cnt) {
+        const unsigned long long a = (unsigned long long)cnt << kRansBits;
+        unsigned long long q = (unsigned long long)((double)a * (1.0 / (double)N));
+        if (q * N > a) --q;
+        else if ((q + 1) * N <= a) ++q;
+        f = q < 1 ? 1 : (int)q;
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
-    const int diff = (int)kRansM - sum;
+    const int diff = (int)kRansM - block_reduce<int>(f, add32, red32);
     if (diff > 0) {
-        // most frequent symbol, smallest index on ties: key = (count, -s)
-        uint32_t bc = 0;
-        int bs = 1 << 30;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int s = lane + 32 * i;
-            if (s < kNres && (cnt[i] > bc || (cnt[i] == bc && s < bs))) {
-                bc = cnt[i];
-                bs = s;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const uint32_t oc = __shfl_xor_sync(kFull, bc, o);
-            const int os = __shfl_xor_sync(kFull, bs, o);
-            if (oc > bc || (oc == bc && os < bs)) {
-                bc = oc;
-                bs = os;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < kPer; ++i)
-            if (lane + 32 * i == bs) f[i] += (uint32_t)diff;
+        // most frequent symbol, smallest index on ties: key (count, 65535 - s)
+        const unsigned long long key = cnt ? ((unsigned long long)cnt << 16) | (unsigned)(0xffff - s) : 0ull;
+        const unsigned long long best = block_reduce<unsigned long long>(key, max64, red64);
+        if (s == 0xffff - (int)(best & 0xffffu)) f += diff;
     } else if (diff < 0) {
         const int D = -diff;   // at most 511
-        uint32_t fmax = 0;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) fmax = max(fmax, f[i]);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) fmax = max(fmax, __shfl_xor_sync(kFull, fmax, o));
+        const int fmax = block_reduce<int>(f, max32, red32);
         // smallest T with E(T) <= D: E(fmax) = 0, and E(fmax - D - 1) > D
         // because the largest entry alone contributes D + 1 there
-        uint32_t lo = fmax > (uint32_t)D ? fmax - (uint32_t)D : 1u, hi = fmax;
+        int lo = fmax > D ? fmax - D : 1, hi = fmax;
         while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            int e = 0;
-#pragma unroll
-            for (int i = 0; i < kPer; ++i) e += f[i] > mid ? (int)(f[i] - mid) : 0;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
-            if (e <= D) hi = mid;
+            const int mid = (lo + hi) >> 1;
+            if (block_reduce<int>(f > mid ? f - mid : 0, add32, red32) <= D) hi = mid;
             else lo = mid + 1;
         }
-        const uint32_t T = lo;
-        int e = 0;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) e += f[i] > T ? (int)(f[i] - T) : 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(kFull, e, o);
-        const int r = D - e;
-        // rank of each entry with f >= T in symbol order s = lane + 32 i
+        const int T = lo;
+        const int r = D - block_reduce<int>(f > T ? f - T : 0, add32, red32);
+        // rank of each entry with f >= T in symbol order
+        const bool cand = f >= T;
+        const unsigned m = __ballot_sync(kFull, cand);
+        __syncthreads();
+        if (lane == 0) red32[warp] = __popc(m);
+        __syncthreads();
         int before = 0;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const bool cand = f[i] >= T;
-            const unsigned m = __ballot_sync(kFull, cand);
-            const int rank = before + __popc(m & ((1u << lane) - 1u));
-            if (cand) f[i] = (rank < r) ? T - 1 : T;
-            before += __popc(m);
-        }
+        for (int w8 = 0; w8 < warp; ++w8) before += red32[w8];
+        const int rank = before + __popc(m & ((1u << lane) - 1u));
+        if (cand) f = (rank < r) ? T - 1 : T;
     }
-#pragma unroll
-    for (int i = 0; i < kPer; ++i)
-        if (lane + 32 * i < kNres) out[lane + 32 * i] = f[i];
+    if (s < kNres) out[s] = (uint32_t)f;
 }
 
 // Exclusive prefix sums of one channel's table (512 entries, entry 511 = 0)
@@ -746,7 +715,7 @@ extern "C" int rans_tables_n(const uint32_t* hist, int ntables, uint32_t* freq, 
         set_error("rans_tables_n: need 4-byte aligned hist and freq and 1 <= ntables <= 65535");
         return SLRME_EINVAL;
     }
-    k_rans_tables<<<ntables, 32, 0, (cudaStream_t)stream>>>(hist, freq);
+    k_rans_tables<<<ntables, kTabThreads, 0, (cudaStream_t)stream>>>(hist, freq);
     return cuda_status("rans_tables_n launch");
 }
 
@@ -756,7 +725,7 @@ extern "C" int rans_tables(const uint32_t* hist3, uint32_t* freq3, slrme_stream_
         set_error("rans_tables: hist3 and freq3 must be non-null and 4-byte aligned");
         return SLRME_EINVAL;
     }
-    k_rans_tables<<<3, 32, 0, (cudaStream_t)stream>>>(hist3, freq3);
+    k_rans_tables<<<3, kTabThreads, 0, (cudaStream_t)stream>>>(hist3, freq3);
     return cuda_status("rans_tables launch");
 }
 
