@@ -44,7 +44,7 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # DRAM bytes per pixel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
-TRAFFIC = {"slr_fit": {"bytes_per_px": 22093696 / (2048 * 1536), "sha": "b2c3817c7b238336"},
+TRAFFIC = {"slr_fit": {"bytes_per_px": 22095872 / (2048 * 1536), "sha": "bd8b71b87ceec424"},
            "sdri_base_roundtrip": {"bytes_per_px": 12650496 / (2048 * 1536), "sha": "2400ac5ad38254ca"}}
 # The base round trip is bound by instruction issue, not by memory: its
 # roofline counts the arithmetic operations its definition needs per pixel

@@ -697,9 +697,10 @@ __device__ __forceinline__ void load_params(const slrme_params* __restrict__ P, 
     }
 }
 
-// The parameters as (a, b) pairs, [c][E], so one 8-byte load gets both.
-__device__ __forceinline__ void load_params_ab(const slrme_params* __restrict__ P, float2* ab) {
-    for (int i = threadIdx.x; i < 3 * kNbin; i += blockDim.x) ab[i] = make_float2((&P->a[0][0])[i], (&P->b[0][0])[i]);
+// The parameters as (a, b) pairs, [c][E], so one 8-byte load gets both;
+// threads 0 .. nthreads - 1 take part.
+__device__ __forceinline__ void load_params_ab(const slrme_params* __restrict__ P, float2* ab, int nthreads) {
+    for (int i = threadIdx.x; i < 3 * kNbin; i += nthreads) ab[i] = make_float2((&P->a[0][0])[i], (&P->b[0][0])[i]);
 }
 
 // One strip: R = M - M* for rows y0 .. y0 + rows - 1, columns xs .. xs + 255;
@@ -1360,7 +1361,6 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k
     char* extra = dyn + (L.extra - smem_addr(dyn));
     SmemBins& bins = *reinterpret_cast<SmemBins*>(extra);
     uint32_t* queue = reinterpret_cast<uint32_t*>(extra + sizeof(SmemBins));
-    bins_clear(bins);
     tile_init_barriers(L);
     __syncthreads();
 
@@ -1368,6 +1368,11 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k
         if (lane == 0) tile_produce(L, &tm_s, &tm_a, &tm_e, A);
         return;
     }
+    // the consumers clear the bins while the first copies are in flight
+    static_assert(sizeof(SmemBins) % 16 == 0 && TileSmem<TmaMode::kFit>::kHead % 16 == 0, "16-byte bin stores");
+    for (int i = threadIdx.x; i < (int)(sizeof(SmemBins) / 16); i += kTileWarps * 32)
+        reinterpret_cast<uint4*>(extra)[i] = make_uint4(0u, 0u, 0u, 0u);
+    consumers_sync();
     const TileConsumer<TmaMode::kFit> C{L, A.max_spins};
     const int w = A.w;
     const bool gf = A.gf != 0;
@@ -1509,9 +1514,6 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_til
     char* extra = dyn + (L.extra - smem_addr(dyn));
     float2* ab = reinterpret_cast<float2*>(extra);
     uint32_t* hist = reinterpret_cast<uint32_t*>(ab + 3 * kNbin);
-    load_params_ab(A.params, ab);
-    if (MODE == TmaMode::kResidual && A.hist)
-        for (int i = threadIdx.x; i < 3 * kNres; i += blockDim.x) hist[i] = 0u;
     tile_init_barriers(L);
     __syncthreads();
 
@@ -1519,6 +1521,11 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_til
         if (lane == 0) tile_produce(L, &tm_s, &tm_a, &tm_e, A);
         return;
     }
+    // the consumers fetch the parameters while the first copies are in flight
+    load_params_ab(A.params, ab, kTileWarps * 32);
+    if (MODE == TmaMode::kResidual && A.hist)
+        for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32) hist[i] = 0u;
+    consumers_sync();
     const TileConsumer<MODE> C{L, A.max_spins};
     const int w = A.w;
     const int64_t n = (int64_t)A.h * w;

@@ -4,8 +4,12 @@
 // HBM-bound: 4 bytes read and 4 bytes written per pixel.  The vector path
 // reads 16 bytes (4 words) per thread per step with non-allocating loads and
 // writes one 32-bit word to each of the four planes; the byte transposition
-// is 6 byte-permutes per 4 pixels.  The statistic is reduced per thread in
-// int64, then per warp and block, with one 64-bit atomic per block.
+// is 6 byte-permutes per 4 pixels.  The statistic of the vector path is
+// 65536 (sum (E + k) - 137 n) + sum LUT16[m] over the nonzero pixels, the
+// same integer as the per-pixel sum of l(p): Yq comes from two 16x8-bit dot
+// products, the three partial sums are 32-bit per loop step and folded into
+// int64 after it.  It is reduced per thread, then per warp and block, with
+// one 64-bit atomic per block.
 #include "slrme_internal.cuh"
 
 #define SLRME_TABLE static __device__ const
@@ -35,6 +39,26 @@ __device__ __forceinline__ int32_t log_lum(uint32_t wd, const int32_t* lut) {
     const int k = (32 - __clz(yq)) - 12;        // bitlen(Yq) - 12, in [2, 11]
     const int m = yq >> k;                       // 2048 .. 4095
     return 65536 * (E - 137 + k) + lut[m - 2048];
+}
+
+// The statistic's parts for the four words of v: sl += LUT16[m], se += E + k
+// and cn += 1 for each word with E > 0 (se also adds E = 0, which is 0).
+// Yq = 4252 R + 14304 G + 1444 B + 10000 = 2126 (2R+1) + 7152 (2G+1) +
+// 722 (2B+1); lut[m - 2048] is LUT16[m].
+__device__ __forceinline__ void lum4(const uint4& v, const int32_t* lut, uint32_t& sl, uint32_t& se,
+                                     uint32_t& cn) {
+    const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t wd = w4[q];
+        const uint32_t yq = __dp2a_hi(1444u, wd, __dp2a_lo(4252u | (14304u << 16), wd, 10000u));
+        const uint32_t k = 20u - __clz(yq);   // bitlen(Yq) - 12, in [2, 11]
+        const int32_t t = lut[(yq >> k) - 2048u];
+        const bool nz = wd > 0xFFFFFFu;
+        sl += nz ? (uint32_t)t : 0u;
+        se += (wd >> 24) + (nz ? k : 0u);
+        cn += nz ? 1u : 0u;
+    }
 }
 
 __device__ __forceinline__ void block_reduce_add(int64_t s, int64_t c, int64_t* stats) {
@@ -73,14 +97,16 @@ __global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict_
     for (int i = threadIdx.x; i < 2048; i += kThreads) lut[i] = kLog2Lut[i];
     __syncthreads();
 
-    int64_t s = 0, c = 0;
+    int64_t sl64 = 0, se64 = 0, c = 0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     constexpr int U = 4;   // independent 16-byte loads in flight per thread
+    // 32-bit parts per step: at most 16 words, each below 2^20 (LUT) and 267 (E + k)
     for (; i + (U - 1) * stride < nv; i += U * stride) {
         uint4 v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) v[u] = ld_stream(rgbe4 + i + u * stride);
+        uint32_t sl = 0, se = 0, cn = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t lo01 = __byte_perm(v[u].x, v[u].y, 0x5140), hi01 = __byte_perm(v[u].x, v[u].y, 0x7362);
@@ -90,11 +116,11 @@ __global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict_
             mG[j] = __byte_perm(lo01, lo23, 0x7632);
             mB[j] = __byte_perm(hi01, hi23, 0x5410);
             eP[j] = __byte_perm(hi01, hi23, 0x7632);
-            int32_t part = log_lum(v[u].x, lut) + log_lum(v[u].y, lut);
-            int32_t part2 = log_lum(v[u].z, lut) + log_lum(v[u].w, lut);
-            s += (int64_t)part + part2;
-            c += (v[u].x >> 24 != 0) + (v[u].y >> 24 != 0) + (v[u].z >> 24 != 0) + (v[u].w >> 24 != 0);
+            lum4(v[u], lut, sl, se, cn);
         }
+        sl64 += sl;
+        se64 += se;
+        c += cn;
     }
     for (; i < nv; i += stride) {
         const uint4 v = ld_stream(rgbe4 + i);
@@ -104,10 +130,13 @@ __global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict_
         mG[i] = __byte_perm(lo01, lo23, 0x7632);
         mB[i] = __byte_perm(hi01, hi23, 0x5410);
         eP[i] = __byte_perm(hi01, hi23, 0x7632);
-        s += (int64_t)log_lum(v.x, lut) + log_lum(v.y, lut) + log_lum(v.z, lut) + log_lum(v.w, lut);
-        c += (v.x >> 24 != 0) + (v.y >> 24 != 0) + (v.z >> 24 != 0) + (v.w >> 24 != 0);
+        uint32_t sl = 0, se = 0, cn = 0;
+        lum4(v, lut, sl, se, cn);
+        sl64 += sl;
+        se64 += se;
+        c += cn;
     }
-    block_reduce_add(s, c, stats);
+    block_reduce_add(65536 * (se64 - 137 * c) + sl64, c, stats);
 }
 
 // Scalar path: any size and alignment, one word per thread per step.
@@ -154,6 +183,9 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
         const bool vec = (n % 4 == 0) && ((uintptr_t)rgbe % 16 == 0) && ((uintptr_t)m3 % 4 == 0) &&
                          ((uintptr_t)e % 4 == 0);
         if (vec) {
+            // a chunk gives a thread at most kSplitChunk / kThreads words: 32-bit parts
+            static_assert(kSplitChunk / kThreads * (1 << 20) < (1ll << 32), "32-bit statistic parts");
+            uint32_t sl = 0, se = 0, cn = 0;
             const uint4* r4 = reinterpret_cast<const uint4*>(rgbe);
             uint32_t* mR = reinterpret_cast<uint32_t*>(m3);
             uint32_t* mG = reinterpret_cast<uint32_t*>(m3 + n);
@@ -167,9 +199,10 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
                 mG[j] = __byte_perm(lo01, lo23, 0x7632);
                 mB[j] = __byte_perm(hi01, hi23, 0x5410);
                 eP[j] = __byte_perm(hi01, hi23, 0x7632);
-                s += (int64_t)log_lum(v.x, lut) + log_lum(v.y, lut) + log_lum(v.z, lut) + log_lum(v.w, lut);
-                c += (v.x >> 24 != 0) + (v.y >> 24 != 0) + (v.z >> 24 != 0) + (v.w >> 24 != 0);
+                lum4(v, lut, sl, se, cn);
             }
+            s = 65536 * ((int64_t)se - 137 * (int64_t)cn) + sl;
+            c = cn;
         } else {
             for (int64_t j = w0 + threadIdx.x; j < w1; j += kThreads) {
                 const uint32_t wd = __ldg(rgbe + j);
