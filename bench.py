@@ -127,6 +127,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The whole job's time for a region every rank timed: the slowest rank's
+    (one all-reduce of a float64 on `device`), or `ms` itself on one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpx_per_s(world: int, px_per_step: int, steps: int, ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each coded `px_per_step`
+    pixels per step for `steps` steps, the slowest within `ms` milliseconds."""
+    return world * px_per_step * steps / (ms / 1e3) / 1e6
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -313,13 +330,10 @@ def run_ours(args) -> None:
                 ev = call_ev[k][q]
                 for i, name in enumerate(calls):
                     per_call[name].append(ev[i].elapsed_time(ev[i + 1]))
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
 
     px_per_step = n * len(qualities)
-    value = world * px_per_step * args.steps / (total_ms / 1e3) / 1e6
+    value = job_mpx_per_s(world, px_per_step, args.steps, total_ms)
 
     # roofline of the dominant call (its own bound: HBM bytes, or ALU operations)
     peaks = load_peaks()
@@ -373,11 +387,8 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
     e2e_ok = bool(torch.equal(hc.h_out, h_rgbe))
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * px_per_step * args.steps / (e2e_ms / 1e3) / 1e6
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
+    e2e_value = job_mpx_per_s(world, px_per_step, args.steps, e2e_ms)
 
     enh = enhancement_coder(c, rgbe, qualities, n, args, flush, stream)
 
