@@ -25,7 +25,12 @@ CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C, IEEE arithmetic, no contraction)."""
+    """Compile the oracle with gcc (plain C, IEEE arithmetic, no contraction).
+    SLRME_ORACLE_LIB names an already built library to load instead (the
+    mutation tests load deliberately broken copies of the oracle this way)."""
+    alt = os.environ.get("SLRME_ORACLE_LIB")
+    if alt:
+        return alt
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
@@ -478,6 +483,13 @@ def rgb_to_ycc(rgb3: np.ndarray) -> np.ndarray:
     x = np.ascontiguousarray(rgb3, dtype=np.uint8)
     out = np.zeros_like(x)
     lib().oracle_rgb_to_ycc(_p(x), x[0].size, _p(out))
+    return out
+
+
+def ycc_to_rgb(ycc3: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(ycc3, dtype=np.uint8)
+    out = np.zeros_like(x)
+    lib().oracle_ycc_to_rgb(_p(x), ctypes.c_int64(x[0].size), _p(out))
     return out
 
 

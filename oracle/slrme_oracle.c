@@ -1220,6 +1220,19 @@ void oracle_rgb_to_ycc(const uint8_t* rgb3, int64_t n, uint8_t* ycc3)
     }
 }
 
+/* T.871's inverse, R = Y + 1.402 (Cr - 128), G = Y - 0.344136 (Cb - 128) -
+ * 0.714136 (Cr - 128), B = Y + 1.772 (Cb - 128), with the weights
+ * round(65536 c), rounded half up and clamped, on full-resolution planes. */
+void oracle_ycc_to_rgb(const uint8_t* ycc3, int64_t n, uint8_t* rgb3)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int Y = ycc3[i], cb = ycc3[n + i] - 128, cr = ycc3[2 * n + i] - 128;
+        rgb3[i] = (uint8_t)clamp255(Y + ((91881 * cr + 32768) >> 16));
+        rgb3[n + i] = (uint8_t)clamp255(Y + ((-22554 * cb - 46802 * cr + 32768) >> 16));
+        rgb3[2 * n + i] = (uint8_t)clamp255(Y + ((116130 * cb + 32768) >> 16));
+    }
+}
+
 /* One plane (ph x pw) through the 8x8 round trip with steps Q; levels (may
  * be NULL) as in oracle_base_levels for one plane. */
 static void plane_roundtrip(const uint8_t* in, int ph, int pw, const int32_t* Q, uint8_t* out, int16_t* levels)
@@ -1282,14 +1295,15 @@ int oracle_base_roundtrip_420(const uint8_t* sdr3, int h, int w, int quality, ui
     plane_roundtrip(ycc, h, w, QY, yd, levels);
     for (int c = 0; c < 2; ++c)
         plane_roundtrip(cs + c * nc, hc, wc, QC, cd + c * nc, levels ? levels + (nbY + c * nbC) * 64 : NULL);
+    /* chroma replicated over its 2x2 pixels, then back to RGB */
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x) {
             int64_t i = (int64_t)y * w + x, k = (int64_t)(y / 2) * wc + x / 2;
-            int Y = yd[i], cb = cd[k] - 128, cr = cd[nc + k] - 128;
-            s3[i] = (uint8_t)clamp255(Y + ((91881 * cr + 32768) >> 16));
-            s3[n + i] = (uint8_t)clamp255(Y + ((-22554 * cb - 46802 * cr + 32768) >> 16));
-            s3[2 * n + i] = (uint8_t)clamp255(Y + ((116130 * cb + 32768) >> 16));
+            ycc[i] = yd[i];
+            ycc[n + i] = cd[k];
+            ycc[2 * n + i] = cd[nc + k];
         }
+    oracle_ycc_to_rgb(ycc, n, s3);
     free(ycc);
     free(cs);
     free(yd);

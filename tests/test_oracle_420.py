@@ -33,6 +33,8 @@ def test_chroma_quantiser_at_q50_is_annex_k2():
     assert list(q[0]) == [17, 18, 24, 47, 99, 99, 99, 99]
     assert list(q[:, 0]) == [17, 18, 24, 47, 99, 99, 99, 99]
     assert (q[4:] == 99).all() and (O.quant_table_chroma(100) == 1).all()
+    # the IJG rule at Q = 75: half of each step, halves rounded up (17 -> 9, 47 -> 24, 99 -> 50)
+    assert np.array_equal(O.quant_table_chroma(75), (q + 1) // 2)
 
 
 def test_colour_transform_is_t871_within_rounding():
@@ -43,10 +45,54 @@ def test_colour_transform_is_t871_within_rounding():
     y = 0.299 * r + 0.587 * g + 0.114 * b
     cb = -0.299 / 1.772 * r - 0.587 / 1.772 * g + 0.5 * b + 128
     cr = 0.5 * r - 0.587 / 1.402 * g - 0.114 / 1.402 * b + 128
+    # rounding to an integer (1/2) plus three 16-bit weights, each within half a unit of 65536 c
+    bound = 0.5 + 3 * 0.5 * 255 / 65536
     for got, want in ((ycc[0], y), (ycc[1], np.clip(cb, 0, 255)), (ycc[2], np.clip(cr, 0, 255))):
-        assert np.abs(got - want).max() <= 0.51
+        assert np.abs(got - want).max() <= bound
     grey = np.tile(np.arange(256, dtype=np.uint8), (3, 1))
     assert np.array_equal(O.rgb_to_ycc(grey), np.stack([np.arange(256), np.full(256, 128), np.full(256, 128)]))
+    # T.871's weight 1/2 is exact: pure blue has Cb = 128 + B / 2 and pure red
+    # Cr = 128 + R / 2, halves rounded up, clamped to 255
+    v = np.arange(256)
+    blue = np.stack([np.zeros(256), np.zeros(256), v]).astype(np.uint8)
+    red = np.stack([v, np.zeros(256), np.zeros(256)]).astype(np.uint8)
+    assert np.array_equal(O.rgb_to_ycc(blue)[1], np.minimum(128 + (v + 1) // 2, 255))
+    assert np.array_equal(O.rgb_to_ycc(red)[2], np.minimum(128 + (v + 1) // 2, 255))
+
+
+def test_inverse_colour_transform_is_t871_within_rounding():
+    # every (Cb, Cr) pair at five luma values against T.871's real-valued
+    # inverse; the bound is the rounding to an integer plus the 16-bit
+    # weights, each within half a unit of 65536 c, over |Cb - 128|, |Cr - 128| <= 128
+    cb, cr = [a.reshape(-1) for a in np.meshgrid(np.arange(256), np.arange(256))]
+    for y in (0, 61, 128, 200, 255):
+        ycc = np.stack([np.full(cb.size, y), cb, cr]).astype(np.uint8)
+        rgb = O.ycc_to_rgb(ycc).astype(np.float64)
+        dcb, dcr = cb - 128.0, cr - 128.0
+        want = (y + 1.402 * dcr, y - 0.344136 * dcb - 0.714136 * dcr, y + 1.772 * dcb)
+        for got, exact, nw in zip(rgb, want, (1, 2, 1)):
+            assert np.abs(got - np.clip(exact, 0, 255)).max() <= 0.5 + nw * 0.5 * 128 / 65536
+    # neutral chroma leaves the luma as it is
+    grey = np.stack([np.arange(256), np.full(256, 128), np.full(256, 128)]).astype(np.uint8)
+    assert np.array_equal(O.ycc_to_rgb(grey), np.tile(np.arange(256, dtype=np.uint8), (3, 1)))
+
+
+def test_chroma_subsampling_rounds_the_2x2_mean_half_up():
+    # rows alternate black and (0, 0, 2): Y = 0 and Cr = 128 for both, Cb = 128
+    # and 129, so every 2x2 chroma mean is 128.5, taken half up to 129; the
+    # subsampled planes are constant, and at Q = 100 (every step 1) a constant
+    # block's only level is its DC, 8 (m - 128)
+    h, w = 16, 32
+    rgb = np.zeros((3, h, w), np.uint8)
+    rgb[2, 1::2] = 2
+    ycc = O.rgb_to_ycc(rgb.reshape(3, -1)).reshape(3, h, w)
+    assert (ycc[0] == 0).all() and (ycc[2] == 128).all()
+    assert (ycc[1, 0::2] == 128).all() and (ycc[1, 1::2] == 129).all()
+    _, lv = O.base_roundtrip_420(rgb, 100)
+    nbY, nbC = O.blocks_420(h, w)
+    cb_blocks, cr_blocks = lv[nbY:nbY + nbC], lv[nbY + nbC:]
+    assert (cb_blocks[:, 0] == 8 * (129 - 128)).all() and (cb_blocks[:, 1:] == 0).all()
+    assert (cr_blocks == 0).all()
 
 
 def test_grey_images_take_the_luminance_path_only():

@@ -92,6 +92,16 @@ def test_quant_table_ijg_rule(quality):
     assert base[7, 7] == 99
 
 
+def test_quality_75_halves_the_table_rounding_halves_up():
+    # the IJG rule scales the K.1 steps by 200 - 2Q percent, rounded to the
+    # nearest integer with halves up: at Q = 75 that is b / 2, so the odd
+    # steps of K.1 (11, 51, 61, ...) become (b + 1) / 2; at Q = 25 it is 2 b
+    base = O.quant_table(50)
+    assert (base % 2 == 1).sum() >= 10
+    assert np.array_equal(O.quant_table(75), (base + 1) // 2)
+    assert np.array_equal(O.quant_table(25), np.minimum(2 * base, 255))
+
+
 def test_quantiser_half_away_from_zero():
     Q = np.full((8, 8), 10, dtype=np.int32)
     F = np.zeros((8, 8), dtype=np.int32)

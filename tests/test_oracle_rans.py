@@ -98,6 +98,26 @@ def test_table_properties():
     assert not O.rans_table(np.zeros(511, np.uint32)).any()   # empty histogram: no table
 
 
+def test_table_tie_rules_on_hand_worked_histograms():
+    # shortfall: three symbols seen once each get floor(2^14 / 3) = 5461,
+    # 16,383 in all; the missing unit goes to the most frequent symbol, the
+    # smallest one on ties
+    c = np.zeros(511, np.uint32)
+    c[[10, 20, 30]] = 1
+    f = O.rans_table(c)
+    assert f[[10, 20, 30]].tolist() == [5462, 5461, 5461]
+    # excess: two symbols seen 10^6 times and 299 seen once (N = 2,000,299)
+    # get floor(10^6 2^14 / N) = 8190 twice and 1 each: 16,679, 295 too many;
+    # units go one at a time from the largest entry, the smaller symbol on
+    # ties, so symbol 5 gives 148 and symbol 6 gives 147
+    c = np.zeros(511, np.uint32)
+    c[5] = c[6] = 10 ** 6
+    c[100:399] = 1
+    f = O.rans_table(c)
+    assert (f[5], f[6]) == (8190 - 148, 8190 - 147)
+    assert (f[100:399] == 1).all() and int(f.sum()) == M
+
+
 def test_zero_frequency_is_rejected():
     n = 100
     r3 = np.zeros(3 * n, np.int16)

@@ -196,6 +196,31 @@ def test_predict_random_against_decimal_rounding():
             assert ms[c, yy, xx] == min(255, max(0, _half_away(float(t))))
 
 
+@pytest.mark.parametrize("a,x,b,k", [(1.0000001192092896, 4080, -4079.50048828125, 0),
+                                     (0.9590728878974915, 2086, -2000.1260986328125, 0),
+                                     (0.07105054706335068, 1101, -76.72665405273438, 1),
+                                     (0.9138873219490051, 3961, -3612.40771484375, 7),
+                                     (0.8200012445449829, 2977, -2340.643798828125, 100),
+                                     (1.403257966041565, 1132, -1333.988037109375, 254)])
+def test_predict_rounds_the_product_before_adding_b(a, x, b, k):
+    # Eq. (8) with 32-bit parameters, every operation an IEEE float32 one:
+    # here float32(float32(a x) + b) is exactly k + 1/2 (rounded away from
+    # zero to k + 1), while the exact a x + b, and so a fused multiply-add,
+    # lies below k + 1/2
+    from fractions import Fraction
+    a32, b32 = np.float32(a), np.float32(b)
+    assert float(a32) == a and float(b32) == b
+    t = np.float32(np.float32(a32 * np.float32(x)) + b32)
+    assert float(t) == k + 0.5
+    assert Fraction(a) * x + Fraction(b) < Fraction(2 * k + 1, 2)
+    x3 = np.full((3, 1, 1), x, np.int32)
+    e = np.full((1, 1), 9, np.uint8)
+    A = np.zeros((3, 256), np.float32)
+    B = np.zeros((3, 256), np.float32)
+    A[:, 9], B[:, 9] = a32, b32
+    assert (O.predict(x3, e, A, B) == k + 1).all()
+
+
 # ------------------------------------------------------------------ residual / decode
 
 

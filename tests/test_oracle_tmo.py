@@ -169,3 +169,39 @@ def test_white_point_operator_close_to_float64_reinhard_eq4_and_brighter():
     assert diff.max() <= 1
     assert (diff == 0).mean() > 0.99
     assert (got >= sdr).all() and (got > sdr).any()   # the factor 1 + L / L_white^2 only brightens
+
+
+def test_tmo_equals_the_exact_operator_away_from_the_thresholds():
+    """The display code is the number of gamma thresholds ((k - 1/2) / 255)^2.2
+    at or below the exact Reinhard value L_d f_c / Y, with f_c the Eq. (3)
+    floats, Y their BT.709 luminance, L = 0.18 Y over the log-average
+    2^((16 J + r) / 16) / 10^4 the key stands for, and L_d = L / (1 + L).
+    The float32 evaluation and the float32 tables move the value by a few
+    ulps (below 2^-21 relative), so wherever the exact value is farther than
+    2^-19 from every threshold the codes are equal."""
+    import bisect
+    mp = pytest.importorskip("mpmath")
+    mp.mp.prec = 80
+    img = synth.make_rgbe(36, 44, seed=31, lo=-3, hi=5, rects=3, highlights=4)
+    sdr, J, r = _tmo_image(img)
+    thr = [mp.power((k - mp.mpf(1) / 2) / 255, mp.mpf(22) / 10) for k in range(1, 256)]
+    lavg = mp.power(2, mp.mpf(16 * J + r) / 16) / 10 ** 4
+    checked = 0
+    words = img.reshape(-1)
+    for p, wd in enumerate(words.tolist()):
+        E = wd >> 24
+        if E == 0:
+            continue
+        f = [(mp.mpf((wd >> (8 * c)) & 255) + mp.mpf(1) / 2) * mp.power(2, E - 136) for c in range(3)]
+        Y = mp.mpf("0.2126") * f[0] + mp.mpf("0.7152") * f[1] + mp.mpf("0.0722") * f[2]
+        L = mp.mpf("0.18") * Y / lavg
+        Ld = L / (1 + L)
+        for c in range(3):
+            v = Ld * f[c] / Y
+            k = bisect.bisect_right(thr, v)          # thresholds at or below v
+            near = min(abs(v - thr[i]) / thr[i] for i in (k - 1, k) if 0 <= i < 255)
+            if near < mp.mpf(2) ** -19:
+                continue
+            assert int(sdr.reshape(3, -1)[c, p]) == k, (p, c)
+            checked += 1
+    assert checked >= 0.99 * 3 * int(((words >> 24) > 0).sum())
