@@ -61,6 +61,31 @@ def test_delta_network_reproduces_the_red_plane():
     assert np.array_equal(out[0], s3[0] - 1)
 
 
+def test_hidden_activations_saturate_at_127():
+    # every hidden layer's bias alone would give 200 and -50: the ReLU clamp
+    # keeps 127 and 0; the last layer sums one 3x3 window of channel 0 with
+    # weight 1 and bias 0: 9 x 127 inside the image (over 255 after the / 4:
+    # the output clamp), fewer on the zero-padded border
+    net = C.random_net(7)
+    for l in range(4):
+        net["w"][l][:] = 0
+        net["m"][l][:] = 1 << 12
+        net["sh"][l] = 12
+        net["b"][l][:] = 200
+        if l < 3:
+            net["b"][l][1::2] = -50
+    net["w"][3][:, 0] = 1
+    net["b"][3][:] = 0
+    net["m"][3][:] = 1 << 10                 # the sum / 4, rounded half up
+    s3 = np.random.default_rng(8).integers(0, 256, size=(3, 5, 6))
+    out = C.infer(s3, np.full((5, 6), 133), 1, net).astype(int)
+    cover = np.full((5, 6), 9)
+    cover[[0, -1], :] -= 3
+    cover[:, [0, -1]] -= 3
+    cover[[0, 0, -1, -1], [0, -1, 0, -1]] = 4
+    assert np.array_equal(out, np.stack([np.minimum((cover * 127 + 2) // 4, 255)] * 3))
+
+
 def test_input_planes():
     s3 = np.array([[[0, 255]], [[128, 1]], [[7, 9]]])
     e = np.array([[0, 250]])

@@ -108,3 +108,48 @@ def test_planted_mistake_fails_a_pin(name, old, new, count, files):
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     # exit status 1: tests ran and at least one failed (not a crash or a collection error)
     assert p.returncode == 1, f"{name}: no pin failed\n{p.stdout[-1500:]}"
+
+
+# The CNN oracle is Python: its mistakes are planted in a scratch copy of the
+# module, loaded under its own name before the pin tests are collected.
+CNN_MUTATIONS = [
+    ("input exponent offset 136", "np.asarray(e, np.int64) - 137 - int(J)", "np.asarray(e, np.int64) - 136 - int(J)"),
+    ("convolution window flipped", 'np.einsum("oc,chw->ohw", w[:, :, dy, dx], win)',
+     'np.einsum("oc,chw->ohw", w[:, :, 2 - dy, 2 - dx], win)'),
+    ("requantisation rounds down", "(acc * m + (1 << (shift - 1))) >> shift", "(acc * m) >> shift"),
+    ("hidden clamp 128", "0, 127 if l < 3 else 255", "0, 128 if l < 3 else 255"),
+    ("correction offset 127", "+ np.asarray(y3, np.int64) - 128", "+ np.asarray(y3, np.int64) - 127"),
+    ("weight step over 128", "max(axis=1) / 127.0", "max(axis=1) / 128.0"),
+    ("activation steps of 1/4", "q = z / SCALE_A", "q = z / (2 * SCALE_A)"),
+    ("backward ignores the quantiser mask", "        g = g * mask\n", "        g = g\n"),
+    ("L1 gradient not averaged", "np.sign(d) / d.size", "np.sign(d)"),
+    ("Adam without bias correction", "mh = m / (1 - b1 ** step)", "mh = m"),
+]
+
+_LOAD_AND_TEST = """
+import importlib.util, sys
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.cnn_oracle", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.cnn_oracle"] = mod
+spec.loader.exec_module(mod)
+oracle.cnn_oracle = mod
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", sys.argv[2]]))
+"""
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,old,new", CNN_MUTATIONS, ids=[m[0] for m in CNN_MUTATIONS])
+def test_planted_cnn_mistake_fails_a_pin(name, old, new):
+    src_path = os.path.join(ROOT, "oracle", "cnn_oracle.py")
+    with open(src_path) as f:
+        src = f.read()
+    assert src.count(old) == 1, "the planted text must occur once"
+    with tempfile.TemporaryDirectory() as tmp:
+        mut = os.path.join(tmp, "cnn_oracle.py")
+        with open(mut, "w") as f:
+            f.write(src.replace(old, new))
+        p = subprocess.run([sys.executable, "-c", _LOAD_AND_TEST, mut, os.path.join(ROOT, "tests", "test_oracle_cnn.py")],
+                           cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 1, f"{name}: no pin failed\n{p.stdout[-1500:]}"
