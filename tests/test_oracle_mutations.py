@@ -17,6 +17,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # (name, text in slrme_oracle.c, replacement, occurrences replaced, pin test files)
 MUTATIONS = [
+    ("frexp exponent offset 129", "int E = ex + 128;", "int E = ex + 129;", 1, ["test_oracle_format.py"]),
+    ("Eq. 3 without the half", "ldexp(M + 0.5, E - 128 - 8)", "ldexp(M + 0.0, E - 128 - 8)", 1,
+     ["test_oracle_format.py"]),
     ("luma weight of R", "return 2126 * (2 * R + 1)", "return 2127 * (2 * R + 1)", 1, ["test_oracle_tmo.py"]),
     ("log-average offset 136", "65536 * (int64_t)(E - 137 + k)", "65536 * (int64_t)(E - 136 + k)", 1,
      ["test_oracle_tmo.py"]),
@@ -51,6 +54,8 @@ MUTATIONS = [
      ["test_oracle_slrme.py"]),
     ("unfiltered x scale 15", "= 16 * S[(int64_t)y * w + x]; continue;", "= 15 * S[(int64_t)y * w + x]; continue;", 1,
      ["test_oracle_slrme.py"]),
+    ("int128 to double ties away from even", "(rem == half && (mant & 1))", "(rem == half)", 1,
+     ["test_oracle_slrme.py"]),
     ("prediction ties round down", "if (t - tr >= 0.5f) r += 1;", "if (t - tr > 0.5f) r += 1;", 1,
      ["test_oracle_slrme.py"]),
     ("prediction fused multiply-add", "float t = a * (float)x;\n    t = t + b;", "float t = fmaf(a, (float)x, b);",
@@ -66,10 +71,18 @@ MUTATIONS = [
      ["test_oracle_rans.py"]),
     ("rANS initial state L + 1", "uint32_t x = RANS_L;", "uint32_t x = RANS_L + 1;", 1, ["test_oracle_rans.py"]),
     ("wavelet right edge zero, both directions", ": x[(2 * i) * step];", ": 0;", 2, ["test_oracle_dwt.py"]),
+    ("raw chunk from 255", "if (src[i] < -255 || src[i] > 255) raw = 1;",
+     "if (src[i] < -255 || src[i] > 254) raw = 1;", 1, ["test_oracle_dwt.py", "test_oracle_rans.py"]),
     ("wavelet prediction rounds up", "hi[i] = (int32_t)(x[(2 * i + 1) * step] - floor_div2(left + right));",
      "hi[i] = (int32_t)(x[(2 * i + 1) * step] - floor_div2(left + right + 1));", 1, ["test_oracle_dwt.py"]),
     ("wavelet update bias 1, both directions", "floor_div4(dl + dr + 2)", "floor_div4(dl + dr + 1)", 2,
      ["test_oracle_dwt.py"]),
+    ("luminance DC length of category 5", "{2, 3, 3, 3, 3, 3, 4, 5, 6, 7, 8, 9}", "{2, 3, 3, 3, 3, 4, 4, 5, 6, 7, 8, 9}",
+     1, ["test_oracle_jpeg.py"]),
+    ("EOB and 0x05 lengths swapped", "0x01, 0x02, 0x03, 0x00, 0x04, 0x11, 0x05,", "0x01, 0x02, 0x03, 0x05, 0x04, 0x11, 0x00,",
+     1, ["test_oracle_jpeg.py"]),
+    ("chrominance DC length of category 2", "{2, 2, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11}",
+     "{2, 2, 3, 3, 4, 5, 6, 7, 8, 9, 10, 11}", 1, ["test_oracle_420.py"]),
     ("ZRL after 17 zeros", "while (run > 15) {", "while (run > 16) {", 1, ["test_oracle_jpeg.py"]),
     ("zigzag transposed", "int lv = L[u * 8 + v];", "int lv = L[v * 8 + u];", 1, ["test_oracle_jpeg.py"]),
     ("DC prediction dropped", "        pred = L[0];\n", "        pred = 0;\n", 1, ["test_oracle_jpeg.py"]),
