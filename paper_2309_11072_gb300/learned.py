@@ -5,7 +5,7 @@ The network and its integer arithmetic are defined in include/slrme.h
 step is a library kernel (crop gather, forward, loss, backward, Adam), turns
 the trained float weights into the integer network, and picks, image by
 image, the estimator whose residuals cost fewer bits (the regression of
-Eq. 8 stays the fallback and the judge).
+Eq. 8 stays the fallback and the yardstick).
 """
 from __future__ import annotations
 
