@@ -73,18 +73,38 @@ def _run_bench(*argv, env=None):
 
 @pytest.mark.slow
 def test_reference_arm_prints_one_line_of_the_contract():
-    """`--impl reference` times the CPU oracle on the bench workload: one JSON
-    line with the same metric and unit, its own cpu_baseline and an e2e
-    object without host-device copies."""
+    """`--impl reference` times the CPU oracle on the bench workload (the
+    7680x4320 image, one band per host core): one JSON line with the same
+    metric and unit, its own cpu_baseline and an e2e object without
+    host-device copies."""
     (line,) = _run_bench("--impl", "reference", "--steps", "1", "--warmup", "0")
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["higher_is_better"] is True and line["bit_exact"] is True and line["value"] > 0
-    assert line["config"]["pixels_per_step"] == 2048 * 1536
+    assert line["config"]["pixels_per_step"] == 7680 * 4320
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] == min(bench.host_cores(), 540) and cb["value"] == line["value"]
+    assert cb["sample"] and cb["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
 
 def test_reference_arm_runs_on_rank_zero_only():
     assert _run_bench("--impl", "reference", "--steps", "1", "--warmup", "0", env={"RANK": "1"}) == []
+
+
+def test_image_bands_cover_every_row_once():
+    import numpy as np
+    img = np.arange(4320 * 16, dtype=np.uint32).reshape(4320, 16)
+    for parts in (1, 7, 16, 72):
+        bands = bench.image_bands(img, parts)
+        assert len(bands) == parts
+        assert all(b.shape[0] >= 8 and b.flags["C_CONTIGUOUS"] for b in bands)
+        assert np.array_equal(np.concatenate(bands), img)
+    # never a band under 8 rows
+    assert len(bench.image_bands(img[:20], 16)) == 2
+    assert len(bench.image_bands(img[:5], 16)) == 1
+
+
+def test_cpu_model_and_cores_are_reported():
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
+    assert bench.host_cores() >= 1

@@ -1,6 +1,8 @@
 """Batch form on the GPU: many uneven images in one persistent launch per
 stage.  Every image must equal the CPU oracle bit for bit, whatever the tile
 choice; the autotuner and the captured CUDA graph must not change a result."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -112,28 +114,71 @@ def test_autotune_and_graph_replay_keep_results():
     bc.close()
 
 
-@pytest.mark.slow
-def test_batch_workload_64_uneven_images():
-    wl = synth.workload_batch()
-    imgs = synth.make_workload_images(wl)
-    bc = B.BatchCodec(wl.sizes, wl.qualities * len(wl.sizes))
+def _oracle_all(imgs, quals, gf_on=True):
+    """The CPU oracle's encoding of every image, one thread per image (the
+    oracle's C calls release the GIL, so the images run on separate cores)."""
+    from concurrent.futures import ThreadPoolExecutor
+    O.lib()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(imgs), os.cpu_count() or 1))) as ex:
+        return list(ex.map(lambda k: None if imgs[k].size == 0 else O.encode(imgs[k], quals[k], gf_on),
+                           range(len(imgs))))
+
+
+def _check_all(bc, imgs, quals, gf_on=True):
+    """Every layer of every image against the oracle, bit for bit."""
+    torch.cuda.synchronize()
+    ref = _oracle_all(imgs, quals, gf_on)
+    m3, e, s3 = _host(bc.m3, np.uint8), _host(bc.e, np.uint8), _host(bc.s3, np.uint8)
+    r3, out, hist = _host(bc.r3, np.int16), _host(bc.out, np.uint32), _host(bc.hist, np.uint32)
+    for i, (img, o) in enumerate(zip(imgs, ref)):
+        h, w = img.shape
+        p = bc.image_params(i)
+        if o is None:
+            assert p["n_used"] == 0, i
+            continue
+        off, n = bc.offset(i), h * w
+        assert np.array_equal(m3[3 * off:3 * off + 3 * n].reshape(3, h, w), o["m3"]), i
+        assert np.array_equal(e[off:off + n].reshape(h, w), o["e"]), i
+        assert np.array_equal(s3[3 * off:3 * off + 3 * n].reshape(3, h, w), o["s3"]), i
+        assert np.array_equal(p["a"].view(np.uint32), o["a"].view(np.uint32)), i
+        assert np.array_equal(p["b"].view(np.uint32), o["b"].view(np.uint32)), i
+        assert np.array_equal(p["n"], o["n"]) and p["n_used"] == o["n_used"], i
+        assert np.array_equal(r3[3 * off:3 * off + 3 * n].reshape(3, h, w), o["r3"]), i
+        assert np.array_equal(hist[i * 3 * 511:(i + 1) * 3 * 511].reshape(3, 511), o["hist"]), i
+        assert np.array_equal(out[off:off + n].reshape(h, w), img), i
+
+
+def test_batch_ctas_that_cross_image_boundaries():
+    """200 small images of one CTA task each, at one CTA per SM: each CTA of
+    the fit, residual and decoder stages takes two or more consecutive
+    tasks, so its shared bins, parameters and histograms change image in
+    the middle of the launch.  Every image must still equal the oracle."""
+    rng = np.random.default_rng(77)
+    sizes = [(int(rng.integers(1, 129)), int(rng.integers(1, 257))) for _ in range(200)]
+    quals = [int(q) for q in rng.choice([30, 50, 75, 90, 100], size=len(sizes))]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(sizes) > sms   # more one-task images than CTAs: some CTAs take two images
+    imgs = _images(sizes, seed0=900)
+    bc = B.BatchCodec(sizes, quals)
     bc.load(imgs)
+    bc.set_tiles(strip_rows=16, fit_ctas_per_sm=1, res_ctas_per_sm=1, split_ctas_per_sm=1, base_ctas_per_sm=1)
     bc.encode()
     bc.decode()
-    torch.cuda.synchronize()
-    out = _host(bc.out, np.uint32)
-    for i, img in enumerate(imgs):
-        h, w = img.shape
-        o = bc.offset(i)
-        assert np.array_equal(out[o:o + h * w].reshape(h, w), img), i
-    # oracle parity, image by image, on the three smallest images
-    small = sorted(range(len(imgs)), key=lambda i: imgs[i].size)[:3]
-    sub = [imgs[i] for i in small]
-    for k, i in enumerate(small):
-        L = bc.image_layers(i)
-        h, w = sub[k].shape
-        o = O.encode(sub[k], wl.qualities[0])
-        assert np.array_equal(_host(L["s3"], np.uint8).reshape(3, h, w), o["s3"])
-        assert np.array_equal(_host(L["r3"], np.int16).reshape(3, h, w), o["r3"])
-        p = bc.image_params(i)
-        assert np.array_equal(p["a"].view(np.uint32), o["a"].view(np.uint32))
+    _check_all(bc, imgs, quals)
+    bc.close()
+
+
+@pytest.mark.slow
+def test_batch_workload_64_uneven_images():
+    """The 64-image uneven workload (about 174 MP): every layer of every image
+    against the oracle, with the tiles the autotuner picks."""
+    wl = synth.workload_batch()
+    imgs = synth.make_workload_images(wl)
+    quals = list(wl.qualities) * len(wl.sizes)
+    bc = B.BatchCodec(wl.sizes, quals)
+    bc.load(imgs)
+    bc.autotune(reps=1)
+    bc.encode()
+    bc.decode()
+    _check_all(bc, imgs, quals)
+    bc.close()
