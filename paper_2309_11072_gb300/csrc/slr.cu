@@ -10,8 +10,6 @@
 // of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
 // them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
 // 32-bit add (values stay <= 4080).
-#include <cuda.h>
-
 #include <initializer_list>
 #include <mutex>
 
@@ -931,7 +929,7 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
     }
 }
 
-// ====================================================================== tensor-map row pipeline
+// ====================================================================== bulk-copy row pipeline
 //
 // For images whose rows are 16-byte aligned (w % 16 == 0, 16-byte aligned
 // planes).  The image is cut into strips of kTileCols = 2048 columns, one
@@ -939,15 +937,17 @@ __global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int
 // all strips, strip after strip, are split into one contiguous range per
 // CTA, and a range becomes tasks of at most kTaskRows rows of one strip.
 // A producer warp streams the range through two shared-memory rings with
-// tensor-map bulk copies (cp.async.bulk.tensor): per S item, the S row of the
-// three planes with 16 halo columns on each side (one 4-D box); per row, its
-// other planes (M and E for the fit and the residual, R and E for the
-// decoder: one 4-D box and one 4-D box of a single plane).  Row j of a task
-// needs S items j, j + 1, j + 2 (rows y - 1, y, y + 1, clamped to the image
-// by the producer, which replicates the edge rows).  A slot's full barrier
-// completes on the bytes of its copies; its empty barrier completes when all
-// consumer warps have arrived.  Box columns past the image are zero-filled by
-// the copy and never read as pixels: edge columns replicate through the
+// 1-D bulk copies (cp.async.bulk, one per plane row: 2 to 4 KB each; a
+// tensor map would cut the 2 KB rows into 16-byte box lines, and moved the
+// same bytes about 1.5 times slower): per S item, the S row of the three
+// planes with 16 halo columns on each side; per row, its other planes (M
+// and E for the fit and the residual, R and E for the decoder).  Row j of a
+// task needs S rows y - 1, y, y + 1 (clamped to the image by the producer,
+// which replicates the edge rows); the consumers keep the filtered rows
+// y - 1 and y in registers, so each S item is read once and released at
+// once, and the S ring runs two items ahead of the aux ring.  A slot's full
+// barrier completes on the bytes of its copies; its empty barrier completes
+// when all consumer warps have arrived.  Edge columns replicate through the
 // neighbour offsets.  Every wait is bounded (see tma.cuh).
 
 constexpr int kTileWarps = 8;                              // consumer warps
@@ -955,14 +955,9 @@ constexpr int kTileThreads = (kTileWarps + 1) * 32;        // + one producer war
 constexpr int kTileCols = kTileWarps * kStripCols;         // 2048
 constexpr int kTileSW = kTileCols + 32;                    // S row with halos, per plane
 constexpr int kTaskRows = 256;
-constexpr int kTileS = 5;                                  // S ring slots
-constexpr int kTileA = 3;                                  // M / E ring slots (fit, residual)
 constexpr uint32_t kTileSBytes = 3u * kTileSW;             // 6240
 constexpr uint32_t kTileSStride = 6272;                    // slot stride, multiple of 128
 static_assert(kTileSStride >= kTileSBytes && kTileSStride % 128 == 0, "S slot");
-// Flush every run this often: a run then holds at most 8 * 16 pixels, which
-// keeps its 32-bit sums exact (see kMaxStripRows).
-constexpr int kRunRows = kMaxStripRows;
 
 enum class TmaMode { kResidual = 0, kDecode = 1, kFit = 2 };
 
@@ -975,19 +970,33 @@ struct TileAux {
     static constexpr uint32_t kBytes = kE + kTileCols;
     static constexpr uint32_t kStride = kBytes;                    // multiple of 128
     static_assert(kStride % 128 == 0, "aux slot");
-    static constexpr int kSlots = kTileA;   // ring slots
-    // CTAs per SM the kernel is built for (the residual kernel's registers
-    // and shared memory allow three; the launch uses three on large images)
-    static constexpr int kCtas = MODE == TmaMode::kResidual ? 3 : 2;
+    // Ring slots: the aux ring (rows j) and the S ring (rows j + 1, so it
+    // runs two items ahead of the aux ring and needs two slots more).  The
+    // fit's bins and queues leave room for 3 aux rows; the residual and the
+    // decoder take deeper rings to keep more bytes in flight per SM.
+    static constexpr int kSlots = MODE == TmaMode::kFit ? 3 : (MODE == TmaMode::kResidual ? 5 : 4);
+    static constexpr int kSSlots = kSlots + 2;
+    // CTAs per SM the kernel is built for
+    static constexpr int kCtas = 2;
 };
 
-struct TileMaps {
-    CUtensorMap s;   // u8 (16, w/16, h, 3): S planes
-    CUtensorMap a;   // u8 (16, w/16, h, 3) M planes, or u16 (8, w/8, h, 3) R planes
-    CUtensorMap e;   // u8 (16, w/16, h, 1): E plane
+// In-order position in a ring of K slots: the slot and the parity of its
+// current use (item i is slot i % K, use i / K).
+template <int K>
+struct RingPos {
+    uint32_t slot, phase;
+    __device__ __forceinline__ void advance() {
+        if (++slot == (uint32_t)K) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
 };
 
 struct TileArgs {
+    const uint8_t* s3;                       // S planes
+    const void* aux;                         // M planes (fit, residual) or R planes (decode)
+    const uint8_t* e;                        // E plane
     int h, w;
     int gf;
     int64_t total_rows;                      // strips * h
@@ -999,15 +1008,6 @@ struct TileArgs {
     unsigned long long* gbins;               // fit
 };
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -1018,16 +1018,18 @@ __device__ __forceinline__ void consumers_sync() {
 }
 
 // The CTA's rows r .. end - 1 in (strip, row) order and its current task.
+// Rows are counted in 32 bits: the tile kernels need w % 16 == 0, so
+// strips * h <= h * w / 2048 + h < 2^31 for every image the ABI accepts.
 struct TileRange {
-    int64_t r, end;
+    int r, end;
     int h;
     int y0, rows, xs;
     __device__ __forceinline__ bool next() {
         if (r >= end) return false;
-        const int64_t c = r / h;
-        y0 = (int)(r - c * h);
-        rows = (int)min(min(end - r, (int64_t)(h - y0)), (int64_t)kTaskRows);
-        xs = (int)c * kTileCols;
+        const int c = r / h;
+        y0 = r - c * h;
+        rows = min(min(end - r, h - y0), kTaskRows);
+        xs = c * kTileCols;
         r += rows;
         return true;
     }
@@ -1035,26 +1037,23 @@ struct TileRange {
 
 __device__ __forceinline__ TileRange tile_range(int64_t total_rows, int h) {
     const int64_t G = gridDim.x, b = blockIdx.x;
-    return TileRange{b * total_rows / G, (b + 1) * total_rows / G, h, 0, 0, 0};
+    return TileRange{(int)(b * total_rows / G), (int)((b + 1) * total_rows / G), h, 0, 0, 0};
 }
 
 // Shared-memory layout of a tile kernel: the two rings, then four barrier
 // arrays, then the mode's own data at `extra`.
 template <TmaMode MODE>
 struct TileSmem {
+    static constexpr int KS = TileAux<MODE>::kSSlots, KA = TileAux<MODE>::kSlots;
     uint32_t s_ring, a_ring, bars, extra;
-    __device__ __forceinline__ uint32_t sfull(int k) const { return bars + 8u * k; }
-    __device__ __forceinline__ uint32_t sempty(int k) const { return bars + 8u * (kTileS + k); }
-    __device__ __forceinline__ uint32_t afull(int k) const { return bars + 8u * (2 * kTileS + k); }
-    __device__ __forceinline__ uint32_t aempty(int k) const {
-        return bars + 8u * (2 * kTileS + TileAux<MODE>::kSlots + k);
-    }
-    __device__ __forceinline__ uint32_t sslot(uint32_t i) const { return s_ring + (i % kTileS) * kTileSStride; }
-    __device__ __forceinline__ uint32_t aslot(uint32_t i) const {
-        return a_ring + (i % TileAux<MODE>::kSlots) * TileAux<MODE>::kStride;
-    }
-    static constexpr uint32_t kRings = kTileS * kTileSStride + TileAux<MODE>::kSlots * TileAux<MODE>::kStride;
-    static constexpr uint32_t kHead = kRings + 8u * 2 * (kTileS + TileAux<MODE>::kSlots);   // multiple of 16
+    __device__ __forceinline__ uint32_t sfull(uint32_t k) const { return bars + 8u * k; }
+    __device__ __forceinline__ uint32_t sempty(uint32_t k) const { return bars + 8u * (KS + k); }
+    __device__ __forceinline__ uint32_t afull(uint32_t k) const { return bars + 8u * (2 * KS + k); }
+    __device__ __forceinline__ uint32_t aempty(uint32_t k) const { return bars + 8u * (2 * KS + KA + k); }
+    __device__ __forceinline__ uint32_t sslot_at(uint32_t k) const { return s_ring + k * kTileSStride; }
+    __device__ __forceinline__ uint32_t aslot_at(uint32_t k) const { return a_ring + k * TileAux<MODE>::kStride; }
+    static constexpr uint32_t kRings = KS * kTileSStride + KA * TileAux<MODE>::kStride;
+    static constexpr uint32_t kHead = kRings + 8u * 2 * (KS + KA);   // multiple of 16
 };
 
 template <TmaMode MODE>
@@ -1062,7 +1061,7 @@ __device__ __forceinline__ TileSmem<MODE> tile_smem(char* dyn) {
     const uint32_t base = (smem_addr(dyn) + 127u) & ~127u;
     TileSmem<MODE> L;
     L.s_ring = base;
-    L.a_ring = base + kTileS * kTileSStride;
+    L.a_ring = base + TileSmem<MODE>::KS * kTileSStride;
     L.bars = base + TileSmem<MODE>::kRings;
     L.extra = base + TileSmem<MODE>::kHead;
     return L;
@@ -1071,11 +1070,11 @@ __device__ __forceinline__ TileSmem<MODE> tile_smem(char* dyn) {
 template <TmaMode MODE>
 __device__ __forceinline__ void tile_init_barriers(const TileSmem<MODE>& L) {
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kTileS; ++k) {
+        for (int k = 0; k < TileSmem<MODE>::KS; ++k) {
             mbar_init(L.sfull(k), 1);
             mbar_init(L.sempty(k), kTileWarps);
         }
-        for (int k = 0; k < TileAux<MODE>::kSlots; ++k) {
+        for (int k = 0; k < TileSmem<MODE>::KA; ++k) {
             mbar_init(L.afull(k), 1);
             mbar_init(L.aempty(k), kTileWarps);
         }
@@ -1083,97 +1082,97 @@ __device__ __forceinline__ void tile_init_barriers(const TileSmem<MODE>& L) {
     }
 }
 
-// The producer (one thread): items in the order the consumers use them.
-// Returns false if a wait for a free slot gave up.
+// The producer (one thread): items in the order the consumers use them,
+// each as 1-D bulk copies of whole plane rows (one per plane; 16-byte
+// aligned because w % 16 == 0 and the planes are 16-byte aligned).  An S
+// item is row ys of the three S planes, columns xs - 16 .. xs + 2063 clipped
+// to the image, at offset x - (xs - 16) of each plane's slot row; an aux item
+// is row y of the three aux planes and of E, columns xs .. xs + 2047 clipped.
+// Slot bytes past the image are never read as pixels.  Stops issuing if a
+// wait for a free slot gave up.
 template <TmaMode MODE>
-__device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const CUtensorMap* tm_s, const CUtensorMap* tm_a,
-                                          const CUtensorMap* tm_e, const TileArgs& A) {
+__device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const TileArgs& A) {
+    constexpr int KS = TileSmem<MODE>::KS, KA = TileSmem<MODE>::KA;
+    constexpr uint32_t kEl = TileAux<MODE>::kElem;
+    const int64_t n = (int64_t)A.h * A.w;
+    const uint8_t* aux = static_cast<const uint8_t*>(A.aux);
     TileRange P = tile_range(A.total_rows, A.h);
-    uint32_t si = 0, ai = 0;
+    uint32_t si = 0, ai = 0;   // items issued
+    RingPos<KS> sp{0u, 0u};
+    RingPos<KA> ap{0u, 0u};
     bool ok = true;
     while (ok && P.next()) {
+        const int xa = max(P.xs - 16, 0), xb = min(P.xs + kTileCols + 16, A.w);
+        const uint32_t s_bytes = (uint32_t)(xb - xa), s_off = (uint32_t)(xa - (P.xs - 16));
+        const uint32_t cols = (uint32_t)(min(P.xs + kTileCols, A.w) - P.xs);
         for (int k = 0; k < P.rows + 2 && ok; ++k) {
             // S item k: row y0 - 1 + k, clamped (edge rows replicate)
             {
-                const int slot = (int)(si % kTileS);
-                if (si >= (uint32_t)kTileS)
-                    ok = mbar_wait(L.sempty(slot), ((si / kTileS) - 1u) & 1u, &g_slrme_status, A.max_spins);
+                if (si >= (uint32_t)KS) ok = mbar_wait(L.sempty(sp.slot), sp.phase ^ 1u, &g_slrme_status, A.max_spins);
                 if (!ok) break;
                 const int ys = min(max(P.y0 - 1 + k, 0), A.h - 1);
+                const uint32_t dst = L.sslot_at(sp.slot) + s_off, bar = L.sfull(sp.slot);
+                const uint8_t* src = A.s3 + (int64_t)ys * A.w + xa;
                 fence_async_shared();
-                mbar_arrive_expect_tx(L.sfull(slot), kTileSBytes);
-                tma_load_4d(L.sslot(si), tm_s, 0, P.xs / 16 - 1, ys, 0, L.sfull(slot));
+                mbar_arrive_expect_tx(bar, 3u * s_bytes);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tma_load_1d(dst + (uint32_t)c * kTileSW, src + c * n, s_bytes, bar);
                 ++si;
+                sp.advance();
             }
             if (k >= 2) {   // the other planes of row y0 + k - 2
-                constexpr uint32_t KA = TileAux<MODE>::kSlots;
-                const int slot = (int)(ai % KA);
-                if (ai >= KA) ok = mbar_wait(L.aempty(slot), ((ai / KA) - 1u) & 1u, &g_slrme_status, A.max_spins);
+                if (ai >= (uint32_t)KA) ok = mbar_wait(L.aempty(ap.slot), ap.phase ^ 1u, &g_slrme_status, A.max_spins);
                 if (!ok) break;
-                const int y = P.y0 + k - 2;
-                const uint32_t dst = L.aslot(ai);
+                const int64_t row = (int64_t)(P.y0 + k - 2) * A.w + P.xs;
+                const uint32_t dst = L.aslot_at(ap.slot), bar = L.afull(ap.slot);
                 fence_async_shared();
-                mbar_arrive_expect_tx(L.afull(slot), TileAux<MODE>::kBytes);
-                if constexpr (MODE == TmaMode::kDecode)
-                    tma_load_4d(dst, tm_a, 0, P.xs / 8, y, 0, L.afull(slot));
-                else
-                    tma_load_4d(dst, tm_a, 0, P.xs / 16, y, 0, L.afull(slot));
-                tma_load_4d(dst + TileAux<MODE>::kE, tm_e, 0, P.xs / 16, y, 0, L.afull(slot));
+                mbar_arrive_expect_tx(bar, (3u * kEl + 1u) * cols);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    tma_load_1d(dst + (uint32_t)c * TileAux<MODE>::kPlane, aux + (c * n + row) * kEl, kEl * cols, bar);
+                tma_load_1d(dst + TileAux<MODE>::kE, A.e + row, cols, bar);
                 ++ai;
+                ap.advance();
             }
         }
     }
     // before leaving, wait (bounded) for the last copy into every slot, so
     // no copy is in flight if the consumers stopped early
     const int spins = ok ? A.max_spins : (1 << 10);
-    for (uint32_t k = si > (uint32_t)kTileS ? si - kTileS : 0; k < si; ++k)
-        mbar_wait(L.sfull((int)(k % kTileS)), (k / kTileS) & 1u, &g_slrme_status, spins);
-    constexpr uint32_t KA = TileAux<MODE>::kSlots;
-    for (uint32_t k = ai > KA ? ai - KA : 0; k < ai; ++k)
-        mbar_wait(L.afull((int)(k % KA)), (k / KA) & 1u, &g_slrme_status, spins);
+    for (uint32_t k = si > (uint32_t)KS ? si - KS : 0; k < si; ++k)
+        mbar_wait(L.sfull(k % KS), (k / KS) & 1u, &g_slrme_status, spins);
+    for (uint32_t k = ai > (uint32_t)KA ? ai - KA : 0; k < ai; ++k)
+        mbar_wait(L.afull(k % KA), (k / KA) & 1u, &g_slrme_status, spins);
 }
 
-// A consumer warp is done with a slot (all lanes call after their last read).
-__device__ __forceinline__ void tile_release(uint32_t empty_bar, int lane) {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(empty_bar);
-}
-
-// One consumer warp's view of the rings: waits and releases by item index.
+// One consumer warp's view of the rings: it waits for, reads and releases
+// the items of each ring in order.
 template <TmaMode MODE>
 struct TileConsumer {
     TileSmem<MODE> L;
     int max_spins;
-    __device__ __forceinline__ bool wait_s(uint32_t i) const {
-        return mbar_wait(L.sfull((int)(i % kTileS)), (i / kTileS) & 1u, &g_slrme_status, max_spins);
+    RingPos<TileSmem<MODE>::KS> s;
+    RingPos<TileSmem<MODE>::KA> a;
+    __device__ __forceinline__ bool wait_s() const {
+        return mbar_wait(L.sfull(s.slot), s.phase, &g_slrme_status, max_spins);
     }
-    __device__ __forceinline__ bool wait_a(uint32_t i) const {
-        constexpr uint32_t KA = TileAux<MODE>::kSlots;
-        return mbar_wait(L.afull((int)(i % KA)), (i / KA) & 1u, &g_slrme_status, max_spins);
+    __device__ __forceinline__ bool wait_a() const {
+        return mbar_wait(L.afull(a.slot), a.phase, &g_slrme_status, max_spins);
     }
-    // all lanes call after their last read of the items
-    __device__ __forceinline__ void release_s(uint32_t i, int lane) const {
+    __device__ __forceinline__ uint32_t s_addr() const { return L.sslot_at(s.slot); }
+    __device__ __forceinline__ uint32_t a_addr() const { return L.aslot_at(a.slot); }
+    // all lanes call after their last read of the current item
+    __device__ __forceinline__ void release_s(int lane) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(L.sempty((int)(i % kTileS)));
+        if (lane == 0) mbar_arrive(L.sempty(s.slot));
+        s.advance();
     }
-    __device__ __forceinline__ void release_a(uint32_t i, int lane) const {
+    __device__ __forceinline__ void release_a(int lane) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(L.aempty((int)(i % TileAux<MODE>::kSlots)));
+        if (lane == 0) mbar_arrive(L.aempty(a.slot));
+        a.advance();
     }
 };
-
-// One lane's S row segment from an S slot (shared address): 8 bytes plus the
-// neighbours at the given offsets.
-__device__ __forceinline__ Row10 tile_seg(uint32_t row, int own, int offl, int offr) {
-    Row10 R;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(R.lo), "=r"(R.hi) : "r"(row + own));
-    uint32_t l, r;
-    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(l) : "r"(row + offl));
-    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(r) : "r"(row + offr));
-    R.l = l;
-    R.r = r;
-    return R;
-}
 
 __device__ __forceinline__ uint2 lds64(uint32_t a) {
     uint2 v;
@@ -1200,65 +1199,172 @@ struct LaneCols {
     }
 };
 
-// x = 16 S* of channel c for the lane's 8 pixels, as 16-bit pairs.
-__device__ __forceinline__ void tile_x(uint32_t sa, uint32_t sb, uint32_t sc, int c, const LaneCols& lc, bool gf,
-                                       uint32_t (&X)[4]) {
-    const uint32_t po = (uint32_t)c * kTileSW;
-    if (gf) {
-        gf_pairs(tile_seg(sa + po, lc.own, lc.offl, lc.offr), tile_seg(sb + po, lc.own, lc.offl, lc.offr),
-                 tile_seg(sc + po, lc.own, lc.offl, lc.offr), true, X);
-    } else {
-        const Row10 r = tile_seg(sb + po, lc.own, lc.offl, lc.offr);
-        gf_pairs(r, r, r, false, X);
+// ---------------------------------------------------------------- fit on the tile pipeline
+//
+// A consumer lane keeps, per channel, the horizontally filtered S rows y - 1
+// and y as 16-bit pairs (the 3x3 binomial filter is separable: [1 2 1] along
+// x, then [1 2 1] along y), so each S row is read from the ring once and
+// released at once.  Its pixels' sums go to two runs per lane: `all` holds
+// both exponent parities, `odd` the odd one; the even run is all - odd.  A run
+// lives until its region changes or its task ends, at most kTaskRows rows of
+// 8 pixels.  sum x x is kept in two parts, sum x (x & 255) and sum x (x >> 8),
+// so every run word stays below 2^32 at that length.
+
+struct Run2 {
+    int E;            // region (the even one for `all`), -1 = none
+    uint32_t n;
+    uint32_t sx[3], sy[3], sxy[3], sxl[3], sxh[3];
+};
+static_assert(8ull * kTaskRows * 4080ull * 255ull < (1ull << 32), "run sums of x y exceed 32 bits");
+
+__device__ __forceinline__ void run2_reset(Run2& a, int E) {
+    a.E = E;
+    a.n = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.sx[c] = a.sy[c] = a.sxy[c] = a.sxl[c] = a.sxh[c] = 0;
+}
+
+__device__ __forceinline__ void run2_sub(Run2& a, const Run2& b) {   // a -= b (E kept)
+    a.n -= b.n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a.sx[c] -= b.sx[c];
+        a.sy[c] -= b.sy[c];
+        a.sxy[c] -= b.sxy[c];
+        a.sxl[c] -= b.sxl[c];
+        a.sxh[c] -= b.sxh[c];
     }
 }
 
-// ---------------------------------------------------------------- fit on the tile pipeline
-
-// One channel of an 8-pixel segment added to a run: x pairs and y bytes
-// already masked to the run's pixels.
-__device__ __forceinline__ void chan_accum(const uint32_t (&x)[4], uint32_t yl, uint32_t yh, RunAcc& a, int c) {
-    uint32_t sx = a.sx[c];
+__device__ __forceinline__ void run2_add(Run2& a, const Run2& b) {   // a += b (E kept)
+    a.n += b.n;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) sx = __dp2a_lo(x[k], 0x0101u, sx);
-    a.sx[c] = sx;
-    a.sy[c] = __dp4a(yl, 0x01010101u, __dp4a(yh, 0x01010101u, a.sy[c]));
-    uint32_t q = __dp2a_lo(x[0], yl, a.sxy[c]);
-    q = __dp2a_hi(x[1], yl, q);
-    q = __dp2a_lo(x[2], yh, q);
-    a.sxy[c] = __dp2a_hi(x[3], yh, q);
-    uint32_t r = a.sxx[c];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t lo16 = x[k] & 0xFFFFu, hi16 = x[k] >> 16;
-        r += lo16 * lo16 + hi16 * hi16;
+    for (int c = 0; c < 3; ++c) {
+        a.sx[c] += b.sx[c];
+        a.sy[c] += b.sy[c];
+        a.sxy[c] += b.sxy[c];
+        a.sxl[c] += b.sxl[c];
+        a.sxh[c] += b.sxh[c];
     }
-    a.sxx[c] = r;
+}
+
+// One channel of an 8-pixel segment added to sums (sum x, sum y, sum x y,
+// sum x (x & 255), sum x (x >> 8)): x as 16-bit pairs and the y bytes, both
+// already masked to the run's pixels (21 operations).
+__device__ __forceinline__ void seg_accum5(const uint32_t (&X)[4], uint32_t yl, uint32_t yh, uint32_t& sx,
+                                           uint32_t& sy, uint32_t& sxy, uint32_t& sxl, uint32_t& sxh) {
+    const uint32_t ps = X[0] + X[1] + X[2] + X[3];   // each half at most 4 * 4080
+    sx = __dp2a_lo(ps, 0x0101u, sx);
+    sy = __dp4a(yl, 0x01010101u, __dp4a(yh, 0x01010101u, sy));
+    uint32_t q = __dp2a_lo(X[0], yl, sxy);
+    q = __dp2a_hi(X[1], yl, q);
+    q = __dp2a_lo(X[2], yh, q);
+    sxy = __dp2a_hi(X[3], yh, q);
+    // x x = x (x & 255) + 256 x (x >> 8): the low and high bytes of each x as
+    // byte operands of the 16 x 8-bit dot products
+    const uint32_t la = __byte_perm(X[0], X[1], 0x6420), ha = __byte_perm(X[0], X[1], 0x7531);
+    const uint32_t lb = __byte_perm(X[2], X[3], 0x6420), hb = __byte_perm(X[2], X[3], 0x7531);
+    uint32_t l = __dp2a_lo(X[0], la, sxl);
+    l = __dp2a_hi(X[1], la, l);
+    l = __dp2a_lo(X[2], lb, l);
+    sxl = __dp2a_hi(X[3], lb, l);
+    uint32_t g = __dp2a_lo(X[0], ha, sxh);
+    g = __dp2a_hi(X[1], ha, g);
+    g = __dp2a_lo(X[2], hb, g);
+    sxh = __dp2a_hi(X[3], hb, g);
+}
+
+__device__ __forceinline__ void seg_accum(const uint32_t (&X)[4], uint32_t yl, uint32_t yh, Run2& r, int c) {
+    seg_accum5(X, yl, yh, r.sx[c], r.sy[c], r.sxy[c], r.sxl[c], r.sxh[c]);
+}
+
+// Horizontal [1 2 1] of one row segment (its 8 bytes lo/hi and the bytes l, r
+// left and right of it) as 16-bit pairs: H[k] = (h(2k), h(2k + 1)).
+__device__ __forceinline__ void hfilter(uint32_t lo, uint32_t hi, uint32_t l, uint32_t r, uint32_t (&H)[4]) {
+    const uint32_t P0 = __byte_perm(lo, 0, 0x4140), P1 = __byte_perm(lo, 0, 0x4342);
+    const uint32_t P2 = __byte_perm(hi, 0, 0x4140), P3 = __byte_perm(hi, 0, 0x4342);
+    const uint32_t L0 = __byte_perm(l, P0, 0x5410);    // (s[-1], s[0])
+    const uint32_t L1 = __byte_perm(P0, P1, 0x5432);   // (s[1], s[2])
+    const uint32_t L2 = __byte_perm(P1, P2, 0x5432);   // (s[3], s[4])
+    const uint32_t L3 = __byte_perm(P2, P3, 0x5432);   // (s[5], s[6])
+    const uint32_t L4 = __byte_perm(P3, r, 0x5432);    // (s[7], s[8])
+    H[0] = L0 + 2u * P0 + L1;
+    H[1] = L1 + 2u * P1 + L2;
+    H[2] = L2 + 2u * P2 + L3;
+    H[3] = L3 + 2u * P3 + L4;
+}
+
+// The bytes of one lane's segment of plane c of an S slot as 16-bit pairs
+// (kGf: horizontally filtered; else unpacked).
+template <bool kGf>
+__device__ __forceinline__ void s_row_pairs(uint32_t slot, int c, const LaneCols& lc, uint32_t (&H)[4]) {
+    const uint32_t row = slot + (uint32_t)c * kTileSW;
+    const uint2 v = lds64(row + lc.own);
+    if constexpr (kGf) {
+        uint32_t l, r;
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(l) : "r"(row + lc.offl));
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(r) : "r"(row + lc.offr));
+        hfilter(v.x, v.y, l, r, H);
+    } else {
+        H[0] = __byte_perm(v.x, 0, 0x4140);
+        H[1] = __byte_perm(v.x, 0, 0x4342);
+        H[2] = __byte_perm(v.y, 0, 0x4140);
+        H[3] = __byte_perm(v.y, 0, 0x4342);
+    }
 }
 
 // Two per-warp queues: flushed runs (their sums) and segments that need
 // per-pixel work (their pixels).  Each is drained by its own code path, one
-// entry per lane, so draining runs -- the common case -- never pays for the
-// per-pixel segment path.  A row queues at most one segment per lane, so the
-// segment queue holds 32 (a row's segments are written piece by piece while
-// the row is processed); runs, complete when queued, go in chunks that fit
-// the 16-entry run queue, draining it in between.
+// entry per lane, so draining runs never pays for the per-pixel segment path.
+// A row queues at most one segment per lane, so the segment queue holds 32 (a
+// row's segments are written piece by piece while the row is processed); runs,
+// complete when queued, go in chunks that fit the 16-entry run queue, draining
+// it in between.  A run entry: N, then per channel sum x, sum y, sum x y,
+// sum x (x & 255) and sum x (x >> 8), then the region (odd stride: distinct
+// banks).
 constexpr int kRunQ = 16;
-constexpr int kRunStride = 15;   // 13 sums, the region, a pad word (odd stride: distinct banks)
-constexpr int kSegQ = 32;        // segment entries of kQueueStride words
+constexpr int kRunWords = 1 + 5 * 3;
+constexpr int kRunStride = kRunWords + 1;   // 17
+constexpr int kSegQ = 32;                   // segment entries of kQueueStride words
 struct FitQueues {
     uint32_t* R;   // run entries
     uint32_t* Q;   // segment entries
     int nr, nq;    // entries queued (warp-uniform)
 };
 
+// Exactness of the tile fit's shared bins: a run entry adds sum x x as two
+// values (sum x (x & 255) and 256 sum x (x >> 8)), so a low word takes at most
+// two additions per pixel; a CTA adds at most kTileFitMaxPixels pixels, which
+// keeps every low word below 2^21 (2^12 - 1) < 2^32 and every high word below
+// 2^19 4080^2 / 2^12 < 2^32.
+constexpr int64_t kTileFitMaxPixels = (int64_t)1 << 19;
+static_assert(2ull * kTileFitMaxPixels * 4095ull < (1ull << 32), "tile fit low words overflow");
+static_assert((unsigned long long)kTileFitMaxPixels * 4080ull * 4080ull / 4096ull < (1ull << 32),
+              "tile fit high words overflow");
+
 __device__ __forceinline__ void drain_runs(FitQueues& fq, SmemBins& bins, int lane) {
     if (lane < fq.nr) {
         const uint32_t* q = fq.R + lane * kRunStride;
-        uint32_t acc[kNsum];
+        const uint32_t B = smem_addr(&bins);
+        const uint32_t lo = B + 4u * (uint32_t)(q[kRunWords] * kNsum), hi = lo + 4u * kNbin * kNsum;
+        red_add(lo, q[0] & 0xFFFu);
+        red_add(hi, q[0] >> 12);
 #pragma unroll
-        for (int j = 0; j < kNsum; ++j) acc[j] = q[j];
-        bins_add32(smem_addr(&bins), (int)q[kNsum], acc);
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t* v = q + 1 + 5 * c;
+            const uint32_t a = 4u * (1 + 4 * c);
+            red_add(lo + a, v[0] & 0xFFFu);
+            red_add(hi + a, v[0] >> 12);
+            red_add(lo + a + 4u, v[1] & 0xFFFu);
+            red_add(hi + a + 4u, v[1] >> 12);
+            red_add(lo + a + 8u, v[2] & 0xFFFu);
+            red_add(hi + a + 8u, v[2] >> 12);
+            // sum x x = sxl + 256 sxh
+            red_add(lo + a + 12u, v[3] & 0xFFFu);
+            red_add(hi + a + 12u, v[3] >> 12);
+            red_add(lo + a + 12u, (v[4] & 0xFu) << 8);
+            red_add(hi + a + 12u, v[4] >> 4);
+        }
     }
     __syncwarp();
     fq.nr = 0;
@@ -1305,7 +1411,7 @@ __device__ __forceinline__ void drain_segs(FitQueues& fq, SmemBins& bins, int la
 // Queues the run of every lane with `want` set: the even run (all - odd,
 // region all.E) or the odd run (odd, region odd.E), in chunks that fit.
 template <bool kEven>
-__device__ __forceinline__ void push_run(FitQueues& fq, bool want, const RunAcc& all, const RunAcc& odd,
+__device__ __forceinline__ void push_run(FitQueues& fq, bool want, const Run2& all, const Run2& odd,
                                          SmemBins& bins, int lane) {
     unsigned m = __ballot_sync(0xffffffffu, want);
     while (m) {
@@ -1315,27 +1421,24 @@ __device__ __forceinline__ void push_run(FitQueues& fq, bool want, const RunAcc&
         while (__popc(take) > kRunQ - fq.nr) take &= ~(1u << (31 - __clz(take)));
         if (take & (1u << lane)) {
             uint32_t* q = fq.R + (fq.nr + __popc(take & ((1u << lane) - 1u))) * kRunStride;
-            if constexpr (kEven) {
-                q[0] = all.n - odd.n;
+            q[0] = kEven ? all.n - odd.n : odd.n;   // even: all - odd; odd: odd
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    q[1 + 4 * c] = all.sx[c] - odd.sx[c];
-                    q[2 + 4 * c] = all.sy[c] - odd.sy[c];
-                    q[3 + 4 * c] = all.sxy[c] - odd.sxy[c];
-                    q[4 + 4 * c] = all.sxx[c] - odd.sxx[c];
+            for (int c = 0; c < 3; ++c) {
+                if constexpr (kEven) {
+                    q[1 + 5 * c] = all.sx[c] - odd.sx[c];
+                    q[2 + 5 * c] = all.sy[c] - odd.sy[c];
+                    q[3 + 5 * c] = all.sxy[c] - odd.sxy[c];
+                    q[4 + 5 * c] = all.sxl[c] - odd.sxl[c];
+                    q[5 + 5 * c] = all.sxh[c] - odd.sxh[c];
+                } else {
+                    q[1 + 5 * c] = odd.sx[c];
+                    q[2 + 5 * c] = odd.sy[c];
+                    q[3 + 5 * c] = odd.sxy[c];
+                    q[4 + 5 * c] = odd.sxl[c];
+                    q[5 + 5 * c] = odd.sxh[c];
                 }
-                q[kNsum] = (uint32_t)all.E;
-            } else {
-                q[0] = odd.n;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    q[1 + 4 * c] = odd.sx[c];
-                    q[2 + 4 * c] = odd.sy[c];
-                    q[3 + 4 * c] = odd.sxy[c];
-                    q[4 + 4 * c] = odd.sxx[c];
-                }
-                q[kNsum] = (uint32_t)odd.E;
             }
+            q[kRunWords] = (uint32_t)(kEven ? all.E : odd.E);
         }
         __syncwarp();
         fq.nr += __popc(take);
@@ -1348,13 +1451,199 @@ constexpr uint32_t kFitExtra = sizeof(SmemBins) + kFitQueueBytes;
 constexpr size_t kTileFitSmem = 128 + TileSmem<TmaMode::kFit>::kHead + kFitExtra;
 static_assert(2 * (kTileFitSmem + 1024) <= 228 * 1024, "two fit CTAs per SM");
 
-// Per lane: `all` holds the sums of both runs, `odd` those of the odd run;
-// the even run is all - odd.  A run that changes region leaves through the
-// warp's queue; a task's runs are flushed every kRunRows rows and at its end.
-__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile(const __grid_constant__ CUtensorMap tm_s,
-                                                               const __grid_constant__ CUtensorMap tm_a,
-                                                               const __grid_constant__ CUtensorMap tm_e,
-                                                               const TileArgs A) {
+// x = 16 S* of channel c for the lane's 8 pixels as 16-bit pairs, from the
+// window (rows y - 1 and y) and the new S row y + 1 in slot `sn`; the window
+// moves down one row.
+template <bool kGf>
+__device__ __forceinline__ void window_x(uint32_t sn, int c, const LaneCols& lc, uint32_t (&Hm)[4],
+                                         uint32_t (&H0)[4], uint32_t (&X)[4]) {
+    uint32_t Hn[4];
+    s_row_pairs<kGf>(sn, c, lc, Hn);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if constexpr (kGf) {
+            X[k] = Hm[k] + 2u * H0[k] + Hn[k];
+            Hm[k] = H0[k];
+        } else {
+            X[k] = H0[k] << 4;
+        }
+        H0[k] = Hn[k];
+    }
+}
+
+// Moves a lane's runs to the region(s) of its next segment: a run whose
+// region changes leaves through the queue first (the even run is all - odd).
+// Ee / Eo: the segment's even / odd region; has_e / has_o: whether it has
+// pixels of that parity.
+__device__ __forceinline__ void runs_rekey(FitQueues& fq, Run2& all, Run2& odd, bool has_e, int Ee, bool has_o,
+                                           int Eo, SmemBins& bins, int lane) {
+    const bool chg_e = has_e && Ee != all.E;
+    const bool chg_o = has_o && Eo != odd.E;
+    push_run<true>(fq, chg_e && all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
+    push_run<false>(fq, chg_o && odd.E >= 0 && odd.n != 0u, all, odd, bins, lane);
+    if (chg_e) {   // the even part left: all = odd
+        const int keep = odd.E;
+        all = odd;
+        all.E = Ee;
+        odd.E = keep;
+    }
+    if (chg_o) {   // the odd part left
+        const int keep = all.E;
+        run2_sub(all, odd);
+        all.E = keep;
+        run2_reset(odd, Eo);
+    }
+}
+
+// The fit's consumer loop over the CTA's tasks.  Per row and lane: the
+// exponent bytes decide, for the whole warp, between the fast path (every
+// lane's 8 pixels in one region: one set of sums per channel, added to the
+// run of the region's parity) and the general one (one even and one odd
+// region per segment: the odd pixels' sums and all sums; anything else is
+// queued for per-pixel work); then, channel by channel, the new S row moves
+// the filter window and x = 16 S* is added.
+template <bool kGf>
+__device__ __forceinline__ void fit_consume(const TileSmem<TmaMode::kFit>& L, const TileArgs& A, SmemBins& bins,
+                                            uint32_t* queue, int warp, int lane) {
+    TileConsumer<TmaMode::kFit> C{L, A.max_spins, {0u, 0u}, {0u, 0u}};
+    const int w = A.w;
+    FitQueues fq;
+    fq.R = queue + warp * (kRunQ * kRunStride + kSegQ * kQueueStride);
+    fq.Q = fq.R + kRunQ * kRunStride;
+    fq.nr = fq.nq = 0;
+    Run2 all, odd;
+    TileRange T = tile_range(A.total_rows, A.h);
+    bool ok = true;
+    while (ok && T.next()) {
+        const LaneCols lc(T.xs, w, warp, lane);
+        run2_reset(all, -1);
+        run2_reset(odd, -1);
+        // the window: rows y0 - 1 and y0 (S items 0 and 1 of the task)
+        uint32_t Hm[3][4], H0[3][4];
+        ok = C.wait_s();
+        if (!ok) break;
+        if constexpr (kGf) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_row_pairs<kGf>(C.s_addr(), c, lc, Hm[c]);
+        }
+        C.release_s(lane);
+        ok = C.wait_s();
+        if (!ok) break;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_row_pairs<kGf>(C.s_addr(), c, lc, H0[c]);
+        C.release_s(lane);
+        for (int j = 0; j < T.rows; ++j) {
+            ok = C.wait_s() && C.wait_a();
+            if (!ok) break;
+            const uint32_t sn = C.s_addr();
+            const uint32_t as = C.a_addr() + kStripCols * warp + 8 * lane;
+            const uint2 ev = lds64(as + TileAux<TmaMode::kFit>::kE);
+            const uint32_t elo = ev.x, ehi = ev.y;
+            const uint32_t E1 = elo & 255u;
+            const bool uni = elo == ehi && elo == E1 * 0x01010101u;
+            if (__all_sync(0xffffffffu, uni || !lc.inside)) {
+                // ---- fast path: one region per lane segment
+                const bool isodd = (E1 & 1u) != 0u;
+                runs_rekey(fq, all, odd, lc.inside && !isodd, (int)E1, lc.inside && isodd, (int)E1, bins, lane);
+                const uint32_t mo = lc.inside && isodd ? 0xFFFFFFFFu : 0u;
+                const uint32_t nadd = lc.inside ? 8u : 0u;
+                all.n += nadd;
+                odd.n += nadd & mo;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
+                    const uint2 mv = lds64(as + (uint32_t)c * TileAux<TmaMode::kFit>::kPlane);
+                    if (lc.inside) {
+                        uint32_t sx = 0u, sy = 0u, sxy = 0u, sxl = 0u, sxh = 0u;   // channel c of the segment
+                        seg_accum5(X, mv.x, mv.y, sx, sy, sxy, sxl, sxh);
+                        all.sx[c] += sx;
+                        all.sy[c] += sy;
+                        all.sxy[c] += sxy;
+                        all.sxl[c] += sxl;
+                        all.sxh[c] += sxh;
+                        odd.sx[c] += sx & mo;
+                        odd.sy[c] += sy & mo;
+                        odd.sxy[c] += sxy & mo;
+                        odd.sxl[c] += sxl & mo;
+                        odd.sxh[c] += sxh & mo;
+                    }
+                }
+            } else {
+                // ---- general path: byte masks of the odd-exponent pixels; the
+                // segment's odd (even) region is the OR of its odd (even) bytes,
+                // which equals each of them exactly when they are all equal
+                const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+                uint32_t eo = (elo & olo) | (ehi & ohi), ee = (elo & ~olo) | (ehi & ~ohi);
+                eo |= eo >> 16;
+                ee |= ee >> 16;
+                const uint32_t Eo = (eo | (eo >> 8)) & 255u, Ee = (ee | (ee >> 8)) & 255u;
+                const uint32_t Eo4 = Eo * 0x01010101u, Ee4 = Ee * 0x01010101u;
+                const bool two = ((((elo ^ Eo4) & olo) | ((ehi ^ Eo4) & ohi) | ((elo ^ Ee4) & ~olo) |
+                                   ((ehi ^ Ee4) & ~ohi)) == 0u);
+                const bool slow = lc.inside && !two;
+                const bool take = lc.inside && two;
+                const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
+                runs_rekey(fq, all, odd, take && po_n != 8u, (int)Ee, po_n != 0u, (int)Eo, bins, lane);
+                const unsigned want = __ballot_sync(0xffffffffu, slow);
+                uint32_t qe = 0u;   // word offset of this lane's segment entry
+                if (want) {
+                    if (fq.nq + __popc(want) > kSegQ) drain_segs(fq, bins, lane);
+                    qe = (uint32_t)(fq.nq + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+                }
+                uint32_t k16[4];
+                mask16(olo, ohi, k16);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
+                    const uint2 mv = lds64(as + (uint32_t)c * TileAux<TmaMode::kFit>::kPlane);
+                    if (take) {
+                        uint32_t xo[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) xo[k] = X[k] & k16[k];
+                        seg_accum(xo, mv.x & olo, mv.y & ohi, odd, c);
+                        seg_accum(X, mv.x, mv.y, all, c);
+                    }
+                    if (want) {   // warp-uniform: skipped when no lane queues a segment
+                        if (slow) {
+                            uint32_t* q = fq.Q + qe;
+                            q[2 + c] = mv.x;
+                            q[5 + c] = mv.y;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) q[8 + 4 * c + k] = X[k];
+                        }
+                    }
+                }
+                odd.n += po_n;
+                all.n += take ? 8u : 0u;
+                if (want) {
+                    if (slow) {
+                        uint32_t* q = fq.Q + qe;
+                        q[0] = elo;
+                        q[1] = ehi;
+                        q[20] = 8u;
+                    }
+                    __syncwarp();
+                    fq.nq += __popc(want);
+                }
+            }
+            C.release_s(lane);
+            C.release_a(lane);
+        }
+        if (!ok) break;
+        // the task's runs leave
+        push_run<true>(fq, all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
+        push_run<false>(fq, odd.E >= 0 && odd.n != 0u, all, odd, bins, lane);
+    }
+    if (ok) {
+        drain_runs(fq, bins, lane);
+        drain_segs(fq, bins, lane);
+    }
+}
+
+template <bool kGf>
+__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile(const TileArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TileSmem<TmaMode::kFit> L = tile_smem<TmaMode::kFit>(dyn);
@@ -1365,7 +1654,7 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k
     __syncthreads();
 
     if (warp == kTileWarps) {
-        if (lane == 0) tile_produce(L, &tm_s, &tm_a, &tm_e, A);
+        if (lane == 0) tile_produce(L, A);
         return;
     }
     // the consumers clear the bins while the first copies are in flight
@@ -1373,117 +1662,7 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k
     for (int i = threadIdx.x; i < (int)(sizeof(SmemBins) / 16); i += kTileWarps * 32)
         reinterpret_cast<uint4*>(extra)[i] = make_uint4(0u, 0u, 0u, 0u);
     consumers_sync();
-    const TileConsumer<TmaMode::kFit> C{L, A.max_spins};
-    const int w = A.w;
-    const bool gf = A.gf != 0;
-    FitQueues fq;
-    fq.R = queue + warp * (kRunQ * kRunStride + kSegQ * kQueueStride);
-    fq.Q = fq.R + kRunQ * kRunStride;
-    fq.nr = fq.nq = 0;
-    RunAcc all, odd;
-    TileRange T = tile_range(A.total_rows, A.h);
-    uint32_t si = 0, ai = 0;
-    bool ok = true;
-    while (ok && T.next()) {
-        const LaneCols lc(T.xs, w, warp, lane);
-        run_reset(all, -1);
-        run_reset(odd, -1);
-        ok = C.wait_s(si) && C.wait_s(si + 1);
-        for (int j = 0; j < T.rows && ok; ++j) {
-            ok = C.wait_s(si + j + 2) && C.wait_a(ai + j);
-            if (!ok) break;
-            const uint32_t sa = L.sslot(si + j), sb = L.sslot(si + j + 1), sc = L.sslot(si + j + 2);
-            const uint32_t as = L.aslot(ai + j) + kStripCols * warp + 8 * lane;
-            const uint2 ev = lds64(as + TileAux<TmaMode::kFit>::kE);
-            const uint32_t elo = ev.x, ehi = ev.y;
-            // byte masks of the odd-exponent pixels and the two exponents
-            const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
-            const uint32_t Eo = max_byte(elo & olo, ehi & ohi);
-            const uint32_t Ee = max_byte(elo & ~olo, ehi & ~ohi);
-            const bool two = ((elo ^ (Eo * 0x01010101u)) & olo) == 0 && ((ehi ^ (Eo * 0x01010101u)) & ohi) == 0 &&
-                             ((elo ^ (Ee * 0x01010101u)) & ~olo) == 0 &&
-                             ((ehi ^ (Ee * 0x01010101u)) & ~ohi) == 0;
-            const bool slow = lc.inside && !two;
-            const bool take = lc.inside && two;
-            const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
-            const bool chg_o = po_n != 0u && (int)Eo != odd.E;
-            const bool chg_e = take && po_n != 8u && (int)Ee != all.E;
-            // a run whose region changes leaves first (the even run is all - odd)
-            push_run<true>(fq, chg_e && all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
-            push_run<false>(fq, chg_o && odd.E >= 0 && odd.n != 0u, all, odd, bins, lane);
-            if (chg_e) {
-                const int keep = odd.E;
-                all = odd;        // the even part leaves: all - odd = 0
-                all.E = (int)Ee;
-                odd.E = keep;
-            }
-            if (chg_o) {
-                const int keep = all.E;
-                run_minus(all, odd);
-                all.E = keep;
-                run_reset(odd, (int)Eo);
-            }
-            const unsigned want = __ballot_sync(0xffffffffu, slow);
-            uint32_t* qe = nullptr;
-            if (want) {
-                if (fq.nq + __popc(want) > kSegQ) drain_segs(fq, bins, lane);
-                qe = fq.Q + (fq.nq + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
-            }
-            uint32_t k16[4];
-            mask16(olo, ohi, k16);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uint32_t X[4];
-                tile_x(sa, sb, sc, c, lc, gf, X);
-                const uint2 mv = lds64(as + (uint32_t)c * TileAux<TmaMode::kFit>::kPlane);
-                if (take) {
-                    uint32_t xo[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) xo[k] = X[k] & k16[k];
-                    chan_accum(xo, mv.x & olo, mv.y & ohi, odd, c);
-                    chan_accum(X, mv.x, mv.y, all, c);
-                }
-                if (slow) {
-                    qe[2 + c] = mv.x;
-                    qe[5 + c] = mv.y;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) qe[8 + 4 * c + k] = X[k];
-                }
-            }
-            odd.n += po_n;
-            all.n += take ? 8u : 0u;
-            if (want) {
-                if (slow) {
-                    qe[0] = elo;
-                    qe[1] = ehi;
-                    qe[20] = 8u;
-                }
-                __syncwarp();
-                fq.nq += __popc(want);
-            }
-            tile_release(L.sempty((int)((si + j) % kTileS)), lane);
-            tile_release(L.aempty((int)((ai + j) % TileAux<TmaMode::kFit>::kSlots)), lane);
-            if ((j + 1) % kRunRows == 0 || j + 1 == T.rows) {
-                // bounded runs: flush both (the even run is all - odd)
-                RunAcc e = all;
-                run_minus(e, odd);
-                e.E = all.E;
-                warp_flush(e, bins, lane);
-                warp_flush(odd, bins, lane);
-                run_reset(all, -1);
-                run_reset(odd, -1);
-            }
-        }
-        if (!ok) break;
-        tile_release(L.sempty((int)((si + T.rows) % kTileS)), lane);
-        tile_release(L.sempty((int)((si + T.rows + 1) % kTileS)), lane);
-        si += T.rows + 2;
-        ai += T.rows;
-    }
-    if (ok) {
-        drain_runs(fq, bins, lane);
-        drain_segs(fq, bins, lane);
-    }
+    fit_consume<kGf>(L, A, bins, queue, warp, lane);
     consumers_sync();
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kTileWarps * 32) {
         const unsigned long long v = ((unsigned long long)bins.hi[i] << 12) + bins.lo[i];
@@ -1498,16 +1677,108 @@ constexpr size_t tile_rows_smem() {
     return 128 + TileSmem<MODE>::kHead + sizeof(float2) * 3 * kNbin +
            (MODE == TmaMode::kResidual ? sizeof(uint32_t) * 3 * kNres : 0);
 }
-static_assert(3 * (tile_rows_smem<TmaMode::kResidual>() + 1024) <= 228 * 1024, "three residual CTAs per SM");
-static_assert(2 * (tile_rows_smem<TmaMode::kDecode>() + 1024) <= 228 * 1024, "two decode CTAs per SM");
+static_assert(TileAux<TmaMode::kResidual>::kCtas * (tile_rows_smem<TmaMode::kResidual>() + 1024) <= 228 * 1024,
+              "residual CTAs per SM");
+static_assert(TileAux<TmaMode::kDecode>::kCtas * (tile_rows_smem<TmaMode::kDecode>() + 1024) <= 228 * 1024,
+              "decode CTAs per SM");
+
+// The residual / decoder consumer loop: per row and lane, the new S row moves
+// the filter window (as in the fit), then Eq. (8) per pixel and channel with
+// the region's (a, b) pair from shared memory; R = M - M* is stored (and
+// counted) or M = R + M* is packed with E into the RGBE words.
+template <TmaMode MODE, bool kGf>
+__device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const TileArgs& A, const float2* ab,
+                                             uint32_t* hist, int warp, int lane) {
+    TileConsumer<MODE> C{L, A.max_spins, {0u, 0u}, {0u, 0u}};
+    const int w = A.w;
+    const int64_t n = (int64_t)A.h * w;
+    TileRange T = tile_range(A.total_rows, A.h);
+    bool ok = true;
+    while (ok && T.next()) {
+        const LaneCols lc(T.xs, w, warp, lane);
+        uint32_t Hm[3][4], H0[3][4];
+        ok = C.wait_s();
+        if (!ok) break;
+        if constexpr (kGf) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_row_pairs<kGf>(C.s_addr(), c, lc, Hm[c]);
+        }
+        C.release_s(lane);
+        ok = C.wait_s();
+        if (!ok) break;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_row_pairs<kGf>(C.s_addr(), c, lc, H0[c]);
+        C.release_s(lane);
+        for (int j = 0; j < T.rows; ++j) {
+            ok = C.wait_s() && C.wait_a();
+            if (!ok) break;
+            const uint32_t sn = C.s_addr();
+            const uint32_t as = C.a_addr() + kStripCols * warp + 8 * lane;
+            const int64_t pix = (int64_t)(T.y0 + j) * w + lc.x0;
+            const uint2 ev = lds64(as + TileAux<MODE>::kE);
+            if constexpr (MODE == TmaMode::kResidual) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
+                    const uint2 mv = lds64(as + (uint32_t)c * TileAux<MODE>::kPlane);
+                    int rr[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
+                        const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
+                        const float2 p = ab[c * kNbin + E];
+                        rr[i] = M - predict_biased(p.x, p.y, x_biased(X, i));
+                    }
+                    if (lc.inside) {
+                        uint4 v;
+                        v.x = __byte_perm((uint32_t)rr[0], (uint32_t)rr[1], 0x5410);
+                        v.y = __byte_perm((uint32_t)rr[2], (uint32_t)rr[3], 0x5410);
+                        v.z = __byte_perm((uint32_t)rr[4], (uint32_t)rr[5], 0x5410);
+                        v.w = __byte_perm((uint32_t)rr[6], (uint32_t)rr[7], 0x5410);
+                        *reinterpret_cast<uint4*>(A.r3_out + c * n + pix) = v;
+                        if (hist) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
+                        }
+                    }
+                }
+            } else {
+                uint32_t word[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) word[i] = __byte_perm(i < 4 ? ev.x : ev.y, 0u, 0x0444 | ((i & 3) << 12));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
+                    // R is 2 bytes per pixel: the lane's offset twice
+                    const uint4 v = lds128(as + (uint32_t)c * TileAux<MODE>::kPlane + (kStripCols * warp + 8 * lane));
+                    const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                        const int E = (int)(word[i] >> 24);
+                        const float2 p = ab[c * kNbin + E];
+                        const int M = rv + predict_biased(p.x, p.y, x_biased(X, i));
+                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
+                    }
+                }
+                if (lc.inside) {
+                    uint4* o4 = reinterpret_cast<uint4*>(A.out + pix);
+                    o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
+                    o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                }
+            }
+            C.release_s(lane);
+            C.release_a(lane);
+        }
+    }
+}
 
 // k_rows_tile<kResidual>: R = M - M* and histograms; k_rows_tile<kDecode>:
 // M = R + M*, repacked with E.
-template <TmaMode MODE>
-__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile(const __grid_constant__ CUtensorMap tm_s,
-                                                                const __grid_constant__ CUtensorMap tm_a,
-                                                                const __grid_constant__ CUtensorMap tm_e,
-                                                                const TileArgs A) {
+template <TmaMode MODE, bool kGf>
+__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile(const TileArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TileSmem<MODE> L = tile_smem<MODE>(dyn);
@@ -1518,7 +1789,7 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_til
     __syncthreads();
 
     if (warp == kTileWarps) {
-        if (lane == 0) tile_produce(L, &tm_s, &tm_a, &tm_e, A);
+        if (lane == 0) tile_produce(L, A);
         return;
     }
     // the consumers fetch the parameters while the first copies are in flight
@@ -1526,83 +1797,7 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_til
     if (MODE == TmaMode::kResidual && A.hist)
         for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32) hist[i] = 0u;
     consumers_sync();
-    const TileConsumer<MODE> C{L, A.max_spins};
-    const int w = A.w;
-    const int64_t n = (int64_t)A.h * w;
-    const bool gf = A.gf != 0;
-    TileRange T = tile_range(A.total_rows, A.h);
-    uint32_t si = 0, ai = 0;
-    bool ok = true;
-    while (ok && T.next()) {
-        const LaneCols lc(T.xs, w, warp, lane);
-        ok = C.wait_s(si) && C.wait_s(si + 1);
-        for (int j = 0; j < T.rows && ok; ++j) {
-            ok = C.wait_s(si + j + 2) && C.wait_a(ai + j);
-            if (!ok) break;
-            const uint32_t sa = L.sslot(si + j), sb = L.sslot(si + j + 1), sc = L.sslot(si + j + 2);
-            const uint32_t as = L.aslot(ai + j);
-            const int y = T.y0 + j;
-            if (lc.inside) {
-                const uint2 ev = lds64(as + TileAux<MODE>::kE + kStripCols * warp + 8 * lane);
-                if constexpr (MODE == TmaMode::kResidual) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        uint32_t X[4];
-                        tile_x(sa, sb, sc, c, lc, gf, X);
-                        const uint2 mv = lds64(as + (uint32_t)c * TileAux<MODE>::kPlane + kStripCols * warp + 8 * lane);
-                        int rr[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
-                            const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
-                            const float2 p = ab[c * kNbin + E];
-                            rr[i] = M - predict(p.x, p.y, half_of(X, i));
-                        }
-                        uint4 v;
-                        v.x = (uint32_t)(rr[0] & 0xFFFF) | ((uint32_t)rr[1] << 16);
-                        v.y = (uint32_t)(rr[2] & 0xFFFF) | ((uint32_t)rr[3] << 16);
-                        v.z = (uint32_t)(rr[4] & 0xFFFF) | ((uint32_t)rr[5] << 16);
-                        v.w = (uint32_t)(rr[6] & 0xFFFF) | ((uint32_t)rr[7] << 16);
-                        *reinterpret_cast<uint4*>(A.r3_out + c * n + (int64_t)y * w + lc.x0) = v;
-                        if (A.hist) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
-                        }
-                    }
-                } else {
-                    uint32_t word[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) word[i] = byte_of(i < 4 ? ev.x : ev.y, i & 3) << 24;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        uint32_t X[4];
-                        tile_x(sa, sb, sc, c, lc, gf, X);
-                        const uint4 v =
-                            lds128(as + (uint32_t)c * TileAux<MODE>::kPlane + 2u * (kStripCols * warp + 8 * lane));
-                        const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
-                            const int E = (int)(word[i] >> 24);
-                            const float2 p = ab[c * kNbin + E];
-                            const int M = rv + predict(p.x, p.y, half_of(X, i));
-                            word[i] |= ((uint32_t)M & 255u) << (8 * c);
-                        }
-                    }
-                    uint4* o4 = reinterpret_cast<uint4*>(A.out + (int64_t)y * w + lc.x0);
-                    o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
-                    o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
-                }
-            }
-            C.release_s(si + j, lane);
-            C.release_a(ai + j, lane);
-        }
-        if (!ok) break;
-        C.release_s(si + T.rows, lane);
-        C.release_s(si + T.rows + 1, lane);
-        si += T.rows + 2;
-        ai += T.rows;
-    }
+    rows_consume<MODE, kGf>(L, A, ab, MODE == TmaMode::kResidual && A.hist ? hist : nullptr, warp, lane);
     if (MODE == TmaMode::kResidual && A.hist) {
         consumers_sync();
         for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32)
@@ -1615,58 +1810,6 @@ bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
     for (const void* p : ptrs)
         if ((uintptr_t)p % 16 != 0) return false;
     return true;
-}
-
-// ---------------------------------------------------------------- tensor maps (host)
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn tensor_map_encoder() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    });
-    return fn;
-}
-
-// Tensor map of `planes` planes of h x w pixels of `esize` bytes, viewed as
-// (16-byte chunk, chunk, row, plane); a box is one row of `box_chunks` chunks
-// of every plane.
-bool plane_map(CUtensorMap* tm, const void* base, int esize, int h, int w, int planes, int box_chunks) {
-    EncodeTiledFn enc = tensor_map_encoder();
-    if (!enc) {
-        set_error("cuTensorMapEncodeTiled is not available from the driver");
-        return false;
-    }
-    const cuuint64_t row = (cuuint64_t)w * esize;
-    const cuuint64_t dims[4] = {(cuuint64_t)(16 / esize), row / 16, (cuuint64_t)h, (cuuint64_t)planes};
-    const cuuint64_t strides[3] = {16, row, row * (cuuint64_t)h};
-    const cuuint32_t box[4] = {(cuuint32_t)(16 / esize), (cuuint32_t)box_chunks, 1, (cuuint32_t)planes};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = enc(tm, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 4,
-                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d plane map", (int)r, h, w);
-        return false;
-    }
-    return true;
-}
-
-template <TmaMode MODE>
-bool tile_maps(TileMaps& M, const uint8_t* s3, const void* aux, const uint8_t* e, int h, int w) {
-    return plane_map(&M.s, s3, 1, h, w, 3, kTileSW / 16) &&
-           plane_map(&M.a, aux, (int)TileAux<MODE>::kElem, h, w, 3, (int)(TileAux<MODE>::kElem * kTileCols / 16)) &&
-           plane_map(&M.e, e, 1, h, w, 1, kTileCols / 16);
 }
 
 // Grid of a tile kernel: at least four rows per CTA; at most two CTAs per SM,
@@ -1697,32 +1840,29 @@ int tile_smem_attr(K kernel, size_t bytes, bool* set) {
 template <TmaMode MODE>
 int launch_rows_tile(const uint8_t* s3, const void* aux, const uint8_t* e, int h, int w, int gf_on,
                      const slrme_params* P, int16_t* r3_out, uint32_t* hist, uint32_t* out, cudaStream_t s) {
-    static bool attr_set[64];
+    static bool attr_gf[64], attr_plain[64];
     constexpr size_t smem = tile_rows_smem<MODE>();
-    int st = tile_smem_attr(k_rows_tile<MODE>, smem, attr_set);
+    auto kernel = gf_on ? k_rows_tile<MODE, true> : k_rows_tile<MODE, false>;
+    int st = tile_smem_attr(kernel, smem, gf_on ? attr_gf : attr_plain);
     if (st != SLRME_OK) return st;
-    TileMaps M;
-    if (!tile_maps<MODE>(M, s3, aux, e, h, w)) return SLRME_ECUDA;
     const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
-    TileArgs A{h, w, gf_on, total_rows, kMaxSpins, P, r3_out, hist, out, nullptr};
-    k_rows_tile<MODE><<<(unsigned)tile_grid(total_rows, 0, TileAux<MODE>::kCtas), kTileThreads, smem, s>>>(M.s, M.a,
-                                                                                                    M.e, A);
+    TileArgs A{s3, aux, e, h, w, gf_on, total_rows, kMaxSpins, P, r3_out, hist, out, nullptr};
+    kernel<<<(unsigned)tile_grid(total_rows, 0, TileAux<MODE>::kCtas), kTileThreads, smem, s>>>(A);
     return cuda_status(MODE == TmaMode::kResidual ? "residual_encode launch" : "residual_decode launch");
 }
 
 int launch_fit_tile(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
                     unsigned long long* bins, cudaStream_t s) {
-    static bool attr_set[64];
-    int st = tile_smem_attr(k_fit_tile, kTileFitSmem, attr_set);
+    static bool attr_gf[64], attr_plain[64];
+    auto kernel = gf_on ? k_fit_tile<true> : k_fit_tile<false>;
+    int st = tile_smem_attr(kernel, kTileFitSmem, gf_on ? attr_gf : attr_plain);
     if (st != SLRME_OK) return st;
-    TileMaps M;
-    if (!tile_maps<TmaMode::kFit>(M, s3, m3, e, h, w)) return SLRME_ECUDA;
     const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
-    // a CTA adds at most kMaxBlockPixels pixels to its bins
-    const int64_t rows_max = kMaxBlockPixels / kTileCols;
-    TileArgs A{h, w, gf_on, total_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr, bins};
-    k_fit_tile<<<(unsigned)tile_grid(total_rows, rows_max, TileAux<TmaMode::kFit>::kCtas), kTileThreads, kTileFitSmem,
-                 s>>>(M.s, M.a, M.e, A);
+    // a CTA adds at most kTileFitMaxPixels pixels to its bins
+    const int64_t rows_max = kTileFitMaxPixels / kTileCols;
+    TileArgs A{s3, m3, e, h, w, gf_on, total_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr, bins};
+    kernel<<<(unsigned)tile_grid(total_rows, rows_max, TileAux<TmaMode::kFit>::kCtas), kTileThreads, kTileFitSmem,
+             s>>>(A);
     return cuda_status("slr_fit launch");
 }
 
