@@ -76,14 +76,15 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8], int r) {
 
 // 8-bit display value: #{k in 1..255 : v >= gamma[k]} for the increasing
 // threshold table (v >= 0).  The float bits of v pick a bucket (exponent and
-// top 7 mantissa bits over [2^-20, 1), plus one bucket below and one above);
-// a bucket holds at most one threshold, and its word is the count below the
-// bucket plus, from bit 8, the low 16 bits of that threshold (0x10000 when
-// there is none), so the count is one lookup and one integer comparison
-// (positive floats order like their bits).  No branch.
+// top 7 mantissa bits over [2^-20, 1), plus one bucket below and one above;
+// the clamp to those is one min-then-max-with-zero instruction); a bucket
+// holds at most one threshold, and its word is the count below the bucket
+// plus, from bit 8, the low 16 bits of that threshold (0x10000 when there is
+// none), so the count is one lookup and one integer comparison (positive
+// floats order like their bits).  No branch.
 __device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {   // code = table + 1
     const int bits = __float_as_int(v);
-    const uint32_t e = code[min(max((bits - 0x35800000) >> 16, -1), 2560)];   // `code` points at bucket 0
+    const uint32_t e = code[__vimin_s32_relu(((bits - 0x35800000) >> 16) + 1, 2561) - 1];   // `code` points at bucket 0
     return (int)(e & 255u) + ((uint32_t)(bits & 0xFFFF) >= (e >> 8) ? 1 : 0);
 }
 
@@ -158,7 +159,9 @@ __device__ __forceinline__ float tmo_L(int mr, int mg, int mb, int E, int J, flo
 
 // The tone-mapping operator of one pixel (Sec. II-B with Sec. IV's
 // Reinhard operator): the three display codes of mantissas (mr, mg, mb) and
-// exponent E, computed for every pixel and zeroed where E = 0 (no branch).
+// exponent E, computed for every pixel without a branch.  Where E = 0 the
+// numerator is 0, so H = 0 / (1 + L) = 0 (1 + L is finite and at least 1),
+// every v is 0 and every code 0.
 // kWhite: the operator with a white point (Reinhard's Eq. 4), lw2 = L_white^2:
 // the numerator is multiplied by 1 + L / lw2 before the division.
 template <bool kWhite = false>
@@ -167,13 +170,12 @@ __device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, 
     float p2d;
     const float L = tmo_L(mr, mg, mb, E, J, kr, &p2d);
     const float den = __fadd_rn(1.0f, L);
-    float num = __fmul_rn(wr, p2d);
+    float num = E == 0 ? 0.0f : __fmul_rn(wr, p2d);
     if (kWhite) num = __fmul_rn(num, __fadd_rn(1.0f, __fdiv_rn(L, lw2)));
     const float H = __fdiv_rn(num, den);
-    const int keep = E == 0 ? 0 : -1;
-    r = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr + 1)), gcode + 1) & keep;
-    g = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg + 1)), gcode + 1) & keep;
-    b = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb + 1)), gcode + 1) & keep;
+    r = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr + 1)), gcode + 1);
+    g = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg + 1)), gcode + 1);
+    b = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb + 1)), gcode + 1);
 }
 
 // Key and quantiser state of one image, as a lane needs it.

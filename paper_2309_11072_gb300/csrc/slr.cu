@@ -1479,6 +1479,7 @@ __device__ __forceinline__ void runs_rekey(FitQueues& fq, Run2& all, Run2& odd, 
                                            int Eo, SmemBins& bins, int lane) {
     const bool chg_e = has_e && Ee != all.E;
     const bool chg_o = has_o && Eo != odd.E;
+    if (!__any_sync(0xffffffffu, chg_e || chg_o)) return;
     push_run<true>(fq, chg_e && all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
     push_run<false>(fq, chg_o && odd.E >= 0 && odd.n != 0u, all, odd, bins, lane);
     if (chg_e) {   // the even part left: all = odd
