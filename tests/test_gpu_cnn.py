@@ -24,13 +24,19 @@ def _host(t, dt):
 
 
 def _mild_net(seed):
+    """A network whose requantisation stays mostly unsaturated: small weights,
+    hidden multipliers 2^12..2^14 at shift 20 (about half of every hidden
+    layer's activations strictly between the ReLU's 0 and 127), and an output
+    layer biased and scaled to spread its values over the byte range."""
     rng = np.random.default_rng(seed)
     net = C.random_net(seed, w_range=24)
     for l in range(4):
         co = net["m"][l].shape[0]
         net["b"][l] = rng.integers(-3000, 3000, size=co).astype(np.int32)
-        net["m"][l] = rng.integers(1 << 10, 1 << 13, size=co).astype(np.int32)
+        net["m"][l] = rng.integers(1 << 12, 1 << 14, size=co).astype(np.int32)
         net["sh"][l] = 20
+    net["b"][3] = rng.integers(4000, 9000, size=3).astype(np.int32)
+    net["m"][3] = rng.integers(1 << 14, 1 << 15, size=3).astype(np.int32)
     return net
 
 
@@ -58,7 +64,9 @@ def test_cnn_infer_matches_integer_oracle(h, w, kind):
     got = _host(mh, np.uint8).reshape(3, h, w)
     assert np.array_equal(got, ref)
     if kind == "mild" and h * w > 100:
-        assert len(np.unique(ref)) > 8           # the test exercises unsaturated values
+        # the test exercises unsaturated values: many distinct outputs, most inside (0, 255)
+        assert len(np.unique(ref)) > 20
+        assert np.mean((ref > 0) & (ref < 255)) > 0.3
 
 
 @pytest.mark.parametrize("h,w", [(9, 17), (48, 80), (130, 70)])
@@ -194,3 +202,47 @@ def test_learned_estimator_pick_is_lossless_and_never_worse():
         pk = Lr.pick_image(_host(L["hist"], np.uint32).reshape(3, 511), test_bc.image_params(i)["n_used"],
                            _host(hist, np.uint32).reshape(3, 511), h * w)
         assert pk.bits <= pk.bits_slr
+
+
+def _shipped_gain(imgs, quality=90):
+    """Per image (bits with the regression, bits with the shipped network),
+    each decode checked lossless."""
+    net = Lr.upload_net(Lr.load_net(Lr.default_weights()))
+    bc = Bm.BatchCodec([im.shape for im in imgs], [quality] * len(imgs))
+    bc.load(imgs)
+    bc.encode()
+    bc.decode()
+    keys = bc.keys()
+    out_rates = []
+    for i, img in enumerate(imgs):
+        L = bc.image_layers(i)
+        h, w = img.shape
+        r3 = torch.empty(3 * h * w, dtype=torch.int16, device=DEV)
+        hist = torch.empty(3 * 511, dtype=torch.int32, device=DEV)
+        Lr.cnn_residual_encode(L["s3"], L["m3"], L["e"], h, w, keys[i], net, L["params"], 1, r3, hist)
+        out = torch.empty(h * w, dtype=torch.int32, device=DEV)
+        Lr.cnn_residual_decode(L["s3"], L["e"], r3, h, w, keys[i], net, L["params"], 1, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(_host(out, np.uint32).reshape(h, w), img)
+        assert np.array_equal(_host(L["out"], np.uint32).reshape(h, w), img)
+        pk = Lr.pick_image(_host(L["hist"], np.uint32).reshape(3, 511), bc.image_params(i)["n_used"],
+                           _host(hist, np.uint32).reshape(3, 511), h * w)
+        out_rates.append((pk.bits_slr, pk.bits_cnn))
+    bc.close()
+    return out_rates
+
+
+@pytest.mark.slow
+def test_shipped_network_beats_the_regression_on_held_out_images():
+    """What the trained network gains: the shipped integer network (trained by
+    learned_eval on 512x512 and 1024x1024 images seeded 10000 and up) against
+    the regression alone on held-out 2048x1536 images of the benchmark's
+    2048x1536 generator (fBm over 8 decades, 40 rectangles, 200 highlights;
+    seeds 20000 and up, never trained on).  Its residuals cost fewer bits on
+    every image, by more than half a bit per pixel on average, and every image
+    decodes losslessly both ways."""
+    imgs = [synth.make_rgbe(1536, 2048, seed=20000 + i, lo=-3.0, hi=5.0, rects=40, highlights=200)
+            for i in range(4)]
+    rates = _shipped_gain(imgs)
+    assert all(cnn < slr for slr, cnn in rates), rates
+    assert np.mean([slr - cnn for slr, cnn in rates]) > 0.5, rates

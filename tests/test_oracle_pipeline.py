@@ -67,3 +67,30 @@ def test_oracle_matches_committed_golden():
     assert enc["a"][:, used].view(np.uint32).reshape(-1).tolist() == g["a_bits"]
     assert enc["b"][:, used].view(np.uint32).reshape(-1).tolist() == g["b_bits"]
     assert enc["r3"].reshape(-1).tolist() == g["r3"]
+
+
+def test_chunked_oracle_equals_the_whole_image_oracle():
+    """The chunk-by-chunk run of the oracle (used at 800 M pixels on the GPU)
+    gives the whole-image oracle's parameters, histograms, S, x = 16 S* and
+    residuals, on 8- and 16-row images with a ragged right edge."""
+    import chunked_oracle as K
+    from paper_2309_11072_gb300 import synth
+    old = K.CHUNK
+    K.CHUNK = 64
+    try:
+        for h, w in [(16, 300), (8, 412), (8, 64)]:
+            img = synth.make_rgbe(h, w, seed=9, lo=-3.0, hi=5.0, rects=2, highlights=5)
+            J, r = O.key(O.lum_stats(img))
+            a, b, cnt, nu = O.solve(K.oracle_sums(img, J, r))
+            o = O.encode(img, K.Q)
+            assert np.array_equal(a.view(np.uint32), o["a"].view(np.uint32))
+            assert np.array_equal(b.view(np.uint32), o["b"].view(np.uint32))
+            assert np.array_equal(cnt, o["n"]) and nu == o["n_used"]
+            assert np.array_equal(K.oracle_hist(img, J, r, a, b), o["hist"].astype(np.int64))
+            for x0, x1 in ((0, 64), (64, 128), ((w - 40) // 8 * 8, w)):
+                so, xo, mo, eo = K.oracle_chunk(img, x0, x1, J, r)
+                assert np.array_equal(so, o["s3"][:, :, x0:x1]) and np.array_equal(xo, o["x3"][:, :, x0:x1])
+                ro, _ = O.residual(mo, O.predict(xo, eo, a, b))
+                assert np.array_equal(ro, o["r3"][:, :, x0:x1])
+    finally:
+        K.CHUNK = old
