@@ -984,12 +984,12 @@ struct TileAux {
 // current use (item i is slot i % K, use i / K).
 template <int K>
 struct RingPos {
-    uint32_t slot, phase;
+    uint32_t v;   // slot * 2 + phase
+    __device__ __forceinline__ uint32_t slot() const { return v >> 1; }
+    __device__ __forceinline__ uint32_t phase() const { return v & 1u; }
     __device__ __forceinline__ void advance() {
-        if (++slot == (uint32_t)K) {
-            slot = 0;
-            phase ^= 1u;
-        }
+        v += 2u;
+        if (v >= 2u * K) v = (v & 1u) ^ 1u;
     }
 };
 
@@ -1098,8 +1098,8 @@ __device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const TileArg
     const uint8_t* aux = static_cast<const uint8_t*>(A.aux);
     TileRange P = tile_range(A.total_rows, A.h);
     uint32_t si = 0, ai = 0;   // items issued
-    RingPos<KS> sp{0u, 0u};
-    RingPos<KA> ap{0u, 0u};
+    RingPos<KS> sp{0u};
+    RingPos<KA> ap{0u};
     bool ok = true;
     while (ok && P.next()) {
         const int xa = max(P.xs - 16, 0), xb = min(P.xs + kTileCols + 16, A.w);
@@ -1108,10 +1108,10 @@ __device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const TileArg
         for (int k = 0; k < P.rows + 2 && ok; ++k) {
             // S item k: row y0 - 1 + k, clamped (edge rows replicate)
             {
-                if (si >= (uint32_t)KS) ok = mbar_wait(L.sempty(sp.slot), sp.phase ^ 1u, &g_slrme_status, A.max_spins);
+                if (si >= (uint32_t)KS) ok = mbar_wait(L.sempty(sp.slot()), sp.phase() ^ 1u, &g_slrme_status, A.max_spins);
                 if (!ok) break;
                 const int ys = min(max(P.y0 - 1 + k, 0), A.h - 1);
-                const uint32_t dst = L.sslot_at(sp.slot) + s_off, bar = L.sfull(sp.slot);
+                const uint32_t dst = L.sslot_at(sp.slot()) + s_off, bar = L.sfull(sp.slot());
                 const uint8_t* src = A.s3 + (int64_t)ys * A.w + xa;
                 fence_async_shared();
                 mbar_arrive_expect_tx(bar, 3u * s_bytes);
@@ -1121,10 +1121,10 @@ __device__ __noinline__ void tile_produce(const TileSmem<MODE>& L, const TileArg
                 sp.advance();
             }
             if (k >= 2) {   // the other planes of row y0 + k - 2
-                if (ai >= (uint32_t)KA) ok = mbar_wait(L.aempty(ap.slot), ap.phase ^ 1u, &g_slrme_status, A.max_spins);
+                if (ai >= (uint32_t)KA) ok = mbar_wait(L.aempty(ap.slot()), ap.phase() ^ 1u, &g_slrme_status, A.max_spins);
                 if (!ok) break;
                 const int64_t row = (int64_t)(P.y0 + k - 2) * A.w + P.xs;
-                const uint32_t dst = L.aslot_at(ap.slot), bar = L.afull(ap.slot);
+                const uint32_t dst = L.aslot_at(ap.slot()), bar = L.afull(ap.slot());
                 fence_async_shared();
                 mbar_arrive_expect_tx(bar, (3u * kEl + 1u) * cols);
 #pragma unroll
@@ -1153,23 +1153,25 @@ struct TileConsumer {
     int max_spins;
     RingPos<TileSmem<MODE>::KS> s;
     RingPos<TileSmem<MODE>::KA> a;
+    // the whole warp waits together (mbar_wait_warp), so every lane sees the
+    // same outcome before the warp-wide steps that follow
     __device__ __forceinline__ bool wait_s() const {
-        return mbar_wait(L.sfull(s.slot), s.phase, &g_slrme_status, max_spins);
+        return mbar_wait_warp(L.sfull(s.slot()), s.phase(), &g_slrme_status, max_spins);
     }
     __device__ __forceinline__ bool wait_a() const {
-        return mbar_wait(L.afull(a.slot), a.phase, &g_slrme_status, max_spins);
+        return mbar_wait_warp(L.afull(a.slot()), a.phase(), &g_slrme_status, max_spins);
     }
-    __device__ __forceinline__ uint32_t s_addr() const { return L.sslot_at(s.slot); }
-    __device__ __forceinline__ uint32_t a_addr() const { return L.aslot_at(a.slot); }
+    __device__ __forceinline__ uint32_t s_addr() const { return L.sslot_at(s.slot()); }
+    __device__ __forceinline__ uint32_t a_addr() const { return L.aslot_at(a.slot()); }
     // all lanes call after their last read of the current item
     __device__ __forceinline__ void release_s(int lane) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(L.sempty(s.slot));
+        if (lane == 0) mbar_arrive(L.sempty(s.slot()));
         s.advance();
     }
     __device__ __forceinline__ void release_a(int lane) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(L.aempty(a.slot));
+        if (lane == 0) mbar_arrive(L.aempty(a.slot()));
         a.advance();
     }
 };
@@ -1504,9 +1506,9 @@ __device__ __forceinline__ void runs_rekey(FitQueues& fq, Run2& all, Run2& odd, 
 // queued for per-pixel work); then, channel by channel, the new S row moves
 // the filter window and x = 16 S* is added.
 template <bool kGf>
-__device__ __forceinline__ void fit_consume(const TileSmem<TmaMode::kFit>& L, const TileArgs& A, SmemBins& bins,
+__device__ __forceinline__ bool fit_consume(const TileSmem<TmaMode::kFit>& L, const TileArgs& A, SmemBins& bins,
                                             uint32_t* queue, int warp, int lane) {
-    TileConsumer<TmaMode::kFit> C{L, A.max_spins, {0u, 0u}, {0u, 0u}};
+    TileConsumer<TmaMode::kFit> C{L, A.max_spins, {0u}, {0u}};
     const int w = A.w;
     FitQueues fq;
     fq.R = queue + warp * (kRunQ * kRunStride + kSegQ * kQueueStride);
@@ -1641,17 +1643,20 @@ __device__ __forceinline__ void fit_consume(const TileSmem<TmaMode::kFit>& L, co
         drain_runs(fq, bins, lane);
         drain_segs(fq, bins, lane);
     }
+    return ok;
 }
 
 template <bool kGf>
 __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile(const TileArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int gave_up;   // a consumer's wait gave up: the CTA's bins are incomplete
     const TileSmem<TmaMode::kFit> L = tile_smem<TmaMode::kFit>(dyn);
     char* extra = dyn + (L.extra - smem_addr(dyn));
     SmemBins& bins = *reinterpret_cast<SmemBins*>(extra);
     uint32_t* queue = reinterpret_cast<uint32_t*>(extra + sizeof(SmemBins));
     tile_init_barriers(L);
+    if (threadIdx.x == 0) gave_up = 0;
     __syncthreads();
 
     if (warp == kTileWarps) {
@@ -1663,8 +1668,11 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k
     for (int i = threadIdx.x; i < (int)(sizeof(SmemBins) / 16); i += kTileWarps * 32)
         reinterpret_cast<uint4*>(extra)[i] = make_uint4(0u, 0u, 0u, 0u);
     consumers_sync();
-    fit_consume<kGf>(L, A, bins, queue, warp, lane);
+    if (!fit_consume<kGf>(L, A, bins, queue, warp, lane) && lane == 0) atomicOr(&gave_up, 1);
     consumers_sync();
+    // after a timeout (reported in the status word) the partial bins are not
+    // added, so the sums hold only whole CTAs' pixels
+    if (gave_up) return;
     for (int i = threadIdx.x; i < kNbin * kNsum; i += kTileWarps * 32) {
         const unsigned long long v = ((unsigned long long)bins.hi[i] << 12) + bins.lo[i];
         if (v) atomicAdd(A.gbins + i, v);
@@ -1690,7 +1698,7 @@ static_assert(TileAux<TmaMode::kDecode>::kCtas * (tile_rows_smem<TmaMode::kDecod
 template <TmaMode MODE, bool kGf>
 __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const TileArgs& A, const float2* ab,
                                              uint32_t* hist, int warp, int lane) {
-    TileConsumer<MODE> C{L, A.max_spins, {0u, 0u}, {0u, 0u}};
+    TileConsumer<MODE> C{L, A.max_spins, {0u}, {0u}};
     const int w = A.w;
     const int64_t n = (int64_t)A.h * w;
     TileRange T = tile_range(A.total_rows, A.h);

@@ -59,4 +59,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* st
     return false;
 }
 
+// The same wait for all 32 lanes of a warp together: the warp polls until
+// every lane sees the phase complete, so the lanes return the same outcome.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* status,
+                                               int max_spins = kMaxSpins) {
+    for (int i = 0; i < max_spins; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (__all_sync(0xffffffffu, done != 0u)) return true;
+    }
+    if ((threadIdx.x & 31) == 0) atomicOr(status, kStatusWaitTimeout);
+    return false;
+}
+
 }  // namespace slrme
