@@ -128,7 +128,10 @@ size_t slr_fit_workspace_bytes(void);
  * - Sizes: the same as slr_fit (h, w >= 0, h*w < 2^31, the range in which the
  *   int64 sums are exact); anything else is rejected with SLRME_EINVAL.
  * - The first call on a device looks up the array's device address (with that
- *   device current); make that first call before any stream capture.
+ *   device current); make that first call before any stream capture.  The
+ *   address is kept with the context it belongs to and looked up again when
+ *   the device's current context changes (after a device reset, say): the
+ *   first call after such a change is again a first call.
  * - All calls share the one array: each call clears it on `stream` before
  *   use, and calls whose GPU work overlaps (other streams, other threads)
  *   race on it and give wrong parameters.  Serialise them. */

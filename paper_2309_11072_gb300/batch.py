@@ -141,6 +141,7 @@ class BatchCodec:
                     hist=self.hist[i * 3 * native.SLRME_NRES:(i + 1) * 3 * native.SLRME_NRES].view(3, -1))
 
     def image_params(self, i: int) -> dict:
+        native.check_device_status("BatchCodec")
         return params_to_numpy(self.image_layers(i)["params"])
 
     # ------------------------------------------------------------ calls
@@ -170,6 +171,7 @@ class BatchCodec:
 
     def lum_stats(self) -> np.ndarray:
         """Per-image log-average statistics of the last encode (int64 [n, 2])."""
+        native.check_device_status("BatchCodec")
         out = np.zeros((self.n, 2), np.int64)
         _call("slrme_batch_lum_stats", ctypes.addressof(self.plan), out.ctypes.data, self._stream())
         return out

@@ -103,9 +103,17 @@ class Codec:
         native.residual_decode(s3, e, r3, self.h, self.w, self.gf_on, params, out, stream)
         return out
 
+    # ------------------------------------------------------------ checks
+    def check(self) -> None:
+        """Waits for the device and raises if a kernel's bounded wait gave up
+        since the last check (the library's status word); encode and decode
+        are asynchronous, so their outputs are trustworthy after this."""
+        native.check_device_status("Codec")
+
     # ------------------------------------------------------------ rate
     def bits_per_pixel(self) -> float:
         """Enhancement-layer rate: H0 of the residual planes + side information."""
+        self.check()
         hist = self.hist.view(3, native.SLRME_NRES).cpu().numpy().view(np.uint32)
         n_used = params_to_numpy(self.params)["n_used"]
         return enhancement_bits_per_pixel(hist, n_used, self.h * self.w)
@@ -183,3 +191,10 @@ class HostCodec:
 
     def streams(self):
         return [st for sl in self.slots for st in (sl["stream"], sl["out_stream"])]
+
+    def wait(self) -> None:
+        """Waits for every call enqueued so far (its host buffers are then
+        filled) and raises if a kernel's bounded wait gave up."""
+        for st in self.streams():
+            st.synchronize()
+        native.check_device_status("HostCodec")

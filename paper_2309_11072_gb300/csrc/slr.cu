@@ -10,6 +10,8 @@
 // of its 8 pixels come from the adjacent lanes by shuffle (strip edges load
 // them).  The 3x3 binomial filter runs on 16-bit pairs: two pixels per
 // 32-bit add (values stay <= 4080).
+#include <cuda.h>
+
 #include <initializer_list>
 #include <mutex>
 
@@ -2012,64 +2014,77 @@ namespace {
 constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned long long g_fit_scratch[kNbin * kNsum];
 static std::mutex g_scratch_mu;
-static void* g_scratch_addr[kMaxDevices];
-static void* g_status_addr[kMaxDevices];
 
-// Device address of g_fit_scratch on the current device, looked up once per
-// device (with that device current).  In host code the array's name is only a
-// host-side stand-in, so kernels must be given this address, never the name.
-int scratch_address(void** out) {
+// A device symbol's address, cached per device ordinal together with the
+// context it was looked up in: if the current context differs (the device's
+// primary context was reset and created again), the address is looked up
+// again, so a cached address never outlives its context.
+struct SymbolCache {
+    void* ctx[kMaxDevices];
+    void* addr[kMaxDevices];
+};
+static SymbolCache g_scratch_cache, g_status_cache;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
+
+// Device address of `symbol` on the current device, looked up with that
+// device current (in host code a __device__ variable's name is only a
+// host-side stand-in, so kernels must be given this address, never the name).
+int symbol_address(const void* symbol, SymbolCache& cache, const char* what, void** out) {
     int dev = -1;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) {
-        set_error("slr_fit_noalloc: cudaGetDevice: %s", cudaGetErrorString(err));
+        set_error("%s: cudaGetDevice: %s", what, cudaGetErrorString(err));
         return SLRME_ECUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) {
-        set_error("slr_fit_noalloc: device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
+        set_error("%s: device ordinal %d outside 0..%d", what, dev, kMaxDevices - 1);
         return SLRME_EINVAL;
     }
+    CtxGetCurrentFn get = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!cache.addr[dev] || !ctx || cache.ctx[dev] != (void*)ctx) {
+        // the lookup makes the device's primary context current if it is not yet
         void* p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_fit_scratch);
+        err = cudaGetSymbolAddress(&p, symbol);
         if (err != cudaSuccess || !p) {
-            set_error("slr_fit_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(err));
+            set_error("%s: cudaGetSymbolAddress: %s", what, cudaGetErrorString(err));
             return SLRME_ECUDA;
         }
-        g_scratch_addr[dev] = p;
+        if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+        cache.addr[dev] = p;
+        cache.ctx[dev] = (void*)ctx;
     }
-    *out = g_scratch_addr[dev];
+    *out = cache.addr[dev];
     return SLRME_OK;
 }
+
+int scratch_address(void** out) { return symbol_address(g_fit_scratch, g_scratch_cache, "slr_fit_noalloc", out); }
 
 }  // namespace
 
 // Device address of the status word g_slrme_status on the current device,
-// looked up once per device, for kernels of other translation units.
+// for kernels of other translation units.
 int status_word_address(int** out) {
-    int dev = -1;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) {
-        set_error("status word: cudaGetDevice: %s", cudaGetErrorString(err));
-        return SLRME_ECUDA;
-    }
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("status word: device ordinal %d outside 0..%d", dev, kMaxDevices - 1);
-        return SLRME_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_status_addr[dev]) {
-        void* p = nullptr;
-        err = cudaGetSymbolAddress(&p, g_slrme_status);
-        if (err != cudaSuccess || !p) {
-            set_error("status word: cudaGetSymbolAddress: %s", cudaGetErrorString(err));
-            return SLRME_ECUDA;
-        }
-        g_status_addr[dev] = p;
-    }
-    *out = (int*)g_status_addr[dev];
-    return SLRME_OK;
+    void* p = nullptr;
+    const int st = symbol_address(&g_slrme_status, g_status_cache, "status word", &p);
+    *out = static_cast<int*>(p);
+    return st;
 }
 
 }  // namespace slrme

@@ -292,6 +292,24 @@ def device_status(clear: bool = True) -> int:
     return v.value
 
 
+# Code of the SlrmeError raised for a non-zero device status word (the library
+# reports a bounded wait that gave up through slrme_device_status, not as the
+# return code of a call: the call had already returned when the wait ran).
+DEVICE_STATUS_ERROR = -4
+
+
+def check_device_status(where: str) -> None:
+    """Waits for the device, then reads and clears the library's status word;
+    raises SlrmeError if a kernel's bounded wait gave up since the last check
+    (the outputs of the calls since then are then incomplete)."""
+    import torch
+    torch.cuda.synchronize()
+    st = device_status(clear=True)
+    if st != 0:
+        raise SlrmeError(where, DEVICE_STATUS_ERROR, f"device status word {st:#x}: a kernel's bounded wait gave up; "
+                                    "the outputs of the calls since the last check are incomplete")
+
+
 def wait_probe(max_spins: int, arrive: bool, stream=None) -> None:
     """Launches the library's bounded-wait self-test (see slrme_wait_probe)."""
     _check("slrme_wait_probe", lib().slrme_wait_probe(int(max_spins), int(bool(arrive)), _stream(stream)))

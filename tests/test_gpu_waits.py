@@ -43,3 +43,26 @@ def test_wait_probe_rejects_bad_bounds():
     assert L.slrme_wait_probe(0, 0, None) == -1
     assert L.slrme_wait_probe(1 << 21, 0, None) == -1
     assert L.slrme_wait_probe(10, 2, None) == -1
+
+
+def test_python_api_raises_on_a_wait_that_gave_up():
+    """The Python API's checks (Codec.check, used by bits_per_pixel; the
+    batch form's parameter and statistic reads) read the status word after
+    waiting for the device: a wait that gave up raises, and the word is
+    cleared so the next check passes."""
+    native.lib()
+    native.device_status(clear=True)
+    h, w = 16, 32
+    c = codec.Codec(h, w, "cuda")
+    c.check()
+    native.wait_probe(1000, arrive=False)
+    with pytest.raises(native.SlrmeError) as err:
+        c.check()
+    assert err.value.code == native.DEVICE_STATUS_ERROR
+    c.check()
+    native.wait_probe(1000, arrive=False)
+    img = synth.make_rgbe(h, w, seed=6, lo=-2.0, hi=4.0)
+    c.encode(torch.from_numpy(img.view(np.int32).reshape(-1).copy()).cuda(), 75)
+    with pytest.raises(native.SlrmeError):
+        c.bits_per_pixel()
+    assert c.bits_per_pixel() > 0
