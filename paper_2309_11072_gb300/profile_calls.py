@@ -1,0 +1,48 @@
+"""A minimal driver of the five coder calls for profilers (ncu).
+
+Builds one benchmark image, runs rgbe_split, sdri_base_roundtrip, slr_fit,
+residual_encode and residual_decode once to warm up, then once more (the
+launches to capture), and checks that the decoded words equal the input and
+that no kernel's bounded wait gave up.  It holds only the one codec's
+buffers on the device (about 0.7 GB at 7680x4320), so a profiler that saves
+and restores device memory between its passes stays quick.
+
+    python -m paper_2309_11072_gb300.profile_calls --workload 8k
+    ncu --set full --clock-control none -k regex:"k_fit_tile|k_rows_tile|k_base" -s 4 -c 4 \\
+        -o prof python -m paper_2309_11072_gb300.profile_calls --workload 8k
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+from . import codec, native, synth
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["8k", "2k"], default="8k")
+    ap.add_argument("--quality", type=int, default=90)
+    args = ap.parse_args(argv)
+    wl = synth.workload_8k() if args.workload == "8k" else synth.workload_2k()
+    (h, w), = wl.sizes
+    img = synth.make_workload_images(wl)[0]
+    rgbe = torch.from_numpy(img.view(np.int32).reshape(-1).copy()).cuda()
+    c = codec.Codec(h, w, "cuda", gf_on=True)
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        native.rgbe_split(rgbe, h, w, c.m3, c.e, c.stats, st)
+        native.sdri_base_roundtrip(c.m3, c.e, h, w, c.stats, args.quality, c.s3, None, st)
+        native.slr_fit(c.s3, c.m3, c.e, h, w, 1, c.sums, c.params, st)
+        native.residual_encode(c.s3, c.m3, c.e, h, w, 1, c.params, c.r3, c.hist, st)
+        native.residual_decode(c.s3, c.e, c.r3, h, w, 1, c.params, c.out, st)
+        c.check()
+    if not torch.equal(c.out, rgbe):
+        raise SystemExit("decoded words differ from the input")
+    print(f"ok {w}x{h} q{args.quality}")
+
+
+if __name__ == "__main__":
+    main()
