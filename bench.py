@@ -764,8 +764,7 @@ def measure_batch(args) -> dict:
     ms = [a.elapsed_time(b) for a, b in ev]
     total = sum(ms)
     px = sum(h * w for h, w in wl.sizes)
-    out = bc.out.cpu().numpy().view(np.uint32)
-    ok = all(np.array_equal(out[bc.offset(i):bc.offset(i) + img.size].reshape(img.shape), img)
+    ok = all(np.array_equal(bc.image_layers(i)["out"].cpu().numpy().view(np.uint32), img)
              for i, img in enumerate(imgs))
     peaks = load_peaks()
     bpp = sum(BYTES_PER_PX.values())

@@ -439,7 +439,7 @@ int cnn_adam_step(float* theta, const float* grad, float* m, float* v, int n, fl
                   int step, slrme_stream_t stream);
 
 /* Training crops from coded images: crops[6 k ..] = (pixel offset of the
- * image's planes as in the batch layout, h, w, y0, x0, J) for crop k;
+ * image's planes as in the batch layout, h, row pitch, y0, x0, J) for crop k;
  * writes x[k] = (S - 128, clamp(E - 137 - J, -128, 127)) and target[k] =
  * R + 128 with R = M - M* the regression's residual, as floats of CH x CW. */
 int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const int16_t* r3, const int64_t* crops, int ncrops, int CH,
@@ -452,25 +452,31 @@ int cnn_gather_crops(const uint8_t* s3, const uint8_t* e, const int16_t* r3, con
  * codes one image at a time; the batch form computes, image by image, exactly
  * what the single-image entry points compute.
  *
- * Layout: all images share batch planes.  Image i occupies pixels
- * [px_offset_i, px_offset_i + h_i w_i) of the word planes (rgbe, e, rgbe_out)
- * and [3 px_offset_i, 3 px_offset_i + 3 h_i w_i) of the three-plane buffers
- * (m3, s3, r3: planes c = 0, 1, 2 of the image at 3 px_offset_i + c h_i w_i).
- * params[i] and hist[i * 3 * 511 ...] hold image i's parameters and histograms. */
+ * Layout: all images share batch planes, and every plane of image i has the
+ * row pitch pitch_i = w_i rounded up to a multiple of 16 (so every row of
+ * every plane starts on a 16-byte boundary and the row stages can stream
+ * whole rows with bulk copies).  With n_i = h_i pitch_i, image i occupies
+ * elements [px_offset_i, px_offset_i + n_i) of the word planes (rgbe, e,
+ * rgbe_out), pixel (y, x) at px_offset_i + y pitch_i + x, and
+ * [3 px_offset_i, 3 px_offset_i + 3 n_i) of the three-plane buffers (m3, s3,
+ * r3: plane c of the image at 3 px_offset_i + c n_i).  The words of the
+ * padding columns x = w_i .. pitch_i - 1 of rgbe must be 0 (the zero word:
+ * no pixel), so they add nothing to the log-average statistic; the outputs
+ * hold no defined values there.  params[i] and hist[i * 3 * 511 ...] hold
+ * image i's parameters and histograms. */
 typedef struct slrme_batch_image {
     int32_t h, w;         /* size: h, w >= 0, h*w < 2^31 */
     int32_t quality;      /* base-layer quality 1..100 */
     int32_t gf_on;        /* Gaussian restoration, 0 or 1 */
-    int64_t px_offset;    /* OUT (slrme_batch_plan_init): first pixel of the image in the batch planes,
-                             a multiple of 16 */
+    int64_t px_offset;    /* OUT (slrme_batch_plan_init): first element of the image in the word planes,
+                             a multiple of 256 */
+    int32_t pitch;        /* OUT (slrme_batch_plan_init): row pitch of every plane of the image */
+    int32_t reserved;
 } slrme_batch_image;
 
 typedef struct slrme_batch_tiles {
-    int32_t strip_rows;         /* rows per strip of fit / residual / decode: 4, 8 or 16 */
     int32_t split_ctas_per_sm;  /* persistent CTAs per SM: split 1..8 */
     int32_t base_ctas_per_sm;   /* base round trip 1..3 */
-    int32_t fit_ctas_per_sm;    /* fit 1..2 */
-    int32_t res_ctas_per_sm;    /* residual and decode 1..2 */
 } slrme_batch_tiles;
 
 /* Host-side plan; the caller owns the struct, the images array (kept alive
@@ -481,14 +487,14 @@ typedef struct slrme_batch_plan {
     const slrme_batch_image* images;
     void* workspace;                    /* device, slrme_batch_workspace_bytes(n_images), 256-byte aligned */
     slrme_batch_tiles tiles;
-    int64_t split_chunks, base_tasks, strip_tasks;   /* task counts for the current tiles */
+    int64_t split_chunks, base_tasks, tile_rows;   /* task counts (tile_rows: rows of 2048-column strips) */
     void* graph;                        /* instantiated CUDA graph (cudaGraphExec_t) or NULL */
 } slrme_batch_plan;
 
-/* Device buffers of one batch (all device pointers, caller-owned).  rgbe,
- * r3 and rgbe_out must be 16-byte aligned, params and hist 4-byte aligned.
- * Sizes: rgbe, e, rgbe_out: total_px elements; m3, s3, r3: 3 total_px;
- * params: n_images; hist: n_images * 3 * 511 (or NULL). */
+/* Device buffers of one batch (all device pointers, caller-owned).  The
+ * planes (rgbe, m3, e, s3, r3, rgbe_out) must be 16-byte aligned, params and
+ * hist 4-byte aligned.  Sizes: rgbe, e, rgbe_out: total_px elements; m3, s3,
+ * r3: 3 total_px; params: n_images; hist: n_images * 3 * 511 (or NULL). */
 typedef struct slrme_batch_buffers {
     const uint32_t* rgbe;
     uint8_t* m3;
@@ -523,9 +529,11 @@ int slrme_batch_encode(const slrme_batch_plan* plan, const slrme_batch_buffers* 
 /* Decoder over the batch (reads s3, e, r3, params; writes rgbe_out). */
 int slrme_batch_decode(const slrme_batch_plan* plan, const slrme_batch_buffers* bufs, slrme_stream_t stream);
 
-/* Times each stage over candidate tiles on this batch (`reps` runs each, best
- * time) and keeps the fastest; synchronous, overwrites the buffers' outputs.
- * The coded results never depend on the tiles. */
+/* Times the split and base stages over candidate grid sizes on this batch
+ * (`reps` runs each, best time) and keeps the fastest; synchronous,
+ * overwrites the buffers' outputs.  The coded results never depend on the
+ * tiles.  (The fit, residual and decoder stages stream whole rows through
+ * shared-memory rings at a fixed two CTAs per SM.) */
 int slrme_batch_autotune(slrme_batch_plan* plan, const slrme_batch_buffers* bufs, int reps, slrme_stream_t stream);
 
 /* Copies the per-image log-average statistics of the last encode (int64

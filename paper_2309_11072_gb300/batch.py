@@ -19,13 +19,12 @@ from .codec import params_to_numpy
 
 class BatchImage(ctypes.Structure):
     _fields_ = [("h", ctypes.c_int32), ("w", ctypes.c_int32), ("quality", ctypes.c_int32),
-                ("gf_on", ctypes.c_int32), ("px_offset", ctypes.c_int64)]
+                ("gf_on", ctypes.c_int32), ("px_offset", ctypes.c_int64), ("pitch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class BatchTiles(ctypes.Structure):
-    _fields_ = [("strip_rows", ctypes.c_int32), ("split_ctas_per_sm", ctypes.c_int32),
-                ("base_ctas_per_sm", ctypes.c_int32), ("fit_ctas_per_sm", ctypes.c_int32),
-                ("res_ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("split_ctas_per_sm", ctypes.c_int32), ("base_ctas_per_sm", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -35,7 +34,7 @@ class BatchPlan(ctypes.Structure):
     _fields_ = [("n_images", ctypes.c_int32), ("total_px", ctypes.c_int64),
                 ("images", ctypes.POINTER(BatchImage)), ("workspace", ctypes.c_void_p),
                 ("tiles", BatchTiles), ("split_chunks", ctypes.c_int64), ("base_tasks", ctypes.c_int64),
-                ("strip_tasks", ctypes.c_int64), ("graph", ctypes.c_void_p)]
+                ("tile_rows", ctypes.c_int64), ("graph", ctypes.c_void_p)]
 
 
 class BatchBuffers(ctypes.Structure):
@@ -88,7 +87,7 @@ class BatchCodec:
         self.device = torch.device(device)
         self.images = (BatchImage * n)()
         for i, ((h, w), q) in enumerate(zip(sizes, qualities)):
-            self.images[i] = BatchImage(int(h), int(w), int(q), int(bool(gf_on)), 0)
+            self.images[i] = BatchImage(int(h), int(w), int(q), int(bool(gf_on)), 0, 0, 0)
         self.ws = torch.zeros(int(_lib().slrme_batch_workspace_bytes(n)), dtype=torch.uint8, device=self.device)
         self.plan = BatchPlan()
         _call("slrme_batch_plan_init", ctypes.addressof(self.plan), ctypes.addressof(self.images), n,
@@ -114,31 +113,43 @@ class BatchCodec:
     def size(self, i: int) -> Tuple[int, int]:
         return int(self.images[i].h), int(self.images[i].w)
 
+    def pitch(self, i: int) -> int:
+        """Row pitch (elements) of every plane of image i."""
+        return int(self.images[i].pitch)
+
     def load(self, imgs: List[np.ndarray]) -> None:
-        """Copy host RGBE images (uint32 [h, w]) into the batch word plane."""
+        """Copy host RGBE images (uint32 [h, w]) into the batch word plane
+        (rows at the image's pitch, padding words zero)."""
         host = np.zeros(int(self.plan.total_px), dtype=np.uint32)
         for i, img in enumerate(imgs):
             h, w = self.size(i)
             assert img.shape == (h, w)
-            o = self.offset(i)
-            host[o:o + h * w] = img.reshape(-1)
+            o, p = self.offset(i), self.pitch(i)
+            host[o:o + h * p].reshape(h, p)[:, :w] = img
         self.rgbe.copy_(torch.from_numpy(host.view(np.int32)))
 
     def _plane3(self, t: torch.Tensor, i: int) -> torch.Tensor:
         h, w = self.size(i)
-        o = 3 * self.offset(i)
-        return t[o:o + 3 * h * w].view(3, h, w)
+        o, p = 3 * self.offset(i), self.pitch(i)
+        return t[o:o + 3 * h * p].view(3, h, p)[:, :, :w]
 
     def _plane1(self, t: torch.Tensor, i: int) -> torch.Tensor:
         h, w = self.size(i)
-        o = self.offset(i)
-        return t[o:o + h * w].view(h, w)
+        o, p = self.offset(i), self.pitch(i)
+        return t[o:o + h * p].view(h, p)[:, :w]
 
     def image_layers(self, i: int) -> dict:
+        """Views of image i's planes ([3, h, w] / [h, w], row stride = pitch)."""
         return dict(m3=self._plane3(self.m3, i), e=self._plane1(self.e, i), s3=self._plane3(self.s3, i),
                     r3=self._plane3(self.r3, i), out=self._plane1(self.out, i),
                     params=self.params[i * native.PARAMS_BYTES // 4:(i + 1) * native.PARAMS_BYTES // 4],
                     hist=self.hist[i * 3 * native.SLRME_NRES:(i + 1) * 3 * native.SLRME_NRES].view(3, -1))
+
+    def dense_layers(self, i: int) -> dict:
+        """image_layers with every plane copied to a dense tensor (rows of w
+        elements), the layout the single-image entry points take."""
+        return {k: (v.contiguous() if k in ("m3", "e", "s3", "r3", "out") else v)
+                for k, v in self.image_layers(i).items()}
 
     def image_params(self, i: int) -> dict:
         native.check_device_status("BatchCodec")

@@ -102,11 +102,13 @@ __device__ __forceinline__ float small_int_to_float(int v) {
     return __fsub_rn(__int_as_float(0x4B000000 | v), 8388608.0f);
 }
 
+// Row y of a plane of row pitch p: columns x0 .. x0 + 7, the last row and
+// column replicated past the edges.
 __device__ __forceinline__ void load8(const uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
-                                      uint8_t (&out)[8]) {
+                                      uint8_t (&out)[8], int p) {
     y = y < h ? y : h - 1;
     if (fast && x0 + 8 <= w) {
-        const uint2 v = __ldg(reinterpret_cast<const uint2*>(plane + (int64_t)y * w + x0));
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(plane + (int64_t)y * p + x0));
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             out[i] = (uint8_t)byte_of(v.x, i);
@@ -117,7 +119,7 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ plane, int h, 
         for (int i = 0; i < 8; ++i) {
             int x = x0 + i;
             x = x < w ? x : w - 1;
-            out[i] = __ldg(plane + (int64_t)y * w + x);
+            out[i] = __ldg(plane + (int64_t)y * p + x);
         }
     }
 }
@@ -131,14 +133,14 @@ __device__ __forceinline__ void unpack8(const uint2 v, uint8_t (&out)[8]) {
 }
 
 __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
-                                       const uint32_t lo, const uint32_t hi) {
+                                       const uint32_t lo, const uint32_t hi, int p) {
     if (y >= h) return;
     if (fast && x0 + 8 <= w) {
-        *reinterpret_cast<uint2*>(plane + (int64_t)y * w + x0) = make_uint2(lo, hi);
+        *reinterpret_cast<uint2*>(plane + (int64_t)y * p + x0) = make_uint2(lo, hi);
     } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            if (x0 + i < w) plane[(int64_t)y * w + x0 + i] = (uint8_t)byte_of(i < 4 ? lo : hi, i & 3);
+            if (x0 + i < w) plane[(int64_t)y * p + x0 + i] = (uint8_t)byte_of(i < 4 ? lo : hi, i & 3);
     }
 }
 
@@ -212,9 +214,11 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
                                           bool fast, int y0, int xb, int lane, const BaseKey& K,
                                           const uint32_t* gcode, int* T, uint8_t* __restrict__ s3,
                                           uint8_t* __restrict__ sdr3, const uint2* pre, int16_t* __restrict__ lv3,
-                                          float lw2 = 0.0f) {
+                                          float lw2 = 0.0f, int p = 0) {
+    // planes of h rows of pitch p (p = 0: p = w)
+    p = p ? p : w;
     const int blk = lane >> 3, sub = lane & 7;   // block in the band, row (phases 1, 3) or column (phase 2)
-    const int64_t n = (int64_t)h * w;
+    const int64_t n = (int64_t)h * p;
     const int J = K.J;
     const float kr = K.kr, wr = K.wr;
     const int x0 = xb + 8 * blk;                 // first column of this lane's block
@@ -230,10 +234,10 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
             unpack8(pre[96], ee);
         } else {
             // rows past the bottom and columns past the right edge replicate the last row/column
-            load8(m3, h, w, y, x0, fast, mr);
-            load8(m3 + n, h, w, y, x0, fast, mg);
-            load8(m3 + 2 * n, h, w, y, x0, fast, mb);
-            load8(e, h, w, y, x0, fast, ee);
+            load8(m3, h, w, y, x0, fast, mr, p);
+            load8(m3 + n, h, w, y, x0, fast, mg, p);
+            load8(m3 + 2 * n, h, w, y, x0, fast, mb, p);
+            load8(e, h, w, y, x0, fast, ee, p);
         }
         int sdr[3][8];
 #pragma unroll
@@ -244,7 +248,7 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
             for (int c = 0; c < 3; ++c) {
                 const uint32_t lo = sdr[c][0] | (sdr[c][1] << 8) | (sdr[c][2] << 16) | (sdr[c][3] << 24);
                 const uint32_t hi = sdr[c][4] | (sdr[c][5] << 8) | (sdr[c][6] << 16) | (sdr[c][7] << 24);
-                store8(sdr3 + c * n, h, w, y, x0, fast, lo, hi);
+                store8(sdr3 + c * n, h, w, y, x0, fast, lo, hi, p);
             }
         }
 #pragma unroll
@@ -310,7 +314,7 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         for (int i = 0; i < 8; ++i) q[i] = (uint32_t)min(max(X[i] >> 15, 0), 255);
         const uint32_t lo = __byte_perm(__byte_perm(q[0], q[1], 0x0040), __byte_perm(q[2], q[3], 0x0040), 0x5410);
         const uint32_t hi = __byte_perm(__byte_perm(q[4], q[5], 0x0040), __byte_perm(q[6], q[7], 0x0040), 0x5410);
-        if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi);
+        if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi, p);
     }
     __syncwarp();
 }
@@ -403,11 +407,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
         const int cols = (im.w + 31) >> 5;
         const int64_t bands = (int64_t)((im.h + 7) >> 3) * cols;
         const int64_t t = (k - B.base_prefix[i]) * kWarps + warp;
-        const bool fast = (im.w % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
+        // pitched rows: 8-byte loads and stores are aligned wherever 8 columns lie inside the image
+        const bool fast = (im.pitch % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
                           ((uintptr_t)s3 % 8 == 0);
         if ((int64_t)im.h * im.w > 0 && t < bands)
             base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
-                      tile[warp], s3, nullptr, nullptr, nullptr);
+                      tile[warp], s3, nullptr, nullptr, nullptr, 0.0f, im.pitch);
     }
 }
 
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_plane_rt(const Planes420 P, const 
         const int x0 = xb + 8 * blk, y = y0 + sub;
         {
             uint8_t px[8];
-            load8(plane, h, w, y, x0, false, px);   // rows and columns past the edge replicate it
+            load8(plane, h, w, y, x0, false, px, w);   // rows and columns past the edge replicate it
             int X[8], F[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) X[i] = px[i];
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(kThreads) k_plane_rt(const Planes420 P, const 
             for (int i = 0; i < 8; ++i) q[i] = (uint32_t)clamp255(X[i] >> 15);
             const uint32_t lo = q[0] | (q[1] << 8) | (q[2] << 16) | (q[3] << 24);
             const uint32_t hi = q[4] | (q[5] << 8) | (q[6] << 16) | (q[7] << 24);
-            if (x0 < w) store8(plane, h, w, y, x0, false, lo, hi);
+            if (x0 < w) store8(plane, h, w, y, x0, false, lo, hi, w);
         }
         __syncwarp();
     }

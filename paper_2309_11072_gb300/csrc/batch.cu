@@ -2,10 +2,11 @@
 // per stage, a tile autotuner, and CUDA-graph capture of the whole chain.
 //
 // A plan lays the images out in shared batch planes (each image's first pixel
-// aligned to 16 pixels), writes the device descriptors and the per-stage task
-// prefix tables into a caller-provided workspace, and holds the tile choice.
-// Stage kernels (split.cu, base.cu, slr.cu) map their task index to an image
-// by binary search over a prefix table.
+// aligned to 256 pixels, every row of every plane to 16 bytes: the row pitch
+// is w rounded up to 16), writes the device descriptors and the per-stage
+// task prefix tables into a caller-provided workspace, and holds the tile
+// choice.  Stage kernels (split.cu, base.cu, slr.cu) map their task index to
+// an image by binary search over a prefix table.
 #include <string.h>
 
 #include <vector>
@@ -15,13 +16,18 @@
 namespace slrme {
 namespace {
 
-constexpr int64_t kAlignPx = 16;
+static_assert(sizeof(slrme_batch_image) == 32 && sizeof(slrme_batch_tiles) == 8, "batch ABI structs");
+static_assert(sizeof(slrme_batch_plan) == 72 && sizeof(slrme_batch_buffers) == 64, "batch ABI structs");
+static_assert(sizeof(BatchImage) == sizeof(slrme_batch_image), "device image descriptor");
+
+constexpr int64_t kAlignPx = 256;
+constexpr int kPitchAlign = 16;
 constexpr size_t kSection = 256;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    size_t img, quant, split_prefix, base_prefix, strip_prefix, lum, sums, total;
+    size_t img, quant, split_prefix, base_prefix, row_prefix, lum, sums, total;
 };
 
 Layout layout(int n) {
@@ -35,7 +41,7 @@ Layout layout(int n) {
     o = round_up(o + sizeof(int64_t) * (size_t)(n + 1), kSection);
     L.base_prefix = o;
     o = round_up(o + sizeof(int64_t) * (size_t)(n + 1), kSection);
-    L.strip_prefix = o;
+    L.row_prefix = o;
     o = round_up(o + sizeof(int64_t) * (size_t)(n + 1), kSection);
     L.lum = o;
     o = round_up(o + sizeof(int64_t) * 2 * (size_t)n, kSection);
@@ -53,35 +59,37 @@ BatchDev device_view(const slrme_batch_plan* p) {
     B.quant = reinterpret_cast<const QuantTable*>(base + L.quant);
     B.split_prefix = reinterpret_cast<const int64_t*>(base + L.split_prefix);
     B.base_prefix = reinterpret_cast<const int64_t*>(base + L.base_prefix);
-    B.strip_prefix = reinterpret_cast<const int64_t*>(base + L.strip_prefix);
+    B.row_prefix = reinterpret_cast<const int64_t*>(base + L.row_prefix);
     B.lum_stats = reinterpret_cast<int64_t*>(base + L.lum);
     B.sums = reinterpret_cast<unsigned long long*>(base + L.sums);
     B.n = p->n_images;
-    B.strip_rows = p->tiles.strip_rows;
     return B;
 }
 
 bool tiles_valid(const slrme_batch_tiles& t) {
-    return (t.strip_rows == 4 || t.strip_rows == 8 || t.strip_rows == 16) && t.split_ctas_per_sm >= 1 &&
-           t.split_ctas_per_sm <= 8 && t.base_ctas_per_sm >= 1 && t.base_ctas_per_sm <= 3 &&
-           t.fit_ctas_per_sm >= 1 && t.fit_ctas_per_sm <= 2 && t.res_ctas_per_sm >= 1 && t.res_ctas_per_sm <= 2;
+    return t.split_ctas_per_sm >= 1 && t.split_ctas_per_sm <= 8 && t.base_ctas_per_sm >= 1 &&
+           t.base_ctas_per_sm <= 3;
 }
 
-// Task prefix tables for the plan's tiles, uploaded synchronously.
+int pitch_of(int w) { return (w + kPitchAlign - 1) / kPitchAlign * kPitchAlign; }
+
+// Task prefix tables, uploaded synchronously: split chunks of 4096 words over
+// each image's pitched plane, base CTA tasks of 8 bands of 8 x 32 pixels, and
+// the rows of 2048-column strips of the row stages.
 int upload_prefixes(slrme_batch_plan* p, cudaStream_t s) {
     const int n = p->n_images;
-    std::vector<int64_t> sp(n + 1), bp(n + 1), tp(n + 1);
-    sp[0] = bp[0] = tp[0] = 0;
+    std::vector<int64_t> sp(n + 1), bp(n + 1), rp(n + 1);
+    sp[0] = bp[0] = rp[0] = 0;
     for (int i = 0; i < n; ++i) {
         const slrme_batch_image& im = p->images[i];
         const int64_t px = (int64_t)im.h * im.w;
-        const int64_t chunks = (px + kSplitChunk - 1) / kSplitChunk;
+        const int64_t words = (int64_t)im.h * pitch_of(im.w);
+        const int64_t chunks = (words + kSplitChunk - 1) / kSplitChunk;
         const int64_t bands = (int64_t)((im.h + 7) / 8) * ((im.w + 31) / 32);
-        const int64_t strips =
-            (int64_t)((im.h + p->tiles.strip_rows - 1) / p->tiles.strip_rows) * ((im.w + kStripColsBatch - 1) / kStripColsBatch);
+        const int64_t rows = px ? (int64_t)((im.w + kTileColsBatch - 1) / kTileColsBatch) * im.h : 0;
         sp[i + 1] = sp[i] + chunks;
         bp[i + 1] = bp[i] + (px ? (bands + 7) / 8 : 0);
-        tp[i + 1] = tp[i] + (px ? (strips + 7) / 8 : 0);
+        rp[i + 1] = rp[i] + rows;
     }
     const Layout L = layout(n);
     char* base = static_cast<char*>(p->workspace);
@@ -89,13 +97,13 @@ int upload_prefixes(slrme_batch_plan* p, cudaStream_t s) {
             cudaSuccess ||
         cudaMemcpyAsync(base + L.base_prefix, bp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
-        cudaMemcpyAsync(base + L.strip_prefix, tp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s) !=
+        cudaMemcpyAsync(base + L.row_prefix, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
         return cuda_status("batch plan upload");
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_status("batch plan upload");
     p->split_chunks = sp[n];
     p->base_tasks = bp[n];
-    p->strip_tasks = tp[n];
+    p->tile_rows = rp[n];
     return SLRME_OK;
 }
 
@@ -114,10 +122,10 @@ bool buffers_ok(const slrme_batch_plan* p, const slrme_batch_buffers* b, bool en
             return false;
         }
     }
-    if (!b->params || (uintptr_t)b->params % 4 || (b->hist && (uintptr_t)b->hist % 4) ||
-        (b->rgbe && (uintptr_t)b->rgbe % 16) || (b->r3 && (uintptr_t)b->r3 % 16) ||
-        (b->rgbe_out && (uintptr_t)b->rgbe_out % 16)) {
-        set_error("batch: params/hist must be 4-byte, rgbe/r3/rgbe_out 16-byte aligned");
+    auto a16 = [](const void* q) { return q == nullptr || (uintptr_t)q % 16 == 0; };
+    if (!b->params || (uintptr_t)b->params % 4 || (b->hist && (uintptr_t)b->hist % 4) || !a16(b->rgbe) ||
+        !a16(b->m3) || !a16(b->e) || !a16(b->s3) || !a16(b->r3) || !a16(b->rgbe_out)) {
+        set_error("batch: params/hist must be 4-byte aligned, the planes 16-byte aligned");
         return false;
     }
     return true;
@@ -128,17 +136,15 @@ int encode_stages(const slrme_batch_plan* p, const slrme_batch_buffers* b, cudaS
     const slrme_batch_tiles& t = p->tiles;
     int st = launch_split_batch(B, p->split_chunks, t.split_ctas_per_sm, b->rgbe, b->m3, b->e, s);
     if (st == SLRME_OK) st = launch_base_batch(B, p->base_tasks, t.base_ctas_per_sm, b->m3, b->e, b->s3, s);
-    if (st == SLRME_OK) st = launch_fit_batch(B, p->strip_tasks, t.fit_ctas_per_sm, b->s3, b->m3, b->e, b->params, s);
+    if (st == SLRME_OK) st = launch_fit_batch(B, p->tile_rows, b->s3, b->m3, b->e, b->params, s);
     if (st == SLRME_OK)
-        st = launch_residual_batch(B, p->strip_tasks, t.res_ctas_per_sm, b->s3, b->m3, b->e, b->params, b->r3,
-                                   b->hist, s);
+        st = launch_residual_batch(B, p->tile_rows, b->s3, b->m3, b->e, b->params, b->r3, b->hist, s);
     return st;
 }
 
 int decode_stage(const slrme_batch_plan* p, const slrme_batch_buffers* b, cudaStream_t s) {
     const BatchDev B = device_view(p);
-    return launch_decode_batch(B, p->strip_tasks, p->tiles.res_ctas_per_sm, b->s3, b->e, b->r3, b->params,
-                               b->rgbe_out, s);
+    return launch_decode_batch(B, p->tile_rows, b->s3, b->e, b->r3, b->params, b->rgbe_out, s);
 }
 
 }  // namespace
@@ -176,14 +182,16 @@ int slrme_batch_plan_init(slrme_batch_plan* plan, slrme_batch_image* images, int
             return SLRME_EINVAL;
         }
         im.px_offset = px;
-        dev[i] = BatchImage{im.h, im.w, im.quality, im.gf_on, px};
-        px += ((int64_t)im.h * im.w + kAlignPx - 1) / kAlignPx * kAlignPx;
+        im.pitch = pitch_of(im.w);
+        im.reserved = 0;
+        dev[i] = BatchImage{im.h, im.w, im.quality, im.gf_on, px, im.pitch, 0};
+        px += ((int64_t)im.h * im.pitch + kAlignPx - 1) / kAlignPx * kAlignPx;
     }
     plan->n_images = n_images;
     plan->total_px = px;
     plan->images = images;
     plan->workspace = workspace;
-    plan->tiles = slrme_batch_tiles{8, 4, 3, 2, 2};
+    plan->tiles = slrme_batch_tiles{4, 3};
     plan->graph = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     const Layout L = layout(n_images);
@@ -215,8 +223,9 @@ int slrme_batch_decode(const slrme_batch_plan* plan, const slrme_batch_buffers* 
     return decode_stage(plan, bufs, (cudaStream_t)stream);
 }
 
-// Times every stage over the candidate tiles on the caller's batch and keeps
-// the fastest; synchronous.  Results do not depend on the tiles, only speed.
+// Times the split and base stages over candidate grid sizes on the caller's
+// batch and keeps the fastest; synchronous.  Results do not depend on the
+// tiles, only speed.
 int slrme_batch_autotune(slrme_batch_plan* plan, const slrme_batch_buffers* bufs, int reps, slrme_stream_t stream) {
     if (!buffers_ok(plan, bufs, true, true) || reps < 1) {
         if (reps < 1) set_error("slrme_batch_autotune: reps must be >= 1");
@@ -262,41 +271,6 @@ int slrme_batch_autotune(slrme_batch_plan* plan, const slrme_batch_buffers* bufs
         if (t < tb) { tb = t; best.base_ctas_per_sm = c; }
     }
     plan->tiles.base_ctas_per_sm = best.base_ctas_per_sm;
-    {
-        // strip height is shared by fit, residual and decode: pick the height
-        // whose best fit + residual + decode time is lowest
-        float best_sum = 1e30f;
-        for (int rows : {4, 8, 16}) {
-            slrme_batch_tiles cand = plan->tiles;
-            cand.strip_rows = rows;
-            st = slrme_batch_set_tiles(plan, &cand, stream);
-            if (st != SLRME_OK) goto done;
-            const BatchDev B = device_view(plan);
-            float tf = 1e30f, trd = 1e30f;
-            int cf = 1, crd = 1;
-            for (int c : {1, 2}) {
-                st = timeit([&] { return launch_fit_batch(B, plan->strip_tasks, c, bufs->s3, bufs->m3, bufs->e,
-                                                          bufs->params, s); }, &t);
-                if (st != SLRME_OK) goto done;
-                if (t < tf) { tf = t; cf = c; }
-                // residual and decode share one grid size
-                float tr = 0.0f, td = 0.0f;
-                st = timeit([&] { return launch_residual_batch(B, plan->strip_tasks, c, bufs->s3, bufs->m3, bufs->e,
-                                                               bufs->params, bufs->r3, bufs->hist, s); }, &tr);
-                if (st != SLRME_OK) goto done;
-                st = timeit([&] { return launch_decode_batch(B, plan->strip_tasks, c, bufs->s3, bufs->e, bufs->r3,
-                                                             bufs->params, bufs->rgbe_out, s); }, &td);
-                if (st != SLRME_OK) goto done;
-                if (tr + td < trd) { trd = tr + td; crd = c; }
-            }
-            if (tf + trd < best_sum) {
-                best_sum = tf + trd;
-                best.strip_rows = rows;
-                best.fit_ctas_per_sm = cf;
-                best.res_ctas_per_sm = crd;
-            }
-        }
-    }
     st = slrme_batch_set_tiles(plan, &best, stream);
 done:
     cudaEventDestroy(e0);

@@ -245,7 +245,7 @@ __global__ void k_gather(const uint8_t* __restrict__ s3b, const uint8_t* __restr
     if (p >= (int64_t)ncrops * hw) return;
     const int k = (int)(p / hw);
     const int yy = (int)((p % hw) / CW), xx = (int)(p % CW);
-    const int64_t* c = crops + 6 * (int64_t)k;   // px, h, w, y0, x0, J
+    const int64_t* c = crops + 6 * (int64_t)k;   // px, h, row pitch, y0, x0, J
     const int64_t px = c[0], h = c[1], w = c[2];
     const int64_t n = h * w, o = (c[3] + yy) * w + c[4] + xx;
     const uint8_t* s3 = s3b + 3 * px;

@@ -559,57 +559,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_fit(const uint8_t* __restrict__
     bins_to_global(bins, gbins, false);
 }
 
-// Vector loads need 8-byte aligned rows of every plane.
-__device__ __forceinline__ bool planes_fast(int w, const void* a, const void* b, const void* c) {
-    return (w % 8 == 0) && ((uintptr_t)a % 8 == 0) && ((uintptr_t)b % 8 == 0) && ((uintptr_t)c % 8 == 0);
-}
-
-// Batch: each CTA task is 8 strips of one image; a CTA works through a
-// contiguous range of tasks, so its bins change image rarely.
-__global__ void __launch_bounds__(kThreads, 2) k_fit_batch(const BatchDev B, int64_t cta_tasks,
-                                                           const uint8_t* __restrict__ s3b,
-                                                           const uint8_t* __restrict__ m3b,
-                                                           const uint8_t* __restrict__ eb) {
-    __shared__ SmemBins bins;
-    __shared__ uint32_t queue[kWarps][32 * kQueueStride];
-    bins_clear(bins);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    FitWarp st;
-    run_reset(st.even, -1);
-    run_reset(st.odd, -1);
-    st.Q = queue[warp];
-    st.queued = 0;
-    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
-    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
-    int cur = -1;
-    for (int64_t k = k0; k < k1; ++k) {
-        const int i = batch_image_of(B.strip_prefix, B.n, k);
-        if (i != cur) {
-            if (cur >= 0) {
-                fit_drain(st, bins, lane);
-                __syncthreads();
-                bins_to_global(bins, B.sums + (int64_t)cur * kNbin * kNsum, true);
-                __syncthreads();
-            }
-            cur = i;
-        }
-        const BatchImage im = B.img[i];
-        const int64_t n = (int64_t)im.h * im.w;
-        const uint8_t* s3 = s3b + 3 * im.px;
-        const uint8_t* m3 = m3b + 3 * im.px;
-        const uint8_t* e = eb + im.px;
-        const int cols = (im.w + kStripCols - 1) / kStripCols;
-        const int64_t strips = (int64_t)((im.h + B.strip_rows - 1) / B.strip_rows) * cols;
-        const int64_t t = (k - B.strip_prefix[i]) * kWarps + warp;
-        if (n > 0 && t < strips)
-            fit_strip(s3, m3, e, im.h, im.w, im.gf_on != 0, planes_fast(im.w, s3, m3, e),
-                      (int)(t / cols) * B.strip_rows, B.strip_rows, (int)(t % cols) * kStripCols, lane, st, bins);
-    }
-    fit_drain(st, bins, lane);
-    __syncthreads();
-    if (cur >= 0) bins_to_global(bins, B.sums + (int64_t)cur * kNbin * kNsum, false);
-}
 
 // ====================================================================== solve
 
@@ -778,52 +727,6 @@ __global__ void __launch_bounds__(kThreads) k_residual(const uint8_t* __restrict
     }
 }
 
-// Batch: CTA tasks of 8 strips of one image; parameters and histogram of the
-// current image stay in shared memory until the CTA moves to the next image.
-__global__ void __launch_bounds__(kThreads) k_residual_batch(const BatchDev B, int64_t cta_tasks,
-                                                             const uint8_t* __restrict__ s3b,
-                                                             const uint8_t* __restrict__ m3b,
-                                                             const uint8_t* __restrict__ eb,
-                                                             const slrme_params* __restrict__ P,
-                                                             int16_t* __restrict__ r3b, uint32_t* __restrict__ ghist) {
-    __shared__ float sa[3 * kNbin], sb[3 * kNbin];
-    __shared__ uint32_t hist[3 * kNres];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
-    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
-    int cur = -1;
-    for (int64_t k = k0; k < k1; ++k) {
-        const int i = batch_image_of(B.strip_prefix, B.n, k);
-        if (i != cur) {
-            __syncthreads();
-            if (cur >= 0 && ghist)
-                for (int j = threadIdx.x; j < 3 * kNres; j += kThreads)
-                    if (hist[j]) atomicAdd(ghist + (int64_t)cur * 3 * kNres + j, hist[j]);
-            load_params(P + i, sa, sb);
-            for (int j = threadIdx.x; j < 3 * kNres; j += kThreads) hist[j] = 0u;
-            __syncthreads();
-            cur = i;
-        }
-        const BatchImage im = B.img[i];
-        const uint8_t* s3 = s3b + 3 * im.px;
-        const uint8_t* m3 = m3b + 3 * im.px;
-        const uint8_t* e = eb + im.px;
-        int16_t* r3 = r3b + 3 * im.px;
-        const int cols = (im.w + kStripCols - 1) / kStripCols;
-        const int64_t strips = (int64_t)((im.h + B.strip_rows - 1) / B.strip_rows) * cols;
-        const int64_t t = (k - B.strip_prefix[i]) * kWarps + warp;
-        const bool fast = planes_fast(im.w, s3, m3, e);
-        if ((int64_t)im.h * im.w > 0 && t < strips)
-            residual_strip(s3, m3, e, im.h, im.w, im.gf_on != 0, fast, fast && ((uintptr_t)r3 % 16 == 0),
-                           (int)(t / cols) * B.strip_rows, B.strip_rows, (int)(t % cols) * kStripCols, lane, sa, sb,
-                           r3, ghist ? hist : nullptr);
-    }
-    __syncthreads();
-    if (cur >= 0 && ghist)
-        for (int j = threadIdx.x; j < 3 * kNres; j += kThreads)
-            if (hist[j]) atomicAdd(ghist + (int64_t)cur * 3 * kNres + j, hist[j]);
-}
-
 // ====================================================================== decode
 
 // One strip: M = R + M*, repacked with E into RGBE words.
@@ -896,41 +799,6 @@ __global__ void __launch_bounds__(kThreads) k_decode(const uint8_t* __restrict__
                      (int)(t % cols) * kStripCols, lane, sa, sb, out);
 }
 
-__global__ void __launch_bounds__(kThreads) k_decode_batch(const BatchDev B, int64_t cta_tasks,
-                                                           const uint8_t* __restrict__ s3b,
-                                                           const uint8_t* __restrict__ eb,
-                                                           const int16_t* __restrict__ r3b,
-                                                           const slrme_params* __restrict__ P,
-                                                           uint32_t* __restrict__ outb) {
-    __shared__ float sa[3 * kNbin], sb[3 * kNbin];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
-    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
-    int cur = -1;
-    for (int64_t k = k0; k < k1; ++k) {
-        const int i = batch_image_of(B.strip_prefix, B.n, k);
-        if (i != cur) {
-            __syncthreads();
-            load_params(P + i, sa, sb);
-            __syncthreads();
-            cur = i;
-        }
-        const BatchImage im = B.img[i];
-        const uint8_t* s3 = s3b + 3 * im.px;
-        const uint8_t* e = eb + im.px;
-        const int16_t* r3 = r3b + 3 * im.px;
-        uint32_t* out = outb + im.px;
-        const int cols = (im.w + kStripCols - 1) / kStripCols;
-        const int64_t strips = (int64_t)((im.h + B.strip_rows - 1) / B.strip_rows) * cols;
-        const int64_t t = (k - B.strip_prefix[i]) * kWarps + warp;
-        const bool fast = (im.w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
-        const bool vec = fast && ((uintptr_t)r3 % 16 == 0) && ((uintptr_t)out % 16 == 0);
-        if ((int64_t)im.h * im.w > 0 && t < strips)
-            decode_strip(s3, e, r3, im.h, im.w, im.gf_on != 0, fast, vec, (int)(t / cols) * B.strip_rows,
-                         B.strip_rows, (int)(t % cols) * kStripCols, lane, sa, sb, out);
-    }
-}
-
 // ====================================================================== bulk-copy row pipeline
 //
 // For images whose rows are 16-byte aligned (w % 16 == 0, 16-byte aligned
@@ -956,6 +824,7 @@ constexpr int kTileWarps = 8;                              // consumer warps
 constexpr int kTileThreads = (kTileWarps + 1) * 32;        // + one producer warp
 constexpr int kTileCols = kTileWarps * kStripCols;         // 2048
 constexpr int kTileSW = kTileCols + 32;                    // S row with halos, per plane
+static_assert(kTileColsBatch == kTileCols, "batch strips are tile strips");
 constexpr int kTaskRows = 256;
 constexpr uint32_t kTileSBytes = 3u * kTileSW;             // 6240
 constexpr uint32_t kTileSStride = 6272;                    // slot stride, multiple of 128
@@ -1240,18 +1109,6 @@ __device__ __forceinline__ void run2_sub(Run2& a, const Run2& b) {   // a -= b (
     }
 }
 
-__device__ __forceinline__ void run2_add(Run2& a, const Run2& b) {   // a += b (E kept)
-    a.n += b.n;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        a.sx[c] += b.sx[c];
-        a.sy[c] += b.sy[c];
-        a.sxy[c] += b.sxy[c];
-        a.sxl[c] += b.sxl[c];
-        a.sxh[c] += b.sxh[c];
-    }
-}
-
 // One channel of an 8-pixel segment added to sums (sum x, sum y, sum x y,
 // sum x (x & 255), sum x (x >> 8)): x as 16-bit pairs and the y bytes, both
 // already masked to the run's pixels (21 operations).
@@ -1379,6 +1236,7 @@ __device__ __forceinline__ void drain_runs(FitQueues& fq, SmemBins& bins, int la
 // have no high part under the split rule; x y and x x take two words).
 __device__ __forceinline__ void drain_segment_pixels(const uint32_t* q, uint32_t B) {
     const uint32_t elo = q[0], ehi = q[1];
+    const int cnt = (int)q[20];   // pixels of the segment (fewer than 8 at an image's right edge)
     uint32_t mlo[3] = {q[2], q[3], q[4]}, mhi[3] = {q[5], q[6], q[7]};
     uint32_t X[3][4];
 #pragma unroll
@@ -1388,20 +1246,22 @@ __device__ __forceinline__ void drain_segment_pixels(const uint32_t* q, uint32_t
     constexpr uint32_t kHi = 4u * kNbin * kNsum;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const uint32_t lo = B + 4u * kNsum * byte_of(i < 4 ? elo : ehi, i & 3);
-        red_add(lo, 1u);
+        if (i < cnt) {
+            const uint32_t lo = B + 4u * kNsum * byte_of(i < 4 ? elo : ehi, i & 3);
+            red_add(lo, 1u);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const uint32_t x = (X[c][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-            const uint32_t y = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
-            const uint32_t xy = x * y, xx = x * x;
-            const uint32_t a = lo + 4u * (1 + 4 * c);
-            red_add(a, x);
-            red_add(a + 4u, y);
-            red_add(a + 8u, xy & 0xFFFu);
-            red_add(a + 8u + kHi, xy >> 12);
-            red_add(a + 12u, xx & 0xFFFu);
-            red_add(a + 12u + kHi, xx >> 12);
+            for (int c = 0; c < 3; ++c) {
+                const uint32_t x = (X[c][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                const uint32_t y = byte_of(i < 4 ? mlo[c] : mhi[c], i & 3);
+                const uint32_t xy = x * y, xx = x * x;
+                const uint32_t a = lo + 4u * (1 + 4 * c);
+                red_add(a, x);
+                red_add(a + 4u, y);
+                red_add(a + 8u, xy & 0xFFFu);
+                red_add(a + 8u + kHi, xy >> 12);
+                red_add(a + 12u, xx & 0xFFFu);
+                red_add(a + 12u + kHi, xx >> 12);
+            }
         }
     }
 }
@@ -1816,6 +1676,525 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_til
     }
 }
 
+
+// ---------------------------------------------------------------- batch form on the row pipeline
+//
+// The same rings and consumers over many images: the rows of every image's
+// 2048-column strips, image after image (row_prefix), are split into one
+// contiguous range per CTA, so a CTA's tasks may belong to several images.
+// Every plane of image i has the row pitch p_i (w_i rounded up to 16), so each
+// row starts 16-byte aligned and the producer copies whole rows rounded up to
+// 16 bytes.  A lane whose 8 columns cross the image's right edge (k < 8 valid
+// pixels) replicates its last valid S byte into byte k before filtering and
+// stores or adds only its k pixels.  At a change of image the consumer warps
+// meet at a barrier to flush the CTA's shared bins or histograms to that
+// image and reload the parameters; a warp whose wait gave up keeps walking
+// the same task sequence (no waits, no work) so that every warp reaches every
+// such barrier.
+
+struct TileBatchArgs {
+    BatchDev B;
+    const uint8_t* s3b;          // S planes of the batch
+    const uint8_t* auxb;         // M planes (fit, residual) or R planes (decode), as bytes
+    const uint8_t* eb;           // E plane
+    int64_t total_rows;          // rows of 2048-column strips over all images
+    int max_spins;
+    const slrme_params* params;  // [n_images]
+    int16_t* r3b;                // residual planes (residual)
+    uint32_t* hist;              // [n_images][3][511] (residual; may be null)
+    uint32_t* outb;              // decoded words (decode)
+};
+
+// A CTA's range of global rows and its current task and image.
+struct BatchRange {
+    int64_t r, end;
+    int64_t base, limit;         // global rows of the current image: [base, limit)
+    int img;
+    const uint8_t* s3;
+    const uint8_t* aux;
+    const uint8_t* e;
+    int64_t px;                  // first element of the image in the word planes
+    int h, w, p, gf;
+    int y0, rows, xs;
+    __device__ __forceinline__ void set(const TileBatchArgs& A, int i, uint32_t elem) {
+        img = i;
+        base = A.B.row_prefix[i];
+        limit = A.B.row_prefix[i + 1];
+        const BatchImage im = A.B.img[i];
+        h = im.h;
+        w = im.w;
+        p = im.pitch;
+        gf = im.gf_on;
+        px = im.px;
+        s3 = A.s3b + 3 * im.px;
+        aux = A.auxb + 3 * im.px * (int64_t)elem;
+        e = A.eb + im.px;
+    }
+    __device__ __forceinline__ bool next(const TileBatchArgs& A, uint32_t elem) {
+        if (r >= end) return false;
+        if (r >= limit) {   // the next image with rows (images without rows have base == limit)
+            int i = img;
+            do {
+                ++i;
+            } while (A.B.row_prefix[i + 1] <= r);
+            set(A, i, elem);
+        }
+        const int64_t local = r - base;
+        const int c = (int)(local / h);
+        y0 = (int)(local - (int64_t)c * h);
+        rows = (int)min(min(end - r, (int64_t)(h - y0)), (int64_t)kTaskRows);
+        xs = c * kTileCols;
+        r += rows;
+        return true;
+    }
+};
+
+__device__ __forceinline__ BatchRange batch_range(const TileBatchArgs& A, uint32_t elem) {
+    const int64_t G = gridDim.x, b = blockIdx.x;
+    BatchRange T;
+    T.r = b * A.total_rows / G;
+    T.end = (b + 1) * A.total_rows / G;
+    T.img = -1;
+    T.base = T.limit = 0;
+    if (T.r < T.end) T.set(A, batch_image_of(A.B.row_prefix, A.B.n, T.r), elem);
+    return T;
+}
+
+// Per-lane geometry of a batch task: as LaneCols, plus the lane's valid
+// pixels k and the byte selectors that copy byte k - 1 into byte k.
+struct LaneColsB {
+    int x0, own, offl, offr, k;
+    uint32_t sel_lo, sel_hi;
+    bool inside, full;
+    __device__ __forceinline__ LaneColsB(int xs, int w, int warp, int lane) {
+        x0 = xs + kStripCols * warp + 8 * lane;
+        own = 16 + kStripCols * warp + 8 * lane;
+        k = min(max(w - x0, 0), 8);
+        inside = k > 0;
+        full = k == 8;
+        offl = x0 == 0 ? own : own - 1;
+        offr = full && x0 + 8 < w ? own + 8 : own + max(k - 1, 0);
+        // result byte j takes source byte j, except byte k (1 <= k <= 7), which takes k - 1
+        const uint32_t id = 0x76543210u;
+        const uint32_t sel = (k >= 1 && k <= 7) ? ((id & ~(0xFu << (4 * k))) | ((uint32_t)(k - 1) << (4 * k))) : id;
+        sel_lo = sel & 0xFFFFu;
+        sel_hi = sel >> 16;
+    }
+};
+
+// x pairs of one S row of channel c for a batch lane (restoration per image).
+__device__ __forceinline__ void s_row_pairs_b(uint32_t slot, int c, const LaneColsB& lc, bool gf, uint32_t (&H)[4]) {
+    const uint32_t row = slot + (uint32_t)c * kTileSW;
+    const uint2 v = lds64(row + lc.own);
+    const uint32_t lo = __byte_perm(v.x, v.y, lc.sel_lo), hi = __byte_perm(v.x, v.y, lc.sel_hi);
+    if (gf) {
+        uint32_t l, r;
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(l) : "r"(row + lc.offl));
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(r) : "r"(row + lc.offr));
+        hfilter(lo, hi, l, r, H);
+    } else {
+        H[0] = __byte_perm(lo, 0, 0x4140);
+        H[1] = __byte_perm(lo, 0, 0x4342);
+        H[2] = __byte_perm(hi, 0, 0x4140);
+        H[3] = __byte_perm(hi, 0, 0x4342);
+    }
+}
+
+__device__ __forceinline__ void window_x_b(uint32_t sn, int c, const LaneColsB& lc, bool gf, uint32_t (&Hm)[4],
+                                           uint32_t (&H0)[4], uint32_t (&X)[4]) {
+    uint32_t Hn[4];
+    s_row_pairs_b(sn, c, lc, gf, Hn);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        X[k] = gf ? Hm[k] + 2u * H0[k] + Hn[k] : H0[k] << 4;
+        Hm[k] = H0[k];
+        H0[k] = Hn[k];
+    }
+}
+
+// The batch producer: as tile_produce, over the images of the CTA's range,
+// with each image's planes, pitch and width (copies rounded up to 16 bytes,
+// which stay inside the pitched row).
+template <TmaMode MODE>
+__device__ __noinline__ void tile_produce_batch(const TileSmem<MODE>& L, const TileBatchArgs& A) {
+    constexpr int KS = TileSmem<MODE>::KS, KA = TileSmem<MODE>::KA;
+    constexpr uint32_t kEl = TileAux<MODE>::kElem;
+    BatchRange P = batch_range(A, kEl);
+    uint32_t si = 0, ai = 0;
+    RingPos<KS> sp{0u};
+    RingPos<KA> ap{0u};
+    bool ok = true;
+    while (ok && P.next(A, kEl)) {
+        const int64_t n = (int64_t)P.h * P.p;
+        const int xa = max(P.xs - 16, 0), xb = min(P.xs + kTileCols + 16, P.w);
+        const uint32_t s_bytes = (uint32_t)(((xb + 15) & ~15) - xa), s_off = (uint32_t)(xa - (P.xs - 16));
+        const uint32_t cols = (uint32_t)(((min(P.xs + kTileCols, P.w) - P.xs) + 15) & ~15);
+        for (int k = 0; k < P.rows + 2 && ok; ++k) {
+            {
+                if (si >= (uint32_t)KS) ok = mbar_wait(L.sempty(sp.slot()), sp.phase() ^ 1u, &g_slrme_status, A.max_spins);
+                if (!ok) break;
+                const int ys = min(max(P.y0 - 1 + k, 0), P.h - 1);
+                const uint32_t dst = L.sslot_at(sp.slot()) + s_off, bar = L.sfull(sp.slot());
+                const uint8_t* src = P.s3 + (int64_t)ys * P.p + xa;
+                fence_async_shared();
+                mbar_arrive_expect_tx(bar, 3u * s_bytes);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tma_load_1d(dst + (uint32_t)c * kTileSW, src + c * n, s_bytes, bar);
+                ++si;
+                sp.advance();
+            }
+            if (k >= 2) {
+                if (ai >= (uint32_t)KA) ok = mbar_wait(L.aempty(ap.slot()), ap.phase() ^ 1u, &g_slrme_status, A.max_spins);
+                if (!ok) break;
+                const int64_t row = (int64_t)(P.y0 + k - 2) * P.p + P.xs;
+                const uint32_t dst = L.aslot_at(ap.slot()), bar = L.afull(ap.slot());
+                fence_async_shared();
+                mbar_arrive_expect_tx(bar, (3u * kEl + 1u) * cols);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    tma_load_1d(dst + (uint32_t)c * TileAux<MODE>::kPlane, P.aux + (c * n + row) * kEl, kEl * cols,
+                                bar);
+                tma_load_1d(dst + TileAux<MODE>::kE, P.e + row, cols, bar);
+                ++ai;
+                ap.advance();
+            }
+        }
+    }
+    const int spins = ok ? A.max_spins : (1 << 10);
+    for (uint32_t k = si > (uint32_t)KS ? si - KS : 0; k < si; ++k)
+        mbar_wait(L.sfull(k % KS), (k / KS) & 1u, &g_slrme_status, spins);
+    for (uint32_t k = ai > (uint32_t)KA ? ai - KA : 0; k < ai; ++k)
+        mbar_wait(L.afull(k % KA), (k / KA) & 1u, &g_slrme_status, spins);
+}
+
+// Adds the CTA's shared bins to image `img`'s sums and clears them (consumer
+// threads; the caller brackets this with consumer barriers).
+__device__ __forceinline__ void bins_flush_consumers(SmemBins& bins, unsigned long long* __restrict__ g, bool add) {
+    for (int i = threadIdx.x; i < kNbin * kNsum; i += kTileWarps * 32) {
+        const unsigned long long v = ((unsigned long long)bins.hi[i] << 12) + bins.lo[i];
+        if (add && v) atomicAdd(g + i, v);
+        bins.lo[i] = bins.hi[i] = 0u;
+    }
+}
+
+// The fit over the batch.  The bins hold one image's sums of at most 256 rows
+// of 2048 pixels (2^19 pixels, the bins' bound) between flushes.
+__device__ __forceinline__ void fit_consume_batch(const TileSmem<TmaMode::kFit>& L, const TileBatchArgs& A,
+                                                  SmemBins& bins, uint32_t* queue, int* gave_up, int warp, int lane) {
+    TileConsumer<TmaMode::kFit> C{L, A.max_spins, {0u}, {0u}};
+    FitQueues fq;
+    fq.R = queue + warp * (kRunQ * kRunStride + kSegQ * kQueueStride);
+    fq.Q = fq.R + kRunQ * kRunStride;
+    fq.nr = fq.nq = 0;
+    Run2 all, odd;
+    BatchRange T = batch_range(A, 1u);
+    bool ok = true;
+    int cur = -1, since = 0;
+    auto flush = [&]() {
+        if (ok) {
+            drain_runs(fq, bins, lane);
+            drain_segs(fq, bins, lane);
+        }
+        consumers_sync();
+        bins_flush_consumers(bins, A.B.sums + (int64_t)cur * kNbin * kNsum, *gave_up == 0);
+        consumers_sync();
+    };
+    while (T.next(A, 1u)) {
+        if (T.img != cur || since + T.rows > kTaskRows) {
+            if (cur >= 0) flush();
+            cur = T.img;
+            since = 0;
+        }
+        since += T.rows;
+        if (!ok) continue;   // after a timeout: walk the tasks (and their barriers) without work
+        const LaneColsB lc(T.xs, T.w, warp, lane);
+        const bool gf = T.gf != 0;
+        run2_reset(all, -1);
+        run2_reset(odd, -1);
+        uint32_t Hm[3][4], H0[3][4];
+        ok = C.wait_s();
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_row_pairs_b(C.s_addr(), c, lc, gf, Hm[c]);
+            C.release_s(lane);
+            ok = C.wait_s();
+        }
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_row_pairs_b(C.s_addr(), c, lc, gf, H0[c]);
+            C.release_s(lane);
+        }
+        for (int j = 0; j < T.rows && ok; ++j) {
+            ok = C.wait_s() && C.wait_a();
+            if (!ok) break;
+            const uint32_t sn = C.s_addr();
+            const uint32_t as = C.a_addr() + kStripCols * warp + 8 * lane;
+            const uint2 ev = lds64(as + TileAux<TmaMode::kFit>::kE);
+            const uint32_t elo = ev.x, ehi = ev.y;
+            const uint32_t E1 = elo & 255u;
+            const bool uni = elo == ehi && elo == E1 * 0x01010101u;
+            if (__all_sync(0xffffffffu, (uni && lc.full) || !lc.inside)) {
+                // fast path: every segment of the warp is whole and in one region
+                const bool isodd = (E1 & 1u) != 0u;
+                runs_rekey(fq, all, odd, lc.inside && !isodd, (int)E1, lc.inside && isodd, (int)E1, bins, lane);
+                const uint32_t mo = lc.inside && isodd ? 0xFFFFFFFFu : 0u;
+                const uint32_t nadd = lc.inside ? 8u : 0u;
+                all.n += nadd;
+                odd.n += nadd & mo;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x_b(sn, c, lc, gf, Hm[c], H0[c], X);
+                    const uint2 mv = lds64(as + (uint32_t)c * TileAux<TmaMode::kFit>::kPlane);
+                    if (lc.inside) {
+                        uint32_t sx = 0u, sy = 0u, sxy = 0u, sxl = 0u, sxh = 0u;
+                        seg_accum5(X, mv.x, mv.y, sx, sy, sxy, sxl, sxh);
+                        all.sx[c] += sx;
+                        all.sy[c] += sy;
+                        all.sxy[c] += sxy;
+                        all.sxl[c] += sxl;
+                        all.sxh[c] += sxh;
+                        odd.sx[c] += sx & mo;
+                        odd.sy[c] += sy & mo;
+                        odd.sxy[c] += sxy & mo;
+                        odd.sxl[c] += sxl & mo;
+                        odd.sxh[c] += sxh & mo;
+                    }
+                }
+                C.release_s(lane);
+                C.release_a(lane);
+                continue;
+            }
+            const uint32_t olo = (elo & 0x01010101u) * 0xFFu, ohi = (ehi & 0x01010101u) * 0xFFu;
+            uint32_t eo = (elo & olo) | (ehi & ohi), ee = (elo & ~olo) | (ehi & ~ohi);
+            eo |= eo >> 16;
+            ee |= ee >> 16;
+            const uint32_t Eo = (eo | (eo >> 8)) & 255u, Ee = (ee | (ee >> 8)) & 255u;
+            const uint32_t Eo4 = Eo * 0x01010101u, Ee4 = Ee * 0x01010101u;
+            const bool two = ((((elo ^ Eo4) & olo) | ((ehi ^ Eo4) & ohi) | ((elo ^ Ee4) & ~olo) |
+                               ((ehi ^ Ee4) & ~ohi)) == 0u);
+            // lanes cut by the image's right edge go to the per-pixel queue
+            const bool slow = lc.inside && (!two || !lc.full);
+            const bool take = lc.inside && two && lc.full;
+            const uint32_t po_n = take ? (uint32_t)(__popc(olo) + __popc(ohi)) >> 3 : 0u;
+            runs_rekey(fq, all, odd, take && po_n != 8u, (int)Ee, po_n != 0u, (int)Eo, bins, lane);
+            const unsigned want = __ballot_sync(0xffffffffu, slow);
+            uint32_t qe = 0u;
+            if (want) {
+                if (fq.nq + __popc(want) > kSegQ) drain_segs(fq, bins, lane);
+                qe = (uint32_t)(fq.nq + __popc(want & ((1u << lane) - 1u))) * kQueueStride;
+            }
+            uint32_t k16[4];
+            mask16(olo, ohi, k16);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint32_t X[4];
+                window_x_b(sn, c, lc, gf, Hm[c], H0[c], X);
+                const uint2 mv = lds64(as + (uint32_t)c * TileAux<TmaMode::kFit>::kPlane);
+                if (take) {
+                    uint32_t xo[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xo[k] = X[k] & k16[k];
+                    seg_accum(xo, mv.x & olo, mv.y & ohi, odd, c);
+                    seg_accum(X, mv.x, mv.y, all, c);
+                }
+                if (want) {
+                    if (slow) {
+                        uint32_t* q = fq.Q + qe;
+                        q[2 + c] = mv.x;
+                        q[5 + c] = mv.y;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) q[8 + 4 * c + k] = X[k];
+                    }
+                }
+            }
+            odd.n += po_n;
+            all.n += take ? 8u : 0u;
+            if (want) {
+                if (slow) {
+                    uint32_t* q = fq.Q + qe;
+                    q[0] = elo;
+                    q[1] = ehi;
+                    q[20] = (uint32_t)lc.k;
+                }
+                __syncwarp();
+                fq.nq += __popc(want);
+            }
+            C.release_s(lane);
+            C.release_a(lane);
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(gave_up, 1);
+            continue;
+        }
+        push_run<true>(fq, all.E >= 0 && all.n != odd.n, all, odd, bins, lane);
+        push_run<false>(fq, odd.E >= 0 && odd.n != 0u, all, odd, bins, lane);
+    }
+    if (cur >= 0) flush();
+}
+
+__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile_batch(const TileBatchArgs A) {
+    extern __shared__ __align__(128) char dyn[];
+    __shared__ int gave_up;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TileSmem<TmaMode::kFit> L = tile_smem<TmaMode::kFit>(dyn);
+    char* extra = dyn + (L.extra - smem_addr(dyn));
+    SmemBins& bins = *reinterpret_cast<SmemBins*>(extra);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(extra + sizeof(SmemBins));
+    tile_init_barriers(L);
+    if (threadIdx.x == 0) gave_up = 0;
+    __syncthreads();
+    if (warp == kTileWarps) {
+        if (lane == 0) tile_produce_batch(L, A);
+        return;
+    }
+    for (int i = threadIdx.x; i < (int)(sizeof(SmemBins) / 16); i += kTileWarps * 32)
+        reinterpret_cast<uint4*>(extra)[i] = make_uint4(0u, 0u, 0u, 0u);
+    consumers_sync();
+    fit_consume_batch(L, A, bins, queue, &gave_up, warp, lane);
+}
+
+// Residual / decoder over the batch: the parameters (and, for the residual,
+// the histograms) of the current image in shared memory, switched at image
+// changes behind consumer barriers.
+template <TmaMode MODE>
+__device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, const TileBatchArgs& A, float2* ab,
+                                                   uint32_t* hist, int warp, int lane) {
+    constexpr uint32_t kEl = TileAux<MODE>::kElem;
+    TileConsumer<MODE> C{L, A.max_spins, {0u}, {0u}};
+    BatchRange T = batch_range(A, kEl);
+    bool ok = true;
+    int cur = -1;
+    const bool with_hist = MODE == TmaMode::kResidual && A.hist != nullptr;
+    while (T.next(A, kEl)) {
+        if (T.img != cur) {
+            consumers_sync();
+            if (with_hist && cur >= 0)
+                for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32) {
+                    if (hist[i]) atomicAdd(A.hist + (int64_t)cur * 3 * kNres + i, hist[i]);
+                    hist[i] = 0u;
+                }
+            load_params_ab(A.params + T.img, ab, kTileWarps * 32);
+            consumers_sync();
+            cur = T.img;
+        }
+        if (!ok) continue;   // after a timeout: walk the tasks (and their barriers) without work
+        const LaneColsB lc(T.xs, T.w, warp, lane);
+        const bool gf = T.gf != 0;
+        const int64_t n = (int64_t)T.h * T.p;
+        uint32_t Hm[3][4], H0[3][4];
+        ok = C.wait_s();
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_row_pairs_b(C.s_addr(), c, lc, gf, Hm[c]);
+            C.release_s(lane);
+            ok = C.wait_s();
+        }
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_row_pairs_b(C.s_addr(), c, lc, gf, H0[c]);
+            C.release_s(lane);
+        }
+        for (int j = 0; j < T.rows && ok; ++j) {
+            ok = C.wait_s() && C.wait_a();
+            if (!ok) break;
+            const uint32_t sn = C.s_addr();
+            const uint32_t as = C.a_addr() + kStripCols * warp + 8 * lane;
+            const int64_t pix = (int64_t)(T.y0 + j) * T.p + lc.x0;
+            const uint2 ev = lds64(as + TileAux<MODE>::kE);
+            if constexpr (MODE == TmaMode::kResidual) {
+                int16_t* r3 = A.r3b + 3 * T.px;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x_b(sn, c, lc, gf, Hm[c], H0[c], X);
+                    const uint2 mv = lds64(as + (uint32_t)c * TileAux<MODE>::kPlane);
+                    int rr[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
+                        const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
+                        const float2 p = ab[c * kNbin + E];
+                        rr[i] = M - predict_biased(p.x, p.y, x_biased(X, i));
+                    }
+                    if (lc.full) {
+                        uint4 v;
+                        v.x = __byte_perm((uint32_t)rr[0], (uint32_t)rr[1], 0x5410);
+                        v.y = __byte_perm((uint32_t)rr[2], (uint32_t)rr[3], 0x5410);
+                        v.z = __byte_perm((uint32_t)rr[4], (uint32_t)rr[5], 0x5410);
+                        v.w = __byte_perm((uint32_t)rr[6], (uint32_t)rr[7], 0x5410);
+                        *reinterpret_cast<uint4*>(r3 + c * n + pix) = v;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (i < lc.k) r3[c * n + pix + i] = (int16_t)rr[i];
+                    }
+                    if (with_hist) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (i < lc.k) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
+                    }
+                }
+            } else {
+                uint32_t word[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) word[i] = __byte_perm(i < 4 ? ev.x : ev.y, 0u, 0x0444 | ((i & 3) << 12));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t X[4];
+                    window_x_b(sn, c, lc, gf, Hm[c], H0[c], X);
+                    const uint4 v = lds128(as + (uint32_t)c * TileAux<MODE>::kPlane + (kStripCols * warp + 8 * lane));
+                    const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                        const int E = (int)(word[i] >> 24);
+                        const float2 p = ab[c * kNbin + E];
+                        const int M = rv + predict_biased(p.x, p.y, x_biased(X, i));
+                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
+                    }
+                }
+                uint32_t* out = A.outb + T.px + pix;
+                if (lc.full) {
+                    uint4* o4 = reinterpret_cast<uint4*>(out);
+                    o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
+                    o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < lc.k) out[i] = word[i];
+                }
+            }
+            C.release_s(lane);
+            C.release_a(lane);
+        }
+    }
+    if (with_hist && cur >= 0) {
+        consumers_sync();
+        for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32)
+            if (hist[i]) atomicAdd(A.hist + (int64_t)cur * 3 * kNres + i, hist[i]);
+    }
+}
+
+template <TmaMode MODE>
+__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile_batch(const TileBatchArgs A) {
+    extern __shared__ __align__(128) char dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TileSmem<MODE> L = tile_smem<MODE>(dyn);
+    char* extra = dyn + (L.extra - smem_addr(dyn));
+    float2* ab = reinterpret_cast<float2*>(extra);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(ab + 3 * kNbin);
+    tile_init_barriers(L);
+    __syncthreads();
+    if (warp == kTileWarps) {
+        if (lane == 0) tile_produce_batch(L, A);
+        return;
+    }
+    if (MODE == TmaMode::kResidual && A.hist)
+        for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32) hist[i] = 0u;
+    rows_consume_batch<MODE>(L, A, ab, hist, warp, lane);
+}
+
 bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
     if (w % 16 != 0) return false;
     for (const void* p : ptrs)
@@ -1877,16 +2256,20 @@ int launch_fit_tile(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int 
     return cuda_status("slr_fit launch");
 }
 
-int strip_ctas(int64_t cta_tasks, int per_sm) {
-    const int64_t cap = (int64_t)geometry().sms * per_sm;
-    int64_t g = cta_tasks < cap ? cta_tasks : cap;
-    return (int)(g < 1 ? 1 : g);
-}
 
 struct StripLaunch {
     int rows;     // strip height
     int blocks;   // CTAs
 };
+
+
+// Grid of the batch row stages: per_sm CTAs per SM, at most one per 4 rows.
+int64_t batch_tile_grid(int64_t tile_rows, int per_sm) {
+    int64_t g = (tile_rows + 3) / 4;
+    const int64_t cap = (int64_t)geometry().sms * per_sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : g;
+}
 
 // Strip height: the tallest of 16, 8, 4 rows that still gives about 32 warps
 // of work per SM (short strips re-read two halo rows of S per strip).
@@ -1964,40 +2347,50 @@ int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r
 
 // ---------------------------------------------------------------- batch launchers
 
-int launch_fit_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3, const uint8_t* m3,
-                     const uint8_t* e, slrme_params* params, cudaStream_t s) {
+int launch_fit_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3, const uint8_t* e,
+                     slrme_params* params, cudaStream_t s) {
     if (cudaMemsetAsync(B.sums, 0, sizeof(unsigned long long) * kNbin * kNsum * (size_t)B.n, s) != cudaSuccess)
         return cuda_status("batch fit memset");
-    if (cta_tasks > 0) {
-        // each block adds at most kMaxBlockPixels pixels (a CTA task is kWarps strips)
-        const int64_t per = fit_strips_per_warp(B.strip_rows);
-        int64_t blocks = strip_ctas(cta_tasks, ctas_per_sm < 2 ? ctas_per_sm : 2);
-        if (blocks < (cta_tasks + per - 1) / per) blocks = (cta_tasks + per - 1) / per;
-        k_fit_batch<<<(unsigned)blocks, kThreads, 0, s>>>(B, cta_tasks, s3, m3, e);
-        const int st = cuda_status("batch fit launch");
+    if (tile_rows > 0) {
+        static bool attr_set[64];
+        int st = tile_smem_attr(k_fit_tile_batch, kTileFitSmem, attr_set);
+        if (st != SLRME_OK) return st;
+        TileBatchArgs A{B, s3, m3, e, tile_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr};
+        k_fit_tile_batch<<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kFit>::kCtas), kTileThreads, kTileFitSmem, s>>>(A);
+        st = cuda_status("batch fit launch");
         if (st != SLRME_OK) return st;
     }
     k_solve_batch<<<dim3(kSolveBlocks, B.n), 32, 0, s>>>(B.sums, params);
     return cuda_status("batch solve launch");
 }
 
-int launch_residual_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3,
-                          const uint8_t* m3, const uint8_t* e, const slrme_params* params, int16_t* r3,
-                          uint32_t* hist, cudaStream_t s) {
+int launch_residual_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3,
+                          const uint8_t* e, const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
     if (hist && cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 3 * kNres * (size_t)B.n, s) != cudaSuccess)
         return cuda_status("batch residual memset");
-    if (cta_tasks == 0) return SLRME_OK;
-    k_residual_batch<<<strip_ctas(cta_tasks, ctas_per_sm), kThreads, 0, s>>>(B, cta_tasks, s3, m3, e, params, r3,
-                                                                             hist);
+    if (tile_rows == 0) return SLRME_OK;
+    static bool attr_set[64];
+    constexpr size_t smem = tile_rows_smem<TmaMode::kResidual>();
+    int st = tile_smem_attr(k_rows_tile_batch<TmaMode::kResidual>, smem, attr_set);
+    if (st != SLRME_OK) return st;
+    TileBatchArgs A{B, s3, m3, e, tile_rows, kMaxSpins, params, r3, hist, nullptr};
+    k_rows_tile_batch<TmaMode::kResidual><<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kResidual>::kCtas), kTileThreads, smem, s>>>(A);
     return cuda_status("batch residual launch");
 }
 
-int launch_decode_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3, const uint8_t* e,
-                        const int16_t* r3, const slrme_params* params, uint32_t* out, cudaStream_t s) {
-    if (cta_tasks == 0) return SLRME_OK;
-    k_decode_batch<<<strip_ctas(cta_tasks, ctas_per_sm), kThreads, 0, s>>>(B, cta_tasks, s3, e, r3, params, out);
+int launch_decode_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* e, const int16_t* r3,
+                        const slrme_params* params, uint32_t* out, cudaStream_t s) {
+    if (tile_rows == 0) return SLRME_OK;
+    static bool attr_set[64];
+    constexpr size_t smem = tile_rows_smem<TmaMode::kDecode>();
+    int st = tile_smem_attr(k_rows_tile_batch<TmaMode::kDecode>, smem, attr_set);
+    if (st != SLRME_OK) return st;
+    TileBatchArgs A{B, s3, reinterpret_cast<const uint8_t*>(r3), e, tile_rows, kMaxSpins, params, nullptr, nullptr,
+                    out};
+    k_rows_tile_batch<TmaMode::kDecode><<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kDecode>::kCtas), kTileThreads, smem, s>>>(A);
     return cuda_status("batch decode launch");
 }
+
 
 }  // namespace slrme
 

@@ -36,6 +36,8 @@ struct BatchImage {
     int32_t quality;
     int32_t gf_on;
     int64_t px;
+    int32_t pitch;      // row pitch of every plane (w rounded up to 16)
+    int32_t reserved;
 };
 
 // Device views of a plan's workspace.  Prefix arrays have n + 1 entries:
@@ -45,11 +47,10 @@ struct BatchDev {
     const QuantTable* quant;         // per image
     const int64_t* split_prefix;     // chunks of 4096 words
     const int64_t* base_prefix;      // CTA tasks of 8 band tasks (8 rows x 32 columns each)
-    const int64_t* strip_prefix;     // CTA tasks of 8 strips (strip_rows x 256 columns each)
+    const int64_t* row_prefix;       // rows of 2048-column strips (strips x h per image)
     int64_t* lum_stats;              // [n][2]
     unsigned long long* sums;        // [n][256 * 13]
     int n;
-    int strip_rows;
 };
 
 // Image of task k by binary search over a prefix array (n is small).
@@ -64,19 +65,18 @@ __device__ __forceinline__ int batch_image_of(const int64_t* prefix, int n, int6
 }
 
 constexpr int kSplitChunk = 4096;   // words per split task
-constexpr int kStripColsBatch = 256;
+constexpr int kTileColsBatch = 2048;  // columns per strip of the row stages
 
 int launch_split_batch(const BatchDev& B, int64_t chunks, int ctas_per_sm, const uint32_t* rgbe, uint8_t* m3,
                        uint8_t* e, cudaStream_t s);
 int launch_base_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* m3, const uint8_t* e,
                       uint8_t* s3, cudaStream_t s);
-int launch_fit_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3, const uint8_t* m3,
-                     const uint8_t* e, slrme_params* params, cudaStream_t s);
-int launch_residual_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3,
-                          const uint8_t* m3, const uint8_t* e, const slrme_params* params, int16_t* r3,
-                          uint32_t* hist, cudaStream_t s);
-int launch_decode_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* s3, const uint8_t* e,
-                        const int16_t* r3, const slrme_params* params, uint32_t* out, cudaStream_t s);
+int launch_fit_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3, const uint8_t* e,
+                     slrme_params* params, cudaStream_t s);
+int launch_residual_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3,
+                          const uint8_t* e, const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s);
+int launch_decode_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* e, const int16_t* r3,
+                        const slrme_params* params, uint32_t* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- launch geometry
 struct Geometry {

@@ -161,8 +161,10 @@ __global__ void __launch_bounds__(kThreads) k_split_scalar(const uint32_t* __res
 }
 
 
-// Batch: one task per chunk of 4096 words of one image; a CTA works through a
-// contiguous range of chunks and adds each chunk's statistic to its image.
+// Batch: one task per chunk of 4096 words of one image's pitched plane (the
+// padding words are zero: no pixel, nothing added to the statistic); a CTA
+// works through a contiguous range of chunks and adds each chunk's statistic
+// to its image.
 __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int64_t chunks,
                                                           const uint32_t* __restrict__ rgbeb,
                                                           uint8_t* __restrict__ m3b, uint8_t* __restrict__ eb) {
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
     for (int64_t k = k0; k < k1; ++k) {
         const int i = batch_image_of(B.split_prefix, B.n, k);
         const BatchImage im = B.img[i];
-        const int64_t n = (int64_t)im.h * im.w;
+        const int64_t n = (int64_t)im.h * im.pitch;
         const int64_t w0 = (k - B.split_prefix[i]) * kSplitChunk, w1 = min(w0 + kSplitChunk, n);
         const uint32_t* rgbe = rgbeb + im.px;
         uint8_t* m3 = m3b + 3 * im.px;

@@ -63,7 +63,7 @@ def _call(name, *args):
 
 
 def _ptr(t):
-    return None if t is None else t.data_ptr()
+    return None if t is None else native._ptr(t)
 
 
 def _stream(stream=None):
@@ -242,7 +242,8 @@ def crop_table(bc, keys: Sequence[int], B: int, H: int, W: int, rng: np.random.G
         h, w = bc.size(i)
         if h < H or w < W:
             continue
-        rows.append((bc.offset(i), h, w, int(rng.integers(0, h - H + 1)), int(rng.integers(0, w - W + 1)),
+        # the crop table's third entry is the row pitch of the image's planes
+        rows.append((bc.offset(i), h, bc.pitch(i), int(rng.integers(0, h - H + 1)), int(rng.integers(0, w - W + 1)),
                      int(keys[i])))
     return np.asarray(rows, np.int64)
 

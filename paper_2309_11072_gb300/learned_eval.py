@@ -65,7 +65,7 @@ def _code_and_pick(timgs, first, quality, net_dev, Bm, Lr, torch, entropy_bits):
     tb.decode()
     tkeys = tb.keys()
     for i, img in enumerate(timgs):
-        L = tb.image_layers(i)
+        L = tb.dense_layers(i)
         h, w = img.shape
         r3 = torch.empty(3 * h * w, dtype=torch.int16, device=dev)
         hist = torch.empty(3 * 511, dtype=torch.int32, device=dev)

@@ -102,6 +102,8 @@ def _ptr(t) -> Optional[int]:
         return None
     if isinstance(t, int):
         return t
+    if not t.is_contiguous():
+        raise ValueError("the library takes dense planes: pass a contiguous tensor")
     return t.data_ptr()
 
 

@@ -115,12 +115,13 @@ def test_params_layout_roundtrip():
 def test_batch_struct_layouts_and_argument_checks():
     import ctypes as C
     from paper_2309_11072_gb300 import batch as B
-    assert C.sizeof(B.BatchImage) == 24 and C.sizeof(B.BatchTiles) == 20
-    assert C.sizeof(B.BatchPlan) == 88 and C.sizeof(B.BatchBuffers) == 64
+    # the sizes the library's static_asserts fix
+    assert C.sizeof(B.BatchImage) == 32 and C.sizeof(B.BatchTiles) == 8
+    assert C.sizeof(B.BatchPlan) == 72 and C.sizeof(B.BatchBuffers) == 64
     L = B._lib()
     assert L.slrme_batch_workspace_bytes(0) == 0
     assert L.slrme_batch_workspace_bytes(64) > 64 * 256 * 13 * 8
-    imgs = (B.BatchImage * 2)(B.BatchImage(8, 8, 90, 1, 0), B.BatchImage(8, 8, 0, 1, 0))   # quality 0
+    imgs = (B.BatchImage * 2)(B.BatchImage(8, 8, 90, 1, 0, 0, 0), B.BatchImage(8, 8, 0, 1, 0, 0, 0))   # quality 0
     plan = B.BatchPlan()
     assert L.slrme_batch_plan_init(C.addressof(plan), C.addressof(imgs), 2, 0x100000, None) == -1
     assert "quality" in native.last_error()

@@ -13,8 +13,11 @@ from paper_2309_11072_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(64, 96), (1, 1), (0, 17), (37, 300), (257, 129), (8, 8), (120, 264), (9, 17), (200, 331), (5, 1000)]
-QUALS = [90, 50, 75, 10, 85, 100, 60, 30, 95, 70]
+# widths on and off the 16-element row pitch; two images wider than one
+# 2048-column strip of the row stages, with a ragged last strip
+SIZES = [(64, 96), (1, 1), (0, 17), (37, 300), (257, 129), (8, 8), (120, 264), (9, 17), (200, 331), (5, 1000),
+         (19, 2050), (6, 4111)]
+QUALS = [90, 50, 75, 10, 85, 100, 60, 30, 95, 70, 80, 40]
 
 
 def _images(sizes, seed0=100):
@@ -79,9 +82,8 @@ def test_batch_results_do_not_depend_on_tiles():
     bc.encode()
     bc.decode()
     ref = _snapshot(bc)
-    for kw in (dict(strip_rows=4, fit_ctas_per_sm=1, res_ctas_per_sm=1, split_ctas_per_sm=1, base_ctas_per_sm=1),
-               dict(strip_rows=16, fit_ctas_per_sm=2, res_ctas_per_sm=2, split_ctas_per_sm=8, base_ctas_per_sm=3),
-               dict(strip_rows=8, fit_ctas_per_sm=1, res_ctas_per_sm=2, split_ctas_per_sm=2, base_ctas_per_sm=2)):
+    for kw in (dict(split_ctas_per_sm=1, base_ctas_per_sm=1), dict(split_ctas_per_sm=8, base_ctas_per_sm=3),
+               dict(split_ctas_per_sm=2, base_ctas_per_sm=2)):
         bc.set_tiles(**kw)
         for t in (bc.m3, bc.s3, bc.r3, bc.out):
             t.zero_()
@@ -98,7 +100,8 @@ def test_autotune_and_graph_replay_keep_results():
     bc.decode()
     ref = _snapshot(bc)
     tiles = bc.autotune(reps=2)
-    assert tiles["strip_rows"] in (4, 8, 16)
+    assert set(tiles) == {"split_ctas_per_sm", "base_ctas_per_sm"}
+    assert 1 <= tiles["split_ctas_per_sm"] <= 8 and 1 <= tiles["base_ctas_per_sm"] <= 3
     bc.encode()
     bc.decode()
     assert _same(_snapshot(bc), ref)
@@ -128,40 +131,41 @@ def _check_all(bc, imgs, quals, gf_on=True):
     """Every layer of every image against the oracle, bit for bit."""
     torch.cuda.synchronize()
     ref = _oracle_all(imgs, quals, gf_on)
-    m3, e, s3 = _host(bc.m3, np.uint8), _host(bc.e, np.uint8), _host(bc.s3, np.uint8)
-    r3, out, hist = _host(bc.r3, np.int16), _host(bc.out, np.uint32), _host(bc.hist, np.uint32)
     for i, (img, o) in enumerate(zip(imgs, ref)):
         h, w = img.shape
         p = bc.image_params(i)
         if o is None:
             assert p["n_used"] == 0, i
             continue
-        off, n = bc.offset(i), h * w
-        assert np.array_equal(m3[3 * off:3 * off + 3 * n].reshape(3, h, w), o["m3"]), i
-        assert np.array_equal(e[off:off + n].reshape(h, w), o["e"]), i
-        assert np.array_equal(s3[3 * off:3 * off + 3 * n].reshape(3, h, w), o["s3"]), i
+        L = bc.image_layers(i)
+        assert np.array_equal(_host(L["m3"], np.uint8).reshape(3, h, w), o["m3"]), i
+        assert np.array_equal(_host(L["e"], np.uint8).reshape(h, w), o["e"]), i
+        assert np.array_equal(_host(L["s3"], np.uint8).reshape(3, h, w), o["s3"]), i
         assert np.array_equal(p["a"].view(np.uint32), o["a"].view(np.uint32)), i
         assert np.array_equal(p["b"].view(np.uint32), o["b"].view(np.uint32)), i
         assert np.array_equal(p["n"], o["n"]) and p["n_used"] == o["n_used"], i
-        assert np.array_equal(r3[3 * off:3 * off + 3 * n].reshape(3, h, w), o["r3"]), i
-        assert np.array_equal(hist[i * 3 * 511:(i + 1) * 3 * 511].reshape(3, 511), o["hist"]), i
-        assert np.array_equal(out[off:off + n].reshape(h, w), img), i
+        assert np.array_equal(_host(L["r3"], np.int16).reshape(3, h, w), o["r3"]), i
+        assert np.array_equal(_host(L["hist"], np.uint32).reshape(3, 511), o["hist"]), i
+        assert np.array_equal(_host(L["out"], np.uint32).reshape(h, w), img), i
 
 
 def test_batch_ctas_that_cross_image_boundaries():
-    """200 small images of one CTA task each, at one CTA per SM: each CTA of
-    the fit, residual and decoder stages takes two or more consecutive
-    tasks, so its shared bins, parameters and histograms change image in
-    the middle of the launch.  Every image must still equal the oracle."""
+    """200 small images (1 to 128 rows): the row stages split the batch's
+    rows into one contiguous range per CTA (two CTAs per SM), about 40 rows
+    each, so most CTAs change image in the middle of the launch (flushing
+    their shared bins and histograms to one image and loading the next
+    one's parameters) and some cover several short images.  Every image
+    must still equal the oracle."""
     rng = np.random.default_rng(77)
     sizes = [(int(rng.integers(1, 129)), int(rng.integers(1, 257))) for _ in range(200)]
     quals = [int(q) for q in rng.choice([30, 50, 75, 90, 100], size=len(sizes))]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert len(sizes) > sms   # more one-task images than CTAs: some CTAs take two images
     imgs = _images(sizes, seed0=900)
     bc = B.BatchCodec(sizes, quals)
+    rows_per_cta = bc.plan.tile_rows / (2 * sms)
+    assert rows_per_cta < 64 and min(h for h, _ in sizes) < rows_per_cta / 4
     bc.load(imgs)
-    bc.set_tiles(strip_rows=16, fit_ctas_per_sm=1, res_ctas_per_sm=1, split_ctas_per_sm=1, base_ctas_per_sm=1)
+    bc.set_tiles(split_ctas_per_sm=1, base_ctas_per_sm=1)
     bc.encode()
     bc.decode()
     _check_all(bc, imgs, quals)

@@ -190,7 +190,7 @@ def test_learned_estimator_pick_is_lossless_and_never_worse():
     net = Lr.upload_net(Lr.export_int_net(tr.theta.cpu().numpy()))
     test_bc, test_imgs, test_keys = _coded_set(3, 160, 42000)
     for i, img in enumerate(test_imgs):
-        L = test_bc.image_layers(i)
+        L = test_bc.dense_layers(i)
         h, w = img.shape
         r3 = torch.empty(3 * h * w, dtype=torch.int16, device=DEV)
         hist = torch.empty(3 * 511, dtype=torch.int32, device=DEV)
@@ -215,7 +215,7 @@ def _shipped_gain(imgs, quality=90):
     keys = bc.keys()
     out_rates = []
     for i, img in enumerate(imgs):
-        L = bc.image_layers(i)
+        L = bc.dense_layers(i)
         h, w = img.shape
         r3 = torch.empty(3 * h * w, dtype=torch.int16, device=DEV)
         hist = torch.empty(3 * 511, dtype=torch.int32, device=DEV)
