@@ -5,7 +5,10 @@ residual_encode and residual_decode once to warm up, then once more (the
 launches to capture), and checks that the decoded words equal the input and
 that no kernel's bounded wait gave up.  It holds only the one codec's
 buffers on the device (about 0.7 GB at 7680x4320), so a profiler that saves
-and restores device memory between its passes stays quick.
+and restores device memory between its passes stays quick.  With
+`--workload batch64` it runs the batch form's encode and decode over the
+64-image uneven workload (about 3.8 GB of batch planes) twice instead, with
+the batch's default grid sizes.
 
     python -m paper_2309_11072_gb300.profile_calls --workload 8k
     ncu --set full --clock-control none -k regex:"k_fit_tile|k_rows_tile|k_base" -s 4 -c 4 \\
@@ -23,9 +26,11 @@ from . import codec, native, synth
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["8k", "2k"], default="8k")
+    ap.add_argument("--workload", choices=["8k", "2k", "batch64"], default="8k")
     ap.add_argument("--quality", type=int, default=90)
     args = ap.parse_args(argv)
+    if args.workload == "batch64":
+        return batch_main()
     wl = synth.workload_8k() if args.workload == "8k" else synth.workload_2k()
     (h, w), = wl.sizes
     img = synth.make_workload_images(wl)[0]
@@ -42,6 +47,22 @@ def main(argv=None):
     if not torch.equal(c.out, rgbe):
         raise SystemExit("decoded words differ from the input")
     print(f"ok {w}x{h} q{args.quality}")
+
+
+def batch_main():
+    from . import batch
+    wl = synth.workload_batch()
+    imgs = synth.make_workload_images(wl)
+    bc = batch.BatchCodec(wl.sizes, list(wl.qualities) * len(wl.sizes))
+    bc.load(imgs)
+    for _ in range(2):
+        bc.encode()
+        bc.decode()
+        native.check_device_status("profile_calls")
+    for i, img in enumerate(imgs):
+        if not np.array_equal(bc.image_layers(i)["out"].cpu().numpy().view(np.uint32), img):
+            raise SystemExit(f"image {i}: decoded words differ from the input")
+    print(f"ok {wl.name}: {len(imgs)} images")
 
 
 if __name__ == "__main__":
