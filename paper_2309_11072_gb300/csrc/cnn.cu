@@ -2,44 +2,50 @@
 //
 // Network (4 -> 16 -> 16 -> 16 -> 3, 3x3, zero padding, int8 weights and
 // activations, int32 accumulation, per-channel requantisation) as declared
-// in include/slrme.h.  One CTA computes a 16 x 32 output tile: the input tile
-// with a 4-pixel halo is staged in shared memory and the four layers run
-// back to back, each as an implicit GEMM (M = 16 pixels of a row, N = 8
-// output channels, K = 16 input channels per 3x3 tap) with ldmatrix and
-// mma.sync.m16n8k16.  int8 values are carried exactly in f16; products and
-// sums are integers below 2^24 (at most 144 * 127 * 127), so the f32
-// accumulator holds them exactly and the integer requantisation follows.
+// in include/slrme.h.  One CTA computes a 32 x 56 output tile: the input tile
+// with a 4-pixel halo (40 x 64) is staged in shared memory and the four
+// layers run back to back, each as an implicit GEMM on the int8 tensor path
+// (mma.sync.m16n8k32.s32.s8.s8.s32: M = 16 pixels, N = 8 output channels,
+// K = 32 = two 3x3 taps of 16 input channels, int32 accumulators).
 //
-// Shared activations: 32 bytes per pixel (16 f16 channels), the two 16-byte
-// halves swapped on every other group of 4 pixels so that both ldmatrix rows
-// and epilogue stores hit distinct banks.
-#include <cuda_fp16.h>
-
+// Shared activations: 16 bytes per pixel (16 int8 channels), every layer's
+// buffer with the same row pitch P = 64 pixels.  A layer's outputs are
+// computed over the flattened index o = r P + x of its output rows, 16 at a
+// time: the A rows of tap (dy, dx) are then the 16 consecutive input pixels
+// from o + dy P + dx, one ldmatrix row (16 bytes) each, so an ldmatrix.x4
+// loads two taps at once (lanes 0-15 one tap, 16-31 the other).  Columns x
+// at or past the layer's output width are computed and stored but never
+// read by a valid output of the next layer.
+//
+// Requantisation a' = clamp(floor((acc m + 2^(s-1)) / 2^s), 0, hi): the MMA
+// gives sum w a; (b m + 2^(s-1)) is a per-channel 64-bit constant, so the
+// product and both additions are one 32 x 32 -> 64-bit multiply-add.  When
+// m <= 2^(s+7) for every channel of the layer (|acc| < 2^24 then keeps the
+// quotient inside int32), the low word of the 64-bit shift is the quotient
+// and one min/max-with-zero instruction clamps it; otherwise the clamp
+// reads the whole 64-bit quotient.
 #include "slrme_internal.cuh"
 
 namespace slrme {
 namespace {
 
-constexpr int TH = 16, TW = 32;                 // output tile
-constexpr int H0 = TH + 8, W0 = TW + 8;         // input tile (halo 4)
-constexpr int H1 = TH + 6, W1 = TW + 6;
-constexpr int H2 = TH + 4, W2 = TW + 4;
-constexpr int H3 = TH + 2, W3 = TW + 2;
+constexpr int TH = 32, TW = 56;                 // output tile
+constexpr int P = TW + 8;                       // row pitch of every activation buffer (pixels)
+constexpr int H0 = TH + 8;                      // rows of the input tile (halo 4)
 constexpr int kThreadsC = 256, kWarpsC = 8;
-constexpr int kBufAPx = H0 * W0;                // holds the input and layer-2 activations
-constexpr int kBufBPx = H1 * W1;                // holds layer-1 and layer-3 activations
-constexpr int kSmemBytes = (kBufAPx + kBufBPx) * 32 + 3 * TH * TW + 3 * kNres * 4 + 2 * 3 * kNbin * 4;
+constexpr int kBufAPx = H0 * P + 2;             // the input and layer-2 activations (+2: flattened overreach)
+constexpr int kBufBPx = (H0 - 2) * P + 2;       // layer-1 and layer-3 activations
+constexpr int GH = TH + 2, GW = TW + 2;         // S with a one-pixel halo, edges replicated (the filter's input)
+constexpr size_t kOffB = (size_t)kBufAPx * 16;
+constexpr size_t kOffMh = kOffB + (size_t)kBufBPx * 16;
+constexpr size_t kOffHist = kOffMh + 3 * TH * TW;
+constexpr size_t kOffPa = kOffHist + 3 * kNres * 4;
+constexpr size_t kOffSg = kOffPa + 2 * 3 * kNbin * 4;
+constexpr int kSmemBytes = (int)(kOffSg + 3 * GH * GW);
+static_assert(kOffB % 16 == 0 && kOffPa % 4 == 0, "cnn shared layout");
+static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "two CNN CTAs per SM");
 
 enum Mode { kInfer = 0, kEncode = 1, kDecode = 2 };
-
-__device__ __forceinline__ uint32_t swz(int pix, int chunk) {   // byte offset of (pixel, 16-byte chunk)
-    return (uint32_t)(pix * 32 + ((chunk ^ ((pix >> 2) & 1)) << 4));
-}
-
-__device__ __forceinline__ uint32_t pack_h2(int lo, int hi) {
-    const __half2 h = __halves2half2(__int2half_rn(lo), __int2half_rn(hi));
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&a)[4]) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -47,12 +53,17 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&a)[4]) {
                  : "r"(addr));
 }
 
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+// D += A B, A 16 x 32 int8 (row), B 32 x 8 int8 (column), D 16 x 8 int32.
+__device__ __forceinline__ void mma_s8(int (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack4_s8(int a, int b, int c, int d) {
+    return ((uint32_t)a & 255u) | (((uint32_t)b & 255u) << 8) | (((uint32_t)c & 255u) << 16) | ((uint32_t)d << 24);
 }
 
 struct LayerRef {
@@ -62,83 +73,108 @@ struct LayerRef {
     int ci, co, shift, hi;
 };
 
-// One layer over the tile: input buffer HIN x WIN -> output HOUT x WOUT
-// (HOUT = HIN - 2).  `halo` is the output's halo around the 16 x 32 tile;
-// outputs outside the image are zero (the next layer's zero padding).  The
-// last layer writes its clamped values to `mh` (uint8 [3][TH][TW]).
-template <int HIN, int WIN, int NT, bool LAST>
+// One layer over the tile: input rows HIN (pitch P) -> output rows HOUT =
+// HIN - 2.  `halo` is the output's halo around the 32 x 56 tile; outputs
+// outside the image are zero (the next layer's zero padding).  The last
+// layer writes its clamped values to `mh` (uint8 [3][TH][TW]).
+template <int HIN, int NT, bool LAST>
 __device__ __forceinline__ void conv_layer(uint32_t in_s, char* out_b, uint8_t* mh, const LayerRef& L, int halo,
                                            int oy, int ox, int h, int w) {
-    constexpr int HOUT = HIN - 2, WOUT = WIN - 2;
-    constexpr int G = (WOUT + 15) / 16;
+    constexpr int HOUT = HIN - 2;
+    const int wout = P - 2 * (4 - halo);            // output width of this layer: 62, 60, 58, 56
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int q = lane & 3, r4 = lane >> 2;
-    // B fragments of all 9 taps: k = input channel, n = output channel
-    uint32_t bf[9][NT][2];
+    const int q = lane & 3, g = lane >> 2;
+    // B fragments of the five tap pairs (taps 2p, 2p + 1; tap 9 is zero):
+    // k = 16 * (tap - 2p) + input channel, n = output channel
+    uint32_t bf[5][NT][2];
 #pragma unroll
-    for (int t = 0; t < 9; ++t)
+    for (int pr = 0; pr < 5; ++pr)
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-            const int n = nt * 8 + r4;
-            int v[4];
+            const int n = nt * 8 + g;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ci = 2 * q + (j & 1) + 8 * (j >> 1);
-                v[j] = (n < L.co && ci < L.ci) ? (int)__ldg(L.w + (n * L.ci + ci) * 9 + t) : 0;
+            for (int half = 0; half < 2; ++half) {
+                const int t = 2 * pr + half;
+                int v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int ci = 4 * q + i;
+                    v[i] = (t < 9 && n < L.co && ci < L.ci) ? (int)__ldg(L.w + (n * L.ci + ci) * 9 + t) : 0;
+                }
+                bf[pr][nt][half] = pack4_s8(v[0], v[1], v[2], v[3]);
             }
-            bf[t][nt][0] = pack_h2(v[0], v[1]);
-            bf[t][nt][1] = pack_h2(v[2], v[3]);
         }
-    int bias[NT][2], mult[NT][2];
+    // per output channel (2q + j of n-tile nt): m and b m + 2^(s-1)
+    const int s = L.shift;
+    int mult[NT][2];
+    long long cst[NT][2];
+    bool narrow = true;
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int co = nt * 8 + 2 * q + j;
-            bias[nt][j] = co < L.co ? __ldg(L.b + co) : 0;
-            mult[nt][j] = co < L.co ? __ldg(L.m + co) : 0;
+            const int m = co < L.co ? __ldg(L.m + co) : 0;
+            const int b = co < L.co ? __ldg(L.b + co) : 0;
+            mult[nt][j] = m;
+            cst[nt][j] = (long long)b * m + (1ll << (s - 1));
+            narrow = narrow && (long long)m <= (1ll << (s + 7));
         }
-    const long long rnd = 1ll << (L.shift - 1);
-    for (int it = warp; it < HOUT * G; it += kWarpsC) {
-        const int r = it / G;
-        const int x0 = min((it % G) * 16, WOUT - 16);
-        float acc[NT][4];
+    narrow = __all_sync(0xffffffffu, narrow);
+    // this lane's A row offsets (pixels) for the five tap pairs
+    int off[5];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+    for (int pr = 0; pr < 5; ++pr) {
+        const int t = min(2 * pr + (lane >> 4), 8);
+        off[pr] = (lane & 15) + (t / 3) * P + t % 3;
+    }
+    for (int c = warp; c < HOUT * (P / 16); c += kWarpsC) {
+        const int o0 = 16 * c;
+        int acc[NT][4];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int pix = (r + t / 3) * WIN + x0 + t % 3 + (lane & 15);
+        for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0;
+#pragma unroll
+        for (int pr = 0; pr < 5; ++pr) {
             uint32_t a[4];
-            ldsm_x4(in_s + swz(pix, lane >> 4), a);
+            ldsm_x4(in_s + 16u * (uint32_t)(o0 + off[pr]), a);
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) mma16816(acc[nt], a, bf[t][nt][0], bf[t][nt][1]);
+            for (int nt = 0; nt < NT; ++nt) mma_s8(acc[nt], a, bf[pr][nt][0], bf[pr][nt][1]);
         }
-        // epilogue: rows r4 and r4 + 8 of the group, channels 2q, 2q + 1 of each n-tile
+        // epilogue: pixels o0 + g and o0 + g + 8, channels 2q, 2q + 1 of each n-tile
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int xo = x0 + r4 + 8 * half;
-            const int gy = oy - halo + r, gx = ox - halo + xo;
-            const bool inside = gy >= 0 && gy < h && gx >= 0 && gx < w;
+        for (int hf = 0; hf < 2; ++hf) {
+            const int o = o0 + g + 8 * hf;
+            const int r = o / P, x = o % P;
+            const int gy = oy - halo + r, gx = ox - halo + x;
+            const bool inside = x < wout && gy >= 0 && gy < h && gx >= 0 && gx < w;
+            int y[NT][2];
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                int y[2];
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const long long v = (long long)(__float2int_rn(acc[nt][2 * half + j]) + bias[nt][j]);
-                    long long z = (v * mult[nt][j] + rnd) >> L.shift;
-                    z = z < 0 ? 0 : (z > L.hi ? L.hi : z);
-                    y[j] = inside ? (int)z : 0;
+                    const long long pv = (long long)acc[nt][2 * hf + j] * mult[nt][j] + cst[nt][j];
+                    int z;
+                    if (narrow) {
+                        z = __vimin_s32_relu((int)(pv >> s), L.hi);
+                    } else {
+                        const long long zz = pv >> s;
+                        z = zz < 0 ? 0 : (zz > L.hi ? L.hi : (int)zz);
+                    }
+                    y[nt][j] = inside ? z : 0;
                 }
-                if (LAST) {
+            if (LAST) {
+                if (x < TW && r < TH) {
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
-                        const int co = nt * 8 + 2 * q + j;
-                        if (co < 3) mh[(co * TH + r) * TW + xo] = (uint8_t)y[j];
+                        const int co = 2 * q + j;
+                        if (co < 3) mh[(co * TH + r) * TW + x] = (uint8_t)y[0][j];
                     }
-                } else {
-                    const int pix = r * WOUT + xo;
-                    *reinterpret_cast<uint32_t*>(out_b + swz(pix, nt) + 4 * q) = pack_h2(y[0], y[1]);
                 }
+            } else {
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+                    *reinterpret_cast<uint16_t*>(out_b + 16 * o + 8 * nt + 2 * q) =
+                        (uint16_t)((y[nt][0] & 255) | (y[nt][1] << 8));
             }
         }
     }
@@ -158,34 +194,31 @@ struct CnnArgs {
     int h, w, J, mode, gf_on;
 };
 
-// x = 16 S* (3x3 binomial, edge replicated) or 16 S at one pixel of one plane.
-__device__ __forceinline__ int gf_at(const uint8_t* __restrict__ S, int h, int w, int y, int x, bool gf) {
-    if (!gf) return 16 * (int)S[(int64_t)y * w + x];
-    int acc = 0;
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = min(max(y + dy, 0), h - 1);
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int xx = min(max(x + dx, 0), w - 1);
-            acc += (2 - (dy != 0)) * (2 - (dx != 0)) * (int)S[(int64_t)yy * w + xx];
-        }
-    }
-    return acc;
+// x = 16 S* (3x3 binomial, edge replicated) or 16 S at tile pixel (r, c) of
+// one plane of the staged S (rows and columns with a one-pixel halo).
+__device__ __forceinline__ int gf_tile(const uint8_t* Sg, int r, int c, bool gf) {
+    const uint8_t* p = Sg + (r + 1) * GW + (c + 1);
+    if (!gf) return 16 * (int)p[0];
+    const int a = p[-GW - 1] + 2 * p[-GW] + p[-GW + 1];
+    const int b = p[-1] + 2 * p[0] + p[1];
+    const int d = p[GW - 1] + 2 * p[GW] + p[GW + 1];
+    return a + 2 * b + d;
 }
 
 __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
     extern __shared__ __align__(128) char smem[];
     char* bufA = smem;
-    char* bufB = smem + kBufAPx * 32;
-    uint8_t* mh = reinterpret_cast<uint8_t*>(bufB + kBufBPx * 32);
-    uint32_t* hist = reinterpret_cast<uint32_t*>(mh + 3 * TH * TW);
-    float* pa = reinterpret_cast<float*>(hist + 3 * kNres);      // regression slopes [3][256]
+    char* bufB = smem + kOffB;
+    uint8_t* mh = reinterpret_cast<uint8_t*>(smem + kOffMh);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + kOffHist);
+    float* pa = reinterpret_cast<float*>(smem + kOffPa);         // regression slopes [3][256]
     float* pb = pa + 3 * kNbin;                                   // intercepts [3][256]
+    uint8_t* Sg = reinterpret_cast<uint8_t*>(smem + kOffSg);     // [3][GH][GW]
     const uint32_t sA = (uint32_t)__cvta_generic_to_shared(bufA), sB = (uint32_t)__cvta_generic_to_shared(bufB);
     const int h = A.h, w = A.w;
     const int64_t n = (int64_t)h * w;
     const bool want_hist = A.mode == kEncode && A.hist;
+    const bool gf = A.gf_on != 0;
     if (want_hist)
         for (int i = threadIdx.x; i < 3 * kNres; i += kThreadsC) hist[i] = 0u;
     if (A.mode != kInfer)
@@ -205,61 +238,67 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int oy = (int)(tile / tiles_x) * TH, ox = (int)(tile % tiles_x) * TW;
         __syncthreads();   // the previous tile's readers are done with the buffers
-        // input tile: S - 128 and the key-relative exponent; zero outside the image
-        for (int p = threadIdx.x; p < kBufAPx; p += kThreadsC) {
-            const int gy = oy - 4 + p / W0, gx = ox - 4 + p % W0;
-            uint4 lo = make_uint4(0u, 0u, 0u, 0u);
+        // input tile: (S - 128, key-relative exponent, 0 ...) per pixel; zero outside the image
+        for (int p = threadIdx.x; p < H0 * P; p += kThreadsC) {
+            const int gy = oy - 4 + p / P, gx = ox - 4 + p % P;
+            uint32_t v = 0u;
             if (gy >= 0 && gy < h && gx >= 0 && gx < w) {
                 const int64_t o = (int64_t)gy * w + gx;
                 int d = (int)A.e[o] - 137 - A.J;
                 d = d < -128 ? -128 : (d > 127 ? 127 : d);
-                lo.x = pack_h2((int)A.s3[o] - 128, (int)A.s3[n + o] - 128);
-                lo.y = pack_h2((int)A.s3[2 * n + o] - 128, d);
+                v = pack4_s8((int)A.s3[o] - 128, (int)A.s3[n + o] - 128, (int)A.s3[2 * n + o] - 128, d);
             }
-            *reinterpret_cast<uint4*>(bufA + swz(p, 0)) = lo;
-            *reinterpret_cast<uint4*>(bufA + swz(p, 1)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(bufA + 16 * p) = make_uint4(v, 0u, 0u, 0u);
         }
+        // S around the tile for the restoration filter (edges replicated)
+        if (A.mode != kInfer)
+            for (int p = threadIdx.x; p < GH * GW; p += kThreadsC) {
+                const int gy = min(max(oy - 1 + p / GW, 0), h - 1), gx = min(max(ox - 1 + p % GW, 0), w - 1);
+                const int64_t o = (int64_t)gy * w + gx;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Sg[c * GH * GW + p] = A.s3[c * n + o];
+            }
         __syncthreads();
-        conv_layer<H0, W0, 2, false>(sA, bufB, nullptr, L1, 3, oy, ox, h, w);
+        conv_layer<H0, 2, false>(sA, bufB, nullptr, L1, 3, oy, ox, h, w);
         __syncthreads();
-        conv_layer<H1, W1, 2, false>(sB, bufA, nullptr, L2, 2, oy, ox, h, w);
+        conv_layer<H0 - 2, 2, false>(sB, bufA, nullptr, L2, 2, oy, ox, h, w);
         __syncthreads();
-        conv_layer<H2, W2, 2, false>(sA, bufB, nullptr, L3, 1, oy, ox, h, w);
+        conv_layer<H0 - 4, 2, false>(sA, bufB, nullptr, L3, 1, oy, ox, h, w);
         __syncthreads();
-        conv_layer<H3, W3, 1, true>(sB, nullptr, mh, L4, 0, oy, ox, h, w);
+        conv_layer<H0 - 6, 1, true>(sB, nullptr, mh, L4, 0, oy, ox, h, w);
         __syncthreads();
         // outputs of the tile, one pixel per thread per step
         for (int p = threadIdx.x; p < TH * TW; p += kThreadsC) {
-            const int gy = oy + p / TW, gx = ox + p % TW;
+            const int r = p / TW, c = p % TW;
+            const int gy = oy + r, gx = ox + c;
             if (gy >= h || gx >= w) continue;
             const int64_t o = (int64_t)gy * w + gx;
             int y3[3] = {mh[p], mh[TH * TW + p], mh[2 * TH * TW + p]};
             if (A.mode == kInfer) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) A.mhat3[c * n + o] = (uint8_t)y3[c];
+                for (int ch = 0; ch < 3; ++ch) A.mhat3[ch * n + o] = (uint8_t)y3[ch];
                 continue;
             }
             // refined estimate: M^ = clamp(M* + y - 128, 0, 255), M* from Eq. (8)
             const int E = A.e[o];
             int mhat[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int ms = predict(pa[c * kNbin + E], pb[c * kNbin + E], gf_at(A.s3 + c * n, h, w, gy, gx,
-                                                                                    A.gf_on != 0));
-                const int v = ms + y3[c] - 128;
-                mhat[c] = v < 0 ? 0 : (v > 255 ? 255 : v);
+            for (int ch = 0; ch < 3; ++ch) {
+                const int ms = predict(pa[ch * kNbin + E], pb[ch * kNbin + E], gf_tile(Sg + ch * GH * GW, r, c, gf));
+                const int v = ms + y3[ch] - 128;
+                mhat[ch] = v < 0 ? 0 : (v > 255 ? 255 : v);
             }
             if (A.mode == kEncode) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const int r = (int)A.m3[c * n + o] - mhat[c];
-                    A.r3_out[c * n + o] = (int16_t)r;
-                    if (want_hist) atomicAdd(&hist[c * kNres + r + 255], 1u);
+                for (int ch = 0; ch < 3; ++ch) {
+                    const int rr = (int)A.m3[ch * n + o] - mhat[ch];
+                    A.r3_out[ch * n + o] = (int16_t)rr;
+                    if (want_hist) atomicAdd(&hist[ch * kNres + rr + 255], 1u);
                 }
             } else {
                 uint32_t wd = (uint32_t)E << 24;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) wd |= ((uint32_t)((int)A.r3[c * n + o] + mhat[c]) & 255u) << (8 * c);
+                for (int ch = 0; ch < 3; ++ch) wd |= ((uint32_t)((int)A.r3[ch * n + o] + mhat[ch]) & 255u) << (8 * ch);
                 A.rgbe_out[o] = wd;
             }
         }

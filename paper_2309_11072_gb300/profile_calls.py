@@ -8,7 +8,9 @@ buffers on the device (about 0.7 GB at 7680x4320), so a profiler that saves
 and restores device memory between its passes stays quick.  With
 `--workload batch64` it runs the batch form's encode and decode over the
 64-image uneven workload (about 3.8 GB of batch planes) twice instead, with
-the batch's default grid sizes.
+the batch's default grid sizes.  With `--call cnn` it codes the image, then
+runs the learned estimator's cnn_residual_encode twice with the shipped
+network and its decoder once, and checks that decoding is lossless.
 
     python -m paper_2309_11072_gb300.profile_calls --workload 8k
     ncu --set full --clock-control none -k regex:"k_fit_tile|k_rows_tile|k_base" -s 4 -c 4 \\
@@ -28,6 +30,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["8k", "2k", "batch64"], default="8k")
     ap.add_argument("--quality", type=int, default=90)
+    ap.add_argument("--call", choices=["coder", "cnn"], default="coder")
     args = ap.parse_args(argv)
     if args.workload == "batch64":
         return batch_main()
@@ -46,7 +49,20 @@ def main(argv=None):
         c.check()
     if not torch.equal(c.out, rgbe):
         raise SystemExit("decoded words differ from the input")
-    print(f"ok {w}x{h} q{args.quality}")
+    if args.call == "cnn":
+        from . import learned as Lr
+        net = Lr.upload_net(Lr.load_net(Lr.default_weights()))
+        J = native.rgbe_key_scale(c.stats.cpu().numpy())[0]
+        r3 = torch.empty_like(c.r3)
+        hist = torch.empty_like(c.hist)
+        for _ in range(2):
+            Lr.cnn_residual_encode(c.s3, c.m3, c.e, h, w, J, net, c.params, 1, r3, hist, st)
+        c.out.zero_()
+        Lr.cnn_residual_decode(c.s3, c.e, r3, h, w, J, net, c.params, 1, c.out, st)
+        c.check()
+        if not torch.equal(c.out, rgbe):
+            raise SystemExit("the learned estimator's decode differs from the input")
+    print(f"ok {w}x{h} q{args.quality} {args.call}")
 
 
 def batch_main():
