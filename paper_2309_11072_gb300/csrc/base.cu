@@ -81,14 +81,15 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8], int r) {
 // threshold table (v >= 0).  The float bits of v pick a bucket (exponent and
 // top 7 mantissa bits over [2^-20, 1), plus one bucket below and one above;
 // the clamp to those is one min-then-max-with-zero instruction); a bucket
-// holds at most one threshold, and its word is the count below the bucket
-// plus, from bit 8, the low 16 bits of that threshold (0x10000 when there is
-// none), so the count is one lookup and one integer comparison (positive
-// floats order like their bits).  No branch.
+// holds at most one threshold, and its word is (count below the bucket) *
+// 2^16 + 2^16 - t, t the low 16 bits of that threshold (2^16 when there is
+// none), so adding the low 16 bits of v's bits carries into bit 16 exactly
+// when they reach t (positive floats order like their bits): the count is
+// one lookup, one addition and one shift.  No branch.
 __device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {   // code = table + 1
     const int bits = __float_as_int(v);
     const uint32_t e = code[__vimin_s32_relu(((bits - 0x35800000) >> 16) + 1, 2561) - 1];   // `code` points at bucket 0
-    return (int)(e & 255u) + ((uint32_t)(bits & 0xFFFF) >= (e >> 8) ? 1 : 0);
+    return (int)((__byte_perm((uint32_t)bits, 0u, 0x4410) + e) >> 16);
 }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
@@ -124,12 +125,9 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ plane, int h, 
     }
 }
 
-__device__ __forceinline__ void unpack8(const uint2 v, uint8_t (&out)[8]) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        out[i] = (uint8_t)byte_of(v.x, i);
-        out[4 + i] = (uint8_t)byte_of(v.y, i);
-    }
+__device__ __forceinline__ uint2 pack8(const uint8_t (&b)[8]) {
+    return make_uint2((uint32_t)b[0] | ((uint32_t)b[1] << 8) | ((uint32_t)b[2] << 16) | ((uint32_t)b[3] << 24),
+                      (uint32_t)b[4] | ((uint32_t)b[5] << 8) | ((uint32_t)b[6] << 16) | ((uint32_t)b[7] << 24));
 }
 
 __device__ __forceinline__ void store8(uint8_t* __restrict__ plane, int h, int w, int y, int x0, bool fast,
@@ -183,6 +181,26 @@ __device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, 
     b = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb + 1)), gcode + 1);
 }
 
+// The same operator from the biased words 0x4B000000 | m of the three
+// mantissas (one byte permute each from the packed planes): Y from the
+// biased words with the bias folded into the constant (exact mod 2^32; Y is
+// small), and float(2 m + 1) = 2 (2^23 + m) + 1 - 2^24 by one exact FMA.
+__device__ __forceinline__ void tmo_pixel_biased(uint32_t br, uint32_t bg, uint32_t bb, int E, int J, float kr,
+                                                 float wr, const uint32_t* gcode, int& r, int& g, int& b) {
+    const uint32_t yq = 4252u * br + 14304u * bg + 1444u * bb + (10000u - 20000u * 0x4B000000u);
+    int d = E - 137 - J;
+    d = d < -100 ? -100 : (d > 100 ? 100 : d);
+    const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
+    const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float((int)yq)), p2d);
+    const float den = __fadd_rn(1.0f, L);
+    const float num = E == 0 ? 0.0f : __fmul_rn(wr, p2d);
+    const float H = __fdiv_rn(num, den);
+    constexpr float kOdd = 1.0f - 16777216.0f;
+    r = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(br), 2.0f, kOdd)), gcode + 1);
+    g = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(bg), 2.0f, kOdd)), gcode + 1);
+    b = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(bb), 2.0f, kOdd)), gcode + 1);
+}
+
 // Key and quantiser state of one image, as a lane needs it.
 struct BaseKey {
     int J;
@@ -225,24 +243,39 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
     const int y = y0 + sub;                      // this lane's row in phases 1 and 3
     // ---------------- phase 1: tone map and forward DCT along x
     {
-        uint8_t mr[8], mg[8], mb[8], ee[8];
+        uint2 wr8, wg8, wb8, we8;   // the lane's 8 pixels of each plane, packed
         if (pre) {
             // the band's bytes, copied to shared memory while the previous band was processed
-            unpack8(pre[0], mr);
-            unpack8(pre[32], mg);
-            unpack8(pre[64], mb);
-            unpack8(pre[96], ee);
+            wr8 = pre[0];
+            wg8 = pre[32];
+            wb8 = pre[64];
+            we8 = pre[96];
         } else {
             // rows past the bottom and columns past the right edge replicate the last row/column
+            uint8_t mr[8], mg[8], mb[8], ee[8];
             load8(m3, h, w, y, x0, fast, mr, p);
             load8(m3 + n, h, w, y, x0, fast, mg, p);
             load8(m3 + 2 * n, h, w, y, x0, fast, mb, p);
             load8(e, h, w, y, x0, fast, ee, p);
+            wr8 = pack8(mr);
+            wg8 = pack8(mg);
+            wb8 = pack8(mb);
+            we8 = pack8(ee);
         }
         int sdr[3][8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            tmo_pixel<kWhite>(mr[i], mg[i], mb[i], ee[i], J, kr, wr, gcode, sdr[0][i], sdr[1][i], sdr[2][i], lw2);
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t sel = 0x7540u | (uint32_t)(i & 3);   // byte i & 3 under the 0x4B000000 bias
+            const uint32_t br = __byte_perm(i < 4 ? wr8.x : wr8.y, 0x4B000000u, sel);
+            const uint32_t bg = __byte_perm(i < 4 ? wg8.x : wg8.y, 0x4B000000u, sel);
+            const uint32_t bb = __byte_perm(i < 4 ? wb8.x : wb8.y, 0x4B000000u, sel);
+            const int E = (int)byte_of(i < 4 ? we8.x : we8.y, i & 3);
+            if (kWhite)
+                tmo_pixel<true>((int)(br & 255u), (int)(bg & 255u), (int)(bb & 255u), E, J, kr, wr, gcode, sdr[0][i],
+                                sdr[1][i], sdr[2][i], lw2);
+            else
+                tmo_pixel_biased(br, bg, bb, E, J, kr, wr, gcode, sdr[0][i], sdr[1][i], sdr[2][i]);
+        }
         if (sdr3 && x0 < w) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -311,7 +344,7 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
         idct8(G, X, (1 << 14) + (128 << 15));
         uint32_t q[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) q[i] = (uint32_t)min(max(X[i] >> 15, 0), 255);
+        for (int i = 0; i < 8; ++i) q[i] = (uint32_t)__vimin_s32_relu(X[i] >> 15, 255);
         const uint32_t lo = __byte_perm(__byte_perm(q[0], q[1], 0x0040), __byte_perm(q[2], q[3], 0x0040), 0x5410);
         const uint32_t hi = __byte_perm(__byte_perm(q[4], q[5], 0x0040), __byte_perm(q[6], q[7], 0x0040), 0x5410);
         if (x0 < w) store8(s3 + c * n, h, w, y, x0, fast, lo, hi, p);

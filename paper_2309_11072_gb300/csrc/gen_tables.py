@@ -17,11 +17,12 @@ Tables (all built in float64 and rounded once):
                   2561: bucket i - 1 (biased exponent e in 107..126 and top 7
                   mantissa bits) for i = 1 .. 2560, i = 0 for v < 2^-20 and
                   i = 2561 for v >= 1; no such bucket holds more than one
-                  threshold either, and the word is start | (t << 8) with
-                  start the count of thresholds below the bucket and t the low
-                  16 bits of the one threshold inside it, or 0x10000 (no
-                  16-bit value reaches it) when there is none, so the code of
-                  v is start + ((bits(v) & 0xFFFF) >= t).
+                  threshold either, and the word is (start << 16) + 0x10000 - t
+                  with start the count of thresholds below the bucket and t the
+                  low 16 bits of the one threshold inside it, or 0x10000 (no
+                  16-bit value reaches it) when there is none; since
+                  (bits(v) & 0xFFFF) + 0x10000 - t < 0x20000, the code of v is
+                  ((bits(v) & 0xFFFF) + word) >> 16 = start + ((bits(v) & 0xFFFF) >= t).
 The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
 
@@ -59,15 +60,18 @@ def main():
         assert len(inside) <= 1 and (k == 255 or k + 2 > 255 or gamma[k + 2] >= hi), b
         start.append(k)
     wr = [f32_bits(1800.0 * 2.0 ** (-r / 16.0)) for r in range(16)]
-    code = [0 | (0x10000 << 8)]
+    def word(start, t):
+        return (start << 16) + 0x10000 - t
+
+    code = [word(0, 0x10000)]
     for b in range(20 * 128):
         lo = (107 << 23) + (b << 16)
         hi = lo + (1 << 16)
         k = sum(1 for t in gamma[1:] if t < lo)
         inside = [t for t in gamma[1:] if lo <= t < hi]
         assert len(inside) <= 1, b
-        code.append(k | ((inside[0] & 0xFFFF) if inside else 0x10000) << 8)
-    code.append(255 | (0x10000 << 8))
+        code.append(word(k, (inside[0] & 0xFFFF) if inside else 0x10000))
+    code.append(word(255, 0x10000))
     def arr(ctype, name, vals, fmt, per_line):
         lines = []
         for i in range(0, len(vals), per_line):

@@ -1597,9 +1597,10 @@ __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const Tile
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
-                        const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
+                        // 0x4B000000 | M: the estimate's bias cancels in the difference
+                        const int Mb = (int)__byte_perm(i < 4 ? mv.x : mv.y, 0x4B000000u, 0x7540u | (uint32_t)(i & 3));
                         const float2 p = ab[c * kNbin + E];
-                        rr[i] = M - predict_biased(p.x, p.y, x_biased(X, i));
+                        rr[i] = Mb - predict_bits(p.x, p.y, x_biased(X, i));
                     }
                     if (lc.inside) {
                         uint4 v;
@@ -1630,7 +1631,8 @@ __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const Tile
                         const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
                         const int E = (int)(word[i] >> 24);
                         const float2 p = ab[c * kNbin + E];
-                        const int M = rv + predict_biased(p.x, p.y, x_biased(X, i));
+                        // the low byte of R + (0x4B000000 + M*) is M
+                        const int M = rv + predict_bits(p.x, p.y, x_biased(X, i));
                         word[i] |= ((uint32_t)M & 255u) << (8 * c);
                     }
                 }
@@ -2113,9 +2115,10 @@ __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, cons
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
-                        const int M = (int)byte_of(i < 4 ? mv.x : mv.y, i & 3);
+                        // 0x4B000000 | M: the estimate's bias cancels in the difference
+                        const int Mb = (int)__byte_perm(i < 4 ? mv.x : mv.y, 0x4B000000u, 0x7540u | (uint32_t)(i & 3));
                         const float2 p = ab[c * kNbin + E];
-                        rr[i] = M - predict_biased(p.x, p.y, x_biased(X, i));
+                        rr[i] = Mb - predict_bits(p.x, p.y, x_biased(X, i));
                     }
                     if (lc.full) {
                         uint4 v;
@@ -2150,7 +2153,8 @@ __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, cons
                         const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
                         const int E = (int)(word[i] >> 24);
                         const float2 p = ab[c * kNbin + E];
-                        const int M = rv + predict_biased(p.x, p.y, x_biased(X, i));
+                        // the low byte of R + (0x4B000000 + M*) is M
+                        const int M = rv + predict_bits(p.x, p.y, x_biased(X, i));
                         word[i] |= ((uint32_t)M & 255u) << (8 * c);
                     }
                 }

@@ -141,12 +141,18 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t w, int i) { return (w >> (8
 // is at least the rounded one, and an integer in between would have to be the
 // rounded value itself), and adding 2^23 rounded down leaves floor(v) in the
 // low mantissa bits.
-__device__ __forceinline__ int predict_biased(float a, float b, uint32_t xbits) {   // xbits = 0x4B000000 | x
+// predict_bits: the same estimate as the biased word 0x4B000000 + M*, for
+// callers that subtract it from (or add it to) another biased or masked value.
+__device__ __forceinline__ int predict_bits(float a, float b, uint32_t xbits) {   // xbits = 0x4B000000 | x
     const float xf = __fsub_rn(__uint_as_float(xbits), 8388608.0f);
     float t = __fadd_rn(__fmul_rn(a, xf), b);
     t = fminf(fmaxf(t, 0.0f), 255.0f);
     const float v = __fadd_rd(t, 0.5f);
-    return __float_as_int(__fadd_rd(v, 8388608.0f)) - 0x4B000000;
+    return __float_as_int(__fadd_rd(v, 8388608.0f));
+}
+
+__device__ __forceinline__ int predict_biased(float a, float b, uint32_t xbits) {   // xbits = 0x4B000000 | x
+    return predict_bits(a, b, xbits) - 0x4B000000;
 }
 
 __device__ __forceinline__ int predict(float a, float b, int x) {

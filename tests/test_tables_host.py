@@ -38,11 +38,12 @@ def test_tables_equal_the_oracles():
 
 def _display_code(v: np.ndarray, code: np.ndarray) -> np.ndarray:
     # the kernel's lookup: bucket from the float bits (clamped to the
-    # below / above buckets), then start + (low 16 bits >= threshold's)
+    # below / above buckets), then (low 16 bits + word) >> 16, the bucket's
+    # start plus one where the low bits reach the threshold's
     bits = np.asarray(v, np.float32).view(np.int32).astype(np.int64)
     idx = np.clip((bits - 0x35800000) >> 16, -1, 2560) + 1
-    e = code[idx]
-    return (e & 255) + ((bits & 0xFFFF) >= (e >> 8)).astype(np.int64)
+    e = code[idx].astype(np.int64)
+    return ((bits & 0xFFFF) + e) >> 16
 
 
 def test_display_code_lookup_equals_the_threshold_count():
