@@ -357,13 +357,16 @@ __device__ __forceinline__ void base_band(const uint8_t* __restrict__ m3, const 
 // the band is not whole -- the right edge of a ragged image -- or the image
 // has no 8-byte rows); false when nothing was copied.
 __device__ __forceinline__ bool prefetch_band(const uint8_t* __restrict__ m3, const uint8_t* __restrict__ e, int h,
-                                              int w, bool fast, int cols, int64_t t, int lane, uint2* slot) {
+                                              int w, bool fast, int cols, int64_t t, int lane, uint2* slot,
+                                              int p = 0) {
+    // planes of h rows of pitch p (p = 0: p = w)
+    p = p ? p : w;
     bool ok = false;
     if (fast) {
         const int y0 = (int)(t / cols) * 8, xb = (int)(t % cols) * 32;
         if (xb + 32 <= w) {
             const int y = min(y0 + (lane & 7), h - 1), x0 = xb + 8 * (lane >> 3);
-            const int64_t n = (int64_t)h * w, off = (int64_t)y * w + x0;
+            const int64_t n = (int64_t)h * p, off = (int64_t)y * p + x0;
             const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot);
             cp_async8(dst, m3 + off);
             cp_async8(dst + 256, m3 + n + off);
@@ -415,37 +418,80 @@ __global__ void __launch_bounds__(kThreads, kBaseCtas) k_base(const uint8_t* __r
     }
 }
 
-// Batch: CTA tasks of 8 band tasks of one image, contiguous ranges per CTA.
+// Batch: CTA tasks of 8 band tasks of one image, contiguous ranges per CTA;
+// a warp takes band (k - first task of the image) * 8 + warp of CTA task k.
+// As in k_base, each warp copies its next band's bytes into shared memory
+// (cp.async) while it processes the current one, across image changes too.
+struct BatchBand {
+    int img;            // -1: none
+    int64_t t;          // band of the image, or past its last band
+};
+
+__device__ __forceinline__ BatchBand batch_band(const BatchDev& B, int64_t k, int warp) {
+    const int i = batch_image_of(B.base_prefix, B.n, k);
+    return BatchBand{i, (k - B.base_prefix[i]) * kWarps + warp};
+}
+
+__device__ __forceinline__ bool batch_fast(const BatchImage& im, const uint8_t* m3b, const uint8_t* eb,
+                                           const uint8_t* s3b) {
+    // pitched rows: 8-byte loads and stores are aligned wherever 8 columns lie inside the image
+    return (im.pitch % 8 == 0) && ((uintptr_t)(m3b + 3 * im.px) % 8 == 0) && ((uintptr_t)(eb + im.px) % 8 == 0) &&
+           ((uintptr_t)(s3b + 3 * im.px) % 8 == 0);
+}
+
+__device__ __forceinline__ bool batch_prefetch(const BatchDev& B, const BatchBand& b, const uint8_t* m3b,
+                                               const uint8_t* eb, const uint8_t* s3b, int lane, uint2* slot) {
+    const BatchImage im = B.img[b.img];
+    const int cols = (im.w + 31) >> 5;
+    const int64_t bands = (int64_t)((im.h + 7) >> 3) * cols;
+    if ((int64_t)im.h * im.w == 0 || b.t >= bands) {
+        cp_async_commit();
+        return false;
+    }
+    return prefetch_band(m3b + 3 * im.px, eb + im.px, im.h, im.w, batch_fast(im, m3b, eb, s3b), cols, b.t, lane, slot,
+                         im.pitch);
+}
+
 __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, int64_t cta_tasks,
                                                             const uint8_t* __restrict__ m3b,
                                                             const uint8_t* __restrict__ eb, uint8_t* __restrict__ s3b) {
     __shared__ uint32_t gcode[kGammaWords];
     __shared__ __align__(16) int tile[kWarps][kTileWords];
+    __shared__ __align__(16) uint2 pre[kWarps][2][4][32];   // [warp][slot][plane][lane]
     load_gamma(gcode);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
-    int cur = -1;
+    if (k0 >= k1) return;
+    int cur = -1, slot = 0;
     BaseKey K;
+    BatchBand b = batch_band(B, k0, warp);
+    bool have = batch_prefetch(B, b, m3b, eb, s3b, lane, &pre[warp][0][0][lane]);
     for (int64_t k = k0; k < k1; ++k) {
-        const int i = batch_image_of(B.base_prefix, B.n, k);
-        if (i != cur) {
-            base_key(B.lum_stats + 2 * i, B.quant[i], lane & 7, K);
-            cur = i;
+        // the next task's band goes out before this one is processed
+        BatchBand nb{-1, 0};
+        bool next = false;
+        if (k + 1 < k1) {
+            nb = batch_band(B, k + 1, warp);
+            next = batch_prefetch(B, nb, m3b, eb, s3b, lane, &pre[warp][slot ^ 1][0][lane]);
+        } else {
+            cp_async_commit();   // one group per band, so "all but the newest" is this band's
         }
-        const BatchImage im = B.img[i];
-        const uint8_t* m3 = m3b + 3 * im.px;
-        const uint8_t* e = eb + im.px;
-        uint8_t* s3 = s3b + 3 * im.px;
+        cp_async_wait_prev();
+        if (b.img != cur) {
+            base_key(B.lum_stats + 2 * b.img, B.quant[b.img], lane & 7, K);
+            cur = b.img;
+        }
+        const BatchImage im = B.img[b.img];
         const int cols = (im.w + 31) >> 5;
         const int64_t bands = (int64_t)((im.h + 7) >> 3) * cols;
-        const int64_t t = (k - B.base_prefix[i]) * kWarps + warp;
-        // pitched rows: 8-byte loads and stores are aligned wherever 8 columns lie inside the image
-        const bool fast = (im.pitch % 8 == 0) && ((uintptr_t)m3 % 8 == 0) && ((uintptr_t)e % 8 == 0) &&
-                          ((uintptr_t)s3 % 8 == 0);
-        if ((int64_t)im.h * im.w > 0 && t < bands)
-            base_band(m3, e, im.h, im.w, fast, (int)(t / cols) * 8, (int)(t % cols) * 32, lane, K, gcode,
-                      tile[warp], s3, nullptr, nullptr, nullptr, 0.0f, im.pitch);
+        if ((int64_t)im.h * im.w > 0 && b.t < bands)
+            base_band(m3b + 3 * im.px, eb + im.px, im.h, im.w, batch_fast(im, m3b, eb, s3b), (int)(b.t / cols) * 8,
+                      (int)(b.t % cols) * 32, lane, K, gcode, tile[warp], s3b + 3 * im.px, nullptr,
+                      have ? &pre[warp][slot][0][lane] : nullptr, nullptr, 0.0f, im.pitch);
+        b = nb;
+        have = next;
+        slot ^= 1;
     }
 }
 

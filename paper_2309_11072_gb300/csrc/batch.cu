@@ -131,20 +131,32 @@ bool buffers_ok(const slrme_batch_plan* p, const slrme_batch_buffers* b, bool en
     return true;
 }
 
+// Restoration over the batch's images with pixels: 0 none, 1 all, 2 mixed.
+int gf_mode(const slrme_batch_plan* p) {
+    bool any_on = false, any_off = false;
+    for (int i = 0; i < p->n_images; ++i) {
+        const slrme_batch_image& im = p->images[i];
+        if ((int64_t)im.h * im.w == 0) continue;
+        (im.gf_on ? any_on : any_off) = true;
+    }
+    return any_on && any_off ? 2 : (any_on ? 1 : 0);
+}
+
 int encode_stages(const slrme_batch_plan* p, const slrme_batch_buffers* b, cudaStream_t s) {
     const BatchDev B = device_view(p);
     const slrme_batch_tiles& t = p->tiles;
     int st = launch_split_batch(B, p->split_chunks, t.split_ctas_per_sm, b->rgbe, b->m3, b->e, s);
     if (st == SLRME_OK) st = launch_base_batch(B, p->base_tasks, t.base_ctas_per_sm, b->m3, b->e, b->s3, s);
-    if (st == SLRME_OK) st = launch_fit_batch(B, p->tile_rows, b->s3, b->m3, b->e, b->params, s);
+    const int gm = gf_mode(p);
+    if (st == SLRME_OK) st = launch_fit_batch(B, p->tile_rows, gm, b->s3, b->m3, b->e, b->params, s);
     if (st == SLRME_OK)
-        st = launch_residual_batch(B, p->tile_rows, b->s3, b->m3, b->e, b->params, b->r3, b->hist, s);
+        st = launch_residual_batch(B, p->tile_rows, gm, b->s3, b->m3, b->e, b->params, b->r3, b->hist, s);
     return st;
 }
 
 int decode_stage(const slrme_batch_plan* p, const slrme_batch_buffers* b, cudaStream_t s) {
     const BatchDev B = device_view(p);
-    return launch_decode_batch(B, p->tile_rows, b->s3, b->e, b->r3, b->params, b->rgbe_out, s);
+    return launch_decode_batch(B, p->tile_rows, gf_mode(p), b->s3, b->e, b->r3, b->params, b->rgbe_out, s);
 }
 
 }  // namespace

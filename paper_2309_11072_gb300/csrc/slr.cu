@@ -1881,6 +1881,9 @@ __device__ __forceinline__ void bins_flush_consumers(SmemBins& bins, unsigned lo
 
 // The fit over the batch.  The bins hold one image's sums of at most 256 rows
 // of 2048 pixels (2^19 pixels, the bins' bound) between flushes.
+// kGfMode: 0 every image without restoration, 1 every image with it, 2
+// mixed (the flag read per image).
+template <int kGfMode>
 __device__ __forceinline__ void fit_consume_batch(const TileSmem<TmaMode::kFit>& L, const TileBatchArgs& A,
                                                   SmemBins& bins, uint32_t* queue, int* gave_up, int warp, int lane) {
     TileConsumer<TmaMode::kFit> C{L, A.max_spins, {0u}, {0u}};
@@ -1910,7 +1913,7 @@ __device__ __forceinline__ void fit_consume_batch(const TileSmem<TmaMode::kFit>&
         since += T.rows;
         if (!ok) continue;   // after a timeout: walk the tasks (and their barriers) without work
         const LaneColsB lc(T.xs, T.w, warp, lane);
-        const bool gf = T.gf != 0;
+        const bool gf = kGfMode == 2 ? T.gf != 0 : kGfMode == 1;
         run2_reset(all, -1);
         run2_reset(odd, -1);
         uint32_t Hm[3][4], H0[3][4];
@@ -2035,6 +2038,7 @@ __device__ __forceinline__ void fit_consume_batch(const TileSmem<TmaMode::kFit>&
     if (cur >= 0) flush();
 }
 
+template <int kGfMode>
 __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile_batch(const TileBatchArgs A) {
     extern __shared__ __align__(128) char dyn[];
     __shared__ int gave_up;
@@ -2053,13 +2057,13 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k
     for (int i = threadIdx.x; i < (int)(sizeof(SmemBins) / 16); i += kTileWarps * 32)
         reinterpret_cast<uint4*>(extra)[i] = make_uint4(0u, 0u, 0u, 0u);
     consumers_sync();
-    fit_consume_batch(L, A, bins, queue, &gave_up, warp, lane);
+    fit_consume_batch<kGfMode>(L, A, bins, queue, &gave_up, warp, lane);
 }
 
 // Residual / decoder over the batch: the parameters (and, for the residual,
 // the histograms) of the current image in shared memory, switched at image
 // changes behind consumer barriers.
-template <TmaMode MODE>
+template <TmaMode MODE, int kGfMode>
 __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, const TileBatchArgs& A, float2* ab,
                                                    uint32_t* hist, int warp, int lane) {
     constexpr uint32_t kEl = TileAux<MODE>::kElem;
@@ -2082,7 +2086,7 @@ __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, cons
         }
         if (!ok) continue;   // after a timeout: walk the tasks (and their barriers) without work
         const LaneColsB lc(T.xs, T.w, warp, lane);
-        const bool gf = T.gf != 0;
+        const bool gf = kGfMode == 2 ? T.gf != 0 : kGfMode == 1;
         const int64_t n = (int64_t)T.h * T.p;
         uint32_t Hm[3][4], H0[3][4];
         ok = C.wait_s();
@@ -2180,7 +2184,7 @@ __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, cons
     }
 }
 
-template <TmaMode MODE>
+template <TmaMode MODE, int kGfMode>
 __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile_batch(const TileBatchArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2196,7 +2200,7 @@ __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_til
     }
     if (MODE == TmaMode::kResidual && A.hist)
         for (int i = threadIdx.x; i < 3 * kNres; i += kTileWarps * 32) hist[i] = 0u;
-    rows_consume_batch<MODE>(L, A, ab, hist, warp, lane);
+    rows_consume_batch<MODE, kGfMode>(L, A, ab, hist, warp, lane);
 }
 
 bool tma_eligible(int w, std::initializer_list<const void*> ptrs) {
@@ -2351,48 +2355,70 @@ int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r
 
 // ---------------------------------------------------------------- batch launchers
 
-int launch_fit_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3, const uint8_t* e,
-                     slrme_params* params, cudaStream_t s) {
+namespace {
+
+template <int kGfMode>
+int fit_batch_kernel(const TileBatchArgs& A, int64_t tile_rows, cudaStream_t s) {
+    static bool attr_set[64];
+    int st = tile_smem_attr(k_fit_tile_batch<kGfMode>, kTileFitSmem, attr_set);
+    if (st != SLRME_OK) return st;
+    k_fit_tile_batch<kGfMode><<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kFit>::kCtas), kTileThreads,
+                                kTileFitSmem, s>>>(A);
+    return cuda_status("batch fit launch");
+}
+
+template <TmaMode MODE, int kGfMode>
+int rows_batch_kernel(const TileBatchArgs& A, int64_t tile_rows, cudaStream_t s) {
+    static bool attr_set[64];
+    constexpr size_t smem = tile_rows_smem<MODE>();
+    int st = tile_smem_attr(k_rows_tile_batch<MODE, kGfMode>, smem, attr_set);
+    if (st != SLRME_OK) return st;
+    k_rows_tile_batch<MODE, kGfMode><<<(unsigned)batch_tile_grid(tile_rows, TileAux<MODE>::kCtas), kTileThreads, smem,
+                                       s>>>(A);
+    return cuda_status(MODE == TmaMode::kResidual ? "batch residual launch" : "batch decode launch");
+}
+
+template <TmaMode MODE>
+int rows_batch(const TileBatchArgs& A, int64_t tile_rows, int gf_mode, cudaStream_t s) {
+    return gf_mode == 0 ? rows_batch_kernel<MODE, 0>(A, tile_rows, s)
+                        : (gf_mode == 1 ? rows_batch_kernel<MODE, 1>(A, tile_rows, s)
+                                        : rows_batch_kernel<MODE, 2>(A, tile_rows, s));
+}
+
+}  // namespace
+
+// gf_mode: 0 no image of the batch uses the restoration, 1 every image does,
+// 2 mixed (each image's flag read on the device).
+int launch_fit_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* m3,
+                     const uint8_t* e, slrme_params* params, cudaStream_t s) {
     if (cudaMemsetAsync(B.sums, 0, sizeof(unsigned long long) * kNbin * kNsum * (size_t)B.n, s) != cudaSuccess)
         return cuda_status("batch fit memset");
     if (tile_rows > 0) {
-        static bool attr_set[64];
-        int st = tile_smem_attr(k_fit_tile_batch, kTileFitSmem, attr_set);
-        if (st != SLRME_OK) return st;
         TileBatchArgs A{B, s3, m3, e, tile_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr};
-        k_fit_tile_batch<<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kFit>::kCtas), kTileThreads, kTileFitSmem, s>>>(A);
-        st = cuda_status("batch fit launch");
+        const int st = gf_mode == 0 ? fit_batch_kernel<0>(A, tile_rows, s)
+                                    : (gf_mode == 1 ? fit_batch_kernel<1>(A, tile_rows, s)
+                                                    : fit_batch_kernel<2>(A, tile_rows, s));
         if (st != SLRME_OK) return st;
     }
     k_solve_batch<<<dim3(kSolveBlocks, B.n), 32, 0, s>>>(B.sums, params);
     return cuda_status("batch solve launch");
 }
 
-int launch_residual_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3,
+int launch_residual_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* m3,
                           const uint8_t* e, const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s) {
     if (hist && cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 3 * kNres * (size_t)B.n, s) != cudaSuccess)
         return cuda_status("batch residual memset");
     if (tile_rows == 0) return SLRME_OK;
-    static bool attr_set[64];
-    constexpr size_t smem = tile_rows_smem<TmaMode::kResidual>();
-    int st = tile_smem_attr(k_rows_tile_batch<TmaMode::kResidual>, smem, attr_set);
-    if (st != SLRME_OK) return st;
     TileBatchArgs A{B, s3, m3, e, tile_rows, kMaxSpins, params, r3, hist, nullptr};
-    k_rows_tile_batch<TmaMode::kResidual><<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kResidual>::kCtas), kTileThreads, smem, s>>>(A);
-    return cuda_status("batch residual launch");
+    return rows_batch<TmaMode::kResidual>(A, tile_rows, gf_mode, s);
 }
 
-int launch_decode_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* e, const int16_t* r3,
-                        const slrme_params* params, uint32_t* out, cudaStream_t s) {
+int launch_decode_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* e,
+                        const int16_t* r3, const slrme_params* params, uint32_t* out, cudaStream_t s) {
     if (tile_rows == 0) return SLRME_OK;
-    static bool attr_set[64];
-    constexpr size_t smem = tile_rows_smem<TmaMode::kDecode>();
-    int st = tile_smem_attr(k_rows_tile_batch<TmaMode::kDecode>, smem, attr_set);
-    if (st != SLRME_OK) return st;
     TileBatchArgs A{B, s3, reinterpret_cast<const uint8_t*>(r3), e, tile_rows, kMaxSpins, params, nullptr, nullptr,
                     out};
-    k_rows_tile_batch<TmaMode::kDecode><<<(unsigned)batch_tile_grid(tile_rows, TileAux<TmaMode::kDecode>::kCtas), kTileThreads, smem, s>>>(A);
-    return cuda_status("batch decode launch");
+    return rows_batch<TmaMode::kDecode>(A, tile_rows, gf_mode, s);
 }
 
 

@@ -71,12 +71,13 @@ int launch_split_batch(const BatchDev& B, int64_t chunks, int ctas_per_sm, const
                        uint8_t* e, cudaStream_t s);
 int launch_base_batch(const BatchDev& B, int64_t cta_tasks, int ctas_per_sm, const uint8_t* m3, const uint8_t* e,
                       uint8_t* s3, cudaStream_t s);
-int launch_fit_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3, const uint8_t* e,
-                     slrme_params* params, cudaStream_t s);
-int launch_residual_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* m3,
+// gf_mode: 0 no image uses the restoration, 1 every image does, 2 mixed.
+int launch_fit_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* m3,
+                     const uint8_t* e, slrme_params* params, cudaStream_t s);
+int launch_residual_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* m3,
                           const uint8_t* e, const slrme_params* params, int16_t* r3, uint32_t* hist, cudaStream_t s);
-int launch_decode_batch(const BatchDev& B, int64_t tile_rows, const uint8_t* s3, const uint8_t* e, const int16_t* r3,
-                        const slrme_params* params, uint32_t* out, cudaStream_t s);
+int launch_decode_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* e,
+                        const int16_t* r3, const slrme_params* params, uint32_t* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- launch geometry
 struct Geometry {
