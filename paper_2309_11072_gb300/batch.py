@@ -79,15 +79,19 @@ def _call(name, *args):
 class BatchCodec:
     """Owns a plan, its workspace and the batch planes for a list of image sizes."""
 
-    def __init__(self, sizes: Sequence[Tuple[int, int]], qualities: Sequence[int], gf_on: bool = True,
+    def __init__(self, sizes: Sequence[Tuple[int, int]], qualities: Sequence[int], gf_on=True,
                  device: str = "cuda"):
+        """gf_on: one restoration flag for every image, or one per image."""
         n = len(sizes)
         if n < 1 or len(qualities) != n:
             raise ValueError("need one quality per image")
+        gfs = [bool(gf_on)] * n if isinstance(gf_on, (bool, int)) else [bool(g) for g in gf_on]
+        if len(gfs) != n:
+            raise ValueError("need one restoration flag per image")
         self.device = torch.device(device)
         self.images = (BatchImage * n)()
-        for i, ((h, w), q) in enumerate(zip(sizes, qualities)):
-            self.images[i] = BatchImage(int(h), int(w), int(q), int(bool(gf_on)), 0, 0, 0)
+        for i, ((h, w), q, g) in enumerate(zip(sizes, qualities, gfs)):
+            self.images[i] = BatchImage(int(h), int(w), int(q), int(g), 0, 0, 0)
         self.ws = torch.zeros(int(_lib().slrme_batch_workspace_bytes(n)), dtype=torch.uint8, device=self.device)
         self.plan = BatchPlan()
         _call("slrme_batch_plan_init", ctypes.addressof(self.plan), ctypes.addressof(self.images), n,

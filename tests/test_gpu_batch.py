@@ -36,6 +36,7 @@ def _host(t, dt):
 
 def _check_against_oracle(bc, imgs, quals, gf_on=True):
     torch.cuda.synchronize()
+    gfs = [gf_on] * len(imgs) if isinstance(gf_on, bool) else list(gf_on)
     for i, img in enumerate(imgs):
         h, w = img.shape
         L = bc.image_layers(i)
@@ -43,7 +44,7 @@ def _check_against_oracle(bc, imgs, quals, gf_on=True):
             p = bc.image_params(i)
             assert p["n_used"] == 0
             continue
-        o = O.encode(img, quals[i], gf_on)
+        o = O.encode(img, quals[i], gfs[i])
         assert np.array_equal(_host(L["m3"], np.uint8).reshape(3, h, w), o["m3"]), i
         assert np.array_equal(_host(L["e"], np.uint8).reshape(h, w), o["e"]), i
         assert np.array_equal(_host(L["s3"], np.uint8).reshape(3, h, w), o["s3"]), i
@@ -73,6 +74,18 @@ def test_batch_matches_oracle_per_image(gf_on):
     bc.encode()
     bc.decode()
     _check_against_oracle(bc, imgs, QUALS, gf_on)
+
+
+def test_batch_with_mixed_restoration_flags():
+    """Images with and without the restoration filter in one batch (the row
+    stages then read each image's flag on the device)."""
+    imgs = _images(SIZES, seed0=700)
+    gfs = [i % 3 != 1 for i in range(len(SIZES))]
+    bc = B.BatchCodec(SIZES, QUALS, gf_on=gfs)
+    bc.load(imgs)
+    bc.encode()
+    bc.decode()
+    _check_against_oracle(bc, imgs, QUALS, gfs)
 
 
 def test_batch_results_do_not_depend_on_tiles():
@@ -122,8 +135,9 @@ def _oracle_all(imgs, quals, gf_on=True):
     oracle's C calls release the GIL, so the images run on separate cores)."""
     from concurrent.futures import ThreadPoolExecutor
     O.lib()
+    gfs = [gf_on] * len(imgs) if isinstance(gf_on, bool) else list(gf_on)
     with ThreadPoolExecutor(max_workers=max(1, min(len(imgs), os.cpu_count() or 1))) as ex:
-        return list(ex.map(lambda k: None if imgs[k].size == 0 else O.encode(imgs[k], quals[k], gf_on),
+        return list(ex.map(lambda k: None if imgs[k].size == 0 else O.encode(imgs[k], quals[k], gfs[k]),
                            range(len(imgs))))
 
 
@@ -154,21 +168,23 @@ def test_batch_ctas_that_cross_image_boundaries():
     rows into one contiguous range per CTA (two CTAs per SM), about 40 rows
     each, so most CTAs change image in the middle of the launch (flushing
     their shared bins and histograms to one image and loading the next
-    one's parameters) and some cover several short images.  Every image
-    must still equal the oracle."""
+    one's parameters) and some cover several short images; the images
+    alternate irregularly between restoration on and off.  Every image must
+    still equal the oracle."""
     rng = np.random.default_rng(77)
     sizes = [(int(rng.integers(1, 129)), int(rng.integers(1, 257))) for _ in range(200)]
     quals = [int(q) for q in rng.choice([30, 50, 75, 90, 100], size=len(sizes))]
+    gfs = [bool(g) for g in rng.random(len(sizes)) < 0.7]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     imgs = _images(sizes, seed0=900)
-    bc = B.BatchCodec(sizes, quals)
+    bc = B.BatchCodec(sizes, quals, gf_on=gfs)
     rows_per_cta = bc.plan.tile_rows / (2 * sms)
     assert rows_per_cta < 64 and min(h for h, _ in sizes) < rows_per_cta / 4
     bc.load(imgs)
     bc.set_tiles(split_ctas_per_sm=1, base_ctas_per_sm=1)
     bc.encode()
     bc.decode()
-    _check_all(bc, imgs, quals)
+    _check_all(bc, imgs, quals, gfs)
     bc.close()
 
 
