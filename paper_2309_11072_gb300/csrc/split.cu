@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(kThreads) k_split_vec(const uint4* __restrict_
     int64_t sl64 = 0, se64 = 0, c = 0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    constexpr int U = 4;   // independent 16-byte loads in flight per thread
-    // 32-bit parts per step: at most 16 words, each below 2^20 (LUT) and 267 (E + k)
+    constexpr int U = 8;   // independent 16-byte loads in flight per thread
+    // 32-bit parts per step: at most 32 words, each below 2^20 (LUT) and 267 (E + k)
     for (; i + (U - 1) * stride < nv; i += U * stride) {
         uint4 v[U];
 #pragma unroll
