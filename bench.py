@@ -342,28 +342,31 @@ def run_ours(args) -> None:
     stage_frac = {name: round(BYTES_PER_PX[name] * n / (avg_us[name] * 1e-6) / 1e9 / peaks["hbm_gbs"], 4)
                   for name in calls}
 
-    # end to end through the public API with host buffers (two streams alternate,
-    # so one call's copies overlap the next call's coding)
+    # end to end through the public API with host buffers: the K steps run as
+    # one job (HostCodec's slots take the calls in turn on their own streams,
+    # so one call's copies back overlap the next call's copy in and coding);
+    # every step copies its input words in and its layers and decoded words
+    # back inside the timed region, and its input comes from host memory, so
+    # no L2 flush is needed between steps
     hc = codec.HostCodec(h, w, "cuda", gf_on=True)
     h_rgbe = torch.from_numpy(img.view(np.int32).reshape(-1).copy()).pin_memory()
     for _ in range(args.warmup):
         for q in qualities:
             hc.roundtrip(h_rgbe, q)
     torch.cuda.synchronize()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     side = hc.streams()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in side:
+        s_.wait_stream(stream)
     for k in range(args.steps):
-        e2e_ev[k][0].record(stream)
-        for s_ in side:
-            s_.wait_stream(stream)
         for q in qualities:
             hc.roundtrip(h_rgbe, q)
-        for s_ in side:
-            stream.wait_stream(s_)
-        e2e_ev[k][1].record(stream)
-        flush.zero_()
+    for s_ in side:
+        stream.wait_stream(s_)
+    e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    e2e_ms = e0.elapsed_time(e1)
     e2e_ok = bool(torch.equal(hc.h_out, h_rgbe))
     e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
     e2e_value = job_mpx_per_s(world, px_per_step, args.steps, e2e_ms)
