@@ -303,19 +303,37 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int oy = (int)(tile / tiles_x) * TH, ox = (int)(tile % tiles_x) * TW;
         __syncthreads();   // the previous tile's readers are done with the buffers
-        // input tile: encoded (S - 128, key-relative exponent, 0 ...) per pixel; encoded zero outside the image
-        for (int p = threadIdx.x; p < H0 * P; p += kThreadsC) {
-            const int gy = oy - 4 + p / P, gx = ox - 4 + p % P;
-            uint32_t v0 = kInZeroPair, v1 = kInZeroPair;
-            if (gy >= 0 && gy < h && gx >= 0 && gx < w) {
-                const int64_t o = (int64_t)gy * w + gx;
-                int d = (int)A.e[o] - 137 - A.J;
-                d = d < -128 ? -128 : (d > 127 ? 127 : d);
-                v0 = enc_in_pair((int)A.s3[o] - 128, (int)A.s3[n + o] - 128);
-                v1 = enc_in_pair((int)A.s3[2 * n + o] - 128, d);
+        // input tile: encoded (S - 128, key-relative exponent, 0 ...) per pixel; encoded zero outside the
+        // image.  Every load of the thread's pixels is issued before the first is used.
+        {
+            constexpr int kIt = (H0 * P + kThreadsC - 1) / kThreadsC;
+            int sv[kIt][4];
+            bool in[kIt];
+#pragma unroll
+            for (int it = 0; it < kIt; ++it) {
+                const int p = threadIdx.x + it * kThreadsC;
+                const int gy = oy - 4 + p / P, gx = ox - 4 + p % P;
+                in[it] = p < H0 * P && gy >= 0 && gy < h && gx >= 0 && gx < w;
+                const int64_t o = in[it] ? (int64_t)gy * w + gx : 0;
+                sv[it][0] = in[it] ? (int)A.s3[o] : 0;
+                sv[it][1] = in[it] ? (int)A.s3[n + o] : 0;
+                sv[it][2] = in[it] ? (int)A.s3[2 * n + o] : 0;
+                sv[it][3] = in[it] ? (int)A.e[o] : 0;
             }
-            *reinterpret_cast<uint4*>(bufA + swz(p, 0)) = make_uint4(v0, v1, 0u, 0u);
-            *reinterpret_cast<uint4*>(bufA + swz(p, 1)) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int it = 0; it < kIt; ++it) {
+                const int p = threadIdx.x + it * kThreadsC;
+                if (p >= H0 * P) break;
+                uint32_t v0 = kInZeroPair, v1 = kInZeroPair;
+                if (in[it]) {
+                    int d = sv[it][3] - 137 - A.J;
+                    d = d < -128 ? -128 : (d > 127 ? 127 : d);
+                    v0 = enc_in_pair(sv[it][0] - 128, sv[it][1] - 128);
+                    v1 = enc_in_pair(sv[it][2] - 128, d);
+                }
+                *reinterpret_cast<uint4*>(bufA + swz(p, 0)) = make_uint4(v0, v1, 0u, 0u);
+                *reinterpret_cast<uint4*>(bufA + swz(p, 1)) = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
         __syncthreads();
         conv_layer<H0, 2, false>(sA, bufB, nullptr, L1, 0, frag, cst_s, mul_s, cor_s, narrow_s, 3, oy, ox, h, w);
@@ -327,49 +345,83 @@ __global__ void __launch_bounds__(kThreadsC, 2) k_cnn(const CnnArgs A) {
                                      w);
         __syncthreads();
         // S around the tile for the restoration filter (edges replicated), into the free input buffer
-        if (A.mode != kInfer)
-            for (int p = threadIdx.x; p < GH * GW; p += kThreadsC) {
+        if (A.mode != kInfer) {
+            constexpr int kIt = (GH * GW + kThreadsC - 1) / kThreadsC;
+            uint8_t sv[kIt][3];
+#pragma unroll
+            for (int it = 0; it < kIt; ++it) {
+                const int p = min(threadIdx.x + it * kThreadsC, GH * GW - 1);
                 const int gy = min(max(oy - 1 + p / GW, 0), h - 1), gx = min(max(ox - 1 + p % GW, 0), w - 1);
                 const int64_t o = (int64_t)gy * w + gx;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) Sg[c * GH * GW + p] = A.s3[c * n + o];
+                for (int c = 0; c < 3; ++c) sv[it][c] = A.s3[c * n + o];
             }
+#pragma unroll
+            for (int it = 0; it < kIt; ++it) {
+                const int p = threadIdx.x + it * kThreadsC;
+                if (p < GH * GW) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Sg[c * GH * GW + p] = sv[it][c];
+                }
+            }
+        }
         conv_layer<H0 - 6, 1, true>(sB, nullptr, mh, L4, 3, frag, cst_s, mul_s, cor_s, narrow_s, 0, oy, ox, h, w);
         __syncthreads();
-        // outputs of the tile, one pixel per thread per step
-        for (int p = threadIdx.x; p < TH * TW; p += kThreadsC) {
-            const int r = p / TW, c = p % TW;
-            const int gy = oy + r, gx = ox + c;
-            if (gy >= h || gx >= w) continue;
-            const int64_t o = (int64_t)gy * w + gx;
-            int y3[3] = {mh[p], mh[TH * TW + p], mh[2 * TH * TW + p]};
-            if (A.mode == kInfer) {
+        // outputs of the tile: a thread's pixels p = threadIdx.x + k * kThreadsC; the exponents and
+        // the mantissas (encoder) or residuals (decoder) of all of them are loaded first
+        {
+            constexpr int kIt = (TH * TW + kThreadsC - 1) / kThreadsC;
+            int Ev[kIt], in3[kIt][3];
+            int64_t ov[kIt];
+            bool ok[kIt];
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) A.mhat3[ch * n + o] = (uint8_t)y3[ch];
-                continue;
-            }
-            // refined estimate: M^ = clamp(M* + y - 128, 0, 255), M* from Eq. (8)
-            const int E = A.e[o];
-            int mhat[3];
+            for (int k = 0; k < kIt; ++k) {
+                const int p = threadIdx.x + k * kThreadsC;
+                const int gy = oy + p / TW, gx = ox + p % TW;
+                ok[k] = p < TH * TW && gy < h && gx < w;
+                ov[k] = ok[k] ? (int64_t)gy * w + gx : 0;
+                const int64_t o = ov[k];
+                Ev[k] = ok[k] && A.mode != kInfer ? (int)A.e[o] : 0;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const int ms = predict(__ldg(pa + ch * kNbin + E), __ldg(pb + ch * kNbin + E),
-                                       gf_tile(Sg + ch * GH * GW, r, c, gf));
-                const int v = ms + y3[ch] - 128;
-                mhat[ch] = v < 0 ? 0 : (v > 255 ? 255 : v);
+                for (int ch = 0; ch < 3; ++ch)
+                    in3[k][ch] = !ok[k] || A.mode == kInfer ? 0
+                                 : (A.mode == kEncode ? (int)A.m3[ch * n + o] : (int)A.r3[ch * n + o]);
             }
-            if (A.mode == kEncode) {
+#pragma unroll
+            for (int k = 0; k < kIt; ++k) {
+                if (!ok[k]) continue;
+                const int p = threadIdx.x + k * kThreadsC;
+                const int r = p / TW, c = p % TW;
+                const int64_t o = ov[k];
+                const int y3[3] = {mh[p], mh[TH * TW + p], mh[2 * TH * TW + p]};
+                if (A.mode == kInfer) {
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) A.mhat3[ch * n + o] = (uint8_t)y3[ch];
+                    continue;
+                }
+                // refined estimate: M^ = clamp(M* + y - 128, 0, 255), M* from Eq. (8)
+                const int E = Ev[k];
+                int mhat[3];
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    const int rr = (int)A.m3[ch * n + o] - mhat[ch];
-                    A.r3_out[ch * n + o] = (int16_t)rr;
-                    if (want_hist) atomicAdd(&hist[ch * kNres + rr + 255], 1u);
+                    const int ms = predict(__ldg(pa + ch * kNbin + E), __ldg(pb + ch * kNbin + E),
+                                           gf_tile(Sg + ch * GH * GW, r, c, gf));
+                    const int v = ms + y3[ch] - 128;
+                    mhat[ch] = v < 0 ? 0 : (v > 255 ? 255 : v);
                 }
-            } else {
-                uint32_t wd = (uint32_t)E << 24;
+                if (A.mode == kEncode) {
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) wd |= ((uint32_t)((int)A.r3[ch * n + o] + mhat[ch]) & 255u) << (8 * ch);
-                A.rgbe_out[o] = wd;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const int rr = in3[k][ch] - mhat[ch];
+                        A.r3_out[ch * n + o] = (int16_t)rr;
+                        if (want_hist) atomicAdd(&hist[ch * kNres + rr + 255], 1u);
+                    }
+                } else {
+                    uint32_t wd = (uint32_t)E << 24;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) wd |= ((uint32_t)(in3[k][ch] + mhat[ch]) & 255u) << (8 * ch);
+                    A.rgbe_out[o] = wd;
+                }
             }
         }
     }
