@@ -1709,8 +1709,9 @@ struct TileBatchArgs {
 
 // A CTA's range of global rows and its current task and image.
 struct BatchRange {
-    int64_t r, end;
-    int64_t base, limit;         // global rows of the current image: [base, limit)
+    int64_t start;               // the CTA's first global row; the counters below are relative to it
+    int r, end;
+    int base, limit;             // rows of the current image: [base, limit)
     int img;
     const uint8_t* s3;
     const uint8_t* aux;
@@ -1720,8 +1721,9 @@ struct BatchRange {
     int y0, rows, xs;
     __device__ __forceinline__ void set(const TileBatchArgs& A, int i, uint32_t elem) {
         img = i;
-        base = A.B.row_prefix[i];
-        limit = A.B.row_prefix[i + 1];
+        // both within one image's rows of the CTA's range, so they fit 32 bits
+        base = (int)(A.B.row_prefix[i] - start);
+        limit = (int)(A.B.row_prefix[i + 1] - start);
         const BatchImage im = A.B.img[i];
         h = im.h;
         w = im.w;
@@ -1738,13 +1740,13 @@ struct BatchRange {
             int i = img;
             do {
                 ++i;
-            } while (A.B.row_prefix[i + 1] <= r);
+            } while (A.B.row_prefix[i + 1] - start <= (int64_t)r);
             set(A, i, elem);
         }
-        const int64_t local = r - base;
-        const int c = (int)(local / h);
-        y0 = (int)(local - (int64_t)c * h);
-        rows = (int)min(min(end - r, (int64_t)(h - y0)), (int64_t)kTaskRows);
+        const int local = r - base;
+        const int c = local / h;
+        y0 = local - c * h;
+        rows = min(min(end - r, h - y0), kTaskRows);
         xs = c * kTileCols;
         r += rows;
         return true;
@@ -1754,11 +1756,12 @@ struct BatchRange {
 __device__ __forceinline__ BatchRange batch_range(const TileBatchArgs& A, uint32_t elem) {
     const int64_t G = gridDim.x, b = blockIdx.x;
     BatchRange T;
-    T.r = b * A.total_rows / G;
-    T.end = (b + 1) * A.total_rows / G;
+    T.start = b * A.total_rows / G;
+    T.r = 0;
+    T.end = (int)((b + 1) * A.total_rows / G - T.start);
     T.img = -1;
     T.base = T.limit = 0;
-    if (T.r < T.end) T.set(A, batch_image_of(A.B.row_prefix, A.B.n, T.r), elem);
+    if (T.r < T.end) T.set(A, batch_image_of(A.B.row_prefix, A.B.n, T.start), elem);
     return T;
 }
 
