@@ -88,6 +88,24 @@ def test_batch_with_mixed_restoration_flags():
     _check_against_oracle(bc, imgs, QUALS, gfs)
 
 
+def test_batch_without_histograms_gives_the_same_residuals():
+    """A batch encode with hist = NULL writes the same residual planes and
+    leaves the histogram buffer alone."""
+    imgs = _images(SIZES, seed0=800)
+    bc = B.BatchCodec(SIZES, QUALS)
+    bc.load(imgs)
+    bc.encode()
+    torch.cuda.synchronize()
+    ref = bc.r3.clone()
+    bc.r3.zero_()
+    bc.hist.fill_(-1)
+    bc.bufs.hist = None
+    bc.encode()
+    torch.cuda.synchronize()
+    assert torch.equal(bc.r3, ref)
+    assert bool((bc.hist == -1).all())
+
+
 def test_batch_results_do_not_depend_on_tiles():
     imgs = _images(SIZES, seed0=300)
     bc = B.BatchCodec(SIZES, QUALS)

@@ -199,6 +199,25 @@ def run_residual(s3, m3, e, a, b, gf_on, offset=0):
     return host(r3, np.int16).reshape(3, h, w), host(hist, np.uint32).reshape(3, 511)
 
 
+@pytest.mark.parametrize("h,w", [(9, 17), (33, 64), (20, 2064)])
+def test_residual_without_histograms(h, w):
+    """hist = NULL: the same residuals, nothing counted (a width that is a
+    multiple of 16 takes the bulk-copy row kernels, the others the strip
+    kernels)."""
+    img = make_img(h, w, "noise", seed=h + 7 * w)
+    rng = np.random.default_rng(h * w)
+    om3, oe = O.rgbe_split(img)
+    s3 = rng.integers(0, 256, size=(3, h, w)).astype(np.uint8)
+    a, b = _random_params(w)
+    n = h * w
+    r3 = torch.empty(3 * n, dtype=torch.int16, device=DEV)
+    params = dev(codec.params_from_numpy(a, b), torch.int32)
+    native.residual_encode(dev(s3), dev(om3), dev(oe), h, w, 1, params, r3, None)
+    torch.cuda.synchronize()
+    or3, _ = O.residual(om3, O.predict(O.gf(s3), oe, a, b))
+    assert np.array_equal(host(r3, np.int16).reshape(3, h, w), or3)
+
+
 def _random_params(seed):
     rng = np.random.default_rng(seed)
     return (rng.uniform(-0.2, 0.2, (3, 256)).astype(np.float32),
