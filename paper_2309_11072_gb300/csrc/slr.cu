@@ -1638,8 +1638,8 @@ __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const Tile
                 }
                 if (lc.inside) {
                     uint4* o4 = reinterpret_cast<uint4*>(A.out + pix);
-                    o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
-                    o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                    __stcs(o4, make_uint4(word[0], word[1], word[2], word[3]));   // streaming stores: the codec never reads its decoded words back
+                    __stcs(o4 + 1, make_uint4(word[4], word[5], word[6], word[7]));
                 }
             }
             C.release_s(lane);
@@ -2168,8 +2168,8 @@ __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, cons
                 uint32_t* out = A.outb + T.px + pix;
                 if (lc.full) {
                     uint4* o4 = reinterpret_cast<uint4*>(out);
-                    o4[0] = make_uint4(word[0], word[1], word[2], word[3]);
-                    o4[1] = make_uint4(word[4], word[5], word[6], word[7]);
+                    __stcs(o4, make_uint4(word[0], word[1], word[2], word[3]));   // streaming stores: the codec never reads its decoded words back
+                    __stcs(o4 + 1, make_uint4(word[4], word[5], word[6], word[7]));
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
