@@ -78,18 +78,18 @@ __device__ __forceinline__ void idct8(const int (&F)[8], int (&x)[8], int r) {
 }
 
 // 8-bit display value: #{k in 1..255 : v >= gamma[k]} for the increasing
-// threshold table (v >= 0).  The float bits of v pick a bucket (exponent and
-// top 7 mantissa bits over [2^-20, 1), plus one bucket below and one above;
-// the clamp to those is one min-then-max-with-zero instruction); a bucket
-// holds at most one threshold, and its word is (count below the bucket) *
-// 2^16 + 2^16 - t, t the low 16 bits of that threshold (2^16 when there is
-// none), so adding the low 16 bits of v's bits carries into bit 16 exactly
-// when they reach t (positive floats order like their bits): the count is
-// one lookup, one addition and one shift.  No branch.
-__device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {   // code = table + 1
-    const int bits = __float_as_int(v);
-    const uint32_t e = code[__vimin_s32_relu(((bits - 0x35800000) >> 16) + 1, 2561) - 1];   // `code` points at bucket 0
-    return (int)((__byte_perm((uint32_t)bits, 0u, 0x4410) + e) >> 16);
+// threshold table (v >= 0, not NaN).  The float bits of v, clamped to the
+// bucket below 2^-20 and the one at 1.0 by a min and a max, pick a bucket by
+// their high half (exponent and top 7 mantissa bits; positive floats order
+// like their bits); a bucket holds at most one threshold, and its word makes
+// (bits + word) >> 16 equal the count below the bucket plus one exactly when
+// the low 16 bits reach that threshold's (the word holds (count - high half)
+// * 2^16 + 2^16 - t, mod 2^32).  One lookup, one addition, one shift; no
+// branch.
+__device__ __forceinline__ int gamma_code(float v, const uint32_t* code) {
+    const int bits = min(max(__float_as_int(v), 0x357F0000), 0x3F800000);
+    const uint32_t e = code[(bits >> 16) - 0x357F];
+    return (int)(((uint32_t)bits + e) >> 16);
 }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src) {
@@ -176,9 +176,9 @@ __device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, 
     float num = E == 0 ? 0.0f : __fmul_rn(wr, p2d);
     if (kWhite) num = __fmul_rn(num, __fadd_rn(1.0f, __fdiv_rn(L, lw2)));
     const float H = __fdiv_rn(num, den);
-    r = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr + 1)), gcode + 1);
-    g = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg + 1)), gcode + 1);
-    b = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb + 1)), gcode + 1);
+    r = gamma_code(__fmul_rn(H, small_int_to_float(2 * mr + 1)), gcode);
+    g = gamma_code(__fmul_rn(H, small_int_to_float(2 * mg + 1)), gcode);
+    b = gamma_code(__fmul_rn(H, small_int_to_float(2 * mb + 1)), gcode);
 }
 
 // The same operator from the biased words 0x4B000000 | m of the three
@@ -188,17 +188,19 @@ __device__ __forceinline__ void tmo_pixel(int mr, int mg, int mb, int E, int J, 
 __device__ __forceinline__ void tmo_pixel_biased(uint32_t br, uint32_t bg, uint32_t bb, int E, int J, float kr,
                                                  float wr, const uint32_t* gcode, int& r, int& g, int& b) {
     const uint32_t yq = 4252u * br + 14304u * bg + 1444u * bb + (10000u - 20000u * 0x4B000000u);
-    int d = E - 137 - J;
-    d = d < -100 ? -100 : (d > 100 ? 100 : d);
-    const float p2d = __int_as_float((127 + d) << 23);      // 2^d, a normal float
+    // 2^d with d = clamp(E - 137 - J, -100, 100) (its exponent field 127 + d);
+    // 0 where E = 0 (the min with E * 256 > 227 acts only there), which makes
+    // L = 0 and the numerator 0, so H = 0 as the operator gives for E = 0
+    const int field = __vimin3_s32(max(E - 10 - J, 27), 227, E << 8);
+    const float p2d = __int_as_float(field << 23);
     const float L = __fmul_rn(__fmul_rn(kr, small_int_to_float((int)yq)), p2d);
     const float den = __fadd_rn(1.0f, L);
-    const float num = E == 0 ? 0.0f : __fmul_rn(wr, p2d);
+    const float num = __fmul_rn(wr, p2d);
     const float H = __fdiv_rn(num, den);
     constexpr float kOdd = 1.0f - 16777216.0f;
-    r = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(br), 2.0f, kOdd)), gcode + 1);
-    g = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(bg), 2.0f, kOdd)), gcode + 1);
-    b = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(bb), 2.0f, kOdd)), gcode + 1);
+    r = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(br), 2.0f, kOdd)), gcode);
+    g = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(bg), 2.0f, kOdd)), gcode);
+    b = gamma_code(__fmul_rn(H, __fmaf_rn(__uint_as_float(bb), 2.0f, kOdd)), gcode);
 }
 
 // Key and quantiser state of one image, as a lane needs it.

@@ -17,12 +17,15 @@ Tables (all built in float64 and rounded once):
                   2561: bucket i - 1 (biased exponent e in 107..126 and top 7
                   mantissa bits) for i = 1 .. 2560, i = 0 for v < 2^-20 and
                   i = 2561 for v >= 1; no such bucket holds more than one
-                  threshold either, and the word is (start << 16) + 0x10000 - t
-                  with start the count of thresholds below the bucket and t the
-                  low 16 bits of the one threshold inside it, or 0x10000 (no
-                  16-bit value reaches it) when there is none; since
+                  threshold either.  Entry i belongs to the float bits whose
+                  high half is 0x357F + i (bits(v) clamped to 0x357F0000 ..
+                  0x3F800000 first), and its word is, mod 2^32,
+                  ((start - 0x357F - i) << 16) + 0x10000 - t, with start the
+                  count of thresholds below the bucket and t the low 16 bits of
+                  the one threshold inside it, or 0x10000 (no 16-bit value
+                  reaches it) when there is none; since
                   (bits(v) & 0xFFFF) + 0x10000 - t < 0x20000, the code of v is
-                  ((bits(v) & 0xFFFF) + word) >> 16 = start + ((bits(v) & 0xFFFF) >= t).
+                  (bits(v) + word) >> 16 = start + ((bits(v) & 0xFFFF) >= t).
 The literals live in the library's device and host code, so no table has to
 be built or copied at run time.
 
@@ -60,18 +63,20 @@ def main():
         assert len(inside) <= 1 and (k == 255 or k + 2 > 255 or gamma[k + 2] >= hi), b
         start.append(k)
     wr = [f32_bits(1800.0 * 2.0 ** (-r / 16.0)) for r in range(16)]
-    def word(start, t):
-        return (start << 16) + 0x10000 - t
+    def word(i, start, t):
+        return (((start - 0x357F - i) << 16) + 0x10000 - t) & 0xFFFFFFFF
 
-    code = [word(0, 0x10000)]
+    code = [word(0, 0, 0x10000)]
     for b in range(20 * 128):
         lo = (107 << 23) + (b << 16)
         hi = lo + (1 << 16)
+        assert lo >> 16 == 0x357F + b + 1
         k = sum(1 for t in gamma[1:] if t < lo)
         inside = [t for t in gamma[1:] if lo <= t < hi]
         assert len(inside) <= 1, b
-        code.append(word(k, (inside[0] & 0xFFFF) if inside else 0x10000))
-    code.append(word(255, 0x10000))
+        code.append(word(b + 1, k, (inside[0] & 0xFFFF) if inside else 0x10000))
+    assert (127 << 23) >> 16 == 0x357F + len(code)
+    code.append(word(len(code), 255, 0x10000))
     def arr(ctype, name, vals, fmt, per_line):
         lines = []
         for i in range(0, len(vals), per_line):

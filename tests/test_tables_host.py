@@ -37,13 +37,13 @@ def test_tables_equal_the_oracles():
 
 
 def _display_code(v: np.ndarray, code: np.ndarray) -> np.ndarray:
-    # the kernel's lookup: bucket from the float bits (clamped to the
-    # below / above buckets), then (low 16 bits + word) >> 16, the bucket's
-    # start plus one where the low bits reach the threshold's
-    bits = np.asarray(v, np.float32).view(np.int32).astype(np.int64)
-    idx = np.clip((bits - 0x35800000) >> 16, -1, 2560) + 1
-    e = code[idx].astype(np.int64)
-    return ((bits & 0xFFFF) + e) >> 16
+    # the kernel's lookup: the float bits clamped to the below / above
+    # buckets, the entry of their high half, then (bits + word) >> 16 mod
+    # 2^32: the bucket's start plus one where the low bits reach the
+    # threshold's
+    bits = np.clip(np.asarray(v, np.float32).view(np.int32).astype(np.int64), 0x357F0000, 0x3F800000)
+    e = code[(bits >> 16) - 0x357F].astype(np.int64)
+    return ((bits + e) & 0xFFFFFFFF) >> 16
 
 
 def test_display_code_lookup_equals_the_threshold_count():
