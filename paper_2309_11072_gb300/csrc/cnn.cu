@@ -109,7 +109,7 @@ struct LayerRef {
 };
 
 // One layer over the tile: input rows HIN (pitch P) -> output rows HOUT =
-// HIN - 2.  `halo` is the output's halo around the 16 x 56 tile; outputs
+// HIN - 2.  `halo` is the output's halo around the 15 x 56 tile; outputs
 // outside the image are the encoded zero (the next layer's zero padding).
 // The last layer writes its clamped values to `mh` (uint8 [3][TH][TW]).
 template <int HIN, int NT, bool LAST>
