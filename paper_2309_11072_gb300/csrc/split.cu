@@ -173,19 +173,30 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
     __syncthreads();
     const int64_t per = (chunks + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, chunks);
+    // the statistic of the current image, added to its pair at each change
+    // of image (the block's chunks are consecutive, so a block changes image
+    // at most a few times)
+    int cur = -1;
+    int64_t s = 0, c = 0;
     for (int64_t k = k0; k < k1; ++k) {
         const int i = batch_image_of(B.split_prefix, B.n, k);
+        if (i != cur) {
+            if (cur >= 0) block_reduce_add(s, c, B.lum_stats + 2 * cur);
+            s = c = 0;
+            cur = i;
+        }
         const BatchImage im = B.img[i];
         const int64_t n = (int64_t)im.h * im.pitch;
         const int64_t w0 = (k - B.split_prefix[i]) * kSplitChunk, w1 = min(w0 + kSplitChunk, n);
         const uint32_t* rgbe = rgbeb + im.px;
         uint8_t* m3 = m3b + 3 * im.px;
         uint8_t* e = eb + im.px;
-        int64_t s = 0, c = 0;
         const bool vec = (n % 4 == 0) && ((uintptr_t)rgbe % 16 == 0) && ((uintptr_t)m3 % 4 == 0) &&
                          ((uintptr_t)e % 4 == 0);
         if (vec) {
-            // a chunk gives a thread at most kSplitChunk / kThreads words: 32-bit parts
+            // a chunk gives a thread kPer 16-byte units, all loaded before the first is used;
+            // 32-bit parts per chunk
+            constexpr int kPer = kSplitChunk / 4 / kThreads;
             static_assert(kSplitChunk / kThreads * (1 << 20) < (1ll << 32), "32-bit statistic parts");
             uint32_t sl = 0, se = 0, cn = 0;
             const uint4* r4 = reinterpret_cast<const uint4*>(rgbe);
@@ -193,18 +204,27 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
             uint32_t* mG = reinterpret_cast<uint32_t*>(m3 + n);
             uint32_t* mB = reinterpret_cast<uint32_t*>(m3 + 2 * n);
             uint32_t* eP = reinterpret_cast<uint32_t*>(e);
-            for (int64_t j = w0 / 4 + threadIdx.x; j < w1 / 4; j += kThreads) {
-                const uint4 v = ld_stream(r4 + j);
-                const uint32_t lo01 = __byte_perm(v.x, v.y, 0x5140), hi01 = __byte_perm(v.x, v.y, 0x7362);
-                const uint32_t lo23 = __byte_perm(v.z, v.w, 0x5140), hi23 = __byte_perm(v.z, v.w, 0x7362);
-                mR[j] = __byte_perm(lo01, lo23, 0x5410);
-                mG[j] = __byte_perm(lo01, lo23, 0x7632);
-                mB[j] = __byte_perm(hi01, hi23, 0x5410);
-                eP[j] = __byte_perm(hi01, hi23, 0x7632);
-                lum4(v, lut, sl, se, cn);
+            uint4 v[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int64_t j = w0 / 4 + threadIdx.x + u * kThreads;
+                v[u] = j < w1 / 4 ? ld_stream(r4 + j) : make_uint4(0u, 0u, 0u, 0u);
             }
-            s = 65536 * ((int64_t)se - 137 * (int64_t)cn) + sl;
-            c = cn;
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int64_t j = w0 / 4 + threadIdx.x + u * kThreads;
+                if (j < w1 / 4) {
+                    const uint32_t lo01 = __byte_perm(v[u].x, v[u].y, 0x5140), hi01 = __byte_perm(v[u].x, v[u].y, 0x7362);
+                    const uint32_t lo23 = __byte_perm(v[u].z, v[u].w, 0x5140), hi23 = __byte_perm(v[u].z, v[u].w, 0x7362);
+                    mR[j] = __byte_perm(lo01, lo23, 0x5410);
+                    mG[j] = __byte_perm(lo01, lo23, 0x7632);
+                    mB[j] = __byte_perm(hi01, hi23, 0x5410);
+                    eP[j] = __byte_perm(hi01, hi23, 0x7632);
+                    lum4(v[u], lut, sl, se, cn);
+                }
+            }
+            s += 65536 * ((int64_t)se - 137 * (int64_t)cn) + sl;
+            c += cn;
         } else {
             for (int64_t j = w0 + threadIdx.x; j < w1; j += kThreads) {
                 const uint32_t wd = __ldg(rgbe + j);
@@ -216,8 +236,8 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
                 c += (wd >> 24) != 0;
             }
         }
-        block_reduce_add(s, c, B.lum_stats + 2 * i);
     }
+    if (cur >= 0) block_reduce_add(s, c, B.lum_stats + 2 * cur);
 }
 
 }  // namespace
