@@ -429,9 +429,13 @@ struct BatchBand {
     int64_t t;          // band of the image, or past its last band
 };
 
-__device__ __forceinline__ BatchBand batch_band(const BatchDev& B, int64_t k, int warp) {
-    const int i = batch_image_of(B.base_prefix, B.n, k);
-    return BatchBand{i, (k - B.base_prefix[i]) * kWarps + warp};
+// Band of CTA task k for this warp; `img` tracks the image of the tasks
+// seen last (they come in increasing order), so a lookup is one compare in
+// the common case.
+__device__ __forceinline__ BatchBand batch_band(const BatchDev& B, int64_t k, int warp, int& img) {
+    if (img < 0) img = batch_image_of(B.base_prefix, B.n, k);
+    while (B.base_prefix[img + 1] <= k) ++img;
+    return BatchBand{img, (k - B.base_prefix[img]) * kWarps + warp};
 }
 
 __device__ __forceinline__ bool batch_fast(const BatchImage& im, const uint8_t* m3b, const uint8_t* eb,
@@ -465,16 +469,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_base_batch(const BatchDev B, in
     const int64_t per = (cta_tasks + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = (int64_t)blockIdx.x * per, k1 = min(k0 + per, cta_tasks);
     if (k0 >= k1) return;
-    int cur = -1, slot = 0;
+    int cur = -1, slot = 0, track = -1;
     BaseKey K;
-    BatchBand b = batch_band(B, k0, warp);
+    BatchBand b = batch_band(B, k0, warp, track);
     bool have = batch_prefetch(B, b, m3b, eb, s3b, lane, &pre[warp][0][0][lane]);
     for (int64_t k = k0; k < k1; ++k) {
         // the next task's band goes out before this one is processed
         BatchBand nb{-1, 0};
         bool next = false;
         if (k + 1 < k1) {
-            nb = batch_band(B, k + 1, warp);
+            nb = batch_band(B, k + 1, warp, track);
             next = batch_prefetch(B, nb, m3b, eb, s3b, lane, &pre[warp][slot ^ 1][0][lane]);
         } else {
             cp_async_commit();   // one group per band, so "all but the newest" is this band's

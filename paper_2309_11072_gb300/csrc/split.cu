@@ -178,8 +178,9 @@ __global__ void __launch_bounds__(kThreads) k_split_batch(const BatchDev B, int6
     // at most a few times)
     int cur = -1;
     int64_t s = 0, c = 0;
+    int i = k0 < k1 ? batch_image_of(B.split_prefix, B.n, k0) : 0;
     for (int64_t k = k0; k < k1; ++k) {
-        const int i = batch_image_of(B.split_prefix, B.n, k);
+        while (B.split_prefix[i + 1] <= k) ++i;   // chunks come in increasing order
         if (i != cur) {
             if (cur >= 0) block_reduce_add(s, c, B.lum_stats + 2 * cur);
             s = c = 0;
