@@ -53,7 +53,7 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
 TRAFFIC = {"slr_fit": {"bytes_per_px": (236632064 + 14152704) / (7680 * 4320), "sha": "722157ed48a41840"},
-           "sdri_base_roundtrip": {"bytes_per_px": (132796928 + 62783744) / (7680 * 4320), "sha": "795882e2dc51c013"}}
+           "sdri_base_roundtrip": {"bytes_per_px": (132826112 + 62897920) / (7680 * 4320), "sha": "db4407c559a0ae81"}}
 # The base round trip is bound by instruction issue, not by memory: its
 # roofline counts the arithmetic operations its definition needs per pixel
 # (tone mapping 24; four 8-point integer DCT passes per channel, 36 butterfly
