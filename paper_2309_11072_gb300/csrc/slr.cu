@@ -1509,7 +1509,11 @@ __device__ __forceinline__ bool fit_consume(const TileSmem<TmaMode::kFit>& L, co
 }
 
 template <bool kGf>
-__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile(const TileArgs A) {
+// The tile kernels hand their argument block by reference to the producer
+// (a separate function): as a grid constant it stays in the parameter bank
+// instead of being copied to each thread's stack, where every read of a field
+// by the consumers would be a local-memory load.
+__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile(const __grid_constant__ TileArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ int gave_up;   // a consumer's wait gave up: the CTA's bins are incomplete
@@ -1651,7 +1655,7 @@ __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const Tile
 // k_rows_tile<kResidual>: R = M - M* and histograms; k_rows_tile<kDecode>:
 // M = R + M*, repacked with E.
 template <TmaMode MODE, bool kGf>
-__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile(const TileArgs A) {
+__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile(const __grid_constant__ TileArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TileSmem<MODE> L = tile_smem<MODE>(dyn);
@@ -2042,7 +2046,7 @@ __device__ __forceinline__ void fit_consume_batch(const TileSmem<TmaMode::kFit>&
 }
 
 template <int kGfMode>
-__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile_batch(const TileBatchArgs A) {
+__global__ void __launch_bounds__(kTileThreads, TileAux<TmaMode::kFit>::kCtas) k_fit_tile_batch(const __grid_constant__ TileBatchArgs A) {
     extern __shared__ __align__(128) char dyn[];
     __shared__ int gave_up;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2188,7 +2192,7 @@ __device__ __forceinline__ void rows_consume_batch(const TileSmem<MODE>& L, cons
 }
 
 template <TmaMode MODE, int kGfMode>
-__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile_batch(const TileBatchArgs A) {
+__global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile_batch(const __grid_constant__ TileBatchArgs A) {
     extern __shared__ __align__(128) char dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const TileSmem<MODE> L = tile_smem<MODE>(dyn);
