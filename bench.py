@@ -52,7 +52,7 @@ BYTES_PER_PX = {"rgbe_split": 8, "sdri_base_roundtrip": 7, "slr_fit": 7, "residu
 # DRAM bytes per pixel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # over one launch, divided by its pixels) with the sha256 of the kernel source the
 # counters were taken on; a changed source reports null.  See profiles/.
-TRAFFIC = {"slr_fit": {"bytes_per_px": (235971584 + 6295040) / (7680 * 4320), "sha": "772597234009771a"},
+TRAFFIC = {"slr_fit": {"bytes_per_px": (235972864 + 6271488) / (7680 * 4320), "sha": "6eb8a3a613e98b85"},
            "sdri_base_roundtrip": {"bytes_per_px": (132826112 + 62897920) / (7680 * 4320), "sha": "db4407c559a0ae81"}}
 # The base round trip is bound by instruction issue, not by memory: its
 # roofline counts the arithmetic operations its definition needs per pixel

@@ -866,16 +866,15 @@ struct RingPos {
 
 struct TileArgs {
     const uint8_t* s3;                       // S planes
-    const void* aux;                         // M planes (fit, residual) or R planes (decode)
+    const void* aux;                         // M planes (fit, residual)
     const uint8_t* e;                        // E plane
     int h, w;
     int gf;
     int64_t total_rows;                      // strips * h
     int max_spins;
-    const slrme_params* params;              // residual / decode
+    const slrme_params* params;              // residual
     int16_t* r3_out;                         // residual
     uint32_t* hist;                          // residual (may be null)
-    uint32_t* out;                           // decode
     unsigned long long* gbins;               // fit
 };
 
@@ -1557,13 +1556,15 @@ static_assert(TileAux<TmaMode::kResidual>::kCtas * (tile_rows_smem<TmaMode::kRes
 static_assert(TileAux<TmaMode::kDecode>::kCtas * (tile_rows_smem<TmaMode::kDecode>() + 1024) <= 228 * 1024,
               "decode CTAs per SM");
 
-// The residual / decoder consumer loop: per row and lane, the new S row moves
-// the filter window (as in the fit), then Eq. (8) per pixel and channel with
-// the region's (a, b) pair from shared memory; R = M - M* is stored (and
-// counted) or M = R + M* is packed with E into the RGBE words.
+// The residual consumer loop: per row and lane, the new S row moves the
+// filter window (as in the fit), then Eq. (8) per pixel and channel with the
+// region's (a, b) pair from shared memory; R = M - M* is stored and counted.
+// (The single-image decoder runs the batch form's row kernel on one image
+// described inline, which was measured faster for it.)
 template <TmaMode MODE, bool kGf>
 __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const TileArgs& A, const float2* ab,
                                              uint32_t* hist, int warp, int lane) {
+    static_assert(MODE == TmaMode::kResidual, "the single-image row kernel is the residual's");
     TileConsumer<MODE> C{L, A.max_spins, {0u}, {0u}};
     const int w = A.w;
     const int64_t n = (int64_t)A.h * w;
@@ -1591,59 +1592,31 @@ __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const Tile
             const uint32_t as = C.a_addr() + kStripCols * warp + 8 * lane;
             const int64_t pix = (int64_t)(T.y0 + j) * w + lc.x0;
             const uint2 ev = lds64(as + TileAux<MODE>::kE);
-            if constexpr (MODE == TmaMode::kResidual) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint32_t X[4];
-                    window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
-                    const uint2 mv = lds64(as + (uint32_t)c * TileAux<MODE>::kPlane);
-                    int rr[8];
+            for (int c = 0; c < 3; ++c) {
+                uint32_t X[4];
+                window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
+                const uint2 mv = lds64(as + (uint32_t)c * TileAux<MODE>::kPlane);
+                int rr[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
-                        // 0x4B000000 | M: the estimate's bias cancels in the difference
-                        const int Mb = (int)__byte_perm(i < 4 ? mv.x : mv.y, 0x4B000000u, 0x7540u | (uint32_t)(i & 3));
-                        const float2 p = ab[c * kNbin + E];
-                        rr[i] = Mb - predict_bits(p.x, p.y, x_biased(X, i));
-                    }
-                    if (lc.inside) {
-                        uint4 v;
-                        v.x = __byte_perm((uint32_t)rr[0], (uint32_t)rr[1], 0x5410);
-                        v.y = __byte_perm((uint32_t)rr[2], (uint32_t)rr[3], 0x5410);
-                        v.z = __byte_perm((uint32_t)rr[4], (uint32_t)rr[5], 0x5410);
-                        v.w = __byte_perm((uint32_t)rr[6], (uint32_t)rr[7], 0x5410);
-                        *reinterpret_cast<uint4*>(A.r3_out + c * n + pix) = v;
-                        if (hist) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
-                        }
-                    }
-                }
-            } else {
-                uint32_t word[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) word[i] = __byte_perm(i < 4 ? ev.x : ev.y, 0u, 0x0444 | ((i & 3) << 12));
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint32_t X[4];
-                    window_x<kGf>(sn, c, lc, Hm[c], H0[c], X);
-                    // R is 2 bytes per pixel: the lane's offset twice
-                    const uint4 v = lds128(as + (uint32_t)c * TileAux<MODE>::kPlane + (kStripCols * warp + 8 * lane));
-                    const uint32_t q4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int rv = (int)(int16_t)((q4[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
-                        const int E = (int)(word[i] >> 24);
-                        const float2 p = ab[c * kNbin + E];
-                        // the low byte of R + (0x4B000000 + M*) is M
-                        const int M = rv + predict_bits(p.x, p.y, x_biased(X, i));
-                        word[i] |= ((uint32_t)M & 255u) << (8 * c);
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    const int E = (int)byte_of(i < 4 ? ev.x : ev.y, i & 3);
+                    // 0x4B000000 | M: the estimate's bias cancels in the difference
+                    const int Mb = (int)__byte_perm(i < 4 ? mv.x : mv.y, 0x4B000000u, 0x7540u | (uint32_t)(i & 3));
+                    const float2 p = ab[c * kNbin + E];
+                    rr[i] = Mb - predict_bits(p.x, p.y, x_biased(X, i));
                 }
                 if (lc.inside) {
-                    uint4* o4 = reinterpret_cast<uint4*>(A.out + pix);
-                    __stcs(o4, make_uint4(word[0], word[1], word[2], word[3]));   // streaming stores: the codec never reads its decoded words back
-                    __stcs(o4 + 1, make_uint4(word[4], word[5], word[6], word[7]));
+                    uint4 v;
+                    v.x = __byte_perm((uint32_t)rr[0], (uint32_t)rr[1], 0x5410);
+                    v.y = __byte_perm((uint32_t)rr[2], (uint32_t)rr[3], 0x5410);
+                    v.z = __byte_perm((uint32_t)rr[4], (uint32_t)rr[5], 0x5410);
+                    v.w = __byte_perm((uint32_t)rr[6], (uint32_t)rr[7], 0x5410);
+                    *reinterpret_cast<uint4*>(A.r3_out + c * n + pix) = v;
+                    if (hist) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) atomicAdd(&hist[c * kNres + rr[i] + 255], 1u);
+                    }
                 }
             }
             C.release_s(lane);
@@ -1652,8 +1625,7 @@ __device__ __forceinline__ void rows_consume(const TileSmem<MODE>& L, const Tile
     }
 }
 
-// k_rows_tile<kResidual>: R = M - M* and histograms; k_rows_tile<kDecode>:
-// M = R + M*, repacked with E.
+// k_rows_tile<kResidual>: R = M - M* and histograms.
 template <TmaMode MODE, bool kGf>
 __global__ void __launch_bounds__(kTileThreads, TileAux<MODE>::kCtas) k_rows_tile(const __grid_constant__ TileArgs A) {
     extern __shared__ __align__(128) char dyn[];
@@ -1709,7 +1681,18 @@ struct TileBatchArgs {
     int16_t* r3b;                // residual planes (residual)
     uint32_t* hist;              // [n_images][3][511] (residual; may be null)
     uint32_t* outb;              // decoded words (decode)
+    // one image described inline (B.img and B.row_prefix null): the
+    // single-image decoder runs these kernels on its dense planes
+    BatchImage one;
+    int64_t one_rows;
 };
+
+__device__ __forceinline__ BatchImage batch_img(const TileBatchArgs& A, int i) {
+    return A.B.img ? A.B.img[i] : A.one;
+}
+__device__ __forceinline__ int64_t batch_prefix(const TileBatchArgs& A, int i) {
+    return A.B.row_prefix ? A.B.row_prefix[i] : (i == 0 ? 0 : A.one_rows);
+}
 
 // A CTA's range of global rows and its current task and image.
 struct BatchRange {
@@ -1726,9 +1709,9 @@ struct BatchRange {
     __device__ __forceinline__ void set(const TileBatchArgs& A, int i, uint32_t elem) {
         img = i;
         // both within one image's rows of the CTA's range, so they fit 32 bits
-        base = (int)(A.B.row_prefix[i] - start);
-        limit = (int)(A.B.row_prefix[i + 1] - start);
-        const BatchImage im = A.B.img[i];
+        base = (int)(batch_prefix(A, i) - start);
+        limit = (int)(batch_prefix(A, i + 1) - start);
+        const BatchImage im = batch_img(A, i);
         h = im.h;
         w = im.w;
         p = im.pitch;
@@ -1744,7 +1727,7 @@ struct BatchRange {
             int i = img;
             do {
                 ++i;
-            } while (A.B.row_prefix[i + 1] - start <= (int64_t)r);
+            } while (batch_prefix(A, i + 1) - start <= (int64_t)r);
             set(A, i, elem);
         }
         const int local = r - base;
@@ -1765,7 +1748,7 @@ __device__ __forceinline__ BatchRange batch_range(const TileBatchArgs& A, uint32
     T.end = (int)((b + 1) * A.total_rows / G - T.start);
     T.img = -1;
     T.base = T.limit = 0;
-    if (T.r < T.end) T.set(A, batch_image_of(A.B.row_prefix, A.B.n, T.start), elem);
+    if (T.r < T.end) T.set(A, A.B.row_prefix ? batch_image_of(A.B.row_prefix, A.B.n, T.start) : 0, elem);
     return T;
 }
 
@@ -2244,16 +2227,16 @@ int tile_smem_attr(K kernel, size_t bytes, bool* set) {
 
 template <TmaMode MODE>
 int launch_rows_tile(const uint8_t* s3, const void* aux, const uint8_t* e, int h, int w, int gf_on,
-                     const slrme_params* P, int16_t* r3_out, uint32_t* hist, uint32_t* out, cudaStream_t s) {
+                     const slrme_params* P, int16_t* r3_out, uint32_t* hist, cudaStream_t s) {
     static bool attr_gf[64], attr_plain[64];
     constexpr size_t smem = tile_rows_smem<MODE>();
     auto kernel = gf_on ? k_rows_tile<MODE, true> : k_rows_tile<MODE, false>;
     int st = tile_smem_attr(kernel, smem, gf_on ? attr_gf : attr_plain);
     if (st != SLRME_OK) return st;
     const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
-    TileArgs A{s3, aux, e, h, w, gf_on, total_rows, kMaxSpins, P, r3_out, hist, out, nullptr};
+    TileArgs A{s3, aux, e, h, w, gf_on, total_rows, kMaxSpins, P, r3_out, hist, nullptr};
     kernel<<<(unsigned)tile_grid(total_rows, 0, TileAux<MODE>::kCtas), kTileThreads, smem, s>>>(A);
-    return cuda_status(MODE == TmaMode::kResidual ? "residual_encode launch" : "residual_decode launch");
+    return cuda_status("residual_encode launch");
 }
 
 int launch_fit_tile(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int h, int w, int gf_on,
@@ -2265,7 +2248,7 @@ int launch_fit_tile(const uint8_t* s3, const uint8_t* m3, const uint8_t* e, int 
     const int64_t total_rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
     // a CTA adds at most kTileFitMaxPixels pixels to its bins
     const int64_t rows_max = kTileFitMaxPixels / kTileCols;
-    TileArgs A{s3, m3, e, h, w, gf_on, total_rows, kMaxSpins, nullptr, nullptr, nullptr, nullptr, bins};
+    TileArgs A{s3, m3, e, h, w, gf_on, total_rows, kMaxSpins, nullptr, nullptr, nullptr, bins};
     kernel<<<(unsigned)tile_grid(total_rows, rows_max, TileAux<TmaMode::kFit>::kCtas), kTileThreads, kTileFitSmem,
              s>>>(A);
     return cuda_status("slr_fit launch");
@@ -2343,17 +2326,33 @@ int launch_residual_encode(const uint8_t* s3, const uint8_t* m3, const uint8_t* 
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)m3 % 8 == 0) &&
                       ((uintptr_t)e % 8 == 0);
     if (tma_eligible(w, {s3, m3, e, r3}))
-        return launch_rows_tile<TmaMode::kResidual>(s3, m3, e, h, w, gf_on, params, r3, hist, nullptr, s);
+        return launch_rows_tile<TmaMode::kResidual>(s3, m3, e, h, w, gf_on, params, r3, hist, s);
     const StripLaunch L = strip_launch(h, w, 2);
     k_residual<<<L.blocks, kThreads, 0, s>>>(s3, m3, e, h, w, gf_on, fast ? 1 : 0, L.rows, params, r3, hist);
     return cuda_status("residual_encode launch");
 }
 
+int launch_decode_one(const TileBatchArgs& A, int64_t rows, int gf_on, cudaStream_t s);
+
 int launch_residual_decode(const uint8_t* s3, const uint8_t* e, const int16_t* r3, int h, int w, int gf_on,
                            const slrme_params* params, uint32_t* rgbe_out, cudaStream_t s) {
     const bool fast = (w % 8 == 0) && ((uintptr_t)s3 % 8 == 0) && ((uintptr_t)e % 8 == 0);
-    if (tma_eligible(w, {s3, e, r3, rgbe_out}))
-        return launch_rows_tile<TmaMode::kDecode>(s3, r3, e, h, w, gf_on, params, nullptr, nullptr, rgbe_out, s);
+    if (tma_eligible(w, {s3, e, r3, rgbe_out})) {
+        // the row-pipeline decoder of the batch form, on one image described inline
+        const int64_t rows = (int64_t)((w + kTileCols - 1) / kTileCols) * h;
+        TileBatchArgs A{};
+        A.s3b = s3;
+        A.auxb = reinterpret_cast<const uint8_t*>(r3);
+        A.eb = e;
+        A.total_rows = rows;
+        A.max_spins = kMaxSpins;
+        A.params = params;
+        A.outb = rgbe_out;
+        A.B.n = 1;
+        A.one = BatchImage{h, w, 0, gf_on, 0, w, 0};
+        A.one_rows = rows;
+        return launch_decode_one(A, rows, gf_on, s);
+    }
     const StripLaunch L = strip_launch(h, w, 2);
     k_decode<<<L.blocks, kThreads, 0, s>>>(s3, e, r3, h, w, gf_on, fast ? 1 : 0, L.rows, params, rgbe_out);
     return cuda_status("residual_decode launch");
@@ -2418,6 +2417,11 @@ int launch_residual_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, con
     if (tile_rows == 0) return SLRME_OK;
     TileBatchArgs A{B, s3, m3, e, tile_rows, kMaxSpins, params, r3, hist, nullptr};
     return rows_batch<TmaMode::kResidual>(A, tile_rows, gf_mode, s);
+}
+
+int launch_decode_one(const TileBatchArgs& A, int64_t rows, int gf_on, cudaStream_t s) {
+    if (rows == 0) return SLRME_OK;
+    return rows_batch<TmaMode::kDecode>(A, rows, gf_on ? 1 : 0, s);
 }
 
 int launch_decode_batch(const BatchDev& B, int64_t tile_rows, int gf_mode, const uint8_t* s3, const uint8_t* e,
